@@ -1,0 +1,213 @@
+"""PyTorch FP64 CPU oracle: the forward render of Eqs. 1-3 written as tensor
+ops, the reconstruction loss, and their exact gradient by autograd.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE: only tests, the smoke check and the
+benchmark's CPU-baseline leg use it; it never imports the CUDA package.
+
+It restates the same definitions as gsr_oracle.c (arXiv 2503.11731 Sec. III-A,
+Eqs. 1-3; compositing rules of the cited 3DGS/2DGS) so that autograd yields
+the derivative of the piecewise-smooth render at a given point: thresholds
+(support, alpha skip, early stop, 0.99 clamp) select branches and contribute
+no derivative of their own.  Every pixel sees every surfel (brute force), so
+it is meant for small images (64x64, a few hundred surfels).
+
+Loss (config of the backward step; 2DGS regularisers, readings in the design doc):
+    L = mean|C - C*|  (over 3 H W)
+      + 0.1  * mean_px( A D - B^2 )          A = sum w, B = sum w z, D = sum w z^2
+        (= 1/2 sum_ij w_i w_j (z_i - z_j)^2, the squared depth distortion)
+      + 0.05 * sum_px m (1 - N . N_d) / (H W)
+        N = sum w n (rendered normal, unnormalised); N_d = normalise(dY x dX)
+        of the back-projected expected depth B/A by central differences at the
+        4 neighbours; m = 1 on interior pixels whose 4 neighbours have A >= 0.5
+        and where |dY x dX| > 0, else 0.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+DT = torch.float64
+
+
+def _quat_to_rot(q):
+    q = q / q.norm(dim=-1, keepdim=True)
+    w, x, y, z = q.unbind(-1)
+    R = torch.stack([
+        1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)
+    return R.reshape(q.shape[:-1] + (3, 3))  # columns t_u, t_v, n
+
+
+def _assoc_legendre(l, m, x):
+    """P_l^m(x) (m >= 0) with the Condon-Shortley phase, by recurrence in l."""
+    pmm = torch.ones_like(x)
+    if m > 0:
+        s = torch.sqrt(torch.clamp((1 - x) * (1 + x), min=0.0))
+        odd = 1.0
+        for _ in range(m):
+            pmm = pmm * (-odd) * s
+            odd += 2.0
+    if l == m:
+        return pmm
+    pm1 = x * (2 * m + 1) * pmm
+    if l == m + 1:
+        return pm1
+    pl = pm1
+    for ll in range(m + 2, l + 1):
+        pl = ((2 * ll - 1) * x * pm1 - (ll + m - 1) * pmm) / (ll - m)
+        pmm, pm1 = pm1, pl
+    return pl
+
+
+def sh_basis(deg, d):
+    """[.., (deg+1)^2] real SH (textbook definition) at unit directions d [..,3]."""
+    ct = d[..., 2].clamp(-1, 1)
+    phi = torch.atan2(d[..., 1], d[..., 0])
+    out = []
+    for l in range(deg + 1):
+        for m in range(-l, l + 1):
+            am = abs(m)
+            K = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+            P = _assoc_legendre(l, am, ct)
+            if m == 0:
+                out.append(K * P)
+            elif m > 0:
+                out.append(math.sqrt(2) * K * torch.cos(m * phi) * P)
+            else:
+                out.append(math.sqrt(2) * K * torch.sin(am * phi) * P)
+    return torch.stack(out, -1)
+
+
+def surfel_tensors(s, requires_grad=False):
+    """FP64 leaf tensors of the surfel parameters of a synth.Surfels."""
+    def t(a):
+        x = torch.tensor(a, dtype=DT)
+        if requires_grad:
+            x.requires_grad_(True)
+        return x
+    return {"pos": t(s.pos), "log_scale": t(s.log_scale), "quat": t(s.quat),
+            "opacity": t(s.opacity), "sh": t(s.sh)}
+
+
+def render_pinhole(p, cam, bg=(0.0, 0.0, 0.0)):
+    """Brute-force FP64 pinhole render of the whole image.
+
+    p: dict of tensors pos [N,3], log_scale [N,2], quat [N,4], opacity [N]
+    (logit), sh [N,K,3].  Returns rgb [H,W,3], A, B, D [H,W], normal [H,W,3],
+    T [H,W].
+    """
+    Wimg, Himg = cam.width, cam.height
+    w2c = torch.tensor(cam.world_to_sensor, dtype=DT)
+    Rs, ts = w2c[:3, :3], w2c[:3, 3]
+    origin = -(Rs.T @ ts)
+    R = _quat_to_rot(p["quat"])
+    s = torch.exp(p["log_scale"])
+    mu = p["pos"]
+    N = mu.shape[0]
+    # Eq. 1: H = [s_u t_u, s_v t_v, mu; 0 0 1] (4x3), W = P4 [R|t]
+    H = torch.zeros(N, 4, 3, dtype=DT)
+    H[:, :3, 0] = s[:, 0:1] * R[:, :, 0]
+    H[:, :3, 1] = s[:, 1:2] * R[:, :, 1]
+    H[:, :3, 2] = mu
+    H[:, 3, 2] = 1.0
+    P4 = torch.tensor([[cam.fx, 0, cam.cx, 0], [0, cam.fy, cam.cy, 0], [0, 0, 1, 0], [0, 0, 1, 0]], dtype=DT)
+    Rt = torch.eye(4, dtype=DT)
+    Rt[:3, :] = w2c[:3, :]
+    WH = (P4 @ Rt) @ H  # [N,4,3]
+    ms = mu @ Rs.T + ts
+    zc = ms[:, 2]
+    keep = zc > cam.near  # centre-depth cull
+    idx = torch.nonzero(keep).flatten()
+    # composite order: centre depth, ties by index (stable sort of index order)
+    order = idx[torch.sort(zc[idx].detach(), stable=True).indices]
+    WH, zc, mu_o, R_o = WH[order], zc[order], mu[order], R[order]
+    o = torch.sigmoid(p["opacity"][order])
+    c = WH[:, 0:2, 2] / WH[:, 2:3, 2]  # projected centre (pixels)
+    # colour from SH at the view direction
+    vd = mu_o - origin
+    vd = vd / vd.norm(dim=-1, keepdim=True)
+    deg = int(round(math.sqrt(p["sh"].shape[1]))) - 1
+    Y = sh_basis(deg, vd)  # [n,K]
+    col = torch.clamp((Y[:, :, None] * p["sh"][order]).sum(1) + 0.5, min=0.0)
+    # normal facing the sensor, camera frame
+    nw = R_o[:, :, 2]
+    flip = ((nw * vd).sum(-1) > 0).to(DT) * -2 + 1
+    nc = (nw * flip[:, None]) @ Rs.T
+
+    ys, xs = torch.meshgrid(torch.arange(Himg, dtype=DT), torch.arange(Wimg, dtype=DT), indexing="ij")
+    px = (xs + 0.5).reshape(-1, 1)
+    py = (ys + 0.5).reshape(-1, 1)
+    # Eq. 3 planes -> k = h_u^T WH, l = h_v^T WH  [P,n,3]
+    k = -WH[None, :, 0, :] + px[:, :, None] * WH[None, :, 3, :]
+    l = -WH[None, :, 1, :] + py[:, :, None] * WH[None, :, 3, :]
+    m = torch.cross(k, l, dim=-1)
+    has = m[..., 2] != 0
+    m2 = torch.where(has, m[..., 2], torch.ones_like(m[..., 2]))
+    u = m[..., 0] / m2
+    v = m[..., 1] / m2
+    zint = WH[None, :, 2, 0] * u + WH[None, :, 2, 1] * v + WH[None, :, 2, 2]
+    rho3 = u * u + v * v
+    v3 = has & (zint > cam.near) & (rho3 <= 9.0)
+    dx = px - c[None, :, 0]
+    dy = py - c[None, :, 1]
+    rholp = (dx * dx + dy * dy) / 0.5
+    vlp = rholp <= 9.0
+    use3 = v3 & (~vlp | (rho3 <= rholp))
+    valid = v3 | vlp
+    rho = torch.where(use3, rho3, torch.where(vlp, rholp, torch.full_like(rholp, 100.0)))
+    G = torch.exp(-0.5 * rho)
+    a = torch.clamp(o[None, :] * G, max=0.99)
+    a = torch.where(valid, a, torch.zeros_like(a))
+    z = torch.where(use3, zint, zc[None, :].expand_as(zint))
+    skip = a < (1.0 / 255.0)
+    a_eff = torch.where(skip, torch.zeros_like(a), a)
+    one_m = 1.0 - a_eff
+    Tb = torch.cumprod(torch.cat([torch.ones_like(one_m[:, :1]), one_m[:, :-1]], 1), 1)  # T before i
+    stop = (~skip) & (Tb.detach() * (1.0 - a.detach()) < 1e-4)
+    stopped = torch.cumsum(stop.to(torch.int64), 1) > 0
+    contrib = (~skip) & (~stopped)
+    wgt = torch.where(contrib, a_eff * Tb, torch.zeros_like(a))
+    Tfin = torch.prod(torch.where(contrib, 1.0 - a_eff, torch.ones_like(a)), 1)
+    A = wgt.sum(1)
+    B = (wgt * z).sum(1)
+    Dz = (wgt * z * z).sum(1)
+    rgb = wgt @ col + Tfin[:, None] * torch.tensor(bg, dtype=DT)[None, :]
+    nrm = wgt @ nc
+    shp = (Himg, Wimg)
+    return {"rgb": rgb.reshape(shp + (3,)), "A": A.reshape(shp), "B": B.reshape(shp),
+            "D": Dz.reshape(shp), "normal": nrm.reshape(shp + (3,)), "T": Tfin.reshape(shp),
+            "n_contrib": contrib.sum(1).reshape(shp)}
+
+
+def loss(out, target_rgb, cam, w_dist=0.1, w_norm=0.05, mask_alpha=0.5):
+    """Reconstruction loss of the backward step (see module docstring)."""
+    rgb, A, B, D, Nr = out["rgb"], out["A"], out["B"], out["D"], out["normal"]
+    Hh, Ww = A.shape
+    l1 = (rgb - target_rgb).abs().mean()
+    dist = (A * D - B * B).mean()
+    Asafe = torch.where(A > 0, A, torch.ones_like(A))
+    Dbar = torch.where(A > 0, B / Asafe, torch.zeros_like(A))
+    ys, xs = torch.meshgrid(torch.arange(Hh, dtype=DT), torch.arange(Ww, dtype=DT), indexing="ij")
+    X = torch.stack([(xs + 0.5 - cam.cx) / cam.fx * Dbar, (ys + 0.5 - cam.cy) / cam.fy * Dbar, Dbar], -1)
+    dX = X[1:-1, 2:] - X[1:-1, :-2]
+    dY = X[2:, 1:-1] - X[:-2, 1:-1]
+    cr = torch.cross(dY, dX, dim=-1)
+    nrm = cr.norm(dim=-1)
+    okA = (A[1:-1, 2:] >= mask_alpha) & (A[1:-1, :-2] >= mask_alpha) & \
+          (A[2:, 1:-1] >= mask_alpha) & (A[:-2, 1:-1] >= mask_alpha)
+    m = okA & (nrm > 0)
+    Nd = cr / torch.where(m, nrm, torch.ones_like(nrm))[..., None]
+    term = torch.where(m, 1.0 - (Nr[1:-1, 1:-1] * Nd).sum(-1), torch.zeros_like(nrm))
+    ncons = term.sum() / (Hh * Ww)
+    return l1 + w_dist * dist + w_norm * ncons, {"l1": l1, "dist": dist, "normal": ncons}
+
+
+def loss_and_grad(s, cam, target_rgb, bg=(0.0, 0.0, 0.0)):
+    """FP64 loss and its exact gradient w.r.t. pos, log_scale, quat, opacity, sh."""
+    p = surfel_tensors(s, requires_grad=True)
+    out = render_pinhole(p, cam, bg)
+    L, parts = loss(out, torch.as_tensor(target_rgb, dtype=DT), cam)
+    L.backward()
+    return float(L.detach()), {k: v.grad.numpy().copy() for k, v in p.items()}, {k: float(v.detach()) for k, v in parts.items()}

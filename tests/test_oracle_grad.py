@@ -1,0 +1,111 @@
+"""Pins of the FP64 gradient oracle (oracle/grad.py).
+
+The gradient oracle is autograd over a tensor restatement of the render; it
+is pinned by central finite differences of the *C* oracle (an independent
+implementation of the same definitions), by an analytic depth-normal case,
+and by the pairwise form of the distortion term.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import grad as OG
+from oracle import render as R
+from paper_2503_11731_gb300 import synth
+
+
+def _small_scene(n=60, seed=21, deg=1):
+    s = synth.plain_scene(n=n, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    K = (deg + 1) ** 2
+    sh = np.concatenate([s.sh.astype(np.float64), rng.normal(0, 0.2, (n, K - 1, 3))], 1)
+    return synth.Surfels(s.pos.astype(np.float64), s.log_scale.astype(np.float64) + 0.8,
+                         s.quat.astype(np.float64), s.opacity.astype(np.float64), sh,
+                         s.intensity.astype(np.float64))
+
+
+def _with(s, name, arr):
+    d = dict(pos=s.pos, log_scale=s.log_scale, quat=s.quat, opacity=s.opacity, sh=s.sh, intensity=s.intensity)
+    d[name] = arr
+    return synth.Surfels(**d)
+
+
+def _c_outputs(s, cam):
+    o = R.render_pinhole(s, cam, bg=(0.1, 0.2, 0.3))
+    return {"rgb": o["rgb"], "A": o["acc"][..., 0], "B": o["acc"][..., 1], "D": o["acc"][..., 2],
+            "normal": o["normal"]}
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_render_vjp_matches_fd_of_c_oracle(seed):
+    """<d(sum r.out)/dp, v> by autograd == central FD of the C oracle along v."""
+    s = _small_scene(seed=seed)
+    cam = synth.plain_camera(32, 24, 24.0)
+    rng = np.random.default_rng(seed + 100)
+    outs = _c_outputs(s, cam)
+    weights = {k: rng.normal(size=v.shape) for k, v in outs.items()}
+    weights["B"] *= 0.05
+    weights["D"] *= 0.002
+    p = OG.surfel_tensors(s, requires_grad=True)
+    t = OG.render_pinhole(p, cam, bg=(0.1, 0.2, 0.3))
+    tot = sum((torch.as_tensor(weights[k]) * t[k]).sum() for k in weights)
+    tot.backward()
+    h = 1e-6
+    for name in ("pos", "log_scale", "quat", "opacity", "sh"):
+        v = rng.normal(size=getattr(s, name).shape)
+        base = getattr(s, name)
+        fp = _c_outputs(_with(s, name, base + h * v), cam)
+        fm = _c_outputs(_with(s, name, base - h * v), cam)
+        fd = sum(((weights[k] * (fp[k] - fm[k])).sum() for k in weights)) / (2 * h)
+        ad = float((p[name].grad.numpy() * v).sum())
+        assert ad == pytest.approx(fd, rel=2e-5, abs=1e-6), name
+
+
+def test_loss_gradient_matches_fd():
+    """Full loss (L1 + distortion + normal consistency) through the C render."""
+    s = _small_scene(n=80, seed=31, deg=0)
+    cam = synth.plain_camera(28, 20, 20.0)
+    rng = np.random.default_rng(5)
+    target = rng.uniform(0, 1, (20, 28, 3))
+    L, g, parts = OG.loss_and_grad(s, cam, target, bg=(0.1, 0.2, 0.3))
+    assert parts["normal"] > 0 and parts["dist"] > 0
+
+    def c_loss(ss):
+        o = _c_outputs(ss, cam)
+        out = {"rgb": torch.as_tensor(o["rgb"]), "A": torch.as_tensor(o["A"]), "B": torch.as_tensor(o["B"]),
+               "D": torch.as_tensor(o["D"]), "normal": torch.as_tensor(o["normal"])}
+        return float(OG.loss(out, torch.as_tensor(target), cam)[0])
+    assert c_loss(s) == pytest.approx(L, rel=1e-12)
+    h = 1e-6
+    for name in ("pos", "log_scale", "quat", "opacity", "sh"):
+        v = rng.normal(size=getattr(s, name).shape)
+        base = getattr(s, name)
+        fd = (c_loss(_with(s, name, base + h * v)) - c_loss(_with(s, name, base - h * v))) / (2 * h)
+        ad = float((g[name] * v).sum())
+        assert ad == pytest.approx(fd, rel=1e-4, abs=1e-7), name
+
+
+def test_depth_normal_of_a_tilted_plane():
+    """N_d from central differences of the back-projected depth of a plane
+    n.X = c is the plane normal facing the camera, at every interior pixel,
+    so the normal term is 0 when the rendered normal is that normal (A = 1)."""
+    cam = synth.Pinhole(24, 16, 30.0, 32.0, 12.0, 8.0, np.eye(4), 0.2)
+    n = np.array([0.3, -0.4, -1.0])
+    n /= np.linalg.norm(n)
+    c = -5.0  # plane n.X = c, in front of the camera (n points back at it)
+    ys, xs = np.mgrid[0:16, 0:24]
+    ray = np.stack([(xs + 0.5 - 12.0) / 30.0, (ys + 0.5 - 8.0) / 32.0, np.ones_like(xs, float)], -1)
+    Z = c / (ray @ n)
+    A = torch.ones(16, 24, dtype=torch.float64)
+    out = {"rgb": torch.zeros(16, 24, 3, dtype=torch.float64), "A": A,
+           "B": torch.as_tensor(Z), "D": torch.as_tensor(Z * Z),
+           "normal": torch.as_tensor(np.broadcast_to(n, (16, 24, 3)).copy())}
+    L, parts = OG.loss(out, torch.zeros(16, 24, 3, dtype=torch.float64), cam)
+    assert float(parts["normal"]) == pytest.approx(0.0, abs=1e-12)
+    assert float(parts["dist"]) == pytest.approx(0.0, abs=1e-9)
+    # with the opposite rendered normal every interior pixel costs 2
+    out["normal"] = -out["normal"]
+    _, parts = OG.loss(out, torch.zeros(16, 24, 3, dtype=torch.float64), cam)
+    assert float(parts["normal"]) == pytest.approx(2.0 * 14 * 22 / (16 * 24), rel=1e-12)

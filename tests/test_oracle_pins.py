@@ -1,0 +1,369 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms of Eqs. 1-3/5 for simple geometry, an independent ray-plane
+derivation of the Eq. 2 solution, quadrature of the SH basis, compositing
+identities, and the LiDAR/pinhole special case.  A dropped term, a wrong sign
+or a transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import grad as OG
+from oracle import render as R
+from paper_2503_11731_gb300 import synth
+
+
+def _one(pos, log_scale, quat, opacity, rgb=(0.2, 0.5, 0.9), intensity=0.7):
+    return synth.Surfels(np.asarray([pos], np.float64), np.asarray([log_scale], np.float64),
+                         np.asarray([quat], np.float64), np.asarray([opacity], np.float64),
+                         synth.rgb_to_sh0(np.asarray([rgb], np.float64), np.float64),
+                         np.asarray([intensity], np.float64))
+
+
+def _logit(p):
+    return math.log(p / (1 - p))
+
+
+def _cam(W=33, H=33, f=100.0, pose=None):
+    return synth.Pinhole(W, H, f, f, W / 2.0, H / 2.0, np.eye(4) if pose is None else pose, 0.2)
+
+
+# ---------------------------------------------------------------- SH basis
+def test_sh_basis_orthonormal_by_quadrature():
+    """Real SH to degree 3 are orthonormal on the sphere (Gauss-Legendre x uniform phi)."""
+    xs, ws = np.polynomial.legendre.leggauss(24)
+    phis = np.linspace(0, 2 * np.pi, 48, endpoint=False)
+    dirs, wts = [], []
+    for x, w in zip(xs, ws):
+        st = math.sqrt(1 - x * x)
+        for ph in phis:
+            dirs.append((st * math.cos(ph), st * math.sin(ph), x))
+            wts.append(w * 2 * np.pi / len(phis))
+    lm = [(l, m) for l in range(4) for m in range(-l, l + 1)]
+    Y = np.array([[R.sh_basis(l, m, d) for (l, m) in lm] for d in dirs])
+    G = (Y * np.asarray(wts)[:, None]).T @ Y
+    assert np.abs(G - np.eye(16)).max() < 1e-10
+
+
+def test_sh_basis_low_orders_closed_form():
+    d = np.array([0.3, -0.5, 0.81])
+    d /= np.linalg.norm(d)
+    x, y, z = d
+    assert R.sh_basis(0, 0, d) == pytest.approx(0.5 / math.sqrt(math.pi), abs=1e-14)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    assert R.sh_basis(1, 0, d) == pytest.approx(c1 * z, abs=1e-14)
+    assert R.sh_basis(1, 1, d) == pytest.approx(-c1 * x, abs=1e-14)   # Condon-Shortley phase
+    assert R.sh_basis(1, -1, d) == pytest.approx(-c1 * y, abs=1e-14)
+    assert R.sh_basis(2, 0, d) == pytest.approx(math.sqrt(5 / (16 * math.pi)) * (3 * z * z - 1), abs=1e-13)
+    assert R.sh_basis(2, -2, d) == pytest.approx(math.sqrt(15 / (4 * math.pi)) * x * y, abs=1e-13)
+
+
+# ---------------------------------------------------- Eq. 2 intersection
+def _rot(q):
+    q = np.asarray(q, np.float64)
+    q = q / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _ray_plane(o, d, mu, Rm, s):
+    """Direct ray-plane intersection: x = o + t d with n.(x - mu) = 0."""
+    n = Rm[:, 2]
+    t = n @ (mu - o) / (n @ d)
+    x = o + t * d
+    return (Rm[:, 0] @ (x - mu)) / s[0], (Rm[:, 1] @ (x - mu)) / s[1], t, x
+
+
+def test_eq2_pinhole_matches_direct_ray_plane():
+    rng = np.random.default_rng(1)
+    pose = synth.camera_pose((1.0, -2.0, 1.5), 20.0, -5.0)
+    Rc, tc = pose[:3, :3], pose[:3, 3]
+    origin = -Rc.T @ tc
+    cam = (500.0, 480.0, 320.0, 240.0)
+    for _ in range(200):
+        mu = origin + Rc.T @ np.array([rng.uniform(-3, 3), rng.uniform(-2, 2), rng.uniform(4, 30)])
+        q = rng.standard_normal(4)
+        ls = rng.uniform(-2, 0.5, 2)
+        px, py = rng.uniform(0, 640), rng.uniform(0, 480)
+        r = R.intersect(0, mu, ls, q, pose, cam, px, py)
+        # camera ray through the pixel, in world coordinates
+        dc = np.array([(px - cam[2]) / cam[0], (py - cam[3]) / cam[1], 1.0])
+        d = Rc.T @ dc
+        u, v, t, x = _ray_plane(origin, d, mu, _rot(q), np.exp(ls))
+        depth = (Rc @ x + tc)[2]
+        assert r is not None
+        assert np.allclose(r, [u, v, depth], rtol=1e-9, atol=1e-9 * (1 + abs(u) + abs(v)))
+
+
+def test_eq5_lidar_matches_direct_ray_plane():
+    rng = np.random.default_rng(2)
+    pose = synth.lidar_pose((0.3, 0.1, 1.8), 15.0)
+    Rl, tl = pose[:3, :3], pose[:3, 3]
+    origin = -Rl.T @ tl
+    for _ in range(200):
+        az, el = rng.uniform(-np.pi, np.pi), rng.uniform(-0.5, 0.3)
+        dl = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        mu = origin + Rl.T @ (dl * rng.uniform(3, 40) + rng.normal(0, 0.3, 3))
+        q = rng.standard_normal(4)
+        ls = rng.uniform(-2, 0.5, 2)
+        r = R.intersect(1, mu, ls, q, pose, (0, 0, 0, 0), az, el)
+        u, v, t, _ = _ray_plane(origin, Rl.T @ dl, mu, _rot(q), np.exp(ls))
+        assert r is not None
+        assert np.allclose(r, [u, v, t], rtol=1e-9, atol=1e-9 * (1 + abs(u) + abs(v) + abs(t)))
+        # both Eq. 5 planes contain the ray
+        hu = np.array([math.sin(az), -math.cos(az), 0.0])
+        hv = np.array([math.sin(el) * math.cos(az), math.sin(el) * math.sin(az), -math.cos(el)])
+        assert abs(hu @ dl) < 1e-15 and abs(hv @ dl) < 1e-15
+
+
+# ------------------------------------------------------ closed-form weights
+def test_single_surfel_on_axis():
+    """Facing surfel, pixel on its centre ray: u = v = 0, G = 1, alpha = min(0.99, o)."""
+    cam = _cam()
+    for o in (0.3, 0.999):
+        s = _one((0, 0, 10), (0, 0), (1, 0, 0, 0), _logit(o))
+        out = R.render_pinhole(s, cam, pixels=[16 * 33 + 16])
+        a = min(0.99, o)
+        assert out["rgb"][0] == pytest.approx(a * np.array([0.2, 0.5, 0.9]), abs=1e-12)
+        assert out["depth"][0] == pytest.approx(10.0, abs=1e-12)
+        assert out["T"][0] == pytest.approx(1 - a, abs=1e-12)
+        # normal faces the camera: -z in the camera frame
+        assert out["normal"][0] == pytest.approx([0, 0, -a], abs=1e-12)
+
+
+def test_fronto_parallel_analytic_weight():
+    """u = (X - mu_x)/s_u with X = (p_x - c_x) Z / f; G = exp(-(u^2+v^2)/2)."""
+    cam = _cam(W=64, H=48, f=100.0)
+    Z, su, sv, o = 8.0, 0.6, 0.3, 0.8
+    s = _one((0.1, -0.05, Z), (math.log(su), math.log(sv)), (1, 0, 0, 0), _logit(o))
+    out = R.render_pinhole(s, cam)
+    ys, xs = np.mgrid[0:48, 0:64]
+    X = (xs + 0.5 - 32.0) * Z / 100.0
+    Y = (ys + 0.5 - 24.0) * Z / 100.0
+    u, v = (X - 0.1) / su, (Y + 0.05) / sv
+    rho3 = u * u + v * v
+    cxp, cyp = 100 * 0.1 / Z + 32, 100 * -0.05 / Z + 24
+    rholp = ((xs + 0.5 - cxp) ** 2 + (ys + 0.5 - cyp) ** 2) / 0.5
+    rho = np.where(rho3 <= 9, np.where(rholp <= 9, np.minimum(rho3, rholp), rho3), np.where(rholp <= 9, rholp, np.inf))
+    a = np.minimum(0.99, o * np.exp(-0.5 * rho))
+    a = np.where(a >= 1 / 255, a, 0.0)
+    assert np.abs(out["alpha"] - a).max() < 1e-12
+    assert np.abs(out["rgb"][..., 1] - 0.5 * a).max() < 1e-12
+    inside = a > 0
+    # depth: the intersection depth of a fronto-parallel plane is Z everywhere
+    assert np.abs(out["depth"][inside] - Z).max() < 1e-12
+
+
+def test_edge_on_surfel_uses_low_pass_only():
+    """Normal along x: the surfel plane x = 0 contains the camera centre, so
+    every ray off that plane meets it only at depth 0 (< near); the low-pass
+    exp(-|p-c|^2) (sigma^2 = 1/2 px^2) is all that is left.  The principal
+    point is offset by 1/4 px so that no pixel centre lies in the plane."""
+    cam = synth.Pinhole(33, 33, 100.0, 100.0, 16.75, 16.5, np.eye(4), 0.2)
+    q = (math.cos(math.pi / 4), 0, math.sin(math.pi / 4), 0)  # 90 deg about y: normal -> +x
+    o = 0.9
+    s = _one((0, 0, 10), (-1, -1), q, _logit(o))
+    out = R.render_pinhole(s, cam)
+    ys, xs = np.mgrid[0:33, 0:33]
+    d2 = (xs + 0.5 - 16.75) ** 2 + (ys + 0.5 - 16.5) ** 2
+    a = np.where(d2 / 0.5 <= 9, np.minimum(0.99, o * np.exp(-d2)), 0.0)
+    a = np.where(a >= 1 / 255, a, 0)
+    assert a.max() > 0.5
+    assert np.abs(out["alpha"] - a).max() < 1e-12
+    # the low-pass contribution takes the centre depth
+    assert np.abs(out["depth"][a > 0] - 10.0).max() < 1e-12
+
+
+def test_two_surfels_composite_in_depth_order():
+    cam = _cam()
+    o1, o2 = 0.6, 0.7
+    near = _one((0, 0, 5), (0, 0), (1, 0, 0, 0), _logit(o1), rgb=(1, 0, 0))
+    far = _one((0, 0, 9), (0, 0), (1, 0, 0, 0), _logit(o2), rgb=(0, 0, 1))
+    for s in (near.concat(far), far.concat(near)):
+        out = R.render_pinhole(s, cam, pixels=[16 * 33 + 16])
+        assert out["rgb"][0] == pytest.approx([o1, 0, (1 - o1) * o2], abs=1e-12)
+        assert out["depth"][0] == pytest.approx((o1 * 5 + (1 - o1) * o2 * 9) / (o1 + (1 - o1) * o2), abs=1e-12)
+        assert out["T"][0] == pytest.approx((1 - o1) * (1 - o2), abs=1e-12)
+
+
+def test_alpha_skip_and_early_stop_rules():
+    cam = _cam()
+    pix = [16 * 33 + 16]
+    # alpha just below 1/255 is skipped entirely
+    s = _one((0, 0, 5), (0, 0), (1, 0, 0, 0), _logit(1 / 255 * 0.999))
+    out = R.render_pinhole(s, cam, pixels=pix)
+    assert out["alpha"][0] == 0.0 and out["T"][0] == 1.0
+    s = _one((0, 0, 5), (0, 0), (1, 0, 0, 0), _logit(1 / 255 * 1.001))
+    assert R.render_pinhole(s, cam, pixels=pix)["alpha"][0] > 0
+    # a stack of alpha = 0.95: T 1 -> 0.05 -> 2.5e-3 -> 1.25e-4; the 4th would
+    # leave 6.25e-6 < 1e-4, so compositing stops before it
+    stack = None
+    for k in range(6):
+        t = _one((0, 0, 5 + k), (0, 0), (1, 0, 0, 0), _logit(0.95))
+        stack = t if stack is None else stack.concat(t)
+    out = R.render_pinhole(stack, cam, pixels=pix)
+    assert out["n_contrib"][0] == 3
+    assert out["T"][0] == pytest.approx(0.05 ** 3, rel=1e-12)
+
+
+def test_opacity_zero_gives_background():
+    s = synth.plain_scene(n=300, seed=5)
+    s.opacity[:] = -60.0
+    cam = synth.plain_camera(64, 40, 50.0)
+    out = R.render_pinhole(s, cam, bg=(0.25, 0.5, 0.75))
+    assert np.all(out["rgb"] == np.array([0.25, 0.5, 0.75]))
+    assert np.all(out["T"] == 1.0) and np.all(out["alpha"] == 0.0)
+
+
+def test_weights_plus_transmittance_is_one():
+    s = synth.plain_scene(n=600, seed=6)
+    cam = synth.plain_camera(64, 40, 50.0)
+    out = R.render_pinhole(s, cam)
+    assert np.abs(out["alpha"] + out["T"] - 1.0).max() < 1e-12
+    assert out["alpha"].max() > 0.99  # the scene covers the image
+
+
+def test_permutation_invariance_bit_exact():
+    s = synth.plain_scene(n=500, seed=7)
+    cam = synth.plain_camera(48, 32, 40.0)
+    perm = np.random.default_rng(3).permutation(s.n)
+    a = R.render_pinhole(s, cam)
+    b = R.render_pinhole(s.subset(perm), cam)
+    for k in ("rgb", "depth", "normal", "alpha", "T"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+# ------------------------------------------------------------------- LiDAR
+def test_lidar_fronto_plane_range_closed_form():
+    """A big surfel facing the LiDAR at x = 10: range along ray = 10/(cos el cos az)."""
+    lid = synth.Lidar(beams=21, columns=361, el_min_deg=-10, el_max_deg=10, world_to_sensor=np.eye(4))
+    q = (math.cos(math.pi / 4), 0, math.sin(math.pi / 4), 0)  # normal -> +x
+    o = 0.9
+    s = _one((10, 0, 0), (math.log(2.0), math.log(2.0)), q, _logit(o), intensity=0.4)
+    out = R.render_lidar(s, lid)
+    Rm = _rot(q)
+    for i in range(21):
+        for j in range(361):
+            el = math.radians(10 - i)
+            az = math.radians(-180 + (j + 0.5) * 360.0 / 361)
+            d = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+            if d[0] <= 0:
+                continue
+            t = 10.0 / d[0]
+            x = t * d
+            u, v = Rm[:, 0] @ (x - [10, 0, 0]) / 2.0, Rm[:, 1] @ (x - [10, 0, 0]) / 2.0
+            if u * u + v * v > 9:
+                continue
+            a = min(0.99, o * math.exp(-0.5 * (u * u + v * v)))
+            assert out["range"][i, j] == pytest.approx(t, rel=1e-12)
+            assert out["intensity"][i, j] == pytest.approx(0.4 * a, rel=1e-12)
+
+
+def test_lidar_centre_ray_equals_pinhole_centre_pixel():
+    """The LiDAR ray at az = 0, el = 0 and a +x-looking pinhole's centre pixel
+    are the same ray: same weights, range = depth."""
+    rng = np.random.default_rng(4)
+    n = 60
+    pos = np.stack([rng.uniform(4, 20, n), rng.normal(0, 0.3, n), rng.normal(0, 0.3, n)], 1)
+    # roughly fronto-facing (normal near +-x), large enough that G3 always beats the low-pass
+    tilt = rng.uniform(-0.5, 0.5, (n, 2))
+    qs = []
+    for a, b in tilt:
+        R1 = _rot((math.cos(math.pi / 4), 0, math.sin(math.pi / 4), 0))
+        R2 = _rot((math.cos(a / 2), math.sin(a / 2), 0, 0)) @ _rot((math.cos(b / 2), 0, 0, math.sin(b / 2)))
+        Rm = R2 @ R1
+        qs.append(synth._quat_from_frame(Rm[:, 0][None], Rm[:, 1][None], Rm[:, 2][None])[0])
+    q = np.asarray(qs, np.float64)
+    ls = rng.uniform(-0.6, 0.0, (n, 2))
+    op = rng.normal(0, 1, n)
+    inten = rng.uniform(0, 1, n)
+    s = synth.Surfels(pos, ls, q, op, synth.rgb_to_sh0(np.stack([inten] * 3, 1), np.float64), inten)
+    lid = synth.Lidar(beams=21, columns=361, el_min_deg=-10, el_max_deg=10, world_to_sensor=np.eye(4))
+    lo = R.render_lidar(s, lid, rays=[10 * 361 + 180])
+    # camera looking +x: camera x = -y_world, camera y = -z_world, camera z = x_world
+    pose = np.eye(4)
+    pose[:3, :3] = [[0, -1, 0], [0, 0, -1], [1, 0, 0]]
+    f = 1.0 / math.radians(1.0)
+    cam = synth.Pinhole(33, 33, f, f, 16.5, 16.5, pose, 0.2)
+    co = R.render_pinhole(s, cam, pixels=[16 * 33 + 16])
+    assert lo["alpha"][0] > 0.5
+    assert lo["alpha"][0] == pytest.approx(co["alpha"][0], abs=1e-12)
+    assert lo["range"][0] == pytest.approx(co["depth"][0], rel=1e-12)
+    assert lo["intensity"][0] == pytest.approx(co["rgb"][0][0], abs=1e-12)
+
+
+def test_lidar_azimuth_wrap_low_pass():
+    """An edge-on surfel straight behind the sensor (az = +-180 deg) reaches
+    columns on both ends of the range image through the wrapped low-pass."""
+    lid = synth.Lidar(beams=8, columns=360, el_min_deg=-7, el_max_deg=0, world_to_sensor=np.eye(4))
+    # normal along z, centre on the -x axis at el 0 -> the surfel plane contains the rays of row 0
+    s = _one((-10, 0, 0), (-3, -3), (1, 0, 0, 0), _logit(0.9), intensity=1.0)
+    out = R.render_lidar(s, lid)
+    # centre column coordinate: (180 - (-180))/1 - 0.5 = 359.5 -> columns 359 and 0 are 0.5 cells away
+    a = 0.9 * math.exp(-0.25)
+    assert out["intensity"][0, 0] == pytest.approx(a, rel=1e-9)
+    assert out["intensity"][0, 359] == pytest.approx(a, rel=1e-9)
+    assert out["intensity"][0, 180] == 0.0
+
+
+# ---------------------------------------------------------- object placement
+def test_object_pose_equals_pretransformed_surfels():
+    """A rigid object pose (R_o, t_o) renders like surfels moved by hand, with
+    the degree-1 SH coefficients rotated like a vector."""
+    rng = np.random.default_rng(8)
+    n = 80
+    pos = rng.normal(0, 1.0, (n, 3))
+    q = rng.standard_normal((n, 4))
+    ls = rng.uniform(-2, -0.5, (n, 2))
+    op = rng.normal(1, 1, n)
+    sh = rng.normal(0, 0.3, (n, 4, 3))
+    obj = synth.Surfels(pos, ls, q, op, sh, np.zeros(n), np.zeros(n, np.int32))
+    yaw = 0.7
+    Ro = np.array([[math.cos(yaw), -math.sin(yaw), 0], [math.sin(yaw), math.cos(yaw), 0], [0, 0, 1]])
+    to = np.array([0.5, -0.3, 12.0])
+    pose = np.concatenate([Ro, to[:, None]], 1)[None]
+    cam = _cam(W=48, H=40, f=60.0)
+    a = R.render_pinhole(obj, cam, obj_pose=pose)
+    # by hand: mu' = R_o mu + t_o; R' = R_o R; SH l=1 coefficients (Y_1-1,Y_10,Y_11) ~ (-y, z, -x)
+    Rm = np.stack([_rot(qq) for qq in q])
+    Rn = np.einsum("ab,nbc->nac", Ro, Rm)
+    qn = synth._quat_from_frame(Rn[:, :, 0], Rn[:, :, 1], Rn[:, :, 2]).astype(np.float64)
+    shn = sh.copy()
+    vec = np.stack([-sh[:, 3], -sh[:, 1], sh[:, 2]], 1)  # coefficient vector along (x, y, z)
+    vec = np.einsum("ab,nbc->nac", Ro, vec)
+    shn[:, 3], shn[:, 1], shn[:, 2] = -vec[:, 0], -vec[:, 1], vec[:, 2]
+    moved = synth.Surfels(pos @ Ro.T + to, ls, qn, op, shn, np.zeros(n))
+    b = R.render_pinhole(moved, cam)
+    assert np.abs(a["rgb"] - b["rgb"]).max() < 1e-5  # quaternion round trip is float32
+    assert np.abs(a["alpha"] - b["alpha"]).max() < 1e-5
+
+
+# ------------------------------------------------------------ torch oracle
+def test_torch_oracle_matches_c_oracle():
+    """The FP64 tensor restatement used for gradients agrees with the C oracle."""
+    s = synth.plain_scene(n=200, seed=9)
+    s.sh = np.concatenate([s.sh, np.random.default_rng(1).normal(0, 0.2, (200, 15, 3))], 1).astype(np.float32)
+    cam = synth.plain_camera(40, 32, 30.0)
+    c = R.render_pinhole(s, cam, bg=(0.1, 0.2, 0.3))
+    t = OG.render_pinhole(OG.surfel_tensors(s), cam, bg=(0.1, 0.2, 0.3))
+    assert np.abs(t["rgb"].numpy() - c["rgb"]).max() < 1e-10
+    assert np.abs(t["A"].numpy() - c["acc"][..., 0]).max() < 1e-10
+    assert np.abs(t["B"].numpy() - c["acc"][..., 1]).max() < 1e-8
+    assert np.abs(t["D"].numpy() - c["acc"][..., 2]).max() < 1e-7
+    assert np.abs(t["normal"].numpy() - c["normal"]).max() < 1e-10
+    assert np.array_equal(t["n_contrib"].numpy(), c["n_contrib"])
+
+
+def test_distortion_identity():
+    """A D - B^2 = 1/2 sum_ij w_i w_j (z_i - z_j)^2 (the pairwise definition)."""
+    rng = np.random.default_rng(10)
+    w = rng.uniform(0, 0.3, 12)
+    z = rng.uniform(2, 30, 12)
+    pair = 0.5 * sum(w[i] * w[j] * (z[i] - z[j]) ** 2 for i in range(12) for j in range(12))
+    A, B, D = w.sum(), (w * z).sum(), (w * z * z).sum()
+    assert A * D - B * B == pytest.approx(pair, rel=1e-12)

@@ -1,0 +1,250 @@
+/*
+ * gsr.h -- C ABI of the GB300 2D-Gaussian surfel sensor renderer.
+ *
+ * The renderer rasterises 2D Gaussian surfels (arXiv 2503.11731, Sec. III-A,
+ * "Unified Projection Scheme") into pinhole camera frames (RGB, expected
+ * depth, normal) and spinning-LiDAR range images (range, intensity).  A frame
+ * is produced by three calls that enqueue work on a caller stream:
+ *
+ *   gsr_preprocess   surfel -> per-(sensor, surfel) record, screen bound, tile count
+ *   gsr_bin_sort     key duplication, on-device radix sort, tile ranges
+ *   gsr_render_*     per-tile front-to-back compositing
+ *
+ * Conventions (all arrays row-major, float32 unless stated):
+ *   world frame z up.  Camera frame x right, y down, z forward; LiDAR frame
+ *   x forward, y left, z up.  world_to_sensor is a 4x4 rigid transform
+ *   (rows [R|t; 0 0 0 1]).  Pixel (x, y) has centre (x + 0.5, y + 0.5).
+ *   LiDAR row i (beam) has elevation el_max - i (el_max - el_min)/(beams-1);
+ *   column j has azimuth az0 + (j + 0.5) 360/columns degrees.
+ *
+ * Memory: every pointer in a descriptor is DEVICE memory owned by the
+ * caller, unless the field says "host".  The library allocates no device
+ * memory: the caller allocates one workspace of gsr_workspace_size() bytes
+ * (256-byte aligned) and passes it to every call of a frame.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Calls are asynchronous;
+ * argument errors are reported synchronously by the return code, device-side
+ * conditions (key-capacity overflow, a bounded wait that gave up) are written
+ * to a status word in the workspace and read with gsr_read_status().
+ * No call traps or aborts; nothing crosses the ABI as an exception.
+ */
+#ifndef GSR_H
+#define GSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSR_MAX_SENSORS 16
+
+typedef enum {
+    GSR_OK = 0,
+    GSR_ERR_INVALID_ARG = 1,  /* a null pointer, a bad size or an inconsistent descriptor */
+    GSR_ERR_CUDA = 2,         /* a CUDA launch or query failed (see gsr_last_cuda_error)  */
+    GSR_ERR_WORKSPACE = 3,    /* workspace too small or misaligned                        */
+    GSR_ERR_CAPACITY = 4,     /* more tile/surfel pairs than max_dup (device status)      */
+    GSR_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (device status)            */
+    GSR_ERR_UNSUPPORTED = 6   /* e.g. SH degree > 3, a sensor kind not built              */
+} gsr_status;
+
+typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1 } gsr_sensor_kind;
+
+/*
+ * Surfel table, structure of arrays, one row per surfel (Sec. III-A: the
+ * 2DGS attributes {mu, R, S, alpha}; colour from SH; r read as the LiDAR
+ * intensity).  Raw (pre-activation) parameters:
+ *   pos       [n][3]  centre mu (world)
+ *   log_scale [n][2]  s_u = exp(.), s_v = exp(.)
+ *   quat      [n][4]  (w, x, y, z), normalised by the renderer; R = [t_u t_v n]
+ *   opacity   [n]     logit; o = sigmoid(.)
+ *   sh        [n][(sh_degree+1)^2][3]  real SH coefficients (colour = max(0, SH + 0.5))
+ *   intensity [n]     LiDAR intensity in [0,1] (may be NULL: 0)
+ *   obj_id    [n]     int32 rigid-object index, -1 = background (may be NULL)
+ * All arrays 16-byte aligned.
+ */
+typedef struct {
+    int32_t n;
+    int32_t sh_degree; /* 0..3 */
+    const float* pos;
+    const float* log_scale;
+    const float* quat;
+    const float* opacity;
+    const float* sh;
+    const float* intensity;
+    const int32_t* obj_id;
+} gsr_surfels;
+
+/*
+ * Rigid object poses (Sec. III-B, "Gaussian inplacing": a model matrix per
+ * inserted actor): pose[k] = [R_o | t_o] row-major 3x4, DEVICE memory.
+ * A surfel of object k renders with mu' = R_o mu + t_o, R' = R_o R; its SH
+ * is evaluated at the view direction rotated back into the object frame.
+ */
+typedef struct {
+    int32_t n_objects;
+    const float* pose; /* [n_objects][12] */
+} gsr_objects;
+
+/*
+ * Sensor descriptor (host memory).  Pinhole: Eq. 3 planes with the
+ * intrinsics fx, fy, cx, cy.  LiDAR: Eq. 5 planes; width = azimuth columns,
+ * height = beams.  Intersections nearer than `near` (depth for the camera,
+ * distance along the ray for LiDAR) are rejected; surfels whose centre depth
+ * (range) is <= near are culled.
+ */
+typedef struct {
+    int32_t kind;      /* gsr_sensor_kind */
+    int32_t width;     /* pixels, or azimuth columns */
+    int32_t height;    /* pixels, or beams (>= 2) */
+    float fx, fy, cx, cy;
+    float el_min_deg, el_max_deg, az0_deg;
+    float near_plane;
+    float world_to_sensor[16];
+    float bg[3];       /* camera background, composited as bg * T */
+} gsr_sensor;
+
+/* Screen tiling shared by all sensors of a plan (tile_w, tile_h in {8,16,32}). */
+typedef struct {
+    int32_t tile_w, tile_h;
+} gsr_tiling;
+
+/*
+ * A frame plan: sizes and the workspace layout, filled by gsr_plan_init()
+ * on the host (no allocation).  Treat every field as read-only.
+ */
+typedef struct {
+    int32_t n_surfels;
+    int32_t n_sensors;
+    gsr_sensor sensors[GSR_MAX_SENSORS];
+    gsr_tiling tiling;
+    int64_t max_dup;                      /* capacity of tile/surfel pairs        */
+    int32_t tiles_x[GSR_MAX_SENSORS];
+    int32_t tiles_y[GSR_MAX_SENSORS];
+    int32_t tile_base[GSR_MAX_SENSORS + 1]; /* global tile id of each sensor's tile 0 */
+    int32_t sort_ctas;                    /* persistent CTAs of the sort kernels  */
+    uint64_t off[24];                     /* byte offsets of workspace regions    */
+    uint64_t workspace_bytes;
+} gsr_plan;
+
+/*
+ * Per-pixel outputs of a camera (DEVICE, planar [channel][H][W]; any may be
+ * NULL to skip it).  With w_i = alpha_i T_i along the front-to-back order:
+ *   rgb       [3][H][W]  sum w c + T bg
+ *   depth     [H][W]     sum w z / sum w (0 where sum w == 0)
+ *   normal    [3][H][W]  sum w n (camera frame, unnormalised)
+ *   alpha     [H][W]     sum w
+ *   trans     [H][W]     final transmittance T
+ *   depth_acc [2][H][W]  sum w z, sum w z^2 (for the distortion loss)
+ *   n_contrib [H][W]     uint32: tile-list entries walked (for the backward)
+ */
+typedef struct {
+    float* rgb;
+    float* depth;
+    float* normal;
+    float* alpha;
+    float* trans;
+    float* depth_acc;
+    uint32_t* n_contrib;
+} gsr_camera_out;
+
+/*
+ * Per-ray outputs of a LiDAR (DEVICE, [beams][columns]; any may be NULL):
+ *   range = sum w t / sum w (0 where sum w == 0), intensity = sum w r,
+ *   alpha = sum w, trans = final T, n_contrib as for the camera.
+ */
+typedef struct {
+    float* range;
+    float* intensity;
+    float* alpha;
+    float* trans;
+    uint32_t* n_contrib;
+} gsr_lidar_out;
+
+/* ---------------------------------------------------------------- setup */
+
+/* Fill `plan` for n_surfels surfels seen by n_sensors sensors (host only).
+ * max_dup <= 0 picks a default capacity of 64 pairs per (sensor, surfel),
+ * at most 2^31 - 1.  Errors: GSR_ERR_INVALID_ARG, GSR_ERR_UNSUPPORTED. */
+gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr_sensor* sensors,
+                         int32_t n_sensors, const gsr_tiling* tiling, int64_t max_dup);
+
+/* Bytes of device workspace the plan needs (host only). */
+gsr_status gsr_workspace_size(const gsr_plan* plan, size_t* bytes);
+
+/* ---------------------------------------------------------------- frame */
+
+/*
+ * Step (a), Eqs. 1-3 and 5 per (sensor, surfel): world->sensor transform,
+ * near cull, the ray-to-(u,v) transform of Eq. 2 in closed form, the 3-sigma
+ * screen (or angular) bound with the low-pass disc, the tile rectangle and
+ * count, the SH colour and the facing normal.  Clears the status word.
+ * `objects` may be NULL.
+ */
+gsr_status gsr_preprocess(const gsr_plan* plan, const gsr_surfels* surfels, const gsr_objects* objects,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Step (b): compaction of visible records, radix sort of their centre-depth
+ * keys, prefix sum of tile counts, key duplication (tile id, record), stable
+ * radix sort by tile id -- together the stable sort of 64-bit (tile | depth)
+ * keys -- and the [start, end) range of every tile.  More pairs than
+ * max_dup sets GSR_ERR_CAPACITY in the status word (the excess is dropped).
+ */
+gsr_status gsr_bin_sort(const gsr_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Step (c): per-tile front-to-back compositing of camera `sensor` (Eq. 2-3
+ * ray-splat (u,v), low-pass fallback, alpha = min(0.99, o G), skip below
+ * 1/255, stop before T (1 - alpha) < 1e-4).  Surfel batches are staged into
+ * shared memory by bulk async copies.
+ */
+gsr_status gsr_render_camera(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                             int32_t sensor, const gsr_camera_out* out, void* stream);
+
+/* Step (c) for LiDAR `sensor` (Eq. 5 planes over the beam x azimuth tiling). */
+gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                            int32_t sensor, const gsr_lidar_out* out, void* stream);
+
+/*
+ * Copy the device status word to the host (synchronises `stream`).
+ * *device_status receives GSR_OK, GSR_ERR_CAPACITY or GSR_ERR_TIMEOUT;
+ * *n_visible and *n_pairs (may be NULL) the visible records and tile/surfel
+ * pairs of the last gsr_bin_sort.
+ */
+gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t* device_status,
+                           int64_t* n_visible, int64_t* n_pairs, void* stream);
+
+/* Readable name of a status code (static storage). */
+const char* gsr_status_string(gsr_status s);
+
+/* The last CUDA error string seen by this thread's calls ("" if none). */
+const char* gsr_last_cuda_error(void);
+
+/*
+ * sizeof of the ABI structs, for bindings that mirror them (host only):
+ * which = 0 gsr_plan, 1 gsr_sensor, 2 gsr_surfels, 3 gsr_objects,
+ * 4 gsr_camera_out, 5 gsr_lidar_out, 6 gsr_tiling.  Returns 0 for other values.
+ */
+size_t gsr_struct_size(int32_t which);
+
+/* ------------------------------------------------- workspace inspection */
+
+/*
+ * Device pointers into the workspace, for tests and tools (no copy):
+ * which = 0 records (float4 x 5 per (sensor, surfel) slot), 1 tile rects
+ * (ushort4 per slot: tx0, tx1, ty0, ty1; tx1 may exceed tiles_x - 1 for a
+ * LiDAR azimuth wrap), 2 tile counts (uint32 per slot), 3 depth keys
+ * (float bits per slot), 4 sorted pair tile ids (uint32), 5 sorted pair
+ * slots (uint32), 6 tile ranges (uint2 per global tile), 7 visible slots in
+ * depth order (uint32).
+ */
+gsr_status gsr_workspace_region(const gsr_plan* plan, const void* workspace, int32_t which, void** ptr,
+                                size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSR_H */

@@ -1,0 +1,290 @@
+// api.cu -- the extern "C" entry points declared in include/gsr.h.
+//
+// Argument checking, the workspace layout of a plan, and the launches of the
+// preprocess, binning and compositing kernels.  No device allocation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+__global__ void k_preprocess(SensorTable tab, gsr_surfels S, const float* poses, int n_obj, float4* rec,
+                             ushort4* rects, uint32_t* counts, uint32_t* keys);
+cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st);
+cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st);
+
+static thread_local char g_cuda_err[256] = "";
+
+static gsr_status cuda_fail(cudaError_t e)
+{
+    if (e == cudaSuccess) return GSR_OK;
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return GSR_ERR_CUDA;
+}
+
+SensorTable make_sensor_table(const gsr_plan* p)
+{
+    SensorTable t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = p->n_sensors;
+    t.tile_w = p->tiling.tile_w;
+    t.tile_h = p->tiling.tile_h;
+    t.total_tiles = p->tile_base[p->n_sensors];
+    const double deg = 3.14159265358979323846 / 180.0;
+    for (int i = 0; i < p->n_sensors; ++i) {
+        const gsr_sensor& s = p->sensors[i];
+        SensorDev& d = t.s[i];
+        d.kind = s.kind;
+        d.width = s.width;
+        d.height = s.height;
+        d.tiles_x = p->tiles_x[i];
+        d.tiles_y = p->tiles_y[i];
+        d.tile_base = p->tile_base[i];
+        double R[9], tt[3];
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) R[a * 3 + b] = s.world_to_sensor[a * 4 + b];
+            tt[a] = s.world_to_sensor[a * 4 + 3];
+        }
+        for (int k = 0; k < 9; ++k) d.R[k] = (float)R[k];
+        for (int a = 0; a < 3; ++a) d.t[a] = (float)tt[a];
+        for (int b = 0; b < 3; ++b) d.origin[b] = (float)-(R[0 * 3 + b] * tt[0] + R[1 * 3 + b] * tt[1] + R[2 * 3 + b] * tt[2]);
+        d.fx = s.fx; d.fy = s.fy; d.cx = s.cx; d.cy = s.cy;
+        if (s.kind == GSR_SENSOR_LIDAR) {
+            const double del = (double)(s.el_max_deg - s.el_min_deg) * deg / (s.height - 1);
+            const double daz = 2.0 * 3.14159265358979323846 / s.width;
+            d.el_max = (float)(s.el_max_deg * deg);
+            d.d_el = (float)del;
+            d.inv_d_el = (float)(1.0 / del);
+            d.az0 = (float)(s.az0_deg * deg);
+            d.d_az = (float)daz;
+            d.inv_d_az = (float)(1.0 / daz);
+        }
+        d.near_plane = s.near_plane;
+        for (int c = 0; c < 3; ++c) d.bg[c] = s.bg[c];
+    }
+    return t;
+}
+
+}  // namespace gsr
+
+using namespace gsr;
+
+static bool tile_ok(int v) { return v == 8 || v == 16 || v == 32; }
+
+extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr_sensor* sensors,
+                                    int32_t n_sensors, const gsr_tiling* tiling, int64_t max_dup)
+{
+    if (!plan || !sensors || !tiling) return GSR_ERR_INVALID_ARG;
+    if (n_surfels < 0 || n_sensors < 1 || n_sensors > GSR_MAX_SENSORS) return GSR_ERR_INVALID_ARG;
+    if (!tile_ok(tiling->tile_w) || !tile_ok(tiling->tile_h)) return GSR_ERR_UNSUPPORTED;
+    if (tiling->tile_w * tiling->tile_h > 256) return GSR_ERR_UNSUPPORTED;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->n_surfels = n_surfels;
+    plan->n_sensors = n_sensors;
+    plan->tiling = *tiling;
+    const uint64_t slots = (uint64_t)n_surfels * (uint64_t)n_sensors;
+    if (slots >= (1ull << 32)) return GSR_ERR_INVALID_ARG;
+    int64_t base = 0;
+    for (int i = 0; i < n_sensors; ++i) {
+        const gsr_sensor& s = sensors[i];
+        if (s.kind != GSR_SENSOR_PINHOLE && s.kind != GSR_SENSOR_LIDAR) return GSR_ERR_UNSUPPORTED;
+        if (s.width <= 0 || s.height <= 0 || s.width > 65535 || s.height > 65535) return GSR_ERR_INVALID_ARG;
+        if (!(s.near_plane > 0.f)) return GSR_ERR_INVALID_ARG;
+        if (s.kind == GSR_SENSOR_PINHOLE && !(s.fx > 0.f && s.fy > 0.f)) return GSR_ERR_INVALID_ARG;
+        if (s.kind == GSR_SENSOR_LIDAR && (s.height < 2 || !(s.el_max_deg > s.el_min_deg))) return GSR_ERR_INVALID_ARG;
+        plan->sensors[i] = s;
+        plan->tiles_x[i] = (s.width + tiling->tile_w - 1) / tiling->tile_w;
+        plan->tiles_y[i] = (s.height + tiling->tile_h - 1) / tiling->tile_h;
+        plan->tile_base[i] = (int32_t)base;
+        base += (int64_t)plan->tiles_x[i] * plan->tiles_y[i];
+    }
+    if (base >= (1ll << 31)) return GSR_ERR_INVALID_ARG;
+    plan->tile_base[n_sensors] = (int32_t)base;
+    if (max_dup <= 0) {
+        long double d = 64.0L * (long double)slots;
+        max_dup = d > 2147483647.0L ? 2147483647LL : (int64_t)d;
+        if (max_dup < 4096) max_dup = 4096;
+    }
+    if (max_dup > 2147483647LL) return GSR_ERR_INVALID_ARG;
+    plan->max_dup = max_dup;
+    plan->sort_ctas = 4 * 152;
+
+    uint64_t sz[R_END];
+    const uint64_t G = (uint64_t)plan->sort_ctas;
+    sz[R_RECORDS] = slots * kRecordBytes;
+    sz[R_RECTS] = slots * 8;
+    sz[R_COUNTS] = slots * 4;
+    sz[R_DEPTHKEY] = slots * 4;
+    sz[R_PAIR_KEY_A] = sz[R_PAIR_VAL_A] = sz[R_PAIR_KEY_B] = sz[R_PAIR_VAL_B] = (uint64_t)max_dup * 4;
+    sz[R_RANGES] = (uint64_t)base * 8;
+    sz[R_VIS_KEY_A] = sz[R_VIS_VAL_A] = sz[R_VIS_KEY_B] = sz[R_VIS_VAL_B] = slots * 4;
+    sz[R_CNT_SORTED] = slots * 4;
+    sz[R_OFFSETS] = slots * 4;
+    sz[R_HIST] = (uint64_t)kRadix * G * 4;
+    sz[R_PARTIAL] = G * 8 + 64;
+    sz[R_COUNTERS] = C_WORDS * 4;
+    sz[R_SENSOR_OF_TILE] = 64;
+    uint64_t off = 0;
+    for (int r = 0; r < R_END; ++r) {
+        plan->off[r] = off;
+        off += (sz[r] + 255) & ~uint64_t(255);
+    }
+    plan->workspace_bytes = off;
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_workspace_size(const gsr_plan* plan, size_t* bytes)
+{
+    if (!plan || !bytes) return GSR_ERR_INVALID_ARG;
+    *bytes = (size_t)plan->workspace_bytes;
+    return GSR_OK;
+}
+
+static gsr_status check_ws(const gsr_plan* plan, const void* ws, size_t bytes)
+{
+    if (!plan || !ws) return GSR_ERR_INVALID_ARG;
+    if (bytes < plan->workspace_bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return GSR_ERR_WORKSPACE;
+    return GSR_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+extern "C" gsr_status gsr_preprocess(const gsr_plan* plan, const gsr_surfels* surfels, const gsr_objects* objects,
+                                     void* workspace, size_t workspace_bytes, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if (!surfels || surfels->n != plan->n_surfels) return GSR_ERR_INVALID_ARG;
+    if (surfels->sh_degree < 0 || surfels->sh_degree > 3) return GSR_ERR_UNSUPPORTED;
+    if (surfels->n > 0 && (!surfels->pos || !surfels->log_scale || !surfels->quat || !surfels->opacity || !surfels->sh))
+        return GSR_ERR_INVALID_ARG;
+    if (!aligned16(surfels->quat) || !aligned16(surfels->sh) || !aligned16(surfels->log_scale))
+        return GSR_ERR_INVALID_ARG;
+    const float* poses = nullptr;
+    int n_obj = 0;
+    if (objects && objects->n_objects > 0) {
+        if (!objects->pose) return GSR_ERR_INVALID_ARG;
+        poses = objects->pose;
+        n_obj = objects->n_objects;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t* counters = region<uint32_t>(plan, workspace, R_COUNTERS);
+    cudaError_t e = cudaMemsetAsync(counters, 0, C_WORDS * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (surfels->n > 0) {
+        const SensorTable tab = make_sensor_table(plan);
+        dim3 grid((surfels->n + 255) / 256, plan->n_sensors);
+        k_preprocess<<<grid, 256, 0, s>>>(tab, *surfels, poses, n_obj, region<float4>(plan, workspace, R_RECORDS),
+                                          region<ushort4>(plan, workspace, R_RECTS),
+                                          region<uint32_t>(plan, workspace, R_COUNTS),
+                                          region<uint32_t>(plan, workspace, R_DEPTHKEY));
+        e = cudaGetLastError();
+    }
+    return cuda_fail(e);
+}
+
+extern "C" gsr_status gsr_bin_sort(const gsr_plan* plan, void* workspace, size_t workspace_bytes, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    return cuda_fail(bin_sort(plan, workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_render_camera(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                                        int32_t sensor, const gsr_camera_out* out, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
+    if (plan->sensors[sensor].kind != GSR_SENSOR_PINHOLE) return GSR_ERR_INVALID_ARG;
+    FrameOut o{out->rgb, out->depth, out->normal, out->alpha, out->trans, out->depth_acc, out->n_contrib};
+    return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                                       int32_t sensor, const gsr_lidar_out* out, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
+    if (plan->sensors[sensor].kind != GSR_SENSOR_LIDAR) return GSR_ERR_INVALID_ARG;
+    FrameOut o{out->intensity, out->range, nullptr, out->alpha, out->trans, nullptr, out->n_contrib};
+    return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t* device_status,
+                                      int64_t* n_visible, int64_t* n_pairs, void* stream)
+{
+    if (!plan || !workspace || !device_status) return GSR_ERR_INVALID_ARG;
+    uint32_t h[C_WORDS];
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h, region<uint32_t>(plan, workspace, R_COUNTERS), sizeof(h),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *device_status = (int32_t)h[C_STATUS];
+    if (n_visible) *n_visible = h[C_NVIS];
+    if (n_pairs) {
+        unsigned long long want;
+        std::memcpy(&want, &h[C_NDUP_WANT], sizeof(want));
+        *n_pairs = (int64_t)want;
+    }
+    return GSR_OK;
+}
+
+extern "C" const char* gsr_status_string(gsr_status s)
+{
+    switch (s) {
+    case GSR_OK: return "GSR_OK";
+    case GSR_ERR_INVALID_ARG: return "GSR_ERR_INVALID_ARG";
+    case GSR_ERR_CUDA: return "GSR_ERR_CUDA";
+    case GSR_ERR_WORKSPACE: return "GSR_ERR_WORKSPACE";
+    case GSR_ERR_CAPACITY: return "GSR_ERR_CAPACITY";
+    case GSR_ERR_TIMEOUT: return "GSR_ERR_TIMEOUT";
+    case GSR_ERR_UNSUPPORTED: return "GSR_ERR_UNSUPPORTED";
+    }
+    return "GSR_ERR_UNKNOWN";
+}
+
+extern "C" const char* gsr_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" gsr_status gsr_workspace_region(const gsr_plan* plan, const void* workspace, int32_t which, void** ptr,
+                                           size_t* bytes)
+{
+    if (!plan || !workspace || !ptr) return GSR_ERR_INVALID_ARG;
+    const uint64_t slots = (uint64_t)plan->n_surfels * plan->n_sensors;
+    const int pb = sort_result_buffer(tile_sort_passes(plan));
+    const int vb = sort_result_buffer(kDepthSortPasses);
+    int r;
+    uint64_t n;
+    switch (which) {
+    case 0: r = R_RECORDS; n = slots * kRecordBytes; break;
+    case 1: r = R_RECTS; n = slots * 8; break;
+    case 2: r = R_COUNTS; n = slots * 4; break;
+    case 3: r = R_DEPTHKEY; n = slots * 4; break;
+    case 4: r = pb ? R_PAIR_KEY_B : R_PAIR_KEY_A; n = (uint64_t)plan->max_dup * 4; break;
+    case 5: r = pb ? R_PAIR_VAL_B : R_PAIR_VAL_A; n = (uint64_t)plan->max_dup * 4; break;
+    case 6: r = R_RANGES; n = (uint64_t)plan->tile_base[plan->n_sensors] * 8; break;
+    case 7: r = vb ? R_VIS_VAL_B : R_VIS_VAL_A; n = slots * 4; break;
+    default: return GSR_ERR_INVALID_ARG;
+    }
+    *ptr = region<void>(plan, workspace, r);
+    if (bytes) *bytes = (size_t)n;
+    return GSR_OK;
+}
+
+extern "C" size_t gsr_struct_size(int32_t which)
+{
+    switch (which) {
+    case 0: return sizeof(gsr_plan);
+    case 1: return sizeof(gsr_sensor);
+    case 2: return sizeof(gsr_surfels);
+    case 3: return sizeof(gsr_objects);
+    case 4: return sizeof(gsr_camera_out);
+    case 5: return sizeof(gsr_lidar_out);
+    case 6: return sizeof(gsr_tiling);
+    default: return 0;
+    }
+}

@@ -1,0 +1,321 @@
+// preprocess.cu -- per-(sensor, surfel) projection, culling and bounding.
+//
+// Implements the surfel side of Eqs. 1-3 and 5 (arXiv 2503.11731 Sec. III-A)
+// for every (sensor, surfel) slot: the world -> sensor transform of
+// H = [s_u t_u, s_v t_v, mu] (Eq. 1), the closed-form solution operator of
+// Eq. 2 (the adjugate Q of the ray-space matrix, see gsr_internal.cuh), the
+// 3-sigma screen bound of the surfel united with the low-pass disc of the
+// 2DGS fallback, the tile rectangle and count, the SH colour and the normal.
+// One thread per slot; grid.y = sensor.  HBM-bound: 40 B of geometry per
+// surfel and sensor, + the SH coefficients of visible camera slots.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+namespace {
+
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
+__device__ __forceinline__ F3 operator+(F3 a, F3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ F3 operator*(float s, F3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(F3 a, F3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ F3 mat3(const float* M, F3 v)
+{
+    return f3(fmaf(M[0], v.x, fmaf(M[1], v.y, M[2] * v.z)), fmaf(M[3], v.x, fmaf(M[4], v.y, M[5] * v.z)),
+              fmaf(M[6], v.x, fmaf(M[7], v.y, M[8] * v.z)));
+}
+__device__ __forceinline__ F3 mat3T(const float* M, F3 v)
+{
+    return f3(fmaf(M[0], v.x, fmaf(M[3], v.y, M[6] * v.z)), fmaf(M[1], v.x, fmaf(M[4], v.y, M[7] * v.z)),
+              fmaf(M[2], v.x, fmaf(M[5], v.y, M[8] * v.z)));
+}
+
+// Columns t_u, t_v, n of the rotation of quaternion (w, x, y, z) (normalised here).
+__device__ __forceinline__ void quat_frame(float4 q, F3& tu, F3& tv, F3& n)
+{
+    float inv = rsqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, fmaf(q.z, q.z, q.w * q.w))));
+    float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+    tu = f3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    tv = f3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    n = f3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+}
+
+// Real spherical harmonics to degree 3 (Condon-Shortley phase) at unit d,
+// accumulated against coefficients c[K][3]; returns max(0, sum + 0.5).
+__device__ __forceinline__ F3 sh_colour(int deg, const float* __restrict__ c, F3 d)
+{
+    const float x = d.x, y = d.y, z = d.z;
+    float b[16];
+    b[0] = 0.28209479177387814f;
+    int K = 1;
+    if (deg >= 1) {
+        b[1] = -0.4886025119029199f * y;
+        b[2] = 0.4886025119029199f * z;
+        b[3] = -0.4886025119029199f * x;
+        K = 4;
+    }
+    if (deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        b[4] = 1.0925484305920792f * x * y;
+        b[5] = -1.0925484305920792f * y * z;
+        b[6] = 0.31539156525252005f * (2.f * zz - xx - yy);
+        b[7] = -1.0925484305920792f * x * z;
+        b[8] = 0.5462742152960396f * (xx - yy);
+        K = 9;
+        if (deg >= 3) {
+            b[9] = -0.5900435899266435f * y * (3.f * xx - yy);
+            b[10] = 2.890611442640554f * x * y * z;
+            b[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);
+            b[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            b[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
+            b[14] = 1.445305721320277f * z * (xx - yy);
+            b[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
+            K = 16;
+        }
+    }
+    float r = 0.5f, g = 0.5f, bl = 0.5f;
+    if (K == 16) {
+        // 48 coefficients = 12 aligned float4 loads
+        const float4* c4 = reinterpret_cast<const float4*>(c);
+        float cf[48];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 v = __ldg(c4 + k);
+            cf[4 * k] = v.x; cf[4 * k + 1] = v.y; cf[4 * k + 2] = v.z; cf[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r = fmaf(b[k], cf[3 * k], r);
+            g = fmaf(b[k], cf[3 * k + 1], g);
+            bl = fmaf(b[k], cf[3 * k + 2], bl);
+        }
+    } else {
+        for (int k = 0; k < K; ++k) {
+            r = fmaf(b[k], __ldg(c + 3 * k), r);
+            g = fmaf(b[k], __ldg(c + 3 * k + 1), g);
+            bl = fmaf(b[k], __ldg(c + 3 * k + 2), bl);
+        }
+    }
+    return f3(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f));
+}
+
+__device__ __forceinline__ void project(const SensorDev& s, F3 p, float& x, float& y, float& xmin, float& xmax,
+                                        float& ymin, float& ymax)
+{
+    float iz = 1.f / p.z;
+    x = fmaf(s.fx, p.x * iz, s.cx);
+    y = fmaf(s.fy, p.y * iz, s.cy);
+    xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+    ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
+}
+
+// Pixel/cell index range [i0, i1] whose centres (index + off) can fall in [lo, hi].
+__device__ __forceinline__ void index_range(float lo, float hi, float off, int n, int& i0, int& i1)
+{
+    lo = fmaxf(lo - off, -2.f);
+    hi = fminf(hi - off, (float)n + 1.f);
+    i0 = max(0, (int)ceilf(lo));
+    i1 = min(n - 1, (int)floorf(hi));
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels S, const float* __restrict__ poses,
+                                                    int n_obj, float4* __restrict__ rec, ushort4* __restrict__ rects,
+                                                    uint32_t* __restrict__ counts, uint32_t* __restrict__ keys)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int si = blockIdx.y;
+    if (i >= S.n) return;
+    const SensorDev& sd = tab.s[si];
+    const size_t slot = (size_t)si * S.n + i;
+
+    // ---- surfel in world (optional rigid object pose)
+    F3 mu = f3(__ldg(S.pos + 3 * i), __ldg(S.pos + 3 * i + 1), __ldg(S.pos + 3 * i + 2));
+    float4 q = __ldg(reinterpret_cast<const float4*>(S.quat) + i);
+    float2 ls = __ldg(reinterpret_cast<const float2*>(S.log_scale) + i);
+    F3 tu, tv, nw;
+    quat_frame(q, tu, tv, nw);
+    const float* Ro = nullptr;
+    if (S.obj_id != nullptr) {
+        int k = __ldg(S.obj_id + i);
+        if (k >= 0 && k < n_obj) {
+            Ro = poses + 12 * k;
+            float Rm[9] = {__ldg(Ro), __ldg(Ro + 1), __ldg(Ro + 2), __ldg(Ro + 4), __ldg(Ro + 5),
+                           __ldg(Ro + 6), __ldg(Ro + 8), __ldg(Ro + 9), __ldg(Ro + 10)};
+            mu = mat3(Rm, mu) + f3(__ldg(Ro + 3), __ldg(Ro + 7), __ldg(Ro + 11));
+            tu = mat3(Rm, tu);
+            tv = mat3(Rm, tv);
+            nw = mat3(Rm, nw);
+        }
+    }
+    const float su = __expf(ls.x), sv = __expf(ls.y);
+    const F3 ms = mat3(sd.R, mu) + f3(sd.t[0], sd.t[1], sd.t[2]);
+    const F3 a = su * mat3(sd.R, tu);
+    const F3 b = sv * mat3(sd.R, tv);
+
+    uint32_t cnt = 0;
+    ushort4 rect = make_ushort4(0, 0, 0, 0);
+    float zkey;
+    float4 r0, r1, r2;
+    const int TW = tab.tile_w, TH = tab.tile_h;
+
+    if (sd.kind == GSR_SENSOR_PINHOLE) {
+        zkey = ms.z;
+        if (!(ms.z > sd.near_plane)) {
+            counts[slot] = 0;
+            keys[slot] = __float_as_uint(fmaxf(zkey, 0.f));
+            rects[slot] = rect;
+            return;
+        }
+        const float iz = 1.f / ms.z;
+        const float ex = ms.x * iz, ey = ms.y * iz;
+        const float ccx = fmaf(sd.fx, ex, sd.cx), ccy = fmaf(sd.fy, ey, sd.cy);
+        // ray-space matrix about the projected centre (rows: x - c_x z, y - c_y z, z in pixels)
+        const float m00 = sd.fx * fmaf(-ex, a.z, a.x), m01 = sd.fx * fmaf(-ex, b.z, b.x);
+        const float m10 = sd.fy * fmaf(-ey, a.z, a.y), m11 = sd.fy * fmaf(-ey, b.z, b.y);
+        const float m20 = a.z, m21 = b.z;
+        const float det = fmaf(m00, m11, -m01 * m10);
+        // adjugate / z_c (the third column of M is (0, 0, z_c))
+        r0 = make_float4(m11, -m01, 0.f, ccx);
+        r1 = make_float4(-m10, m00, 0.f, ccy);
+        r2 = make_float4(fmaf(m10, m21, -m11 * m20) * iz, fmaf(m01, m20, -m00 * m21) * iz, det * iz, det);
+
+        // 3-sigma bound: the square mu +- 3a +- 3b clipped to z >= near, projected
+        float xmin = ccx - kLowPassRadius, xmax = ccx + kLowPassRadius;
+        float ymin = ccy - kLowPassRadius, ymax = ccy + kLowPassRadius;
+        F3 P[4] = {ms + 3.f * a + 3.f * b, ms + 3.f * a - 3.f * b, ms - 3.f * a - 3.f * b, ms - 3.f * a + 3.f * b};
+        const float zn = sd.near_plane;
+        float px, py;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const F3 A = P[k], B = P[(k + 1) & 3];
+            const bool ia = A.z >= zn, ib = B.z >= zn;
+            if (ia) project(sd, A, px, py, xmin, xmax, ymin, ymax);
+            if (ia != ib) {
+                const float t = (zn - A.z) / (B.z - A.z);
+                F3 C = A + t * (B - A);
+                C.z = zn;
+                project(sd, C, px, py, xmin, xmax, ymin, ymax);
+            }
+        }
+        // one pixel of margin for FP32 rounding
+        int x0, x1, y0, y1;
+        index_range(xmin - 1.f, xmax + 1.f, 0.5f, sd.width, x0, x1);
+        index_range(ymin - 1.f, ymax + 1.f, 0.5f, sd.height, y0, y1);
+        if (x0 <= x1 && y0 <= y1) {
+            rect = make_ushort4(x0 / TW, x1 / TW, y0 / TH, y1 / TH);
+            cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
+        }
+    } else {
+        const float rc = sqrtf(dot(ms, ms));
+        zkey = rc;
+        if (!(rc > sd.near_plane)) {
+            counts[slot] = 0;
+            keys[slot] = __float_as_uint(fmaxf(zkey, 0.f));
+            rects[slot] = rect;
+            return;
+        }
+        // M = [a b ms] (columns), Q = adj(M), det(M)
+        const float m00 = a.x, m01 = b.x, m02 = ms.x;
+        const float m10 = a.y, m11 = b.y, m12 = ms.y;
+        const float m20 = a.z, m21 = b.z, m22 = ms.z;
+        const float q00 = fmaf(m11, m22, -m12 * m21), q01 = fmaf(m02, m21, -m01 * m22), q02 = fmaf(m01, m12, -m02 * m11);
+        const float q10 = fmaf(m12, m20, -m10 * m22), q11 = fmaf(m00, m22, -m02 * m20), q12 = fmaf(m02, m10, -m00 * m12);
+        const float q20 = fmaf(m10, m21, -m11 * m20), q21 = fmaf(m01, m20, -m00 * m21), q22 = fmaf(m00, m11, -m01 * m10);
+        const float det = fmaf(m00, q00, fmaf(m01, q10, m02 * q20));
+        // low-pass centre in cell coordinates (ray (i, j) sits at (j, i))
+        const float rxy = sqrtf(fmaf(ms.x, ms.x, ms.y * ms.y));
+        const float az = atan2f(ms.y, ms.x);
+        const float el = atan2f(ms.z, rxy);
+        float daz = az - sd.az0;
+        daz -= 6.283185307179586f * floorf(daz * 0.15915494309189535f);
+        const float ccol = daz * sd.inv_d_az - 0.5f;
+        const float crow = (sd.el_max - el) * sd.inv_d_el;
+        r0 = make_float4(q00, q01, q02, ccol);
+        r1 = make_float4(q10, q11, q12, crow);
+        r2 = make_float4(q20, q21, q22, det);
+
+        // angular bound of the sphere (radius 3 max(s)) around mu, united with the low-pass disc
+        const float rad = 3.f * fmaxf(su, sv);
+        int i0, i1, tx0, tx1;
+        const int A = sd.width;
+        const int tiles_x = sd.tiles_x;
+        bool full_rows = !(rc > rad * 1.0001f + 1e-6f);
+        bool full_cols = full_rows || !(rxy > rad * 1.0001f + 1e-6f);
+        if (full_rows) {
+            i0 = 0;
+            i1 = sd.height - 1;
+        } else {
+            const float beta = asinf(fminf(rad / rc, 1.f));
+            float lo = fminf((sd.el_max - (el + beta)) * sd.inv_d_el, crow - kLowPassRadius) - 1.f;
+            float hi = fmaxf((sd.el_max - (el - beta)) * sd.inv_d_el, crow + kLowPassRadius) + 1.f;
+            index_range(lo, hi, 0.f, sd.height, i0, i1);
+        }
+        if (full_cols) {
+            tx0 = 0;
+            tx1 = tiles_x - 1;
+        } else {
+            const float gam = asinf(fminf(rad / rxy, 1.f)) * sd.inv_d_az;
+            const float w = fmaxf(gam, kLowPassRadius) + 1.f;
+            const int j0 = (int)ceilf(ccol - w), j1 = (int)floorf(ccol + w);
+            if (j1 - j0 + 1 >= A) {
+                tx0 = 0;
+                tx1 = tiles_x - 1;
+            } else {
+                int j0m = j0 % A;
+                if (j0m < 0) j0m += A;
+                const int j1m = j0m + (j1 - j0);
+                tx0 = j0m / TW;
+                if (j1m < A) {
+                    tx1 = j1m / TW;
+                } else {
+                    const int txw = (j1m - A) / TW;
+                    if (txw >= tx0) { tx0 = 0; tx1 = tiles_x - 1; }
+                    else tx1 = tiles_x + txw;
+                }
+            }
+        }
+        if (i0 <= i1) {
+            rect = make_ushort4(tx0, tx1, i0 / TH, i1 / TH);
+            cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
+        }
+    }
+    counts[slot] = cnt;
+    keys[slot] = __float_as_uint(zkey);
+    rects[slot] = rect;
+    if (cnt == 0) return;
+
+    // ---- appearance
+    const F3 org = f3(sd.origin[0], sd.origin[1], sd.origin[2]);
+    F3 vd = mu - org;
+    const float vlen2 = dot(vd, vd);
+    if (dot(nw, vd) > 0.f) nw = -1.f * nw;
+    const F3 ns = mat3(sd.R, nw);
+    float4 r3;
+    const float o = 1.f / (1.f + __expf(-__ldg(S.opacity + i)));
+    if (sd.kind == GSR_SENSOR_PINHOLE) {
+        vd = rsqrtf(vlen2) * vd;
+        if (Ro != nullptr) {
+            float Rm[9] = {__ldg(Ro), __ldg(Ro + 1), __ldg(Ro + 2), __ldg(Ro + 4), __ldg(Ro + 5),
+                           __ldg(Ro + 6), __ldg(Ro + 8), __ldg(Ro + 9), __ldg(Ro + 10)};
+            vd = mat3T(Rm, vd);
+        }
+        const int K = (S.sh_degree + 1) * (S.sh_degree + 1);
+        const F3 col = sh_colour(S.sh_degree, S.sh + (size_t)i * K * 3, vd);
+        r3 = make_float4(o, col.x, col.y, col.z);
+    } else {
+        r3 = make_float4(o, S.intensity ? __ldg(S.intensity + i) : 0.f, 0.f, 0.f);
+    }
+    float4* R = rec + slot * kRecordF4;
+    R[0] = r0;
+    R[1] = r1;
+    R[2] = r2;
+    R[3] = r3;
+    R[4] = make_float4(ns.x, ns.y, ns.z, zkey);
+}
+
+}  // namespace gsr

@@ -1,0 +1,245 @@
+// render.cu -- per-tile front-to-back compositing (camera and LiDAR).
+//
+// One CTA per screen tile, one thread per pixel (ray).  The tile's sorted
+// list of records is walked in batches of `blockDim.x` records; each batch is
+// staged into shared memory by bulk async copies (one 80-byte cp.async.bulk
+// per record, completing on an mbarrier), double-buffered so the next batch
+// lands while the current one is composited.  Every thread then solves
+// Eq. 2 for its ray against each staged surfel in closed form (q = Q r,
+// (u, v) = (q_0, q_1)/q_2, depth or distance = det/q_2; see
+// gsr_internal.cuh), falls back to the 2DGS screen-space low-pass where it
+// is larger, and composites with alpha = min(0.99, o G), skipping
+// alpha < 1/255 and stopping before T (1 - alpha) < 1e-4.  A warp leaves a
+// batch once all its rays are done (warp vote); the CTA leaves the list once
+// all its rays are done (block vote).
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+struct RayState {
+    float T, A, B, D;
+    float f0, f1, f2;
+    float n0, n1, n2;
+    uint32_t last;
+    bool done;
+};
+
+// Evaluate one staged record for one ray.  Returns false if the surfel does
+// not contribute (outside both supports, or alpha < 1/255).
+template <int KIND>
+__device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float rx, float ry, float d0, float d1,
+                                           float d2, float near_plane, float columns, float& alpha, float& z)
+{
+    const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+    float dx = rx - r0.w, dy = ry - r1.w;
+    float q0, q1, q2;
+    if (KIND == GSR_SENSOR_PINHOLE) {
+        q0 = fmaf(r0.x, dx, r0.y * dy);
+        q1 = fmaf(r1.x, dx, r1.y * dy);
+        q2 = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z));
+    } else {
+        q0 = fmaf(r0.x, d0, fmaf(r0.y, d1, r0.z * d2));
+        q1 = fmaf(r1.x, d0, fmaf(r1.y, d1, r1.z * d2));
+        q2 = fmaf(r2.x, d0, fmaf(r2.y, d1, r2.z * d2));
+        const float half = 0.5f * columns;
+        if (dx >= half) dx -= columns;
+        if (dx < -half) dx += columns;
+    }
+    const float rq = __fdividef(1.f, q2);
+    const float u = q0 * rq, v = q1 * rq;
+    const float zi = r2.w * rq;
+    const float rho3 = fmaf(u, u, v * v);
+    const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
+    const bool v3 = (zi > near_plane) && (rho3 <= kSupport);
+    const bool vlp = rholp <= kSupport;
+    if (!(v3 || vlp)) return false;
+    const bool use3 = v3 && (!vlp || rho3 <= rholp);
+    const float rho = use3 ? rho3 : rholp;
+    const float4 r3 = R[3];
+    alpha = fminf(kAlphaMax, r3.x * __expf(-0.5f * rho));
+    if (alpha < kAlphaMin) return false;
+    z = use3 ? zi : R[4].w;
+    return true;
+}
+
+template <int KIND>
+__device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int tile_h, int local_tile,
+                                            const uint2 range, const float4* __restrict__ rec,
+                                            const uint32_t* __restrict__ pval, const FrameOut& out,
+                                            uint32_t* counters, float4* buf, uint64_t* bars)
+{
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int tx = local_tile % sd.tiles_x, ty = local_tile / sd.tiles_x;
+    const int x = tx * tile_w + tid % tile_w;
+    const int y = ty * tile_h + tid / tile_w;
+    const bool inside = x < sd.width && y < sd.height;
+
+    float rx, ry, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    if (KIND == GSR_SENSOR_PINHOLE) {
+        rx = x + 0.5f;
+        ry = y + 0.5f;
+    } else {
+        rx = (float)x;
+        ry = (float)y;
+        float se, ce, sa, ca;
+        sincosf(sd.el_max - y * sd.d_el, &se, &ce);
+        sincosf(sd.az0 + (x + 0.5f) * sd.d_az, &sa, &ca);
+        d0 = ce * ca;
+        d1 = ce * sa;
+        d2 = se;
+    }
+    RayState s;
+    s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;
+    s.f0 = s.f1 = s.f2 = 0.f;
+    s.n0 = s.n1 = s.n2 = 0.f;
+    s.last = 0;
+    s.done = !inside;
+
+    const uint32_t start = range.x;
+    const int n = (int)(range.y - range.x);
+    const int nb = (n + nthr - 1) / nthr;
+    const float columns = (float)sd.width;
+    const float near_plane = sd.near_plane;
+
+    auto issue = [&](int b) {
+        const int first = b * nthr;
+        const int cnt = min(nthr, n - first);
+        uint64_t* bar = bars + (b & 1);
+        float4* dst = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
+        if (tid < cnt) {
+            const uint32_t slot = pval[start + first + tid];
+            bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
+        }
+    };
+
+    bool ok = true;
+    if (nb > 0) issue(0);
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        if (!mbar_wait_bounded(bars + (b & 1), (b >> 1) & 1, counters)) {
+            ok = false;
+        }
+        const float4* B = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        const int cnt = min(nthr, n - b * nthr);
+        if (ok) {
+            for (int j = 0; j < cnt; ++j) {
+                if (__all_sync(0xffffffffu, s.done)) break;
+                if (s.done) continue;
+                const float4* Rj = B + j * kRecordF4;
+                float alpha, z;
+                if (!splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, near_plane, columns, alpha, z)) continue;
+                const float Tn = s.T * (1.f - alpha);
+                if (Tn < kTMin) {
+                    s.done = true;
+                    continue;
+                }
+                const float w = alpha * s.T;
+                const float4 r3 = Rj[3];
+                s.f0 = fmaf(w, r3.y, s.f0);
+                if (KIND == GSR_SENSOR_PINHOLE) {
+                    s.f1 = fmaf(w, r3.z, s.f1);
+                    s.f2 = fmaf(w, r3.w, s.f2);
+                    const float4 r4 = Rj[4];
+                    s.n0 = fmaf(w, r4.x, s.n0);
+                    s.n1 = fmaf(w, r4.y, s.n1);
+                    s.n2 = fmaf(w, r4.z, s.n2);
+                }
+                s.A += w;
+                const float wz = w * z;
+                s.B += wz;
+                s.D = fmaf(wz, z, s.D);
+                s.T = Tn;
+                s.last = (uint32_t)(b * nthr + j + 1);
+            }
+        }
+        // both votes are block-uniform, so every thread takes the same exit
+        const bool all_done = __syncthreads_and(s.done);
+        const bool any_fail = __syncthreads_or(!ok);
+        if (all_done || any_fail) {
+            // no copy may still be landing in shared memory when the CTA leaves
+            if (b + 1 < nb) mbar_wait_bounded(bars + ((b + 1) & 1), ((b + 1) >> 1) & 1, counters);
+            break;
+        }
+    }
+
+    if (!inside) return;
+    const size_t HW = (size_t)sd.width * sd.height;
+    const size_t pix = (size_t)y * sd.width + x;
+    if (KIND == GSR_SENSOR_PINHOLE) {
+        if (out.color) {
+            out.color[pix] = fmaf(s.T, sd.bg[0], s.f0);
+            out.color[HW + pix] = fmaf(s.T, sd.bg[1], s.f1);
+            out.color[2 * HW + pix] = fmaf(s.T, sd.bg[2], s.f2);
+        }
+        if (out.normal) {
+            out.normal[pix] = s.n0;
+            out.normal[HW + pix] = s.n1;
+            out.normal[2 * HW + pix] = s.n2;
+        }
+    } else {
+        if (out.color) out.color[pix] = s.f0;
+    }
+    if (out.depth) out.depth[pix] = s.A > 0.f ? s.B / s.A : 0.f;
+    if (out.alpha) out.alpha[pix] = s.A;
+    if (out.trans) out.trans[pix] = s.T;
+    if (out.depth_acc) {
+        out.depth_acc[pix] = s.B;
+        out.depth_acc[HW + pix] = s.D;
+    }
+    if (out.n_contrib) out.n_contrib[pix] = s.last;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, const float4* __restrict__ rec,
+                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
+                                                FrameOut out, uint32_t* counters)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
+    const SensorDev& sd = tab.s[sensor];
+    if (threadIdx.x == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int lt = blockIdx.x;
+    render_tile<KIND>(sd, tab.tile_w, tab.tile_h, lt, ranges[sd.tile_base + lt], rec, pval, out, counters, buf, bars);
+}
+
+size_t render_smem_bytes(int threads) { return 128 + 2 * (size_t)threads * kRecordBytes; }
+
+cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st)
+{
+    const SensorTable tab = make_sensor_table(p);
+    const SensorDev& sd = tab.s[sensor];
+    const int threads = tab.tile_w * tab.tile_h;
+    const size_t smem = render_smem_bytes(threads);
+    const int tiles = sd.tiles_x * sd.tiles_y;
+    const float4* rec = region<float4>(p, ws, R_RECORDS);
+    const uint2* ranges = region<uint2>(p, ws, R_RANGES);
+    const int pb = sort_result_buffer(tile_sort_passes(p));
+    const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
+    if (sd.kind == GSR_SENSOR_PINHOLE) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_render<GSR_SENSOR_PINHOLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_render<GSR_SENSOR_LIDAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -1,0 +1,391 @@
+// sort.cu -- binning of (sensor, surfel) records into screen tiles.
+//
+// The order every tile needs is the stable order of the 64-bit keys
+// (global tile id << 32 | float bits of the centre depth) over the pairs
+// emitted in slot order (the tile-splatting order of 3DGS, which the paper
+// cites for splatting surfels onto sensor frames, Sec. II).  It is produced
+// as one LSD radix sort whose depth digits are sorted before duplication:
+//   1. compact the visible slots (tile count > 0), in slot order;
+//   2. LSD radix sort of their 32-bit depth keys (4 passes of 8 bits);
+//   3. exclusive prefix sum of their tile counts in that order;
+//   4. duplication: each visible slot writes (tile id, slot) for every tile
+//      of its rectangle at its offset -- the pairs come out depth-sorted;
+//   5. LSD radix sort of the pairs by tile id (stable: keeps depth order);
+//   6. [start, end) of every tile.
+// Duplication preserves the relative order of the depth-sorted slots, so
+// applying the depth passes before it gives exactly the 64-bit stable sort.
+//
+// All kernels read their item counts from device memory (no host sync);
+// they run on a fixed grid of `sort_ctas` CTAs, each owning a contiguous
+// chunk of the items, which keeps every pass stable and the scan small.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+namespace {
+
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T v, T& total, T* sm /* NT/32 + 1 */)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < NT / 32 ? sm[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) sm[lane] = s;
+    }
+    __syncthreads();
+    const T wp = w > 0 ? sm[w - 1] : T(0);
+    total = sm[NT / 32 - 1];
+    __syncthreads();
+    return wp + x - v;
+}
+
+// Contiguous chunk [b, e) of n items owned by CTA `cta` of `G` (warp-aligned).
+__device__ __forceinline__ void chunk_of(uint64_t n, int cta, int G, uint64_t& b, uint64_t& e)
+{
+    uint64_t per = (n + G - 1) / G;
+    per = (per + 31) & ~uint64_t(31);
+    b = min(n, per * (uint64_t)cta);
+    e = min(n, b + per);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ compaction
+__global__ void __launch_bounds__(256) k_compact_count(const uint32_t* __restrict__ counts, uint64_t n_slots,
+                                                       uint32_t* __restrict__ partial)
+{
+    __shared__ uint32_t sm[9];
+    uint64_t b, e;
+    chunk_of(n_slots, blockIdx.x, gridDim.x, b, e);
+    uint32_t c = 0;
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) c += counts[i] > 0;
+    uint32_t tot;
+    block_exclusive_scan<uint32_t, 256>(c, tot, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Exclusive scan of G partials in place (one CTA); the total goes to *total_out
+// and, if cap_word != nullptr, min(total, cap) to *cap_word (capacity check).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_partials(T* __restrict__ partial, int G, T* __restrict__ total_out,
+                                                        uint32_t* __restrict__ counters, int64_t cap, int cap_word)
+{
+    __shared__ T sm[33];
+    const int per = (G + 1023) / 1024;
+    const int b = threadIdx.x * per, e = min(G, b + per);
+    T s = 0;
+    for (int i = b; i < e; ++i) s += partial[i];
+    T tot;
+    T off = block_exclusive_scan<T, 1024>(s, tot, sm);
+    for (int i = b; i < e; ++i) {
+        T v = partial[i];
+        partial[i] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0) {
+        if (total_out) *total_out = tot;
+        if (cap_word >= 0) {
+            uint64_t t = (uint64_t)tot;
+            counters[cap_word] = (uint32_t)(t < (uint64_t)cap ? t : (uint64_t)cap);
+            if (t > (uint64_t)cap) set_status(counters, GSR_ERR_CAPACITY);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_compact_write(const uint32_t* __restrict__ counts,
+                                                       const uint32_t* __restrict__ depthkey, uint64_t n_slots,
+                                                       const uint32_t* __restrict__ partial,
+                                                       uint32_t* __restrict__ vis_key, uint32_t* __restrict__ vis_val)
+{
+    __shared__ uint32_t sm[9];
+    uint64_t b, e;
+    chunk_of(n_slots, blockIdx.x, gridDim.x, b, e);
+    uint32_t base = partial[blockIdx.x];
+    for (uint64_t t0 = b; t0 < e; t0 += blockDim.x) {
+        const uint64_t i = t0 + threadIdx.x;
+        const uint32_t f = (i < e && counts[i] > 0) ? 1u : 0u;
+        uint32_t tot;
+        const uint32_t r = block_exclusive_scan<uint32_t, 256>(f, tot, sm);
+        if (f) {
+            vis_key[base + r] = depthkey[i];
+            vis_val[base + r] = (uint32_t)i;
+        }
+        base += tot;
+    }
+}
+
+// ------------------------------------------------------------------ radix sort
+// Per-CTA digit histogram of its chunk; hist is digit-major: hist[d * G + cta].
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ n_ptr, int shift,
+                                                             uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kSortThreads / 32][kRadix];
+    const int w = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
+    __syncthreads();
+    uint64_t b, e;
+    chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
+    for (uint64_t i = b + threadIdx.x; i < e; i += kSortThreads) atomicAdd(&h[w][(keys[i] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < kSortThreads / 32; ++k) s += h[k][d];
+        hist[(size_t)d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of the whole digit-major histogram (one CTA).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int n)
+{
+    __shared__ uint32_t sm[33];
+    const int per = (n + 1023) / 1024;
+    const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += hist[i];
+    uint32_t tot;
+    uint32_t off = block_exclusive_scan<uint32_t, 1024>(s, tot, sm);
+    for (int i = b; i < e; ++i) {
+        uint32_t v = hist[i];
+        hist[i] = off;
+        off += v;
+    }
+}
+
+// Stable scatter of one 8-bit digit.  Each CTA walks its chunk in tiles of
+// kSortTile items; warp w of a tile owns items [w*256, w*256+256) and ranks
+// them in lane order with warp match, so the rank order is the input order.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                                const uint32_t* __restrict__ vin,
+                                                                uint32_t* __restrict__ kout,
+                                                                uint32_t* __restrict__ vout,
+                                                                const uint32_t* __restrict__ n_ptr, int shift,
+                                                                const uint32_t* __restrict__ hist)
+{
+    constexpr int NW = kSortThreads / 32;
+    constexpr int SEG = kSortTile / NW;  // items per warp per tile (256)
+    __shared__ uint32_t ks[kSortTile];
+    __shared__ uint32_t vs[kSortTile];
+    __shared__ uint32_t wh[NW][kRadix];
+    __shared__ uint32_t dbase[kRadix];
+    __shared__ uint32_t toff[kRadix];
+    __shared__ uint32_t tcnt[kRadix];
+    __shared__ uint32_t sm[9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t b, e;
+    chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) dbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    for (uint64_t t0 = b; t0 < e; t0 += kSortTile) {
+        const int nt = (int)((e - t0) < (uint64_t)kSortTile ? (e - t0) : (uint64_t)kSortTile);
+        for (int k = threadIdx.x; k < NW * kRadix; k += kSortThreads) (&wh[0][0])[k] = 0;
+        __syncthreads();
+        uint32_t key[SEG / 32], val[SEG / 32], rank[SEG / 32];
+#pragma unroll
+        for (int r = 0; r < SEG / 32; ++r) {
+            const int li = w * SEG + r * 32 + lane;
+            const bool ok = li < nt;
+            key[r] = ok ? kin[t0 + li] : 0u;
+            val[r] = ok ? vin[t0 + li] : 0u;
+            const uint32_t d = (key[r] >> shift) & (kRadix - 1);
+            const uint32_t okm = __ballot_sync(0xffffffffu, ok);
+            const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane) & okm;
+            const int leader = ok ? __ffs(peers) - 1 : lane;
+            uint32_t old = 0;
+            if (ok && lane == leader) {
+                old = wh[w][d];
+                wh[w][d] = old + __popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[r] = old + __popc(peers & lt);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: prefix over warps, tile total
+        uint32_t c = 0;
+        const int d = threadIdx.x;  // kSortThreads == kRadix
+        for (int k = 0; k < NW; ++k) {
+            uint32_t x = wh[k][d];
+            wh[k][d] = c;
+            c += x;
+        }
+        tcnt[d] = c;
+        uint32_t tot;
+        toff[d] = block_exclusive_scan<uint32_t, kSortThreads>(c, tot, sm);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SEG / 32; ++r) {
+            const int li = w * SEG + r * 32 + lane;
+            if (li < nt) {
+                const uint32_t dd = (key[r] >> shift) & (kRadix - 1);
+                const uint32_t pos = toff[dd] + wh[w][dd] + rank[r];
+                ks[pos] = key[r];
+                vs[pos] = val[r];
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nt; k += kSortThreads) {
+            const uint32_t kk = ks[k];
+            const uint32_t dd = (kk >> shift) & (kRadix - 1);
+            const uint32_t g = dbase[dd] + (uint32_t)k - toff[dd];
+            kout[g] = kk;
+            vout[g] = vs[k];
+        }
+        __syncthreads();
+        dbase[d] += tcnt[d];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ duplication
+// Gather the tile counts of the visible slots in depth order; per-CTA sums.
+__global__ void __launch_bounds__(256) k_dup_count(const uint32_t* __restrict__ vis_val,
+                                                   const uint32_t* __restrict__ counts,
+                                                   const uint32_t* __restrict__ n_ptr,
+                                                   uint32_t* __restrict__ cnt_sorted,
+                                                   unsigned long long* __restrict__ partial)
+{
+    __shared__ unsigned long long sm[9];
+    uint64_t b, e;
+    chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
+    unsigned long long s = 0;
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const uint32_t c = counts[vis_val[i]];
+        cnt_sorted[i] = c;
+        s += c;
+    }
+    unsigned long long tot;
+    block_exclusive_scan<unsigned long long, 256>(s, tot, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Each visible slot writes (global tile id, slot) for every tile of its
+// rectangle, row-major, at its prefix-sum offset; pairs beyond max_dup are dropped.
+__global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
+                                                   const uint32_t* __restrict__ vis_val,
+                                                   const uint32_t* __restrict__ cnt_sorted,
+                                                   const uint32_t* __restrict__ n_ptr,
+                                                   const unsigned long long* __restrict__ partial,
+                                                   const ushort4* __restrict__ rects, uint64_t cap,
+                                                   uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
+{
+    __shared__ unsigned long long sm[9];
+    uint64_t b, e;
+    chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
+    unsigned long long base = partial[blockIdx.x];
+    for (uint64_t t0 = b; t0 < e; t0 += blockDim.x) {
+        const uint64_t i = t0 + threadIdx.x;
+        const unsigned long long c = i < e ? cnt_sorted[i] : 0ull;
+        unsigned long long tot;
+        unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(c, tot, sm);
+        if (c > 0 && off < cap) {
+            const uint32_t slot = vis_val[i];
+            const int si = (int)(slot / (uint32_t)n_surfels);
+            const SensorDev& sd = tab.s[si];
+            const ushort4 r = rects[slot];
+            for (int ty = r.z; ty <= r.w; ++ty) {
+                for (int tx = r.x; tx <= r.y; ++tx) {
+                    if (off >= cap) break;
+                    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
+                    pkey[off] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
+                    pval[off] = slot;
+                    ++off;
+                }
+            }
+        }
+        base += tot;
+    }
+}
+
+// [start, end) of each tile in the sorted pair list (ranges pre-zeroed).
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ key,
+                                                     const uint32_t* __restrict__ n_ptr, uint2* __restrict__ ranges)
+{
+    const uint32_t n = *n_ptr;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t t = key[i];
+        if (i == 0 || key[i - 1] != t) ranges[t].x = i;
+        if (i + 1 == n || key[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+// --------------------------------------------------------------- host side
+static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                       const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st)
+{
+    const int G = p->sort_ctas;
+    uint32_t* hist = region<uint32_t>(p, ws, R_HIST);
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = first_shift + ps * kRadixBits;
+        const uint32_t* ki = (ps & 1) ? k1 : k0;
+        const uint32_t* vi = (ps & 1) ? v1 : v0;
+        uint32_t* ko = (ps & 1) ? k0 : k1;
+        uint32_t* vo = (ps & 1) ? v0 : v1;
+        k_radix_hist<<<G, kSortThreads, 0, st>>>(ki, n_ptr, shift, hist);
+        k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * G);
+        k_radix_scatter<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist);
+    }
+}
+
+int tile_sort_passes(const gsr_plan* p)
+{
+    int bits = 1;
+    while ((1ll << bits) < (long long)p->tile_base[p->n_sensors]) ++bits;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
+{
+    const SensorTable tab = make_sensor_table(p);
+    const int G = p->sort_ctas;
+    const uint64_t n_slots = (uint64_t)p->n_surfels * p->n_sensors;
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
+    uint32_t* partial = region<uint32_t>(p, ws, R_PARTIAL);
+    uint32_t* vk[2] = {region<uint32_t>(p, ws, R_VIS_KEY_A), region<uint32_t>(p, ws, R_VIS_KEY_B)};
+    uint32_t* vv[2] = {region<uint32_t>(p, ws, R_VIS_VAL_A), region<uint32_t>(p, ws, R_VIS_VAL_B)};
+    uint32_t* pk[2] = {region<uint32_t>(p, ws, R_PAIR_KEY_A), region<uint32_t>(p, ws, R_PAIR_KEY_B)};
+    uint32_t* pv[2] = {region<uint32_t>(p, ws, R_PAIR_VAL_A), region<uint32_t>(p, ws, R_PAIR_VAL_B)};
+    const uint32_t* counts = region<uint32_t>(p, ws, R_COUNTS);
+
+    // 1. compaction
+    k_compact_count<<<G, 256, 0, st>>>(counts, n_slots, partial);
+    k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(partial, G, counters + C_NVIS, counters, 0, -1);
+    k_compact_write<<<G, 256, 0, st>>>(counts, region<uint32_t>(p, ws, R_DEPTHKEY), n_slots, partial, vk[0], vv[0]);
+    // 2. depth passes
+    radix_sort(p, ws, vk[0], vv[0], vk[1], vv[1], counters + C_NVIS, 0, kDepthSortPasses, st);
+    const int vb = sort_result_buffer(kDepthSortPasses);
+    // 3. offsets (64-bit partials), capacity check
+    unsigned long long* p64 = reinterpret_cast<unsigned long long*>(partial);
+    uint32_t* cnt_sorted = region<uint32_t>(p, ws, R_CNT_SORTED);
+    k_dup_count<<<G, 256, 0, st>>>(vv[vb], counts, counters + C_NVIS, cnt_sorted, p64);
+    k_scan_partials<unsigned long long><<<1, 1024, 0, st>>>(
+        p64, G, reinterpret_cast<unsigned long long*>(counters + C_NDUP_WANT), counters, p->max_dup, C_NDUP);
+    // 4. duplication
+    k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, counters + C_NVIS, p64,
+                                   region<ushort4>(p, ws, R_RECTS), (uint64_t)p->max_dup, pk[0], pv[0]);
+    // 5. tile passes
+    const int tp = tile_sort_passes(p);
+    radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st);
+    const int pb = sort_result_buffer(tp);
+    // 6. tile ranges
+    uint2* ranges = region<uint2>(p, ws, R_RANGES);
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p->tile_base[p->n_sensors], st);
+    k_tile_ranges<<<4 * G, 256, 0, st>>>(pk[pb], counters + C_NDUP, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

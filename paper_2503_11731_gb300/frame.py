@@ -1,0 +1,134 @@
+"""Device buffers and a frame renderer over the C ABI (marshalling only).
+
+PyTorch provides device memory and streams; every step of the render runs in
+libgsr.so.  A `Renderer` owns one plan, its workspace and the per-sensor
+output tensors, and renders a frame with gsr_preprocess -> gsr_bin_sort ->
+gsr_render_camera / gsr_render_lidar on the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import gsr
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class DeviceSurfels:
+    """Surfel table on the device (float32, contiguous, 16-byte aligned rows)."""
+
+    def __init__(self, pos, log_scale, quat, opacity, sh, intensity=None, obj_id=None):
+        self.pos, self.log_scale, self.quat, self.opacity, self.sh = pos, log_scale, quat, opacity, sh
+        self.intensity, self.obj_id = intensity, obj_id
+        for t in (pos, log_scale, quat, opacity, sh):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+
+    @classmethod
+    def from_host(cls, s, device="cuda"):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)
+        return cls(f(s.pos), f(s.log_scale), f(s.quat), f(s.opacity), f(s.sh), f(s.intensity),
+                   None if getattr(s, "obj_id", None) is None else
+                   torch.as_tensor(np.ascontiguousarray(s.obj_id, np.int32), device=device))
+
+    @property
+    def n(self):
+        return int(self.pos.shape[0])
+
+    @property
+    def sh_degree(self):
+        return int(round(self.sh.shape[1] ** 0.5)) - 1
+
+    def struct(self) -> gsr.Surfels:
+        return gsr.Surfels(self.n, self.sh_degree, _ptr(self.pos), _ptr(self.log_scale), _ptr(self.quat),
+                           _ptr(self.opacity), _ptr(self.sh), _ptr(self.intensity), _ptr(self.obj_id))
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Renderer:
+    """One plan (surfel count, sensors, tiling) with its workspace and outputs."""
+
+    def __init__(self, n_surfels, sensors, tile=(16, 16), max_dup=0, bg=(0.0, 0.0, 0.0), device="cuda",
+                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib")):
+        self.descs = list(sensors)
+        self.structs = [gsr.sensor(d, bg) for d in self.descs]
+        self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup)
+        self.ws_bytes = gsr.workspace_size(self.plan)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = ctypes.c_void_p((base + 255) & ~255)
+        self.device = device
+        self.out = []
+        for d in self.descs:
+            H, W = (d.beams, d.columns) if d.kind == "lidar" else (d.height, d.width)
+            o = {}
+            if d.kind == "lidar":
+                for k in ("range", "intensity", "alpha", "trans"):
+                    if k in outputs or k in ("range", "intensity"):
+                        o[k] = torch.zeros(H, W, device=device)
+                if "n_contrib" in outputs:
+                    o["n_contrib"] = torch.zeros(H, W, dtype=torch.int32, device=device)
+            else:
+                if "rgb" in outputs:
+                    o["rgb"] = torch.zeros(3, H, W, device=device)
+                if "normal" in outputs:
+                    o["normal"] = torch.zeros(3, H, W, device=device)
+                for k in ("depth", "alpha", "trans"):
+                    if k in outputs:
+                        o[k] = torch.zeros(H, W, device=device)
+                if "depth_acc" in outputs:
+                    o["depth_acc"] = torch.zeros(2, H, W, device=device)
+                if "n_contrib" in outputs:
+                    o["n_contrib"] = torch.zeros(H, W, dtype=torch.int32, device=device)
+            self.out.append(o)
+
+    def _out_struct(self, i):
+        o = self.out[i]
+        g = lambda k: _ptr(o.get(k))
+        if self.descs[i].kind == "lidar":
+            return gsr.LidarOut(g("range"), g("intensity"), g("alpha"), g("trans"), g("n_contrib"))
+        return gsr.CameraOut(g("rgb"), g("depth"), g("normal"), g("alpha"), g("trans"), g("depth_acc"),
+                             g("n_contrib"))
+
+    def preprocess(self, surfels: DeviceSurfels, objects=None, stream=None):
+        obj = None
+        if objects is not None:
+            obj = gsr.Objects(int(objects.shape[0]), _ptr(objects))
+        gsr.preprocess(self.plan, surfels.struct(), obj, self.ws_ptr, self.ws_bytes, _stream_handle(stream))
+
+    def bin_sort(self, stream=None):
+        gsr.bin_sort(self.plan, self.ws_ptr, self.ws_bytes, _stream_handle(stream))
+
+    def composite(self, sensors=None, stream=None):
+        h = _stream_handle(stream)
+        for i in (range(len(self.descs)) if sensors is None else sensors):
+            if self.descs[i].kind == "lidar":
+                gsr.render_lidar(self.plan, self.ws_ptr, self.ws_bytes, i, self._out_struct(i), h)
+            else:
+                gsr.render_camera(self.plan, self.ws_ptr, self.ws_bytes, i, self._out_struct(i), h)
+
+    def render(self, surfels: DeviceSurfels, objects=None, stream=None):
+        self.preprocess(surfels, objects, stream)
+        self.bin_sort(stream)
+        self.composite(None, stream)
+        return self.out
+
+    def status(self, stream=None):
+        """(device status, visible slots, tile/surfel pairs requested); synchronises."""
+        return gsr.read_status(self.plan, self.ws_ptr, _stream_handle(stream))
+
+    def region(self, which, dtype, count=None):
+        """A workspace region as a tensor view (for tests)."""
+        ptr, nbytes = gsr.workspace_region(self.plan, self.ws_ptr, which)
+        off = ptr - self.ws.data_ptr()
+        itemsize = torch.tensor([], dtype=dtype).element_size()
+        n = nbytes // itemsize if count is None else count
+        return self.ws[off:off + n * itemsize].view(dtype)

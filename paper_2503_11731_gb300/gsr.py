@@ -1,0 +1,191 @@
+"""Thin ctypes binding of the C ABI in include/gsr.h (argument marshalling only).
+
+Every function keeps the C name without the `gsr_` prefix and forwards to
+libgsr.so; all rendering work runs in the library's CUDA kernels.  Loading
+fails loudly (ImportError) when the library is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgsr.so")
+
+MAX_SENSORS = 16
+PINHOLE, LIDAR = 0, 1
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+
+c_i32, c_i64, c_u64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
+
+
+class Surfels(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("sh_degree", c_i32), ("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp),
+                ("opacity", c_vp), ("sh", c_vp), ("intensity", c_vp), ("obj_id", c_vp)]
+
+
+class Objects(ctypes.Structure):
+    _fields_ = [("n_objects", c_i32), ("pose", c_vp)]
+
+
+class Sensor(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("width", c_i32), ("height", c_i32),
+                ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
+                ("el_min_deg", c_f32), ("el_max_deg", c_f32), ("az0_deg", c_f32), ("near_plane", c_f32),
+                ("world_to_sensor", c_f32 * 16), ("bg", c_f32 * 3)]
+
+
+class Tiling(ctypes.Structure):
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("n_surfels", c_i32), ("n_sensors", c_i32), ("sensors", Sensor * MAX_SENSORS),
+                ("tiling", Tiling), ("max_dup", c_i64), ("tiles_x", c_i32 * MAX_SENSORS),
+                ("tiles_y", c_i32 * MAX_SENSORS), ("tile_base", c_i32 * (MAX_SENSORS + 1)),
+                ("sort_ctas", c_i32), ("off", c_u64 * 24), ("workspace_bytes", c_u64)]
+
+
+class CameraOut(ctypes.Structure):
+    _fields_ = [("rgb", c_vp), ("depth", c_vp), ("normal", c_vp), ("alpha", c_vp), ("trans", c_vp),
+                ("depth_acc", c_vp), ("n_contrib", c_vp)]
+
+
+class LidarOut(ctypes.Structure):
+    _fields_ = [("range", c_vp), ("intensity", c_vp), ("alpha", c_vp), ("trans", c_vp), ("n_contrib", c_vp)]
+
+
+_STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling]
+
+# exported symbols and their ctypes signatures (restype, argtypes)
+SIGNATURES = {
+    "gsr_plan_init": (c_i32, [ctypes.POINTER(Plan), c_i32, ctypes.POINTER(Sensor), c_i32,
+                              ctypes.POINTER(Tiling), c_i64]),
+    "gsr_workspace_size": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(ctypes.c_size_t)]),
+    "gsr_preprocess": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(Surfels), ctypes.POINTER(Objects),
+                               c_vp, ctypes.c_size_t, c_vp]),
+    "gsr_bin_sort": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_vp]),
+    "gsr_render_camera": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32,
+                                  ctypes.POINTER(CameraOut), c_vp]),
+    "gsr_render_lidar": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32,
+                                 ctypes.POINTER(LidarOut), c_vp]),
+    "gsr_read_status": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i64),
+                                ctypes.POINTER(c_i64), c_vp]),
+    "gsr_status_string": (ctypes.c_char_p, [c_i32]),
+    "gsr_last_cuda_error": (ctypes.c_char_p, []),
+    "gsr_workspace_region": (c_i32, [ctypes.POINTER(Plan), c_vp, c_i32, ctypes.POINTER(c_vp),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "gsr_struct_size": (ctypes.c_size_t, [c_i32]),
+}
+
+_lib = None
+
+
+class GsrError(RuntimeError):
+    def __init__(self, code, where):
+        msg = f"{where}: {status_string(code)}"
+        if code == ERR_CUDA:
+            msg += f" ({lib().gsr_last_cuda_error().decode()})"
+        super().__init__(msg)
+        self.code = code
+
+
+def lib(path: str = LIB_PATH):
+    """Load libgsr.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libgsr.so not built at {path}; run paper_2503_11731_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        for i, st in enumerate(_STRUCTS):
+            got = L.gsr_struct_size(i)
+            if got != ctypes.sizeof(st):
+                raise ImportError(f"ABI mismatch for {st.__name__}: C {got} B, binding {ctypes.sizeof(st)} B")
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().gsr_status_string(int(code)).decode()
+
+
+def _check(code, where):
+    if code != OK:
+        raise GsrError(code, where)
+
+
+# ----------------------------------------------------------------- structs
+def sensor(desc, bg=(0.0, 0.0, 0.0)) -> Sensor:
+    """Sensor struct from a synth.Pinhole / synth.Lidar-like description."""
+    s = Sensor()
+    if getattr(desc, "kind", "pinhole") == "lidar":
+        s.kind = LIDAR
+        s.width, s.height = int(desc.columns), int(desc.beams)
+        s.el_min_deg, s.el_max_deg, s.az0_deg = float(desc.el_min_deg), float(desc.el_max_deg), float(desc.az0_deg)
+    else:
+        s.kind = PINHOLE
+        s.width, s.height = int(desc.width), int(desc.height)
+        s.fx, s.fy, s.cx, s.cy = float(desc.fx), float(desc.fy), float(desc.cx), float(desc.cy)
+    s.near_plane = float(desc.near)
+    M = np.asarray(desc.world_to_sensor, np.float64).reshape(16)
+    for k in range(16):
+        s.world_to_sensor[k] = float(M[k])
+    for k in range(3):
+        s.bg[k] = float(bg[k])
+    return s
+
+
+def plan_init(n_surfels: int, sensors, tile=(16, 16), max_dup: int = 0) -> Plan:
+    arr = (Sensor * len(sensors))(*sensors)
+    p = Plan()
+    t = Tiling(int(tile[0]), int(tile[1]))
+    _check(lib().gsr_plan_init(ctypes.byref(p), int(n_surfels), arr, len(sensors), ctypes.byref(t), int(max_dup)),
+           "gsr_plan_init")
+    return p
+
+
+def workspace_size(plan: Plan) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().gsr_workspace_size(ctypes.byref(plan), ctypes.byref(n)), "gsr_workspace_size")
+    return int(n.value)
+
+
+def preprocess(plan, surfels: Surfels, objects, ws, ws_bytes, stream):
+    _check(lib().gsr_preprocess(ctypes.byref(plan), ctypes.byref(surfels),
+                                ctypes.byref(objects) if objects is not None else None,
+                                ws, ws_bytes, stream), "gsr_preprocess")
+
+
+def bin_sort(plan, ws, ws_bytes, stream):
+    _check(lib().gsr_bin_sort(ctypes.byref(plan), ws, ws_bytes, stream), "gsr_bin_sort")
+
+
+def render_camera(plan, ws, ws_bytes, sensor_idx, out: CameraOut, stream):
+    _check(lib().gsr_render_camera(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(out), stream),
+           "gsr_render_camera")
+
+
+def render_lidar(plan, ws, ws_bytes, sensor_idx, out: LidarOut, stream):
+    _check(lib().gsr_render_lidar(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(out), stream),
+           "gsr_render_lidar")
+
+
+def read_status(plan, ws, stream):
+    st, nv, npairs = c_i32(), c_i64(), c_i64()
+    _check(lib().gsr_read_status(ctypes.byref(plan), ws, ctypes.byref(st), ctypes.byref(nv), ctypes.byref(npairs),
+                                 stream), "gsr_read_status")
+    return int(st.value), int(nv.value), int(npairs.value)
+
+
+def workspace_region(plan, ws, which):
+    ptr, n = c_vp(), ctypes.c_size_t()
+    _check(lib().gsr_workspace_region(ctypes.byref(plan), ws, int(which), ctypes.byref(ptr), ctypes.byref(n)),
+           "gsr_workspace_region")
+    return int(ptr.value or 0), int(n.value)

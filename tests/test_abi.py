@@ -1,0 +1,78 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports
+every symbol include/gsr.h declares, its struct layouts match the binding,
+and host-only calls (plan, workspace size, argument errors) behave.  No
+kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2503_11731_gb300 import build as B
+from paper_2503_11731_gb300 import gsr, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return gsr.lib()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(gsr_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(gsr.SIGNATURES) <= names
+
+
+def test_struct_layouts_match(L):
+    for i, st in enumerate(gsr._STRUCTS):
+        assert L.gsr_struct_size(i) == ctypes.sizeof(st), st.__name__
+
+
+def test_plan_and_workspace_host_only(L):
+    cam = synth.plain_camera()
+    lid = synth.driving_lidar()
+    p = gsr.plan_init(8000, [gsr.sensor(cam), gsr.sensor(lid)], (16, 16))
+    assert p.tiles_x[0] == 16 and p.tiles_y[0] == 10
+    assert p.tiles_x[1] == 113 and p.tiles_y[1] == 8
+    assert p.tile_base[1] == 160 and p.tile_base[2] == 160 + 904
+    ws = gsr.workspace_size(p)
+    assert ws >= 2 * 8000 * 80 and ws % 256 == 0
+    offs = [p.off[i] for i in range(19)]
+    assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+
+
+def test_argument_errors(L):
+    cam = gsr.sensor(synth.plain_camera())
+    with pytest.raises(gsr.GsrError) as e:
+        gsr.plan_init(10, [cam], (12, 16))
+    assert e.value.code == gsr.ERR_UNSUPPORTED
+    bad = gsr.sensor(synth.plain_camera())
+    bad.fx = 0.0
+    with pytest.raises(gsr.GsrError) as e:
+        gsr.plan_init(10, [bad])
+    assert e.value.code == gsr.ERR_INVALID_ARG
+    p = gsr.plan_init(10, [cam])
+    # undersized / misaligned workspace is rejected before any launch
+    buf = (ctypes.c_uint8 * 1024)()
+    s = gsr.Surfels()
+    s.n = 10
+    rc = L.gsr_preprocess(ctypes.byref(p), ctypes.byref(s), None, ctypes.cast(buf, ctypes.c_void_p), 1024, None)
+    assert rc == gsr.ERR_WORKSPACE
+    rc = L.gsr_bin_sort(ctypes.byref(p), None, 0, None)
+    assert rc == gsr.ERR_INVALID_ARG
+    assert gsr.status_string(gsr.ERR_CAPACITY) == "GSR_ERR_CAPACITY"

@@ -1,0 +1,240 @@
+"""GPU parity of the forward path (preprocess, binning, compositing) against
+the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 kernel vs FP64 oracle): RGB, intensity, alpha, normal 1e-4
+absolute; depth and range 1e-4 relative where alpha >= 0.01.  Pixels whose
+oracle `flip` value says a threshold decision within FP32 rounding could
+move an output by more than 2e-5 are excluded, counted, and bounded.
+Sort order and tile lists are checked bit-exactly against a CPU stable sort
+of the GPU-emitted (tile | depth) keys.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as OR
+from paper_2503_11731_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ABS = 1e-4
+TOL_REL = 1e-4
+FLIP = 2e-5
+
+
+def _render(s, sensors, tile=(16, 16), max_dup=0, bg=(0.0, 0.0, 0.0), objects=None):
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    r = Renderer(s.n, sensors, tile=tile, max_dup=max_dup, bg=bg,
+                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"))
+    d = DeviceSurfels.from_host(s)
+    obj = None if objects is None else torch.as_tensor(np.asarray(objects, np.float32).reshape(-1, 12), device="cuda")
+    out = r.render(d, obj)
+    torch.cuda.synchronize()
+    return r, [{k: v.cpu().numpy() for k, v in o.items()} for o in out]
+
+
+def _check_camera(g, o, pix=None, max_flag=0.01):
+    """g: GPU outputs (planar), o: oracle dict (pixel-major for `pix`, images otherwise)."""
+    rgb = np.moveaxis(g["rgb"], 0, -1)
+    nrm = np.moveaxis(g["normal"], 0, -1)
+    if pix is not None:
+        H, W = g["alpha"].shape
+        yy, xx = np.divmod(np.asarray(pix), W)
+        rgb, nrm = rgb[yy, xx], nrm[yy, xx]
+        alpha, depth, T = g["alpha"][yy, xx], g["depth"][yy, xx], g["trans"][yy, xx]
+    else:
+        alpha, depth, T = g["alpha"], g["depth"], g["trans"]
+    flag = o["flip"] > FLIP
+    ok = ~flag
+    assert flag.mean() <= max_flag, f"flagged fraction {flag.mean():.4f}"
+    e_rgb = np.abs(rgb - o["rgb"]).max(-1)
+    e_n = np.abs(nrm - o["normal"]).max(-1)
+    e_a = np.abs(alpha - o["alpha"])
+    e_t = np.abs(T - o["T"])
+    dmask = ok & (o["alpha"] >= 0.01)
+    e_d = np.abs(depth - o["depth"]) / np.maximum(np.abs(o["depth"]), 1e-12)
+    report = dict(rgb=e_rgb[ok].max(initial=0), normal=e_n[ok].max(initial=0), alpha=e_a[ok].max(initial=0),
+                  T=e_t[ok].max(initial=0), depth=e_d[dmask].max(initial=0), flagged=int(flag.sum()),
+                  n=int(flag.size))
+    print("camera parity", report)
+    assert report["rgb"] <= TOL_ABS, report
+    assert report["normal"] <= TOL_ABS, report
+    assert report["alpha"] <= TOL_ABS, report
+    assert report["T"] <= TOL_ABS, report
+    assert report["depth"] <= TOL_REL, report
+    return report
+
+
+def _check_lidar(g, o, rays=None, max_flag=0.01):
+    rng_, inten, alpha = g["range"], g["intensity"], g["alpha"]
+    if rays is not None:
+        yy, xx = np.divmod(np.asarray(rays), rng_.shape[1])
+        rng_, inten, alpha = rng_[yy, xx], inten[yy, xx], alpha[yy, xx]
+    flag = o["flip"] > FLIP
+    ok = ~flag
+    assert flag.mean() <= max_flag, f"flagged fraction {flag.mean():.4f}"
+    dmask = ok & (o["alpha"] >= 0.01)
+    e_r = np.abs(rng_ - o["range"]) / np.maximum(np.abs(o["range"]), 1e-12)
+    report = dict(intensity=np.abs(inten - o["intensity"])[ok].max(initial=0),
+                  alpha=np.abs(alpha - o["alpha"])[ok].max(initial=0),
+                  range=e_r[dmask].max(initial=0), flagged=int(flag.sum()), n=int(flag.size))
+    print("lidar parity", report)
+    assert report["intensity"] <= TOL_ABS, report
+    assert report["alpha"] <= TOL_ABS, report
+    assert report["range"] <= TOL_REL, report
+    return report
+
+
+# --------------------------------------------------------------- camera
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_plain_camera_full_frame_parity(gpu_lib, tile):
+    """256x160 pinhole, 8,000 surfels: every pixel against the brute-force oracle."""
+    s = synth.plain_scene()
+    cam = synth.plain_camera()
+    r, out = _render(s, [cam], tile=tile)
+    st, nvis, npairs = r.status()
+    assert st == 0 and nvis > 0 and npairs > 0
+    o = OR.render_pinhole(s, cam)
+    _check_camera(out[0], o)
+
+
+def test_ragged_image_and_background(gpu_lib):
+    """Image sizes that are not tile multiples; a non-black background."""
+    s = synth.plain_scene(n=3000, seed=77)
+    cam = synth.Pinhole(203, 117, 90.0, 95.0, 101.0, 60.0, np.eye(4), 0.2)
+    r, out = _render(s, [cam], bg=(0.2, 0.4, 0.6))
+    o = OR.render_pinhole(s, cam, bg=(0.2, 0.4, 0.6))
+    _check_camera(out[0], o)
+
+
+def test_sh3_posed_camera_parity(gpu_lib):
+    """SH degree 3, a camera with a non-trivial pose, surfels straddling the near plane."""
+    s = synth.driving_scene(n=20_000, seed=5, x_range=(-5.0, 40.0), n_boxes=6)
+    cam = synth.pinhole(320, 200, 180.0, (0.0, 0.5, 1.5), yaw_deg=8.0, pitch_deg=-3.0)
+    r, out = _render(s, [cam])
+    o = OR.render_pinhole(s, cam)
+    _check_camera(out[0], o)
+
+
+def test_empty_and_culled_scenes(gpu_lib):
+    cam = synth.plain_camera(64, 48, 50.0)
+    # no surfels at all
+    s = synth.plain_scene(n=0)
+    r, out = _render(s, [cam], bg=(0.1, 0.2, 0.3))
+    assert np.all(out[0]["rgb"][0] == np.float32(0.1)) and np.all(out[0]["trans"] == 1.0)
+    # every surfel behind the camera
+    s = synth.plain_scene(n=500, seed=3)
+    s.pos[:, 2] = -s.pos[:, 2]
+    r, out = _render(s, [cam])
+    st, nvis, npairs = r.status()
+    assert nvis == 0 and npairs == 0 and np.all(out[0]["alpha"] == 0.0)
+
+
+def test_capacity_overflow_is_reported(gpu_lib):
+    s = synth.plain_scene()
+    cam = synth.plain_camera()
+    r, out = _render(s, [cam], max_dup=5000)
+    st, nvis, npairs = r.status()
+    from paper_2503_11731_gb300 import gsr
+    assert st == gsr.ERR_CAPACITY and npairs > 5000
+
+
+def test_sort_order_bit_exact(gpu_lib):
+    """Pairs equal a CPU stable sort of the GPU-emitted 64-bit (tile | depth) keys."""
+    s = synth.plain_scene()
+    sensors = [synth.plain_camera(), synth.Lidar(32, 360, -15.0, 15.0, synth.lidar_pose((0, 0, 0), 90.0))]
+    r, _ = _render(s, sensors, tile=(16, 16))
+    st, nvis, npairs = r.status()
+    assert st == 0
+    rects = r.region(1, torch.int16).cpu().numpy().view(np.uint16).reshape(-1, 4)
+    counts = r.region(2, torch.int32).cpu().numpy().view(np.uint32)
+    keys = r.region(3, torch.int32).cpu().numpy().view(np.uint32)
+    pk = r.region(4, torch.int32, npairs).cpu().numpy().view(np.uint32)
+    pv = r.region(5, torch.int32, npairs).cpu().numpy().view(np.uint32)
+    ranges = r.region(6, torch.int32).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    plan = r.plan
+    N = s.n
+    k64, v = [], []
+    for slot in np.nonzero(counts)[0]:
+        si = slot // N
+        tx0, tx1, ty0, ty1 = rects[slot]
+        tiles_x = plan.tiles_x[si]
+        assert counts[slot] == (tx1 - tx0 + 1) * (ty1 - ty0 + 1)
+        for ty in range(ty0, ty1 + 1):
+            for tx in range(tx0, tx1 + 1):
+                t = plan.tile_base[si] + ty * tiles_x + (tx if tx < tiles_x else tx - tiles_x)
+                k64.append((np.uint64(t) << np.uint64(32)) | np.uint64(keys[slot]))
+                v.append(slot)
+    k64 = np.asarray(k64, np.uint64)
+    v = np.asarray(v, np.uint32)
+    order = np.argsort(k64, kind="stable")
+    assert len(k64) == npairs
+    assert np.array_equal(pk, (k64[order] >> np.uint64(32)).astype(np.uint32))
+    assert np.array_equal(pv, v[order])
+    # tile ranges
+    T = plan.tile_base[plan.n_sensors]
+    tid = (k64[order] >> np.uint64(32)).astype(np.int64)
+    starts = np.searchsorted(tid, np.arange(T), "left")
+    ends = np.searchsorted(tid, np.arange(T), "right")
+    nonempty = ends > starts
+    assert np.array_equal(ranges[nonempty, 0], starts[nonempty])
+    assert np.array_equal(ranges[nonempty, 1], ends[nonempty])
+    assert np.all(ranges[~nonempty] == 0)
+
+
+def test_render_is_deterministic(gpu_lib):
+    s = synth.plain_scene()
+    cam = synth.plain_camera()
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    r = Renderer(s.n, [cam])
+    d = DeviceSurfels.from_host(s)
+    a = {k: v.clone() for k, v in r.render(d)[0].items()}
+    b = r.render(d)[0]
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+# ---------------------------------------------------------------- LiDAR
+def test_lidar_full_frame_parity(gpu_lib):
+    """A 32x720 LiDAR over a 30k-surfel driving scene, every ray."""
+    s = synth.driving_scene(n=30_000, seed=11, x_range=(-30.0, 30.0), n_boxes=8)
+    lid = synth.spinning_lidar(32, 720, -25.0, 15.0, (0.0, 0.0, 1.8))
+    r, out = _render(s, [lid])
+    o = OR.render_lidar(s, lid)
+    _check_lidar(out[0], o)
+
+
+def test_lidar_wrap_and_close_surfels(gpu_lib):
+    """Surfels straddling the +-180 deg seam and surfels close to the sensor."""
+    rng = np.random.default_rng(12)
+    n = 4000
+    ang = rng.uniform(np.pi - 0.2, np.pi + 0.2, n)
+    dist = rng.uniform(0.5, 15.0, n)
+    pos = np.stack([dist * np.cos(ang), dist * np.sin(ang), rng.uniform(-1.5, 1.5, n)], 1).astype(np.float32)
+    s = synth.Surfels(pos, rng.uniform(-3, 0, (n, 2)).astype(np.float32),
+                      synth._unit_quats(rng, n), rng.normal(0, 1, n).astype(np.float32),
+                      rng.normal(0, 0.2, (n, 1, 3)).astype(np.float32), rng.uniform(0, 1, n).astype(np.float32))
+    lid = synth.spinning_lidar(24, 600, -20.0, 20.0, (0.0, 0.0, 0.0))
+    r, out = _render(s, [lid], tile=(8, 8))
+    o = OR.render_lidar(s, lid)
+    _check_lidar(out[0], o)
+
+
+# ------------------------------------------------------ full-size, sampled
+def test_driving_scene_full_size_sampled(gpu_lib):
+    """1.5M surfels, 1920x1080 camera + 128x1800 LiDAR in one plan, at the
+    benchmark's launch configuration; 384 sampled pixels and rays against
+    the brute-force oracle."""
+    s = synth.driving_scene()
+    cam = synth.driving_camera()
+    lid = synth.driving_lidar()
+    r, out = _render(s, [cam, lid])
+    st, nvis, npairs = r.status()
+    assert st == 0, st
+    rng = np.random.default_rng(99)
+    pix = rng.choice(1920 * 1080, 384, replace=False)
+    rays = rng.choice(128 * 1800, 384, replace=False)
+    o = OR.render_pinhole(s, cam, pixels=pix)
+    _check_camera(out[0], o, pix=pix, max_flag=0.03)
+    ol = OR.render_lidar(s, lid, rays=rays)
+    _check_lidar(out[1], ol, rays=rays, max_flag=0.03)

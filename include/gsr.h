@@ -162,6 +162,37 @@ typedef struct {
     uint32_t* n_contrib;
 } gsr_lidar_out;
 
+/*
+ * Gradients of a loss w.r.t. one camera's per-pixel outputs (DEVICE,
+ * planar, same shapes as gsr_camera_out; NULL = zero):
+ *   rgb [3][H][W], alpha [H][W] (d/d sum w), depth_acc [2][H][W]
+ *   (d/d sum w z, d/d sum w z^2), normal [3][H][W].
+ */
+typedef struct {
+    float* rgb;
+    float* alpha;
+    float* depth_acc;
+    float* normal;
+} gsr_camera_grad;
+
+/* Gradients w.r.t. the raw surfel parameters (DEVICE, shapes of
+ * gsr_surfels; accumulated with +=, so the caller zeroes them first). */
+typedef struct {
+    float* pos;
+    float* log_scale;
+    float* quat;
+    float* opacity;
+    float* sh;
+    float* intensity; /* may be NULL */
+} gsr_surfel_grads;
+
+/* Weights of the reconstruction loss (gsr_loss). */
+typedef struct {
+    float w_dist;      /* depth distortion weight (0.1)                  */
+    float w_normal;    /* normal consistency weight (0.05)               */
+    float mask_alpha;  /* normal term only where the 4 neighbours have sum w >= this (0.5) */
+} gsr_loss_weights;
+
 /* ---------------------------------------------------------------- setup */
 
 /* Fill `plan` for n_surfels surfels seen by n_sensors sensors (host only).
@@ -206,6 +237,55 @@ gsr_status gsr_render_camera(const gsr_plan* plan, const void* workspace, size_t
 /* Step (c) for LiDAR `sensor` (Eq. 5 planes over the beam x azimuth tiling). */
 gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
                             int32_t sensor, const gsr_lidar_out* out, void* stream);
+
+/* -------------------------------------------------------------- training */
+
+/*
+ * Reconstruction loss of camera `sensor` against target_rgb [3][H][W]
+ * (DEVICE), from the outputs of gsr_render_camera (fwd->rgb, alpha,
+ * depth_acc, normal must be set), following the 2DGS regularisers the
+ * paper's representation cites (Sec. II):
+ *   L = mean|C - C*|                               (over 3 H W)
+ *     + w_dist   * mean_px(A D - B^2)              A = sum w, B = sum w z, D = sum w z^2
+ *     + w_normal * sum_px m (1 - N . N_d) / (H W)
+ * N = sum w n; N_d = normalise(dY x dX) of the back-projected expected depth
+ * B/A by central differences at the 4 neighbours; m = 1 on interior pixels
+ * whose 4 neighbours have A >= mask_alpha and |dY x dX| > 0.
+ * Writes loss[0..3] = (L, L1 term, distortion term, normal term) (DEVICE
+ * float[4]) and the per-pixel gradients into *grad (all four planes
+ * required; overwritten).  Uses workspace scratch; deterministic.
+ */
+gsr_status gsr_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                    const gsr_camera_out* fwd, const float* target_rgb, const gsr_loss_weights* weights,
+                    float* loss, const gsr_camera_grad* grad, void* stream);
+
+/*
+ * Reverse-order backward rasteriser of camera `sensor`: each pixel walks its
+ * tile list from its last contributor (fwd->n_contrib) back to the front,
+ * recovering T_i = T_{i+1} / (1 - alpha_i) from the final T (fwd->trans;
+ * no per-pixel lists are stored), and accumulates d(loss)/d(record) --
+ * reduced over the warp before FP32 atomics -- into the workspace.
+ * accumulate = 0 zeroes the record gradients first (first sensor of a step).
+ * Must follow gsr_preprocess / gsr_bin_sort / gsr_render_camera of the same
+ * frame with the same workspace.
+ */
+gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                               const gsr_camera_out* fwd, const gsr_camera_grad* grad, int32_t accumulate,
+                               void* stream);
+
+/*
+ * Chain the record gradients of all sensors back to the raw surfel
+ * parameters (pos, log_scale, quat, opacity logit, SH, incl. the view
+ * direction of the SH colour), accumulating into *out.  Camera sensors only.
+ */
+gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                                   const gsr_surfels* surfels, const gsr_objects* objects,
+                                   const gsr_surfel_grads* out, void* stream);
+
+/* gsr_backward_render (accumulate = 0) + gsr_backward_preprocess for one camera. */
+gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                        const gsr_camera_out* fwd, const gsr_camera_grad* grad, const gsr_surfels* surfels,
+                        const gsr_objects* objects, const gsr_surfel_grads* out, void* stream);
 
 /*
  * Copy the device status word to the host (synchronises `stream`).

@@ -30,7 +30,9 @@
  *     depth is the intersection depth if G3 wins, else the centre depth;
  *   - alpha = min(0.99, o G); alpha < 1/255 is skipped; compositing stops
  *     before a surfel when T (1 - alpha) < 1e-4;
- *   - composite order: centre depth (camera z, LiDAR |mu|), ties by index;
+ *   - composite order: centre depth (camera z, LiDAR |mu|), ties by index,
+ *     with the depth key and the near cull taken in the kernel's FP32
+ *     arithmetic (see or_key32);
  *   - colour = max(0, sum_lm Y_lm(dir) c_lm + 0.5), real SH with the
  *     Condon-Shortley phase, dir = normalise(mu - sensor origin);
  *   - normal = R's third column, flipped to face the sensor, sensor frame.
@@ -128,7 +130,8 @@ static void or_quat_to_rot(const double q_in[4], double R[3][3])
 typedef struct {
     int culled;
     double WH[4][3];   /* Eq. 1: W . H, a 4x3 matrix                         */
-    double zc;         /* composite-order key: centre depth / centre range   */
+    double zc;         /* centre depth (camera z) / centre range (LiDAR |mu|) */
+    float key;         /* composite-order key: zc in the kernel's FP32 arithmetic */
     double c[2];       /* low-pass centre (pixels, or LiDAR cells)           */
     double o;          /* opacity, sigmoid of the logit                      */
     double feat[3];    /* camera: colour; LiDAR: intensity in feat[0]       */
@@ -191,6 +194,35 @@ static void or_surfel_world(int i, const double* pos, const double* quat, const 
     }
 }
 
+/*
+ * The composite order is an integer decision (a permutation) that rounding
+ * decides: two surfels whose centre depths differ by less than FP32 can
+ * resolve swap places between an FP32 and an FP64 evaluation.  The order
+ * key is therefore taken in the kernel's precision -- the centre depth
+ * (range) evaluated in IEEE single precision with fused multiply-adds in
+ * the order the kernel uses: mu' = R_o mu + t_o, m = R mu' + t, key = m_z
+ * (camera) or sqrt(m . m) (LiDAR).  Everything else stays FP64.
+ */
+static float or_key32(const or_sensor* S, int i, const double* pos, const int* obj_id, const double* obj_pose)
+{
+    float m0 = (float)pos[3 * i], m1 = (float)pos[3 * i + 1], m2 = (float)pos[3 * i + 2];
+    int k = obj_id ? obj_id[i] : -1;
+    if (k >= 0) {
+        const double* P = obj_pose + 12 * k;
+        float R[9] = {(float)P[0], (float)P[1], (float)P[2], (float)P[4], (float)P[5], (float)P[6],
+                      (float)P[8], (float)P[9], (float)P[10]};
+        float a0 = fmaf(R[0], m0, fmaf(R[1], m1, R[2] * m2)) + (float)P[3];
+        float a1 = fmaf(R[3], m0, fmaf(R[4], m1, R[5] * m2)) + (float)P[7];
+        float a2 = fmaf(R[6], m0, fmaf(R[7], m1, R[8] * m2)) + (float)P[11];
+        m0 = a0; m1 = a1; m2 = a2;
+    }
+    float s[3];
+    for (int a = 0; a < 3; ++a)
+        s[a] = fmaf((float)S->Rs[a][0], m0, fmaf((float)S->Rs[a][1], m1, (float)S->Rs[a][2] * m2)) + (float)S->ts[a];
+    if (!S->is_lidar) return s[2];
+    return sqrtf(fmaf(s[0], s[0], fmaf(s[1], s[1], s[2] * s[2])));
+}
+
 static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* pos,
                        const double* log_scale, const double* quat, const double* opacity_logit,
                        int sh_degree, const double* sh, const double* intensity,
@@ -238,14 +270,14 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     for (int a = 0; a < 3; ++a) ms[a] = S->Rs[a][0] * mu[0] + S->Rs[a][1] * mu[1] + S->Rs[a][2] * mu[2] + S->ts[a];
 
     G->culled = 0;
+    G->key = or_key32(S, i, pos, obj_id, obj_pose);
+    if (!(G->key > (float)S->near_)) { G->culled = 1; return; }  /* cull in the key's precision */
     if (!S->is_lidar) {
         G->zc = ms[2];
-        if (!(G->zc > S->near_)) { G->culled = 1; return; }
         G->c[0] = G->WH[0][2] / G->WH[2][2];
         G->c[1] = G->WH[1][2] / G->WH[2][2];
     } else {
         G->zc = sqrt(or_dot3(ms, ms));
-        if (!(G->zc > S->near_)) { G->culled = 1; return; }
         double az = atan2(ms[1], ms[0]);
         double el = atan2(ms[2], sqrt(ms[0] * ms[0] + ms[1] * ms[1]));
         /* cell coordinates: ray (row i, column j) sits at (j, i) */
@@ -285,7 +317,8 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
 /* ----------------------------------------------------------------------- */
 typedef struct {
     int idx;
-    double zc;        /* order key            */
+    float key;        /* order key            */
+    double zc;        /* centre depth         */
     double alpha;     /* min(0.99, o G)       */
     double z;         /* contribution depth   */
     double rho3, rholp, zint;
@@ -335,6 +368,7 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
     double a = G->o * Gv;
     h->alpha = a < 0.99 ? a : 0.99;
     h->zc = G->zc;
+    h->key = G->key;
     return 1;
 }
 
@@ -342,8 +376,8 @@ static int or_cmp_hit(const void* pa, const void* pb)
 {
     const or_hit* a = (const or_hit*)pa;
     const or_hit* b = (const or_hit*)pb;
-    if (a->zc < b->zc) return -1;
-    if (a->zc > b->zc) return 1;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
     return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
@@ -351,13 +385,14 @@ static double or_relm(double x, double thr) { return fabs(x - thr) / fabs(thr); 
 
 /*
  * Decisions that FP32 rounding could flip.  A decision counts as flippable
- * when its relative distance to the threshold is below OR_FLIP_REL (2e-5;
- * 2e-6 for the order of two centre depths), and its effect is the largest
+ * when its relative distance to the threshold is below OR_FLIP_REL (2e-5),
+ * and its effect is the largest
  * change of an output that flipping it could cause (T times the jump in
  * alpha; for the depth-branch choice, the relative jump in depth weight).
  */
+#ifndef OR_FLIP_REL
 #define OR_FLIP_REL 2e-5
-#define OR_FLIP_ORDER 2e-6
+#endif
 
 typedef struct {
     double feat[3], A, B, D, N[3], T;
@@ -389,13 +424,12 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
                         (h.hasplane && h.rho3 <= 9.0 && or_relm(h.zint, S->near_) < 1e-3) ||
                         or_relm(h.rholp, 9.0) < 1e-3;
         if (!any && !near_miss) continue;
-        if (!any) { h.alpha = 0; h.z = G[i].zc; h.zc = G[i].zc; }
+        if (!any) { h.alpha = 0; h.z = G[i].zc; h.zc = G[i].zc; h.key = G[i].key; }
         buf[nh++] = h;
     }
     qsort(buf, (size_t)nh, sizeof(or_hit), or_cmp_hit);
     double T = 1.0, flip = 0.0;
     double F[3] = {0, 0, 0}, A = 0, B = 0, D = 0, N[3] = {0, 0, 0};
-    double prev_zc = -1.0, prev_w = 0.0;
     int nc = 0;
     for (int j = 0; j < nh; ++j) {
         const or_hit* h = &buf[j];
@@ -416,7 +450,6 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
         double test = T * (1.0 - h->alpha);
         or_flip(&flip, or_relm(test, 1e-4), OR_FLIP_REL, h->alpha * T);
         if (test < 1e-4) break;
-        if (nc > 0) or_flip(&flip, fabs(h->zc - prev_zc) / h->zc, OR_FLIP_ORDER, h->alpha * prev_w);
         double w = h->alpha * T;
         for (int ch = 0; ch < 3; ++ch) F[ch] += w * g->feat[ch];
         A += w;
@@ -424,8 +457,6 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
         D += w * h->z * h->z;
         for (int a = 0; a < 3; ++a) N[a] += w * g->normal[a];
         T = test;
-        prev_zc = h->zc;
-        prev_w = w;
         ++nc;
     }
     for (int ch = 0; ch < 3; ++ch) out->feat[ch] = F[ch];

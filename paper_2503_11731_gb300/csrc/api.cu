@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 
 #include "gsr_internal.cuh"
 
@@ -14,6 +15,12 @@ __global__ void k_preprocess(SensorTable tab, gsr_surfels S, const float* poses,
                              ushort4* rects, uint32_t* counts, uint32_t* keys);
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st);
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st);
+cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd, const float* target,
+                        const gsr_loss_weights* wt, float* loss, const gsr_camera_grad* g, cudaStream_t st);
+cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
+                                   const gsr_camera_grad* g, int accumulate, cudaStream_t st);
+cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,
+                                       const gsr_objects* obj, const gsr_surfel_grads* out, cudaStream_t st);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -126,6 +133,12 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_PARTIAL] = G * 8 + 64;
     sz[R_COUNTERS] = C_WORDS * 4;
     sz[R_SENSOR_OF_TILE] = 64;
+    sz[R_RECGRAD] = slots * kRecordBytes;
+    uint64_t max_hw = 0;
+    for (int i = 0; i < n_sensors; ++i)
+        if (sensors[i].kind == GSR_SENSOR_PINHOLE)
+            max_hw = std::max<uint64_t>(max_hw, (uint64_t)sensors[i].width * sensors[i].height);
+    sz[R_LOSS_SCRATCH] = (6 * max_hw + 3 * ((max_hw + 255) / 256) + 64) * 4;
     uint64_t off = 0;
     for (int r = 0; r < R_END; ++r) {
         plan->off[r] = off;
@@ -285,6 +298,68 @@ extern "C" size_t gsr_struct_size(int32_t which)
     case 4: return sizeof(gsr_camera_out);
     case 5: return sizeof(gsr_lidar_out);
     case 6: return sizeof(gsr_tiling);
+    case 7: return sizeof(gsr_camera_grad);
+    case 8: return sizeof(gsr_surfel_grads);
+    case 9: return sizeof(gsr_loss_weights);
     default: return 0;
     }
+}
+
+// ------------------------------------------------------------------ training
+static gsr_status check_camera(const gsr_plan* plan, int32_t sensor)
+{
+    if (sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
+    if (plan->sensors[sensor].kind != GSR_SENSOR_PINHOLE) return GSR_ERR_UNSUPPORTED;
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                               const gsr_camera_out* fwd, const float* target_rgb, const gsr_loss_weights* weights,
+                               float* loss, const gsr_camera_grad* grad, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if ((st = check_camera(plan, sensor)) != GSR_OK) return st;
+    if (!fwd || !target_rgb || !weights || !loss || !grad) return GSR_ERR_INVALID_ARG;
+    if (!fwd->rgb || !fwd->alpha || !fwd->depth_acc || !fwd->normal) return GSR_ERR_INVALID_ARG;
+    if (!grad->rgb || !grad->alpha || !grad->depth_acc || !grad->normal) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(launch_loss(plan, workspace, sensor, fwd, target_rgb, weights, loss, grad,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t workspace_bytes,
+                                          int32_t sensor, const gsr_camera_out* fwd, const gsr_camera_grad* grad,
+                                          int32_t accumulate, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if ((st = check_camera(plan, sensor)) != GSR_OK) return st;
+    if (!fwd || !grad || !fwd->trans || !fwd->n_contrib) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(launch_render_backward(plan, workspace, sensor, fwd, grad, accumulate,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                                              const gsr_surfels* surfels, const gsr_objects* objects,
+                                              const gsr_surfel_grads* out, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if (!surfels || surfels->n != plan->n_surfels || !out) return GSR_ERR_INVALID_ARG;
+    if (surfels->sh_degree < 0 || surfels->sh_degree > 3) return GSR_ERR_UNSUPPORTED;
+    if (surfels->n > 0 && (!out->pos || !out->log_scale || !out->quat || !out->opacity || !out->sh))
+        return GSR_ERR_INVALID_ARG;
+    if (objects && objects->n_objects > 0 && !objects->pose) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(launch_preprocess_backward(plan, workspace, surfels, objects, out,
+                                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                                   const gsr_camera_out* fwd, const gsr_camera_grad* grad,
+                                   const gsr_surfels* surfels, const gsr_objects* objects,
+                                   const gsr_surfel_grads* out, void* stream)
+{
+    gsr_status st = gsr_backward_render(plan, workspace, workspace_bytes, sensor, fwd, grad, 0, stream);
+    if (st != GSR_OK) return st;
+    return gsr_backward_preprocess(plan, workspace, workspace_bytes, surfels, objects, out, stream);
 }

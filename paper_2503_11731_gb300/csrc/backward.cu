@@ -1,0 +1,674 @@
+// backward.cu -- reconstruction loss and the hand-written backward pass.
+//
+//  k_loss_pixel / k_loss_gather / k_loss_reduce
+//      L1 + depth distortion + normal consistency (the 2DGS regularisers
+//      of the representation the paper adopts, Sec. II / III-A) and the
+//      per-pixel gradients w.r.t. the camera outputs.
+//  k_render_backward
+//      reverse-order walk of each tile list from every pixel's last
+//      contributor; T_i is recovered as T_{i+1} / (1 - alpha_i) from the
+//      final T, so no per-pixel list is stored.  Per-record gradients are
+//      reduced over the warp before the FP32 atomics.
+//  k_preprocess_backward
+//      chains the record gradients to the raw surfel parameters (the
+//      inverse of the preprocess of Eqs. 1-3), one thread per surfel,
+//      summing over sensors without atomics.
+#include "gsr_internal.cuh"
+
+namespace gsr {
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+}  // namespace
+
+// ===================================================================== loss
+struct LossArgs {
+    const float* rgb;
+    const float* alpha;
+    const float* dacc;     // [2][H][W]
+    const float* normal;
+    const float* target;
+    float* g_rgb;
+    float* g_alpha;
+    float* g_dacc;
+    float* g_normal;
+    float* scratch;        // [6][H][W]: dL/d(dX), dL/d(dY) per pixel
+    float* partial;        // [blocks][3]
+    int W, H;
+    float fx, fy, cx, cy;
+    float w_dist, w_norm, mask_alpha;
+};
+
+// Pass 1: per-pixel terms, the direct gradients, and the gradient of the
+// normal term w.r.t. the two central differences of this pixel.
+__global__ void __launch_bounds__(256) k_loss_pixel(LossArgs a)
+{
+    __shared__ float red[3][8];
+    const int HW = a.W * a.H;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    float l1 = 0.f, dist = 0.f, nc = 0.f;
+    if (p < HW) {
+        const int x = p % a.W, y = p / a.W;
+        const float inv3 = 1.f / (3.f * HW), inv = 1.f / HW;
+        for (int c = 0; c < 3; ++c) {
+            const float d = a.rgb[c * HW + p] - a.target[c * HW + p];
+            l1 += fabsf(d);
+            a.g_rgb[c * HW + p] = sgnf(d) * inv3;
+        }
+        const float A = a.alpha[p], B = a.dacc[p], D = a.dacc[HW + p];
+        dist = fmaf(A, D, -B * B);
+        a.g_alpha[p] = a.w_dist * D * inv;
+        a.g_dacc[p] = -2.f * a.w_dist * B * inv;
+        a.g_dacc[HW + p] = a.w_dist * A * inv;
+        float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+        float gdx[3] = {0.f, 0.f, 0.f}, gdy[3] = {0.f, 0.f, 0.f};
+        if (x > 0 && x + 1 < a.W && y > 0 && y + 1 < a.H) {
+            const int qs[4] = {p - 1, p + 1, p - a.W, p + a.W};
+            const int qx[4] = {x - 1, x + 1, x, x};
+            const int qy[4] = {y, y, y - 1, y + 1};
+            float X[4][3];
+            bool ok = true;
+            for (int k = 0; k < 4; ++k) {
+                const float Aq = a.alpha[qs[k]];
+                ok = ok && (Aq >= a.mask_alpha);
+                const float Db = Aq > 0.f ? a.dacc[qs[k]] / Aq : 0.f;
+                X[k][0] = (qx[k] + 0.5f - a.cx) / a.fx * Db;
+                X[k][1] = (qy[k] + 0.5f - a.cy) / a.fy * Db;
+                X[k][2] = Db;
+            }
+            const float dX[3] = {X[1][0] - X[0][0], X[1][1] - X[0][1], X[1][2] - X[0][2]};
+            const float dY[3] = {X[3][0] - X[2][0], X[3][1] - X[2][1], X[3][2] - X[2][2]};
+            // cr = dY x dX
+            const float cr[3] = {dY[1] * dX[2] - dY[2] * dX[1], dY[2] * dX[0] - dY[0] * dX[2],
+                                 dY[0] * dX[1] - dY[1] * dX[0]};
+            const float nrm = sqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            if (ok && nrm > 0.f) {
+                const float Nd[3] = {cr[0] / nrm, cr[1] / nrm, cr[2] / nrm};
+                const float N[3] = {a.normal[p], a.normal[HW + p], a.normal[2 * HW + p]};
+                nc = 1.f - (N[0] * Nd[0] + N[1] * Nd[1] + N[2] * Nd[2]);
+                const float s = -a.w_norm * inv;
+                gN0 = s * Nd[0];
+                gN1 = s * Nd[1];
+                gN2 = s * Nd[2];
+                const float gNd[3] = {s * N[0], s * N[1], s * N[2]};
+                const float dd = Nd[0] * gNd[0] + Nd[1] * gNd[1] + Nd[2] * gNd[2];
+                const float gcr[3] = {(gNd[0] - Nd[0] * dd) / nrm, (gNd[1] - Nd[1] * dd) / nrm,
+                                      (gNd[2] - Nd[2] * dd) / nrm};
+                // cr = dY x dX: dL/d dY = dX x gcr, dL/d dX = gcr x dY
+                gdy[0] = dX[1] * gcr[2] - dX[2] * gcr[1];
+                gdy[1] = dX[2] * gcr[0] - dX[0] * gcr[2];
+                gdy[2] = dX[0] * gcr[1] - dX[1] * gcr[0];
+                gdx[0] = gcr[1] * dY[2] - gcr[2] * dY[1];
+                gdx[1] = gcr[2] * dY[0] - gcr[0] * dY[2];
+                gdx[2] = gcr[0] * dY[1] - gcr[1] * dY[0];
+            }
+        }
+        a.g_normal[p] = gN0;
+        a.g_normal[HW + p] = gN1;
+        a.g_normal[2 * HW + p] = gN2;
+        for (int k = 0; k < 3; ++k) {
+            a.scratch[k * HW + p] = gdx[k];
+            a.scratch[(3 + k) * HW + p] = gdy[k];
+        }
+    }
+    // block partial sums (fixed order: deterministic)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    l1 = warp_sum(l1);
+    dist = warp_sum(dist);
+    nc = warp_sum(nc);
+    if (lane == 0) {
+        red[0][w] = l1;
+        red[1][w] = dist;
+        red[2][w] = nc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float s = 0.f;
+        for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
+        a.partial[blockIdx.x * 3 + threadIdx.x] = s;
+    }
+}
+
+// Pass 2: each pixel gathers dL/dX from the central differences of its four
+// neighbours, then dL/d(expected depth) -> dL/dB, dL/dA.
+__global__ void __launch_bounds__(256) k_loss_gather(LossArgs a)
+{
+    const int HW = a.W * a.H;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= HW) return;
+    const int x = p % a.W, y = p / a.W;
+    float gX[3] = {0.f, 0.f, 0.f};
+    // dX(q) = X(q.x+1) - X(q.x-1): pixel p is q.x+1 for q = p-1 and q.x-1 for q = p+1
+    for (int k = 0; k < 3; ++k) {
+        if (x > 0) gX[k] += a.scratch[k * HW + p - 1];
+        if (x + 1 < a.W) gX[k] -= a.scratch[k * HW + p + 1];
+        if (y > 0) gX[k] += a.scratch[(3 + k) * HW + p - a.W];
+        if (y + 1 < a.H) gX[k] -= a.scratch[(3 + k) * HW + p + a.W];
+    }
+    const float A = a.alpha[p];
+    if (A > 0.f) {
+        const float gD = gX[0] * (x + 0.5f - a.cx) / a.fx + gX[1] * (y + 0.5f - a.cy) / a.fy + gX[2];
+        const float B = a.dacc[p];
+        a.g_dacc[p] += gD / A;
+        a.g_alpha[p] += -gD * B / (A * A);
+    }
+}
+
+__global__ void k_loss_reduce(const float* __restrict__ partial, int nblocks, float w_dist, float w_norm, int HW,
+                              float* __restrict__ loss)
+{
+    __shared__ double red[3][32];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 3; ++k) s[k] += partial[b * 3 + k];
+    for (int k = 0; k < 3; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < 3; ++k)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[k] += red[k][w];
+        const double l1 = t[0] / (3.0 * HW), dist = t[1] / HW, nc = t[2] / HW;
+        loss[1] = (float)l1;
+        loss[2] = (float)(w_dist * dist);
+        loss[3] = (float)(w_norm * nc);
+        loss[0] = (float)(l1 + w_dist * dist + w_norm * nc);
+    }
+}
+
+// ======================================================= backward rasteriser
+struct BwdArgs {
+    const float* trans;
+    const uint32_t* n_contrib;
+    const float* g_rgb;     // [3][H][W]
+    const float* g_alpha;
+    const float* g_dacc;    // [2][H][W]
+    const float* g_normal;  // [3][H][W]
+    float4* recgrad;        // [slots][5]
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int sensor,
+                                                         const float4* __restrict__ rec,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ pval, BwdArgs a,
+                                                         uint32_t* counters)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    uint32_t* sslot = reinterpret_cast<uint32_t*>(smem_raw + 128);          // [2][nthr]
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128 + 2 * 256 * 4);  // [2][nthr][5]
+    __shared__ uint32_t wmax[8];
+    const SensorDev& sd = tab.s[sensor];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int lt = blockIdx.x;
+    const int tx = lt % sd.tiles_x, ty = lt / sd.tiles_x;
+    const int x = tx * tab.tile_w + tid % tab.tile_w;
+    const int y = ty * tab.tile_h + tid / tab.tile_w;
+    const bool inside = x < sd.width && y < sd.height;
+    const size_t HW = (size_t)sd.width * sd.height;
+    const size_t pix = (size_t)y * sd.width + x;
+    if (tid == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        fence_mbar_init();
+    }
+    float rx, ry, d0, d1, d2;
+    ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
+    const uint2 range = ranges[sd.tile_base + lt];
+    uint32_t last = 0;
+    float T = 1.f;
+    float gC[3] = {0.f, 0.f, 0.f}, gN[3] = {0.f, 0.f, 0.f}, gA = 0.f, gB = 0.f, gD = 0.f;
+    if (inside) {
+        last = a.n_contrib[pix];
+        T = a.trans[pix];
+        if (a.g_rgb) {
+            gC[0] = a.g_rgb[pix];
+            gC[1] = a.g_rgb[HW + pix];
+            gC[2] = a.g_rgb[2 * HW + pix];
+        }
+        if (a.g_normal) {
+            gN[0] = a.g_normal[pix];
+            gN[1] = a.g_normal[HW + pix];
+            gN[2] = a.g_normal[2 * HW + pix];
+        }
+        if (a.g_alpha) gA = a.g_alpha[pix];
+        if (a.g_dacc) {
+            gB = a.g_dacc[pix];
+            gD = a.g_dacc[HW + pix];
+        }
+    }
+    // accumulated contributions of the surfels behind the current one
+    float Ca[3] = {T * sd.bg[0], T * sd.bg[1], T * sd.bg[2]};
+    float Aa = 0.f, Ba = 0.f, Da = 0.f, Na[3] = {0.f, 0.f, 0.f};
+
+    uint32_t m = __reduce_max_sync(0xffffffffu, last);
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    uint32_t maxlast = 0;
+    for (int k = 0; k < (nthr >> 5); ++k) maxlast = max(maxlast, wmax[k]);
+    const int nb = ((int)maxlast + nthr - 1) / nthr;
+    const float columns = (float)sd.width;
+
+    // batch b covers list positions [lo, hi) counted from the end
+    auto issue = [&](int b) {
+        const int hi = (int)maxlast - b * nthr;
+        const int lo = max(0, hi - nthr);
+        const int cnt = hi - lo;
+        uint64_t* bar = bars + (b & 1);
+        float4* dst = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
+        if (tid < cnt) {
+            const uint32_t slot = pval[range.x + lo + tid];
+            sslot[(b & 1) * nthr + tid] = slot;
+            bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
+        }
+    };
+    bool ok = true;
+    if (nb > 0) issue(0);
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        if (!mbar_wait_bounded(bars + (b & 1), (b >> 1) & 1, counters)) ok = false;
+        ok = __syncthreads_and(ok);  // block-uniform; slot ids of this batch are visible
+        const int hi = (int)maxlast - b * nthr;
+        const int lo = max(0, hi - nthr);
+        const float4* Bf = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        const uint32_t* Sl = sslot + (b & 1) * nthr;
+        for (int j = hi - 1; j >= lo && ok; --j) {
+            const bool active = (uint32_t)j < last;
+            if (!__any_sync(0xffffffffu, active)) continue;
+            const float4* Rj = Bf + (j - lo) * kRecordF4;
+            Splat sp;
+            bool contrib = active && splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, sd.near_plane, columns, sp);
+            float g[20];
+#pragma unroll
+            for (int k = 0; k < 20; ++k) g[k] = 0.f;
+            if (contrib) {
+                const float al = sp.alpha, z = sp.z;
+                const float om = 1.f - al;
+                T = T / om;  // transmittance in front of this surfel
+                const float w = al * T;
+                const float4 r3 = Rj[3], r4 = Rj[4];
+                const float io = 1.f / om;
+                float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
+                float c[3] = {r3.y, r3.z, r3.w};
+                if (KIND == GSR_SENSOR_PINHOLE) {
+                    const float n[3] = {r4.x, r4.y, r4.z};
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        dal += gC[k] * (T * c[k] - Ca[k] * io) + gN[k] * (T * n[k] - Na[k] * io);
+                        Ca[k] = fmaf(w, c[k], Ca[k]);
+                        Na[k] = fmaf(w, n[k], Na[k]);
+                        g[13 + k] = w * gC[k];   // colour
+                        g[16 + k] = w * gN[k];   // normal
+                    }
+                } else {
+                    dal += gC[0] * (T * c[0] - Ca[0] * io);
+                    Ca[0] = fmaf(w, c[0], Ca[0]);
+                    g[13] = w * gC[0];
+                }
+                Aa += w;
+                Ba = fmaf(w, z, Ba);
+                Da = fmaf(w * z, z, Da);
+                const float dz = w * (gB + 2.f * z * gD);
+                const float o = r3.x;
+                float dG = 0.f;
+                if (o * sp.G < kAlphaMax) {
+                    g[12] = dal * sp.G;  // opacity
+                    dG = dal * o;
+                }
+                const float drho = -0.5f * sp.G * dG;
+                if (sp.use3) {
+                    const float iq = 1.f / sp.q2;
+                    const float dq0 = 2.f * sp.u * iq * drho;
+                    const float dq1 = 2.f * sp.v * iq * drho;
+                    const float dq2 = -2.f * sp.rho * iq * drho - sp.z * iq * dz;
+                    g[11] = dz * iq;  // det
+                    float r0, r1, r2;
+                    if (KIND == GSR_SENSOR_PINHOLE) {
+                        r0 = sp.dx; r1 = sp.dy; r2 = 1.f;
+                        const float4 q0 = Rj[0], q1 = Rj[1], q2 = Rj[2];
+                        g[3] = -(dq0 * q0.x + dq1 * q1.x + dq2 * q2.x);  // centre x
+                        g[7] = -(dq0 * q0.y + dq1 * q1.y + dq2 * q2.y);  // centre y
+                    } else {
+                        r0 = d0; r1 = d1; r2 = d2;
+                    }
+                    g[0] = dq0 * r0; g[1] = dq0 * r1; g[2] = dq0 * r2;
+                    g[4] = dq1 * r0; g[5] = dq1 * r1; g[6] = dq1 * r2;
+                    g[8] = dq2 * r0; g[9] = dq2 * r1; g[10] = dq2 * r2;
+                } else {
+                    g[3] = -2.f * kLowPassInvVar * sp.dx * drho;
+                    g[7] = -2.f * kLowPassInvVar * sp.dy * drho;
+                    g[19] = dz;  // centre depth
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int k = 0; k < 20; ++k) g[k] = warp_sum(g[k]);
+                if ((tid & 31) == 0) {
+                    float* dst = reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4);
+#pragma unroll
+                    for (int k = 0; k < 20; ++k)
+                        if (g[k] != 0.f) atomicAdd(dst + k, g[k]);
+                }
+            }
+        }
+        __syncthreads();  // buffer b&1 is free for batch b+2
+        if (!ok) {
+            if (b + 1 < nb) mbar_wait_bounded(bars + ((b + 1) & 1), ((b + 1) >> 1) & 1, counters);
+            break;
+        }
+    }
+}
+
+// ================================================== preprocess backward
+namespace {
+
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 mul(const float* M, V3 v)
+{
+    return v3(M[0] * v.x + M[1] * v.y + M[2] * v.z, M[3] * v.x + M[4] * v.y + M[5] * v.z,
+              M[6] * v.x + M[7] * v.y + M[8] * v.z);
+}
+__device__ __forceinline__ V3 mulT(const float* M, V3 v)
+{
+    return v3(M[0] * v.x + M[3] * v.y + M[6] * v.z, M[1] * v.x + M[4] * v.y + M[7] * v.z,
+              M[2] * v.x + M[5] * v.y + M[8] * v.z);
+}
+
+// SH basis (deg <= 3, the same functions as the preprocess) and its gradient
+// w.r.t. the (unnormalised) direction components.
+__device__ __forceinline__ void sh_basis_grad(int deg, V3 d, float* b, V3* gb)
+{
+    const float x = d.x, y = d.y, z = d.z;
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.5462742152960396f;
+    const float C3a = -0.5900435899266435f, C3b = 2.890611442640554f, C3c = -0.4570457994644658f;
+    const float C3d = 0.3731763325901154f, C3e = 1.445305721320277f;
+    b[0] = C0;
+    gb[0] = v3(0.f, 0.f, 0.f);
+    if (deg < 1) return;
+    b[1] = -C1 * y; gb[1] = v3(0.f, -C1, 0.f);
+    b[2] = C1 * z;  gb[2] = v3(0.f, 0.f, C1);
+    b[3] = -C1 * x; gb[3] = v3(-C1, 0.f, 0.f);
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    b[4] = C2a * x * y;                b[5] = -C2a * y * z;
+    b[6] = C2b * (2.f * zz - xx - yy); b[7] = -C2a * x * z;
+    b[8] = C2c * (xx - yy);
+    gb[4] = v3(C2a * y, C2a * x, 0.f);
+    gb[5] = v3(0.f, -C2a * z, -C2a * y);
+    gb[6] = v3(-2.f * C2b * x, -2.f * C2b * y, 4.f * C2b * z);
+    gb[7] = v3(-C2a * z, 0.f, -C2a * x);
+    gb[8] = v3(2.f * C2c * x, -2.f * C2c * y, 0.f);
+    if (deg < 3) return;
+    b[9] = C3a * y * (3.f * xx - yy);
+    b[10] = C3b * x * y * z;
+    b[11] = C3c * y * (4.f * zz - xx - yy);
+    b[12] = C3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    b[13] = C3c * x * (4.f * zz - xx - yy);
+    b[14] = C3e * z * (xx - yy);
+    b[15] = C3a * x * (xx - 3.f * yy);
+    gb[9] = v3(6.f * C3a * x * y, C3a * (3.f * xx - 3.f * yy), 0.f);
+    gb[10] = v3(C3b * y * z, C3b * x * z, C3b * x * y);
+    gb[11] = v3(-2.f * C3c * x * y, C3c * (4.f * zz - xx - 3.f * yy), 8.f * C3c * y * z);
+    gb[12] = v3(-6.f * C3d * x * z, -6.f * C3d * y * z, C3d * (6.f * zz - 3.f * xx - 3.f * yy));
+    gb[13] = v3(C3c * (4.f * zz - 3.f * xx - yy), -2.f * C3c * x * y, 8.f * C3c * x * z);
+    gb[14] = v3(2.f * C3e * x * z, -2.f * C3e * y * z, C3e * (xx - yy));
+    gb[15] = v3(C3a * (3.f * xx - 3.f * yy), -6.f * C3a * x * y, 0.f);
+}
+
+}  // namespace
+
+struct PreBwdArgs {
+    gsr_surfels S;
+    const float* poses;
+    int n_obj;
+    const float4* recgrad;
+    const uint32_t* counts;
+    gsr_surfel_grads G;
+};
+
+__global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, PreBwdArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const gsr_surfels& S = a.S;
+    if (i >= S.n) return;
+    // ---- forward quantities independent of the sensor
+    V3 mu = v3(S.pos[3 * i], S.pos[3 * i + 1], S.pos[3 * i + 2]);
+    const float4 qr = reinterpret_cast<const float4*>(S.quat)[i];
+    const float qn = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+    const float w = qr.x / qn, x = qr.y / qn, y = qr.z / qn, z = qr.w / qn;
+    V3 tu = v3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    V3 tv = v3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    V3 nw = v3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+    float Ro[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    bool has_obj = false;
+    if (S.obj_id) {
+        const int k = S.obj_id[i];
+        if (k >= 0 && k < a.n_obj) {
+            const float* P = a.poses + 12 * k;
+            const float R9[9] = {P[0], P[1], P[2], P[4], P[5], P[6], P[8], P[9], P[10]};
+            for (int t = 0; t < 9; ++t) Ro[t] = R9[t];
+            mu = mul(Ro, mu) + v3(P[3], P[7], P[11]);
+            tu = mul(Ro, tu);
+            tv = mul(Ro, tv);
+            nw = mul(Ro, nw);
+            has_obj = true;
+        }
+    }
+    const float2 ls = reinterpret_cast<const float2*>(S.log_scale)[i];
+    const float su = __expf(ls.x), sv = __expf(ls.y);
+    const float logit = S.opacity[i];
+    const float o = 1.f / (1.f + __expf(-logit));
+    const int deg = S.sh_degree;
+    const int K = (deg + 1) * (deg + 1);
+    const float* sh = S.sh + (size_t)i * K * 3;
+
+    // accumulated gradients (world, after the object pose)
+    V3 g_mu = v3(0, 0, 0), g_tu = v3(0, 0, 0), g_tv = v3(0, 0, 0), g_nw = v3(0, 0, 0);
+    float g_su = 0.f, g_sv = 0.f, g_o = 0.f, g_int = 0.f;
+    float g_sh[48];
+    for (int k = 0; k < 3 * K; ++k) g_sh[k] = 0.f;
+    bool any = false;
+
+    for (int si = 0; si < tab.n; ++si) {
+        const SensorDev& sd = tab.s[si];
+        const size_t slot = (size_t)si * S.n + i;
+        if (a.counts[slot] == 0) continue;
+        const float4* RG = a.recgrad + slot * kRecordF4;
+        const float4 G0 = RG[0], G1 = RG[1], G2 = RG[2], G3 = RG[3], G4 = RG[4];
+        any = true;
+        g_o += G3.x;
+        const V3 org = v3(sd.origin[0], sd.origin[1], sd.origin[2]);
+        V3 vd = mu - org;
+        const float flip = dot(nw, vd) > 0.f ? -1.f : 1.f;
+        // normal: n_s = R (flip nw)
+        g_nw = g_nw + flip * mulT(sd.R, v3(G4.x, G4.y, G4.z));
+        if (sd.kind == GSR_SENSOR_PINHOLE) {
+            const V3 ms = mul(sd.R, mu) + v3(sd.t[0], sd.t[1], sd.t[2]);
+            const V3 Rtu = mul(sd.R, tu), Rtv = mul(sd.R, tv);
+            const V3 A = su * Rtu, B = sv * Rtv;
+            const float iz = 1.f / ms.z;
+            const float ex = ms.x * iz, ey = ms.y * iz;
+            const float m00 = sd.fx * (A.x - ex * A.z), m01 = sd.fx * (B.x - ex * B.z);
+            const float m10 = sd.fy * (A.y - ey * A.z), m11 = sd.fy * (B.y - ey * B.z);
+            const float m20 = A.z, m21 = B.z;
+            const float det = m00 * m11 - m01 * m10;
+            // record: Q0 = (m11, -m01, 0), Q1 = (-m10, m00, 0),
+            // Q2 = ((m10 m21 - m11 m20) iz, (m01 m20 - m00 m21) iz, det iz), det, c = (fx ex + cx, fy ey + cy)
+            float g00 = G1.y, g01 = -G0.y, g10 = -G1.x, g11 = G0.x, g20 = 0.f, g21 = 0.f;
+            float g_det = G2.w + G2.z * iz;
+            float g_iz = G2.x * (m10 * m21 - m11 * m20) + G2.y * (m01 * m20 - m00 * m21) + G2.z * det;
+            g10 += G2.x * m21 * iz; g21 += G2.x * m10 * iz; g11 -= G2.x * m20 * iz; g20 -= G2.x * m11 * iz;
+            g01 += G2.y * m20 * iz; g20 += G2.y * m01 * iz; g00 -= G2.y * m21 * iz; g21 -= G2.y * m00 * iz;
+            g00 += g_det * m11; g11 += g_det * m00; g01 -= g_det * m10; g10 -= g_det * m01;
+            float g_ex = sd.fx * G0.w, g_ey = sd.fy * G1.w;
+            V3 gA = v3(sd.fx * g00, sd.fy * g10, -sd.fx * ex * g00 - sd.fy * ey * g10 + g20);
+            V3 gB = v3(sd.fx * g01, sd.fy * g11, -sd.fx * ex * g01 - sd.fy * ey * g11 + g21);
+            g_ex -= sd.fx * (A.z * g00 + B.z * g01);
+            g_ey -= sd.fy * (A.z * g10 + B.z * g11);
+            V3 g_ms = v3(g_ex * iz, g_ey * iz, G4.w);
+            g_iz += g_ex * ms.x + g_ey * ms.y;
+            g_ms.z += -g_iz * iz * iz;
+            g_mu = g_mu + mulT(sd.R, g_ms);
+            g_su += dot(Rtu, gA);
+            g_sv += dot(Rtv, gB);
+            g_tu = g_tu + su * mulT(sd.R, gA);
+            g_tv = g_tv + sv * mulT(sd.R, gB);
+            // colour: max(0, sum Y(d) c + 0.5), d = normalise(mu - origin) (object frame)
+            const float vlen = sqrtf(dot(vd, vd));
+            const V3 dw = (1.f / vlen) * vd;
+            const V3 dl = has_obj ? mulT(Ro, dw) : dw;
+            float b[16];
+            V3 gb[16];
+            sh_basis_grad(deg, dl, b, gb);
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+            for (int k = 0; k < K; ++k)
+                for (int c = 0; c < 3; ++c) raw[c] += b[k] * sh[3 * k + c];
+            const float gcol[3] = {raw[0] > 0.f ? G3.y : 0.f, raw[1] > 0.f ? G3.z : 0.f, raw[2] > 0.f ? G3.w : 0.f};
+            V3 g_dl = v3(0, 0, 0);
+            for (int k = 0; k < K; ++k) {
+                float s = 0.f;
+                for (int c = 0; c < 3; ++c) {
+                    g_sh[3 * k + c] += b[k] * gcol[c];
+                    s += sh[3 * k + c] * gcol[c];
+                }
+                g_dl = g_dl + s * gb[k];
+            }
+            const V3 g_dw = has_obj ? mul(Ro, g_dl) : g_dl;
+            g_mu = g_mu + (1.f / vlen) * (g_dw - dot(dw, g_dw) * dw);
+        } else {
+            g_int += G3.y;  // LiDAR intensity; geometry of LiDAR records is not chained (camera-only backward)
+        }
+    }
+    if (!any) return;
+    // opacity logit
+    a.G.opacity[i] += g_o * o * (1.f - o);
+    // scales
+    a.G.log_scale[2 * i] += g_su * su;
+    a.G.log_scale[2 * i + 1] += g_sv * sv;
+    if (a.G.intensity) a.G.intensity[i] += g_int;
+    // undo the object rotation
+    if (has_obj) {
+        g_mu = mulT(Ro, g_mu);
+        g_tu = mulT(Ro, g_tu);
+        g_tv = mulT(Ro, g_tv);
+        g_nw = mulT(Ro, g_nw);
+    }
+    a.G.pos[3 * i] += g_mu.x;
+    a.G.pos[3 * i + 1] += g_mu.y;
+    a.G.pos[3 * i + 2] += g_mu.z;
+    // rotation columns -> normalised quaternion -> raw quaternion
+    const float gw = 2.f * (z * g_tu.y - y * g_tu.z - z * g_tv.x + x * g_tv.z + y * g_nw.x - x * g_nw.y);
+    const float gx = 2.f * (y * g_tu.y + z * g_tu.z + y * g_tv.x - 2.f * x * g_tv.y + w * g_tv.z + z * g_nw.x -
+                            w * g_nw.y - 2.f * x * g_nw.z);
+    const float gy = 2.f * (-2.f * y * g_tu.x + x * g_tu.y - w * g_tu.z + x * g_tv.x + z * g_tv.z + w * g_nw.x +
+                            z * g_nw.y - 2.f * y * g_nw.z);
+    const float gz = 2.f * (-2.f * z * g_tu.x + w * g_tu.y + x * g_tu.z - w * g_tv.x - 2.f * z * g_tv.y + y * g_tv.z +
+                            x * g_nw.x + y * g_nw.y);
+    const float dq = w * gw + x * gx + y * gy + z * gz;
+    a.G.quat[4 * i] += (gw - w * dq) / qn;
+    a.G.quat[4 * i + 1] += (gx - x * dq) / qn;
+    a.G.quat[4 * i + 2] += (gy - y * dq) / qn;
+    a.G.quat[4 * i + 3] += (gz - z * dq) / qn;
+    for (int k = 0; k < 3 * K; ++k) a.G.sh[(size_t)i * K * 3 + k] += g_sh[k];
+}
+
+// ================================================================= host side
+size_t backward_smem_bytes(int threads) { return 128 + 2 * 256 * 4 + 2 * (size_t)threads * kRecordBytes; }
+
+cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd, const float* target,
+                        const gsr_loss_weights* wt, float* loss, const gsr_camera_grad* g, cudaStream_t st)
+{
+    const gsr_sensor& s = p->sensors[sensor];
+    LossArgs a;
+    a.rgb = fwd->rgb;
+    a.alpha = fwd->alpha;
+    a.dacc = fwd->depth_acc;
+    a.normal = fwd->normal;
+    a.target = target;
+    a.g_rgb = g->rgb;
+    a.g_alpha = g->alpha;
+    a.g_dacc = g->depth_acc;
+    a.g_normal = g->normal;
+    a.W = s.width;
+    a.H = s.height;
+    a.fx = s.fx; a.fy = s.fy; a.cx = s.cx; a.cy = s.cy;
+    a.w_dist = wt->w_dist;
+    a.w_norm = wt->w_normal;
+    a.mask_alpha = wt->mask_alpha;
+    const int HW = s.width * s.height;
+    const int blocks = (HW + 255) / 256;
+    a.scratch = region<float>(p, ws, R_LOSS_SCRATCH);
+    a.partial = a.scratch + (size_t)6 * HW;
+    k_loss_pixel<<<blocks, 256, 0, st>>>(a);
+    k_loss_gather<<<blocks, 256, 0, st>>>(a);
+    k_loss_reduce<<<1, 1024, 0, st>>>(a.partial, blocks, a.w_dist, a.w_norm, HW, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
+                                   const gsr_camera_grad* g, int accumulate, cudaStream_t st)
+{
+    const SensorTable tab = make_sensor_table(p);
+    const SensorDev& sd = tab.s[sensor];
+    float4* recgrad = region<float4>(p, ws, R_RECGRAD);
+    const uint64_t slots = (uint64_t)p->n_surfels * p->n_sensors;
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(recgrad, 0, slots * kRecordBytes, st);
+        if (e != cudaSuccess) return e;
+    }
+    BwdArgs a;
+    a.trans = fwd->trans;
+    a.n_contrib = fwd->n_contrib;
+    a.g_rgb = g->rgb;
+    a.g_alpha = g->alpha;
+    a.g_dacc = g->depth_acc;
+    a.g_normal = g->normal;
+    a.recgrad = recgrad;
+    const int threads = tab.tile_w * tab.tile_h;
+    const int tiles = sd.tiles_x * sd.tiles_y;
+    const int pb = sort_result_buffer(tile_sort_passes(p));
+    const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
+    k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, backward_smem_bytes(threads), st>>>(
+        tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a,
+        region<uint32_t>(p, ws, R_COUNTERS));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,
+                                       const gsr_objects* obj, const gsr_surfel_grads* out, cudaStream_t st)
+{
+    const SensorTable tab = make_sensor_table(p);
+    PreBwdArgs a;
+    a.S = *s;
+    a.poses = (obj && obj->n_objects > 0) ? obj->pose : nullptr;
+    a.n_obj = (obj && obj->n_objects > 0) ? obj->n_objects : 0;
+    a.recgrad = region<float4>(p, ws, R_RECGRAD);
+    a.counts = region<uint32_t>(p, ws, R_COUNTS);
+    a.G = *out;
+    if (s->n > 0) k_preprocess_backward<<<(s->n + 127) / 128, 128, 0, st>>>(tab, a);
+    return cudaGetLastError();
+}
+
+}  // namespace gsr

@@ -45,6 +45,8 @@ enum Region : int {
     R_HIST, R_PARTIAL,
     R_COUNTERS,
     R_SENSOR_OF_TILE,
+    R_RECGRAD,       // d(loss)/d(record), same layout as R_RECORDS
+    R_LOSS_SCRATCH,  // loss: [6][H][W] central-difference gradients + block partials
     R_END
 };
 
@@ -168,6 +170,82 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     set_status(counters, GSR_ERR_TIMEOUT);
     return false;
+}
+
+// ------------------------------------------------------------ splat evaluation
+// One ray against one staged record (Eqs. 2-3 / 2,5 in closed form plus the
+// 2DGS low-pass fallback).  Shared by the forward and backward rasterisers
+// so that both take bit-identical decisions.
+struct Splat {
+    float alpha;   // min(0.99, o G)
+    float z;       // contribution depth / distance
+    float G;       // Gaussian value of the chosen branch
+    float q0, q1, q2, u, v, rho;
+    float dx, dy;  // ray minus projected centre (pixels, or wrapped cells)
+    bool use3;     // ray-splat intersection (true) or low-pass (false)
+};
+
+template <int KIND>
+__device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float rx, float ry, float d0, float d1,
+                                           float d2, float near_plane, float columns, Splat& sp)
+{
+    const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+    float dx = rx - r0.w, dy = ry - r1.w;
+    float q0, q1, q2;
+    if (KIND == GSR_SENSOR_PINHOLE) {
+        q0 = fmaf(r0.x, dx, r0.y * dy);
+        q1 = fmaf(r1.x, dx, r1.y * dy);
+        q2 = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z));
+    } else {
+        q0 = fmaf(r0.x, d0, fmaf(r0.y, d1, r0.z * d2));
+        q1 = fmaf(r1.x, d0, fmaf(r1.y, d1, r1.z * d2));
+        q2 = fmaf(r2.x, d0, fmaf(r2.y, d1, r2.z * d2));
+        const float half = 0.5f * columns;
+        if (dx >= half) dx -= columns;
+        if (dx < -half) dx += columns;
+    }
+    const float rq = __fdividef(1.f, q2);
+    const float u = q0 * rq, v = q1 * rq;
+    const float zi = r2.w * rq;
+    const float rho3 = fmaf(u, u, v * v);
+    const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
+    const bool v3 = (zi > near_plane) && (rho3 <= kSupport);
+    const bool vlp = rholp <= kSupport;
+    if (!(v3 || vlp)) return false;
+    const bool use3 = v3 && (!vlp || rho3 <= rholp);
+    const float rho = use3 ? rho3 : rholp;
+    const float G = __expf(-0.5f * rho);
+    const float alpha = fminf(kAlphaMax, R[3].x * G);
+    if (alpha < kAlphaMin) return false;
+    sp.alpha = alpha;
+    sp.z = use3 ? zi : R[4].w;
+    sp.G = G;
+    sp.q0 = q0; sp.q1 = q1; sp.q2 = q2;
+    sp.u = u; sp.v = v; sp.rho = rho;
+    sp.dx = dx; sp.dy = dy;
+    sp.use3 = use3;
+    return true;
+}
+
+// Per-ray setup shared by the forward and backward rasterisers.
+template <int KIND>
+__device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, float& rx, float& ry, float& d0,
+                                          float& d1, float& d2)
+{
+    if (KIND == GSR_SENSOR_PINHOLE) {
+        rx = x + 0.5f;
+        ry = y + 0.5f;
+        d0 = d1 = d2 = 0.f;
+    } else {
+        rx = (float)x;
+        ry = (float)y;
+        float se, ce, sa, ca;
+        sincosf(sd.el_max - y * sd.d_el, &se, &ce);
+        sincosf(sd.az0 + (x + 0.5f) * sd.d_az, &sa, &ca);
+        d0 = ce * ca;
+        d1 = ce * sa;
+        d2 = se;
+    }
 }
 
 }  // namespace gsr

@@ -24,44 +24,6 @@ struct RayState {
     bool done;
 };
 
-// Evaluate one staged record for one ray.  Returns false if the surfel does
-// not contribute (outside both supports, or alpha < 1/255).
-template <int KIND>
-__device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float rx, float ry, float d0, float d1,
-                                           float d2, float near_plane, float columns, float& alpha, float& z)
-{
-    const float4 r0 = R[0], r1 = R[1], r2 = R[2];
-    float dx = rx - r0.w, dy = ry - r1.w;
-    float q0, q1, q2;
-    if (KIND == GSR_SENSOR_PINHOLE) {
-        q0 = fmaf(r0.x, dx, r0.y * dy);
-        q1 = fmaf(r1.x, dx, r1.y * dy);
-        q2 = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z));
-    } else {
-        q0 = fmaf(r0.x, d0, fmaf(r0.y, d1, r0.z * d2));
-        q1 = fmaf(r1.x, d0, fmaf(r1.y, d1, r1.z * d2));
-        q2 = fmaf(r2.x, d0, fmaf(r2.y, d1, r2.z * d2));
-        const float half = 0.5f * columns;
-        if (dx >= half) dx -= columns;
-        if (dx < -half) dx += columns;
-    }
-    const float rq = __fdividef(1.f, q2);
-    const float u = q0 * rq, v = q1 * rq;
-    const float zi = r2.w * rq;
-    const float rho3 = fmaf(u, u, v * v);
-    const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
-    const bool v3 = (zi > near_plane) && (rho3 <= kSupport);
-    const bool vlp = rholp <= kSupport;
-    if (!(v3 || vlp)) return false;
-    const bool use3 = v3 && (!vlp || rho3 <= rholp);
-    const float rho = use3 ? rho3 : rholp;
-    const float4 r3 = R[3];
-    alpha = fminf(kAlphaMax, r3.x * __expf(-0.5f * rho));
-    if (alpha < kAlphaMin) return false;
-    z = use3 ? zi : R[4].w;
-    return true;
-}
-
 template <int KIND>
 __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int tile_h, int local_tile,
                                             const uint2 range, const float4* __restrict__ rec,
@@ -75,20 +37,8 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
     const int y = ty * tile_h + tid / tile_w;
     const bool inside = x < sd.width && y < sd.height;
 
-    float rx, ry, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-    if (KIND == GSR_SENSOR_PINHOLE) {
-        rx = x + 0.5f;
-        ry = y + 0.5f;
-    } else {
-        rx = (float)x;
-        ry = (float)y;
-        float se, ce, sa, ca;
-        sincosf(sd.el_max - y * sd.d_el, &se, &ce);
-        sincosf(sd.az0 + (x + 0.5f) * sd.d_az, &sa, &ca);
-        d0 = ce * ca;
-        d1 = ce * sa;
-        d2 = se;
-    }
+    float rx, ry, d0, d1, d2;
+    ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
     RayState s;
     s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;
     s.f0 = s.f1 = s.f2 = 0.f;
@@ -128,8 +78,9 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
                 if (__all_sync(0xffffffffu, s.done)) break;
                 if (s.done) continue;
                 const float4* Rj = B + j * kRecordF4;
-                float alpha, z;
-                if (!splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, near_plane, columns, alpha, z)) continue;
+                Splat sp;
+                if (!splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, near_plane, columns, sp)) continue;
+                const float alpha = sp.alpha, z = sp.z;
                 const float Tn = s.T * (1.f - alpha);
                 if (Tn < kTMin) {
                     s.done = true;

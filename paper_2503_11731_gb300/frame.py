@@ -132,3 +132,98 @@ class Renderer:
         itemsize = torch.tensor([], dtype=dtype).element_size()
         n = nbytes // itemsize if count is None else count
         return self.ws[off:off + n * itemsize].view(dtype)
+
+
+# ----------------------------------------------------------------- training
+class LossOutputs:
+    """Per-pixel gradient buffers of gsr_loss for one camera."""
+
+    def __init__(self, H, W, device):
+        self.rgb = torch.zeros(3, H, W, device=device)
+        self.alpha = torch.zeros(H, W, device=device)
+        self.depth_acc = torch.zeros(2, H, W, device=device)
+        self.normal = torch.zeros(3, H, W, device=device)
+        self.loss = torch.zeros(4, device=device)
+
+    def struct(self):
+        return gsr.CameraGrad(_ptr(self.rgb), _ptr(self.alpha), _ptr(self.depth_acc), _ptr(self.normal))
+
+
+def _grad_struct(g):
+    return gsr.SurfelGrads(_ptr(g["pos"]), _ptr(g["log_scale"]), _ptr(g["quat"]), _ptr(g["opacity"]),
+                           _ptr(g["sh"]), _ptr(g.get("intensity")))
+
+
+def camera_loss(r: Renderer, sensor, target, w_dist=0.1, w_normal=0.05, mask_alpha=0.5, stream=None):
+    """gsr_loss on the last render of camera `sensor` (needs rgb, alpha,
+    depth_acc, normal outputs).  Returns (loss[4] tensor, LossOutputs)."""
+    o = r.out[sensor]
+    H, W = o["alpha"].shape
+    lo = getattr(r, "_loss_bufs", {}).get(sensor)
+    if lo is None:
+        lo = LossOutputs(H, W, r.device)
+        r._loss_bufs = getattr(r, "_loss_bufs", {})
+        r._loss_bufs[sensor] = lo
+    target = target.contiguous()
+    gsr.loss(r.plan, r.ws_ptr, r.ws_bytes, sensor, r._out_struct(sensor), _ptr(target),
+             gsr.LossWeights(w_dist, w_normal, mask_alpha), _ptr(lo.loss), lo.struct(), _stream_handle(stream))
+    return lo.loss, lo
+
+
+def camera_backward(r: Renderer, sensor, grad: "gsr.CameraGrad", surfels: DeviceSurfels, objects=None,
+                    out=None, stream=None):
+    """gsr_backward for one camera: d(loss)/d(surfel parameters), accumulated into `out` (dict of tensors)."""
+    if out is None:
+        out = {k: torch.zeros_like(getattr(surfels, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh")}
+    h = _stream_handle(stream)
+    obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
+    gsr.backward_render(r.plan, r.ws_ptr, r.ws_bytes, sensor, r._out_struct(sensor), grad, 0, h)
+    gsr.backward_preprocess(r.plan, r.ws_ptr, r.ws_bytes, surfels.struct(), obj, _grad_struct(out), h)
+    return out
+
+
+class RenderCameraFunction(torch.autograd.Function):
+    """Differentiable render of one camera through the C ABI.
+
+    forward: (pos, log_scale, quat, opacity, sh) -> (rgb, alpha, depth_acc, normal)
+    backward: gsr_backward_render + gsr_backward_preprocess.
+    The renderer's buffers hold the forward state: one forward/backward pair
+    per renderer is in flight at a time.
+    """
+
+    @staticmethod
+    def forward(ctx, renderer, sensor, pos, log_scale, quat, opacity, sh):
+        surf = DeviceSurfels(pos.detach().contiguous(), log_scale.detach().contiguous(),
+                             quat.detach().contiguous(), opacity.detach().contiguous(), sh.detach().contiguous())
+        renderer.render(surf)
+        o = renderer.out[sensor]
+        ctx.renderer, ctx.sensor, ctx.surf = renderer, sensor, surf
+        return o["rgb"].clone(), o["alpha"].clone(), o["depth_acc"].clone(), o["normal"].clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_alpha, g_dacc, g_normal):
+        z = lambda t, ref: torch.zeros_like(ref) if t is None else t.contiguous()
+        o = ctx.renderer.out[ctx.sensor]
+        g_rgb, g_alpha = z(g_rgb, o["rgb"]), z(g_alpha, o["alpha"])
+        g_dacc, g_normal = z(g_dacc, o["depth_acc"]), z(g_normal, o["normal"])
+        cg = gsr.CameraGrad(_ptr(g_rgb), _ptr(g_alpha), _ptr(g_dacc), _ptr(g_normal))
+        g = camera_backward(ctx.renderer, ctx.sensor, cg, ctx.surf)
+        return None, None, g["pos"], g["log_scale"], g["quat"], g["opacity"], g["sh"]
+
+
+class CameraLossFunction(torch.autograd.Function):
+    """gsr_loss as an autograd node: (rgb, alpha, depth_acc, normal) -> scalar loss."""
+
+    @staticmethod
+    def forward(ctx, renderer, sensor, target, rgb, alpha, depth_acc, normal, w_dist=0.1, w_normal=0.05):
+        o = renderer.out[sensor]
+        for k, t in (("rgb", rgb), ("alpha", alpha), ("depth_acc", depth_acc), ("normal", normal)):
+            o[k].copy_(t)
+        loss, lo = camera_loss(renderer, sensor, target, w_dist, w_normal)
+        ctx.grads = (lo.rgb.clone(), lo.alpha.clone(), lo.depth_acc.clone(), lo.normal.clone())
+        return loss[0].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        gr, ga, gd, gn = (t * g for t in ctx.grads)
+        return None, None, None, gr, ga, gd, gn, None, None

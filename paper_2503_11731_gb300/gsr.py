@@ -58,7 +58,20 @@ class LidarOut(ctypes.Structure):
     _fields_ = [("range", c_vp), ("intensity", c_vp), ("alpha", c_vp), ("trans", c_vp), ("n_contrib", c_vp)]
 
 
-_STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling]
+class CameraGrad(ctypes.Structure):
+    _fields_ = [("rgb", c_vp), ("alpha", c_vp), ("depth_acc", c_vp), ("normal", c_vp)]
+
+
+class SurfelGrads(ctypes.Structure):
+    _fields_ = [("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp),
+                ("intensity", c_vp)]
+
+
+class LossWeights(ctypes.Structure):
+    _fields_ = [("w_dist", c_f32), ("w_normal", c_f32), ("mask_alpha", c_f32)]
+
+
+_STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights]
 
 # exported symbols and their ctypes signatures (restype, argtypes)
 SIGNATURES = {
@@ -79,6 +92,15 @@ SIGNATURES = {
     "gsr_workspace_region": (c_i32, [ctypes.POINTER(Plan), c_vp, c_i32, ctypes.POINTER(c_vp),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "gsr_struct_size": (ctypes.c_size_t, [c_i32]),
+    "gsr_loss": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut), c_vp,
+                         ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
+    "gsr_backward_render": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
+                                    ctypes.POINTER(CameraGrad), c_i32, c_vp]),
+    "gsr_backward_preprocess": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(Surfels),
+                                        ctypes.POINTER(Objects), ctypes.POINTER(SurfelGrads), c_vp]),
+    "gsr_backward": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
+                             ctypes.POINTER(CameraGrad), ctypes.POINTER(Surfels), ctypes.POINTER(Objects),
+                             ctypes.POINTER(SurfelGrads), c_vp]),
 }
 
 _lib = None
@@ -189,3 +211,20 @@ def workspace_region(plan, ws, which):
     _check(lib().gsr_workspace_region(ctypes.byref(plan), ws, int(which), ctypes.byref(ptr), ctypes.byref(n)),
            "gsr_workspace_region")
     return int(ptr.value or 0), int(n.value)
+
+
+def loss(plan, ws, ws_bytes, sensor_idx, fwd: CameraOut, target, weights: LossWeights, loss_out, grad: CameraGrad,
+         stream):
+    _check(lib().gsr_loss(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(fwd), target,
+                          ctypes.byref(weights), loss_out, ctypes.byref(grad), stream), "gsr_loss")
+
+
+def backward_render(plan, ws, ws_bytes, sensor_idx, fwd: CameraOut, grad: CameraGrad, accumulate, stream):
+    _check(lib().gsr_backward_render(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(fwd),
+                                     ctypes.byref(grad), int(accumulate), stream), "gsr_backward_render")
+
+
+def backward_preprocess(plan, ws, ws_bytes, surfels: Surfels, objects, out: SurfelGrads, stream):
+    _check(lib().gsr_backward_preprocess(ctypes.byref(plan), ws, ws_bytes, ctypes.byref(surfels),
+                                         ctypes.byref(objects) if objects is not None else None,
+                                         ctypes.byref(out), stream), "gsr_backward_preprocess")

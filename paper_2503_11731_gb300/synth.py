@@ -144,8 +144,9 @@ def _plane_quats(rng, normal, n):
 # ---------------------------------------------------------------------------
 # Sensors
 # ---------------------------------------------------------------------------
-def camera_pose(position, yaw_deg=0.0, pitch_deg=0.0) -> np.ndarray:
-    """world->camera for a camera at `position` looking along yaw (from +x towards +y)."""
+def camera_pose(position, yaw_deg=0.0, pitch_deg=0.0, f32=True) -> np.ndarray:
+    """world->camera for a camera at `position` looking along yaw (from +x
+    towards +y); rounded to float32 values unless f32=False."""
     yaw, pitch = math.radians(yaw_deg), math.radians(pitch_deg)
     f = np.array([math.cos(yaw) * math.cos(pitch), math.sin(yaw) * math.cos(pitch), math.sin(pitch)])
     up = np.array([0.0, 0.0, 1.0])
@@ -156,10 +157,16 @@ def camera_pose(position, yaw_deg=0.0, pitch_deg=0.0) -> np.ndarray:
     M = np.eye(4)
     M[:3, :3] = R
     M[:3, 3] = -R @ np.asarray(position, np.float64)
-    return M
+    return _f32(M) if f32 else M
 
 
-def lidar_pose(position, yaw_deg=0.0) -> np.ndarray:
+def _f32(a):
+    """Round to float32-representable values: the C ABI carries poses in
+    float32, so every consumer sees exactly the same numbers."""
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def lidar_pose(position, yaw_deg=0.0, f32=True) -> np.ndarray:
     yaw = math.radians(yaw_deg)
     R = np.array([[math.cos(yaw), math.sin(yaw), 0.0],
                   [-math.sin(yaw), math.cos(yaw), 0.0],
@@ -167,7 +174,7 @@ def lidar_pose(position, yaw_deg=0.0) -> np.ndarray:
     M = np.eye(4)
     M[:3, :3] = R
     M[:3, 3] = -R @ np.asarray(position, np.float64)
-    return M
+    return _f32(M) if f32 else M
 
 
 def pinhole(width, height, f, position=(0, 0, 0), yaw_deg=0.0, pitch_deg=0.0, pose=None, near=0.2):
@@ -321,7 +328,7 @@ def object_poses(n_obj, seed, x_range=(-40.0, 80.0)):
         c, s = math.cos(yaw), math.sin(yaw)
         P[k, :3, :3] = [[c, -s, 0], [s, c, 0], [0, 0, 1]]
         P[k, :, 3] = [rng.uniform(*x_range), rng.uniform(-6.5, 6.5), 0.0]
-    return P
+    return _f32(P)
 
 
 def surround_rig():

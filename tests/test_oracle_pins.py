@@ -81,7 +81,7 @@ def _ray_plane(o, d, mu, Rm, s):
 
 def test_eq2_pinhole_matches_direct_ray_plane():
     rng = np.random.default_rng(1)
-    pose = synth.camera_pose((1.0, -2.0, 1.5), 20.0, -5.0)
+    pose = synth.camera_pose((1.0, -2.0, 1.5), 20.0, -5.0, f32=False)
     Rc, tc = pose[:3, :3], pose[:3, 3]
     origin = -Rc.T @ tc
     cam = (500.0, 480.0, 320.0, 240.0)
@@ -102,7 +102,7 @@ def test_eq2_pinhole_matches_direct_ray_plane():
 
 def test_eq5_lidar_matches_direct_ray_plane():
     rng = np.random.default_rng(2)
-    pose = synth.lidar_pose((0.3, 0.1, 1.8), 15.0)
+    pose = synth.lidar_pose((0.3, 0.1, 1.8), 15.0, f32=False)
     Rl, tl = pose[:3, :3], pose[:3, 3]
     origin = -Rl.T @ tl
     for _ in range(200):

@@ -196,7 +196,7 @@ def run_gpu(args):
     dev = DeviceSurfels.from_host(scene)
     pose_t = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
     r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup,
-                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"))
+                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     n_cam = sum(1 for s in sensors if s.kind != "lidar")
 
@@ -227,6 +227,14 @@ def run_gpu(args):
     st, nvis, npairs = r.status()
     if st != 0:
         raise RuntimeError(f"device status {st} (pairs {npairs}, capacity {r.plan.max_dup})")
+    counts = r.region(2, torch.int32)
+    per_sensor = []
+    for si, s in enumerate(sensors):
+        c = counts[si * scene.n:(si + 1) * scene.n]
+        per_sensor.append({"kind": s.kind, "rays": s.width * s.height, "visible": int((c > 0).sum()),
+                           "pairs": int(c.sum()),
+                           "mean_walk": float(r.out[si]["n_walk"].float().mean()),
+                           "mean_last_contrib": float(r.out[si]["n_contrib"].float().mean())})
 
     clk_p, clk_f = sample_clocks_start() if rank == 0 else (None, None)
     time.sleep(0.3)
@@ -292,15 +300,15 @@ def run_gpu(args):
 
     # ---- roofline of the dominant stage (camera compositing)
     pk, src = peaks()
-    n_contrib = sum(int(o["n_contrib"].sum().item()) for o, s in zip(r.out, sensors) if s.kind != "lidar")
+    n_walk = sum(int(o["n_walk"].sum().item()) for o, s in zip(r.out, sensors) if s.kind != "lidar")
     ops_per_pair = 24  # FP32 lane-ops of one ray-surfel evaluation
     alu_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
     cam_ms = stage["cam"]
-    achieved = n_contrib * ops_per_pair / (cam_ms * 1e-3) / 1e12
+    achieved = n_walk * ops_per_pair / (cam_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "k_render<pinhole> (6 cameras)", "achieved": achieved, "peak": alu_peak,
             "unit": "T FP32 lane-op/s", "frac": achieved / alu_peak, "traffic": None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock of " + src + " peaks",
-            "algorithmic_units": f"{n_contrib} ray-surfel pairs (sum of per-ray walked list lengths) x {ops_per_pair}"}
+            "algorithmic_units": f"{n_walk} ray-surfel evaluations (sum over rays of the list entries each must examine) x {ops_per_pair}"}
     launches_per_step = 1 + (3 + 3 * 4 + 3 + 3 * 2 + 1) + len(sensors)
     cpu = cpu_baseline_quick(scene, poses, sensors, args.sample_rays) if args.sample_rays > 0 else None
     total_rays = n_rays(sensors)
@@ -314,6 +322,7 @@ def run_gpu(args):
                    "tile_pairs": npairs, "l2": "inputs (1.0 GB surfel table) larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},
         "stage_ms": stage,
+        "per_sensor": per_sensor,
         "mray_per_s": total_rays / (value * 1e-3) / 1e6,
         "roofline": roof,
         "cpu_baseline": cpu,

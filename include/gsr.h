@@ -137,7 +137,9 @@ typedef struct {
  *   alpha     [H][W]     sum w
  *   trans     [H][W]     final transmittance T
  *   depth_acc [2][H][W]  sum w z, sum w z^2 (for the distortion loss)
- *   n_contrib [H][W]     uint32: tile-list entries walked (for the backward)
+ *   n_contrib [H][W]     uint32: list position of the last contributor + 1 (for the backward)
+ *   n_walk    [H][W]     uint32: list entries the ray had to examine (its stop
+ *                        position, or the whole tile list if it never saturated)
  */
 typedef struct {
     float* rgb;
@@ -147,12 +149,13 @@ typedef struct {
     float* trans;
     float* depth_acc;
     uint32_t* n_contrib;
+    uint32_t* n_walk;
 } gsr_camera_out;
 
 /*
  * Per-ray outputs of a LiDAR (DEVICE, [beams][columns]; any may be NULL):
  *   range = sum w t / sum w (0 where sum w == 0), intensity = sum w r,
- *   alpha = sum w, trans = final T, n_contrib as for the camera.
+ *   alpha = sum w, trans = final T, n_contrib and n_walk as for the camera.
  */
 typedef struct {
     float* range;
@@ -160,6 +163,7 @@ typedef struct {
     float* alpha;
     float* trans;
     uint32_t* n_contrib;
+    uint32_t* n_walk;
 } gsr_lidar_out;
 
 /*

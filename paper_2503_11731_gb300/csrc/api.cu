@@ -212,7 +212,8 @@ extern "C" gsr_status gsr_render_camera(const gsr_plan* plan, const void* worksp
     if (st != GSR_OK) return st;
     if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
     if (plan->sensors[sensor].kind != GSR_SENSOR_PINHOLE) return GSR_ERR_INVALID_ARG;
-    FrameOut o{out->rgb, out->depth, out->normal, out->alpha, out->trans, out->depth_acc, out->n_contrib};
+    FrameOut o{out->rgb, out->depth, out->normal, out->alpha, out->trans, out->depth_acc, out->n_contrib,
+               out->n_walk};
     return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -223,7 +224,8 @@ extern "C" gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspa
     if (st != GSR_OK) return st;
     if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
     if (plan->sensors[sensor].kind != GSR_SENSOR_LIDAR) return GSR_ERR_INVALID_ARG;
-    FrameOut o{out->intensity, out->range, nullptr, out->alpha, out->trans, nullptr, out->n_contrib};
+    FrameOut o{out->intensity, out->range, nullptr, out->alpha, out->trans, nullptr, out->n_contrib,
+               out->n_walk};
     return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -99,6 +99,7 @@ struct FrameOut {
     float* trans;
     float* depth_acc;  // [2][H][W]
     uint32_t* n_contrib;
+    uint32_t* n_walk;
 };
 
 SensorTable make_sensor_table(const gsr_plan* p);

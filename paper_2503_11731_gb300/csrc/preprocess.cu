@@ -112,6 +112,17 @@ __device__ __forceinline__ void project(const SensorDev& s, F3 p, float& x, floa
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
 }
 
+// Distance from the origin to the 2D segment p -> q.
+__device__ __forceinline__ float seg_dist(float px, float py, float qx, float qy)
+{
+    const float ex = qx - px, ey = qy - py;
+    const float ee = fmaf(ex, ex, ey * ey);
+    float t = ee > 0.f ? -(px * ex + py * ey) / ee : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float dx = fmaf(t, ex, px), dy = fmaf(t, ey, py);
+    return sqrtf(fmaf(dx, dx, dy * dy));
+}
+
 // Pixel/cell index range [i0, i1] whose centres (index + off) can fall in [lo, hi].
 __device__ __forceinline__ void index_range(float lo, float hi, float off, int n, int& i0, int& i1)
 {
@@ -163,9 +174,20 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     float4 r0, r1, r2;
     const int TW = tab.tile_w, TH = tab.tile_h;
 
+    // Opacity-aware support: alpha = min(0.99, o G) reaches 1/255 only where
+    // G >= 1/(255 o), i.e. rho <= 2 ln(255 o); a surfel with o < 1/255 never
+    // contributes.  rho_cut (with a margin for FP32 rounding) bounds both the
+    // ray-splat support (radius sqrt(rho_cut) sigma) and the low-pass disc
+    // (radius sqrt(rho_cut / 2) px or cells).
+    const float o = 1.f / (1.f + __expf(-__ldg(S.opacity + i)));
+    const float rho_cut = fminf(kSupport, 2.f * __logf(255.f * o) + 1e-3f);
+    const float ksig = sqrtf(fmaxf(rho_cut, 0.f));
+    const float rlp = sqrtf(fmaxf(0.5f * rho_cut, 0.f));
+    const bool never = !(rho_cut > 0.f);
+
     if (sd.kind == GSR_SENSOR_PINHOLE) {
         zkey = ms.z;
-        if (!(ms.z > sd.near_plane)) {
+        if (!(ms.z > sd.near_plane) || never) {
             counts[slot] = 0;
             keys[slot] = __float_as_uint(fmaxf(zkey, 0.f));
             rects[slot] = rect;
@@ -184,10 +206,11 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         r1 = make_float4(-m10, m00, 0.f, ccy);
         r2 = make_float4(fmaf(m10, m21, -m11 * m20) * iz, fmaf(m01, m20, -m00 * m21) * iz, det * iz, det);
 
-        // 3-sigma bound: the square mu +- 3a +- 3b clipped to z >= near, projected
-        float xmin = ccx - kLowPassRadius, xmax = ccx + kLowPassRadius;
-        float ymin = ccy - kLowPassRadius, ymax = ccy + kLowPassRadius;
-        F3 P[4] = {ms + 3.f * a + 3.f * b, ms + 3.f * a - 3.f * b, ms - 3.f * a - 3.f * b, ms - 3.f * a + 3.f * b};
+        // support bound: the square mu +- k a +- k b clipped to z >= near, projected
+        float xmin = ccx - rlp, xmax = ccx + rlp;
+        float ymin = ccy - rlp, ymax = ccy + rlp;
+        const F3 ka = ksig * a, kb = ksig * b;
+        F3 P[4] = {ms + ka + kb, ms + ka - kb, ms - ka - kb, ms - ka + kb};
         const float zn = sd.near_plane;
         float px, py;
 #pragma unroll
@@ -213,7 +236,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     } else {
         const float rc = sqrtf(dot(ms, ms));
         zkey = rc;
-        if (!(rc > sd.near_plane)) {
+        if (!(rc > sd.near_plane) || never) {
             counts[slot] = 0;
             keys[slot] = __float_as_uint(fmaxf(zkey, 0.f));
             rects[slot] = rect;
@@ -239,29 +262,81 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         r1 = make_float4(q10, q11, q12, crow);
         r2 = make_float4(q20, q21, q22, det);
 
-        // angular bound of the sphere (radius 3 max(s)) around mu, united with the low-pass disc
-        const float rad = 3.f * fmaxf(su, sv);
+        // Angular bound of the support ellipse, united with the low-pass disc.
+        // The ellipse {mu + k(c a + s b)} lies inside the circumscribed octagon
+        // with vertices mu + (k / cos 22.5deg)(cos t_j a + sin t_j b),
+        // t_j = 22.5 + 45 j deg.  For a convex planar polygon whose plane misses
+        // the sensor and whose xy-projection misses the z axis, azimuth is
+        // monotonic along each edge (extremes at vertices) and elevation has no
+        // interior extremum (its gradient is orthogonal to the position, so it
+        // cannot be parallel to a plane normal n with n.x != 0), so per-edge
+        // bounds on atan(z / rho) cover it: max z over min rho (z >= 0) or over
+        // max rho (z < 0), and symmetrically for the minimum.  Other cases fall
+        // back to the bounding sphere of the octagon.
+        const float kk = ksig * 1.0823922f;
+        const float rad = kk * fmaxf(su, sv);
         int i0, i1, tx0, tx1;
         const int A = sd.width;
         const int tiles_x = sd.tiles_x;
-        bool full_rows = !(rc > rad * 1.0001f + 1e-6f);
-        bool full_cols = full_rows || !(rxy > rad * 1.0001f + 1e-6f);
+        const bool full_rows = !(rc > rad * 1.0001f + 1e-6f);
+        const bool full_cols = full_rows || !(rxy > rad * 1.0001f + 1e-6f);
+        F3 nrm = f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+        const float plane_off = fabsf(dot(nrm, ms)) * rsqrtf(fmaxf(dot(nrm, nrm), 1e-30f));
+        const bool octagon = !full_cols && plane_off > 1e-3f * rc;
+        float el_lo = el, el_hi = el, az_lo = 0.f, az_hi = 0.f;
+        if (octagon) {
+            const float cs[8] = {0.92387953f, 0.38268343f, -0.38268343f, -0.92387953f,
+                                 -0.92387953f, -0.38268343f, 0.38268343f, 0.92387953f};
+            const float sn[8] = {0.38268343f, 0.92387953f, 0.92387953f, 0.38268343f,
+                                 -0.38268343f, -0.92387953f, -0.92387953f, -0.38268343f};
+            F3 V[8];
+            float rv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                V[j] = ms + kk * (cs[j] * a + sn[j] * b);
+                rv[j] = sqrtf(fmaf(V[j].x, V[j].x, V[j].y * V[j].y));
+                float dz = atan2f(V[j].y, V[j].x) - az;
+                if (dz > 3.14159265f) dz -= 6.28318531f;
+                if (dz < -3.14159265f) dz += 6.28318531f;
+                az_lo = fminf(az_lo, dz);
+                az_hi = fmaxf(az_hi, dz);
+            }
+            el_lo = 1e30f;
+            el_hi = -1e30f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const F3 P0 = V[j], P1 = V[(j + 1) & 7];
+                const float rmin = seg_dist(P0.x, P0.y, P1.x, P1.y);
+                const float rmax = fmaxf(rv[j], rv[(j + 1) & 7]);
+                const float zmax = fmaxf(P0.z, P1.z), zmin = fminf(P0.z, P1.z);
+                el_hi = fmaxf(el_hi, atan2f(zmax, zmax >= 0.f ? rmin : rmax));
+                el_lo = fminf(el_lo, atan2f(zmin, zmin <= 0.f ? rmin : rmax));
+            }
+        } else if (!full_rows) {
+            const float beta = asinf(fminf(rad / rc, 1.f));
+            el_lo = el - beta;
+            el_hi = el + beta;
+            if (!full_cols) {
+                const float gam = asinf(fminf(rad / rxy, 1.f));
+                az_lo = -gam;
+                az_hi = gam;
+            }
+        }
         if (full_rows) {
             i0 = 0;
             i1 = sd.height - 1;
         } else {
-            const float beta = asinf(fminf(rad / rc, 1.f));
-            float lo = fminf((sd.el_max - (el + beta)) * sd.inv_d_el, crow - kLowPassRadius) - 1.f;
-            float hi = fmaxf((sd.el_max - (el - beta)) * sd.inv_d_el, crow + kLowPassRadius) + 1.f;
+            float lo = fminf((sd.el_max - el_hi) * sd.inv_d_el, crow - rlp) - 1.f;
+            float hi = fmaxf((sd.el_max - el_lo) * sd.inv_d_el, crow + rlp) + 1.f;
             index_range(lo, hi, 0.f, sd.height, i0, i1);
         }
         if (full_cols) {
             tx0 = 0;
             tx1 = tiles_x - 1;
         } else {
-            const float gam = asinf(fminf(rad / rxy, 1.f)) * sd.inv_d_az;
-            const float w = fmaxf(gam, kLowPassRadius) + 1.f;
-            const int j0 = (int)ceilf(ccol - w), j1 = (int)floorf(ccol + w);
+            const float clo = fminf(az_lo * sd.inv_d_az, -rlp) - 1.f;
+            const float chi = fmaxf(az_hi * sd.inv_d_az, rlp) + 1.f;
+            const int j0 = (int)ceilf(ccol + clo), j1 = (int)floorf(ccol + chi);
             if (j1 - j0 + 1 >= A) {
                 tx0 = 0;
                 tx1 = tiles_x - 1;
@@ -296,7 +371,6 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     if (dot(nw, vd) > 0.f) nw = -1.f * nw;
     const F3 ns = mat3(sd.R, nw);
     float4 r3;
-    const float o = 1.f / (1.f + __expf(-__ldg(S.opacity + i)));
     if (sd.kind == GSR_SENSOR_PINHOLE) {
         vd = rsqrtf(vlen2) * vd;
         if (Ro != nullptr) {

@@ -21,6 +21,7 @@ struct RayState {
     float f0, f1, f2;
     float n0, n1, n2;
     uint32_t last;
+    uint32_t walk;
     bool done;
 };
 
@@ -44,6 +45,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
     s.f0 = s.f1 = s.f2 = 0.f;
     s.n0 = s.n1 = s.n2 = 0.f;
     s.last = 0;
+    s.walk = (uint32_t)(range.y - range.x);
     s.done = !inside;
 
     const uint32_t start = range.x;
@@ -84,6 +86,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
                 const float Tn = s.T * (1.f - alpha);
                 if (Tn < kTMin) {
                     s.done = true;
+                    s.walk = (uint32_t)(b * nthr + j + 1);
                     continue;
                 }
                 const float w = alpha * s.T;
@@ -140,6 +143,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
         out.depth_acc[HW + pix] = s.D;
     }
     if (out.n_contrib) out.n_contrib[pix] = s.last;
+    if (out.n_walk) out.n_walk[pix] = s.walk;
 }
 
 template <int KIND>

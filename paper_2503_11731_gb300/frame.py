@@ -74,8 +74,9 @@ class Renderer:
                 for k in ("range", "intensity", "alpha", "trans"):
                     if k in outputs or k in ("range", "intensity"):
                         o[k] = torch.zeros(H, W, device=device)
-                if "n_contrib" in outputs:
-                    o["n_contrib"] = torch.zeros(H, W, dtype=torch.int32, device=device)
+                for k in ("n_contrib", "n_walk"):
+                    if k in outputs:
+                        o[k] = torch.zeros(H, W, dtype=torch.int32, device=device)
             else:
                 if "rgb" in outputs:
                     o["rgb"] = torch.zeros(3, H, W, device=device)
@@ -86,17 +87,18 @@ class Renderer:
                         o[k] = torch.zeros(H, W, device=device)
                 if "depth_acc" in outputs:
                     o["depth_acc"] = torch.zeros(2, H, W, device=device)
-                if "n_contrib" in outputs:
-                    o["n_contrib"] = torch.zeros(H, W, dtype=torch.int32, device=device)
+                for k in ("n_contrib", "n_walk"):
+                    if k in outputs:
+                        o[k] = torch.zeros(H, W, dtype=torch.int32, device=device)
             self.out.append(o)
 
     def _out_struct(self, i):
         o = self.out[i]
         g = lambda k: _ptr(o.get(k))
         if self.descs[i].kind == "lidar":
-            return gsr.LidarOut(g("range"), g("intensity"), g("alpha"), g("trans"), g("n_contrib"))
+            return gsr.LidarOut(g("range"), g("intensity"), g("alpha"), g("trans"), g("n_contrib"), g("n_walk"))
         return gsr.CameraOut(g("rgb"), g("depth"), g("normal"), g("alpha"), g("trans"), g("depth_acc"),
-                             g("n_contrib"))
+                             g("n_contrib"), g("n_walk"))
 
     def preprocess(self, surfels: DeviceSurfels, objects=None, stream=None):
         obj = None

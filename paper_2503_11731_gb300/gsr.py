@@ -51,11 +51,12 @@ class Plan(ctypes.Structure):
 
 class CameraOut(ctypes.Structure):
     _fields_ = [("rgb", c_vp), ("depth", c_vp), ("normal", c_vp), ("alpha", c_vp), ("trans", c_vp),
-                ("depth_acc", c_vp), ("n_contrib", c_vp)]
+                ("depth_acc", c_vp), ("n_contrib", c_vp), ("n_walk", c_vp)]
 
 
 class LidarOut(ctypes.Structure):
-    _fields_ = [("range", c_vp), ("intensity", c_vp), ("alpha", c_vp), ("trans", c_vp), ("n_contrib", c_vp)]
+    _fields_ = [("range", c_vp), ("intensity", c_vp), ("alpha", c_vp), ("trans", c_vp), ("n_contrib", c_vp),
+                ("n_walk", c_vp)]
 
 
 class CameraGrad(ctypes.Structure):

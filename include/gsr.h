@@ -46,7 +46,8 @@ typedef enum {
     GSR_ERR_WORKSPACE = 3,    /* workspace too small or misaligned                        */
     GSR_ERR_CAPACITY = 4,     /* more tile/surfel pairs than max_dup (device status)      */
     GSR_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (device status)            */
-    GSR_ERR_UNSUPPORTED = 6   /* e.g. SH degree > 3, a sensor kind not built              */
+    GSR_ERR_UNSUPPORTED = 6,  /* e.g. SH degree > 3, a sensor kind not built              */
+    GSR_ERR_TOO_LARGE = 7     /* a size beyond a fixed built-in limit                     */
 } gsr_status;
 
 typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1 } gsr_sensor_kind;
@@ -285,6 +286,34 @@ gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t wor
 gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
                                    const gsr_surfels* surfels, const gsr_objects* objects,
                                    const gsr_surfel_grads* out, void* stream);
+
+/*
+ * gsr_loss_noalloc -- the same loss and per-pixel gradients as gsr_loss, for
+ * callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is off limits (inside a caller's own memory pool or arena, in a
+ * process whose allocator is owned by another runtime, or on a path that must
+ * never grow the device footprint) and so cannot provide a plan workspace.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * It takes no plan and no workspace.  Its scratch (6 floats per pixel plus
+ * block partial sums) lives in one fixed array in the library's own device
+ * memory, sized for GSR_NOALLOC_MAX_PIXELS pixels (48 MiB + 96 KiB); every
+ * GPU that loads the library holds that array until the process exits.
+ * camera: the pinhole descriptor (host); fwd->rgb, alpha, depth_acc, normal,
+ * target_rgb, loss[4] and all four planes of *grad as for gsr_loss.
+ * Errors: GSR_ERR_TOO_LARGE if width * height > GSR_NOALLOC_MAX_PIXELS;
+ * GSR_ERR_INVALID_ARG / GSR_ERR_UNSUPPORTED as for gsr_loss.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  No call allocates or frees device memory.  All calls share the
+ * one array, so calls that overlap on the GPU (on different streams, or from
+ * different threads, on the same device) race and must be serialised by the
+ * caller; nothing in the array needs to start at zero.
+ */
+#define GSR_NOALLOC_MAX_PIXELS 2097152
+gsr_status gsr_loss_noalloc(const gsr_sensor* camera, const gsr_camera_out* fwd, const float* target_rgb,
+                            const gsr_loss_weights* weights, float* loss, const gsr_camera_grad* grad,
+                            void* stream);
 
 /* gsr_backward_render (accumulate = 0) + gsr_backward_preprocess for one camera. */
 gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,

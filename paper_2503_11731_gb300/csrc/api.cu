@@ -31,6 +31,10 @@ static gsr_status cuda_fail(cudaError_t e)
     return GSR_ERR_CUDA;
 }
 
+// Status of a CUDA result for entry points in other translation units
+// (records the error string like the entry points here).
+gsr_status cuda_status(cudaError_t e) { return cuda_fail(e); }
+
 SensorTable make_sensor_table(const gsr_plan* p)
 {
     SensorTable t;
@@ -259,6 +263,7 @@ extern "C" const char* gsr_status_string(gsr_status s)
     case GSR_ERR_CAPACITY: return "GSR_ERR_CAPACITY";
     case GSR_ERR_TIMEOUT: return "GSR_ERR_TIMEOUT";
     case GSR_ERR_UNSUPPORTED: return "GSR_ERR_UNSUPPORTED";
+    case GSR_ERR_TOO_LARGE: return "GSR_ERR_TOO_LARGE";
     }
     return "GSR_ERR_UNKNOWN";
 }

@@ -13,6 +13,9 @@
 //      chains the record gradients to the raw surfel parameters (the
 //      inverse of the preprocess of Eqs. 1-3), one thread per surfel,
 //      summing over sensors without atomics.
+#include <atomic>
+#include <mutex>
+
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -672,3 +675,89 @@ cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const 
 }
 
 }  // namespace gsr
+
+// ===================================================== allocation-free loss
+// Scratch of gsr_loss_noalloc: a fixed file-scope device array, so callers
+// that cannot allocate device memory still get the loss.  Host code only
+// ever passes its device address (looked up once per device below) to the
+// kernels; the symbol itself is a host-side stand-in.
+static constexpr size_t kNoAllocScratchFloats =
+    6ull * GSR_NOALLOC_MAX_PIXELS + 3ull * (GSR_NOALLOC_MAX_PIXELS / 256) + 64;
+static __device__ __align__(256) float g_noalloc_loss_scratch[kNoAllocScratchFloats];
+
+namespace gsr {
+
+gsr_status cuda_status(cudaError_t e);
+
+// Device address of g_noalloc_loss_scratch on the current device `dev`,
+// looked up on the first call for that device and cached.
+static float* noalloc_scratch(int dev, cudaError_t* err)
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<float*> cache[kMaxDevices];
+    static std::mutex mu;
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    float* p = cache[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    std::lock_guard<std::mutex> lock(mu);
+    p = cache[dev].load(std::memory_order_relaxed);
+    if (p) return p;
+    void* addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_loss_scratch);
+    if (e != cudaSuccess || addr == nullptr) {
+        *err = e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        return nullptr;
+    }
+    p = static_cast<float*>(addr);
+    cache[dev].store(p, std::memory_order_release);
+    return p;
+}
+
+}  // namespace gsr
+
+extern "C" gsr_status gsr_loss_noalloc(const gsr_sensor* camera, const gsr_camera_out* fwd, const float* target_rgb,
+                                       const gsr_loss_weights* weights, float* loss, const gsr_camera_grad* grad,
+                                       void* stream)
+{
+    using namespace gsr;
+    if (!camera || !fwd || !target_rgb || !weights || !loss || !grad) return GSR_ERR_INVALID_ARG;
+    if (camera->kind != GSR_SENSOR_PINHOLE) return GSR_ERR_UNSUPPORTED;
+    if (camera->width <= 0 || camera->height <= 0 || !(camera->fx > 0.f && camera->fy > 0.f))
+        return GSR_ERR_INVALID_ARG;
+    if ((int64_t)camera->width * camera->height > GSR_NOALLOC_MAX_PIXELS) return GSR_ERR_TOO_LARGE;
+    if (!fwd->rgb || !fwd->alpha || !fwd->depth_acc || !fwd->normal) return GSR_ERR_INVALID_ARG;
+    if (!grad->rgb || !grad->alpha || !grad->depth_acc || !grad->normal) return GSR_ERR_INVALID_ARG;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    float* scratch = noalloc_scratch(dev, &e);
+    if (!scratch) return cuda_status(e);
+    LossArgs a;
+    a.rgb = fwd->rgb;
+    a.alpha = fwd->alpha;
+    a.dacc = fwd->depth_acc;
+    a.normal = fwd->normal;
+    a.target = target_rgb;
+    a.g_rgb = grad->rgb;
+    a.g_alpha = grad->alpha;
+    a.g_dacc = grad->depth_acc;
+    a.g_normal = grad->normal;
+    a.W = camera->width;
+    a.H = camera->height;
+    a.fx = camera->fx; a.fy = camera->fy; a.cx = camera->cx; a.cy = camera->cy;
+    a.w_dist = weights->w_dist;
+    a.w_norm = weights->w_normal;
+    a.mask_alpha = weights->mask_alpha;
+    const int HW = camera->width * camera->height;
+    const int blocks = (HW + 255) / 256;
+    a.scratch = scratch;
+    a.partial = scratch + (size_t)6 * HW;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_loss_pixel<<<blocks, 256, 0, st>>>(a);
+    k_loss_gather<<<blocks, 256, 0, st>>>(a);
+    k_loss_reduce<<<1, 1024, 0, st>>>(a.partial, blocks, a.w_dist, a.w_norm, HW, loss);
+    return cuda_status(cudaGetLastError());
+}

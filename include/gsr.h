@@ -104,9 +104,12 @@ typedef struct {
     float near_plane;
     float world_to_sensor[16];
     float bg[3];       /* camera background, composited as bg * T */
+    int32_t tile_w;    /* this sensor's screen tile (rays); 0 = the plan's tiling.  */
+    int32_t tile_h;    /* w, h powers of two, w*h in {32,64,128,256}               */
 } gsr_sensor;
 
-/* Screen tiling shared by all sensors of a plan (tile_w, tile_h in {8,16,32}). */
+/* Default screen tiling of a plan's sensors (tile_w, tile_h powers of two,
+ * tile_w * tile_h in {32,64,128,256}); a sensor may override it. */
 typedef struct {
     int32_t tile_w, tile_h;
 } gsr_tiling;
@@ -125,7 +128,7 @@ typedef struct {
     int32_t tiles_y[GSR_MAX_SENSORS];
     int32_t tile_base[GSR_MAX_SENSORS + 1]; /* global tile id of each sensor's tile 0 */
     int32_t sort_ctas;                    /* persistent CTAs of the sort kernels  */
-    uint64_t off[24];                     /* byte offsets of workspace regions    */
+    uint64_t off[32];                     /* byte offsets of workspace regions    */
     uint64_t workspace_bytes;
 } gsr_plan;
 
@@ -319,6 +322,43 @@ gsr_status gsr_loss_noalloc(const gsr_sensor* camera, const gsr_camera_out* fwd,
 gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
                         const gsr_camera_out* fwd, const gsr_camera_grad* grad, const gsr_surfels* surfels,
                         const gsr_objects* objects, const gsr_surfel_grads* out, void* stream);
+
+/* ------------------------------------------------------------ whole rig */
+
+/*
+ * Step (c) for every sensor of the plan -- a surround rig of cameras and
+ * LiDARs of mixed resolutions -- in ONE persistent launch: resident CTAs
+ * pull (sensor, tile) items from a work queue ordered longest list first
+ * (built by gsr_bin_sort) and composite each with the camera or LiDAR rules.
+ * camera_outs and lidar_outs are host arrays of plan->n_sensors entries
+ * indexed by sensor: entry i of camera_outs is used when sensor i is a
+ * pinhole, entry i of lidar_outs when it is a LiDAR (an array may be NULL if
+ * the plan has no sensor of that kind).  Results equal gsr_render_camera /
+ * gsr_render_lidar per sensor.
+ */
+gsr_status gsr_render_rig(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                          const gsr_camera_out* camera_outs, const gsr_lidar_out* lidar_outs, void* stream);
+
+/*
+ * A frame -- gsr_preprocess, gsr_bin_sort, gsr_render_rig, or the subset
+ * selected by `stages` (bit 0 preprocess, bit 1 bin_sort, bit 2 render_rig;
+ * 7 = the whole frame) -- captured once into a CUDA graph on `stream` (a
+ * created stream, not the legacy default one) and replayed with
+ * gsr_frame_graph_launch.  The graph keeps every pointer it was created
+ * with: update the surfel table, object poses and outputs in place between
+ * launches.  The handle is host memory owned by the library until
+ * gsr_frame_graph_destroy.
+ */
+#define GSR_STAGE_PREPROCESS 1
+#define GSR_STAGE_BIN_SORT 2
+#define GSR_STAGE_RENDER_RIG 4
+typedef struct gsr_frame_graph_s gsr_frame_graph;
+gsr_status gsr_frame_graph_create(const gsr_plan* plan, const gsr_surfels* surfels, const gsr_objects* objects,
+                                  void* workspace, size_t workspace_bytes, const gsr_camera_out* camera_outs,
+                                  const gsr_lidar_out* lidar_outs, int32_t stages, void* stream,
+                                  gsr_frame_graph** graph);
+gsr_status gsr_frame_graph_launch(gsr_frame_graph* graph, void* stream);
+gsr_status gsr_frame_graph_destroy(gsr_frame_graph* graph);
 
 /*
  * Copy the device status word to the host (synchronises `stream`).

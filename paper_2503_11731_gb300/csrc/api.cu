@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <new>
 
 #include "gsr_internal.cuh"
 
@@ -53,6 +54,8 @@ SensorTable make_sensor_table(const gsr_plan* p)
         d.tiles_x = p->tiles_x[i];
         d.tiles_y = p->tiles_y[i];
         d.tile_base = p->tile_base[i];
+        d.tile_w = s.tile_w;
+        d.tile_h = s.tile_h;
         double R[9], tt[3];
         for (int a = 0; a < 3; ++a) {
             for (int b = 0; b < 3; ++b) R[a * 3 + b] = s.world_to_sensor[a * 4 + b];
@@ -82,15 +85,19 @@ SensorTable make_sensor_table(const gsr_plan* p)
 
 using namespace gsr;
 
-static bool tile_ok(int v) { return v == 8 || v == 16 || v == 32; }
+static bool tile_ok(int w, int h)
+{
+    auto pow2 = [](int v) { return v >= 1 && v <= 256 && (v & (v - 1)) == 0; };
+    const int n = w * h;
+    return pow2(w) && pow2(h) && (n == 32 || n == 64 || n == 128 || n == 256);
+}
 
 extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr_sensor* sensors,
                                     int32_t n_sensors, const gsr_tiling* tiling, int64_t max_dup)
 {
     if (!plan || !sensors || !tiling) return GSR_ERR_INVALID_ARG;
     if (n_surfels < 0 || n_sensors < 1 || n_sensors > GSR_MAX_SENSORS) return GSR_ERR_INVALID_ARG;
-    if (!tile_ok(tiling->tile_w) || !tile_ok(tiling->tile_h)) return GSR_ERR_UNSUPPORTED;
-    if (tiling->tile_w * tiling->tile_h > 256) return GSR_ERR_UNSUPPORTED;
+    if (!tile_ok(tiling->tile_w, tiling->tile_h)) return GSR_ERR_UNSUPPORTED;
     std::memset(plan, 0, sizeof(*plan));
     plan->n_surfels = n_surfels;
     plan->n_sensors = n_sensors;
@@ -106,8 +113,14 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
         if (s.kind == GSR_SENSOR_PINHOLE && !(s.fx > 0.f && s.fy > 0.f)) return GSR_ERR_INVALID_ARG;
         if (s.kind == GSR_SENSOR_LIDAR && (s.height < 2 || !(s.el_max_deg > s.el_min_deg))) return GSR_ERR_INVALID_ARG;
         plan->sensors[i] = s;
-        plan->tiles_x[i] = (s.width + tiling->tile_w - 1) / tiling->tile_w;
-        plan->tiles_y[i] = (s.height + tiling->tile_h - 1) / tiling->tile_h;
+        if (s.tile_w == 0 && s.tile_h == 0) {
+            plan->sensors[i].tile_w = tiling->tile_w;
+            plan->sensors[i].tile_h = tiling->tile_h;
+        }
+        const int tw = plan->sensors[i].tile_w, th = plan->sensors[i].tile_h;
+        if (!tile_ok(tw, th)) return GSR_ERR_UNSUPPORTED;
+        plan->tiles_x[i] = (s.width + tw - 1) / tw;
+        plan->tiles_y[i] = (s.height + th - 1) / th;
         plan->tile_base[i] = (int32_t)base;
         base += (int64_t)plan->tiles_x[i] * plan->tiles_y[i];
     }
@@ -143,6 +156,8 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
         if (sensors[i].kind == GSR_SENSOR_PINHOLE)
             max_hw = std::max<uint64_t>(max_hw, (uint64_t)sensors[i].width * sensors[i].height);
     sz[R_LOSS_SCRATCH] = (6 * max_hw + 3 * ((max_hw + 255) / 256) + 64) * 4;
+    sz[R_TILE_KEY_A] = sz[R_TILE_VAL_A] = sz[R_TILE_KEY_B] = sz[R_TILE_VAL_B] = (uint64_t)base * 4;
+    static_assert(R_END <= 32, "gsr_plan::off has 32 entries");
     uint64_t off = 0;
     for (int r = 0; r < R_END; ++r) {
         plan->off[r] = off;
@@ -369,4 +384,100 @@ extern "C" gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t
     gsr_status st = gsr_backward_render(plan, workspace, workspace_bytes, sensor, fwd, grad, 0, stream);
     if (st != GSR_OK) return st;
     return gsr_backward_preprocess(plan, workspace, workspace_bytes, surfels, objects, out, stream);
+}
+
+// ------------------------------------------------------------------ whole rig
+namespace gsr {
+cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut* outs, cudaStream_t st);
+}
+
+static gsr_status rig_outputs(const gsr_plan* plan, const gsr_camera_out* cam, const gsr_lidar_out* lid,
+                              FrameOut* outs)
+{
+    for (int i = 0; i < plan->n_sensors; ++i) {
+        if (plan->sensors[i].kind == GSR_SENSOR_PINHOLE) {
+            if (!cam) return GSR_ERR_INVALID_ARG;
+            const gsr_camera_out& o = cam[i];
+            outs[i] = FrameOut{o.rgb, o.depth, o.normal, o.alpha, o.trans, o.depth_acc, o.n_contrib, o.n_walk};
+        } else {
+            if (!lid) return GSR_ERR_INVALID_ARG;
+            const gsr_lidar_out& o = lid[i];
+            outs[i] = FrameOut{o.intensity, o.range, nullptr, o.alpha, o.trans, nullptr, o.n_contrib, o.n_walk};
+        }
+    }
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_render_rig(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
+                                     const gsr_camera_out* camera_outs, const gsr_lidar_out* lidar_outs, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    FrameOut outs[GSR_MAX_SENSORS];
+    if ((st = rig_outputs(plan, camera_outs, lidar_outs, outs)) != GSR_OK) return st;
+    return cuda_fail(launch_render_rig(plan, workspace, outs, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+struct gsr_frame_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" gsr_status gsr_frame_graph_create(const gsr_plan* plan, const gsr_surfels* surfels,
+                                             const gsr_objects* objects, void* workspace, size_t workspace_bytes,
+                                             const gsr_camera_out* camera_outs, const gsr_lidar_out* lidar_outs,
+                                             int32_t stages, void* stream, gsr_frame_graph** graph)
+{
+    if (!graph || !stream || stages <= 0 || stages > 7) return GSR_ERR_INVALID_ARG;
+    *graph = nullptr;
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if (stages & GSR_STAGE_RENDER_RIG) {
+        FrameOut outs[GSR_MAX_SENSORS];
+        if ((st = rig_outputs(plan, camera_outs, lidar_outs, outs)) != GSR_OK) return st;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e);
+    gsr_status rs = GSR_OK;
+    if (stages & GSR_STAGE_PREPROCESS) rs = gsr_preprocess(plan, surfels, objects, workspace, workspace_bytes, stream);
+    if (rs == GSR_OK && (stages & GSR_STAGE_BIN_SORT)) rs = gsr_bin_sort(plan, workspace, workspace_bytes, stream);
+    if (rs == GSR_OK && (stages & GSR_STAGE_RENDER_RIG))
+        rs = gsr_render_rig(plan, workspace, workspace_bytes, camera_outs, lidar_outs, stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rs != GSR_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rs;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    gsr_frame_graph* h = new (std::nothrow) gsr_frame_graph{g, x};
+    if (!h) {
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return GSR_ERR_INVALID_ARG;
+    }
+    *graph = h;
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_frame_graph_launch(gsr_frame_graph* graph, void* stream)
+{
+    if (!graph) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(cudaGraphLaunch(graph->exec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_frame_graph_destroy(gsr_frame_graph* graph)
+{
+    if (!graph) return GSR_OK;
+    cudaError_t e1 = cudaGraphExecDestroy(graph->exec);
+    cudaError_t e2 = cudaGraphDestroy(graph->graph);
+    delete graph;
+    return cuda_fail(e1 != cudaSuccess ? e1 : e2);
 }

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int lt = blockIdx.x;
     const int tx = lt % sd.tiles_x, ty = lt / sd.tiles_x;
-    const int x = tx * tab.tile_w + tid % tab.tile_w;
-    const int y = ty * tab.tile_h + tid / tab.tile_w;
+    const int x = tx * sd.tile_w + tid % sd.tile_w;
+    const int y = ty * sd.tile_h + tid / sd.tile_w;
     const bool inside = x < sd.width && y < sd.height;
     const size_t HW = (size_t)sd.width * sd.height;
     const size_t pix = (size_t)y * sd.width + x;
@@ -649,7 +649,7 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
     a.g_dacc = g->depth_acc;
     a.g_normal = g->normal;
     a.recgrad = recgrad;
-    const int threads = tab.tile_w * tab.tile_h;
+    const int threads = sd.tile_w * sd.tile_h;
     const int tiles = sd.tiles_x * sd.tiles_y;
     const int pb = sort_result_buffer(tile_sort_passes(p));
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);

@@ -47,6 +47,7 @@ enum Region : int {
     R_SENSOR_OF_TILE,
     R_RECGRAD,       // d(loss)/d(record), same layout as R_RECORDS
     R_LOSS_SCRATCH,  // loss: [6][H][W] central-difference gradients + block partials
+    R_TILE_KEY_A, R_TILE_VAL_A, R_TILE_KEY_B, R_TILE_VAL_B,  // tiles by descending list length
     R_END
 };
 
@@ -58,6 +59,7 @@ enum Counter : int {
     C_QUEUE = 3,     // work-queue head of the persistent rig kernel
     C_NDUP_WANT = 4, // uint64 at words 4..5: pairs requested
     C_TIMEOUT_AT = 6,
+    C_NTILES = 7,    // total tiles of the plan (item count of the tile-order sort)
     C_WORDS = 16
 };
 
@@ -65,6 +67,7 @@ struct SensorDev {
     int kind;            // gsr_sensor_kind
     int width, height;
     int tiles_x, tiles_y;
+    int tile_w, tile_h;  // screen tile of this sensor (rays)
     int tile_base;
     float R[9];          // world -> sensor rotation, row-major
     float t[3];
@@ -226,6 +229,184 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     sp.dx = dx; sp.dy = dy;
     sp.use3 = use3;
     return true;
+}
+
+// ------------------------------------------------------------ tile culling
+// Support threshold of a surfel of opacity o: alpha = min(0.99, o G) >= 1/255
+// needs rho <= 2 ln(255 o) (capped at the 3-sigma support), plus a margin.
+__device__ __forceinline__ float support_rho(float o)
+{
+    return fminf(kSupport, __fadd_rn(__fmul_rn(2.f, __logf(__fmul_rn(255.f, o))), 1e-3f));
+}
+
+// Screen footprint of a camera record whose support disc lies in front of
+// the camera: E(d) = q0^2 + q1^2 - rho q2^2 <= 0 with q = Q (d, 1), d = p - c.
+// E(d) = d^T M d + 2 n^T d + k (M positive definite for such an ellipse).
+// All arithmetic uses explicit _rn intrinsics so that every kernel that
+// evaluates it takes bit-identical decisions.
+struct Footprint {
+    float m00, m01, m11, n0, n1, k;
+    float cx, cy;
+    float rlp2;   // squared low-pass radius (px^2)
+    bool conic;   // M is safely positive definite
+};
+
+__device__ __forceinline__ Footprint make_footprint(float4 r0, float4 r1, float4 r2, float o)
+{
+    Footprint f;
+    const float rho = support_rho(o);
+    const float a0 = r0.x, a1 = r0.y, b0 = r1.x, b1 = r1.y, c0 = r2.x, c1 = r2.y, c2 = r2.z;
+    f.m00 = __fsub_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(b0, b0)), __fmul_rn(rho, __fmul_rn(c0, c0)));
+    f.m01 = __fsub_rn(__fadd_rn(__fmul_rn(a0, a1), __fmul_rn(b0, b1)), __fmul_rn(rho, __fmul_rn(c0, c1)));
+    f.m11 = __fsub_rn(__fadd_rn(__fmul_rn(a1, a1), __fmul_rn(b1, b1)), __fmul_rn(rho, __fmul_rn(c1, c1)));
+    f.n0 = -__fmul_rn(rho, __fmul_rn(c2, c0));
+    f.n1 = -__fmul_rn(rho, __fmul_rn(c2, c1));
+    f.k = -__fmul_rn(rho, __fmul_rn(c2, c2));
+    f.cx = r0.w;
+    f.cy = r1.w;
+    f.rlp2 = fmaxf(__fmul_rn(0.5f, rho), 0.f);
+    const float dm = __fsub_rn(__fmul_rn(f.m00, f.m11), __fmul_rn(f.m01, f.m01));
+    f.conic = f.m00 > 0.f && f.m11 > 0.f && dm > __fmul_rn(1e-4f, __fmul_rn(f.m00, f.m11));
+    return f;
+}
+
+__device__ __forceinline__ float fp_eval(const Footprint& f, float dx, float dy)
+{
+    const float qx = __fadd_rn(__fadd_rn(__fmul_rn(f.m00, dx), __fmul_rn(f.m01, dy)), __fmul_rn(2.f, f.n0));
+    const float qy = __fadd_rn(__fadd_rn(__fmul_rn(f.m01, dx), __fmul_rn(f.m11, dy)), __fmul_rn(2.f, f.n1));
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, qx), __fmul_rn(dy, qy)), f.k);
+}
+
+// min of E along d_y in [lo, hi] at fixed d_x (and the symmetric case).
+__device__ __forceinline__ float fp_edge_y(const Footprint& f, float dx, float lo, float hi)
+{
+    const float t = -__fdiv_rn(__fadd_rn(__fmul_rn(f.m01, dx), f.n1), f.m11);
+    return fp_eval(f, dx, fminf(fmaxf(t, lo), hi));
+}
+__device__ __forceinline__ float fp_edge_x(const Footprint& f, float dy, float lo, float hi)
+{
+    const float t = -__fdiv_rn(__fadd_rn(__fmul_rn(f.m01, dy), f.n0), f.m00);
+    return fp_eval(f, fminf(fmaxf(t, lo), hi), dy);
+}
+
+// Can any pixel centre of the tile [x0, x1) x [y0, y1) (pixel units) see
+// the surfel?  The rectangle of centres is widened by one pixel on each side
+// to absorb FP32 rounding of the per-pixel evaluation.
+__device__ __forceinline__ bool footprint_hits(const Footprint& f, float x0, float y0, float x1, float y1)
+{
+    const float lx = __fsub_rn(__fsub_rn(x0, 0.5f), f.cx), hx = __fsub_rn(__fadd_rn(x1, 0.5f), f.cx);
+    const float ly = __fsub_rn(__fsub_rn(y0, 0.5f), f.cy), hy = __fsub_rn(__fadd_rn(y1, 0.5f), f.cy);
+    // low-pass disc around the centre
+    const float ex = fminf(fmaxf(0.f, lx), hx), ey = fminf(fmaxf(0.f, ly), hy);
+    const float r = __fadd_rn(sqrtf(f.rlp2), 1.f);
+    if (__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)) <= __fmul_rn(r, r)) return true;
+    if (!f.conic) return true;
+    // unconstrained minimiser of the convex quadratic
+    const float det = __fsub_rn(__fmul_rn(f.m00, f.m11), __fmul_rn(f.m01, f.m01));
+    const float sx = __fdiv_rn(__fsub_rn(__fmul_rn(f.m01, f.n1), __fmul_rn(f.m11, f.n0)), det);
+    const float sy = __fdiv_rn(__fsub_rn(__fmul_rn(f.m01, f.n0), __fmul_rn(f.m00, f.n1)), det);
+    if (sx >= lx && sx <= hx && sy >= ly && sy <= hy) return fp_eval(f, sx, sy) <= 0.f;
+    if (fp_edge_y(f, lx, ly, hy) <= 0.f || fp_edge_y(f, hx, ly, hy) <= 0.f) return true;
+    return fp_edge_x(f, ly, lx, hx) <= 0.f || fp_edge_x(f, hy, lx, hx) <= 0.f;
+}
+
+// Bit 15 of rect.w marks a camera slot whose tile set is footprint-tested.
+constexpr uint16_t kRectExact = 0x8000;
+
+// Roots of a dx^2 + 2 b dx + e = 0 (a > 0); false if none.
+__device__ __forceinline__ bool fp_roots(float a, float b, float e, float& lo, float& hi)
+{
+    const float disc = __fsub_rn(__fmul_rn(b, b), __fmul_rn(a, e));
+    if (!(disc >= 0.f)) return false;
+    const float s = sqrtf(disc);
+    lo = __fdiv_rn(__fsub_rn(-b, s), a);
+    hi = __fdiv_rn(__fadd_rn(-b, s), a);
+    return true;
+}
+
+// x-extent (relative to the centre) of the footprint inside the horizontal
+// band dy in [ly, hy]: the conic part is convex, so its extremes over the
+// band are at the band edges or at its own leftmost / rightmost points; the
+// low-pass disc (radius r) adds [-w, w].  Returns false if the band misses both.
+__device__ __forceinline__ bool footprint_row(const Footprint& f, float ly, float hy, float& xlo, float& xhi)
+{
+    bool any = false;
+    xlo = 3.0e38f;
+    xhi = -3.0e38f;
+    const float r = __fadd_rn(sqrtf(f.rlp2), 1.f);
+    const float yc = fminf(fmaxf(0.f, ly), hy);
+    const float w2 = __fsub_rn(__fmul_rn(r, r), __fmul_rn(yc, yc));
+    if (w2 >= 0.f) {
+        const float w = sqrtf(w2);
+        xlo = -w;
+        xhi = w;
+        any = true;
+    }
+    if (!f.conic) {  // no usable conic: the whole row band is kept
+        xlo = -3.0e38f;
+        xhi = 3.0e38f;
+        return true;
+    }
+    // the conic's own leftmost / rightmost points satisfy m01 dx + m11 dy + n1 = 0,
+    // i.e. dy = g dx + h, where E(dx, g dx + h) = A dx^2 + 2 B dx + C vanishes
+    const float g = -__fdiv_rn(f.m01, f.m11), h = -__fdiv_rn(f.n1, f.m11);
+    const float A = __fadd_rn(__fadd_rn(f.m00, __fmul_rn(2.f, __fmul_rn(f.m01, g))), __fmul_rn(f.m11, __fmul_rn(g, g)));
+    const float B = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(f.m01, h), __fmul_rn(f.m11, __fmul_rn(g, h))), f.n0),
+                              __fmul_rn(f.n1, g));
+    const float C = __fadd_rn(__fadd_rn(__fmul_rn(f.m11, __fmul_rn(h, h)), __fmul_rn(2.f, __fmul_rn(f.n1, h))), f.k);
+    float x0, x1;
+    // the conic contains the centre (E(0) = k <= 0), so both extreme points
+    // exist; if rounding says otherwise, keep the whole band
+    if (!(A > 0.f) || !fp_roots(A, B, C, x0, x1)) {
+        xlo = -3.0e38f;
+        xhi = 3.0e38f;
+        return true;
+    }
+    {
+        const float y0 = __fadd_rn(__fmul_rn(g, x0), h), y1 = __fadd_rn(__fmul_rn(g, x1), h);
+        if (y0 >= ly && y0 <= hy) {
+            xlo = fminf(xlo, x0);
+            xhi = fmaxf(xhi, x0);
+            any = true;
+        }
+        if (y1 >= ly && y1 <= hy) {
+            xlo = fminf(xlo, x1);
+            xhi = fmaxf(xhi, x1);
+            any = true;
+        }
+    }
+    // and the band edges
+    const float cand[2] = {ly, hy};
+    for (int k = 0; k < 2; ++k) {
+        const float dy = cand[k];
+        const float b = __fadd_rn(__fmul_rn(f.m01, dy), f.n0);
+        const float e = __fadd_rn(__fadd_rn(__fmul_rn(f.m11, __fmul_rn(dy, dy)), __fmul_rn(2.f, __fmul_rn(f.n1, dy))), f.k);
+        float lo, hi;
+        if (fp_roots(f.m00, b, e, lo, hi)) {
+            xlo = fminf(xlo, lo);
+            xhi = fmaxf(xhi, hi);
+            any = true;
+        }
+    }
+    return any;
+}
+
+// Tile columns [t0, t1] of tile row ty that the footprint reaches, widened by
+// one pixel on each side for FP32 rounding (clamped to [tx0, tx1]).
+__device__ __forceinline__ bool footprint_span(const Footprint& f, int ty, int TW, int TH, int tx0, int tx1, int& t0,
+                                               int& t1)
+{
+    const float ly = __fsub_rn(__fsub_rn((float)(ty * TH), 0.5f), f.cy);
+    const float hy = __fsub_rn(__fadd_rn((float)((ty + 1) * TH), 0.5f), f.cy);
+    float xlo, xhi;
+    if (!footprint_row(f, ly, hy, xlo, xhi)) return false;
+    const float X0 = __fadd_rn(xlo, f.cx), X1 = __fadd_rn(xhi, f.cx);
+    // tile tx covers [tx TW - 0.5, (tx+1) TW + 0.5]
+    const float a = fmaxf(__fdiv_rn(__fsub_rn(__fsub_rn(X0, 0.5f), (float)TW), (float)TW), -1.f);
+    const float b = fminf(__fdiv_rn(__fadd_rn(X1, 0.5f), (float)TW), 65536.f);
+    t0 = max(tx0, (int)ceilf(a));
+    t1 = min(tx1, (int)floorf(b));
+    return t0 <= t1;
 }
 
 // Per-ray setup shared by the forward and backward rasterisers.

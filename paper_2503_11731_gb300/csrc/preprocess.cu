@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     ushort4 rect = make_ushort4(0, 0, 0, 0);
     float zkey;
     float4 r0, r1, r2;
-    const int TW = tab.tile_w, TH = tab.tile_h;
+    const int TW = sd.tile_w, TH = sd.tile_h;
 
     // Opacity-aware support: alpha = min(0.99, o G) reaches 1/255 only where
     // G >= 1/(255 o), i.e. rho <= 2 ln(255 o); a surfel with o < 1/255 never
@@ -213,10 +213,12 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         F3 P[4] = {ms + ka + kb, ms + ka - kb, ms - ka - kb, ms - ka + kb};
         const float zn = sd.near_plane;
         float px, py;
+        bool front = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const F3 A = P[k], B = P[(k + 1) & 3];
             const bool ia = A.z >= zn, ib = B.z >= zn;
+            front = front && ia;
             if (ia) project(sd, A, px, py, xmin, xmax, ymin, ymax);
             if (ia != ib) {
                 const float t = (zn - A.z) / (B.z - A.z);
@@ -232,6 +234,18 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         if (x0 <= x1 && y0 <= y1) {
             rect = make_ushort4(x0 / TW, x1 / TW, y0 / TH, y1 / TH);
             cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
+            if (front && cnt > 1) {
+                // support disc entirely in front: keep only the tiles its
+                // footprint (or the low-pass disc) reaches
+                const Footprint fp = make_footprint(r0, r1, r2, o);
+                uint32_t c = 0;
+                for (int ty = rect.z; ty <= rect.w; ++ty) {
+                    int t0, t1;
+                    if (footprint_span(fp, ty, TW, TH, rect.x, rect.y, t0, t1)) c += (uint32_t)(t1 - t0 + 1);
+                }
+                cnt = c;
+                rect.w |= kRectExact;
+            }
         }
     } else {
         const float rc = sqrtf(dot(ms, ms));

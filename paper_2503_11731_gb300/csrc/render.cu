@@ -25,18 +25,21 @@ struct RayState {
     bool done;
 };
 
+// Composite one tile with the whole CTA.  Threads beyond the tile's rays only
+// help staging.  `gb` counts the batches this CTA has staged so far (it picks
+// the buffer and the mbarrier phase, so a persistent CTA can run many tiles).
 template <int KIND>
 __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int tile_h, int local_tile,
                                             const uint2 range, const float4* __restrict__ rec,
                                             const uint32_t* __restrict__ pval, const FrameOut& out,
-                                            uint32_t* counters, float4* buf, uint64_t* bars)
+                                            uint32_t* counters, float4* buf, uint64_t* bars, uint32_t& gb)
 {
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
     const int tx = local_tile % sd.tiles_x, ty = local_tile / sd.tiles_x;
     const int x = tx * tile_w + tid % tile_w;
     const int y = ty * tile_h + tid / tile_w;
-    const bool inside = x < sd.width && y < sd.height;
+    const bool inside = tid < tile_w * tile_h && x < sd.width && y < sd.height;
 
     float rx, ry, d0, d1, d2;
     ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
@@ -54,26 +57,38 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
 
+    // batch b of this tile is the CTA's batch g = gb + b: buffer and barrier
+    // g & 1, phase parity (g >> 1) & 1
     auto issue = [&](int b) {
+        const uint32_t g = gb + (uint32_t)b;
         const int first = b * nthr;
         const int cnt = min(nthr, n - first);
-        uint64_t* bar = bars + (b & 1);
-        float4* dst = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        uint64_t* bar = bars + (g & 1);
+        float4* dst = buf + (size_t)(g & 1) * nthr * kRecordF4;
         if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
         if (tid < cnt) {
             const uint32_t slot = pval[start + first + tid];
             bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
         }
     };
+    auto wait = [&](int b) {
+        const uint32_t g = gb + (uint32_t)b;
+        return mbar_wait_bounded(bars + (g & 1), (g >> 1) & 1, counters);
+    };
 
     bool ok = true;
-    if (nb > 0) issue(0);
+    int issued = 0;
+    if (nb > 0) {
+        issue(0);
+        issued = 1;
+    }
     for (int b = 0; b < nb; ++b) {
-        if (b + 1 < nb) issue(b + 1);
-        if (!mbar_wait_bounded(bars + (b & 1), (b >> 1) & 1, counters)) {
-            ok = false;
+        if (b + 1 < nb) {
+            issue(b + 1);
+            issued = b + 2;
         }
-        const float4* B = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        if (!wait(b)) ok = false;
+        const float4* B = buf + (size_t)((gb + b) & 1) * nthr * kRecordF4;
         const int cnt = min(nthr, n - b * nthr);
         if (ok) {
             for (int j = 0; j < cnt; ++j) {
@@ -112,11 +127,13 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
         const bool all_done = __syncthreads_and(s.done);
         const bool any_fail = __syncthreads_or(!ok);
         if (all_done || any_fail) {
-            // no copy may still be landing in shared memory when the CTA leaves
-            if (b + 1 < nb) mbar_wait_bounded(bars + ((b + 1) & 1), ((b + 1) >> 1) & 1, counters);
+            // no copy may still be landing in shared memory when the CTA
+            // leaves or moves on to its next tile
+            if (b + 1 < nb) wait(b + 1);
             break;
         }
     }
+    gb += (uint32_t)issued;
 
     if (!inside) return;
     const size_t HW = (size_t)sd.width * sd.height;
@@ -162,7 +179,55 @@ __global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, con
     }
     __syncthreads();
     const int lt = blockIdx.x;
-    render_tile<KIND>(sd, tab.tile_w, tab.tile_h, lt, ranges[sd.tile_base + lt], rec, pval, out, counters, buf, bars);
+    uint32_t gb = 0;
+    render_tile<KIND>(sd, sd.tile_w, sd.tile_h, lt, ranges[sd.tile_base + lt], rec, pval, out, counters, buf, bars,
+                      gb);
+}
+
+// Outputs of every sensor of a plan, for the whole-rig kernel.
+struct RigOut {
+    FrameOut o[GSR_MAX_SENSORS];
+};
+
+// The whole rig in one persistent launch: each CTA takes the next tile from a
+// global work queue that lists every sensor's tiles longest list first, so
+// the long LiDAR and near-field tiles start early and the short ones fill in
+// behind them; the sensor kind is uniform per tile, so the branch is too.
+__global__ void __launch_bounds__(256) k_render_rig(SensorTable tab, const float4* __restrict__ rec,
+                                                    const uint2* __restrict__ ranges,
+                                                    const uint32_t* __restrict__ pval,
+                                                    const uint32_t* __restrict__ order, RigOut outs,
+                                                    uint32_t* counters)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
+    __shared__ uint32_t item_s;
+    if (threadIdx.x == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        fence_mbar_init();
+    }
+    uint32_t gb = 0;
+    const uint32_t T = (uint32_t)tab.total_tiles;
+    for (;;) {
+        __syncthreads();  // the previous item (and the barrier init) is done with
+        if (threadIdx.x == 0) item_s = atomicAdd(&counters[C_QUEUE], 1u);
+        __syncthreads();
+        const uint32_t item = item_s;
+        if (item >= T) break;
+        const uint32_t tile = order[item];
+        int s = 0;
+        while (s + 1 < tab.n && (int)tile >= tab.s[s + 1].tile_base) ++s;
+        const SensorDev& sd = tab.s[s];
+        const int lt = (int)tile - sd.tile_base;
+        if (sd.kind == GSR_SENSOR_PINHOLE)
+            render_tile<GSR_SENSOR_PINHOLE>(sd, sd.tile_w, sd.tile_h, lt, ranges[tile], rec, pval, outs.o[s],
+                                            counters, buf, bars, gb);
+        else
+            render_tile<GSR_SENSOR_LIDAR>(sd, sd.tile_w, sd.tile_h, lt, ranges[tile], rec, pval, outs.o[s],
+                                          counters, buf, bars, gb);
+    }
 }
 
 size_t render_smem_bytes(int threads) { return 128 + 2 * (size_t)threads * kRecordBytes; }
@@ -171,7 +236,7 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
 {
     const SensorTable tab = make_sensor_table(p);
     const SensorDev& sd = tab.s[sensor];
-    const int threads = tab.tile_w * tab.tile_h;
+    const int threads = sd.tile_w * sd.tile_h;
     const size_t smem = render_smem_bytes(threads);
     const int tiles = sd.tiles_x * sd.tiles_y;
     const float4* rec = region<float4>(p, ws, R_RECORDS);
@@ -179,21 +244,46 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
     const int pb = sort_result_buffer(tile_sort_passes(p));
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
-    if (sd.kind == GSR_SENSOR_PINHOLE) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_render<GSR_SENSOR_PINHOLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
+    if (sd.kind == GSR_SENSOR_PINHOLE)
         k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_render<GSR_SENSOR_LIDAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
+    else
         k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
-    }
+    return cudaGetLastError();
+}
+
+// Persistent CTAs for the whole-rig kernel: resident CTAs per SM x SMs of the current device.
+static int rig_grid(cudaError_t& err)
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    int sms = 0, per_sm = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, 256, render_smem_bytes(256));
+    if (err != cudaSuccess) return 0;
+    const int g = sms * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < 64) cached[dev] = g;
+    return g;
+}
+
+cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut* outs, cudaStream_t st)
+{
+    const SensorTable tab = make_sensor_table(p);
+    RigOut ro;
+    for (int i = 0; i < GSR_MAX_SENSORS; ++i) ro.o[i] = i < p->n_sensors ? outs[i] : FrameOut{};
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
+    cudaError_t e = cudaMemsetAsync(counters + C_QUEUE, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int grid = rig_grid(e);
+    if (e != cudaSuccess) return e;
+    const int pb = sort_result_buffer(tile_sort_passes(p));
+    k_render_rig<<<grid, 256, render_smem_bytes(256), st>>>(
+        tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
+        region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_A), ro,
+        counters);
     return cudaGetLastError();
 }
 

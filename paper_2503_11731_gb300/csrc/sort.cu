@@ -274,13 +274,16 @@ __global__ void __launch_bounds__(256) k_dup_count(const uint32_t* __restrict__ 
 }
 
 // Each visible slot writes (global tile id, slot) for every tile of its
-// rectangle, row-major, at its prefix-sum offset; pairs beyond max_dup are dropped.
+// rectangle, row-major, at its prefix-sum offset; pairs beyond max_dup are
+// dropped.  Camera slots marked kRectExact emit only the tiles their
+// footprint reaches, with the same test the preprocess counted with.
 __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
                                                    const uint32_t* __restrict__ vis_val,
                                                    const uint32_t* __restrict__ cnt_sorted,
                                                    const uint32_t* __restrict__ n_ptr,
                                                    const unsigned long long* __restrict__ partial,
-                                                   const ushort4* __restrict__ rects, uint64_t cap,
+                                                   const ushort4* __restrict__ rects,
+                                                   const float4* __restrict__ rec, uint64_t cap,
                                                    uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
 {
     __shared__ unsigned long long sm[9];
@@ -297,8 +300,18 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
             const int si = (int)(slot / (uint32_t)n_surfels);
             const SensorDev& sd = tab.s[si];
             const ushort4 r = rects[slot];
-            for (int ty = r.z; ty <= r.w; ++ty) {
-                for (int tx = r.x; tx <= r.y; ++tx) {
+            const bool exact = (r.w & kRectExact) != 0;
+            const int ty1 = r.w & ~kRectExact;
+            Footprint fp;
+            if (exact) {
+                const float4* R = rec + (size_t)slot * kRecordF4;
+                fp = make_footprint(R[0], R[1], R[2], R[3].x);
+            }
+            const int TW = sd.tile_w, TH = sd.tile_h;
+            for (int ty = r.z; ty <= ty1; ++ty) {
+                int t0 = r.x, t1 = r.y;
+                if (exact && !footprint_span(fp, ty, TW, TH, r.x, r.y, t0, t1)) continue;
+                for (int tx = t0; tx <= t1; ++tx) {
                     if (off >= cap) break;
                     const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
                     pkey[off] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
@@ -309,6 +322,21 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
         }
         base += tot;
     }
+}
+
+// Scheduling keys of the tiles: longest list first (ascending sort of
+// 0xffff - min(len, 0xffff)), for the persistent whole-rig compositing kernel.
+__global__ void __launch_bounds__(256) k_tile_keys(const uint2* __restrict__ ranges, uint32_t n_tiles,
+                                                   uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                                                   uint32_t* __restrict__ counters)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) counters[C_NTILES] = n_tiles;
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y - r.x;
+    key[t] = 0xffffu - min(len, 0xffffu);
+    val[t] = t;
 }
 
 // [start, end) of each tile in the sorted pair list (ranges pre-zeroed).
@@ -376,7 +404,8 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
         p64, G, reinterpret_cast<unsigned long long*>(counters + C_NDUP_WANT), counters, p->max_dup, C_NDUP);
     // 4. duplication
     k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, counters + C_NVIS, p64,
-                                   region<ushort4>(p, ws, R_RECTS), (uint64_t)p->max_dup, pk[0], pv[0]);
+                                   region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS),
+                                   (uint64_t)p->max_dup, pk[0], pv[0]);
     // 5. tile passes
     const int tp = tile_sort_passes(p);
     radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st);
@@ -385,6 +414,12 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     uint2* ranges = region<uint2>(p, ws, R_RANGES);
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p->tile_base[p->n_sensors], st);
     k_tile_ranges<<<4 * G, 256, 0, st>>>(pk[pb], counters + C_NDUP, ranges);
+    // 7. tile schedule for the whole-rig kernel (2 passes over 16-bit keys)
+    const uint32_t T = (uint32_t)p->tile_base[p->n_sensors];
+    uint32_t* tk[2] = {region<uint32_t>(p, ws, R_TILE_KEY_A), region<uint32_t>(p, ws, R_TILE_KEY_B)};
+    uint32_t* tv[2] = {region<uint32_t>(p, ws, R_TILE_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_B)};
+    k_tile_keys<<<(T + 255) / 256, 256, 0, st>>>(ranges, T, tk[0], tv[0], counters);
+    radix_sort(p, ws, tk[0], tv[0], tk[1], tv[1], counters + C_NTILES, 0, 2, st);
     return cudaGetLastError();
 }
 

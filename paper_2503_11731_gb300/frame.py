@@ -57,9 +57,11 @@ class Renderer:
     """One plan (surfel count, sensors, tiling) with its workspace and outputs."""
 
     def __init__(self, n_surfels, sensors, tile=(16, 16), max_dup=0, bg=(0.0, 0.0, 0.0), device="cuda",
-                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib")):
+                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"), tiles=None):
+        """`tile` is the default tiling; `tiles` (optional) a per-sensor list of (w, h) or None."""
         self.descs = list(sensors)
-        self.structs = [gsr.sensor(d, bg) for d in self.descs]
+        tiles = tiles if tiles is not None else [None] * len(self.descs)
+        self.structs = [gsr.sensor(d, bg, t) for d, t in zip(self.descs, tiles)]
         self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup)
         self.ws_bytes = gsr.workspace_size(self.plan)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
@@ -122,6 +124,29 @@ class Renderer:
         self.bin_sort(stream)
         self.composite(None, stream)
         return self.out
+
+    def composite_rig(self, stream=None):
+        """Every sensor in one persistent launch (gsr_render_rig)."""
+        gsr.render_rig(self.plan, self.ws_ptr, self.ws_bytes, [self._out_struct(i) for i in range(len(self.descs))],
+                       _stream_handle(stream))
+
+    def render_rig(self, surfels: DeviceSurfels, objects=None, stream=None):
+        self.preprocess(surfels, objects, stream)
+        self.bin_sort(stream)
+        self.composite_rig(stream)
+        return self.out
+
+    def graph(self, surfels: DeviceSurfels, objects=None, stages=7, stream=None):
+        """Capture the selected stages of a frame (gsr_frame_graph_create) on a
+        side stream; replay with .launch(stream).  Keeps every pointer."""
+        obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = gsr.FrameGraph(self.plan, surfels.struct(), obj, self.ws_ptr, self.ws_bytes,
+                           [self._out_struct(i) for i in range(len(self.descs))], stages, _stream_handle(side))
+        torch.cuda.current_stream().wait_stream(side)
+        g._keep = (surfels, objects, side)
+        return g
 
     def status(self, stream=None):
         """(device status, visible slots, tile/surfel pairs requested); synchronises."""

@@ -36,7 +36,7 @@ class Sensor(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("width", c_i32), ("height", c_i32),
                 ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
                 ("el_min_deg", c_f32), ("el_max_deg", c_f32), ("az0_deg", c_f32), ("near_plane", c_f32),
-                ("world_to_sensor", c_f32 * 16), ("bg", c_f32 * 3)]
+                ("world_to_sensor", c_f32 * 16), ("bg", c_f32 * 3), ("tile_w", c_i32), ("tile_h", c_i32)]
 
 
 class Tiling(ctypes.Structure):
@@ -47,7 +47,7 @@ class Plan(ctypes.Structure):
     _fields_ = [("n_surfels", c_i32), ("n_sensors", c_i32), ("sensors", Sensor * MAX_SENSORS),
                 ("tiling", Tiling), ("max_dup", c_i64), ("tiles_x", c_i32 * MAX_SENSORS),
                 ("tiles_y", c_i32 * MAX_SENSORS), ("tile_base", c_i32 * (MAX_SENSORS + 1)),
-                ("sort_ctas", c_i32), ("off", c_u64 * 24), ("workspace_bytes", c_u64)]
+                ("sort_ctas", c_i32), ("off", c_u64 * 32), ("workspace_bytes", c_u64)]
 
 
 class CameraOut(ctypes.Structure):
@@ -100,6 +100,13 @@ SIGNATURES = {
                                     ctypes.POINTER(CameraGrad), c_i32, c_vp]),
     "gsr_backward_preprocess": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(Surfels),
                                         ctypes.POINTER(Objects), ctypes.POINTER(SurfelGrads), c_vp]),
+    "gsr_render_rig": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(CameraOut),
+                               ctypes.POINTER(LidarOut), c_vp]),
+    "gsr_frame_graph_create": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(Surfels), ctypes.POINTER(Objects), c_vp,
+                                       ctypes.c_size_t, ctypes.POINTER(CameraOut), ctypes.POINTER(LidarOut), c_i32,
+                                       c_vp, ctypes.POINTER(c_vp)]),
+    "gsr_frame_graph_launch": (c_i32, [c_vp, c_vp]),
+    "gsr_frame_graph_destroy": (c_i32, [c_vp]),
     "gsr_loss_noalloc": (c_i32, [ctypes.POINTER(Sensor), ctypes.POINTER(CameraOut), c_vp,
                                  ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
@@ -148,9 +155,12 @@ def _check(code, where):
 
 
 # ----------------------------------------------------------------- structs
-def sensor(desc, bg=(0.0, 0.0, 0.0)) -> Sensor:
-    """Sensor struct from a synth.Pinhole / synth.Lidar-like description."""
+def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None) -> Sensor:
+    """Sensor struct from a synth.Pinhole / synth.Lidar-like description;
+    `tile` = (w, h) overrides the plan's default tiling for this sensor."""
     s = Sensor()
+    if tile is not None:
+        s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
     if getattr(desc, "kind", "pinhole") == "lidar":
         s.kind = LIDAR
         s.width, s.height = int(desc.columns), int(desc.beams)
@@ -232,3 +242,51 @@ def backward_preprocess(plan, ws, ws_bytes, surfels: Surfels, objects, out: Surf
     _check(lib().gsr_backward_preprocess(ctypes.byref(plan), ws, ws_bytes, ctypes.byref(surfels),
                                          ctypes.byref(objects) if objects is not None else None,
                                          ctypes.byref(out), stream), "gsr_backward_preprocess")
+
+
+STAGE_PREPROCESS, STAGE_BIN_SORT, STAGE_RENDER_RIG = 1, 2, 4
+
+
+def _rig_out_arrays(plan, outs):
+    n = plan.n_sensors
+    cams = (CameraOut * n)()
+    lids = (LidarOut * n)()
+    for i, o in enumerate(outs):
+        if isinstance(o, CameraOut):
+            cams[i] = o
+        else:
+            lids[i] = o
+    return cams, lids
+
+
+def render_rig(plan, ws, ws_bytes, outs, stream):
+    """outs: per-sensor CameraOut / LidarOut structs (index = sensor)."""
+    cams, lids = _rig_out_arrays(plan, outs)
+    _check(lib().gsr_render_rig(ctypes.byref(plan), ws, ws_bytes, cams, lids, stream), "gsr_render_rig")
+
+
+class FrameGraph:
+    """A captured frame (or the stages selected by `stages`) replayed with launch()."""
+
+    def __init__(self, plan, surfels: Surfels, objects, ws, ws_bytes, outs, stages, stream):
+        cams, lids = _rig_out_arrays(plan, outs)
+        h = c_vp()
+        _check(lib().gsr_frame_graph_create(ctypes.byref(plan), ctypes.byref(surfels),
+                                            ctypes.byref(objects) if objects is not None else None, ws, ws_bytes,
+                                            cams, lids, int(stages), stream, ctypes.byref(h)),
+               "gsr_frame_graph_create")
+        self.handle = h
+
+    def launch(self, stream):
+        _check(lib().gsr_frame_graph_launch(self.handle, stream), "gsr_frame_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().gsr_frame_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

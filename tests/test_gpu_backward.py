@@ -139,12 +139,13 @@ def test_gradient_finite_differences_on_gpu(gpu_lib):
         return float(camera_loss(r, 0, t)[0][0])
     rng = np.random.default_rng(9)
     # perturb a few surfels at a time: a shift of every surfel crosses many
-    # support / alpha-skip boundaries, which FP32 differences cannot resolve;
-    # a rotation moves the support boundary of a whole surfel at once, so
-    # quaternions get a smaller step and a looser bound; the FP64 oracle
-    # comparison above is the tight check.
-    steps = {"pos": 1e-3, "log_scale": 1e-3, "quat": 2e-4, "opacity": 1e-2, "sh": 1e-2}
-    tols = {"quat": 0.1}
+    # support / alpha-skip boundaries, which FP32 differences cannot resolve.
+    # Rotations are left out: turning a surfel moves its whole hard support
+    # boundary, so the loss jumps along that direction and the difference
+    # quotient grows as the step shrinks instead of converging; the rotation
+    # gradient is checked against the FP64 oracle gradient above.
+    steps = {"pos": 1e-3, "log_scale": 1e-3, "opacity": 1e-2, "sh": 1e-2}
+    tols = {}
     for name, h in steps.items():
         base = getattr(s, name)
         v = rng.normal(size=base.shape).astype(np.float32)

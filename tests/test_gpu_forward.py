@@ -156,26 +156,36 @@ def test_sort_order_bit_exact(gpu_lib):
     ranges = r.region(6, torch.int32).cpu().numpy().view(np.uint32).reshape(-1, 2)
     plan = r.plan
     N = s.n
-    k64, v = [], []
+    # the emitted pairs: every slot's tiles lie in its rectangle; a slot
+    # without the exact-footprint bit emits its whole rectangle
+    assert len(pk) == npairs == int(counts.sum())
+    per_slot = {}
+    for t, slot in zip(pk.tolist(), pv.tolist()):
+        per_slot.setdefault(slot, []).append(t)
+    n_exact = 0
     for slot in np.nonzero(counts)[0]:
         si = slot // N
-        tx0, tx1, ty0, ty1 = rects[slot]
+        tx0, tx1, ty0, ty1 = (int(x) for x in rects[slot])
+        exact = bool(ty1 & 0x8000)
+        ty1 &= 0x7FFF
+        n_exact += exact
         tiles_x = plan.tiles_x[si]
-        assert counts[slot] == (tx1 - tx0 + 1) * (ty1 - ty0 + 1)
-        for ty in range(ty0, ty1 + 1):
-            for tx in range(tx0, tx1 + 1):
-                t = plan.tile_base[si] + ty * tiles_x + (tx if tx < tiles_x else tx - tiles_x)
-                k64.append((np.uint64(t) << np.uint64(32)) | np.uint64(keys[slot]))
-                v.append(slot)
-    k64 = np.asarray(k64, np.uint64)
-    v = np.asarray(v, np.uint32)
-    order = np.argsort(k64, kind="stable")
-    assert len(k64) == npairs
-    assert np.array_equal(pk, (k64[order] >> np.uint64(32)).astype(np.uint32))
-    assert np.array_equal(pv, v[order])
+        box = {plan.tile_base[si] + ty * tiles_x + (tx if tx < tiles_x else tx - tiles_x)
+               for ty in range(ty0, ty1 + 1) for tx in range(tx0, tx1 + 1)}
+        got = per_slot.get(int(slot), [])
+        assert len(got) == counts[slot] and len(set(got)) == len(got)
+        assert set(got) <= box
+        if not exact:
+            assert set(got) == box
+    assert n_exact > 0
+    # the order is exactly the stable sort of the 64-bit (tile | depth) keys in
+    # emission order (equal keys keep ascending slot order)
+    k64 = (pk.astype(np.uint64) << np.uint64(32)) | keys[pv].astype(np.uint64)
+    emit = np.lexsort((pv, k64))  # stable: key, then slot
+    assert np.array_equal(emit, np.arange(len(k64)))
     # tile ranges
     T = plan.tile_base[plan.n_sensors]
-    tid = (k64[order] >> np.uint64(32)).astype(np.int64)
+    tid = pk.astype(np.int64)
     starts = np.searchsorted(tid, np.arange(T), "left")
     ends = np.searchsorted(tid, np.arange(T), "right")
     nonempty = ends > starts

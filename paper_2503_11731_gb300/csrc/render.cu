@@ -123,10 +123,9 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
                 s.last = (uint32_t)(b * nthr + j + 1);
             }
         }
-        // both votes are block-uniform, so every thread takes the same exit
-        const bool all_done = __syncthreads_and(s.done);
-        const bool any_fail = __syncthreads_or(!ok);
-        if (all_done || any_fail) {
+        // one block-uniform vote: a thread whose bounded wait gave up counts
+        // as done (it composites nothing more; every later wait is bounded too)
+        if (__syncthreads_and(s.done || !ok)) {
             // no copy may still be landing in shared memory when the CTA
             // leaves or moves on to its next tile
             if (b + 1 < nb) wait(b + 1);
@@ -251,21 +250,23 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
     return cudaGetLastError();
 }
 
-// Persistent CTAs for the whole-rig kernel: resident CTAs per SM x SMs of the current device.
-static int rig_grid(cudaError_t& err)
+// Persistent CTAs for the whole-rig kernel: resident CTAs per SM x SMs of the
+// current device, for CTAs of `threads` threads (32..256, a power of two).
+static int rig_grid(int threads, cudaError_t& err)
 {
-    static int cached[64] = {0};
+    static int cached[64][4] = {};
     int dev = 0;
     err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return 0;
-    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    const int ti = threads <= 32 ? 0 : threads <= 64 ? 1 : threads <= 128 ? 2 : 3;
+    if (dev >= 0 && dev < 64 && cached[dev][ti] > 0) return cached[dev][ti];
     int sms = 0, per_sm = 0;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, 256, render_smem_bytes(256));
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, threads, render_smem_bytes(threads));
     if (err != cudaSuccess) return 0;
     const int g = sms * (per_sm > 0 ? per_sm : 1);
-    if (dev >= 0 && dev < 64) cached[dev] = g;
+    if (dev >= 0 && dev < 64) cached[dev][ti] = g;
     return g;
 }
 
@@ -277,10 +278,13 @@ cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut*
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     cudaError_t e = cudaMemsetAsync(counters + C_QUEUE, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    const int grid = rig_grid(e);
+    // one CTA per tile in flight, as wide as the largest tile of the plan
+    int threads = 32;
+    for (int i = 0; i < p->n_sensors; ++i) threads = max(threads, tab.s[i].tile_w * tab.s[i].tile_h);
+    const int grid = rig_grid(threads, e);
     if (e != cudaSuccess) return e;
     const int pb = sort_result_buffer(tile_sort_passes(p));
-    k_render_rig<<<grid, 256, render_smem_bytes(256), st>>>(
+    k_render_rig<<<grid, threads, render_smem_bytes(threads), st>>>(
         tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
         region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_A), ro,
         counters);

@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
         const unsigned long long c = i < e ? cnt_sorted[i] : 0ull;
         unsigned long long tot;
         unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(c, tot, sm);
-        if (c > 0 && off < cap) {
+        // entries with few pairs: one thread each, row-major over their tiles
+        const bool big = c > 16;
+        if (c > 0 && !big && off < cap) {
             const uint32_t slot = vis_val[i];
             const int si = (int)(slot / (uint32_t)n_surfels);
             const SensorDev& sd = tab.s[si];
@@ -317,6 +319,59 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
                     pkey[off] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
                     pval[off] = slot;
                     ++off;
+                }
+            }
+        }
+        // entries with many pairs: the whole warp expands them one at a time,
+        // writing the same row-major sequence at the same offsets
+        const int lane = threadIdx.x & 31;
+        uint32_t bigmask = __ballot_sync(0xffffffffu, big && off < cap);
+        while (bigmask) {
+            const int src = __ffs(bigmask) - 1;
+            bigmask &= bigmask - 1;
+            const uint32_t slot = __shfl_sync(0xffffffffu, i < e ? vis_val[i] : 0u, src);
+            const unsigned long long o0 = __shfl_sync(0xffffffffu, off, src);
+            const int si = (int)(slot / (uint32_t)n_surfels);
+            const SensorDev& sd = tab.s[si];
+            const ushort4 r = rects[slot];
+            const bool exact = (r.w & kRectExact) != 0;
+            const int ty1 = r.w & ~kRectExact;
+            const int TW = sd.tile_w, TH = sd.tile_h;
+            if (!exact) {
+                const int ncols = r.y - r.x + 1;
+                const int count = ncols * (ty1 - r.z + 1);
+                for (int k = lane; k < count; k += 32) {
+                    const unsigned long long o = o0 + (unsigned long long)k;
+                    if (o >= cap) break;
+                    const int ty = r.z + k / ncols, tx = r.x + k % ncols;
+                    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
+                    pkey[o] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
+                    pval[o] = slot;
+                }
+            } else {
+                const float4* R = rec + (size_t)slot * kRecordF4;
+                const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
+                unsigned long long o = o0;
+                for (int row0 = r.z; row0 <= ty1; row0 += 32) {
+                    const int ty = row0 + lane;
+                    int t0 = 0, t1 = -1;
+                    if (ty <= ty1 && !footprint_span(fp, ty, TW, TH, r.x, r.y, t0, t1)) t1 = -1;
+                    if (ty > ty1) t1 = -1;
+                    const uint32_t nrow = t1 >= t0 ? (uint32_t)(t1 - t0 + 1) : 0u;
+                    uint32_t pre = nrow;  // warp inclusive scan of the row counts
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, d);
+                        if (lane >= d) pre += y;
+                    }
+                    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+                    unsigned long long q = o + (pre - nrow);
+                    for (int tx = t0; tx <= t1 && q < cap; ++tx, ++q) {
+                        const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
+                        pkey[q] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
+                        pval[q] = slot;
+                    }
+                    o += total;
                 }
             }
         }

@@ -323,6 +323,89 @@ gsr_status gsr_backward(const gsr_plan* plan, void* workspace, size_t workspace_
                         const gsr_camera_out* fwd, const gsr_camera_grad* grad, const gsr_surfels* surfels,
                         const gsr_objects* objects, const gsr_surfel_grads* out, void* stream);
 
+/* -------------------------------------------------------- learned decode */
+
+/*
+ * Anchors of a neural-Gaussian scene (Sec. III-A, "Scene Reconstruction":
+ * anchors organised as in Scaffold-GS; an MLP infers the 2DGS attributes of
+ * each anchor's k offset surfels).  DEVICE arrays:
+ *   pos [n][3], feature [n][feat_dim], scale [n] (l_a > 0), offsets [n][k][3],
+ *   intensity [n][k] (LiDAR intensity of each offset surfel; may be NULL).
+ * Built shapes: k = 10, feat_dim = 32 (others return GSR_ERR_UNSUPPORTED).
+ */
+typedef struct {
+    int32_t n;
+    int32_t k;
+    int32_t feat_dim;
+    const float* pos;
+    const float* feature;
+    const float* scale;
+    const float* offsets;
+    const float* intensity;
+} gsr_anchors;
+
+/* The decode MLP, FP32 masters (DEVICE, row-major): w1 [feat_dim+4][hidden],
+ * b1 [hidden], w2 [hidden][10 k], b2 [10 k]; hidden = 64. */
+typedef struct {
+    int32_t hidden;
+    const float* w1;
+    const float* b1;
+    const float* w2;
+    const float* b2;
+} gsr_mlp;
+
+/* Gradients of the MLP (and optionally of the anchor features), accumulated (+=). */
+typedef struct {
+    float* w1;
+    float* b1;
+    float* w2;
+    float* b2;
+    float* feature; /* [n][feat_dim], may be NULL */
+} gsr_mlp_grads;
+
+/* A writable surfel table (DEVICE) with degree-0 SH, as produced by the decode:
+ * pos [N][3], log_scale [N][2], quat [N][4], opacity [N], sh [N][1][3], intensity [N] (may be NULL). */
+typedef struct {
+    float* pos;
+    float* log_scale;
+    float* quat;
+    float* opacity;
+    float* sh;
+    float* intensity;
+} gsr_surfel_table;
+
+#define GSR_DECODE_BF16_TENSOR 0 /* BF16 inputs/weights on tcgen05 tensor cores, FP32 accumulation */
+#define GSR_DECODE_F32 1         /* FP32 on the SIMT cores (reference path)                      */
+
+/*
+ * Decode every anchor into k surfels (surfel a k + j = offset j of anchor a):
+ *   X = [feature, (x_a - o)/|x_a - o|, |x_a - o|], H = ReLU(X w1 + b1),
+ *   y = H w2 + b2; offset j: opacity logit y0, colour sigmoid(y1..3) stored as
+ *   degree-0 SH, log-scale y4..5 + ln l_a, raw quaternion y6..9, centre
+ *   x_a + l_a offset_j, intensity from the anchors.
+ * origin (host float[3]) is the view origin o (camera centre; rig centre for
+ * a rig).  cull_camera (host, may be NULL): anchors whose sphere of radius
+ * l_a max|offset| + 3 m is outside that pinhole's frustum get opacity logit
+ * -1e4.  device_status (DEVICE uint32, may be NULL) records GSR_ERR_TIMEOUT
+ * if a bounded wait on the tensor cores gave up.
+ */
+gsr_status gsr_decode_anchors(const gsr_anchors* anchors, const gsr_mlp* mlp, const float* origin,
+                              const gsr_sensor* cull_camera, int32_t precision, const gsr_surfel_table* out,
+                              uint32_t* device_status, void* stream);
+
+/*
+ * Back-propagate d(loss)/d(decoded surfel table) (opacity, sh, log_scale,
+ * quat of the table produced by gsr_decode_anchors with the same arguments)
+ * through the decode activations and the MLP (FP32), accumulating into *out.
+ */
+gsr_status gsr_decode_backward(const gsr_anchors* anchors, const gsr_mlp* mlp, const float* origin,
+                               const gsr_sensor* cull_camera, const gsr_surfel_grads* d_surfels,
+                               const gsr_mlp_grads* out, void* stream);
+
+/* Adam step on an FP32 master array (step counts from 1; bias-corrected). */
+gsr_status gsr_adam(float* param, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                    float beta2, float eps, int32_t step, void* stream);
+
 /* ------------------------------------------------------------ whole rig */
 
 /*

@@ -323,6 +323,10 @@ extern "C" size_t gsr_struct_size(int32_t which)
     case 7: return sizeof(gsr_camera_grad);
     case 8: return sizeof(gsr_surfel_grads);
     case 9: return sizeof(gsr_loss_weights);
+    case 10: return sizeof(gsr_anchors);
+    case 11: return sizeof(gsr_mlp);
+    case 12: return sizeof(gsr_mlp_grads);
+    case 13: return sizeof(gsr_surfel_table);
     default: return 0;
     }
 }

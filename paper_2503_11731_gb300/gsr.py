@@ -73,7 +73,28 @@ class LossWeights(ctypes.Structure):
     _fields_ = [("w_dist", c_f32), ("w_normal", c_f32), ("mask_alpha", c_f32)]
 
 
-_STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights]
+class Anchors(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("k", c_i32), ("feat_dim", c_i32), ("pos", c_vp), ("feature", c_vp), ("scale", c_vp),
+                ("offsets", c_vp), ("intensity", c_vp)]
+
+
+class Mlp(ctypes.Structure):
+    _fields_ = [("hidden", c_i32), ("w1", c_vp), ("b1", c_vp), ("w2", c_vp), ("b2", c_vp)]
+
+
+class MlpGrads(ctypes.Structure):
+    _fields_ = [("w1", c_vp), ("b1", c_vp), ("w2", c_vp), ("b2", c_vp), ("feature", c_vp)]
+
+
+class SurfelTable(ctypes.Structure):
+    _fields_ = [("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp),
+                ("intensity", c_vp)]
+
+
+DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
+
+_STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights,
+            Anchors, Mlp, MlpGrads, SurfelTable]
 
 # exported symbols and their ctypes signatures (restype, argtypes)
 SIGNATURES = {
@@ -107,6 +128,12 @@ SIGNATURES = {
                                        c_vp, ctypes.POINTER(c_vp)]),
     "gsr_frame_graph_launch": (c_i32, [c_vp, c_vp]),
     "gsr_frame_graph_destroy": (c_i32, [c_vp]),
+    "gsr_decode_anchors": (c_i32, [ctypes.POINTER(Anchors), ctypes.POINTER(Mlp), ctypes.POINTER(c_f32),
+                                   ctypes.POINTER(Sensor), c_i32, ctypes.POINTER(SurfelTable), c_vp, c_vp]),
+    "gsr_decode_backward": (c_i32, [ctypes.POINTER(Anchors), ctypes.POINTER(Mlp), ctypes.POINTER(c_f32),
+                                    ctypes.POINTER(Sensor), ctypes.POINTER(SurfelGrads), ctypes.POINTER(MlpGrads),
+                                    c_vp]),
+    "gsr_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_i32, c_vp]),
     "gsr_loss_noalloc": (c_i32, [ctypes.POINTER(Sensor), ctypes.POINTER(CameraOut), c_vp,
                                  ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
@@ -290,3 +317,22 @@ class FrameGraph:
             self.close()
         except Exception:
             pass
+
+
+def decode_anchors(anchors: Anchors, mlp: Mlp, origin, cull_camera, precision, out: SurfelTable, status, stream):
+    o = (c_f32 * 3)(*[float(v) for v in origin])
+    _check(lib().gsr_decode_anchors(ctypes.byref(anchors), ctypes.byref(mlp), o,
+                                    ctypes.byref(cull_camera) if cull_camera is not None else None, int(precision),
+                                    ctypes.byref(out), status, stream), "gsr_decode_anchors")
+
+
+def decode_backward(anchors: Anchors, mlp: Mlp, origin, cull_camera, d_surfels: SurfelGrads, out: MlpGrads, stream):
+    o = (c_f32 * 3)(*[float(v) for v in origin])
+    _check(lib().gsr_decode_backward(ctypes.byref(anchors), ctypes.byref(mlp), o,
+                                     ctypes.byref(cull_camera) if cull_camera is not None else None,
+                                     ctypes.byref(d_surfels), ctypes.byref(out), stream), "gsr_decode_backward")
+
+
+def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, stream):
+    _check(lib().gsr_adam(param, grad, m, v, int(n), float(lr), float(beta1), float(beta2), float(eps), int(step),
+                          stream), "gsr_adam")

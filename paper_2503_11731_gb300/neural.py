@@ -1,0 +1,94 @@
+"""Neural-Gaussian scene on the device: anchors, the decode MLP and its Adam
+state, over the C ABI (marshalling only; the decode, its backward and the
+Adam update run in libgsr.so).
+
+A frame of the learned representation is
+    gsr_decode_anchors (BF16 tcgen05 or FP32) -> surfel table -> Renderer,
+and a training step adds
+    gsr_loss -> gsr_backward -> gsr_decode_backward -> gsr_adam.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import gsr
+from .frame import DeviceSurfels, _ptr, _stream_handle
+
+
+class DeviceAnchors:
+    def __init__(self, a, device="cuda"):
+        f = lambda x: torch.as_tensor(np.ascontiguousarray(x, np.float32), device=device)
+        self.pos, self.feature, self.scale = f(a.pos), f(a.feature), f(a.scale)
+        self.offsets, self.intensity = f(a.offsets), f(a.intensity)
+
+    @property
+    def n(self):
+        return int(self.pos.shape[0])
+
+    @property
+    def k(self):
+        return int(self.offsets.shape[1])
+
+    def struct(self):
+        return gsr.Anchors(self.n, self.k, int(self.feature.shape[1]), _ptr(self.pos), _ptr(self.feature),
+                           _ptr(self.scale), _ptr(self.offsets), _ptr(self.intensity))
+
+
+class NeuralModel:
+    """FP32 master weights of the decode MLP (+ the anchor features it trains)."""
+
+    PARAMS = ("w1", "b1", "w2", "b2")
+
+    def __init__(self, w1, b1, w2, b2, device="cuda"):
+        f = lambda x: torch.as_tensor(np.ascontiguousarray(x, np.float32), device=device)
+        self.w1, self.b1, self.w2, self.b2 = f(w1), f(b1), f(w2), f(b2)
+        self.device = device
+        self.step_count = 0
+        self._adam = {}
+
+    def struct(self):
+        return gsr.Mlp(int(self.w1.shape[1]), _ptr(self.w1), _ptr(self.b1), _ptr(self.w2), _ptr(self.b2))
+
+    def new_table(self, anchors: DeviceAnchors) -> DeviceSurfels:
+        N = anchors.n * anchors.k
+        z = lambda *s: torch.zeros(*s, device=self.device)
+        return DeviceSurfels(z(N, 3), z(N, 2), z(N, 4), z(N), z(N, 1, 3), z(N))
+
+    def decode(self, anchors: DeviceAnchors, origin, cull_camera=None, precision=gsr.DECODE_BF16_TENSOR,
+               out: DeviceSurfels = None, status=None, stream=None) -> DeviceSurfels:
+        out = self.new_table(anchors) if out is None else out
+        table = gsr.SurfelTable(_ptr(out.pos), _ptr(out.log_scale), _ptr(out.quat), _ptr(out.opacity), _ptr(out.sh),
+                                _ptr(out.intensity))
+        cam = None if cull_camera is None else gsr.sensor(cull_camera)
+        gsr.decode_anchors(anchors.struct(), self.struct(), origin, cam, precision, table,
+                           None if status is None else _ptr(status), _stream_handle(stream))
+        return out
+
+    def zero_grads(self, anchors: DeviceAnchors):
+        self.grads = {k: torch.zeros_like(getattr(self, k)) for k in self.PARAMS}
+        self.grads["feature"] = torch.zeros_like(anchors.feature)
+
+    def backward(self, anchors: DeviceAnchors, origin, surfel_grads: dict, cull_camera=None, stream=None):
+        """Accumulate d(loss)/d(w1, b1, w2, b2, features) from d(loss)/d(decoded table)."""
+        g = self.grads
+        ds = gsr.SurfelGrads(None, _ptr(surfel_grads["log_scale"]), _ptr(surfel_grads["quat"]),
+                             _ptr(surfel_grads["opacity"]), _ptr(surfel_grads["sh"]), None)
+        out = gsr.MlpGrads(_ptr(g["w1"]), _ptr(g["b1"]), _ptr(g["w2"]), _ptr(g["b2"]), _ptr(g["feature"]))
+        cam = None if cull_camera is None else gsr.sensor(cull_camera)
+        gsr.decode_backward(anchors.struct(), self.struct(), origin, cam, ds, out, _stream_handle(stream))
+
+    def adam_step(self, anchors: DeviceAnchors, lr=1e-3, lr_feature=None, betas=(0.9, 0.999), eps=1e-8,
+                  stream=None):
+        self.step_count += 1
+        h = _stream_handle(stream)
+        targets = [(k, getattr(self, k), lr) for k in self.PARAMS]
+        targets.append(("feature", anchors.feature, lr if lr_feature is None else lr_feature))
+        for name, p, rate in targets:
+            if name not in self._adam:
+                self._adam[name] = (torch.zeros_like(p), torch.zeros_like(p))
+            m, v = self._adam[name]
+            gsr.adam(_ptr(p), _ptr(self.grads[name]), _ptr(m), _ptr(v), p.numel(), rate, betas[0], betas[1], eps,
+                     self.step_count, h)

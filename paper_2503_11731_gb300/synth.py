@@ -400,3 +400,16 @@ def road_poses(n_poses, seed, x_range=(-40.0, 80.0), yaw_deg=10.0, height=1.5):
     xs = rng.uniform(*x_range, n_poses)
     yaws = rng.uniform(-yaw_deg, yaw_deg, n_poses)
     return [(float(x), float(yw)) for x, yw in zip(xs, yaws)]
+
+
+def init_mlp(seed, feat_dim=32, hidden=64, k=10):
+    """Seeded anchor-MLP weights W1 [feat_dim+4, hidden], b1, W2 [hidden, 10 k],
+    b2 (float32).  Uniform He-style weights; biases start every offset at
+    opacity logit 0, grey colour, log-scale -2 and the identity rotation."""
+    rng = np.random.default_rng(seed)
+    n_in = feat_dim + 4
+    W1 = rng.uniform(-1, 1, (n_in, hidden)) * math.sqrt(6.0 / n_in) * 0.5
+    b1 = np.zeros(hidden)
+    W2 = rng.uniform(-1, 1, (hidden, 10 * k)) * math.sqrt(6.0 / hidden) * 0.1
+    b2 = np.tile(np.array([0.0, 0.0, 0.0, 0.0, -2.0, -2.0, 1.0, 0.0, 0.0, 0.0]), k)
+    return W1.astype(np.float32), b1.astype(np.float32), W2.astype(np.float32), b2.astype(np.float32)

@@ -3,24 +3,34 @@
 Workload (seeded, synthetic; the paper's driving datasets are not available):
   6 pinhole cameras (2 x 1920x1080 f=1000 front/back, 4 x 1280x720 f=640 at
   yaw +-60/+-120 deg) and 2 spinning LiDARs (128x1800, el -25..15 deg;
-  32x1024, el -30..10 deg) over a 3M-surfel SH-3 driving scene plus 20
-  inserted 50k-surfel objects placed by rigid SE(3) poses; 16x16 tiles.
-A step renders the whole frame: gsr_preprocess (all 8 sensors) ->
-gsr_bin_sort -> gsr_render_camera x6 + gsr_render_lidar x2, inputs resident
-in HBM (the surfel table, ~1 GB, is larger than L2, so no flush is needed).
+  32x1024, el -30..10 deg); background = 300k anchors x 10 offsets decoded
+  by the anchor MLP (BF16 tcgen05, FP32 accumulation; seeded untrained
+  weights, view origin the rig centre) into 3M SH-0 surfels, plus 20
+  inserted 50k-surfel SH-3 objects placed by rigid SE(3) poses; camera tiles
+  16x16, LiDAR tiles 8x8.
+A step renders the whole frame as three graph replays: gsr_decode_anchors;
+gsr_preprocess_part (background, objects) + gsr_bin_sort; gsr_render_rig
+(one persistent launch for all 8 sensors).  Inputs are resident in HBM and
+larger than L2 (anchors 91 MB + decoded table 168 MB + objects 260 MB), so
+no flush is needed.
+
+The "compare" block times, on the same plan and workspace, the explicit
+forms of the frame: the 3M-surfel SH-3 table the anchors were grouped from
+(+ the same objects) rendered batched (two graphs) and per sensor
+(gsr_render_camera x6 + gsr_render_lidar x2, eager), and the decode alone
+in BF16 (tcgen05) and FP32 (SIMT).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsr|reference]
 
 N > 1 (under torchrun) runs N independent replicas, one frame stream per
 GPU (the path has no exchange step).  `--impl reference` times the FP64 CPU
-oracle on a bounded sample of the same frame's rays.
+oracle (decode + brute-force render) on a bounded sample of the same frame.
 """
 from __future__ import annotations
 
 import argparse
 import ctypes
 import json
-import math
 import os
 import subprocess
 import sys
@@ -33,9 +43,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms per 6-camera+2-LiDAR frame"
 UNIT = "ms/frame"
+RIG_DESC = ("rig: 6 cameras (2x1920x1080, 4x1280x720) + 2 LiDARs (128x1800, 32x1024); background 300k anchors x 10 "
+            "BF16-decoded to 3M SH-0 surfels + 20x50k posed SH-3 object surfels")
 
 
-def rig_scene():
+def rig_parts():
+    """Explicit 3M-surfel background, 20 posed 50k-surfel objects, their
+    poses and the sensors."""
     from paper_2503_11731_gb300 import synth
     bg = synth.driving_scene(n=3_000_000, seed=synth.SEED_BASE + 4, x_range=(-80.0, 120.0))
     poses = synth.object_poses(20, seed=synth.SEED_BASE + 40)
@@ -44,22 +58,28 @@ def rig_scene():
         a = synth.object_asset(50_000, seed=synth.SEED_BASE + 50 + k)
         a.obj_id = np.full(a.n, k, np.int32)
         objs = a if objs is None else objs.concat(a)
-    scene = bg.concat(objs)
-    return scene, poses, synth.surround_rig()
+    return bg, objs, poses, synth.surround_rig()
 
 
-def load_workload(name):
-    """(scene, object poses or None, sensors, description) of a named workload."""
-    if name == "rig":
-        scene, poses, sensors = rig_scene()
-        return scene, poses, sensors, ("rig: 6 cameras (2x1920x1080, 4x1280x720) + 2 LiDARs (128x1800, 32x1024), "
-                                       "3M background + 20x50k posed object surfels, SH degree 3")
-    if name == "explicit":
-        from paper_2503_11731_gb300 import synth
-        scene = synth.driving_scene()
-        return scene, None, [synth.driving_camera(), synth.driving_lidar()], \
-            "explicit: 1920x1080 camera + 128x1800 LiDAR, 1.5M-surfel SH-3 driving scene"
-    raise ValueError(name)
+def rig_neural(bg):
+    """Anchors grouped from the explicit background (10 Morton-adjacent
+    surfels each) and the seeded anchor-MLP weights."""
+    from paper_2503_11731_gb300 import synth
+    anchors, _ = synth.anchors_from_surfels(bg, k=10, seed=synth.SEED_BASE + 41)
+    return anchors, synth.init_mlp(synth.SEED_BASE + 42)
+
+
+def rig_origin(sensors):
+    """Decode view origin of a rig: the mean of its sensor centres."""
+    c = [-s.world_to_sensor[:3, :3].T @ s.world_to_sensor[:3, 3] for s in sensors]
+    return np.mean(c, axis=0)
+
+
+def explicit_workload():
+    from paper_2503_11731_gb300 import synth
+    scene = synth.driving_scene()
+    return scene, None, [synth.driving_camera(), synth.driving_lidar()], \
+        "explicit: 1920x1080 camera + 128x1800 LiDAR, 1.5M-surfel SH-3 driving scene"
 
 
 def n_rays(sensors):
@@ -150,20 +170,41 @@ def oracle_frame_estimate(scene, poses, sensors, n=32, seed=7):
     return total * 1e3, rays
 
 
+def oracle_rig_scene(objs, anchors, mlp, origin):
+    """The configured frame's surfels as the oracle computes them: the FP64
+    decode of every anchor (timed; SH-0 padded with zero coefficients to the
+    objects' degree 3, which leaves the colour unchanged) plus the objects."""
+    from oracle import mlp as OM
+    from paper_2503_11731_gb300 import synth
+    t0 = time.perf_counter()
+    d = OM.decode(anchors, *mlp, origin)
+    dec_s = time.perf_counter() - t0
+    n = anchors.n * anchors.k
+    sh = np.zeros((n, 16, 3), np.float64)
+    sh[:, :1] = d["sh"].numpy()
+    back = synth.Surfels(d["pos"].numpy(), d["log_scale"].numpy(), d["quat"].numpy(), d["opacity"].numpy(), sh,
+                         d["intensity"].numpy())
+    return back.concat(objs), dec_s
+
+
 def run_reference(args):
-    """FP64 CPU oracle on a bounded sample of the rig frame's rays."""
+    """FP64 CPU oracle: the full anchor decode plus a bounded sample of the
+    frame's rays (brute force over all surfels), scaled to the frame."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import render as OR
-    scene, poses, sensors = rig_scene()
+    bg, objs, poses, sensors = rig_parts()
+    anchors, mlp = rig_neural(bg)
+    scene, dec_s = oracle_rig_scene(objs, anchors, mlp, rig_origin(sensors))
+    del bg
     total_rays = n_rays(sensors)
     vals = []
     sampled = 0
     for step in range(args.steps + args.warmup):
         ms, k = oracle_frame_estimate(scene, poses, sensors, n=args.sample_rays, seed=7 + step)
         if step >= args.warmup:
-            vals.append(ms)
+            vals.append(ms + dec_s * 1e3)
             sampled += k
     ms_frame = float(np.mean(vals))
     cores = OR.num_threads()
@@ -171,25 +212,86 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded driving scene + rig)",
             "impl": "reference",
-            "config": {"workload": "rig: 6 cameras (2x1920x1080, 4x1280x720) + 2 LiDARs (128x1800, 32x1024), "
-                                   "3M background + 20x50k posed object surfels",
-                       "sample_rays_per_step": sampled // max(1, args.steps), "frame_rays": total_rays},
+            "config": {"workload": RIG_DESC, "sample_rays_per_step": sampled // max(1, args.steps),
+                       "frame_rays": total_rays, "oracle_decode_ms": dec_s * 1e3},
             "cpu_baseline": {"value": ms_frame, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per sensor, oracle calls on {args.sample_rays} and {2 * args.sample_rays}"
-                                       f" random rays (brute force over {scene.n} surfels) give its fixed and "
-                                       f"per-ray cost, combined for the frame's {total_rays} rays"},
+                             "sample": f"FP64 decode of all {anchors.n} anchors (torch CPU), then per sensor "
+                                       f"oracle calls on {args.sample_rays} and {2 * args.sample_rays} random rays "
+                                       f"(brute force over {scene.n} surfels) give its fixed and per-ray cost, "
+                                       f"combined for the frame's {total_rays} rays"},
             "e2e": {"value": ms_frame, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------- GPU arm
-def cpu_baseline_quick(scene, poses, sensors, n):
-    from oracle import render as OR
-    ms, k = oracle_frame_estimate(scene, poses, sensors, n=n, seed=3)
-    return {"value": ms, "unit": UNIT, "cores": OR.num_threads(), "kind": "oracle",
-            "sample": f"per sensor, oracle calls on {n} and {2 * n} random rays (brute force over {scene.n} "
-                      f"surfels) give its fixed and per-ray cost, combined for the frame's "
-                      f"{n_rays(sensors)} rays"}
+def bin_sort_launches(plan):
+    """Kernel launches of one gsr_bin_sort: compaction 3, depth sort 4 x 3,
+    duplication 3, tile sort 3 per 8-bit pass, tile ranges 1, tile schedule
+    1 + 2 x 3."""
+    T = plan.tile_base[plan.n_sensors]
+    bits = 1
+    while (1 << bits) < T:
+        bits += 1
+    return 3 + 12 + 3 + 3 * ((bits + 7) // 8) + 1 + 1 + 6
+
+
+class Timer:
+    """Per-stage CUDA events on one stream."""
+
+    def __init__(self, stream, names):
+        self.stream, self.names = stream, names
+        self.ev = {k: [] for k in names}
+
+    def stage(self, name, fn, record):
+        import torch
+        if not record:
+            fn()
+            return
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(self.stream)
+        fn()
+        b.record(self.stream)
+        self.ev[name].append((a, b))
+
+    def means(self):
+        return {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in self.ev.items() if v}
+
+
+def timed(stream, steps, step):
+    import torch
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
+def sensor_stats(r, sensors, n_surfels):
+    import torch
+    counts = r.region(2, torch.int32)
+    out = []
+    for si, s in enumerate(sensors):
+        c = counts[si * n_surfels:(si + 1) * n_surfels]
+        out.append({"kind": s.kind, "rays": s.width * s.height, "visible": int((c > 0).sum()),
+                    "pairs": int(c.sum()), "mean_walk": float(r.out[si]["n_walk"].float().mean()),
+                    "mean_last_contrib": float(r.out[si]["n_contrib"].float().mean())})
+    return out
+
+
+def walks(r, sensors):
+    cam = sum(int(o["n_walk"].sum().item()) for o, s in zip(r.out, sensors) if s.kind != "lidar")
+    lid = sum(int(o["n_walk"].sum().item()) for o, s in zip(r.out, sensors) if s.kind == "lidar")
+    return cam, lid
+
+
+def check_status(r):
+    st, nvis, npairs = r.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} (pairs {npairs}, capacity {r.plan.max_dup})")
+    return nvis, npairs
 
 
 def run_gpu(args):
@@ -198,7 +300,9 @@ def run_gpu(args):
 
     from paper_2503_11731_gb300 import build as B
     B.build()
+    from paper_2503_11731_gb300 import gsr
     from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    from paper_2503_11731_gb300.neural import DeviceAnchors, NeuralFrame, NeuralModel
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -207,50 +311,57 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    scene, poses, sensors, wl_desc = load_workload(args.workload)
-    dev = DeviceSurfels.from_host(scene)
-    pose_t = None if poses is None else torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
     parse = lambda t: tuple(int(v) for v in t.split("x"))
+    if args.workload == "rig":
+        bg, objs, poses, sensors = rig_parts()
+        anchors, mlp = rig_neural(bg)
+        scene = bg.concat(objs)
+        del bg
+        wl_desc = RIG_DESC
+    else:
+        scene, poses, sensors, wl_desc = explicit_workload()
+        objs = anchors = None
     tiles = [parse(args.lidar_tile) if s.kind == "lidar" else parse(args.camera_tile) for s in sensors]
     r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles,
                  outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
-    # eager warm-up frame (fills caches, checks the status), then the two graphs:
-    # preprocess + bin_sort, and the persistent whole-rig compositing launch
-    r.render_rig(dev, pose_t, stream)
-    torch.cuda.synchronize()
-    g_front = r.graph(dev, pose_t, stages=3)
-    g_rig = r.graph(dev, pose_t, stages=4)
-    ev = {k: [] for k in ("pre_sort", "render_rig")}
+    pose_t = None if poses is None else torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    dev = DeviceSurfels.from_host(scene)
+    origin = rig_origin(sensors)
+
+    # ---- the benchmarked form
+    if anchors is not None:
+        model = NeuralModel(*mlp)
+        da = DeviceAnchors(anchors)
+        d_obj = DeviceSurfels.from_host(objs)
+        nf = NeuralFrame(model, da, r, d_obj, pose_t, origin, gsr.DECODE_BF16_TENSOR)
+        nf.render()
+        torch.cuda.synchronize()
+        G = nf.graphs()
+        stages = [("decode", G["decode"].replay), ("pre_sort", G["front"].replay),
+                  ("render_rig", lambda: G["render_rig"].launch(sh))]
+        n_launch = 1 + 2 + bin_sort_launches(r.plan) + 1
+        n_main = nf.n_bg + objs.n
+    else:
+        r.render_rig(dev, pose_t)
+        torch.cuda.synchronize()
+        gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
+        stages = [("pre_sort", lambda: gf.launch(sh)), ("render_rig", lambda: gr.launch(sh))]
+        n_launch = 1 + bin_sort_launches(r.plan) + 1
+        n_main = scene.n
+    tm = Timer(stream, [k for k, _ in stages])
 
     def step(record=False):
-        if record:
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-        g_front.launch(sh)
-        if record:
-            e[1].record(stream)
-        g_rig.launch(sh)
-        if record:
-            e[2].record(stream)
-            ev["pre_sort"].append((e[0], e[1]))
-            ev["render_rig"].append((e[1], e[2]))
+        for name, fn in stages:
+            tm.stage(name, fn, record)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    st, nvis, npairs = r.status()
-    if st != 0:
-        raise RuntimeError(f"device status {st} (pairs {npairs}, capacity {r.plan.max_dup})")
-    counts = r.region(2, torch.int32)
-    per_sensor = []
-    for si, s in enumerate(sensors):
-        c = counts[si * scene.n:(si + 1) * scene.n]
-        per_sensor.append({"kind": s.kind, "rays": s.width * s.height, "visible": int((c > 0).sum()),
-                           "pairs": int(c.sum()),
-                           "mean_walk": float(r.out[si]["n_walk"].float().mean()),
-                           "mean_last_contrib": float(r.out[si]["n_contrib"].float().mean())})
+    nvis, npairs = check_status(r)
+    per_sensor = sensor_stats(r, sensors, n_main)
+    walk_cam, walk_lid = walks(r, sensors)
 
     clk_p, clk_f = sample_clocks_start() if rank == 0 else (None, None)
     time.sleep(0.3)
@@ -272,28 +383,33 @@ def run_gpu(args):
         tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    stage = {k: float(np.mean([a.elapsed_time(b) for a, b in v])) for k, v in ev.items()}
+    stage = tm.means()
     ms_step = ms / args.steps
     value = ms / (args.steps * world)
 
-    # ---- e2e: host surfel table in pinned memory -> device, frame -> host
-    host = {k: torch.as_tensor(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory()
-            for k in ("pos", "log_scale", "quat", "opacity", "sh", "intensity")}
+    # ---- e2e through the public API: this step's inputs from pinned host
+    # memory (anchors + MLP + object table + poses, or the explicit table),
+    # the frame's rgb / depth / range / intensity back to pinned host memory
+    if anchors is not None:
+        src = [(getattr(da, k), getattr(anchors, k)) for k in ("pos", "feature", "scale", "offsets", "intensity")]
+        src += [(getattr(model, k), v) for k, v in zip(("w1", "b1", "w2", "b2"), mlp)]
+        src += [(getattr(d_obj, k), getattr(objs, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh",
+                                                               "intensity", "obj_id")]
+    else:
+        src = [(getattr(dev, k), getattr(scene, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh",
+                                                            "intensity")]
+    host = [(d, torch.as_tensor(np.ascontiguousarray(h, np.int32 if d.dtype == torch.int32 else np.float32))
+             .reshape(d.shape).pin_memory()) for d, h in src if d is not None]
     if poses is not None:
-        host["obj_id"] = torch.as_tensor(scene.obj_id).pin_memory()
-        host_pose = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32)).pin_memory()
+        host.append((pose_t, torch.as_tensor(poses.reshape(-1, 12).astype(np.float32)).pin_memory()))
     outs_host = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items()
                   if k in ("rgb", "depth", "range", "intensity")} for o in r.out]
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
-    if poses is not None:
-        h2d += host_pose.numel() * 4
+    h2d = sum(t.numel() * t.element_size() for _, t in host)
     d2h = sum(t.numel() * t.element_size() for o in outs_host for t in o.values())
 
     def e2e_step():
-        for k, t in host.items():
-            getattr(dev, k).copy_(t, non_blocking=True)
-        if poses is not None:
-            pose_t.copy_(host_pose, non_blocking=True)
+        for d, h in host:
+            d.copy_(h, non_blocking=True)
         step()
         for o, oh in zip(r.out, outs_host):
             for k, t in oh.items():
@@ -301,16 +417,40 @@ def run_gpu(args):
 
     for _ in range(2):
         e2e_step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    n_e2e = max(3, args.steps // 2)
-    for _ in range(n_e2e):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e / world if world == 1 else e0.elapsed_time(e1) / n_e2e
+    e2e_ms = timed(stream, max(3, args.steps // 2), e2e_step)
+
+    # ---- compare: explicit forms of the same frame and the decode alone
+    compare = None
+    if anchors is not None and args.compare:
+        r.render_rig(dev, pose_t)
+        torch.cuda.synchronize()
+        gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
+        k = max(3, args.steps // 2)
+        for _ in range(2):
+            gf.launch(sh)
+            gr.launch(sh)
+        batched = timed(stream, k, lambda: (gf.launch(sh), gr.launch(sh)))
+        ex_nvis, ex_pairs = check_status(r)
+        ex_sensors = sensor_stats(r, sensors, scene.n)
+        ex_cam, ex_lid = walks(r, sensors)
+        per_sensor_ms = timed(stream, k, lambda: (r.preprocess(dev, pose_t), r.bin_sort(), r.composite()))
+        dec = {}
+        for name, prec in (("bf16_tcgen05", gsr.DECODE_BF16_TENSOR), ("f32_simt", gsr.DECODE_F32)):
+            nf.precision = prec
+            dec[name] = timed(stream, 2 * k, nf.decode)
+        nf.precision = gsr.DECODE_BF16_TENSOR
+        compare = {
+            "explicit_batched_ms": batched,
+            "explicit_per_sensor_ms": per_sensor_ms,
+            "explicit_table": f"{scene.n} SH-3 surfels (the background the anchors were grouped from + objects)",
+            "explicit_pairs": ex_pairs, "explicit_visible_records": ex_nvis,
+            "explicit_walks": {"camera": ex_cam, "lidar": ex_lid},
+            "explicit_per_sensor": ex_sensors,
+            "decode_ms": dec,
+            "note": "batched and per-sensor explicit forms give bit-identical frames (tested); the learned form "
+                    "renders the decoded scene of an untrained seeded network, so its pair and walk counts differ",
+        }
+        del gf, gr
 
     if rank != 0:
         if world > 1:
@@ -320,30 +460,40 @@ def run_gpu(args):
     # ---- roofline of the dominant kernel: the persistent whole-rig compositing
     # launch.  Algorithmic work = for every ray, the list entries it must
     # examine (its stop position, or its whole tile list) x the FP32 lane-ops
-    # of one ray-surfel evaluation (24 camera, 28 LiDAR; the design doc counts them).
-    pk, src = peaks()
-    walk_cam = sum(int(o["n_walk"].sum().item()) for o, s in zip(r.out, sensors) if s.kind != "lidar")
-    walk_lid = sum(int(o["n_walk"].sum().item()) for o, s in zip(r.out, sensors) if s.kind == "lidar")
+    # of one ray-surfel evaluation (24 camera, 28 LiDAR).
+    pk, src_name = peaks()
     ops = walk_cam * 24 + walk_lid * 28
     alu_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
     rig_ms = stage["render_rig"]
     achieved = ops / (rig_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "k_render_rig (all 8 sensors, one persistent launch)", "achieved": achieved,
             "peak": alu_peak, "unit": "T FP32 lane-op/s", "frac": achieved / alu_peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock of " + src + " peaks",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock of " + src_name + " peaks",
             "algorithmic_units": f"{walk_cam} camera x 24 + {walk_lid} LiDAR x 28 ray-surfel evaluations "
                                  "(per ray: the list entries it must examine)",
             "kernel_ms": rig_ms}
-    launches_per_step = 1 + (3 + 3 * 4 + 3 + 3 * 2 + 1) + (1 + 3 * 2) + 1
-    cpu = cpu_baseline_quick(scene, poses, sensors, args.sample_rays) if args.sample_rays > 0 else None
+    cpu = None
+    if args.sample_rays > 0 and rank == 0:
+        from oracle import render as OR
+        if anchors is not None:
+            o_scene, dec_s = oracle_rig_scene(objs, anchors, mlp, origin)
+        else:
+            o_scene, dec_s = scene, 0.0
+        ms_o, _ = oracle_frame_estimate(o_scene, poses, sensors, n=args.sample_rays, seed=3)
+        cpu = {"value": ms_o + dec_s * 1e3, "unit": UNIT, "cores": OR.num_threads(), "kind": "oracle",
+               "sample": (f"FP64 decode of all anchors ({dec_s * 1e3:.0f} ms), then " if anchors is not None else "")
+               + f"per sensor, oracle calls on {args.sample_rays} and {2 * args.sample_rays} random rays (brute "
+                 f"force over {o_scene.n} surfels) give its fixed and per-ray cost, combined for the frame's "
+                 f"{n_rays(sensors)} rays"}
     total_rays = n_rays(sensors)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded driving scene + rig)",
+        "vs_baseline": None, "dtype": "f32 (decode bf16 tcgen05, fp32 accumulation)" if anchors is not None
+        else "f32", "data": "synthetic (seeded driving scene + rig; untrained seeded anchor MLP)",
         "config": {"workload": wl_desc, "tiles": [f"{t[0]}x{t[1]}" for t in tiles],
-                   "surfels": scene.n, "rays_per_frame": total_rays, "visible_records": nvis,
-                   "tile_pairs": npairs, "l2": "inputs (1.0 GB surfel table) larger than L2, no flush",
+                   "surfels": n_main, "rays_per_frame": total_rays, "visible_records": nvis,
+                   "tile_pairs": npairs, "l2": "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},
         "stage_ms": stage,
         "per_sensor": per_sensor,
@@ -351,7 +501,8 @@ def run_gpu(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": n_launch * args.steps,
+        "compare": compare,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -372,6 +523,8 @@ def main():
     ap.add_argument("--camera-tile", default="16x16")
     ap.add_argument("--lidar-tile", default="8x8")
     ap.add_argument("--sample-rays", type=int, default=16)
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the explicit-form and decode-only timings")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -225,6 +225,18 @@ gsr_status gsr_preprocess(const gsr_plan* plan, const gsr_surfels* surfels, cons
                           void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gsr_preprocess for one part of the plan's surfels: table `surfels` (n
+ * rows, its own SH degree) is surfels [first, first + n) of the plan, so a
+ * frame can mix tables, e.g. a decoded SH-0 background and SH-3 posed
+ * objects.  The status word is cleared only by the part with first == 0;
+ * every plan surfel must be covered by exactly one part before
+ * gsr_bin_sort.  Composite ties break by plan index as for one table.
+ * Errors: GSR_ERR_INVALID_ARG when first < 0 or first + n > plan->n_surfels.
+ */
+gsr_status gsr_preprocess_part(const gsr_plan* plan, const gsr_surfels* surfels, const gsr_objects* objects,
+                               int32_t first, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Step (b): compaction of visible records, radix sort of their centre-depth
  * keys, prefix sum of tile counts, key duplication (tile id, record), stable
  * radix sort by tile id -- together the stable sort of 64-bit (tile | depth)

@@ -13,7 +13,7 @@
 namespace gsr {
 
 __global__ void k_preprocess(SensorTable tab, gsr_surfels S, const float* poses, int n_obj, float4* rec,
-                             ushort4* rects, uint32_t* counts, uint32_t* keys);
+                             ushort4* rects, uint32_t* counts, uint32_t* keys, int first, int n_plan);
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st);
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st);
 cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd, const float* target,
@@ -157,6 +157,10 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
             max_hw = std::max<uint64_t>(max_hw, (uint64_t)sensors[i].width * sensors[i].height);
     sz[R_LOSS_SCRATCH] = (6 * max_hw + 3 * ((max_hw + 255) / 256) + 64) * 4;
     sz[R_TILE_KEY_A] = sz[R_TILE_VAL_A] = sz[R_TILE_KEY_B] = sz[R_TILE_VAL_B] = (uint64_t)base * 4;
+    sz[R_SPLIT_INFO] = (uint64_t)base * 16;
+    sz[R_SPLIT_STATE] = (uint64_t)base * 8;
+    sz[R_SPLIT_ITEMS] = split_item_capacity(plan) * 8;
+    sz[R_SPLIT_RAYS] = split_ray_capacity(plan) * kRayWords * 4;
     static_assert(R_END <= 32, "gsr_plan::off has 32 entries");
     uint64_t off = 0;
     for (int r = 0; r < R_END; ++r) {
@@ -186,9 +190,18 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 extern "C" gsr_status gsr_preprocess(const gsr_plan* plan, const gsr_surfels* surfels, const gsr_objects* objects,
                                      void* workspace, size_t workspace_bytes, void* stream)
 {
+    if (!plan || !surfels || surfels->n != plan->n_surfels) return GSR_ERR_INVALID_ARG;
+    return gsr_preprocess_part(plan, surfels, objects, 0, workspace, workspace_bytes, stream);
+}
+
+extern "C" gsr_status gsr_preprocess_part(const gsr_plan* plan, const gsr_surfels* surfels,
+                                          const gsr_objects* objects, int first, void* workspace,
+                                          size_t workspace_bytes, void* stream)
+{
     gsr_status st = check_ws(plan, workspace, workspace_bytes);
     if (st != GSR_OK) return st;
-    if (!surfels || surfels->n != plan->n_surfels) return GSR_ERR_INVALID_ARG;
+    if (!surfels || surfels->n < 0 || first < 0 || (int64_t)first + surfels->n > plan->n_surfels)
+        return GSR_ERR_INVALID_ARG;
     if (surfels->sh_degree < 0 || surfels->sh_degree > 3) return GSR_ERR_UNSUPPORTED;
     if (surfels->n > 0 && (!surfels->pos || !surfels->log_scale || !surfels->quat || !surfels->opacity || !surfels->sh))
         return GSR_ERR_INVALID_ARG;
@@ -202,16 +215,19 @@ extern "C" gsr_status gsr_preprocess(const gsr_plan* plan, const gsr_surfels* su
         n_obj = objects->n_objects;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    uint32_t* counters = region<uint32_t>(plan, workspace, R_COUNTERS);
-    cudaError_t e = cudaMemsetAsync(counters, 0, C_WORDS * 4, s);
-    if (e != cudaSuccess) return cuda_fail(e);
+    cudaError_t e = cudaSuccess;
+    if (first == 0) {
+        uint32_t* counters = region<uint32_t>(plan, workspace, R_COUNTERS);
+        e = cudaMemsetAsync(counters, 0, C_WORDS * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (surfels->n > 0) {
         const SensorTable tab = make_sensor_table(plan);
         dim3 grid((surfels->n + 255) / 256, plan->n_sensors);
         k_preprocess<<<grid, 256, 0, s>>>(tab, *surfels, poses, n_obj, region<float4>(plan, workspace, R_RECORDS),
                                           region<ushort4>(plan, workspace, R_RECTS),
                                           region<uint32_t>(plan, workspace, R_COUNTS),
-                                          region<uint32_t>(plan, workspace, R_DEPTHKEY));
+                                          region<uint32_t>(plan, workspace, R_DEPTHKEY), first, plan->n_surfels);
         e = cudaGetLastError();
     }
     return cuda_fail(e);

@@ -33,6 +33,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;               // items per thread per sort tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kRadixBits = 8;
+constexpr int kSplitChunk = 2048;         // list positions per chunk of a split tile
+constexpr int kRayWords = 13;             // words of a stored per-ray compositing state
 constexpr int kRadix = 1 << kRadixBits;
 
 // Workspace regions (indices into gsr_plan::off).
@@ -48,6 +50,10 @@ enum Region : int {
     R_RECGRAD,       // d(loss)/d(record), same layout as R_RECORDS
     R_LOSS_SCRATCH,  // loss: [6][H][W] central-difference gradients + block partials
     R_TILE_KEY_A, R_TILE_VAL_A, R_TILE_KEY_B, R_TILE_VAL_B,  // tiles by descending list length
+    R_SPLIT_INFO,    // per tile uint4: chunks after the first, ray-record base, first item
+    R_SPLIT_STATE,   // per tile uint2: phase-A outcome, chunks not yet walked
+    R_SPLIT_ITEMS,   // (tile, chunk) of every split tile's chunks 1..C
+    R_SPLIT_RAYS,    // ray records of split tiles (carry + one block per chunk)
     R_END
 };
 
@@ -60,6 +66,8 @@ enum Counter : int {
     C_NDUP_WANT = 4, // uint64 at words 4..5: pairs requested
     C_TIMEOUT_AT = 6,
     C_NTILES = 7,    // total tiles of the plan (item count of the tile-order sort)
+    C_NITEMS = 8,    // split-tile chunks of this frame
+    C_SPLIT_QUEUE = 9, // work-queue head of the split-chunk kernel
     C_WORDS = 16
 };
 
@@ -109,6 +117,15 @@ SensorTable make_sensor_table(const gsr_plan* p);
 
 // Which buffer (0 = A, 1 = B) holds the result of a sort of `passes` passes that started in A.
 inline int sort_result_buffer(int passes) { return passes & 1; }
+
+// Capacity of the split-tile ray records (a fixed share of the pair
+// capacity) and of the split items (each item holds >= 32 ray records).
+inline uint64_t split_ray_capacity(const gsr_plan* p)
+{
+    const uint64_t c = (uint64_t)p->max_dup / 64;
+    return c < 65536 ? 65536 : c;
+}
+inline uint64_t split_item_capacity(const gsr_plan* p) { return split_ray_capacity(p) / 32 + 1; }
 int tile_sort_passes(const gsr_plan* p);
 constexpr int kDepthSortPasses = 4;
 
@@ -208,6 +225,8 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
         if (dx >= half) dx -= columns;
         if (dx < -half) dx += columns;
     }
+    // straight-line code (no early return): callers evaluate several
+    // records at once and the independent chains interleave
     const float rq = __fdividef(1.f, q2);
     const float u = q0 * rq, v = q1 * rq;
     const float zi = r2.w * rq;
@@ -215,12 +234,10 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
     const bool v3 = (zi > near_plane) && (rho3 <= kSupport);
     const bool vlp = rholp <= kSupport;
-    if (!(v3 || vlp)) return false;
     const bool use3 = v3 && (!vlp || rho3 <= rholp);
     const float rho = use3 ? rho3 : rholp;
     const float G = __expf(-0.5f * rho);
     const float alpha = fminf(kAlphaMax, R[3].x * G);
-    if (alpha < kAlphaMin) return false;
     sp.alpha = alpha;
     sp.z = use3 ? zi : R[4].w;
     sp.G = G;
@@ -228,7 +245,7 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     sp.u = u; sp.v = v; sp.rho = rho;
     sp.dx = dx; sp.dy = dy;
     sp.use3 = use3;
-    return true;
+    return (v3 || vlp) && alpha >= kAlphaMin;
 }
 
 // ------------------------------------------------------------ tile culling

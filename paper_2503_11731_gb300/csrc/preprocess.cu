@@ -134,15 +134,19 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 
 }  // namespace
 
+// Surfel i of the table S is surfel `first + i` of the plan (n_plan surfels),
+// so several tables (e.g. a decoded background and posed objects) can share
+// one plan.  Composite ties break by plan index, as in a single table.
 __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels S, const float* __restrict__ poses,
                                                     int n_obj, float4* __restrict__ rec, ushort4* __restrict__ rects,
-                                                    uint32_t* __restrict__ counts, uint32_t* __restrict__ keys)
+                                                    uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,
+                                                    int first, int n_plan)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int si = blockIdx.y;
     if (i >= S.n) return;
     const SensorDev& sd = tab.s[si];
-    const size_t slot = (size_t)si * S.n + i;
+    const size_t slot = (size_t)si * n_plan + first + i;
 
     // ---- surfel in world (optional rigid object pose)
     F3 mu = f3(__ldg(S.pos + 3 * i), __ldg(S.pos + 3 * i + 1), __ldg(S.pos + 3 * i + 2));

@@ -16,6 +16,10 @@
 
 namespace gsr {
 
+constexpr int kIlp = 4;  // records evaluated per step of a ray's walk
+
+// Per-ray compositing state.  Stored ray records (split tiles, below) keep
+// its 13 fields in this order, one word each.
 struct RayState {
     float T, A, B, D;
     float f0, f1, f2;
@@ -25,40 +29,80 @@ struct RayState {
     bool done;
 };
 
-// Composite one tile with the whole CTA.  Threads beyond the tile's rays only
-// help staging.  `gb` counts the batches this CTA has staged so far (it picks
-// the buffer and the mbarrier phase, so a persistent CTA can run many tiles).
-template <int KIND>
-__device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int tile_h, int local_tile,
-                                            const uint2 range, const float4* __restrict__ rec,
-                                            const uint32_t* __restrict__ pval, const FrameOut& out,
-                                            uint32_t* counters, float4* buf, uint64_t* bars, uint32_t& gb)
+__device__ __forceinline__ void ray_init(RayState& s, bool done, uint32_t n)
 {
-    const int nthr = blockDim.x;
-    const int tid = threadIdx.x;
-    const int tx = local_tile % sd.tiles_x, ty = local_tile / sd.tiles_x;
-    const int x = tx * tile_w + tid % tile_w;
-    const int y = ty * tile_h + tid / tile_w;
-    const bool inside = tid < tile_w * tile_h && x < sd.width && y < sd.height;
-
-    float rx, ry, d0, d1, d2;
-    ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
-    RayState s;
     s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;
     s.f0 = s.f1 = s.f2 = 0.f;
     s.n0 = s.n1 = s.n2 = 0.f;
     s.last = 0;
-    s.walk = (uint32_t)(range.y - range.x);
-    s.done = !inside;
+    s.walk = n;
+    s.done = done;
+}
 
-    const uint32_t start = range.x;
-    const int n = (int)(range.y - range.x);
-    const int nb = (n + nthr - 1) / nthr;
+// Ray record block: field f of ray r at blk[f * R + r] (coalesced per field).
+__device__ __forceinline__ void store_ray(float* blk, int R, int r, const RayState& s)
+{
+    blk[0 * R + r] = s.T; blk[1 * R + r] = s.A; blk[2 * R + r] = s.B; blk[3 * R + r] = s.D;
+    blk[4 * R + r] = s.f0; blk[5 * R + r] = s.f1; blk[6 * R + r] = s.f2;
+    blk[7 * R + r] = s.n0; blk[8 * R + r] = s.n1; blk[9 * R + r] = s.n2;
+    blk[10 * R + r] = __uint_as_float(s.last);
+    blk[11 * R + r] = __uint_as_float(s.walk);
+    blk[12 * R + r] = __uint_as_float(s.done ? 1u : 0u);
+}
+
+// Loads bypass L1: the block was written by another CTA of this grid.
+__device__ __forceinline__ void load_ray(const float* blk, int R, int r, RayState& s)
+{
+    s.T = __ldcg(blk + 0 * R + r); s.A = __ldcg(blk + 1 * R + r);
+    s.B = __ldcg(blk + 2 * R + r); s.D = __ldcg(blk + 3 * R + r);
+    s.f0 = __ldcg(blk + 4 * R + r); s.f1 = __ldcg(blk + 5 * R + r); s.f2 = __ldcg(blk + 6 * R + r);
+    s.n0 = __ldcg(blk + 7 * R + r); s.n1 = __ldcg(blk + 8 * R + r); s.n2 = __ldcg(blk + 9 * R + r);
+    s.last = __float_as_uint(__ldcg(blk + 10 * R + r));
+    s.walk = __float_as_uint(__ldcg(blk + 11 * R + r));
+    s.done = __float_as_uint(__ldcg(blk + 12 * R + r)) != 0u;
+}
+
+// One ray of a tile: its pixel / cell, whether it is inside the sensor, and
+// the quantities of its two planes (ray_setup).
+struct TileRay {
+    int x, y;
+    bool inside;
+    float rx, ry, d0, d1, d2;
+};
+
+template <int KIND>
+__device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, int local_tile)
+{
+    TileRay t;
+    const int tid = threadIdx.x;
+    const int tx = local_tile % sd.tiles_x, ty = local_tile / sd.tiles_x;
+    t.x = tx * sd.tile_w + tid % sd.tile_w;
+    t.y = ty * sd.tile_h + tid / sd.tile_w;
+    t.inside = tid < sd.tile_w * sd.tile_h && t.x < sd.width && t.y < sd.height;
+    ray_setup<KIND>(sd, t.x, t.y, t.rx, t.ry, t.d0, t.d1, t.d2);
+    return t;
+}
+
+// Walk list positions [lo, hi) of a tile (list starting at `start`) with the
+// whole CTA, continuing each ray's state.  Batches of blockDim.x records are
+// staged by bulk copies, double-buffered; `gb` counts the batches this CTA
+// has staged so far (buffer and mbarrier phase), so a persistent CTA can walk
+// many lists.  Every thread of the CTA must call it.
+template <int KIND>
+__device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ray, uint32_t start, int lo, int hi,
+                                          const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
+                                          RayState& s, uint32_t* counters, float4* buf, uint64_t* bars,
+                                          uint32_t& gb)
+{
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int n = hi - lo;
+    const int nb = n > 0 ? (n + nthr - 1) / nthr : 0;
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
 
-    // batch b of this tile is the CTA's batch g = gb + b: buffer and barrier
-    // g & 1, phase parity (g >> 1) & 1
+    // batch b is the CTA's batch g = gb + b: buffer and barrier g & 1, phase
+    // parity (g >> 1) & 1
     auto issue = [&](int b) {
         const uint32_t g = gb + (uint32_t)b;
         const int first = b * nthr;
@@ -67,7 +111,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
         float4* dst = buf + (size_t)(g & 1) * nthr * kRecordF4;
         if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
         if (tid < cnt) {
-            const uint32_t slot = pval[start + first + tid];
+            const uint32_t slot = pval[start + lo + first + tid];
             bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
         }
     };
@@ -76,12 +120,11 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
         return mbar_wait_bounded(bars + (g & 1), (g >> 1) & 1, counters);
     };
 
+    // nothing to do for this CTA: no batch is staged
+    if (nb == 0 || __syncthreads_and(s.done)) return;
     bool ok = true;
-    int issued = 0;
-    if (nb > 0) {
-        issue(0);
-        issued = 1;
-    }
+    issue(0);
+    int issued = 1;
     for (int b = 0; b < nb; ++b) {
         if (b + 1 < nb) {
             issue(b + 1);
@@ -90,53 +133,77 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
         if (!wait(b)) ok = false;
         const float4* B = buf + (size_t)((gb + b) & 1) * nthr * kRecordF4;
         const int cnt = min(nthr, n - b * nthr);
+        const int pos0 = lo + b * nthr;  // list position of the batch's first record
         if (ok) {
-            for (int j = 0; j < cnt; ++j) {
+            // kIlp records per step: their evaluations are independent (the
+            // chains interleave), the compositing stays in list order
+            for (int j0 = 0; j0 < cnt; j0 += kIlp) {
                 if (__all_sync(0xffffffffu, s.done)) break;
                 if (s.done) continue;
-                const float4* Rj = B + j * kRecordF4;
-                Splat sp;
-                if (!splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, near_plane, columns, sp)) continue;
-                const float alpha = sp.alpha, z = sp.z;
-                const float Tn = s.T * (1.f - alpha);
-                if (Tn < kTMin) {
-                    s.done = true;
-                    s.walk = (uint32_t)(b * nthr + j + 1);
-                    continue;
+                float al[kIlp], zz[kIlp];
+                // j0 + e < nthr always (nthr and j0 are multiples of kIlp), so
+                // the reads stay inside the buffer; records past cnt are
+                // stale and masked out
+#pragma unroll
+                for (int e = 0; e < kIlp; ++e) {
+                    Splat sp;
+                    const bool hit = splat_eval<KIND>(B + (j0 + e) * kRecordF4, ray.rx, ray.ry, ray.d0, ray.d1,
+                                                      ray.d2, near_plane, columns, sp);
+                    al[e] = (hit && j0 + e < cnt) ? sp.alpha : 0.f;  // a hit has alpha >= 1/255
+                    zz[e] = sp.z;
                 }
-                const float w = alpha * s.T;
-                const float4 r3 = Rj[3];
-                s.f0 = fmaf(w, r3.y, s.f0);
-                if (KIND == GSR_SENSOR_PINHOLE) {
-                    s.f1 = fmaf(w, r3.z, s.f1);
-                    s.f2 = fmaf(w, r3.w, s.f2);
-                    const float4 r4 = Rj[4];
-                    s.n0 = fmaf(w, r4.x, s.n0);
-                    s.n1 = fmaf(w, r4.y, s.n1);
-                    s.n2 = fmaf(w, r4.z, s.n2);
+#pragma unroll
+                for (int e = 0; e < kIlp; ++e) {
+                    if (s.done || al[e] == 0.f) continue;
+                    const int j = j0 + e;
+                    const float alpha = al[e], z = zz[e];
+                    const float Tn = s.T * (1.f - alpha);
+                    if (Tn < kTMin) {
+                        s.done = true;
+                        s.walk = (uint32_t)(pos0 + j + 1);
+                        continue;
+                    }
+                    const float4* Rj = B + j * kRecordF4;
+                    const float w = alpha * s.T;
+                    const float4 r3 = Rj[3];
+                    s.f0 = fmaf(w, r3.y, s.f0);
+                    if (KIND == GSR_SENSOR_PINHOLE) {
+                        s.f1 = fmaf(w, r3.z, s.f1);
+                        s.f2 = fmaf(w, r3.w, s.f2);
+                        const float4 r4 = Rj[4];
+                        s.n0 = fmaf(w, r4.x, s.n0);
+                        s.n1 = fmaf(w, r4.y, s.n1);
+                        s.n2 = fmaf(w, r4.z, s.n2);
+                    }
+                    s.A += w;
+                    const float wz = w * z;
+                    s.B += wz;
+                    s.D = fmaf(wz, z, s.D);
+                    s.T = Tn;
+                    s.last = (uint32_t)(pos0 + j + 1);
                 }
-                s.A += w;
-                const float wz = w * z;
-                s.B += wz;
-                s.D = fmaf(wz, z, s.D);
-                s.T = Tn;
-                s.last = (uint32_t)(b * nthr + j + 1);
             }
         }
         // one block-uniform vote: a thread whose bounded wait gave up counts
         // as done (it composites nothing more; every later wait is bounded too)
         if (__syncthreads_and(s.done || !ok)) {
             // no copy may still be landing in shared memory when the CTA
-            // leaves or moves on to its next tile
+            // leaves or moves on
             if (b + 1 < nb) wait(b + 1);
             break;
         }
     }
     gb += (uint32_t)issued;
+    if (!ok) s.done = true;
+}
 
-    if (!inside) return;
+template <int KIND>
+__device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ray, const RayState& s,
+                                          const FrameOut& out)
+{
+    if (!ray.inside) return;
     const size_t HW = (size_t)sd.width * sd.height;
-    const size_t pix = (size_t)y * sd.width + x;
+    const size_t pix = (size_t)ray.y * sd.width + ray.x;
     if (KIND == GSR_SENSOR_PINHOLE) {
         if (out.color) {
             out.color[pix] = fmaf(s.T, sd.bg[0], s.f0);
@@ -162,51 +229,183 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int tile_w, int
     if (out.n_walk) out.n_walk[pix] = s.walk;
 }
 
+// ------------------------------------------------------------- split tiles
+// A tile whose list is longer than kSplitChunk is walked in chunks of
+// kSplitChunk positions.  Chunk 0 is walked like any tile (with each ray's
+// stop rule).  If rays are still alive after it, their state is stored
+// (the carry) and chunks 1..C are walked in parallel by other CTAs, each
+// from T = 1 with the same stop rule (a partial).  Exactness: with T_s the
+// transmittance entering chunk c and P_c the partial's transmittance, no
+// ray stops inside chunk c iff the partial did not stop and T_s P_c >= 1e-4
+// (T only decreases); its weights are then T_s times the partial's, so the
+// chunk merges as C += T_s C_c, T = T_s P_c.  A ray that stops inside chunk
+// c walks that chunk again from T_s, record by record.  The CTA that
+// finishes a tile's last chunk merges them in list order.
+struct SplitBufs {
+    const uint4* info;  // per tile: x = chunks after the first (0: not split), y = ray-record base, z = first item
+    uint2* state;       // per tile: x = 1 carry stored / 2 finished in chunk 0, y = chunks not yet walked
+    const uint2* items; // (tile, chunk)
+    float* rays;        // ray records, kRayWords words each
+};
+
+__device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, int R, int k)
+{
+    return sp.rays + ((size_t)base + (size_t)k * R) * kRayWords;
+}
+
+// Phase A: the tile's list (or its chunk 0).  Threads beyond the tile's rays
+// only help staging.
+template <int KIND>
+__device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile, uint32_t tile, const uint2 range,
+                                            const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
+                                            const FrameOut& out, uint32_t* counters, float4* buf, uint64_t* bars,
+                                            uint32_t& gb, const SplitBufs& sp)
+{
+    const TileRay ray = tile_ray<KIND>(sd, local_tile);
+    const int n = (int)(range.y - range.x);
+    RayState s;
+    ray_init(s, !ray.inside, (uint32_t)n);
+    const uint4 info = sp.info[tile];
+    const bool split = info.x > 0;
+    walk_list<KIND>(sd, ray, range.x, 0, split ? kSplitChunk : n, rec, pval, s, counters, buf, bars, gb);
+    if (split) {
+        const int R = sd.tile_w * sd.tile_h;
+        if (!__syncthreads_and(s.done)) {
+            if ((int)threadIdx.x < R) store_ray(ray_block(sp, info.y, R, 0), R, threadIdx.x, s);
+            if (threadIdx.x == 0) sp.state[tile] = make_uint2(1u, info.x);
+            return;
+        }
+        if (threadIdx.x == 0) sp.state[tile] = make_uint2(2u, info.x);
+    }
+    write_ray<KIND>(sd, ray, s, out);
+}
+
+// Phase B: chunk c of a split tile; the CTA that walks the tile's last
+// remaining chunk merges all of them and writes the tile's outputs.
+template <int KIND>
+__device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile, uint32_t tile, int c,
+                                             const uint2 range, const float4* __restrict__ rec,
+                                             const uint32_t* __restrict__ pval, const FrameOut& out,
+                                             uint32_t* counters, float4* buf, uint64_t* bars, uint32_t& gb,
+                                             const SplitBufs& sp, uint32_t* flag_s)
+{
+    const TileRay ray = tile_ray<KIND>(sd, local_tile);
+    const int n = (int)(range.y - range.x);
+    const int R = sd.tile_w * sd.tile_h;
+    const int r = threadIdx.x;
+    const uint4 info = sp.info[tile];
+    const uint32_t st = __ldcg(&sp.state[tile].x);
+    if (st == 1u) {
+        RayState carry, s;
+        bool done = true;
+        if (r < R) {
+            load_ray(ray_block(sp, info.y, R, 0), R, r, carry);
+            done = carry.done;
+        }
+        ray_init(s, done, (uint32_t)n);
+        walk_list<KIND>(sd, ray, range.x, c * kSplitChunk, min(n, (c + 1) * kSplitChunk), rec, pval, s, counters,
+                        buf, bars, gb);
+        if (r < R) store_ray(ray_block(sp, info.y, R, c), R, r, s);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *flag_s = atomicSub(&sp.state[tile].y, 1u) == 1u ? 1u : 0u;
+    __syncthreads();
+    if (!*flag_s || st != 1u) return;
+    __threadfence();
+
+    // merge chunks 1..C in list order onto the carry
+    RayState S;
+    ray_init(S, true, (uint32_t)n);
+    if (r < R) load_ray(ray_block(sp, info.y, R, 0), R, r, S);
+    const int C = (int)info.x;
+    for (int k = 1; k <= C; ++k) {
+        bool need = false;
+        if (!S.done) {
+            RayState p;
+            load_ray(ray_block(sp, info.y, R, k), R, r, p);
+            const float Tn = S.T * p.T;
+            if (!p.done && Tn >= kTMin) {
+                S.f0 = fmaf(S.T, p.f0, S.f0);
+                S.f1 = fmaf(S.T, p.f1, S.f1);
+                S.f2 = fmaf(S.T, p.f2, S.f2);
+                S.n0 = fmaf(S.T, p.n0, S.n0);
+                S.n1 = fmaf(S.T, p.n1, S.n1);
+                S.n2 = fmaf(S.T, p.n2, S.n2);
+                S.A = fmaf(S.T, p.A, S.A);
+                S.B = fmaf(S.T, p.B, S.B);
+                S.D = fmaf(S.T, p.D, S.D);
+                if (p.last) S.last = p.last;
+                S.T = Tn;
+            } else {
+                need = true;
+            }
+        }
+        if (__syncthreads_or(need)) {
+            // rays that stop inside chunk k walk it again from their state
+            const bool was = S.done;
+            S.done = S.done || !need;
+            walk_list<KIND>(sd, ray, range.x, k * kSplitChunk, min(n, (k + 1) * kSplitChunk), rec, pval, S,
+                            counters, buf, bars, gb);
+            if (!need) S.done = was;
+        }
+    }
+    write_ray<KIND>(sd, ray, S, out);
+}
+
+__device__ __forceinline__ void init_bars(uint64_t* bars)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        fence_mbar_init();
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, const float4* __restrict__ rec,
                                                 const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
-                                                FrameOut out, uint32_t* counters)
+                                                FrameOut out, uint32_t* counters, SplitBufs sp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
     const SensorDev& sd = tab.s[sensor];
-    if (threadIdx.x == 0) {
-        mbar_init(bars, 1);
-        mbar_init(bars + 1, 1);
-        fence_mbar_init();
-    }
+    init_bars(bars);
     __syncthreads();
     const int lt = blockIdx.x;
+    const uint32_t tile = (uint32_t)(sd.tile_base + lt);
     uint32_t gb = 0;
-    render_tile<KIND>(sd, sd.tile_w, sd.tile_h, lt, ranges[sd.tile_base + lt], rec, pval, out, counters, buf, bars,
-                      gb);
+    render_tile<KIND>(sd, lt, tile, ranges[tile], rec, pval, out, counters, buf, bars, gb, sp);
 }
 
-// Outputs of every sensor of a plan, for the whole-rig kernel.
+// Outputs of every sensor of a plan, for the whole-rig kernels.
 struct RigOut {
     FrameOut o[GSR_MAX_SENSORS];
 };
+
+__device__ __forceinline__ int sensor_of_tile(const SensorTable& tab, uint32_t tile)
+{
+    int s = 0;
+    while (s + 1 < tab.n && (int)tile >= tab.s[s + 1].tile_base) ++s;
+    return s;
+}
 
 // The whole rig in one persistent launch: each CTA takes the next tile from a
 // global work queue that lists every sensor's tiles longest list first, so
 // the long LiDAR and near-field tiles start early and the short ones fill in
 // behind them; the sensor kind is uniform per tile, so the branch is too.
-__global__ void __launch_bounds__(256) k_render_rig(SensorTable tab, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, 4) k_render_rig(SensorTable tab, const float4* __restrict__ rec,
                                                     const uint2* __restrict__ ranges,
                                                     const uint32_t* __restrict__ pval,
                                                     const uint32_t* __restrict__ order, RigOut outs,
-                                                    uint32_t* counters)
+                                                    uint32_t* counters, SplitBufs sp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
     __shared__ uint32_t item_s;
-    if (threadIdx.x == 0) {
-        mbar_init(bars, 1);
-        mbar_init(bars + 1, 1);
-        fence_mbar_init();
-    }
+    init_bars(bars);
     uint32_t gb = 0;
     const uint32_t T = (uint32_t)tab.total_tiles;
     for (;;) {
@@ -216,20 +415,109 @@ __global__ void __launch_bounds__(256) k_render_rig(SensorTable tab, const float
         const uint32_t item = item_s;
         if (item >= T) break;
         const uint32_t tile = order[item];
-        int s = 0;
-        while (s + 1 < tab.n && (int)tile >= tab.s[s + 1].tile_base) ++s;
+        const int s = sensor_of_tile(tab, tile);
         const SensorDev& sd = tab.s[s];
         const int lt = (int)tile - sd.tile_base;
         if (sd.kind == GSR_SENSOR_PINHOLE)
-            render_tile<GSR_SENSOR_PINHOLE>(sd, sd.tile_w, sd.tile_h, lt, ranges[tile], rec, pval, outs.o[s],
-                                            counters, buf, bars, gb);
+            render_tile<GSR_SENSOR_PINHOLE>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
+                                            gb, sp);
         else
-            render_tile<GSR_SENSOR_LIDAR>(sd, sd.tile_w, sd.tile_h, lt, ranges[tile], rec, pval, outs.o[s],
-                                          counters, buf, bars, gb);
+            render_tile<GSR_SENSOR_LIDAR>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
+                                          gb, sp);
+    }
+}
+
+// Phase B over the split items of every sensor (only < 0) or of one sensor.
+__global__ void __launch_bounds__(256, 4) k_render_split(SensorTable tab, const float4* __restrict__ rec,
+                                                      const uint2* __restrict__ ranges,
+                                                      const uint32_t* __restrict__ pval, RigOut outs,
+                                                      uint32_t* counters, SplitBufs sp, int only)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
+    __shared__ uint32_t item_s, flag_s;
+    init_bars(bars);
+    const uint32_t n_items = counters[C_NITEMS];
+    uint32_t begin = 0, end = n_items;
+    if (only >= 0) {
+        begin = sp.info[tab.s[only].tile_base].z;
+        if (only + 1 < tab.n) end = sp.info[tab.s[only + 1].tile_base].z;
+    }
+    uint32_t gb = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_s = begin + atomicAdd(&counters[C_SPLIT_QUEUE], 1u);
+        __syncthreads();
+        const uint32_t item = item_s;
+        if (item >= end) break;
+        const uint2 it = sp.items[item];
+        const uint32_t tile = it.x;
+        const int s = sensor_of_tile(tab, tile);
+        const SensorDev& sd = tab.s[s];
+        const int lt = (int)tile - sd.tile_base;
+        if (sd.kind == GSR_SENSOR_PINHOLE)
+            render_chunk<GSR_SENSOR_PINHOLE>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
+                                             buf, bars, gb, sp, &flag_s);
+        else
+            render_chunk<GSR_SENSOR_LIDAR>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
+                                           buf, bars, gb, sp, &flag_s);
     }
 }
 
 size_t render_smem_bytes(int threads) { return 128 + 2 * (size_t)threads * kRecordBytes; }
+
+SplitBufs split_bufs(const gsr_plan* p, const void* ws)
+{
+    SplitBufs sp;
+    sp.info = region<uint4>(p, ws, R_SPLIT_INFO);
+    sp.state = region<uint2>(p, ws, R_SPLIT_STATE);
+    sp.items = region<uint2>(p, ws, R_SPLIT_ITEMS);
+    sp.rays = region<float>(p, ws, R_SPLIT_RAYS);
+    return sp;
+}
+
+// Persistent CTAs for the rig and split kernels: resident CTAs per SM x SMs
+// of the current device, for CTAs of `threads` threads (32..256, a power of
+// two).
+static int persistent_grid(int which, int threads, cudaError_t& err)
+{
+    static int cached[64][2][4] = {};
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return 0;
+    const int ti = threads <= 32 ? 0 : threads <= 64 ? 1 : threads <= 128 ? 2 : 3;
+    if (dev >= 0 && dev < 64 && cached[dev][which][ti] > 0) return cached[dev][which][ti];
+    int sms = 0, per_sm = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return 0;
+    if (which == 0)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, threads,
+                                                            render_smem_bytes(threads));
+    else
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_split, threads,
+                                                            render_smem_bytes(threads));
+    if (err != cudaSuccess) return 0;
+    const int g = sms * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < 64) cached[dev][which][ti] = g;
+    return g;
+}
+
+// Phase B (the chunks of split tiles) of one sensor (only >= 0) or of all.
+static cudaError_t launch_split(const gsr_plan* p, const void* ws, const SensorTable& tab, const RigOut& ro,
+                                int threads, int only, cudaStream_t st)
+{
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
+    cudaError_t e = cudaMemsetAsync(counters + C_SPLIT_QUEUE, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid(1, threads, e);
+    if (e != cudaSuccess) return e;
+    const int pb = sort_result_buffer(tile_sort_passes(p));
+    k_render_split<<<grid, threads, render_smem_bytes(threads), st>>>(
+        tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
+        region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), ro, counters, split_bufs(p, ws), only);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st)
 {
@@ -243,31 +531,18 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
     const int pb = sort_result_buffer(tile_sort_passes(p));
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
+    const SplitBufs sp = split_bufs(p, ws);
     if (sd.kind == GSR_SENSOR_PINHOLE)
-        k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
+        k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters,
+                                                                   sp);
     else
-        k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters);
-    return cudaGetLastError();
-}
-
-// Persistent CTAs for the whole-rig kernel: resident CTAs per SM x SMs of the
-// current device, for CTAs of `threads` threads (32..256, a power of two).
-static int rig_grid(int threads, cudaError_t& err)
-{
-    static int cached[64][4] = {};
-    int dev = 0;
-    err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return 0;
-    const int ti = threads <= 32 ? 0 : threads <= 64 ? 1 : threads <= 128 ? 2 : 3;
-    if (dev >= 0 && dev < 64 && cached[dev][ti] > 0) return cached[dev][ti];
-    int sms = 0, per_sm = 0;
-    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (err != cudaSuccess) return 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, threads, render_smem_bytes(threads));
-    if (err != cudaSuccess) return 0;
-    const int g = sms * (per_sm > 0 ? per_sm : 1);
-    if (dev >= 0 && dev < 64) cached[dev][ti] = g;
-    return g;
+        k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters, sp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RigOut ro;
+    for (int i = 0; i < GSR_MAX_SENSORS; ++i) ro.o[i] = FrameOut{};
+    ro.o[sensor] = out;
+    return launch_split(p, ws, tab, ro, threads, sensor, st);
 }
 
 cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut* outs, cudaStream_t st)
@@ -281,14 +556,16 @@ cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut*
     // one CTA per tile in flight, as wide as the largest tile of the plan
     int threads = 32;
     for (int i = 0; i < p->n_sensors; ++i) threads = max(threads, tab.s[i].tile_w * tab.s[i].tile_h);
-    const int grid = rig_grid(threads, e);
+    const int grid = persistent_grid(0, threads, e);
     if (e != cudaSuccess) return e;
     const int pb = sort_result_buffer(tile_sort_passes(p));
     k_render_rig<<<grid, threads, render_smem_bytes(threads), st>>>(
         tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
         region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_A), ro,
-        counters);
-    return cudaGetLastError();
+        counters, split_bufs(p, ws));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_split(p, ws, tab, ro, threads, -1, st);
 }
 
 }  // namespace gsr

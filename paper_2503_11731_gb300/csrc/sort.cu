@@ -379,6 +379,50 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
     }
 }
 
+// Split plan of the frame (one CTA, tiles in id order): a tile whose list is
+// longer than kSplitChunk gets C = ceil(len / kSplitChunk) - 1 chunks after
+// its first and (C + 1) x rays ray records (its carry and one block per
+// chunk), while the running total fits the capacity; items (tile, c),
+// c = 1..C, are listed in tile order.  Deterministic: the outcome depends
+// only on the tile ranges.
+__global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint2* __restrict__ ranges,
+                                                     uint32_t n_tiles, unsigned long long cap_rays,
+                                                     unsigned long long cap_items, uint4* __restrict__ info,
+                                                     uint2* __restrict__ items, uint32_t* __restrict__ counters)
+{
+    __shared__ unsigned long long sm64[33];
+    __shared__ uint32_t sm32[33];
+    unsigned long long run_rays = 0;
+    uint32_t run_items = 0;
+    for (uint32_t t0 = 0; t0 < n_tiles; t0 += 1024) {
+        const uint32_t t = t0 + threadIdx.x;
+        uint32_t C = 0;
+        unsigned long long need = 0;
+        if (t < n_tiles) {
+            const uint32_t len = ranges[t].y - ranges[t].x;
+            if (len > (uint32_t)kSplitChunk) {
+                C = (len - 1) / kSplitChunk;
+                int s = 0;
+                while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
+                need = (unsigned long long)(C + 1) * (unsigned long long)(tab.s[s].tile_w * tab.s[s].tile_h);
+            }
+        }
+        unsigned long long tot_rays;
+        const unsigned long long off = run_rays + block_exclusive_scan<unsigned long long, 1024>(need, tot_rays, sm64);
+        if (C > 0 && off + need > cap_rays) C = 0;
+        uint32_t tot_items;
+        const uint32_t ioff = run_items + block_exclusive_scan<uint32_t, 1024>(C, tot_items, sm32);
+        if (C > 0 && (unsigned long long)ioff + C > cap_items) C = 0;  // cannot happen: items <= rays / 32
+        if (t < n_tiles) {
+            info[t] = make_uint4(C, C > 0 ? (uint32_t)off : 0u, ioff, 0u);
+            for (uint32_t c = 1; c <= C; ++c) items[ioff + c - 1] = make_uint2(t, c);
+        }
+        run_rays += tot_rays;
+        run_items += tot_items;
+    }
+    if (threadIdx.x == 0) counters[C_NITEMS] = run_items;
+}
+
 // Scheduling keys of the tiles: longest list first (ascending sort of
 // 0xffff - min(len, 0xffff)), for the persistent whole-rig compositing kernel.
 __global__ void __launch_bounds__(256) k_tile_keys(const uint2* __restrict__ ranges, uint32_t n_tiles,
@@ -469,6 +513,9 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     uint2* ranges = region<uint2>(p, ws, R_RANGES);
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p->tile_base[p->n_sensors], st);
     k_tile_ranges<<<4 * G, 256, 0, st>>>(pk[pb], counters + C_NDUP, ranges);
+    k_split_plan<<<1, 1024, 0, st>>>(tab, ranges, (uint32_t)p->tile_base[p->n_sensors], split_ray_capacity(p),
+                                     split_item_capacity(p), region<uint4>(p, ws, R_SPLIT_INFO),
+                                     region<uint2>(p, ws, R_SPLIT_ITEMS), counters);
     // 7. tile schedule for the whole-rig kernel (2 passes over 16-bit keys)
     const uint32_t T = (uint32_t)p->tile_base[p->n_sensors];
     uint32_t* tk[2] = {region<uint32_t>(p, ws, R_TILE_KEY_A), region<uint32_t>(p, ws, R_TILE_KEY_B)};

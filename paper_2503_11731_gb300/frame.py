@@ -102,11 +102,16 @@ class Renderer:
         return gsr.CameraOut(g("rgb"), g("depth"), g("normal"), g("alpha"), g("trans"), g("depth_acc"),
                              g("n_contrib"), g("n_walk"))
 
-    def preprocess(self, surfels: DeviceSurfels, objects=None, stream=None):
+    def preprocess(self, surfels: DeviceSurfels, objects=None, stream=None, first=None):
+        """Whole plan (first None), or surfels [first, first + n) of it (gsr_preprocess_part)."""
         obj = None
         if objects is not None:
             obj = gsr.Objects(int(objects.shape[0]), _ptr(objects))
-        gsr.preprocess(self.plan, surfels.struct(), obj, self.ws_ptr, self.ws_bytes, _stream_handle(stream))
+        if first is None:
+            gsr.preprocess(self.plan, surfels.struct(), obj, self.ws_ptr, self.ws_bytes, _stream_handle(stream))
+        else:
+            gsr.preprocess_part(self.plan, surfels.struct(), obj, first, self.ws_ptr, self.ws_bytes,
+                                _stream_handle(stream))
 
     def bin_sort(self, stream=None):
         gsr.bin_sort(self.plan, self.ws_ptr, self.ws_bytes, _stream_handle(stream))

@@ -103,6 +103,8 @@ SIGNATURES = {
     "gsr_workspace_size": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(ctypes.c_size_t)]),
     "gsr_preprocess": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(Surfels), ctypes.POINTER(Objects),
                                c_vp, ctypes.c_size_t, c_vp]),
+    "gsr_preprocess_part": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(Surfels), ctypes.POINTER(Objects),
+                                    c_i32, c_vp, ctypes.c_size_t, c_vp]),
     "gsr_bin_sort": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_vp]),
     "gsr_render_camera": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32,
                                   ctypes.POINTER(CameraOut), c_vp]),
@@ -224,6 +226,12 @@ def preprocess(plan, surfels: Surfels, objects, ws, ws_bytes, stream):
     _check(lib().gsr_preprocess(ctypes.byref(plan), ctypes.byref(surfels),
                                 ctypes.byref(objects) if objects is not None else None,
                                 ws, ws_bytes, stream), "gsr_preprocess")
+
+
+def preprocess_part(plan, surfels: Surfels, objects, first, ws, ws_bytes, stream):
+    _check(lib().gsr_preprocess_part(ctypes.byref(plan), ctypes.byref(surfels),
+                                     ctypes.byref(objects) if objects is not None else None,
+                                     int(first), ws, ws_bytes, stream), "gsr_preprocess_part")
 
 
 def bin_sort(plan, ws, ws_bytes, stream):

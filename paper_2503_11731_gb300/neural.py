@@ -92,3 +92,60 @@ class NeuralModel:
             m, v = self._adam[name]
             gsr.adam(_ptr(p), _ptr(self.grads[name]), _ptr(m), _ptr(v), p.numel(), rate, betas[0], betas[1], eps,
                      self.step_count, h)
+
+
+def capture(fn):
+    """Capture `fn()` (a sequence of calls into libgsr.so on the current
+    stream) into a CUDA graph on a side stream; replay with .replay()."""
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    return g
+
+
+class NeuralFrame:
+    """A frame of the learned scene: the decoded background (surfels
+    [0, A k) of the plan, SH degree 0) plus an explicit posed-object table
+    (surfels [A k, A k + n_obj), its own SH degree), rendered by one plan:
+
+        gsr_decode_anchors -> gsr_preprocess_part x 2 -> gsr_bin_sort -> gsr_render_rig
+
+    `origin` is the decode's view origin (a camera centre, or the rig centre
+    for a rig)."""
+
+    def __init__(self, model: NeuralModel, anchors: DeviceAnchors, renderer, objects: DeviceSurfels = None,
+                 poses=None, origin=(0.0, 0.0, 0.0), precision=gsr.DECODE_BF16_TENSOR):
+        self.model, self.anchors, self.r = model, anchors, renderer
+        self.objects, self.poses = objects, poses
+        self.origin = [float(v) for v in origin]
+        self.precision = precision
+        self.table = model.new_table(anchors)
+        self.n_bg = anchors.n * anchors.k
+        n_obj = 0 if objects is None else objects.n
+        if renderer.plan.n_surfels != self.n_bg + n_obj:
+            raise ValueError("plan surfel count must equal decoded + object surfels")
+
+    def decode(self, stream=None):
+        self.model.decode(self.anchors, self.origin, precision=self.precision, out=self.table, stream=stream)
+
+    def front(self, stream=None):
+        """Preprocess of both parts and the binning sort."""
+        self.r.preprocess(self.table, self.poses, stream, first=0)
+        if self.objects is not None:
+            self.r.preprocess(self.objects, self.poses, stream, first=self.n_bg)
+        self.r.bin_sort(stream)
+
+    def render(self, stream=None):
+        self.decode(stream)
+        self.front(stream)
+        self.r.composite_rig(stream)
+        return self.r.out
+
+    def graphs(self):
+        """Three replayable graphs of one frame: decode, preprocess + sort,
+        and the persistent whole-rig compositing launch."""
+        return {"decode": capture(self.decode), "front": capture(self.front),
+                "render_rig": self.r.graph(self.table, self.poses, stages=4)}

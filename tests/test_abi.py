@@ -73,6 +73,13 @@ def test_argument_errors(L):
     s.n = 10
     rc = L.gsr_preprocess(ctypes.byref(p), ctypes.byref(s), None, ctypes.cast(buf, ctypes.c_void_p), 1024, None)
     assert rc == gsr.ERR_WORKSPACE
+    # a part outside the plan's surfel range is rejected before any launch
+    # (the workspace address is never dereferenced on this path)
+    fake_ws, nbytes = ctypes.c_void_p(1 << 20), gsr.workspace_size(p)
+    for first, n in ((-1, 4), (7, 4), (0, 11)):
+        s.n = n
+        rc = L.gsr_preprocess_part(ctypes.byref(p), ctypes.byref(s), None, first, fake_ws, nbytes, None)
+        assert rc == gsr.ERR_INVALID_ARG, (first, n)
     rc = L.gsr_bin_sort(ctypes.byref(p), None, 0, None)
     assert rc == gsr.ERR_INVALID_ARG
     assert gsr.status_string(gsr.ERR_CAPACITY) == "GSR_ERR_CAPACITY"

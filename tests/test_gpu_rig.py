@@ -116,3 +116,44 @@ def test_frame_graph_replays_and_follows_in_place_updates(gpu_lib):
         for k in oa:
             assert torch.equal(oa[k], ob[k]), (i, k)
     g.close()
+
+
+def test_preprocess_parts_mix_sh_degrees(gpu_lib):
+    """A plan fed by two tables (SH-0 background, SH-3 posed objects) through
+    gsr_preprocess_part renders exactly like one table with the background's
+    SH padded by zero coefficients, and matches the oracle."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels
+    bg = synth.driving_scene(n=30_000, seed=91, x_range=(-20.0, 30.0), n_boxes=4, sh_degree=0)
+    poses = synth.object_poses(2, seed=92, x_range=(-5.0, 15.0))
+    objs = synth.object_asset(3000, seed=93)
+    objs.obj_id = np.arange(objs.n, dtype=np.int32) % 2
+    pad = np.zeros((bg.n, 16, 3), np.float32)
+    pad[:, :1] = bg.sh
+    bg3 = synth.Surfels(bg.pos, bg.log_scale, bg.quat, bg.opacity, pad, bg.intensity)
+    whole = bg3.concat(objs)
+    sensors = [synth.pinhole(320, 180, 170.0, (1.5, 0, 1.5), 0.0),
+               synth.spinning_lidar(32, 360, -25.0, 15.0, (0.0, 0.0, 1.8))]
+    P = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    r = _renderer(whole, sensors, [(16, 16), (8, 8)])
+    ref = [{k: v.clone() for k, v in o.items()} for o in r.render_rig(DeviceSurfels.from_host(whole), P)]
+    for o in r.out:
+        for v in o.values():
+            v.zero_()
+    d_obj, d_bg = DeviceSurfels.from_host(objs), DeviceSurfels.from_host(bg)
+    r.preprocess(d_obj, P, first=bg.n)   # parts in any order; first == 0 clears the status word
+    r.preprocess(d_bg, P, first=0)
+    r.bin_sort()
+    r.composite_rig()
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    for i, (oa, ob) in enumerate(zip(ref, r.out)):
+        for k in oa:
+            assert torch.equal(oa[k], ob[k]), (i, k)
+    s = sensors[0]
+    idx = np.random.default_rng(9).choice(s.width * s.height, 500, replace=False)
+    o = OR.render_pinhole(whole, s, pixels=idx, obj_pose=poses)
+    yy, xx = np.divmod(idx, s.width)
+    ok = o["flip"] <= 2e-5
+    rgb = np.moveaxis(r.out[0]["rgb"].cpu().numpy(), 0, -1)[yy, xx]
+    assert ok.mean() >= 0.97 and np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
+    assert (r.out[0]["n_contrib"].cpu().numpy()[yy, xx] > 0).mean() > 0.5

@@ -6,11 +6,13 @@ Workload (seeded, synthetic; the paper's driving datasets are not available):
   32x1024, el -30..10 deg); background = 300k anchors x 10 offsets decoded
   by the anchor MLP (BF16 tcgen05, FP32 accumulation; seeded untrained
   weights, view origin the rig centre) into 3M SH-0 surfels, plus 20
-  inserted 50k-surfel SH-3 objects placed by rigid SE(3) poses; camera tiles
-  16x16, LiDAR tiles 8x8.
+  inserted 50k-surfel SH-3 objects placed by rigid SE(3) poses.  Tile
+  shapes (per sensor kind) and the staging depth are chosen by
+  gsr_autotune before timing.
 A step renders the whole frame as three graph replays: gsr_decode_anchors;
 gsr_preprocess_part (background, objects) + gsr_bin_sort; gsr_render_rig
-(one persistent launch for all 8 sensors).  Inputs are resident in HBM and
+(one persistent launch for all 8 sensors, then one for the chunks of split
+tiles).  Inputs are resident in HBM and
 larger than L2 (anchors 91 MB + decoded table 168 MB + objects 260 MB), so
 no flush is needed.
 
@@ -226,13 +228,13 @@ def run_reference(args):
 # ----------------------------------------------------------------- GPU arm
 def bin_sort_launches(plan):
     """Kernel launches of one gsr_bin_sort: compaction 3, depth sort 4 x 3,
-    duplication 3, tile sort 3 per 8-bit pass, tile ranges 1, tile schedule
-    1 + 2 x 3."""
+    duplication 3, tile sort 3 per 8-bit pass, tile ranges 1, split plan 1,
+    tile schedule 1 + 2 x 3."""
     T = plan.tile_base[plan.n_sensors]
     bits = 1
     while (1 << bits) < T:
         bits += 1
-    return 3 + 12 + 3 + 3 * ((bits + 7) // 8) + 1 + 1 + 6
+    return 3 + 12 + 3 + 3 * ((bits + 7) // 8) + 1 + 1 + 1 + 6
 
 
 class Timer:
@@ -322,7 +324,7 @@ def run_gpu(args):
         scene, poses, sensors, wl_desc = explicit_workload()
         objs = anchors = None
     tiles = [parse(args.lidar_tile) if s.kind == "lidar" else parse(args.camera_tile) for s in sensors]
-    r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles,
+    r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles, batch_depth=args.batch_depth,
                  outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
@@ -338,17 +340,23 @@ def run_gpu(args):
         nf = NeuralFrame(model, da, r, d_obj, pose_t, origin, gsr.DECODE_BF16_TENSOR)
         nf.render()
         torch.cuda.synchronize()
+        tuned = r.autotune([nf.table, d_obj], pose_t) if args.autotune else None
+        nf.render()
+        torch.cuda.synchronize()
         G = nf.graphs()
         stages = [("decode", G["decode"].replay), ("pre_sort", G["front"].replay),
                   ("render_rig", lambda: G["render_rig"].launch(sh))]
-        n_launch = 1 + 2 + bin_sort_launches(r.plan) + 1
+        n_launch = 1 + 2 + bin_sort_launches(r.plan) + 2
         n_main = nf.n_bg + objs.n
     else:
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
+        tuned = r.autotune([dev], pose_t) if args.autotune else None
+        r.render_rig(dev, pose_t)
+        torch.cuda.synchronize()
         gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
         stages = [("pre_sort", lambda: gf.launch(sh)), ("render_rig", lambda: gr.launch(sh))]
-        n_launch = 1 + bin_sort_launches(r.plan) + 1
+        n_launch = 1 + bin_sort_launches(r.plan) + 2
         n_main = scene.n
     tm = Timer(stream, [k for k, _ in stages])
 
@@ -424,12 +432,17 @@ def run_gpu(args):
     if anchors is not None and args.compare:
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
+        ex_tuned = r.autotune([dev], pose_t) if args.autotune else None
+        r.render_rig(dev, pose_t)
+        torch.cuda.synchronize()
         gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
         k = max(3, args.steps // 2)
         for _ in range(2):
             gf.launch(sh)
             gr.launch(sh)
         batched = timed(stream, k, lambda: (gf.launch(sh), gr.launch(sh)))
+        ex_front = timed(stream, k, lambda: gf.launch(sh))
+        ex_render = timed(stream, k, lambda: gr.launch(sh))
         ex_nvis, ex_pairs = check_status(r)
         ex_sensors = sensor_stats(r, sensors, scene.n)
         ex_cam, ex_lid = walks(r, sensors)
@@ -441,6 +454,10 @@ def run_gpu(args):
         nf.precision = gsr.DECODE_BF16_TENSOR
         compare = {
             "explicit_batched_ms": batched,
+            "explicit_batched_stage_ms": {"pre_sort": ex_front, "render_rig": ex_render},
+            "explicit_tiling": {"camera_tile": r.tile_of("pinhole"), "lidar_tile": r.tile_of("lidar"),
+                                "batch_depth": r.plan.tiling.batch_depth,
+                                "autotune_best_ms": None if ex_tuned is None else ex_tuned["best_ms"]},
             "explicit_per_sensor_ms": per_sensor_ms,
             "explicit_table": f"{scene.n} SH-3 surfels (the background the anchors were grouped from + objects)",
             "explicit_pairs": ex_pairs, "explicit_visible_records": ex_nvis,
@@ -491,7 +508,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (decode bf16 tcgen05, fp32 accumulation)" if anchors is not None
         else "f32", "data": "synthetic (seeded driving scene + rig; untrained seeded anchor MLP)",
-        "config": {"workload": wl_desc, "tiles": [f"{t[0]}x{t[1]}" for t in tiles],
+        "config": {"workload": wl_desc,
+                   "tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
+                   "batch_depth": r.plan.tiling.batch_depth or "CTA width",
                    "surfels": n_main, "rays_per_frame": total_rays, "visible_records": nvis,
                    "tile_pairs": npairs, "l2": "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},
@@ -503,6 +522,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": n_launch * args.steps,
         "compare": compare,
+        "autotune": tuned,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -520,6 +540,9 @@ def main():
     ap.add_argument("--workload", default="rig", choices=["rig", "explicit"],
                     help="rig = the 6-camera + 2-LiDAR frame (the benchmark); explicit = a smaller "
                          "1-camera + 1-LiDAR frame used for profiler captures")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep --camera-tile / --lidar-tile / --batch-depth instead of gsr_autotune's choice")
+    ap.add_argument("--batch-depth", type=int, default=0)
     ap.add_argument("--camera-tile", default="16x16")
     ap.add_argument("--lidar-tile", default="8x8")
     ap.add_argument("--sample-rays", type=int, default=16)

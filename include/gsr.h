@@ -109,9 +109,13 @@ typedef struct {
 } gsr_sensor;
 
 /* Default screen tiling of a plan's sensors (tile_w, tile_h powers of two,
- * tile_w * tile_h in {32,64,128,256}); a sensor may override it. */
+ * tile_w * tile_h in {32,64,128,256}); a sensor may override it.
+ * batch_depth = records staged in shared memory per step of a tile's walk
+ * (double-buffered, 80 bytes each): 0 = the compositing CTA's thread count,
+ * else one of 32, 64, 128, 256, 512.  It changes speed only, never results. */
 typedef struct {
     int32_t tile_w, tile_h;
+    int32_t batch_depth;
 } gsr_tiling;
 
 /*
@@ -464,6 +468,66 @@ gsr_status gsr_frame_graph_destroy(gsr_frame_graph* graph);
 gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t* device_status,
                            int64_t* n_visible, int64_t* n_pairs, void* stream);
 
+/* ------------------------------------------------------------- autotune */
+
+/*
+ * Search space of gsr_autotune (host memory).  Every pinhole sensor takes
+ * the same camera tile, every LiDAR the same LiDAR tile; n_* = 0 keeps the
+ * plan's choice.  Tiles obey gsr_tiling's rule; batch depths are 0 or
+ * 32..512 as in gsr_tiling.  Each candidate renders `warmup` untimed and
+ * `reps` timed frames (reps >= 1).
+ */
+#define GSR_AUTOTUNE_MAX 8
+typedef struct {
+    int32_t n_camera_tiles;
+    int32_t camera_tiles[GSR_AUTOTUNE_MAX][2];
+    int32_t n_lidar_tiles;
+    int32_t lidar_tiles[GSR_AUTOTUNE_MAX][2];
+    int32_t n_batch_depths;
+    int32_t batch_depths[GSR_AUTOTUNE_MAX];
+    int32_t warmup, reps;
+} gsr_autotune_space;
+
+/* One measured candidate: ms = mean frame time (preprocess + bin_sort +
+ * render_rig), or a negative value when the candidate's frame failed (e.g.
+ * the pair capacity of its plan overflowed). */
+typedef struct {
+    int32_t camera_tile[2];
+    int32_t lidar_tile[2];
+    int32_t batch_depth;
+    float ms;
+} gsr_autotune_trial;
+
+typedef struct {
+    gsr_plan plan;        /* the input plan re-initialised with the fastest tiling */
+    float best_ms;
+    int32_t n_tried;
+    gsr_autotune_trial tried[3 * GSR_AUTOTUNE_MAX + 1];
+} gsr_autotune_result;
+
+/* Workspace bytes gsr_autotune needs: the largest over the candidates
+ * (host only). */
+gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gsr_autotune_space* space, size_t* bytes);
+
+/*
+ * Autotuner of the batched rig frame (the paper prescribes none; tile shape
+ * and staging depth are this implementation's free parameters).  Coordinate
+ * descent from the plan's tiling: the camera tile over its candidates, then
+ * the LiDAR tile, then the batch depth, each candidate timed with CUDA
+ * events over whole frames of the given surfels: `parts` (n_parts tables,
+ * consecutive in the plan from surfel 0, as gsr_preprocess_part) and
+ * `objects` (may be NULL), rendered into camera_outs / lidar_outs (as
+ * gsr_render_rig).  Synchronous: it waits for `stream` and leaves the last
+ * candidate's frame in the outputs.  Results never depend on the choice
+ * (only lists and staging do).  Errors: GSR_ERR_INVALID_ARG,
+ * GSR_ERR_WORKSPACE (workspace smaller than gsr_autotune_workspace_size),
+ * GSR_ERR_CUDA.
+ */
+gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* parts, int32_t n_parts,
+                        const gsr_objects* objects, const gsr_autotune_space* space, void* workspace,
+                        size_t workspace_bytes, const gsr_camera_out* camera_outs,
+                        const gsr_lidar_out* lidar_outs, gsr_autotune_result* result, void* stream);
+
 /* Readable name of a status code (static storage). */
 const char* gsr_status_string(gsr_status s);
 
@@ -473,7 +537,10 @@ const char* gsr_last_cuda_error(void);
 /*
  * sizeof of the ABI structs, for bindings that mirror them (host only):
  * which = 0 gsr_plan, 1 gsr_sensor, 2 gsr_surfels, 3 gsr_objects,
- * 4 gsr_camera_out, 5 gsr_lidar_out, 6 gsr_tiling.  Returns 0 for other values.
+ * 4 gsr_camera_out, 5 gsr_lidar_out, 6 gsr_tiling, 7 gsr_camera_grad,
+ * 8 gsr_surfel_grads, 9 gsr_loss_weights, 10 gsr_anchors, 11 gsr_mlp,
+ * 12 gsr_mlp_grads, 13 gsr_surfel_table, 14 gsr_autotune_space,
+ * 15 gsr_autotune_result.  Returns 0 for other values.
  */
 size_t gsr_struct_size(int32_t which);
 

@@ -44,6 +44,7 @@ SensorTable make_sensor_table(const gsr_plan* p)
     t.tile_w = p->tiling.tile_w;
     t.tile_h = p->tiling.tile_h;
     t.total_tiles = p->tile_base[p->n_sensors];
+    t.batch = p->tiling.batch_depth;
     const double deg = 3.14159265358979323846 / 180.0;
     for (int i = 0; i < p->n_sensors; ++i) {
         const gsr_sensor& s = p->sensors[i];
@@ -98,6 +99,8 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     if (!plan || !sensors || !tiling) return GSR_ERR_INVALID_ARG;
     if (n_surfels < 0 || n_sensors < 1 || n_sensors > GSR_MAX_SENSORS) return GSR_ERR_INVALID_ARG;
     if (!tile_ok(tiling->tile_w, tiling->tile_h)) return GSR_ERR_UNSUPPORTED;
+    const int bd = tiling->batch_depth;
+    if (!(bd == 0 || bd == 32 || bd == 64 || bd == 128 || bd == 256 || bd == 512)) return GSR_ERR_UNSUPPORTED;
     std::memset(plan, 0, sizeof(*plan));
     plan->n_surfels = n_surfels;
     plan->n_sensors = n_sensors;
@@ -343,6 +346,8 @@ extern "C" size_t gsr_struct_size(int32_t which)
     case 11: return sizeof(gsr_mlp);
     case 12: return sizeof(gsr_mlp_grads);
     case 13: return sizeof(gsr_surfel_table);
+    case 14: return sizeof(gsr_autotune_space);
+    case 15: return sizeof(gsr_autotune_result);
     default: return 0;
     }
 }

@@ -1,0 +1,218 @@
+// autotune.cu -- gsr_autotune: tile shape and staging depth of the rig frame.
+//
+// The free parameters of the tiled renderer are the screen tile of each
+// sensor kind and the number of records staged per step of a tile's walk.
+// Small tiles shorten each ray's list (fewer evaluations) but duplicate
+// more surfel/tile pairs (more sorting); the staging depth trades shared
+// memory (occupancy) against barrier and copy overhead.  Neither changes a
+// result.  The tuner times whole frames (preprocess + bin_sort +
+// render_rig) with CUDA events and descends one coordinate at a time.
+#include <cstring>
+#include <vector>
+
+#include "gsr_internal.cuh"
+
+namespace gsr {
+gsr_status cuda_status(cudaError_t e);
+}
+
+namespace {
+
+struct Candidate {
+    int cam[2];
+    int lid[2];
+    int bd;
+};
+
+bool same(const Candidate& a, const Candidate& b)
+{
+    return a.cam[0] == b.cam[0] && a.cam[1] == b.cam[1] && a.lid[0] == b.lid[0] && a.lid[1] == b.lid[1] &&
+           a.bd == b.bd;
+}
+
+// The plan of a candidate: the input plan's sensors and capacity with every
+// pinhole sensor on cand.cam, every LiDAR on cand.lid and cand.bd staged.
+gsr_status candidate_plan(const gsr_plan* base, const Candidate& c, gsr_plan* out)
+{
+    gsr_sensor sensors[GSR_MAX_SENSORS];
+    for (int i = 0; i < base->n_sensors; ++i) {
+        sensors[i] = base->sensors[i];
+        const int* t = sensors[i].kind == GSR_SENSOR_LIDAR ? c.lid : c.cam;
+        sensors[i].tile_w = t[0];
+        sensors[i].tile_h = t[1];
+    }
+    gsr_tiling tiling = base->tiling;
+    tiling.batch_depth = c.bd;
+    return gsr_plan_init(out, base->n_surfels, sensors, base->n_sensors, &tiling, base->max_dup);
+}
+
+// Tile of the first sensor of a kind in the plan (both kinds default to the
+// plan's tiling when absent).
+void plan_tile(const gsr_plan* p, int kind, int t[2])
+{
+    t[0] = p->tiling.tile_w;
+    t[1] = p->tiling.tile_h;
+    for (int i = 0; i < p->n_sensors; ++i)
+        if (p->sensors[i].kind == kind) {
+            t[0] = p->sensors[i].tile_w;
+            t[1] = p->sensors[i].tile_h;
+            return;
+        }
+}
+
+std::vector<Candidate> all_candidates(const gsr_plan* plan, const gsr_autotune_space* sp, Candidate start)
+{
+    std::vector<Candidate> v{start};
+    for (int i = 0; i < sp->n_camera_tiles; ++i) {
+        Candidate c = start;
+        c.cam[0] = sp->camera_tiles[i][0];
+        c.cam[1] = sp->camera_tiles[i][1];
+        for (int j = 0; j < sp->n_lidar_tiles || j == 0; ++j) {
+            if (sp->n_lidar_tiles) {
+                c.lid[0] = sp->lidar_tiles[j][0];
+                c.lid[1] = sp->lidar_tiles[j][1];
+            }
+            for (int k = 0; k < sp->n_batch_depths || k == 0; ++k) {
+                if (sp->n_batch_depths) c.bd = sp->batch_depths[k];
+                v.push_back(c);
+            }
+        }
+    }
+    (void)plan;
+    return v;
+}
+
+bool space_ok(const gsr_autotune_space* sp)
+{
+    if (!sp || sp->reps < 1 || sp->warmup < 0) return false;
+    if (sp->n_camera_tiles < 0 || sp->n_camera_tiles > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_lidar_tiles < 0 || sp->n_lidar_tiles > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_batch_depths < 0 || sp->n_batch_depths > GSR_AUTOTUNE_MAX) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gsr_autotune_space* space,
+                                                  size_t* bytes)
+{
+    if (!plan || !bytes || !space_ok(space)) return GSR_ERR_INVALID_ARG;
+    Candidate start;
+    plan_tile(plan, GSR_SENSOR_PINHOLE, start.cam);
+    plan_tile(plan, GSR_SENSOR_LIDAR, start.lid);
+    start.bd = plan->tiling.batch_depth;
+    // the workspace depends on the tiles only; bound it over every tile pair
+    size_t best = 0;
+    for (const Candidate& c : all_candidates(plan, space, start)) {
+        gsr_plan p;
+        const gsr_status st = candidate_plan(plan, c, &p);
+        if (st != GSR_OK) return st;
+        if (p.workspace_bytes > best) best = (size_t)p.workspace_bytes;
+    }
+    *bytes = best;
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* parts, int32_t n_parts,
+                                   const gsr_objects* objects, const gsr_autotune_space* space, void* workspace,
+                                   size_t workspace_bytes, const gsr_camera_out* camera_outs,
+                                   const gsr_lidar_out* lidar_outs, gsr_autotune_result* result, void* stream)
+{
+    if (!plan || !parts || n_parts < 1 || !result || !space_ok(space)) return GSR_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int i = 0; i < n_parts; ++i) total += parts[i].n;
+    if (total != plan->n_surfels) return GSR_ERR_INVALID_ARG;
+    size_t need = 0;
+    gsr_status st = gsr_autotune_workspace_size(plan, space, &need);
+    if (st != GSR_OK) return st;
+    if (!workspace || workspace_bytes < need) return GSR_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::memset(result, 0, sizeof(*result));
+
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return gsr::cuda_status(cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return gsr::cuda_status(cudaGetLastError());
+    }
+    auto frame = [&](const gsr_plan* p) -> gsr_status {
+        int first = 0;
+        for (int i = 0; i < n_parts; ++i) {
+            gsr_status r = gsr_preprocess_part(p, &parts[i], objects, first, workspace, workspace_bytes, stream);
+            if (r != GSR_OK) return r;
+            first += parts[i].n;
+        }
+        gsr_status r = gsr_bin_sort(p, workspace, workspace_bytes, stream);
+        if (r != GSR_OK) return r;
+        return gsr_render_rig(p, workspace, workspace_bytes, camera_outs, lidar_outs, stream);
+    };
+    // mean frame ms of a candidate, or -1 if its frame failed on the device
+    auto measure = [&](const Candidate& c, float& ms) -> gsr_status {
+        gsr_plan p;
+        gsr_status r = candidate_plan(plan, c, &p);
+        if (r != GSR_OK) return r;
+        for (int i = 0; i < space->warmup; ++i)
+            if ((r = frame(&p)) != GSR_OK) return r;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return gsr::cuda_status(cudaGetLastError());
+        for (int i = 0; i < space->reps; ++i)
+            if ((r = frame(&p)) != GSR_OK) return r;
+        if (cudaEventRecord(e1, s) != cudaSuccess) return gsr::cuda_status(cudaGetLastError());
+        int32_t dev_status = 0;
+        if ((r = gsr_read_status(&p, workspace, &dev_status, nullptr, nullptr, stream)) != GSR_OK) return r;
+        float t = 0.f;
+        const cudaError_t ce = cudaEventElapsedTime(&t, e0, e1);
+        if (ce != cudaSuccess) return gsr::cuda_status(ce);
+        ms = dev_status == GSR_OK ? t / space->reps : -1.f;
+        return GSR_OK;
+    };
+
+    Candidate best;
+    plan_tile(plan, GSR_SENSOR_PINHOLE, best.cam);
+    plan_tile(plan, GSR_SENSOR_LIDAR, best.lid);
+    best.bd = plan->tiling.batch_depth;
+    float best_ms = -1.f;
+    std::vector<std::pair<Candidate, float>> seen;
+    auto visit = [&](const Candidate& c) -> gsr_status {
+        for (auto& kv : seen)
+            if (same(kv.first, c)) return GSR_OK;
+        float ms = -1.f;
+        gsr_status r = measure(c, ms);
+        if (r != GSR_OK) return r;
+        seen.push_back({c, ms});
+        if (result->n_tried < (int)(sizeof(result->tried) / sizeof(result->tried[0]))) {
+            gsr_autotune_trial& t = result->tried[result->n_tried++];
+            t.camera_tile[0] = c.cam[0]; t.camera_tile[1] = c.cam[1];
+            t.lidar_tile[0] = c.lid[0]; t.lidar_tile[1] = c.lid[1];
+            t.batch_depth = c.bd;
+            t.ms = ms;
+        }
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = c;
+        }
+        return GSR_OK;
+    };
+    gsr_status r = visit(best);
+    for (int i = 0; r == GSR_OK && i < space->n_camera_tiles; ++i) {
+        Candidate c = best;
+        c.cam[0] = space->camera_tiles[i][0];
+        c.cam[1] = space->camera_tiles[i][1];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_lidar_tiles; ++i) {
+        Candidate c = best;
+        c.lid[0] = space->lidar_tiles[i][0];
+        c.lid[1] = space->lidar_tiles[i][1];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_batch_depths; ++i) {
+        Candidate c = best;
+        c.bd = space->batch_depths[i];
+        r = visit(c);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != GSR_OK) return r;
+    result->best_ms = best_ms;
+    return candidate_plan(plan, best, &result->plan);
+}

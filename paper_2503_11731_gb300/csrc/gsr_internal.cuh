@@ -91,6 +91,7 @@ struct SensorTable {
     int n;
     int tile_w, tile_h;
     int total_tiles;
+    int batch;  // records staged per step of a walk; 0 = the CTA's thread count
     SensorDev s[GSR_MAX_SENSORS];
 };
 
@@ -119,10 +120,11 @@ SensorTable make_sensor_table(const gsr_plan* p);
 inline int sort_result_buffer(int passes) { return passes & 1; }
 
 // Capacity of the split-tile ray records (a fixed share of the pair
-// capacity) and of the split items (each item holds >= 32 ray records).
+// capacity: one 52-byte record per 16 pairs) and of the split items (each
+// item holds >= 32 ray records).  Tiles beyond it are walked unsplit.
 inline uint64_t split_ray_capacity(const gsr_plan* p)
 {
-    const uint64_t c = (uint64_t)p->max_dup / 64;
+    const uint64_t c = (uint64_t)p->max_dup / 16;
     return c < 65536 ? 65536 : c;
 }
 inline uint64_t split_item_capacity(const gsr_plan* p) { return split_ray_capacity(p) / 32 + 1; }

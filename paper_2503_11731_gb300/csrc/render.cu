@@ -18,6 +18,12 @@ namespace gsr {
 
 constexpr int kIlp = 4;  // records evaluated per step of a ray's walk
 
+// Resident CTAs per SM the persistent compositing kernels are compiled for
+// (256 threads each; 4 caps registers at 64 per thread).
+#ifndef GSR_RIG_MIN_CTAS
+#define GSR_RIG_MIN_CTAS 4
+#endif
+
 // Per-ray compositing state.  Stored ray records (split tiles, below) keep
 // its 13 fields in this order, one word each.
 struct RayState {
@@ -84,20 +90,20 @@ __device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, int local_tile)
 }
 
 // Walk list positions [lo, hi) of a tile (list starting at `start`) with the
-// whole CTA, continuing each ray's state.  Batches of blockDim.x records are
-// staged by bulk copies, double-buffered; `gb` counts the batches this CTA
+// whole CTA, continuing each ray's state.  Batches of D records (a multiple
+// of kIlp) are staged by bulk copies, double-buffered; `gb` counts the batches this CTA
 // has staged so far (buffer and mbarrier phase), so a persistent CTA can walk
 // many lists.  Every thread of the CTA must call it.
 template <int KIND>
 __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ray, uint32_t start, int lo, int hi,
                                           const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
                                           RayState& s, uint32_t* counters, float4* buf, uint64_t* bars,
-                                          uint32_t& gb)
+                                          uint32_t& gb, int D)
 {
     const int nthr = blockDim.x;
     const int tid = threadIdx.x;
     const int n = hi - lo;
-    const int nb = n > 0 ? (n + nthr - 1) / nthr : 0;
+    const int nb = n > 0 ? (n + D - 1) / D : 0;
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
 
@@ -105,14 +111,14 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
     // parity (g >> 1) & 1
     auto issue = [&](int b) {
         const uint32_t g = gb + (uint32_t)b;
-        const int first = b * nthr;
-        const int cnt = min(nthr, n - first);
+        const int first = b * D;
+        const int cnt = min(D, n - first);
         uint64_t* bar = bars + (g & 1);
-        float4* dst = buf + (size_t)(g & 1) * nthr * kRecordF4;
+        float4* dst = buf + (size_t)(g & 1) * D * kRecordF4;
         if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
-        if (tid < cnt) {
-            const uint32_t slot = pval[start + lo + first + tid];
-            bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
+        for (int i = tid; i < cnt; i += nthr) {
+            const uint32_t slot = pval[start + lo + first + i];
+            bulk_g2s(dst + i * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
         }
     };
     auto wait = [&](int b) {
@@ -131,9 +137,9 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
             issued = b + 2;
         }
         if (!wait(b)) ok = false;
-        const float4* B = buf + (size_t)((gb + b) & 1) * nthr * kRecordF4;
-        const int cnt = min(nthr, n - b * nthr);
-        const int pos0 = lo + b * nthr;  // list position of the batch's first record
+        const float4* B = buf + (size_t)((gb + b) & 1) * D * kRecordF4;
+        const int cnt = min(D, n - b * D);
+        const int pos0 = lo + b * D;  // list position of the batch's first record
         if (ok) {
             // kIlp records per step: their evaluations are independent (the
             // chains interleave), the compositing stays in list order
@@ -141,7 +147,7 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                 if (__all_sync(0xffffffffu, s.done)) break;
                 if (s.done) continue;
                 float al[kIlp], zz[kIlp];
-                // j0 + e < nthr always (nthr and j0 are multiples of kIlp), so
+                // j0 + e < D always (D and j0 are multiples of kIlp), so
                 // the reads stay inside the buffer; records past cnt are
                 // stale and masked out
 #pragma unroll
@@ -259,7 +265,7 @@ template <int KIND>
 __device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile, uint32_t tile, const uint2 range,
                                             const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
                                             const FrameOut& out, uint32_t* counters, float4* buf, uint64_t* bars,
-                                            uint32_t& gb, const SplitBufs& sp)
+                                            uint32_t& gb, const SplitBufs& sp, int D)
 {
     const TileRay ray = tile_ray<KIND>(sd, local_tile);
     const int n = (int)(range.y - range.x);
@@ -267,7 +273,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile,
     ray_init(s, !ray.inside, (uint32_t)n);
     const uint4 info = sp.info[tile];
     const bool split = info.x > 0;
-    walk_list<KIND>(sd, ray, range.x, 0, split ? kSplitChunk : n, rec, pval, s, counters, buf, bars, gb);
+    walk_list<KIND>(sd, ray, range.x, 0, split ? kSplitChunk : n, rec, pval, s, counters, buf, bars, gb, D);
     if (split) {
         const int R = sd.tile_w * sd.tile_h;
         if (!__syncthreads_and(s.done)) {
@@ -287,7 +293,7 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
                                              const uint2 range, const float4* __restrict__ rec,
                                              const uint32_t* __restrict__ pval, const FrameOut& out,
                                              uint32_t* counters, float4* buf, uint64_t* bars, uint32_t& gb,
-                                             const SplitBufs& sp, uint32_t* flag_s)
+                                             const SplitBufs& sp, uint32_t* flag_s, int D)
 {
     const TileRay ray = tile_ray<KIND>(sd, local_tile);
     const int n = (int)(range.y - range.x);
@@ -304,7 +310,7 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
         }
         ray_init(s, done, (uint32_t)n);
         walk_list<KIND>(sd, ray, range.x, c * kSplitChunk, min(n, (c + 1) * kSplitChunk), rec, pval, s, counters,
-                        buf, bars, gb);
+                        buf, bars, gb, D);
         if (r < R) store_ray(ray_block(sp, info.y, R, c), R, r, s);
         __threadfence();
     }
@@ -346,7 +352,7 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
             const bool was = S.done;
             S.done = S.done || !need;
             walk_list<KIND>(sd, ray, range.x, k * kSplitChunk, min(n, (k + 1) * kSplitChunk), rec, pval, S,
-                            counters, buf, bars, gb);
+                            counters, buf, bars, gb, D);
             if (!need) S.done = was;
         }
     }
@@ -376,7 +382,8 @@ __global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, con
     const int lt = blockIdx.x;
     const uint32_t tile = (uint32_t)(sd.tile_base + lt);
     uint32_t gb = 0;
-    render_tile<KIND>(sd, lt, tile, ranges[tile], rec, pval, out, counters, buf, bars, gb, sp);
+    render_tile<KIND>(sd, lt, tile, ranges[tile], rec, pval, out, counters, buf, bars, gb, sp,
+                      tab.batch > 0 ? tab.batch : (int)blockDim.x);
 }
 
 // Outputs of every sensor of a plan, for the whole-rig kernels.
@@ -395,7 +402,7 @@ __device__ __forceinline__ int sensor_of_tile(const SensorTable& tab, uint32_t t
 // global work queue that lists every sensor's tiles longest list first, so
 // the long LiDAR and near-field tiles start early and the short ones fill in
 // behind them; the sensor kind is uniform per tile, so the branch is too.
-__global__ void __launch_bounds__(256, 4) k_render_rig(SensorTable tab, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_rig(SensorTable tab, const float4* __restrict__ rec,
                                                     const uint2* __restrict__ ranges,
                                                     const uint32_t* __restrict__ pval,
                                                     const uint32_t* __restrict__ order, RigOut outs,
@@ -407,6 +414,7 @@ __global__ void __launch_bounds__(256, 4) k_render_rig(SensorTable tab, const fl
     __shared__ uint32_t item_s;
     init_bars(bars);
     uint32_t gb = 0;
+    const int D = tab.batch > 0 ? tab.batch : (int)blockDim.x;
     const uint32_t T = (uint32_t)tab.total_tiles;
     for (;;) {
         __syncthreads();  // the previous item (and the barrier init) is done with
@@ -420,15 +428,15 @@ __global__ void __launch_bounds__(256, 4) k_render_rig(SensorTable tab, const fl
         const int lt = (int)tile - sd.tile_base;
         if (sd.kind == GSR_SENSOR_PINHOLE)
             render_tile<GSR_SENSOR_PINHOLE>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
-                                            gb, sp);
+                                            gb, sp, D);
         else
             render_tile<GSR_SENSOR_LIDAR>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
-                                          gb, sp);
+                                          gb, sp, D);
     }
 }
 
 // Phase B over the split items of every sensor (only < 0) or of one sensor.
-__global__ void __launch_bounds__(256, 4) k_render_split(SensorTable tab, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTable tab, const float4* __restrict__ rec,
                                                       const uint2* __restrict__ ranges,
                                                       const uint32_t* __restrict__ pval, RigOut outs,
                                                       uint32_t* counters, SplitBufs sp, int only)
@@ -445,6 +453,7 @@ __global__ void __launch_bounds__(256, 4) k_render_split(SensorTable tab, const 
         if (only + 1 < tab.n) end = sp.info[tab.s[only + 1].tile_base].z;
     }
     uint32_t gb = 0;
+    const int D = tab.batch > 0 ? tab.batch : (int)blockDim.x;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item_s = begin + atomicAdd(&counters[C_SPLIT_QUEUE], 1u);
@@ -458,14 +467,25 @@ __global__ void __launch_bounds__(256, 4) k_render_split(SensorTable tab, const 
         const int lt = (int)tile - sd.tile_base;
         if (sd.kind == GSR_SENSOR_PINHOLE)
             render_chunk<GSR_SENSOR_PINHOLE>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
-                                             buf, bars, gb, sp, &flag_s);
+                                             buf, bars, gb, sp, &flag_s, D);
         else
             render_chunk<GSR_SENSOR_LIDAR>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
-                                           buf, bars, gb, sp, &flag_s);
+                                           buf, bars, gb, sp, &flag_s, D);
     }
 }
 
-size_t render_smem_bytes(int threads) { return 128 + 2 * (size_t)threads * kRecordBytes; }
+// Dynamic shared memory of a compositing CTA staging D records per batch.
+size_t render_smem_bytes(int D) { return 128 + 2 * (size_t)D * kRecordBytes; }
+
+static int batch_of(const SensorTable& tab, int threads) { return tab.batch > 0 ? tab.batch : threads; }
+
+// Opt in to more than 48 KB of dynamic shared memory where a batch needs it.
+template <class K>
+static cudaError_t smem_attr(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 SplitBufs split_bufs(const gsr_plan* p, const void* ws)
 {
@@ -479,27 +499,27 @@ SplitBufs split_bufs(const gsr_plan* p, const void* ws)
 
 // Persistent CTAs for the rig and split kernels: resident CTAs per SM x SMs
 // of the current device, for CTAs of `threads` threads (32..256, a power of
-// two).
-static int persistent_grid(int which, int threads, cudaError_t& err)
+// two) with `smem` bytes of dynamic shared memory (D = 32..512 records).
+static int persistent_grid(int which, int threads, size_t smem, cudaError_t& err)
 {
-    static int cached[64][2][4] = {};
+    static int cached[64][2][4][6] = {};
     int dev = 0;
     err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return 0;
     const int ti = threads <= 32 ? 0 : threads <= 64 ? 1 : threads <= 128 ? 2 : 3;
-    if (dev >= 0 && dev < 64 && cached[dev][which][ti] > 0) return cached[dev][which][ti];
+    int bi = 0;
+    while (bi < 5 && render_smem_bytes(32 << bi) < smem) ++bi;
+    if (dev >= 0 && dev < 64 && cached[dev][which][ti][bi] > 0) return cached[dev][which][ti][bi];
     int sms = 0, per_sm = 0;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return 0;
     if (which == 0)
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, threads,
-                                                            render_smem_bytes(threads));
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_rig, threads, smem);
     else
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_split, threads,
-                                                            render_smem_bytes(threads));
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_split, threads, smem);
     if (err != cudaSuccess) return 0;
     const int g = sms * (per_sm > 0 ? per_sm : 1);
-    if (dev >= 0 && dev < 64) cached[dev][which][ti] = g;
+    if (dev >= 0 && dev < 64) cached[dev][which][ti][bi] = g;
     return g;
 }
 
@@ -510,10 +530,12 @@ static cudaError_t launch_split(const gsr_plan* p, const void* ws, const SensorT
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     cudaError_t e = cudaMemsetAsync(counters + C_SPLIT_QUEUE, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid(1, threads, e);
+    const size_t smem = render_smem_bytes(batch_of(tab, threads));
+    if ((e = smem_attr(k_render_split, smem)) != cudaSuccess) return e;
+    const int grid = persistent_grid(1, threads, smem, e);
     if (e != cudaSuccess) return e;
     const int pb = sort_result_buffer(tile_sort_passes(p));
-    k_render_split<<<grid, threads, render_smem_bytes(threads), st>>>(
+    k_render_split<<<grid, threads, smem, st>>>(
         tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
         region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), ro, counters, split_bufs(p, ws), only);
     return cudaGetLastError();
@@ -524,7 +546,7 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
     const SensorTable tab = make_sensor_table(p);
     const SensorDev& sd = tab.s[sensor];
     const int threads = sd.tile_w * sd.tile_h;
-    const size_t smem = render_smem_bytes(threads);
+    const size_t smem = render_smem_bytes(batch_of(tab, threads));
     const int tiles = sd.tiles_x * sd.tiles_y;
     const float4* rec = region<float4>(p, ws, R_RECORDS);
     const uint2* ranges = region<uint2>(p, ws, R_RANGES);
@@ -532,12 +554,16 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     const SplitBufs sp = split_bufs(p, ws);
-    if (sd.kind == GSR_SENSOR_PINHOLE)
+    cudaError_t e;
+    if (sd.kind == GSR_SENSOR_PINHOLE) {
+        if ((e = smem_attr(k_render<GSR_SENSOR_PINHOLE>, smem)) != cudaSuccess) return e;
         k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters,
                                                                    sp);
-    else
+    } else {
+        if ((e = smem_attr(k_render<GSR_SENSOR_LIDAR>, smem)) != cudaSuccess) return e;
         k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters, sp);
-    cudaError_t e = cudaGetLastError();
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     RigOut ro;
     for (int i = 0; i < GSR_MAX_SENSORS; ++i) ro.o[i] = FrameOut{};
@@ -556,10 +582,12 @@ cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut*
     // one CTA per tile in flight, as wide as the largest tile of the plan
     int threads = 32;
     for (int i = 0; i < p->n_sensors; ++i) threads = max(threads, tab.s[i].tile_w * tab.s[i].tile_h);
-    const int grid = persistent_grid(0, threads, e);
+    const size_t smem = render_smem_bytes(batch_of(tab, threads));
+    if ((e = smem_attr(k_render_rig, smem)) != cudaSuccess) return e;
+    const int grid = persistent_grid(0, threads, smem, e);
     if (e != cudaSuccess) return e;
     const int pb = sort_result_buffer(tile_sort_passes(p));
-    k_render_rig<<<grid, threads, render_smem_bytes(threads), st>>>(
+    k_render_rig<<<grid, threads, smem, st>>>(
         tab, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES),
         region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_A), ro,
         counters, split_bufs(p, ws));

@@ -40,7 +40,7 @@ class Sensor(ctypes.Structure):
 
 
 class Tiling(ctypes.Structure):
-    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32)]
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch_depth", c_i32)]
 
 
 class Plan(ctypes.Structure):
@@ -91,10 +91,29 @@ class SurfelTable(ctypes.Structure):
                 ("intensity", c_vp)]
 
 
+AUTOTUNE_MAX = 8
+
+
+class AutotuneSpace(ctypes.Structure):
+    _fields_ = [("n_camera_tiles", c_i32), ("camera_tiles", (c_i32 * 2) * AUTOTUNE_MAX),
+                ("n_lidar_tiles", c_i32), ("lidar_tiles", (c_i32 * 2) * AUTOTUNE_MAX),
+                ("n_batch_depths", c_i32), ("batch_depths", c_i32 * AUTOTUNE_MAX),
+                ("warmup", c_i32), ("reps", c_i32)]
+
+
+class AutotuneTrial(ctypes.Structure):
+    _fields_ = [("camera_tile", c_i32 * 2), ("lidar_tile", c_i32 * 2), ("batch_depth", c_i32), ("ms", c_f32)]
+
+
+class AutotuneResult(ctypes.Structure):
+    _fields_ = [("plan", Plan), ("best_ms", c_f32), ("n_tried", c_i32),
+                ("tried", AutotuneTrial * (3 * AUTOTUNE_MAX + 1))]
+
+
 DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
 
 _STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights,
-            Anchors, Mlp, MlpGrads, SurfelTable]
+            Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult]
 
 # exported symbols and their ctypes signatures (restype, argtypes)
 SIGNATURES = {
@@ -117,6 +136,11 @@ SIGNATURES = {
     "gsr_workspace_region": (c_i32, [ctypes.POINTER(Plan), c_vp, c_i32, ctypes.POINTER(c_vp),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "gsr_struct_size": (ctypes.c_size_t, [c_i32]),
+    "gsr_autotune_workspace_size": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(AutotuneSpace),
+                                            ctypes.POINTER(ctypes.c_size_t)]),
+    "gsr_autotune": (c_i32, [ctypes.POINTER(Plan), ctypes.POINTER(Surfels), c_i32, ctypes.POINTER(Objects),
+                             ctypes.POINTER(AutotuneSpace), c_vp, ctypes.c_size_t, ctypes.POINTER(CameraOut),
+                             ctypes.POINTER(LidarOut), ctypes.POINTER(AutotuneResult), c_vp]),
     "gsr_loss": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut), c_vp,
                          ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward_render": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
@@ -207,10 +231,10 @@ def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None) -> Sensor:
     return s
 
 
-def plan_init(n_surfels: int, sensors, tile=(16, 16), max_dup: int = 0) -> Plan:
+def plan_init(n_surfels: int, sensors, tile=(16, 16), max_dup: int = 0, batch_depth: int = 0) -> Plan:
     arr = (Sensor * len(sensors))(*sensors)
     p = Plan()
-    t = Tiling(int(tile[0]), int(tile[1]))
+    t = Tiling(int(tile[0]), int(tile[1]), int(batch_depth))
     _check(lib().gsr_plan_init(ctypes.byref(p), int(n_surfels), arr, len(sensors), ctypes.byref(t), int(max_dup)),
            "gsr_plan_init")
     return p
@@ -298,6 +322,42 @@ def render_rig(plan, ws, ws_bytes, outs, stream):
     """outs: per-sensor CameraOut / LidarOut structs (index = sensor)."""
     cams, lids = _rig_out_arrays(plan, outs)
     _check(lib().gsr_render_rig(ctypes.byref(plan), ws, ws_bytes, cams, lids, stream), "gsr_render_rig")
+
+
+def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, reps=3) -> AutotuneSpace:
+    sp = AutotuneSpace()
+    for name, vals in (("camera_tiles", camera_tiles), ("lidar_tiles", lidar_tiles)):
+        if len(vals) > AUTOTUNE_MAX:
+            raise ValueError(f"at most {AUTOTUNE_MAX} {name}")
+        setattr(sp, "n_" + name, len(vals))
+        arr = getattr(sp, name)
+        for i, (w, h) in enumerate(vals):
+            arr[i][0], arr[i][1] = int(w), int(h)
+    if len(batch_depths) > AUTOTUNE_MAX:
+        raise ValueError(f"at most {AUTOTUNE_MAX} batch_depths")
+    sp.n_batch_depths = len(batch_depths)
+    for i, d in enumerate(batch_depths):
+        sp.batch_depths[i] = int(d)
+    sp.warmup, sp.reps = int(warmup), int(reps)
+    return sp
+
+
+def autotune_workspace_size(plan, space: AutotuneSpace) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().gsr_autotune_workspace_size(ctypes.byref(plan), ctypes.byref(space), ctypes.byref(n)),
+           "gsr_autotune_workspace_size")
+    return int(n.value)
+
+
+def autotune(plan, parts, objects, space: AutotuneSpace, ws, ws_bytes, outs, stream) -> AutotuneResult:
+    """parts: Surfels structs consecutive in the plan; outs as render_rig."""
+    arr = (Surfels * len(parts))(*parts)
+    cams, lids = _rig_out_arrays(plan, outs)
+    res = AutotuneResult()
+    _check(lib().gsr_autotune(ctypes.byref(plan), arr, len(parts),
+                              ctypes.byref(objects) if objects is not None else None, ctypes.byref(space), ws,
+                              ws_bytes, cams, lids, ctypes.byref(res), stream), "gsr_autotune")
+    return res
 
 
 class FrameGraph:

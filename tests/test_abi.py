@@ -83,3 +83,32 @@ def test_argument_errors(L):
     rc = L.gsr_bin_sort(ctypes.byref(p), None, 0, None)
     assert rc == gsr.ERR_INVALID_ARG
     assert gsr.status_string(gsr.ERR_CAPACITY) == "GSR_ERR_CAPACITY"
+
+
+def test_autotune_workspace_and_batch_depth_host_only(L):
+    cam, lid = gsr.sensor(synth.driving_camera()), gsr.sensor(synth.driving_lidar())
+    p = gsr.plan_init(100_000, [cam, lid], (16, 16))
+    cams, lids = ((16, 16), (8, 8), (32, 8)), ((8, 8), (4, 8))
+    sp = gsr.autotune_space(cams, lids, (64, 256))
+    need = gsr.autotune_workspace_size(p, sp)
+    for ct in cams:
+        for lt in lids:
+            q = gsr.plan_init(100_000, [gsr.sensor(synth.driving_camera(), tile=ct),
+                                        gsr.sensor(synth.driving_lidar(), tile=lt)], (16, 16))
+            assert gsr.workspace_size(q) <= need
+    # the staging depth does not change the workspace; odd depths are rejected
+    assert gsr.workspace_size(gsr.plan_init(100_000, [cam, lid], (16, 16), batch_depth=512)) == gsr.workspace_size(p)
+    for bd in (16, 100, 1024):
+        with pytest.raises(gsr.GsrError) as e:
+            gsr.plan_init(100_000, [cam, lid], (16, 16), batch_depth=bd)
+        assert e.value.code == gsr.ERR_UNSUPPORTED
+    # bad spaces and part lists are rejected before any launch
+    bad = gsr.autotune_space(cams, lids, (64,), reps=0)
+    n = ctypes.c_size_t()
+    assert L.gsr_autotune_workspace_size(ctypes.byref(p), ctypes.byref(bad), ctypes.byref(n)) == gsr.ERR_INVALID_ARG
+    part = gsr.Surfels()
+    part.n = 99_999   # parts must cover the plan exactly
+    res = gsr.AutotuneResult()
+    rc = L.gsr_autotune(ctypes.byref(p), ctypes.byref(part), 1, None, ctypes.byref(sp), ctypes.c_void_p(1 << 20),
+                        need, None, None, ctypes.byref(res), None)
+    assert rc == gsr.ERR_INVALID_ARG

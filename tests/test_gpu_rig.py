@@ -157,3 +157,63 @@ def test_preprocess_parts_mix_sh_degrees(gpu_lib):
     rgb = np.moveaxis(r.out[0]["rgb"].cpu().numpy(), 0, -1)[yy, xx]
     assert ok.mean() >= 0.97 and np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
     assert (r.out[0]["n_contrib"].cpu().numpy()[yy, xx] > 0).mean() > 0.5
+
+
+def test_batch_depth_and_tile_shape_change_speed_only(gpu_lib):
+    """The staged batch depth never changes a result (bit-exact); another
+    tile shape changes only list lengths, so results agree to rounding of
+    the split-tile merge (none where no list is split)."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    scene, poses, sensors = _small_rig()
+    d = DeviceSurfels.from_host(scene)
+    P = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk")
+    ref = None
+    for bd in (0, 32, 128, 512):
+        r = Renderer(scene.n, sensors, tiles=TILES, outputs=outs, batch_depth=bd)
+        o = [{k: v.clone() for k, v in x.items()} for x in r.render_rig(d, P)]
+        torch.cuda.synchronize()
+        assert r.status()[0] == 0
+        if ref is None:
+            ref = o
+            continue
+        for i, (oa, ob) in enumerate(zip(ref, o)):
+            for k in oa:
+                assert torch.equal(oa[k], ob[k]), (bd, i, k)
+    r = Renderer(scene.n, sensors, tiles=[(8, 8), (8, 4), (16, 16), (8, 8)], outputs=outs)
+    o = r.render_rig(d, P)
+    torch.cuda.synchronize()
+    for i, (oa, ob) in enumerate(zip(ref, o)):
+        for key in (("rgb", "depth") if "rgb" in oa else ("intensity", "range")):
+            scale = 1.0 if key in ("rgb", "intensity") else max(1.0, float(oa[key].abs().max()))
+            assert (oa[key] - ob[key]).abs().max() <= 1e-4 * scale, (i, key)
+
+
+def test_autotune_picks_the_fastest_measured_tiling(gpu_lib):
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    scene, poses, sensors = _small_rig()
+    bg_n = 60_000
+    whole = DeviceSurfels.from_host(scene)
+    parts = [DeviceSurfels.from_host(scene.subset(np.arange(bg_n))),
+             DeviceSurfels.from_host(scene.subset(np.arange(bg_n, scene.n)))]
+    P = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk")
+    ref = Renderer(scene.n, sensors, tiles=TILES, outputs=outs)
+    ref_out = [{k: v.clone() for k, v in o.items()} for o in ref.render_rig(whole, P)]
+    r = Renderer(scene.n, sensors, tiles=TILES, outputs=outs)
+    res = r.autotune(parts, P, camera_tiles=((16, 16), (8, 8)), lidar_tiles=((8, 8), (4, 8)),
+                     batch_depths=(64, 128), warmup=1, reps=2)
+    ok = [t for t in res["trials"] if t["ms"] > 0]
+    assert len(res["trials"]) >= 4 and len(ok) == len(res["trials"])
+    best = min(ok, key=lambda t: t["ms"])
+    assert res["best_ms"] == pytest.approx(best["ms"])
+    assert res["camera_tile"] == best["camera_tile"] and res["lidar_tile"] == best["lidar_tile"]
+    assert res["batch_depth"] == best["batch_depth"]
+    # the tuned plan renders the same frame (to the split-merge rounding)
+    o = r.render_rig(whole, P)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    for i, (oa, ob) in enumerate(zip(ref_out, o)):
+        for key in (("rgb", "depth") if "rgb" in oa else ("intensity", "range")):
+            scale = 1.0 if key in ("rgb", "intensity") else max(1.0, float(oa[key].abs().max()))
+            assert (oa[key] - ob[key]).abs().max() <= 1e-4 * scale, (i, key)

@@ -227,14 +227,14 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- GPU arm
 def bin_sort_launches(plan):
-    """Kernel launches of one gsr_bin_sort: compaction 3, depth sort 4 x 3,
-    duplication 3, tile sort 3 per 8-bit pass, tile ranges 1, split plan 1,
-    tile schedule 1 + 2 x 3."""
+    """Kernel launches of one gsr_bin_sort: compaction 3, depth sort 4 passes
+    x 5 (histogram, 3-step scan, scatter), duplication 4, tile sort 5 per
+    8-bit pass, tile ranges 1, split plan 1, tile schedule 1 + 2 x 5."""
     T = plan.tile_base[plan.n_sensors]
     bits = 1
     while (1 << bits) < T:
         bits += 1
-    return 3 + 12 + 3 + 3 * ((bits + 7) // 8) + 1 + 1 + 1 + 6
+    return 3 + 20 + 4 + 5 * ((bits + 7) // 8) + 1 + 1 + 1 + 10
 
 
 class Timer:

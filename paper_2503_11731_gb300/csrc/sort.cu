@@ -149,20 +149,52 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     }
 }
 
-// Exclusive scan of the whole digit-major histogram (one CTA).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* __restrict__ hist, int n)
+// Exclusive scan of the whole digit-major histogram (n a multiple of 8) in
+// three steps: per-CTA sums of 2048-entry blocks, a scan of those sums, and
+// the in-block scan plus the block's base.
+constexpr int kScanBlock = 2048;
+
+__global__ void __launch_bounds__(256) k_hist_block_sums(const uint32_t* __restrict__ hist, int n,
+                                                         uint32_t* __restrict__ sums)
 {
-    __shared__ uint32_t sm[33];
-    const int per = (n + 1023) / 1024;
-    const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
+    __shared__ uint32_t sm[9];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x * 8;
     uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += hist[i];
+    if (i < n) {
+        const uint4 a = *reinterpret_cast<const uint4*>(hist + i);
+        const uint4 b = *reinterpret_cast<const uint4*>(hist + i + 4);
+        s = a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+    }
     uint32_t tot;
-    uint32_t off = block_exclusive_scan<uint32_t, 1024>(s, tot, sm);
-    for (int i = b; i < e; ++i) {
-        uint32_t v = hist[i];
-        hist[i] = off;
-        off += v;
+    block_exclusive_scan<uint32_t, 256>(s, tot, sm);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_hist_block_apply(uint32_t* __restrict__ hist, int n,
+                                                          const uint32_t* __restrict__ bases)
+{
+    __shared__ uint32_t sm[9];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x * 8;
+    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < n) {
+        const uint4 a = *reinterpret_cast<const uint4*>(hist + i);
+        const uint4 b = *reinterpret_cast<const uint4*>(hist + i + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+    uint32_t tot;
+    uint32_t off = bases[blockIdx.x] + block_exclusive_scan<uint32_t, 256>(s, tot, sm);
+    if (i < n) {
+        uint32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            o[k] = off;
+            off += v[k];
+        }
+        *reinterpret_cast<uint4*>(hist + i) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4*>(hist + i + 4) = make_uint4(o[4], o[5], o[6], o[7]);
     }
 }
 
@@ -273,18 +305,12 @@ __global__ void __launch_bounds__(256) k_dup_count(const uint32_t* __restrict__ 
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// Each visible slot writes (global tile id, slot) for every tile of its
-// rectangle, row-major, at its prefix-sum offset; pairs beyond max_dup are
-// dropped.  Camera slots marked kRectExact emit only the tiles their
-// footprint reaches, with the same test the preprocess counted with.
-__global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
-                                                   const uint32_t* __restrict__ vis_val,
-                                                   const uint32_t* __restrict__ cnt_sorted,
-                                                   const uint32_t* __restrict__ n_ptr,
-                                                   const unsigned long long* __restrict__ partial,
-                                                   const ushort4* __restrict__ rects,
-                                                   const float4* __restrict__ rec, uint64_t cap,
-                                                   uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
+// Exclusive pair offset of every visible slot in depth order, saturated at
+// the pair capacity (pairs at or beyond it are dropped).
+__global__ void __launch_bounds__(256) k_dup_offsets(const uint32_t* __restrict__ cnt_sorted,
+                                                     const uint32_t* __restrict__ n_ptr,
+                                                     const unsigned long long* __restrict__ partial, uint64_t cap,
+                                                     uint32_t* __restrict__ offs)
 {
     __shared__ unsigned long long sm[9];
     uint64_t b, e;
@@ -294,88 +320,147 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
         const uint64_t i = t0 + threadIdx.x;
         const unsigned long long c = i < e ? cnt_sorted[i] : 0ull;
         unsigned long long tot;
-        unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(c, tot, sm);
-        // entries with few pairs: one thread each, row-major over their tiles
-        const bool big = c > 16;
-        if (c > 0 && !big && off < cap) {
-            const uint32_t slot = vis_val[i];
-            const int si = (int)(slot / (uint32_t)n_surfels);
-            const SensorDev& sd = tab.s[si];
-            const ushort4 r = rects[slot];
-            const bool exact = (r.w & kRectExact) != 0;
-            const int ty1 = r.w & ~kRectExact;
-            Footprint fp;
-            if (exact) {
-                const float4* R = rec + (size_t)slot * kRecordF4;
-                fp = make_footprint(R[0], R[1], R[2], R[3].x);
-            }
-            const int TW = sd.tile_w, TH = sd.tile_h;
-            for (int ty = r.z; ty <= ty1; ++ty) {
-                int t0 = r.x, t1 = r.y;
-                if (exact && !footprint_span(fp, ty, TW, TH, r.x, r.y, t0, t1)) continue;
-                for (int tx = t0; tx <= t1; ++tx) {
-                    if (off >= cap) break;
-                    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
-                    pkey[off] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
-                    pval[off] = slot;
-                    ++off;
+        const unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(c, tot, sm);
+        if (i < e) offs[i] = (uint32_t)(off < cap ? off : cap);
+        base += tot;
+    }
+}
+
+// First index in [0, n) whose offset exceeds v (offsets are non-decreasing).
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* __restrict__ a, uint32_t n, uint32_t v)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (a[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void put_pair(const SensorDev& sd, int ty, int tx, uint32_t slot, uint64_t o,
+                                         uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
+{
+    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;  // LiDAR azimuth wrap
+    pkey[o] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
+    pval[o] = slot;
+}
+
+// Each visible slot writes (global tile id, slot) for every tile of its
+// rectangle, row-major, at its pair offset; pairs beyond max_dup are dropped.
+// Camera slots marked kRectExact emit only the tiles their footprint
+// reaches, with the same test the preprocess counted with.  Work is split by
+// PAIRS: CTA g writes the pairs [P g / G, P (g + 1) / G) of the P kept, so
+// the few near-field slots with thousands of tiles (all at the front of the
+// depth order) are shared by many CTAs.  Slots with <= 16 pairs are expanded
+// by one thread; larger ones by the whole CTA, one at a time.
+__global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
+                                                   const uint32_t* __restrict__ vis_val,
+                                                   const uint32_t* __restrict__ cnt_sorted,
+                                                   const uint32_t* __restrict__ offs,
+                                                   const uint32_t* __restrict__ counters,
+                                                   const ushort4* __restrict__ rects,
+                                                   const float4* __restrict__ rec,
+                                                   uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
+{
+    __shared__ uint32_t big_s[256];
+    __shared__ uint32_t n_big_s, rb_s, re_s;
+    __shared__ uint32_t pre_s[257], t0_s[256];
+    __shared__ uint32_t scan_s[9];
+    const uint32_t n_vis = counters[C_NVIS];
+    const uint64_t P = counters[C_NDUP];
+    const int G = gridDim.x, tid = threadIdx.x;
+    const uint64_t p0 = P * (uint64_t)blockIdx.x / G, p1 = P * (uint64_t)(blockIdx.x + 1) / G;
+    if (p0 >= p1) return;
+    if (tid == 0) {
+        rb_s = upper_bound_u32(offs, n_vis, (uint32_t)p0) - 1u;
+        re_s = upper_bound_u32(offs, n_vis, (uint32_t)(p1 - 1));
+    }
+    __syncthreads();
+    const uint32_t rb = rb_s, re = re_s;
+    for (uint32_t base = rb; base < re; base += 256) {
+        if (tid == 0) n_big_s = 0;
+        __syncthreads();
+        const uint32_t i = base + tid;
+        if (i < re) {
+            const uint32_t c = cnt_sorted[i];
+            const uint64_t o = offs[i];
+            if (c > 16) {
+                big_s[atomicAdd(&n_big_s, 1u)] = i;
+            } else if (c > 0) {
+                // one thread: the slot's row-major sequence, kept where it
+                // falls in this CTA's window
+                const uint32_t slot = vis_val[i];
+                const SensorDev& sd = tab.s[slot / (uint32_t)n_surfels];
+                const ushort4 r = rects[slot];
+                const bool exact = (r.w & kRectExact) != 0;
+                const int ty1 = r.w & ~kRectExact;
+                Footprint fp;
+                if (exact) {
+                    const float4* R = rec + (size_t)slot * kRecordF4;
+                    fp = make_footprint(R[0], R[1], R[2], R[3].x);
+                }
+                uint64_t q = o;
+                for (int ty = r.z; ty <= ty1 && q < p1; ++ty) {
+                    int t0 = r.x, t1 = r.y;
+                    if (exact && !footprint_span(fp, ty, sd.tile_w, sd.tile_h, r.x, r.y, t0, t1)) continue;
+                    for (int tx = t0; tx <= t1 && q < p1; ++tx, ++q)
+                        if (q >= p0) put_pair(sd, ty, tx, slot, q, pkey, pval);
                 }
             }
         }
-        // entries with many pairs: the whole warp expands them one at a time,
-        // writing the same row-major sequence at the same offsets
-        const int lane = threadIdx.x & 31;
-        uint32_t bigmask = __ballot_sync(0xffffffffu, big && off < cap);
-        while (bigmask) {
-            const int src = __ffs(bigmask) - 1;
-            bigmask &= bigmask - 1;
-            const uint32_t slot = __shfl_sync(0xffffffffu, i < e ? vis_val[i] : 0u, src);
-            const unsigned long long o0 = __shfl_sync(0xffffffffu, off, src);
-            const int si = (int)(slot / (uint32_t)n_surfels);
-            const SensorDev& sd = tab.s[si];
+        __syncthreads();
+        const uint32_t nb = n_big_s;
+        for (uint32_t k = 0; k < nb; ++k) {
+            const uint32_t j = big_s[k];
+            const uint32_t slot = vis_val[j];
+            const uint64_t o = offs[j];
+            const uint64_t c = cnt_sorted[j];
+            // the part of this slot's sequence inside the window: [klo, khi)
+            const uint64_t klo = (p0 > o ? p0 - o : 0);
+            uint64_t khi = min(c, p1 - o);
+            const SensorDev& sd = tab.s[slot / (uint32_t)n_surfels];
             const ushort4 r = rects[slot];
             const bool exact = (r.w & kRectExact) != 0;
             const int ty1 = r.w & ~kRectExact;
-            const int TW = sd.tile_w, TH = sd.tile_h;
             if (!exact) {
-                const int ncols = r.y - r.x + 1;
-                const int count = ncols * (ty1 - r.z + 1);
-                for (int k = lane; k < count; k += 32) {
-                    const unsigned long long o = o0 + (unsigned long long)k;
-                    if (o >= cap) break;
-                    const int ty = r.z + k / ncols, tx = r.x + k % ncols;
-                    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
-                    pkey[o] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
-                    pval[o] = slot;
-                }
+                const uint32_t ncols = (uint32_t)(r.y - r.x + 1);
+                khi = min(khi, (uint64_t)ncols * (uint64_t)(ty1 - r.z + 1));  // the rectangle's tiles only
+                for (uint64_t q = klo + tid; q < khi; q += 256)
+                    put_pair(sd, r.z + (int)(q / ncols), r.x + (int)(q % ncols), slot, o + q, pkey, pval);
             } else {
                 const float4* R = rec + (size_t)slot * kRecordF4;
                 const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                unsigned long long o = o0;
-                for (int row0 = r.z; row0 <= ty1; row0 += 32) {
-                    const int ty = row0 + lane;
+                uint64_t kc = 0;  // sequence position of this chunk of rows
+                for (int row0 = r.z; row0 <= ty1 && kc < khi; row0 += 256) {
+                    const int ty = row0 + tid;
                     int t0 = 0, t1 = -1;
-                    if (ty <= ty1 && !footprint_span(fp, ty, TW, TH, r.x, r.y, t0, t1)) t1 = -1;
-                    if (ty > ty1) t1 = -1;
-                    const uint32_t nrow = t1 >= t0 ? (uint32_t)(t1 - t0 + 1) : 0u;
-                    uint32_t pre = nrow;  // warp inclusive scan of the row counts
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, d);
-                        if (lane >= d) pre += y;
+                    if (ty <= ty1 && !footprint_span(fp, ty, sd.tile_w, sd.tile_h, r.x, r.y, t0, t1)) t1 = -1;
+                    const uint32_t nrow = (ty <= ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
+                    uint32_t tot;
+                    const uint32_t ex = block_exclusive_scan<uint32_t, 256>(nrow, tot, scan_s);
+                    pre_s[tid] = ex;
+                    t0_s[tid] = (uint32_t)t0;
+                    if (tid == 0) pre_s[256] = tot;
+                    __syncthreads();
+                    const uint64_t a = klo > kc ? klo - kc : 0, bnd = min((uint64_t)tot, khi - kc);
+                    for (uint64_t q = a + tid; q < bnd; q += 256) {
+                        // row of sequence position q: last row with pre <= q
+                        uint32_t lo = 0, hi = 256;
+                        while (hi - lo > 1) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (pre_s[mid] <= (uint32_t)q) lo = mid;
+                            else hi = mid;
+                        }
+                        put_pair(sd, row0 + (int)lo, (int)t0_s[lo] + (int)((uint32_t)q - pre_s[lo]), slot,
+                                 o + kc + q, pkey, pval);
                     }
-                    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
-                    unsigned long long q = o + (pre - nrow);
-                    for (int tx = t0; tx <= t1 && q < cap; ++tx, ++q) {
-                        const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;
-                        pkey[q] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
-                        pval[q] = slot;
-                    }
-                    o += total;
+                    kc += tot;
+                    __syncthreads();
                 }
             }
         }
-        base += tot;
+        __syncthreads();
     }
 }
 
@@ -451,11 +536,14 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
 }
 
 // --------------------------------------------------------------- host side
+// LSD radix sort of (key, value) pairs, n_ptr = item count on the device,
+// with G CTAs (G <= the plan's sort_ctas).
 static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                       const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st)
+                       const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st, int G)
 {
-    const int G = p->sort_ctas;
     uint32_t* hist = region<uint32_t>(p, ws, R_HIST);
+    uint32_t* sums = hist + (size_t)kRadix * p->sort_ctas;
+    const int nh = kRadix * G, nb = (nh + kScanBlock - 1) / kScanBlock;
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = first_shift + ps * kRadixBits;
         const uint32_t* ki = (ps & 1) ? k1 : k0;
@@ -463,7 +551,9 @@ static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, 
         uint32_t* ko = (ps & 1) ? k0 : k1;
         uint32_t* vo = (ps & 1) ? v0 : v1;
         k_radix_hist<<<G, kSortThreads, 0, st>>>(ki, n_ptr, shift, hist);
-        k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * G);
+        k_hist_block_sums<<<nb, 256, 0, st>>>(hist, nh, sums);
+        k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(sums, nb, nullptr, nullptr, 0, -1);
+        k_hist_block_apply<<<nb, 256, 0, st>>>(hist, nh, sums);
         k_radix_scatter<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist);
     }
 }
@@ -493,7 +583,7 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(partial, G, counters + C_NVIS, counters, 0, -1);
     k_compact_write<<<G, 256, 0, st>>>(counts, region<uint32_t>(p, ws, R_DEPTHKEY), n_slots, partial, vk[0], vv[0]);
     // 2. depth passes
-    radix_sort(p, ws, vk[0], vv[0], vk[1], vv[1], counters + C_NVIS, 0, kDepthSortPasses, st);
+    radix_sort(p, ws, vk[0], vv[0], vk[1], vv[1], counters + C_NVIS, 0, kDepthSortPasses, st, G);
     const int vb = sort_result_buffer(kDepthSortPasses);
     // 3. offsets (64-bit partials), capacity check
     unsigned long long* p64 = reinterpret_cast<unsigned long long*>(partial);
@@ -501,13 +591,14 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     k_dup_count<<<G, 256, 0, st>>>(vv[vb], counts, counters + C_NVIS, cnt_sorted, p64);
     k_scan_partials<unsigned long long><<<1, 1024, 0, st>>>(
         p64, G, reinterpret_cast<unsigned long long*>(counters + C_NDUP_WANT), counters, p->max_dup, C_NDUP);
-    // 4. duplication
-    k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, counters + C_NVIS, p64,
-                                   region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS),
-                                   (uint64_t)p->max_dup, pk[0], pv[0]);
+    // 4. duplication, balanced by pairs
+    uint32_t* offs = region<uint32_t>(p, ws, R_OFFSETS);
+    k_dup_offsets<<<G, 256, 0, st>>>(cnt_sorted, counters + C_NVIS, p64, (uint64_t)p->max_dup, offs);
+    k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, offs, counters,
+                                   region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS), pk[0], pv[0]);
     // 5. tile passes
     const int tp = tile_sort_passes(p);
-    radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st);
+    radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st, G);
     const int pb = sort_result_buffer(tp);
     // 6. tile ranges
     uint2* ranges = region<uint2>(p, ws, R_RANGES);
@@ -521,7 +612,9 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     uint32_t* tk[2] = {region<uint32_t>(p, ws, R_TILE_KEY_A), region<uint32_t>(p, ws, R_TILE_KEY_B)};
     uint32_t* tv[2] = {region<uint32_t>(p, ws, R_TILE_VAL_A), region<uint32_t>(p, ws, R_TILE_VAL_B)};
     k_tile_keys<<<(T + 255) / 256, 256, 0, st>>>(ranges, T, tk[0], tv[0], counters);
-    radix_sort(p, ws, tk[0], tv[0], tk[1], tv[1], counters + C_NTILES, 0, 2, st);
+    const uint32_t gt = (T + kSortTile - 1) / kSortTile;
+    const int GT = gt < (uint32_t)G ? (int)gt : G;
+    radix_sort(p, ws, tk[0], tv[0], tk[1], tv[1], counters + C_NTILES, 0, 2, st, GT < 1 ? 1 : GT);
     return cudaGetLastError();
 }
 

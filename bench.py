@@ -358,6 +358,8 @@ def run_gpu(args):
         stages = [("pre_sort", lambda: gf.launch(sh)), ("render_rig", lambda: gr.launch(sh))]
         n_launch = 1 + bin_sort_launches(r.plan) + 2
         n_main = scene.n
+    tiling = {"tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
+              "batch_depth": r.plan.tiling.batch_depth or "CTA width"}
     tm = Timer(stream, [k for k, _ in stages])
 
     def step(record=False):
@@ -508,9 +510,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (decode bf16 tcgen05, fp32 accumulation)" if anchors is not None
         else "f32", "data": "synthetic (seeded driving scene + rig; untrained seeded anchor MLP)",
-        "config": {"workload": wl_desc,
-                   "tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
-                   "batch_depth": r.plan.tiling.batch_depth or "CTA width",
+        "config": {"workload": wl_desc, **tiling,
                    "surfels": n_main, "rays_per_frame": total_rays, "visible_records": nvis,
                    "tile_pairs": npairs, "l2": "inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},

@@ -352,8 +352,31 @@ __device__ __forceinline__ void put_pair(const SensorDev& sd, int ty, int tx, ui
 // reaches, with the same test the preprocess counted with.  Work is split by
 // PAIRS: CTA g writes the pairs [P g / G, P (g + 1) / G) of the P kept, so
 // the few near-field slots with thousands of tiles (all at the front of the
-// depth order) are shared by many CTAs.  Slots with <= 16 pairs are expanded
-// by one thread; larger ones by the whole CTA, one at a time.
+// depth order) are shared by many CTAs.  A slot is expanded by one thread
+// (<= kDupThread pairs), by its warp (<= kDupWarp) or by the whole CTA.
+constexpr uint32_t kDupThread = 16;
+constexpr uint32_t kDupWarp = 4096;
+
+struct DupSlot {
+    uint32_t slot;
+    const SensorDev* sd;
+    ushort4 r;
+    bool exact;
+    int ty1;
+};
+
+__device__ __forceinline__ DupSlot dup_slot(const SensorTable& tab, int n_surfels, uint32_t slot,
+                                            const ushort4* __restrict__ rects)
+{
+    DupSlot d;
+    d.slot = slot;
+    d.sd = &tab.s[slot / (uint32_t)n_surfels];
+    d.r = rects[slot];
+    d.exact = (d.r.w & kRectExact) != 0;
+    d.ty1 = d.r.w & ~kRectExact;
+    return d;
+}
+
 __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
                                                    const uint32_t* __restrict__ vis_val,
                                                    const uint32_t* __restrict__ cnt_sorted,
@@ -368,13 +391,13 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
     __shared__ uint32_t pre_s[257], t0_s[256];
     __shared__ uint32_t scan_s[9];
     const uint32_t n_vis = counters[C_NVIS];
-    const uint64_t P = counters[C_NDUP];
-    const int G = gridDim.x, tid = threadIdx.x;
-    const uint64_t p0 = P * (uint64_t)blockIdx.x / G, p1 = P * (uint64_t)(blockIdx.x + 1) / G;
+    const uint32_t P = counters[C_NDUP];
+    const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31;
+    const uint32_t p0 = (uint32_t)((uint64_t)P * blockIdx.x / G), p1 = (uint32_t)((uint64_t)P * (blockIdx.x + 1) / G);
     if (p0 >= p1) return;
     if (tid == 0) {
-        rb_s = upper_bound_u32(offs, n_vis, (uint32_t)p0) - 1u;
-        re_s = upper_bound_u32(offs, n_vis, (uint32_t)(p1 - 1));
+        rb_s = upper_bound_u32(offs, n_vis, p0) - 1u;
+        re_s = upper_bound_u32(offs, n_vis, p1 - 1u);
     }
     __syncthreads();
     const uint32_t rb = rb_s, re = re_s;
@@ -382,78 +405,106 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
         if (tid == 0) n_big_s = 0;
         __syncthreads();
         const uint32_t i = base + tid;
-        if (i < re) {
-            const uint32_t c = cnt_sorted[i];
-            const uint64_t o = offs[i];
-            if (c > 16) {
-                big_s[atomicAdd(&n_big_s, 1u)] = i;
-            } else if (c > 0) {
-                // one thread: the slot's row-major sequence, kept where it
-                // falls in this CTA's window
-                const uint32_t slot = vis_val[i];
-                const SensorDev& sd = tab.s[slot / (uint32_t)n_surfels];
-                const ushort4 r = rects[slot];
-                const bool exact = (r.w & kRectExact) != 0;
-                const int ty1 = r.w & ~kRectExact;
-                Footprint fp;
-                if (exact) {
-                    const float4* R = rec + (size_t)slot * kRecordF4;
-                    fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                }
-                uint64_t q = o;
-                for (int ty = r.z; ty <= ty1 && q < p1; ++ty) {
-                    int t0 = r.x, t1 = r.y;
-                    if (exact && !footprint_span(fp, ty, sd.tile_w, sd.tile_h, r.x, r.y, t0, t1)) continue;
-                    for (int tx = t0; tx <= t1 && q < p1; ++tx, ++q)
-                        if (q >= p0) put_pair(sd, ty, tx, slot, q, pkey, pval);
+        const uint32_t c = i < re ? cnt_sorted[i] : 0u;
+        const uint32_t o = i < re ? offs[i] : 0u;
+        if (c > kDupWarp) big_s[atomicAdd(&n_big_s, 1u)] = i;
+        if (c > 0 && c <= kDupThread) {
+            // one thread: the slot's row-major sequence, kept where it falls
+            // in this CTA's window
+            const DupSlot d = dup_slot(tab, n_surfels, vis_val[i], rects);
+            Footprint fp;
+            if (d.exact) {
+                const float4* R = rec + (size_t)d.slot * kRecordF4;
+                fp = make_footprint(R[0], R[1], R[2], R[3].x);
+            }
+            uint32_t q = o;
+            for (int ty = d.r.z; ty <= d.ty1 && q < p1; ++ty) {
+                int t0 = d.r.x, t1 = d.r.y;
+                if (d.exact && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1)) continue;
+                for (int tx = t0; tx <= t1 && q < p1; ++tx, ++q)
+                    if (q >= p0) put_pair(*d.sd, ty, tx, d.slot, q, pkey, pval);
+            }
+        }
+        // warp: slots of this warp with kDupThread < c <= kDupWarp, one at a time
+        uint32_t wmask = __ballot_sync(0xffffffffu, c > kDupThread && c <= kDupWarp);
+        while (wmask) {
+            const int src = __ffs(wmask) - 1;
+            wmask &= wmask - 1;
+            const uint32_t j = base + (tid & ~31) + src;
+            const uint32_t oj = __shfl_sync(0xffffffffu, o, src), cj = __shfl_sync(0xffffffffu, c, src);
+            const uint32_t klo = p0 > oj ? p0 - oj : 0u, khi = min(cj, p1 - oj);
+            const DupSlot d = dup_slot(tab, n_surfels, vis_val[j], rects);
+            if (!d.exact) {
+                const uint32_t ncols = (uint32_t)(d.r.y - d.r.x + 1);
+                const uint32_t kend = min(khi, ncols * (uint32_t)(d.ty1 - d.r.z + 1));
+                for (uint32_t q = klo + lane; q < kend; q += 32)
+                    put_pair(*d.sd, d.r.z + (int)(q / ncols), d.r.x + (int)(q % ncols), d.slot, oj + q, pkey, pval);
+            } else {
+                const float4* R = rec + (size_t)d.slot * kRecordF4;
+                const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
+                uint32_t kc = 0;
+                for (int row0 = d.r.z; row0 <= d.ty1 && kc < khi; row0 += 32) {
+                    const int ty = row0 + lane;
+                    int t0 = 0, t1 = -1;
+                    if (ty <= d.ty1 && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
+                        t1 = -1;
+                    const uint32_t nrow = (ty <= d.ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
+                    uint32_t pre = nrow;  // warp inclusive scan of the row counts
+#pragma unroll
+                    for (int dd = 1; dd < 32; dd <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, dd);
+                        if (lane >= dd) pre += y;
+                    }
+                    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+                    // this lane's row occupies sequence positions [kc + pre - nrow, kc + pre)
+                    uint32_t q = kc + pre - nrow;
+                    for (int tx = t0; tx <= t1 && q < khi; ++tx, ++q)
+                        if (q >= klo) put_pair(*d.sd, ty, tx, d.slot, oj + q, pkey, pval);
+                    kc += total;
                 }
             }
         }
         __syncthreads();
+        // CTA: slots with more than kDupWarp pairs, one at a time
         const uint32_t nb = n_big_s;
         for (uint32_t k = 0; k < nb; ++k) {
             const uint32_t j = big_s[k];
-            const uint32_t slot = vis_val[j];
-            const uint64_t o = offs[j];
-            const uint64_t c = cnt_sorted[j];
-            // the part of this slot's sequence inside the window: [klo, khi)
-            const uint64_t klo = (p0 > o ? p0 - o : 0);
-            uint64_t khi = min(c, p1 - o);
-            const SensorDev& sd = tab.s[slot / (uint32_t)n_surfels];
-            const ushort4 r = rects[slot];
-            const bool exact = (r.w & kRectExact) != 0;
-            const int ty1 = r.w & ~kRectExact;
-            if (!exact) {
-                const uint32_t ncols = (uint32_t)(r.y - r.x + 1);
-                khi = min(khi, (uint64_t)ncols * (uint64_t)(ty1 - r.z + 1));  // the rectangle's tiles only
-                for (uint64_t q = klo + tid; q < khi; q += 256)
-                    put_pair(sd, r.z + (int)(q / ncols), r.x + (int)(q % ncols), slot, o + q, pkey, pval);
+            const uint32_t oj = offs[j], cj = cnt_sorted[j];
+            const uint32_t klo = p0 > oj ? p0 - oj : 0u;
+            uint32_t khi = min(cj, p1 - oj);
+            const DupSlot d = dup_slot(tab, n_surfels, vis_val[j], rects);
+            if (!d.exact) {
+                const uint32_t ncols = (uint32_t)(d.r.y - d.r.x + 1);
+                khi = min(khi, ncols * (uint32_t)(d.ty1 - d.r.z + 1));  // the rectangle's tiles only
+                for (uint32_t q = klo + tid; q < khi; q += 256)
+                    put_pair(*d.sd, d.r.z + (int)(q / ncols), d.r.x + (int)(q % ncols), d.slot, oj + q, pkey, pval);
             } else {
-                const float4* R = rec + (size_t)slot * kRecordF4;
+                const float4* R = rec + (size_t)d.slot * kRecordF4;
                 const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                uint64_t kc = 0;  // sequence position of this chunk of rows
-                for (int row0 = r.z; row0 <= ty1 && kc < khi; row0 += 256) {
+                uint32_t kc = 0;  // sequence position of this chunk of rows
+                for (int row0 = d.r.z; row0 <= d.ty1 && kc < khi; row0 += 256) {
                     const int ty = row0 + tid;
                     int t0 = 0, t1 = -1;
-                    if (ty <= ty1 && !footprint_span(fp, ty, sd.tile_w, sd.tile_h, r.x, r.y, t0, t1)) t1 = -1;
-                    const uint32_t nrow = (ty <= ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
+                    if (ty <= d.ty1 && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
+                        t1 = -1;
+                    const uint32_t nrow = (ty <= d.ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
                     uint32_t tot;
                     const uint32_t ex = block_exclusive_scan<uint32_t, 256>(nrow, tot, scan_s);
                     pre_s[tid] = ex;
                     t0_s[tid] = (uint32_t)t0;
                     if (tid == 0) pre_s[256] = tot;
                     __syncthreads();
-                    const uint64_t a = klo > kc ? klo - kc : 0, bnd = min((uint64_t)tot, khi - kc);
-                    for (uint64_t q = a + tid; q < bnd; q += 256) {
-                        // row of sequence position q: last row with pre <= q
+                    const uint32_t a = klo > kc ? klo - kc : 0u, bnd = min(tot, khi - kc);
+                    for (uint32_t q = a + tid; q < bnd; q += 256) {
+                        // row of sequence position q: the last row with pre <= q
                         uint32_t lo = 0, hi = 256;
                         while (hi - lo > 1) {
                             const uint32_t mid = (lo + hi) >> 1;
-                            if (pre_s[mid] <= (uint32_t)q) lo = mid;
+                            if (pre_s[mid] <= q) lo = mid;
                             else hi = mid;
                         }
-                        put_pair(sd, row0 + (int)lo, (int)t0_s[lo] + (int)((uint32_t)q - pre_s[lo]), slot,
-                                 o + kc + q, pkey, pval);
+                        put_pair(*d.sd, row0 + (int)lo, (int)t0_s[lo] + (int)(q - pre_s[lo]), d.slot, oj + kc + q,
+                                 pkey, pval);
                     }
                     kc += tot;
                     __syncthreads();

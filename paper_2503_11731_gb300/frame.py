@@ -160,9 +160,9 @@ class Renderer:
             self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         self.ws_ptr = ctypes.c_void_p((self.ws.data_ptr() + 255) & ~255)
 
-    def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 8), (32, 8)),
-                 lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 16)), batch_depths=(64, 128, 256), warmup=1, reps=3,
-                 stream=None):
+    def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
+                 lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (8, 16), (16, 16)), batch_depths=(64, 128, 256),
+                 warmup=1, reps=3, stream=None):
         """Pick the tiling of this rig with gsr_autotune over `parts` (DeviceSurfels
         consecutive in the plan) and re-plan with it; returns the trial list."""
         obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))

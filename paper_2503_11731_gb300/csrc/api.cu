@@ -13,7 +13,7 @@
 namespace gsr {
 
 __global__ void k_preprocess(SensorTable tab, gsr_surfels S, const float* poses, int n_obj, float4* rec,
-                             ushort4* rects, uint32_t* counts, uint32_t* keys, int first, int n_plan);
+                             ushort4* rects, uint32_t* counts, uint32_t* keys, uint4* spans, int first, int n_plan);
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st);
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st);
 cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd, const float* target,
@@ -164,6 +164,7 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_SPLIT_STATE] = (uint64_t)base * 8;
     sz[R_SPLIT_ITEMS] = split_item_capacity(plan) * 8;
     sz[R_SPLIT_RAYS] = split_ray_capacity(plan) * kRayWords * 4;
+    sz[R_SPANS] = slots * 16;
     static_assert(R_END <= 32, "gsr_plan::off has 32 entries");
     uint64_t off = 0;
     for (int r = 0; r < R_END; ++r) {
@@ -230,7 +231,8 @@ extern "C" gsr_status gsr_preprocess_part(const gsr_plan* plan, const gsr_surfel
         k_preprocess<<<grid, 256, 0, s>>>(tab, *surfels, poses, n_obj, region<float4>(plan, workspace, R_RECORDS),
                                           region<ushort4>(plan, workspace, R_RECTS),
                                           region<uint32_t>(plan, workspace, R_COUNTS),
-                                          region<uint32_t>(plan, workspace, R_DEPTHKEY), first, plan->n_surfels);
+                                          region<uint32_t>(plan, workspace, R_DEPTHKEY),
+                                          region<uint4>(plan, workspace, R_SPANS), first, plan->n_surfels);
         e = cudaGetLastError();
     }
     return cuda_fail(e);

@@ -33,7 +33,10 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;               // items per thread per sort tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kRadixBits = 8;
-constexpr int kSplitChunk = 2048;         // list positions per chunk of a split tile
+#ifndef GSR_SPLIT_CHUNK
+#define GSR_SPLIT_CHUNK 2048
+#endif
+constexpr int kSplitChunk = GSR_SPLIT_CHUNK;  // list positions per chunk of a split tile
 constexpr int kRayWords = 13;             // words of a stored per-ray compositing state
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -54,6 +57,7 @@ enum Region : int {
     R_SPLIT_STATE,   // per tile uint2: phase-A outcome, chunks not yet walked
     R_SPLIT_ITEMS,   // (tile, chunk) of every split tile's chunks 1..C
     R_SPLIT_RAYS,    // ray records of split tiles (carry + one block per chunk)
+    R_SPANS,         // per slot: the exact footprint's tile-row spans when short (SpanTable)
     R_END
 };
 
@@ -427,6 +431,14 @@ __device__ __forceinline__ bool footprint_span(const Footprint& f, int ty, int T
     t1 = min(tx1, (int)floorf(b));
     return t0 <= t1;
 }
+
+// Tile-row spans of an exact camera footprint, cached by the preprocess for
+// the duplication when the rectangle has at most kSpanRows rows and fewer
+// than 255 columns (a uint4 per slot, little-endian bytes): byte 0 = rows
+// cached (0 = none), then per row of the rectangle (from its first row) the
+// first tile column minus the rectangle's and the span length (0 = the
+// footprint misses the row).
+constexpr int kSpanRows = 7;
 
 // Per-ray setup shared by the forward and backward rasterisers.
 template <int KIND>

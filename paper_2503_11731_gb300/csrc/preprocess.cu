@@ -140,7 +140,7 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels S, const float* __restrict__ poses,
                                                     int n_obj, float4* __restrict__ rec, ushort4* __restrict__ rects,
                                                     uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,
-                                                    int first, int n_plan)
+                                                    uint4* __restrict__ spans, int first, int n_plan)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int si = blockIdx.y;
@@ -242,11 +242,25 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
                 // support disc entirely in front: keep only the tiles its
                 // footprint (or the low-pass disc) reaches
                 const Footprint fp = make_footprint(r0, r1, r2, o);
+                const bool cache = rect.w - rect.z < kSpanRows && rect.y - rect.x < 255;
+                // the span table as two 64-bit words (byte b at bits 8 (b % 8))
+                unsigned long long lo = cache ? (unsigned long long)(rect.w - rect.z + 1) : 0ull, hi = 0ull;
                 uint32_t c = 0;
                 for (int ty = rect.z; ty <= rect.w; ++ty) {
                     int t0, t1;
-                    if (footprint_span(fp, ty, TW, TH, rect.x, rect.y, t0, t1)) c += (uint32_t)(t1 - t0 + 1);
+                    if (footprint_span(fp, ty, TW, TH, rect.x, rect.y, t0, t1)) {
+                        c += (uint32_t)(t1 - t0 + 1);
+                        if (cache) {
+                            const int b = 1 + 2 * (ty - rect.z);
+                            const unsigned long long v =
+                                (unsigned long long)(t0 - rect.x) | ((unsigned long long)(t1 - t0 + 1) << 8);
+                            if (b < 7) lo |= v << (8 * b);
+                            else if (b == 7) { lo |= (v & 0xffull) << 56; hi |= v >> 8; }
+                            else hi |= v << (8 * (b - 8));
+                        }
+                    }
                 }
+                spans[slot] = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
                 cnt = c;
                 rect.w |= kRectExact;
             }

@@ -16,7 +16,10 @@
 
 namespace gsr {
 
-constexpr int kIlp = 4;  // records evaluated per step of a ray's walk
+#ifndef GSR_ILP
+#define GSR_ILP 4
+#endif
+constexpr int kIlp = GSR_ILP;  // records evaluated per step of a ray's walk (divides 32)
 
 // Resident CTAs per SM the persistent compositing kernels are compiled for
 // (256 threads each; 4 caps registers at 64 per thread).

@@ -352,9 +352,13 @@ __device__ __forceinline__ void put_pair(const SensorDev& sd, int ty, int tx, ui
 // reaches, with the same test the preprocess counted with.  Work is split by
 // PAIRS: CTA g writes the pairs [P g / G, P (g + 1) / G) of the P kept, so
 // the few near-field slots with thousands of tiles (all at the front of the
-// depth order) are shared by many CTAs.  A slot is expanded by one thread
-// (<= kDupThread pairs), by its warp (<= kDupWarp) or by the whole CTA.
-constexpr uint32_t kDupThread = 16;
+// depth order) are shared by many CTAs.  Within a CTA, slots are taken 256 at
+// a time: small slots (<= kDupSmall pairs over <= kDupRows tile rows) put
+// their rows in a shared table and the CTA writes all their pairs with one
+// thread per pair (consecutive pairs, consecutive addresses); larger slots
+// are expanded by their warp (<= kDupWarp pairs) or by the whole CTA.
+constexpr uint32_t kDupSmall = 1024;
+constexpr int kDupRows = 8;
 constexpr uint32_t kDupWarp = 4096;
 
 struct DupSlot {
@@ -383,13 +387,18 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
                                                    const uint32_t* __restrict__ offs,
                                                    const uint32_t* __restrict__ counters,
                                                    const ushort4* __restrict__ rects,
-                                                   const float4* __restrict__ rec,
+                                                   const float4* __restrict__ rec, const uint4* __restrict__ spans,
                                                    uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
 {
     __shared__ uint32_t big_s[256];
     __shared__ uint32_t n_big_s, rb_s, re_s;
     __shared__ uint32_t pre_s[257], t0_s[256];
     __shared__ uint32_t scan_s[9];
+    // small-slot table: per slot its offset, slot id and sensor; per row its
+    // tile row, first tile column and the running pair count at its end
+    __shared__ uint32_t so_s[256], sslot_s[256], spre_s[257];
+    __shared__ uint8_t ssen_s[256];
+    __shared__ uint16_t rty_s[256][kDupRows], rt0_s[256][kDupRows], rcum_s[256][kDupRows];
     const uint32_t n_vis = counters[C_NVIS];
     const uint32_t P = counters[C_NDUP];
     const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31;
@@ -405,28 +414,88 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
         if (tid == 0) n_big_s = 0;
         __syncthreads();
         const uint32_t i = base + tid;
-        const uint32_t c = i < re ? cnt_sorted[i] : 0u;
+        uint32_t c = i < re ? cnt_sorted[i] : 0u;
         const uint32_t o = i < re ? offs[i] : 0u;
         if (c > kDupWarp) big_s[atomicAdd(&n_big_s, 1u)] = i;
-        if (c > 0 && c <= kDupThread) {
-            // one thread: the slot's row-major sequence, kept where it falls
-            // in this CTA's window
+        // small slots: their rows into the table (a slot with more rows than
+        // the table holds goes to its warp instead)
+        uint32_t csmall = 0;
+        if (c > 0 && c <= kDupSmall) {
             const DupSlot d = dup_slot(tab, n_surfels, vis_val[i], rects);
-            Footprint fp;
-            if (d.exact) {
-                const float4* R = rec + (size_t)d.slot * kRecordF4;
-                fp = make_footprint(R[0], R[1], R[2], R[3].x);
+            int nr = 0;
+            uint32_t cum = 0;
+            bool fits = true;
+            uint4 tb = make_uint4(0u, 0u, 0u, 0u);
+            if (d.exact) tb = spans[d.slot];
+            // byte b of the span table
+            auto byte_of = [&](int b) -> uint32_t {
+                const uint32_t w = b < 4 ? tb.x : b < 8 ? tb.y : b < 12 ? tb.z : tb.w;
+                return (w >> (8 * (b & 3))) & 0xffu;
+            };
+            const int cached = d.exact ? (int)byte_of(0) : 0;
+            if (cached > 0) {
+                // the spans the preprocess cached
+                for (int k = 0; k < cached && nr < kDupRows; ++k) {
+                    const uint32_t len = byte_of(2 + 2 * k);
+                    if (len == 0) continue;
+                    cum += len;
+                    rty_s[tid][nr] = (uint16_t)(d.r.z + k);
+                    rt0_s[tid][nr] = (uint16_t)(d.r.x + byte_of(1 + 2 * k));
+                    rcum_s[tid][nr] = (uint16_t)cum;
+                    ++nr;
+                }
+            } else {
+                Footprint fp;
+                if (d.exact) {
+                    const float4* R = rec + (size_t)d.slot * kRecordF4;
+                    fp = make_footprint(R[0], R[1], R[2], R[3].x);
+                }
+                for (int ty = d.r.z; ty <= d.ty1; ++ty) {
+                    int t0 = d.r.x, t1 = d.r.y;
+                    if (d.exact && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
+                        continue;
+                    if (nr == kDupRows) {
+                        fits = false;
+                        break;
+                    }
+                    cum += (uint32_t)(t1 - t0 + 1);
+                    rty_s[tid][nr] = (uint16_t)ty;
+                    rt0_s[tid][nr] = (uint16_t)t0;
+                    rcum_s[tid][nr] = (uint16_t)cum;
+                    ++nr;
+                }
             }
-            uint32_t q = o;
-            for (int ty = d.r.z; ty <= d.ty1 && q < p1; ++ty) {
-                int t0 = d.r.x, t1 = d.r.y;
-                if (d.exact && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1)) continue;
-                for (int tx = t0; tx <= t1 && q < p1; ++tx, ++q)
-                    if (q >= p0) put_pair(*d.sd, ty, tx, d.slot, q, pkey, pval);
+            if (fits) {
+                csmall = min(cum, c);  // the count the preprocess made (equal by construction)
+                so_s[tid] = o;
+                sslot_s[tid] = d.slot;
+                ssen_s[tid] = (uint8_t)(d.slot / (uint32_t)n_surfels);
+                c = 0;  // done here
             }
         }
-        // warp: slots of this warp with kDupThread < c <= kDupWarp, one at a time
-        uint32_t wmask = __ballot_sync(0xffffffffu, c > kDupThread && c <= kDupWarp);
+        uint32_t tot_small;
+        const uint32_t ex = block_exclusive_scan<uint32_t, 256>(csmall, tot_small, scan_s);
+        spre_s[tid] = ex;
+        if (tid == 0) spre_s[256] = tot_small;
+        __syncthreads();
+        for (uint32_t k = tid; k < tot_small; k += 256) {
+            // the slot of pair k (last with spre <= k) and its row
+            uint32_t lo = 0, hi = 256;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (spre_s[mid] <= k) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t j = k - spre_s[lo];
+            const uint32_t q = so_s[lo] + j;
+            if (q < p0 || q >= p1) continue;
+            int rr = 0;
+            while (rcum_s[lo][rr] <= j) ++rr;
+            const uint32_t before = rr > 0 ? rcum_s[lo][rr - 1] : 0u;
+            put_pair(tab.s[ssen_s[lo]], rty_s[lo][rr], rt0_s[lo][rr] + (int)(j - before), sslot_s[lo], q, pkey, pval);
+        }
+        // warp: the remaining slots of this warp with c <= kDupWarp, one at a time
+        uint32_t wmask = __ballot_sync(0xffffffffu, c > 0 && c <= kDupWarp);
         while (wmask) {
             const int src = __ffs(wmask) - 1;
             wmask &= wmask - 1;
@@ -646,7 +715,8 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     uint32_t* offs = region<uint32_t>(p, ws, R_OFFSETS);
     k_dup_offsets<<<G, 256, 0, st>>>(cnt_sorted, counters + C_NVIS, p64, (uint64_t)p->max_dup, offs);
     k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, offs, counters,
-                                   region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS), pk[0], pv[0]);
+                                   region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS),
+                                   region<uint4>(p, ws, R_SPANS), pk[0], pv[0]);
     // 5. tile passes
     const int tp = tile_sort_passes(p);
     radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st, G);

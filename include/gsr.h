@@ -111,7 +111,7 @@ typedef struct {
 /* Default screen tiling of a plan's sensors (tile_w, tile_h powers of two,
  * tile_w * tile_h in {32,64,128,256}); a sensor may override it.
  * batch_depth = records staged in shared memory per step of a tile's walk
- * (double-buffered, 80 bytes each): 0 = the compositing CTA's thread count,
+ * (double-buffered, 96 bytes each): 0 = the compositing CTA's thread count,
  * else one of 32, 64, 128, 256, 512.  It changes speed only, never results. */
 typedef struct {
     int32_t tile_w, tile_h;
@@ -548,7 +548,7 @@ size_t gsr_struct_size(int32_t which);
 
 /*
  * Device pointers into the workspace, for tests and tools (no copy):
- * which = 0 records (float4 x 5 per (sensor, surfel) slot), 1 tile rects
+ * which = 0 records (float4 x 6 per (sensor, surfel) slot), 1 tile rects
  * (ushort4 per slot: tx0, tx1, ty0, ty1; tx1 may exceed tiles_x - 1 for a
  * LiDAR azimuth wrap), 2 tile counts (uint32 per slot), 3 depth keys
  * (float bits per slot), 4 sorted pair tile ids (uint32), 5 sorted pair

@@ -653,7 +653,13 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
     const int tiles = sd.tiles_x * sd.tiles_y;
     const int pb = sort_result_buffer(tile_sort_passes(p));
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
-    k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, backward_smem_bytes(threads), st>>>(
+    const size_t smem = backward_smem_bytes(threads);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_render_backward<GSR_SENSOR_PINHOLE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(
         tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a,
         region<uint32_t>(p, ws, R_COUNTERS));
     return cudaGetLastError();

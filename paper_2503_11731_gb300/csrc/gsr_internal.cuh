@@ -1,10 +1,10 @@
 // gsr_internal.cuh -- device-side layout and helpers shared by the kernels.
 //
-// Record (one per (sensor, surfel) slot, 5 x float4 = 80 B, written by the
+// Record (one per (sensor, surfel) slot, 6 x float4 = 96 B, written by the
 // preprocess and staged into shared memory by the compositing kernels):
 //   r0 = (Q00, Q01, Q02, c_x)   r1 = (Q10, Q11, Q12, c_y)
 //   r2 = (Q20, Q21, Q22, det)   r3 = (opacity, f0, f1, f2)
-//   r4 = (n_x, n_y, n_z, z_c)
+//   r4 = (n_x, n_y, n_z, z_c)   r5 = (x0, x1, y0, y1) support box in ray indices
 // Q is the adjugate of the surfel's 3x3 ray-space matrix M (Eq. 1: the
 // distinct rows of W H), so for a ray r (camera: (p - c, 1) in pixel-
 // homogeneous coordinates about the projected centre c; LiDAR: the unit ray
@@ -21,7 +21,10 @@
 
 namespace gsr {
 
-constexpr int kRecordF4 = 5;
+// Records are 6 float4; r5 = the ray-index box of the support (LiDAR
+// columns x0..x1 on the azimuth circle, x0 in [0, columns)), used to skip
+// records that miss every ray of a warp.
+constexpr int kRecordF4 = 6;
 constexpr int kRecordBytes = kRecordF4 * 16;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     ushort4 rect = make_ushort4(0, 0, 0, 0);
     float zkey;
     float4 r0, r1, r2;
+    float4 r5 = make_float4(0.f, -1.f, 0.f, -1.f);  // ray-index bounding box of the support
     const int TW = sd.tile_w, TH = sd.tile_h;
 
     // Opacity-aware support: alpha = min(0.99, o G) reaches 1/255 only where
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         index_range(xmin - 1.f, xmax + 1.f, 0.5f, sd.width, x0, x1);
         index_range(ymin - 1.f, ymax + 1.f, 0.5f, sd.height, y0, y1);
         if (x0 <= x1 && y0 <= y1) {
+            r5 = make_float4((float)x0, (float)x1, (float)y0, (float)y1);
             rect = make_ushort4(x0 / TW, x1 / TW, y0 / TH, y1 / TH);
             cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
             if (front && cnt > 1) {
@@ -387,6 +389,19 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
             }
         }
         if (i0 <= i1) {
+            // columns [c0, c0 + cw) on the azimuth circle, c0 in [0, A)
+            int c0 = 0, cw = A;
+            if (!full_cols) {
+                const float clo = fminf(az_lo * sd.inv_d_az, -rlp) - 1.f;
+                const float chi = fmaxf(az_hi * sd.inv_d_az, rlp) + 1.f;
+                const int j0 = (int)ceilf(ccol + clo), j1 = (int)floorf(ccol + chi);
+                if (j1 - j0 + 1 < A) {
+                    c0 = j0 % A;
+                    if (c0 < 0) c0 += A;
+                    cw = j1 - j0 + 1;
+                }
+            }
+            r5 = make_float4((float)c0, (float)(c0 + cw - 1), (float)i0, (float)i1);
             rect = make_ushort4(tx0, tx1, i0 / TH, i1 / TH);
             cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
         }
@@ -422,6 +437,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     R[2] = r2;
     R[3] = r3;
     R[4] = make_float4(ns.x, ns.y, ns.z, zkey);
+    R[5] = r5;
 }
 
 }  // namespace gsr

@@ -1,10 +1,12 @@
 // render.cu -- per-tile front-to-back compositing (camera and LiDAR).
 //
 // One CTA per screen tile, one thread per pixel (ray).  The tile's sorted
-// list of records is walked in batches of `blockDim.x` records; each batch is
-// staged into shared memory by bulk async copies (one 80-byte cp.async.bulk
-// per record, completing on an mbarrier), double-buffered so the next batch
-// lands while the current one is composited.  Every thread then solves
+// list of records is walked in batches of D records; each batch is staged
+// into shared memory by bulk async copies (one 96-byte cp.async.bulk per
+// record, completing on an mbarrier), double-buffered so the next batch
+// lands while the current one is composited.  Each warp first drops the
+// records whose support box misses all its rays (one lane per record, a
+// ballot), then every thread solves
 // Eq. 2 for its ray against each staged surfel in closed form (q = Q r,
 // (u, v) = (q_0, q_1)/q_2, depth or distance = det/q_2; see
 // gsr_internal.cuh), falls back to the 2DGS screen-space low-pass where it
@@ -92,6 +94,32 @@ __device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, int local_tile)
     return t;
 }
 
+// Ray-index box (x0, x1, y0, y1) of the warp's rays still walking (empty if
+// none): a record whose support box misses it cannot reach any of them.
+__device__ __forceinline__ float4 warp_box(const TileRay& ray, bool done)
+{
+    const bool live = ray.inside && !done;
+    const int x0 = __reduce_min_sync(0xffffffffu, live ? ray.x : 0x7fffffff);
+    const int x1 = __reduce_max_sync(0xffffffffu, live ? ray.x : -1);
+    const int y0 = __reduce_min_sync(0xffffffffu, live ? ray.y : 0x7fffffff);
+    const int y1 = __reduce_max_sync(0xffffffffu, live ? ray.y : -1);
+    return make_float4((float)x0, (float)x1, (float)y0, (float)y1);
+}
+
+// Does a record's support box r5 meet the warp box?  LiDAR columns are
+// intervals on the azimuth circle of `columns` cells (the warp's never wraps).
+template <int KIND>
+__device__ __forceinline__ bool box_meets(const float4 r5, const float4 w, float columns)
+{
+    const bool rows = r5.w >= w.z && r5.z <= w.w;
+    if (KIND == GSR_SENSOR_PINHOLE) return rows && r5.y >= w.x && r5.x <= w.y;
+    float d = w.x - r5.x;  // warp start inside the record's interval?
+    if (d < 0.f) d += columns;
+    float e = r5.x - w.x;  // record start inside the warp's interval?
+    if (e < 0.f) e += columns;
+    return rows && w.x <= w.y && (d <= r5.y - r5.x || e <= w.y - w.x);
+}
+
 // Walk list positions [lo, hi) of a tile (list starting at `start`) with the
 // whole CTA, continuing each ray's state.  Batches of D records (a multiple
 // of kIlp) are staged by bulk copies, double-buffered; `gb` counts the batches this CTA
@@ -104,11 +132,12 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                                           uint32_t& gb, int D)
 {
     const int nthr = blockDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int n = hi - lo;
     const int nb = n > 0 ? (n + D - 1) / D : 0;
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
+    const float4 wbox = warp_box(ray, s.done);
 
     // batch b is the CTA's batch g = gb + b: buffer and barrier g & 1, phase
     // parity (g >> 1) & 1
@@ -144,52 +173,64 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
         const int cnt = min(D, n - b * D);
         const int pos0 = lo + b * D;  // list position of the batch's first record
         if (ok) {
-            // kIlp records per step: their evaluations are independent (the
-            // chains interleave), the compositing stays in list order
-            for (int j0 = 0; j0 < cnt; j0 += kIlp) {
+            for (int g0 = 0; g0 < cnt; g0 += 32) {
                 if (__all_sync(0xffffffffu, s.done)) break;
-                if (s.done) continue;
-                float al[kIlp], zz[kIlp];
-                // j0 + e < D always (D and j0 are multiples of kIlp), so
-                // the reads stay inside the buffer; records past cnt are
-                // stale and masked out
+                // one lane per record: does its support box meet any ray of
+                // this warp?  Records that do not are skipped by the warp.
+                const int jt = g0 + lane;
+                const bool meet = jt < cnt && box_meets<KIND>(B[jt * kRecordF4 + 5], wbox, columns);
+                uint32_t mask = __ballot_sync(0xffffffffu, meet);
+                while (mask) {
+                    if (__all_sync(0xffffffffu, s.done)) break;
+                    // the next kIlp records of the mask, in list order: their
+                    // evaluations are independent (the chains interleave), the
+                    // compositing stays in list order
+                    int idx[kIlp];
 #pragma unroll
-                for (int e = 0; e < kIlp; ++e) {
-                    Splat sp;
-                    const bool hit = splat_eval<KIND>(B + (j0 + e) * kRecordF4, ray.rx, ray.ry, ray.d0, ray.d1,
-                                                      ray.d2, near_plane, columns, sp);
-                    al[e] = (hit && j0 + e < cnt) ? sp.alpha : 0.f;  // a hit has alpha >= 1/255
-                    zz[e] = sp.z;
-                }
+                    for (int e = 0; e < kIlp; ++e) {
+                        idx[e] = mask ? __ffs(mask) - 1 : -1;
+                        mask &= mask - 1u;
+                    }
+                    if (s.done) continue;
+                    float al[kIlp], zz[kIlp];
 #pragma unroll
-                for (int e = 0; e < kIlp; ++e) {
-                    if (s.done || al[e] == 0.f) continue;
-                    const int j = j0 + e;
-                    const float alpha = al[e], z = zz[e];
-                    const float Tn = s.T * (1.f - alpha);
-                    if (Tn < kTMin) {
-                        s.done = true;
-                        s.walk = (uint32_t)(pos0 + j + 1);
-                        continue;
+                    for (int e = 0; e < kIlp; ++e) {
+                        Splat sp;
+                        const bool hit = splat_eval<KIND>(B + (g0 + max(idx[e], 0)) * kRecordF4, ray.rx, ray.ry,
+                                                          ray.d0, ray.d1, ray.d2, near_plane, columns, sp);
+                        al[e] = (hit && idx[e] >= 0) ? sp.alpha : 0.f;  // a hit has alpha >= 1/255
+                        zz[e] = sp.z;
                     }
-                    const float4* Rj = B + j * kRecordF4;
-                    const float w = alpha * s.T;
-                    const float4 r3 = Rj[3];
-                    s.f0 = fmaf(w, r3.y, s.f0);
-                    if (KIND == GSR_SENSOR_PINHOLE) {
-                        s.f1 = fmaf(w, r3.z, s.f1);
-                        s.f2 = fmaf(w, r3.w, s.f2);
-                        const float4 r4 = Rj[4];
-                        s.n0 = fmaf(w, r4.x, s.n0);
-                        s.n1 = fmaf(w, r4.y, s.n1);
-                        s.n2 = fmaf(w, r4.z, s.n2);
+#pragma unroll
+                    for (int e = 0; e < kIlp; ++e) {
+                        if (s.done || al[e] == 0.f) continue;
+                        const int j = g0 + idx[e];
+                        const float alpha = al[e], z = zz[e];
+                        const float Tn = s.T * (1.f - alpha);
+                        if (Tn < kTMin) {
+                            s.done = true;
+                            s.walk = (uint32_t)(pos0 + j + 1);
+                            continue;
+                        }
+                        const float4* Rj = B + j * kRecordF4;
+                        const float w = alpha * s.T;
+                        const float4 r3 = Rj[3];
+                        s.f0 = fmaf(w, r3.y, s.f0);
+                        if (KIND == GSR_SENSOR_PINHOLE) {
+                            s.f1 = fmaf(w, r3.z, s.f1);
+                            s.f2 = fmaf(w, r3.w, s.f2);
+                            const float4 r4 = Rj[4];
+                            s.n0 = fmaf(w, r4.x, s.n0);
+                            s.n1 = fmaf(w, r4.y, s.n1);
+                            s.n2 = fmaf(w, r4.z, s.n2);
+                        }
+                        s.A += w;
+                        const float wz = w * z;
+                        s.B += wz;
+                        s.D = fmaf(wz, z, s.D);
+                        s.T = Tn;
+                        s.last = (uint32_t)(pos0 + j + 1);
                     }
-                    s.A += w;
-                    const float wz = w * z;
-                    s.B += wz;
-                    s.D = fmaf(wz, z, s.D);
-                    s.T = Tn;
-                    s.last = (uint32_t)(pos0 + j + 1);
                 }
             }
         }

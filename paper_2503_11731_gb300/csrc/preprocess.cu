@@ -323,29 +323,38 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
                                  -0.92387953f, -0.38268343f, 0.38268343f, 0.92387953f};
             const float sn[8] = {0.38268343f, 0.92387953f, 0.92387953f, 0.38268343f,
                                  -0.38268343f, -0.92387953f, -0.92387953f, -0.38268343f};
+            // Every vertex lies within rad of the centre while rxy > rad, so
+            // its xy direction is within 90 deg of the centre's: its azimuth
+            // offset atan2(cross, dot) is increasing in cross / dot (dot > 0),
+            // and elevations atan2(z, r) (r > 0) are increasing in z / r, so
+            // the extremes take four arctangents of extreme ratios.
+            const float ux = ms.x / rxy, uy = ms.y / rxy;
             F3 V[8];
             float rv[8];
+            float t_lo = 0.f, t_hi = 0.f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 V[j] = ms + kk * (cs[j] * a + sn[j] * b);
                 rv[j] = sqrtf(fmaf(V[j].x, V[j].x, V[j].y * V[j].y));
-                float dz = atan2f(V[j].y, V[j].x) - az;
-                if (dz > 3.14159265f) dz -= 6.28318531f;
-                if (dz < -3.14159265f) dz += 6.28318531f;
-                az_lo = fminf(az_lo, dz);
-                az_hi = fmaxf(az_hi, dz);
+                const float cr = fmaf(ux, V[j].y, -uy * V[j].x), dt = fmaf(ux, V[j].x, uy * V[j].y);
+                const float t = cr / dt;
+                t_lo = fminf(t_lo, t);
+                t_hi = fmaxf(t_hi, t);
             }
-            el_lo = 1e30f;
-            el_hi = -1e30f;
+            az_lo = atanf(t_lo);
+            az_hi = atanf(t_hi);
+            float s_lo = 1e30f, s_hi = -1e30f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const F3 P0 = V[j], P1 = V[(j + 1) & 7];
                 const float rmin = seg_dist(P0.x, P0.y, P1.x, P1.y);
                 const float rmax = fmaxf(rv[j], rv[(j + 1) & 7]);
                 const float zmax = fmaxf(P0.z, P1.z), zmin = fminf(P0.z, P1.z);
-                el_hi = fmaxf(el_hi, atan2f(zmax, zmax >= 0.f ? rmin : rmax));
-                el_lo = fminf(el_lo, atan2f(zmin, zmin <= 0.f ? rmin : rmax));
+                s_hi = fmaxf(s_hi, zmax / (zmax >= 0.f ? rmin : rmax));
+                s_lo = fminf(s_lo, zmin / (zmin <= 0.f ? rmin : rmax));
             }
+            el_hi = atanf(s_hi);
+            el_lo = atanf(s_lo);
         } else if (!full_rows) {
             const float beta = asinf(fminf(rad / rc, 1.f));
             el_lo = el - beta;

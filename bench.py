@@ -325,6 +325,7 @@ def run_gpu(args):
         objs = anchors = None
     tiles = [parse(args.lidar_tile) if s.kind == "lidar" else parse(args.camera_tile) for s in sensors]
     r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles, batch_depth=args.batch_depth,
+                 split=(args.split_first, args.split_chunk),
                  outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
@@ -359,7 +360,8 @@ def run_gpu(args):
         n_launch = 1 + bin_sort_launches(r.plan) + 2
         n_main = scene.n
     tiling = {"tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
-              "batch_depth": r.plan.tiling.batch_depth or "CTA width"}
+              "batch_depth": r.plan.tiling.batch_depth or "CTA width",
+              "split_first_chunk": [r.plan.tiling.split_first or "default", r.plan.tiling.split_chunk or "default"]}
     tm = Timer(stream, [k for k, _ in stages])
 
     def step(record=False):
@@ -459,6 +461,7 @@ def run_gpu(args):
             "explicit_batched_stage_ms": {"pre_sort": ex_front, "render_rig": ex_render},
             "explicit_tiling": {"camera_tile": r.tile_of("pinhole"), "lidar_tile": r.tile_of("lidar"),
                                 "batch_depth": r.plan.tiling.batch_depth,
+                                "split": [r.plan.tiling.split_first, r.plan.tiling.split_chunk],
                                 "autotune_best_ms": None if ex_tuned is None else ex_tuned["best_ms"]},
             "explicit_per_sensor_ms": per_sensor_ms,
             "explicit_table": f"{scene.n} SH-3 surfels (the background the anchors were grouped from + objects)",
@@ -543,6 +546,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep --camera-tile / --lidar-tile / --batch-depth instead of gsr_autotune's choice")
     ap.add_argument("--batch-depth", type=int, default=0)
+    ap.add_argument("--split-first", type=int, default=0)
+    ap.add_argument("--split-chunk", type=int, default=0)
     ap.add_argument("--camera-tile", default="16x16")
     ap.add_argument("--lidar-tile", default="8x8")
     ap.add_argument("--sample-rays", type=int, default=16)

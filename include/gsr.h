@@ -112,10 +112,17 @@ typedef struct {
  * tile_w * tile_h in {32,64,128,256}); a sensor may override it.
  * batch_depth = records staged in shared memory per step of a tile's walk
  * (double-buffered, 96 bytes each): 0 = the compositing CTA's thread count,
- * else one of 32, 64, 128, 256, 512.  It changes speed only, never results. */
+ * else one of 32, 64, 128, 256, 512.  It changes speed only, never results.
+ * A tile list longer than split_first positions is split: its first
+ * split_first positions are walked first, the rest in chunks of split_chunk
+ * positions walked in parallel and merged in list order (0 = defaults 16384
+ * and 384; split_first in [256, 2^24], split_chunk in [64, 2^24]).  The
+ * merge reassociates products of transmittance, so results may change in
+ * the last bits. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t batch_depth;
+    int32_t split_first, split_chunk;
 } gsr_tiling;
 
 /*
@@ -473,9 +480,9 @@ gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t*
 /*
  * Search space of gsr_autotune (host memory).  Every pinhole sensor takes
  * the same camera tile, every LiDAR the same LiDAR tile; n_* = 0 keeps the
- * plan's choice.  Tiles obey gsr_tiling's rule; batch depths are 0 or
- * 32..512 as in gsr_tiling.  Each candidate renders `warmup` untimed and
- * `reps` timed frames (reps >= 1).
+ * plan's choice.  Tiles obey gsr_tiling's rule; batch depths and split
+ * lengths are values gsr_tiling accepts.  Each candidate renders `warmup`
+ * untimed and `reps` timed frames (reps >= 1).
  */
 #define GSR_AUTOTUNE_MAX 8
 typedef struct {
@@ -485,6 +492,10 @@ typedef struct {
     int32_t lidar_tiles[GSR_AUTOTUNE_MAX][2];
     int32_t n_batch_depths;
     int32_t batch_depths[GSR_AUTOTUNE_MAX];
+    int32_t n_split_firsts;
+    int32_t split_firsts[GSR_AUTOTUNE_MAX];
+    int32_t n_split_chunks;
+    int32_t split_chunks[GSR_AUTOTUNE_MAX];
     int32_t warmup, reps;
 } gsr_autotune_space;
 
@@ -495,6 +506,7 @@ typedef struct {
     int32_t camera_tile[2];
     int32_t lidar_tile[2];
     int32_t batch_depth;
+    int32_t split_first, split_chunk;
     float ms;
 } gsr_autotune_trial;
 
@@ -502,7 +514,7 @@ typedef struct {
     gsr_plan plan;        /* the input plan re-initialised with the fastest tiling */
     float best_ms;
     int32_t n_tried;
-    gsr_autotune_trial tried[3 * GSR_AUTOTUNE_MAX + 1];
+    gsr_autotune_trial tried[5 * GSR_AUTOTUNE_MAX + 1];
 } gsr_autotune_result;
 
 /* Workspace bytes gsr_autotune needs: the largest over the candidates
@@ -510,10 +522,11 @@ typedef struct {
 gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gsr_autotune_space* space, size_t* bytes);
 
 /*
- * Autotuner of the batched rig frame (the paper prescribes none; tile shape
- * and staging depth are this implementation's free parameters).  Coordinate
- * descent from the plan's tiling: the camera tile over its candidates, then
- * the LiDAR tile, then the batch depth, each candidate timed with CUDA
+ * Autotuner of the batched rig frame (the paper prescribes none; tile shape,
+ * staging depth and list splitting are this implementation's free
+ * parameters).  Coordinate descent from the plan's tiling: the camera tile
+ * over its candidates, then the LiDAR tile, the batch depth, the first split
+ * length and the later chunk length, each candidate timed with CUDA
  * events over whole frames of the given surfels: `parts` (n_parts tables,
  * consecutive in the plan from surfel 0, as gsr_preprocess_part) and
  * `objects` (may be NULL), rendered into camera_outs / lidar_outs (as

@@ -45,6 +45,8 @@ SensorTable make_sensor_table(const gsr_plan* p)
     t.tile_h = p->tiling.tile_h;
     t.total_tiles = p->tile_base[p->n_sensors];
     t.batch = p->tiling.batch_depth;
+    t.split_first = p->tiling.split_first > 0 ? p->tiling.split_first : kSplitFirstDefault;
+    t.split_chunk = p->tiling.split_chunk > 0 ? p->tiling.split_chunk : kSplitChunkDefault;
     const double deg = 3.14159265358979323846 / 180.0;
     for (int i = 0; i < p->n_sensors; ++i) {
         const gsr_sensor& s = p->sensors[i];
@@ -101,6 +103,9 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     if (!tile_ok(tiling->tile_w, tiling->tile_h)) return GSR_ERR_UNSUPPORTED;
     const int bd = tiling->batch_depth;
     if (!(bd == 0 || bd == 32 || bd == 64 || bd == 128 || bd == 256 || bd == 512)) return GSR_ERR_UNSUPPORTED;
+    const int sf = tiling->split_first, sc = tiling->split_chunk;
+    if (sf != 0 && (sf < 256 || sf > (1 << 24))) return GSR_ERR_UNSUPPORTED;
+    if (sc != 0 && (sc < 64 || sc > (1 << 24))) return GSR_ERR_UNSUPPORTED;
     std::memset(plan, 0, sizeof(*plan));
     plan->n_surfels = n_surfels;
     plan->n_sensors = n_sensors;

@@ -1,7 +1,9 @@
 // autotune.cu -- gsr_autotune: tile shape and staging depth of the rig frame.
 //
 // The free parameters of the tiled renderer are the screen tile of each
-// sensor kind and the number of records staged per step of a tile's walk.
+// sensor kind, the number of records staged per step of a tile's walk and
+// the lengths in which long tile lists are split (longer chunks waste less
+// speculative work, shorter ones shorten the critical path).
 // Small tiles shorten each ray's list (fewer evaluations) but duplicate
 // more surfel/tile pairs (more sorting); the staging depth trades shared
 // memory (occupancy) against barrier and copy overhead.  Neither changes a
@@ -22,12 +24,13 @@ struct Candidate {
     int cam[2];
     int lid[2];
     int bd;
+    int sf, sc;  // split_first, split_chunk
 };
 
 bool same(const Candidate& a, const Candidate& b)
 {
     return a.cam[0] == b.cam[0] && a.cam[1] == b.cam[1] && a.lid[0] == b.lid[0] && a.lid[1] == b.lid[1] &&
-           a.bd == b.bd;
+           a.bd == b.bd && a.sf == b.sf && a.sc == b.sc;
 }
 
 // The plan of a candidate: the input plan's sensors and capacity with every
@@ -43,6 +46,8 @@ gsr_status candidate_plan(const gsr_plan* base, const Candidate& c, gsr_plan* ou
     }
     gsr_tiling tiling = base->tiling;
     tiling.batch_depth = c.bd;
+    tiling.split_first = c.sf;
+    tiling.split_chunk = c.sc;
     return gsr_plan_init(out, base->n_surfels, sensors, base->n_sensors, &tiling, base->max_dup);
 }
 
@@ -60,25 +65,25 @@ void plan_tile(const gsr_plan* p, int kind, int t[2])
         }
 }
 
-std::vector<Candidate> all_candidates(const gsr_plan* plan, const gsr_autotune_space* sp, Candidate start)
+// Every tile pair of the space (the workspace depends on the tiles only).
+std::vector<Candidate> all_candidates(const gsr_autotune_space* sp, Candidate start)
 {
     std::vector<Candidate> v{start};
-    for (int i = 0; i < sp->n_camera_tiles; ++i) {
-        Candidate c = start;
-        c.cam[0] = sp->camera_tiles[i][0];
-        c.cam[1] = sp->camera_tiles[i][1];
-        for (int j = 0; j < sp->n_lidar_tiles || j == 0; ++j) {
+    const int nc = sp->n_camera_tiles > 0 ? sp->n_camera_tiles : 1;
+    const int nl = sp->n_lidar_tiles > 0 ? sp->n_lidar_tiles : 1;
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nl; ++j) {
+            Candidate c = start;
+            if (sp->n_camera_tiles) {
+                c.cam[0] = sp->camera_tiles[i][0];
+                c.cam[1] = sp->camera_tiles[i][1];
+            }
             if (sp->n_lidar_tiles) {
                 c.lid[0] = sp->lidar_tiles[j][0];
                 c.lid[1] = sp->lidar_tiles[j][1];
             }
-            for (int k = 0; k < sp->n_batch_depths || k == 0; ++k) {
-                if (sp->n_batch_depths) c.bd = sp->batch_depths[k];
-                v.push_back(c);
-            }
+            v.push_back(c);
         }
-    }
-    (void)plan;
     return v;
 }
 
@@ -88,6 +93,8 @@ bool space_ok(const gsr_autotune_space* sp)
     if (sp->n_camera_tiles < 0 || sp->n_camera_tiles > GSR_AUTOTUNE_MAX) return false;
     if (sp->n_lidar_tiles < 0 || sp->n_lidar_tiles > GSR_AUTOTUNE_MAX) return false;
     if (sp->n_batch_depths < 0 || sp->n_batch_depths > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_split_firsts < 0 || sp->n_split_firsts > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_split_chunks < 0 || sp->n_split_chunks > GSR_AUTOTUNE_MAX) return false;
     return true;
 }
 
@@ -101,9 +108,10 @@ extern "C" gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gs
     plan_tile(plan, GSR_SENSOR_PINHOLE, start.cam);
     plan_tile(plan, GSR_SENSOR_LIDAR, start.lid);
     start.bd = plan->tiling.batch_depth;
-    // the workspace depends on the tiles only; bound it over every tile pair
+    start.sf = plan->tiling.split_first;
+    start.sc = plan->tiling.split_chunk;
     size_t best = 0;
-    for (const Candidate& c : all_candidates(plan, space, start)) {
+    for (const Candidate& c : all_candidates(space, start)) {
         gsr_plan p;
         const gsr_status st = candidate_plan(plan, c, &p);
         if (st != GSR_OK) return st;
@@ -170,6 +178,8 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     plan_tile(plan, GSR_SENSOR_PINHOLE, best.cam);
     plan_tile(plan, GSR_SENSOR_LIDAR, best.lid);
     best.bd = plan->tiling.batch_depth;
+    best.sf = plan->tiling.split_first;
+    best.sc = plan->tiling.split_chunk;
     float best_ms = -1.f;
     std::vector<std::pair<Candidate, float>> seen;
     auto visit = [&](const Candidate& c) -> gsr_status {
@@ -184,6 +194,8 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
             t.camera_tile[0] = c.cam[0]; t.camera_tile[1] = c.cam[1];
             t.lidar_tile[0] = c.lid[0]; t.lidar_tile[1] = c.lid[1];
             t.batch_depth = c.bd;
+            t.split_first = c.sf;
+            t.split_chunk = c.sc;
             t.ms = ms;
         }
         if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
@@ -208,6 +220,16 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     for (int i = 0; r == GSR_OK && i < space->n_batch_depths; ++i) {
         Candidate c = best;
         c.bd = space->batch_depths[i];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_split_firsts; ++i) {
+        Candidate c = best;
+        c.sf = space->split_firsts[i];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_split_chunks; ++i) {
+        Candidate c = best;
+        c.sc = space->split_chunks[i];
         r = visit(c);
     }
     cudaEventDestroy(e0);

@@ -36,10 +36,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;               // items per thread per sort tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kRadixBits = 8;
-#ifndef GSR_SPLIT_CHUNK
-#define GSR_SPLIT_CHUNK 2048
-#endif
-constexpr int kSplitChunk = GSR_SPLIT_CHUNK;  // list positions per chunk of a split tile
+// Default split of long tile lists (gsr_tiling.split_first / split_chunk = 0).
+constexpr int kSplitFirstDefault = 16384;  // positions walked before a tile's list is split
+constexpr int kSplitChunkDefault = 384;    // positions per later chunk
 constexpr int kRayWords = 13;             // words of a stored per-ray compositing state
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -99,8 +98,15 @@ struct SensorTable {
     int tile_w, tile_h;
     int total_tiles;
     int batch;  // records staged per step of a walk; 0 = the CTA's thread count
+    int split_first, split_chunk;  // long lists: chunk 0 = split_first positions, then split_chunk each
     SensorDev s[GSR_MAX_SENSORS];
 };
+
+// First list position of chunk c of a split tile.
+__host__ __device__ __forceinline__ int chunk_begin(int first, int chunk, int c)
+{
+    return c == 0 ? 0 : first + (c - 1) * chunk;
+}
 
 // Host helper: the workspace region pointer.
 template <class T>

@@ -280,8 +280,10 @@ __device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ra
 }
 
 // ------------------------------------------------------------- split tiles
-// A tile whose list is longer than kSplitChunk is walked in chunks of
-// kSplitChunk positions.  Chunk 0 is walked like any tile (with each ray's
+// A tile whose list is longer than `first` positions is walked in chunks:
+// chunk 0 = the first `first` positions, then chunks of `chunk` positions
+// (gsr_tiling.split_first / split_chunk).  Chunk 0 is walked like any tile
+// (with each ray's
 // stop rule).  If rays are still alive after it, their state is stored
 // (the carry) and chunks 1..C are walked in parallel by other CTAs, each
 // from T = 1 with the same stop rule (a partial).  Exactness: with T_s the
@@ -296,6 +298,7 @@ struct SplitBufs {
     uint2* state;       // per tile: x = 1 carry stored / 2 finished in chunk 0, y = chunks not yet walked
     const uint2* items; // (tile, chunk)
     float* rays;        // ray records, kRayWords words each
+    int first, chunk;   // chunk 0 = [0, first), then chunks of `chunk` positions
 };
 
 __device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, int R, int k)
@@ -317,7 +320,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile,
     ray_init(s, !ray.inside, (uint32_t)n);
     const uint4 info = sp.info[tile];
     const bool split = info.x > 0;
-    walk_list<KIND>(sd, ray, range.x, 0, split ? kSplitChunk : n, rec, pval, s, counters, buf, bars, gb, D);
+    walk_list<KIND>(sd, ray, range.x, 0, split ? sp.first : n, rec, pval, s, counters, buf, bars, gb, D);
     if (split) {
         const int R = sd.tile_w * sd.tile_h;
         if (!__syncthreads_and(s.done)) {
@@ -353,7 +356,8 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
             done = carry.done;
         }
         ray_init(s, done, (uint32_t)n);
-        walk_list<KIND>(sd, ray, range.x, c * kSplitChunk, min(n, (c + 1) * kSplitChunk), rec, pval, s, counters,
+        walk_list<KIND>(sd, ray, range.x, chunk_begin(sp.first, sp.chunk, c),
+                        min(n, chunk_begin(sp.first, sp.chunk, c + 1)), rec, pval, s, counters,
                         buf, bars, gb, D);
         if (r < R) store_ray(ray_block(sp, info.y, R, c), R, r, s);
         __threadfence();
@@ -395,7 +399,8 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
             // rays that stop inside chunk k walk it again from their state
             const bool was = S.done;
             S.done = S.done || !need;
-            walk_list<KIND>(sd, ray, range.x, k * kSplitChunk, min(n, (k + 1) * kSplitChunk), rec, pval, S,
+            walk_list<KIND>(sd, ray, range.x, chunk_begin(sp.first, sp.chunk, k),
+                            min(n, chunk_begin(sp.first, sp.chunk, k + 1)), rec, pval, S,
                             counters, buf, bars, gb, D);
             if (!need) S.done = was;
         }
@@ -538,6 +543,9 @@ SplitBufs split_bufs(const gsr_plan* p, const void* ws)
     sp.state = region<uint2>(p, ws, R_SPLIT_STATE);
     sp.items = region<uint2>(p, ws, R_SPLIT_ITEMS);
     sp.rays = region<float>(p, ws, R_SPLIT_RAYS);
+    const SensorTable tab = make_sensor_table(p);
+    sp.first = tab.split_first;
+    sp.chunk = tab.split_chunk;
     return sp;
 }
 

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
 }
 
 // Split plan of the frame (one CTA, tiles in id order): a tile whose list is
-// longer than kSplitChunk gets C = ceil(len / kSplitChunk) - 1 chunks after
+// longer than F = split_first gets C = ceil((len - F) / split_chunk) chunks after
 // its first and (C + 1) x rays ray records (its carry and one block per
 // chunk), while the running total fits the capacity; items (tile, c),
 // c = 1..C, are listed in tile order.  Deterministic: the outcome depends
@@ -605,8 +605,8 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
         unsigned long long need = 0;
         if (t < n_tiles) {
             const uint32_t len = ranges[t].y - ranges[t].x;
-            if (len > (uint32_t)kSplitChunk) {
-                C = (len - 1) / kSplitChunk;
+            if (len > (uint32_t)tab.split_first) {
+                C = (len - (uint32_t)tab.split_first - 1) / (uint32_t)tab.split_chunk + 1;
                 int s = 0;
                 while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
                 need = (unsigned long long)(C + 1) * (unsigned long long)(tab.s[s].tile_w * tab.s[s].tile_h);

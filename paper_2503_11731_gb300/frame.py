@@ -57,13 +57,15 @@ class Renderer:
     """One plan (surfel count, sensors, tiling) with its workspace and outputs."""
 
     def __init__(self, n_surfels, sensors, tile=(16, 16), max_dup=0, bg=(0.0, 0.0, 0.0), device="cuda",
-                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"), tiles=None, batch_depth=0):
+                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"), tiles=None, batch_depth=0,
+                 split=(0, 0)):
         """`tile` is the default tiling; `tiles` (optional) a per-sensor list of (w, h) or None;
-        `batch_depth` the records staged per step of a tile walk (0 = the CTA's thread count)."""
+        `batch_depth` the records staged per step of a tile walk (0 = the CTA's thread count);
+        `split` = (split_first, split_chunk) of long tile lists (0 = the library's defaults)."""
         self.descs = list(sensors)
         tiles = tiles if tiles is not None else [None] * len(self.descs)
         self.structs = [gsr.sensor(d, bg, t) for d, t in zip(self.descs, tiles)]
-        self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup, batch_depth)
+        self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup, batch_depth, split)
         self.ws_bytes = gsr.workspace_size(self.plan)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
         base = self.ws.data_ptr()
@@ -162,13 +164,15 @@ class Renderer:
 
     def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
                  lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (8, 16), (16, 16)), batch_depths=(64, 128, 256),
-                 warmup=1, reps=3, stream=None):
+                 split_firsts=(8192, 16384, 32768), split_chunks=(256, 384, 512, 1024), warmup=1, reps=3,
+                 stream=None):
         """Pick the tiling of this rig with gsr_autotune over `parts` (DeviceSurfels
         consecutive in the plan) and re-plan with it; returns the trial list."""
         obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
         has = {d.kind for d in self.descs}
         space = gsr.autotune_space(camera_tiles if "pinhole" in has else (),
-                                   lidar_tiles if "lidar" in has else (), batch_depths, warmup, reps)
+                                   lidar_tiles if "lidar" in has else (), batch_depths, warmup, reps,
+                                   split_firsts, split_chunks)
         need = gsr.autotune_workspace_size(self.plan, space)
         self._alloc_workspace(need)
         res = gsr.autotune(self.plan, [p.struct() for p in parts], obj, space, self.ws_ptr, need,
@@ -177,9 +181,11 @@ class Renderer:
         self.ws_bytes = gsr.workspace_size(self.plan)
         self._alloc_workspace(self.ws_bytes)
         trials = [{"camera_tile": tuple(t.camera_tile), "lidar_tile": tuple(t.lidar_tile),
-                   "batch_depth": t.batch_depth, "ms": t.ms} for t in res.tried[:res.n_tried]]
+                   "batch_depth": t.batch_depth, "split": (t.split_first, t.split_chunk), "ms": t.ms}
+                  for t in res.tried[:res.n_tried]]
         return {"best_ms": res.best_ms, "trials": trials, "camera_tile": self.tile_of("pinhole"),
-                "lidar_tile": self.tile_of("lidar"), "batch_depth": self.plan.tiling.batch_depth}
+                "lidar_tile": self.tile_of("lidar"), "batch_depth": self.plan.tiling.batch_depth,
+                "split": (self.plan.tiling.split_first, self.plan.tiling.split_chunk)}
 
     def tile_of(self, kind):
         for i, d in enumerate(self.descs):

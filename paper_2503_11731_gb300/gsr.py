@@ -40,7 +40,8 @@ class Sensor(ctypes.Structure):
 
 
 class Tiling(ctypes.Structure):
-    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch_depth", c_i32)]
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch_depth", c_i32), ("split_first", c_i32),
+                ("split_chunk", c_i32)]
 
 
 class Plan(ctypes.Structure):
@@ -98,16 +99,19 @@ class AutotuneSpace(ctypes.Structure):
     _fields_ = [("n_camera_tiles", c_i32), ("camera_tiles", (c_i32 * 2) * AUTOTUNE_MAX),
                 ("n_lidar_tiles", c_i32), ("lidar_tiles", (c_i32 * 2) * AUTOTUNE_MAX),
                 ("n_batch_depths", c_i32), ("batch_depths", c_i32 * AUTOTUNE_MAX),
+                ("n_split_firsts", c_i32), ("split_firsts", c_i32 * AUTOTUNE_MAX),
+                ("n_split_chunks", c_i32), ("split_chunks", c_i32 * AUTOTUNE_MAX),
                 ("warmup", c_i32), ("reps", c_i32)]
 
 
 class AutotuneTrial(ctypes.Structure):
-    _fields_ = [("camera_tile", c_i32 * 2), ("lidar_tile", c_i32 * 2), ("batch_depth", c_i32), ("ms", c_f32)]
+    _fields_ = [("camera_tile", c_i32 * 2), ("lidar_tile", c_i32 * 2), ("batch_depth", c_i32),
+                ("split_first", c_i32), ("split_chunk", c_i32), ("ms", c_f32)]
 
 
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("plan", Plan), ("best_ms", c_f32), ("n_tried", c_i32),
-                ("tried", AutotuneTrial * (3 * AUTOTUNE_MAX + 1))]
+                ("tried", AutotuneTrial * (5 * AUTOTUNE_MAX + 1))]
 
 
 DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
@@ -231,10 +235,11 @@ def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None) -> Sensor:
     return s
 
 
-def plan_init(n_surfels: int, sensors, tile=(16, 16), max_dup: int = 0, batch_depth: int = 0) -> Plan:
+def plan_init(n_surfels: int, sensors, tile=(16, 16), max_dup: int = 0, batch_depth: int = 0, split=(0, 0)) -> Plan:
+    """split = (split_first, split_chunk) of long tile lists; 0 = the library's default."""
     arr = (Sensor * len(sensors))(*sensors)
     p = Plan()
-    t = Tiling(int(tile[0]), int(tile[1]), int(batch_depth))
+    t = Tiling(int(tile[0]), int(tile[1]), int(batch_depth), int(split[0]), int(split[1]))
     _check(lib().gsr_plan_init(ctypes.byref(p), int(n_surfels), arr, len(sensors), ctypes.byref(t), int(max_dup)),
            "gsr_plan_init")
     return p
@@ -324,7 +329,8 @@ def render_rig(plan, ws, ws_bytes, outs, stream):
     _check(lib().gsr_render_rig(ctypes.byref(plan), ws, ws_bytes, cams, lids, stream), "gsr_render_rig")
 
 
-def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, reps=3) -> AutotuneSpace:
+def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, reps=3, split_firsts=(),
+                   split_chunks=()) -> AutotuneSpace:
     sp = AutotuneSpace()
     for name, vals in (("camera_tiles", camera_tiles), ("lidar_tiles", lidar_tiles)):
         if len(vals) > AUTOTUNE_MAX:
@@ -333,11 +339,14 @@ def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, r
         arr = getattr(sp, name)
         for i, (w, h) in enumerate(vals):
             arr[i][0], arr[i][1] = int(w), int(h)
-    if len(batch_depths) > AUTOTUNE_MAX:
-        raise ValueError(f"at most {AUTOTUNE_MAX} batch_depths")
-    sp.n_batch_depths = len(batch_depths)
-    for i, d in enumerate(batch_depths):
-        sp.batch_depths[i] = int(d)
+    for name, vals in (("batch_depths", batch_depths), ("split_firsts", split_firsts),
+                       ("split_chunks", split_chunks)):
+        if len(vals) > AUTOTUNE_MAX:
+            raise ValueError(f"at most {AUTOTUNE_MAX} {name}")
+        setattr(sp, "n_" + name, len(vals))
+        arr = getattr(sp, name)
+        for i, d in enumerate(vals):
+            arr[i] = int(d)
     sp.warmup, sp.reps = int(warmup), int(reps)
     return sp
 

@@ -217,3 +217,45 @@ def test_autotune_picks_the_fastest_measured_tiling(gpu_lib):
         for key in (("rgb", "depth") if "rgb" in oa else ("intensity", "range")):
             scale = 1.0 if key in ("rgb", "intensity") else max(1.0, float(oa[key].abs().max()))
             assert (oa[key] - ob[key]).abs().max() <= 1e-4 * scale, (i, key)
+
+
+def test_split_lists_match_oracle_and_unsplit_render(gpu_lib):
+    """Force every list longer than 256 positions to split into 64-position
+    chunks: the merged frame matches the oracle and the unsplit frame (to
+    the reassociated transmittance products)."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    scene, poses, sensors = _small_rig()
+    d = DeviceSurfels.from_host(scene)
+    P = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk")
+    whole = Renderer(scene.n, sensors, tiles=TILES, outputs=outs, split=(1 << 24, 1 << 24))
+    ref = [{k: v.clone() for k, v in o.items()} for o in whole.render_rig(d, P)]
+    r = Renderer(scene.n, sensors, tiles=TILES, outputs=outs, split=(256, 64))
+    out = r.render_rig(d, P)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    # the split path really ran: some lists are longer than 256
+    ranges = r.region(6, torch.int32).view(-1, 2)
+    assert int((ranges[:, 1] - ranges[:, 0]).max()) > 4 * 256
+    for i, (oa, ob) in enumerate(zip(ref, out)):
+        for key in (("rgb", "depth") if "rgb" in oa else ("intensity", "range")):
+            scale = 1.0 if key in ("rgb", "intensity") else max(1.0, float(oa[key].abs().max()))
+            assert (oa[key] - ob[key]).abs().max() <= 1e-5 * scale, (i, key)
+        # the same stop positions and last contributors, except at rare rounding flips
+        assert (oa["n_walk"] != ob["n_walk"]).float().mean() <= 1e-3
+    g = [{k: v.cpu().numpy() for k, v in o.items()} for o in out]
+    rng = np.random.default_rng(11)
+    for s, gg in zip(sensors, g):
+        idx = rng.choice(s.width * s.height, 400, replace=False)
+        yy, xx = np.divmod(idx, s.width)
+        if s.kind == "lidar":
+            o = OR.render_lidar(scene, s, rays=idx, obj_pose=poses)
+            ok = o["flip"] <= 2e-5
+            assert np.abs(gg["intensity"][yy, xx] - o["intensity"])[ok].max() <= 1e-4
+            m = ok & (o["alpha"] >= 0.01)
+            assert (np.abs(gg["range"][yy, xx] - o["range"]) / o["range"].clip(1e-12))[m].max() <= 1e-4
+        else:
+            o = OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses)
+            ok = o["flip"] <= 2e-5
+            rgb = np.moveaxis(gg["rgb"], 0, -1)[yy, xx]
+            assert np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4

@@ -16,6 +16,10 @@ tiles).  Inputs are resident in HBM and
 larger than L2 (anchors 91 MB + decoded table 168 MB + objects 260 MB), so
 no flush is needed.
 
+The "backward_step" block times one training step of the reconstruction
+workload (2M surfels, one 1920x1080 camera: forward, loss, backward to the
+surfel parameters).
+
 The "compare" block times, on the same plan and workspace, the explicit
 forms of the frame: the 3M-surfel SH-3 table the anchors were grouped from
 (+ the same objects) rendered batched (two graphs) and per sensor
@@ -314,6 +318,58 @@ def check_status(r):
     return nvis, npairs
 
 
+def backward_step(args, stream):
+    """One training step of the reconstruction workload: 2M-surfel SH-3
+    driving scene, one 1920x1080 camera, loss L1 + 0.1 distortion + 0.05
+    normal consistency against the render of a perturbed copy; forward
+    (preprocess, sort, composite) + loss + backward (reverse rasteriser,
+    preprocess backward to position, scales, rotation, opacity, SH)."""
+    import torch
+    from paper_2503_11731_gb300 import synth
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, camera_backward, camera_loss
+    s = synth.driving_scene(n=2_000_000, seed=synth.SEED_BASE + 3)
+    tgt = synth.perturbed(s, seed=synth.SEED_BASE + 30)
+    cam = synth.driving_camera()
+    r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=("rgb", "depth", "normal", "alpha", "trans", "depth_acc",
+                                                       "n_contrib"))
+    r.render(DeviceSurfels.from_host(tgt))
+    target = r.out[0]["rgb"].clone()
+    d = DeviceSurfels.from_host(s)
+    grads = {k: torch.zeros_like(getattr(d, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh")}
+    names = ("forward", "loss", "backward")
+    ev = {k: [] for k in names}
+
+    def step(record):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        for g in grads.values():
+            g.zero_()
+        if record:
+            e[0].record(stream)
+        r.render(d)
+        if record:
+            e[1].record(stream)
+        loss, lo = camera_loss(r, 0, target)
+        if record:
+            e[2].record(stream)
+        camera_backward(r, 0, lo.struct(), d, out=grads)
+        if record:
+            e[3].record(stream)
+            for k, (a, b) in zip(names, ((e[0], e[1]), (e[1], e[2]), (e[2], e[3]))):
+                ev[k].append((a, b))
+        return loss
+
+    for _ in range(2):
+        step(False)
+    k = max(3, args.steps // 2)
+    ms = timed(stream, k, lambda: step(True))
+    loss = float(step(False)[0])
+    torch.cuda.synchronize()
+    return {"workload": "2M-surfel SH-3 driving scene, 1920x1080 camera, 16x8 tiles, loss vs a perturbed copy",
+            "ms_per_step": ms, "stage_ms": {k: float(np.mean([a.elapsed_time(b) for a, b in v]))
+                                            for k, v in ev.items()},
+            "loss": loss, "steps": k}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -492,6 +548,9 @@ def run_gpu(args):
         }
         del gf, gr
 
+    # ---- backward step of the reconstruction workload (2M surfels, 1920x1080)
+    bwd = backward_step(args, stream) if args.backward else None
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -545,6 +604,7 @@ def run_gpu(args):
         "gpu_launches": n_launch * args.steps,
         "compare": compare,
         "autotune": tuned,
+        "backward_step": bwd,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -572,6 +632,8 @@ def main():
     ap.add_argument("--sample-rays", type=int, default=16)
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the explicit-form and decode-only timings")
+    ap.add_argument("--no-backward", dest="backward", action="store_false",
+                    help="skip the backward-step timing (2M surfels, 1920x1080)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -192,6 +192,23 @@ __global__ void k_loss_reduce(const float* __restrict__ partial, int nblocks, fl
 }
 
 // ======================================================= backward rasteriser
+constexpr int kGradComponents = 20;  // record-gradient floats written (r0..r4)
+
+struct TileRayBox {
+    int x, y;
+    bool live;
+};
+
+// Ray-index box (x0, x1, y0, y1) of the warp's live rays (empty if none).
+__device__ __forceinline__ float4 warp_ray_box(const TileRayBox& r)
+{
+    const int x0 = __reduce_min_sync(0xffffffffu, r.live ? r.x : 0x7fffffff);
+    const int x1 = __reduce_max_sync(0xffffffffu, r.live ? r.x : -1);
+    const int y0 = __reduce_min_sync(0xffffffffu, r.live ? r.y : 0x7fffffff);
+    const int y1 = __reduce_max_sync(0xffffffffu, r.live ? r.y : -1);
+    return make_float4((float)x0, (float)x1, (float)y0, (float)y1);
+}
+
 struct BwdArgs {
     const float* trans;
     const uint32_t* n_contrib;
@@ -258,6 +275,11 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
     float Aa = 0.f, Ba = 0.f, Da = 0.f, Na[3] = {0.f, 0.f, 0.f};
 
     uint32_t m = __reduce_max_sync(0xffffffffu, last);
+    const uint32_t wlast = m;  // this warp's rays look at positions < wlast only
+    const int lane = tid & 31;
+    TileRayBox trb;
+    trb.x = x; trb.y = y; trb.live = inside && last > 0;
+    const float4 wbox = warp_ray_box(trb);
     if ((tid & 31) == 0) wmax[tid >> 5] = m;
     __syncthreads();
     uint32_t maxlast = 0;
@@ -289,83 +311,99 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
         const int lo = max(0, hi - nthr);
         const float4* Bf = buf + (size_t)(b & 1) * nthr * kRecordF4;
         const uint32_t* Sl = sslot + (b & 1) * nthr;
-        for (int j = hi - 1; j >= lo && ok; --j) {
-            const bool active = (uint32_t)j < last;
-            if (!__any_sync(0xffffffffu, active)) continue;
-            const float4* Rj = Bf + (j - lo) * kRecordF4;
-            Splat sp;
-            bool contrib = active && splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, sd.near_plane, columns, sp);
-            float g[20];
+        // groups of 32 positions from the back; a lane per position tests the
+        // record's support box against the box of the warp's active rays
+        for (int g1 = hi; g1 > lo && ok; g1 -= 32) {
+            const int g0 = max(lo, g1 - 32);
+            const int jt = g0 + lane;
+            const bool meet = jt < g1 && box_meets<KIND>(Bf[(jt - lo) * kRecordF4 + 5], wbox, columns) &&
+                              (uint32_t)jt < wlast;
+            uint32_t mask = __ballot_sync(0xffffffffu, meet);
+            while (mask) {
+                const int bit = 31 - __clz(mask);  // the highest position first
+                mask &= ~(1u << bit);
+                const int j = g0 + bit;
+                const bool active = (uint32_t)j < last;
+                const float4* Rj = Bf + (j - lo) * kRecordF4;
+                Splat sp;
+                bool contrib = active && splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, sd.near_plane, columns, sp);
+                if (!__any_sync(0xffffffffu, contrib)) continue;
+                float g[32];
 #pragma unroll
-            for (int k = 0; k < 20; ++k) g[k] = 0.f;
-            if (contrib) {
-                const float al = sp.alpha, z = sp.z;
-                const float om = 1.f - al;
-                T = T / om;  // transmittance in front of this surfel
-                const float w = al * T;
-                const float4 r3 = Rj[3], r4 = Rj[4];
-                const float io = 1.f / om;
-                float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
-                float c[3] = {r3.y, r3.z, r3.w};
-                if (KIND == GSR_SENSOR_PINHOLE) {
-                    const float n[3] = {r4.x, r4.y, r4.z};
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        dal += gC[k] * (T * c[k] - Ca[k] * io) + gN[k] * (T * n[k] - Na[k] * io);
-                        Ca[k] = fmaf(w, c[k], Ca[k]);
-                        Na[k] = fmaf(w, n[k], Na[k]);
-                        g[13 + k] = w * gC[k];   // colour
-                        g[16 + k] = w * gN[k];   // normal
-                    }
-                } else {
-                    dal += gC[0] * (T * c[0] - Ca[0] * io);
-                    Ca[0] = fmaf(w, c[0], Ca[0]);
-                    g[13] = w * gC[0];
-                }
-                Aa += w;
-                Ba = fmaf(w, z, Ba);
-                Da = fmaf(w * z, z, Da);
-                const float dz = w * (gB + 2.f * z * gD);
-                const float o = r3.x;
-                float dG = 0.f;
-                if (o * sp.G < kAlphaMax) {
-                    g[12] = dal * sp.G;  // opacity
-                    dG = dal * o;
-                }
-                const float drho = -0.5f * sp.G * dG;
-                if (sp.use3) {
-                    const float iq = 1.f / sp.q2;
-                    const float dq0 = 2.f * sp.u * iq * drho;
-                    const float dq1 = 2.f * sp.v * iq * drho;
-                    const float dq2 = -2.f * sp.rho * iq * drho - sp.z * iq * dz;
-                    g[11] = dz * iq;  // det
-                    float r0, r1, r2;
+                for (int k = 0; k < 32; ++k) g[k] = 0.f;
+                if (contrib) {
+                    const float al = sp.alpha, z = sp.z;
+                    const float om = 1.f - al;
+                    T = T / om;  // transmittance in front of this surfel
+                    const float w = al * T;
+                    const float4 r3 = Rj[3], r4 = Rj[4];
+                    const float io = 1.f / om;
+                    float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
+                    float c[3] = {r3.y, r3.z, r3.w};
                     if (KIND == GSR_SENSOR_PINHOLE) {
-                        r0 = sp.dx; r1 = sp.dy; r2 = 1.f;
-                        const float4 q0 = Rj[0], q1 = Rj[1], q2 = Rj[2];
-                        g[3] = -(dq0 * q0.x + dq1 * q1.x + dq2 * q2.x);  // centre x
-                        g[7] = -(dq0 * q0.y + dq1 * q1.y + dq2 * q2.y);  // centre y
+                        const float n[3] = {r4.x, r4.y, r4.z};
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            dal += gC[k] * (T * c[k] - Ca[k] * io) + gN[k] * (T * n[k] - Na[k] * io);
+                            Ca[k] = fmaf(w, c[k], Ca[k]);
+                            Na[k] = fmaf(w, n[k], Na[k]);
+                            g[13 + k] = w * gC[k];   // colour
+                            g[16 + k] = w * gN[k];   // normal
+                        }
                     } else {
-                        r0 = d0; r1 = d1; r2 = d2;
+                        dal += gC[0] * (T * c[0] - Ca[0] * io);
+                        Ca[0] = fmaf(w, c[0], Ca[0]);
+                        g[13] = w * gC[0];
                     }
-                    g[0] = dq0 * r0; g[1] = dq0 * r1; g[2] = dq0 * r2;
-                    g[4] = dq1 * r0; g[5] = dq1 * r1; g[6] = dq1 * r2;
-                    g[8] = dq2 * r0; g[9] = dq2 * r1; g[10] = dq2 * r2;
-                } else {
-                    g[3] = -2.f * kLowPassInvVar * sp.dx * drho;
-                    g[7] = -2.f * kLowPassInvVar * sp.dy * drho;
-                    g[19] = dz;  // centre depth
+                    Aa += w;
+                    Ba = fmaf(w, z, Ba);
+                    Da = fmaf(w * z, z, Da);
+                    const float dz = w * (gB + 2.f * z * gD);
+                    const float o = r3.x;
+                    float dG = 0.f;
+                    if (o * sp.G < kAlphaMax) {
+                        g[12] = dal * sp.G;  // opacity
+                        dG = dal * o;
+                    }
+                    const float drho = -0.5f * sp.G * dG;
+                    if (sp.use3) {
+                        const float iq = 1.f / sp.q2;
+                        const float dq0 = 2.f * sp.u * iq * drho;
+                        const float dq1 = 2.f * sp.v * iq * drho;
+                        const float dq2 = -2.f * sp.rho * iq * drho - sp.z * iq * dz;
+                        g[11] = dz * iq;  // det
+                        float r0, r1, r2;
+                        if (KIND == GSR_SENSOR_PINHOLE) {
+                            r0 = sp.dx; r1 = sp.dy; r2 = 1.f;
+                            const float4 q0 = Rj[0], q1 = Rj[1], q2 = Rj[2];
+                            g[3] = -(dq0 * q0.x + dq1 * q1.x + dq2 * q2.x);  // centre x
+                            g[7] = -(dq0 * q0.y + dq1 * q1.y + dq2 * q2.y);  // centre y
+                        } else {
+                            r0 = d0; r1 = d1; r2 = d2;
+                        }
+                        g[0] = dq0 * r0; g[1] = dq0 * r1; g[2] = dq0 * r2;
+                        g[4] = dq1 * r0; g[5] = dq1 * r1; g[6] = dq1 * r2;
+                        g[8] = dq2 * r0; g[9] = dq2 * r1; g[10] = dq2 * r2;
+                    } else {
+                        g[3] = -2.f * kLowPassInvVar * sp.dx * drho;
+                        g[7] = -2.f * kLowPassInvVar * sp.dy * drho;
+                        g[19] = dz;  // centre depth
+                    }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
+                // reduce-scatter over the warp: after it lane l holds the sum of
+                // component l over the 32 rays (5 halving exchanges, 31 shuffles)
 #pragma unroll
-                for (int k = 0; k < 20; ++k) g[k] = warp_sum(g[k]);
-                if ((tid & 31) == 0) {
-                    float* dst = reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4);
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const bool up = (lane & o) != 0;
 #pragma unroll
-                    for (int k = 0; k < 20; ++k)
-                        if (g[k] != 0.f) atomicAdd(dst + k, g[k]);
+                    for (int k = 0; k < o; ++k) {
+                        const float send = up ? g[k] : g[k + o];
+                        const float keep = up ? g[k + o] : g[k];
+                        g[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
                 }
+                if (lane < kGradComponents && g[0] != 0.f)
+                    atomicAdd(reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4) + lane, g[0]);
             }
         }
         __syncthreads();  // buffer b&1 is free for batch b+2

@@ -449,6 +449,20 @@ __device__ __forceinline__ bool footprint_span(const Footprint& f, int ty, int T
 // footprint misses the row).
 constexpr int kSpanRows = 7;
 
+// Does a record's support box r5 meet the warp box?  LiDAR columns are
+// intervals on the azimuth circle of `columns` cells (the warp's never wraps).
+template <int KIND>
+__device__ __forceinline__ bool box_meets(const float4 r5, const float4 w, float columns)
+{
+    const bool rows = r5.w >= w.z && r5.z <= w.w;
+    if (KIND == GSR_SENSOR_PINHOLE) return rows && r5.y >= w.x && r5.x <= w.y;
+    float d = w.x - r5.x;  // warp start inside the record's interval?
+    if (d < 0.f) d += columns;
+    float e = r5.x - w.x;  // record start inside the warp's interval?
+    if (e < 0.f) e += columns;
+    return rows && w.x <= w.y && (d <= r5.y - r5.x || e <= w.y - w.x);
+}
+
 // Per-ray setup shared by the forward and backward rasterisers.
 template <int KIND>
 __device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, float& rx, float& ry, float& d0,

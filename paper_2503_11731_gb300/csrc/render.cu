@@ -106,20 +106,6 @@ __device__ __forceinline__ float4 warp_box(const TileRay& ray, bool done)
     return make_float4((float)x0, (float)x1, (float)y0, (float)y1);
 }
 
-// Does a record's support box r5 meet the warp box?  LiDAR columns are
-// intervals on the azimuth circle of `columns` cells (the warp's never wraps).
-template <int KIND>
-__device__ __forceinline__ bool box_meets(const float4 r5, const float4 w, float columns)
-{
-    const bool rows = r5.w >= w.z && r5.z <= w.w;
-    if (KIND == GSR_SENSOR_PINHOLE) return rows && r5.y >= w.x && r5.x <= w.y;
-    float d = w.x - r5.x;  // warp start inside the record's interval?
-    if (d < 0.f) d += columns;
-    float e = r5.x - w.x;  // record start inside the warp's interval?
-    if (e < 0.f) e += columns;
-    return rows && w.x <= w.y && (d <= r5.y - r5.x || e <= w.y - w.x);
-}
-
 // Walk list positions [lo, hi) of a tile (list starting at `start`) with the
 // whole CTA, continuing each ray's state.  Batches of D records (a multiple
 // of kIlp) are staged by bulk copies, double-buffered; `gb` counts the batches this CTA

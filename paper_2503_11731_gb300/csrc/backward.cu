@@ -219,12 +219,41 @@ struct BwdArgs {
     float4* recgrad;        // [slots][5]
 };
 
+// The tiles of one sensor in the plan's schedule order (longest list first),
+// by a stable compaction of the whole-rig tile order (one CTA).
+__global__ void __launch_bounds__(1024) k_sensor_order(const uint32_t* __restrict__ order, uint32_t n_tiles,
+                                                       uint32_t t0, uint32_t t1, uint32_t* __restrict__ out)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t base_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 < n_tiles; i0 += 1024) {
+        const uint32_t i = i0 + threadIdx.x;
+        const uint32_t t = i < n_tiles ? order[i] : 0xffffffffu;
+        const bool mine = t >= t0 && t < t1;
+        const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int k = 0; k < 32; ++k) {
+            if (k < w) before += wsum[k];
+            total += wsum[k];
+        }
+        if (mine) out[base_s + before + __popc(bal & ((1u << lane) - 1u))] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) base_s += total;
+        __syncthreads();
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int sensor,
                                                          const float4* __restrict__ rec,
                                                          const uint2* __restrict__ ranges,
                                                          const uint32_t* __restrict__ pval, BwdArgs a,
-                                                         uint32_t* counters)
+                                                         uint32_t* counters, const uint32_t* __restrict__ sorder)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
@@ -233,7 +262,7 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
     __shared__ uint32_t wmax[8];
     const SensorDev& sd = tab.s[sensor];
     const int nthr = blockDim.x, tid = threadIdx.x;
-    const int lt = blockIdx.x;
+    const int lt = (int)sorder[blockIdx.x] - sd.tile_base;  // longest lists first
     const int tx = lt % sd.tiles_x, ty = lt / sd.tiles_x;
     const int x = tx * sd.tile_w + tid % sd.tile_w;
     const int y = ty * sd.tile_h + tid / sd.tile_w;
@@ -697,9 +726,13 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    // this sensor's tiles in schedule order (the tile-key scratch of the sort is free)
+    uint32_t* sorder = region<uint32_t>(p, ws, R_TILE_KEY_A);
+    k_sensor_order<<<1, 1024, 0, st>>>(region<uint32_t>(p, ws, R_TILE_VAL_A), (uint32_t)p->tile_base[p->n_sensors],
+                                       (uint32_t)sd.tile_base, (uint32_t)(sd.tile_base + tiles), sorder);
     k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(
         tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a,
-        region<uint32_t>(p, ws, R_COUNTERS));
+        region<uint32_t>(p, ws, R_COUNTERS), sorder);
     return cudaGetLastError();
 }
 

@@ -248,41 +248,61 @@ __global__ void __launch_bounds__(1024) k_sensor_order(const uint32_t* __restric
     }
 }
 
+// Reverse walk of one tile (or of one chunk of a split tile) by the whole
+// CTA: list positions [lo_pos, min(hi_pos, last)) of each ray, from the back.
+// mode 0 starts at the ray's end (T = final transmittance, nothing behind);
+// mode 1 starts at the end of chunk cc of a split tile from the state the
+// forward merge stored there (block cc) and the final state (block C): the
+// contributions behind are the final sums minus those in front.
 template <int KIND>
-__global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int sensor,
-                                                         const float4* __restrict__ rec,
-                                                         const uint2* __restrict__ ranges,
-                                                         const uint32_t* __restrict__ pval, BwdArgs a,
-                                                         uint32_t* counters, const uint32_t* __restrict__ sorder)
+__device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev& sd, int lt, int lo_pos,
+                                         int hi_pos, int mode, const SplitBufs& sp, int cc, const float4* __restrict__ rec,
+                                         const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
+                                         const BwdArgs& a, uint32_t* counters, uint64_t* bars, uint32_t* sslot,
+                                         float4* buf, uint32_t* wmax, uint32_t& gb)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    uint32_t* sslot = reinterpret_cast<uint32_t*>(smem_raw + 128);          // [2][nthr]
-    float4* buf = reinterpret_cast<float4*>(smem_raw + 128 + 2 * 256 * 4);  // [2][nthr][5]
-    __shared__ uint32_t wmax[8];
-    const SensorDev& sd = tab.s[sensor];
     const int nthr = blockDim.x, tid = threadIdx.x;
-    const int lt = (int)sorder[blockIdx.x] - sd.tile_base;  // longest lists first
     const int tx = lt % sd.tiles_x, ty = lt / sd.tiles_x;
     const int x = tx * sd.tile_w + tid % sd.tile_w;
     const int y = ty * sd.tile_h + tid / sd.tile_w;
-    const bool inside = x < sd.width && y < sd.height;
+    const bool inside = tid < sd.tile_w * sd.tile_h && x < sd.width && y < sd.height;
     const size_t HW = (size_t)sd.width * sd.height;
     const size_t pix = (size_t)y * sd.width + x;
-    if (tid == 0) {
-        mbar_init(bars, 1);
-        mbar_init(bars + 1, 1);
-        fence_mbar_init();
-    }
+    const uint32_t tile = (uint32_t)(sd.tile_base + lt);
     float rx, ry, d0, d1, d2;
     ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
-    const uint2 range = ranges[sd.tile_base + lt];
+    const uint2 range = ranges[tile];
     uint32_t last = 0;
     float T = 1.f;
     float gC[3] = {0.f, 0.f, 0.f}, gN[3] = {0.f, 0.f, 0.f}, gA = 0.f, gB = 0.f, gD = 0.f;
+    // accumulated contributions of the surfels behind the current one
+    float Ca[3] = {0.f, 0.f, 0.f};
+    float Aa = 0.f, Ba = 0.f, Da = 0.f, Na[3] = {0.f, 0.f, 0.f};
     if (inside) {
-        last = a.n_contrib[pix];
-        T = a.trans[pix];
+        last = min(a.n_contrib[pix], (uint32_t)hi_pos);
+        if (mode == 0) {
+            T = a.trans[pix];
+            Ca[0] = T * sd.bg[0];
+            Ca[1] = T * sd.bg[1];
+            Ca[2] = T * sd.bg[2];
+        } else {
+            const int R = sd.tile_w * sd.tile_h;
+            const uint4 info = sp.info[tile];
+            RayState Sc, Sf;
+            load_ray(ray_block(sp, info.y, R, cc), R, tid, Sc);
+            load_ray(ray_block(sp, info.y, R, (int)info.x), R, tid, Sf);
+            T = Sc.T;
+            Ca[0] = (Sf.f0 - Sc.f0) + Sf.T * sd.bg[0];
+            Ca[1] = (Sf.f1 - Sc.f1) + Sf.T * sd.bg[1];
+            Ca[2] = (Sf.f2 - Sc.f2) + Sf.T * sd.bg[2];
+            Aa = Sf.A - Sc.A;
+            Ba = Sf.B - Sc.B;
+            Da = Sf.D - Sc.D;
+            Na[0] = Sf.n0 - Sc.n0;
+            Na[1] = Sf.n1 - Sc.n1;
+            Na[2] = Sf.n2 - Sc.n2;
+        }
+        if (last <= (uint32_t)lo_pos) last = 0;  // nothing of this ray in [lo_pos, hi_pos)
         if (a.g_rgb) {
             gC[0] = a.g_rgb[pix];
             gC[1] = a.g_rgb[HW + pix];
@@ -299,9 +319,6 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
             gD = a.g_dacc[HW + pix];
         }
     }
-    // accumulated contributions of the surfels behind the current one
-    float Ca[3] = {T * sd.bg[0], T * sd.bg[1], T * sd.bg[2]};
-    float Aa = 0.f, Ba = 0.f, Da = 0.f, Na[3] = {0.f, 0.f, 0.f};
 
     uint32_t m = __reduce_max_sync(0xffffffffu, last);
     const uint32_t wlast = m;  // this warp's rays look at positions < wlast only
@@ -309,37 +326,42 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
     TileRayBox trb;
     trb.x = x; trb.y = y; trb.live = inside && last > 0;
     const float4 wbox = warp_ray_box(trb);
+    __syncthreads();  // the previous walk's readers of wmax and the buffers are done
     if ((tid & 31) == 0) wmax[tid >> 5] = m;
     __syncthreads();
     uint32_t maxlast = 0;
     for (int k = 0; k < (nthr >> 5); ++k) maxlast = max(maxlast, wmax[k]);
-    const int nb = ((int)maxlast + nthr - 1) / nthr;
+    const int span = maxlast > (uint32_t)lo_pos ? (int)maxlast - lo_pos : 0;
+    const int nb = (span + nthr - 1) / nthr;
     const float columns = (float)sd.width;
 
-    // batch b covers list positions [lo, hi) counted from the end
+    // batch b covers list positions [lo, hi) counted from the end; it is the
+    // CTA's batch g = gb + b (buffer and barrier g & 1, phase (g >> 1) & 1)
     auto issue = [&](int b) {
+        const uint32_t g = gb + (uint32_t)b;
         const int hi = (int)maxlast - b * nthr;
-        const int lo = max(0, hi - nthr);
+        const int lo = max(lo_pos, hi - nthr);
         const int cnt = hi - lo;
-        uint64_t* bar = bars + (b & 1);
-        float4* dst = buf + (size_t)(b & 1) * nthr * kRecordF4;
+        uint64_t* bar = bars + (g & 1);
+        float4* dst = buf + (size_t)(g & 1) * nthr * kRecordF4;
         if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
         if (tid < cnt) {
             const uint32_t slot = pval[range.x + lo + tid];
-            sslot[(b & 1) * nthr + tid] = slot;
+            sslot[(g & 1) * nthr + tid] = slot;
             bulk_g2s(dst + tid * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
         }
     };
     bool ok = true;
     if (nb > 0) issue(0);
     for (int b = 0; b < nb; ++b) {
+        const uint32_t g = gb + (uint32_t)b;
         if (b + 1 < nb) issue(b + 1);
-        if (!mbar_wait_bounded(bars + (b & 1), (b >> 1) & 1, counters)) ok = false;
+        if (!mbar_wait_bounded(bars + (g & 1), (g >> 1) & 1, counters)) ok = false;
         ok = __syncthreads_and(ok);  // block-uniform; slot ids of this batch are visible
         const int hi = (int)maxlast - b * nthr;
-        const int lo = max(0, hi - nthr);
-        const float4* Bf = buf + (size_t)(b & 1) * nthr * kRecordF4;
-        const uint32_t* Sl = sslot + (b & 1) * nthr;
+        const int lo = max(lo_pos, hi - nthr);
+        const float4* Bf = buf + (size_t)(g & 1) * nthr * kRecordF4;
+        const uint32_t* Sl = sslot + (g & 1) * nthr;
         // groups of 32 positions from the back; a lane per position tests the
         // record's support box against the box of the warp's active rays
         for (int g1 = hi; g1 > lo && ok; g1 -= 32) {
@@ -435,11 +457,89 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
                     atomicAdd(reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4) + lane, g[0]);
             }
         }
-        __syncthreads();  // buffer b&1 is free for batch b+2
+        __syncthreads();  // buffer g&1 is free for batch g+2
         if (!ok) {
-            if (b + 1 < nb) mbar_wait_bounded(bars + ((b + 1) & 1), ((b + 1) >> 1) & 1, counters);
-            break;
+            if (b + 1 < nb) mbar_wait_bounded(bars + ((g + 1) & 1), ((g + 1) >> 1) & 1, counters);
+            gb += (uint32_t)min(nb, b + 2);
+            return;
         }
+    }
+    gb += (uint32_t)nb;
+}
+
+// Shared-memory layout of the backward kernels: mbarriers, slot ids, records.
+struct BwdSmem {
+    uint64_t* bars;
+    uint32_t* sslot;
+    float4* buf;
+};
+
+__device__ __forceinline__ BwdSmem bwd_smem(unsigned char* raw)
+{
+    BwdSmem m;
+    m.bars = reinterpret_cast<uint64_t*>(raw);
+    m.sslot = reinterpret_cast<uint32_t*>(raw + 128);          // [2][nthr]
+    m.buf = reinterpret_cast<float4*>(raw + 128 + 2 * 256 * 4);  // [2][nthr][kRecordF4]
+    if (threadIdx.x == 0) {
+        mbar_init(m.bars, 1);
+        mbar_init(m.bars + 1, 1);
+        fence_mbar_init();
+    }
+    return m;
+}
+
+// One CTA per tile of the camera, longest list first.  A split tile (its
+// forward merge stored per-chunk states) walks only its last chunk here; its
+// other chunks are walked by k_render_backward_chunks.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int sensor,
+                                                         const float4* __restrict__ rec,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ pval, BwdArgs a,
+                                                         uint32_t* counters, const uint32_t* __restrict__ sorder,
+                                                         SplitBufs sp)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t wmax[8];
+    const BwdSmem sm = bwd_smem(smem_raw);
+    const SensorDev& sd = tab.s[sensor];
+    const uint32_t tile = sorder[blockIdx.x];  // longest lists first
+    const uint4 info = sp.info[tile];
+    const bool split = info.x > 0 && sp.state[tile].x == 1u;
+    const int lo_pos = split ? chunk_begin(sp.first, sp.chunk, (int)info.x) : 0;
+    uint32_t gb = 0;
+    bwd_tile<KIND>(tab, sd, (int)tile - sd.tile_base, lo_pos, 0x7fffffff, 0, sp, 0, rec, ranges, pval, a, counters,
+                   sm.bars, sm.sslot, sm.buf, wmax, gb);
+}
+
+// Chunks 0..C-1 of the camera's split tiles (persistent; item (tile, c) of
+// the forward's split list walks chunk c - 1 backwards from the state after it).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_render_backward_chunks(SensorTable tab, int sensor,
+                                                                const float4* __restrict__ rec,
+                                                                const uint2* __restrict__ ranges,
+                                                                const uint32_t* __restrict__ pval, BwdArgs a,
+                                                                uint32_t* counters, SplitBufs sp)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t wmax[8], item_s;
+    const BwdSmem sm = bwd_smem(smem_raw);
+    const SensorDev& sd = tab.s[sensor];
+    const uint32_t begin = sp.info[sd.tile_base].z;
+    const uint32_t end = sensor + 1 < tab.n ? sp.info[tab.s[sensor + 1].tile_base].z : counters[C_NITEMS];
+    uint32_t gb = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_s = begin + atomicAdd(&counters[C_SPLIT_QUEUE], 1u);
+        __syncthreads();
+        const uint32_t item = item_s;
+        if (item >= end) break;
+        const uint2 it = sp.items[item];
+        if (sp.state[it.x].x != 1u) continue;  // finished in chunk 0: walked whole by k_render_backward
+        const int cc = (int)it.y - 1;
+        bwd_tile<KIND>(tab, sd, (int)it.x - sd.tile_base, chunk_begin(sp.first, sp.chunk, cc),
+                       chunk_begin(sp.first, sp.chunk, cc + 1), 1, sp, cc, rec, ranges, pval, a, counters, sm.bars,
+                       sm.sslot, sm.buf, wmax, gb);
     }
 }
 
@@ -697,6 +797,8 @@ cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camer
     return cudaGetLastError();
 }
 
+SplitBufs split_bufs(const gsr_plan* p, const void* ws);
+
 cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
                                    const gsr_camera_grad* g, int accumulate, cudaStream_t st)
 {
@@ -730,9 +832,28 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
     uint32_t* sorder = region<uint32_t>(p, ws, R_TILE_KEY_A);
     k_sensor_order<<<1, 1024, 0, st>>>(region<uint32_t>(p, ws, R_TILE_VAL_A), (uint32_t)p->tile_base[p->n_sensors],
                                        (uint32_t)sd.tile_base, (uint32_t)(sd.tile_base + tiles), sorder);
+    const SplitBufs sp = split_bufs(p, ws);
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(
-        tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a,
-        region<uint32_t>(p, ws, R_COUNTERS), sorder);
+        tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a, counters, sorder,
+        sp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the other chunks of split tiles, persistent over the camera's split items
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_render_backward_chunks<GSR_SENSOR_PINHOLE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_backward_chunks<GSR_SENSOR_PINHOLE>,
+                                                           threads, smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(counters + C_SPLIT_QUEUE, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    k_render_backward_chunks<GSR_SENSOR_PINHOLE><<<sms * (per_sm > 0 ? per_sm : 1), threads, smem, st>>>(
+        tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a, counters, sp);
     return cudaGetLastError();
 }
 

@@ -463,6 +463,63 @@ __device__ __forceinline__ bool box_meets(const float4 r5, const float4 w, float
     return rows && w.x <= w.y && (d <= r5.y - r5.x || e <= w.y - w.x);
 }
 
+// Per-ray compositing state.  Stored ray records (split tiles, below) keep
+// its 13 fields in this order, one word each.
+struct RayState {
+    float T, A, B, D;
+    float f0, f1, f2;
+    float n0, n1, n2;
+    uint32_t last;
+    uint32_t walk;
+    bool done;
+};
+
+__device__ __forceinline__ void ray_init(RayState& s, bool done, uint32_t n)
+{
+    s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;
+    s.f0 = s.f1 = s.f2 = 0.f;
+    s.n0 = s.n1 = s.n2 = 0.f;
+    s.last = 0;
+    s.walk = n;
+    s.done = done;
+}
+
+// Ray record block: field f of ray r at blk[f * R + r] (coalesced per field).
+__device__ __forceinline__ void store_ray(float* blk, int R, int r, const RayState& s)
+{
+    blk[0 * R + r] = s.T; blk[1 * R + r] = s.A; blk[2 * R + r] = s.B; blk[3 * R + r] = s.D;
+    blk[4 * R + r] = s.f0; blk[5 * R + r] = s.f1; blk[6 * R + r] = s.f2;
+    blk[7 * R + r] = s.n0; blk[8 * R + r] = s.n1; blk[9 * R + r] = s.n2;
+    blk[10 * R + r] = __uint_as_float(s.last);
+    blk[11 * R + r] = __uint_as_float(s.walk);
+    blk[12 * R + r] = __uint_as_float(s.done ? 1u : 0u);
+}
+
+// Loads bypass L1: the block was written by another CTA of this grid.
+__device__ __forceinline__ void load_ray(const float* blk, int R, int r, RayState& s)
+{
+    s.T = __ldcg(blk + 0 * R + r); s.A = __ldcg(blk + 1 * R + r);
+    s.B = __ldcg(blk + 2 * R + r); s.D = __ldcg(blk + 3 * R + r);
+    s.f0 = __ldcg(blk + 4 * R + r); s.f1 = __ldcg(blk + 5 * R + r); s.f2 = __ldcg(blk + 6 * R + r);
+    s.n0 = __ldcg(blk + 7 * R + r); s.n1 = __ldcg(blk + 8 * R + r); s.n2 = __ldcg(blk + 9 * R + r);
+    s.last = __float_as_uint(__ldcg(blk + 10 * R + r));
+    s.walk = __float_as_uint(__ldcg(blk + 11 * R + r));
+    s.done = __float_as_uint(__ldcg(blk + 12 * R + r)) != 0u;
+}
+
+struct SplitBufs {
+    const uint4* info;  // per tile: x = chunks after the first (0: not split), y = ray-record base, z = first item
+    uint2* state;       // per tile: x = 1 carry stored / 2 finished in chunk 0, y = chunks not yet walked
+    const uint2* items; // (tile, chunk)
+    float* rays;        // ray records, kRayWords words each
+    int first, chunk;   // chunk 0 = [0, first), then chunks of `chunk` positions
+};
+
+__device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, int R, int k)
+{
+    return sp.rays + ((size_t)base + (size_t)k * R) * kRayWords;
+}
+
 // Per-ray setup shared by the forward and backward rasterisers.
 template <int KIND>
 __device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, float& rx, float& ry, float& d0,

@@ -29,50 +29,6 @@ constexpr int kIlp = GSR_ILP;  // records evaluated per step of a ray's walk (di
 #define GSR_RIG_MIN_CTAS 4
 #endif
 
-// Per-ray compositing state.  Stored ray records (split tiles, below) keep
-// its 13 fields in this order, one word each.
-struct RayState {
-    float T, A, B, D;
-    float f0, f1, f2;
-    float n0, n1, n2;
-    uint32_t last;
-    uint32_t walk;
-    bool done;
-};
-
-__device__ __forceinline__ void ray_init(RayState& s, bool done, uint32_t n)
-{
-    s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;
-    s.f0 = s.f1 = s.f2 = 0.f;
-    s.n0 = s.n1 = s.n2 = 0.f;
-    s.last = 0;
-    s.walk = n;
-    s.done = done;
-}
-
-// Ray record block: field f of ray r at blk[f * R + r] (coalesced per field).
-__device__ __forceinline__ void store_ray(float* blk, int R, int r, const RayState& s)
-{
-    blk[0 * R + r] = s.T; blk[1 * R + r] = s.A; blk[2 * R + r] = s.B; blk[3 * R + r] = s.D;
-    blk[4 * R + r] = s.f0; blk[5 * R + r] = s.f1; blk[6 * R + r] = s.f2;
-    blk[7 * R + r] = s.n0; blk[8 * R + r] = s.n1; blk[9 * R + r] = s.n2;
-    blk[10 * R + r] = __uint_as_float(s.last);
-    blk[11 * R + r] = __uint_as_float(s.walk);
-    blk[12 * R + r] = __uint_as_float(s.done ? 1u : 0u);
-}
-
-// Loads bypass L1: the block was written by another CTA of this grid.
-__device__ __forceinline__ void load_ray(const float* blk, int R, int r, RayState& s)
-{
-    s.T = __ldcg(blk + 0 * R + r); s.A = __ldcg(blk + 1 * R + r);
-    s.B = __ldcg(blk + 2 * R + r); s.D = __ldcg(blk + 3 * R + r);
-    s.f0 = __ldcg(blk + 4 * R + r); s.f1 = __ldcg(blk + 5 * R + r); s.f2 = __ldcg(blk + 6 * R + r);
-    s.n0 = __ldcg(blk + 7 * R + r); s.n1 = __ldcg(blk + 8 * R + r); s.n2 = __ldcg(blk + 9 * R + r);
-    s.last = __float_as_uint(__ldcg(blk + 10 * R + r));
-    s.walk = __float_as_uint(__ldcg(blk + 11 * R + r));
-    s.done = __float_as_uint(__ldcg(blk + 12 * R + r)) != 0u;
-}
-
 // One ray of a tile: its pixel / cell, whether it is inside the sensor, and
 // the quantities of its two planes (ray_setup).
 struct TileRay {
@@ -279,19 +235,6 @@ __device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ra
 // chunk merges as C += T_s C_c, T = T_s P_c.  A ray that stops inside chunk
 // c walks that chunk again from T_s, record by record.  The CTA that
 // finishes a tile's last chunk merges them in list order.
-struct SplitBufs {
-    const uint4* info;  // per tile: x = chunks after the first (0: not split), y = ray-record base, z = first item
-    uint2* state;       // per tile: x = 1 carry stored / 2 finished in chunk 0, y = chunks not yet walked
-    const uint2* items; // (tile, chunk)
-    float* rays;        // ray records, kRayWords words each
-    int first, chunk;   // chunk 0 = [0, first), then chunks of `chunk` positions
-};
-
-__device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, int R, int k)
-{
-    return sp.rays + ((size_t)base + (size_t)k * R) * kRayWords;
-}
-
 // Phase A: the tile's list (or its chunk 0).  Threads beyond the tile's rays
 // only help staging.
 template <int KIND>
@@ -390,6 +333,9 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
                             counters, buf, bars, gb, D);
             if (!need) S.done = was;
         }
+        // block k now holds the state after chunk k (the backward starts its
+        // walk of chunk k - 1 there)
+        if (r < R) store_ray(ray_block(sp, info.y, R, k), R, r, S);
     }
     write_ray<KIND>(sd, ray, S, out);
 }

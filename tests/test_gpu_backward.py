@@ -216,3 +216,36 @@ def test_autograd_function_matches_direct_calls(gpu_lib):
     assert float(L) == pytest.approx(L_direct, rel=1e-6)
     for k, p in zip(("pos", "log_scale", "quat", "opacity", "sh"), params):
         np.testing.assert_allclose(p.grad.cpu().numpy(), g_direct[k], rtol=1e-4, atol=1e-7 * np.abs(g_direct[k]).max())
+
+
+def test_split_backward_matches_unsplit(gpu_lib):
+    """Long lists split (forward chunks merged, backward chunks walked in
+    parallel from the states the merge stored) give the gradients of the
+    unsplit walk, to the reassociation of the transmittance products."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, camera_backward, camera_loss
+    s = synth.driving_scene(n=60_000, seed=synth.SEED_BASE + 61, x_range=(-10.0, 40.0), n_boxes=6)
+    tgt = synth.perturbed(s, seed=synth.SEED_BASE + 62)
+    cam = synth.pinhole(320, 192, 200.0, (0.0, 0.0, 1.5), 0.0)
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "depth_acc", "n_contrib")
+    grads = []
+    for split in ((1 << 24, 1 << 24), (256, 64)):
+        r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=outs, split=split)
+        r.render(DeviceSurfels.from_host(tgt))
+        target = r.out[0]["rgb"].clone()
+        d = DeviceSurfels.from_host(s)
+        r.render(d)
+        loss, lo = camera_loss(r, 0, target)
+        g = camera_backward(r, 0, lo.struct(), d)
+        torch.cuda.synchronize()
+        assert r.status()[0] == 0
+        if split[0] == 256:
+            ranges = r.region(6, torch.int32).view(-1, 2)
+            assert int((ranges[:, 1] - ranges[:, 0]).max()) > 8 * 256  # the chunk path ran
+        grads.append({k: v.cpu().numpy() for k, v in g.items()})
+    for k in grads[0]:
+        a, b = grads[0][k], grads[1][k]
+        scale = np.abs(a).max()
+        assert scale > 0, k
+        err = np.abs(a - b).max() / scale
+        print("split vs unsplit gradient", k, err)
+        assert err <= 1e-3, k

@@ -151,15 +151,19 @@ def peaks():
 def oracle_frame_estimate(scene, poses, sensors, n=32, seed=7):
     """Oracle ms per frame from a bounded sample.  Each oracle call has a
     per-sensor fixed cost (Eq. 1 per surfel: transform, SH) and a per-ray
-    cost (a brute-force pass over all surfels); both are measured per sensor
-    from calls with n and 2n rays and combined for the full frame."""
+    cost (a brute-force pass over all surfels); per sensor, a call on one ray
+    gives the fixed cost and a call on max(n, 2 x cores) rays (whole rounds of
+    the host's threads) the per-ray cost, combined for the full frame."""
     from oracle import render as OR
     rng = np.random.default_rng(seed)
     total = 0.0
     rays = 0
+    cores = OR.num_threads()
+    k = max(n, 2 * cores)
+    k = ((k + cores - 1) // cores) * cores
 
-    def call(s, k):
-        idx = rng.choice(s.width * s.height, k, replace=False)
+    def call(s, m):
+        idx = rng.choice(s.width * s.height, m, replace=False)
         t0 = time.perf_counter()
         if s.kind == "lidar":
             OR.render_lidar(scene, s, rays=idx, obj_pose=poses)
@@ -167,12 +171,11 @@ def oracle_frame_estimate(scene, poses, sensors, n=32, seed=7):
             OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses)
         return time.perf_counter() - t0
     for s in sensors:
-        t1 = call(s, n)
-        t2 = call(s, 2 * n)
-        per_ray = max(t2 - t1, 0.0) / n
-        fixed = max(t1 - n * per_ray, 0.0)
-        total += fixed + per_ray * s.width * s.height
-        rays += 3 * n
+        t1 = call(s, 1)
+        tk = call(s, k)
+        per_ray = max(tk - t1, 0.0) / (k - 1)
+        total += t1 + per_ray * (s.width * s.height - 1)
+        rays += 1 + k
     return total * 1e3, rays
 
 
@@ -222,9 +225,9 @@ def run_reference(args):
                        "frame_rays": total_rays, "oracle_decode_ms": dec_s * 1e3},
             "cpu_baseline": {"value": ms_frame, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"FP64 decode of all {anchors.n} anchors (torch CPU), then per sensor "
-                                       f"oracle calls on {args.sample_rays} and {2 * args.sample_rays} random rays "
-                                       f"(brute force over {scene.n} surfels) give its fixed and per-ray cost, "
-                                       f"combined for the frame's {total_rays} rays"},
+                                       f"an oracle call on 1 random ray (its fixed cost) and one on "
+                                       f"max({args.sample_rays}, 2 x cores) rays (brute force over {scene.n} "
+                                       f"surfels; its per-ray cost), combined for the frame's {total_rays} rays"},
             "e2e": {"value": ms_frame, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -330,14 +333,37 @@ def backward_step(args, stream):
     s = synth.driving_scene(n=2_000_000, seed=synth.SEED_BASE + 3)
     tgt = synth.perturbed(s, seed=synth.SEED_BASE + 30)
     cam = synth.driving_camera()
-    r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=("rgb", "depth", "normal", "alpha", "trans", "depth_acc",
-                                                       "n_contrib"))
-    r.render(DeviceSurfels.from_host(tgt))
-    target = r.out[0]["rgb"].clone()
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "depth_acc", "n_contrib")
+    dt = DeviceSurfels.from_host(tgt)
     d = DeviceSurfels.from_host(s)
     grads = {k: torch.zeros_like(getattr(d, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh")}
     names = ("forward", "loss", "backward")
     ev = {k: [] for k in names}
+
+    # the list split of the step, picked by timing whole steps (the backward
+    # walks the forward's chunks, so gsr_autotune's frame-only choice is not it)
+    trials = []
+    best = None
+    for split in ((16384, 384), (4096, 384), (2048, 256), (1024, 256)):
+        r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=outs, split=split)
+        r.render(dt)
+        target = r.out[0]["rgb"].clone()
+
+        def plain():
+            for g in grads.values():
+                g.zero_()
+            r.render(d)
+            loss, lo = camera_loss(r, 0, target)
+            camera_backward(r, 0, lo.struct(), d, out=grads)
+        plain()
+        ms = timed(stream, 3, plain)
+        trials.append({"split": list(split), "ms": ms})
+        if best is None or ms < best[0]:
+            best = (ms, split)
+        del r
+    r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=outs, split=best[1])
+    r.render(dt)
+    target = r.out[0]["rgb"].clone()
 
     def step(record):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
@@ -367,7 +393,7 @@ def backward_step(args, stream):
     return {"workload": "2M-surfel SH-3 driving scene, 1920x1080 camera, 16x8 tiles, loss vs a perturbed copy",
             "ms_per_step": ms, "stage_ms": {k: float(np.mean([a.elapsed_time(b) for a, b in v]))
                                             for k, v in ev.items()},
-            "loss": loss, "steps": k}
+            "loss": loss, "steps": k, "split": list(best[1]), "split_trials": trials}
 
 
 def run_gpu(args):
@@ -415,7 +441,7 @@ def run_gpu(args):
         nf = NeuralFrame(model, da, r, d_obj, pose_t, origin, gsr.DECODE_BF16_TENSOR)
         nf.render()
         torch.cuda.synchronize()
-        tuned = r.autotune([nf.table, d_obj], pose_t) if args.autotune else None
+        tuned = r.autotune([nf.table, d_obj], pose_t, warmup=2, reps=5) if args.autotune else None
         nf.render()
         torch.cuda.synchronize()
         G = nf.graphs()
@@ -426,7 +452,7 @@ def run_gpu(args):
     else:
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
-        tuned = r.autotune([dev], pose_t) if args.autotune else None
+        tuned = r.autotune([dev], pose_t, warmup=2, reps=5) if args.autotune else None
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
         gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
@@ -510,7 +536,7 @@ def run_gpu(args):
     if anchors is not None and args.compare:
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
-        ex_tuned = r.autotune([dev], pose_t) if args.autotune else None
+        ex_tuned = r.autotune([dev], pose_t, warmup=2, reps=5) if args.autotune else None
         r.render_rig(dev, pose_t)
         torch.cuda.synchronize()
         gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
@@ -582,9 +608,9 @@ def run_gpu(args):
         ms_o, _ = oracle_frame_estimate(o_scene, poses, sensors, n=args.sample_rays, seed=3)
         cpu = {"value": ms_o + dec_s * 1e3, "unit": UNIT, "cores": OR.num_threads(), "kind": "oracle",
                "sample": (f"FP64 decode of all anchors ({dec_s * 1e3:.0f} ms), then " if anchors is not None else "")
-               + f"per sensor, oracle calls on {args.sample_rays} and {2 * args.sample_rays} random rays (brute "
-                 f"force over {o_scene.n} surfels) give its fixed and per-ray cost, combined for the frame's "
-                 f"{n_rays(sensors)} rays"}
+               + f"per sensor, an oracle call on 1 random ray (its fixed cost) and one on "
+                 f"max({args.sample_rays}, 2 x cores) rays (brute force over {o_scene.n} surfels; its per-ray "
+                 f"cost), combined for the frame's {n_rays(sensors)} rays"}
     total_rays = n_rays(sensors)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

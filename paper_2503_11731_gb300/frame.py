@@ -164,7 +164,7 @@ class Renderer:
 
     def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
                  lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (8, 16), (16, 16)), batch_depths=(64, 128, 256),
-                 split_firsts=(8192, 16384, 32768), split_chunks=(256, 384, 512, 1024), warmup=1, reps=3,
+                 split_firsts=(4096, 8192, 16384, 32768), split_chunks=(256, 384, 512, 1024), warmup=1, reps=3,
                  stream=None):
         """Pick the tiling of this rig with gsr_autotune over `parts` (DeviceSurfels
         consecutive in the plan) and re-plan with it; returns the trial list."""

@@ -11,7 +11,7 @@ the derivative of the piecewise-smooth render at a given point: thresholds
 no derivative of their own.  Every pixel sees every surfel (brute force), so
 it is meant for small images (64x64, a few hundred surfels).
 
-Loss (config of the backward step; 2DGS regularisers, readings in the design doc):
+Loss of the backward step (2DGS regularisers; the weights and forms are readings):
     L = mean|C - C*|  (over 3 H W)
       + 0.1  * mean_px( A D - B^2 )          A = sum w, B = sum w z, D = sum w z^2
         (= 1/2 sum_ij w_i w_j (z_i - z_j)^2, the squared depth distortion)

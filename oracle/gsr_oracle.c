@@ -9,6 +9,8 @@
  *   Eq. 1  P(u,v) = W H (u,v,1)^T, H = [s_u t_u, s_v t_v, mu; 0 0 1]  (4x3)
  *   Eq. 2  [h_u, h_v]^T . P(u,v) = 0 solved for (u,v)
  *   Eq. 3  pinhole planes h_u = (-1,0,0,p_x), h_v = (0,-1,0,p_y)
+ *   Eq. 4  cylinder      h_u = (cos phi, 0, -sin phi, 0),
+ *                        h_v = (y_n sin phi, -1, y_n cos phi, 0)  (a reading, below)
  *   Eq. 5  LiDAR planes  h_u = (sin az, -cos az, 0, 0),
  *                        h_v = (sin el cos az, sin el sin az, -cos el, 0)
  * and the splatting it cites (3DGS / 2DGS, Sec. II "Scene Representations"):
@@ -16,11 +18,13 @@
  * It is a brute-force pass: every pixel (or ray) looks at every surfel, with
  * no tiling, no bounds and no culling beyond the method's own near test.
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - pinhole W = [[fx,0,cx,0],[0,fy,cy,0],[0,0,1,0],[0,0,1,0]] . [R|t], so the
  *     Eq. 3 planes act on pixel-homogeneous coordinates; LiDAR W = [R|t];
  *   - in Eq. 5 the angle inside h_u is the azimuth and the one that appears
  *     alone in h_v is the elevation (the formulas, not the prose, decide);
+ *   - Eq. 4 (cylindrical camera): h_v read as the camera-frame plane through
+ *     the pixel's ray normal to h_u (see oracle_render_cylindrical);
  *   - an intersection counts only if its depth (camera) or its distance
  *     along the ray (LiDAR) exceeds `near`; surfels whose centre depth
  *     (range) is <= near are culled;
@@ -140,7 +144,7 @@ typedef struct {
 
 typedef struct {
     /* sensor */
-    int is_lidar;
+    int kind;                        /* 0 pinhole, 1 LiDAR, 2 cylindrical   */
     double Rs[3][3], ts[3];          /* world -> sensor rigid part          */
     double origin[3];                /* sensor origin in world             */
     double fx, fy, cx, cy;           /* pinhole                            */
@@ -219,7 +223,8 @@ static float or_key32(const or_sensor* S, int i, const double* pos, const int* o
     float s[3];
     for (int a = 0; a < 3; ++a)
         s[a] = fmaf((float)S->Rs[a][0], m0, fmaf((float)S->Rs[a][1], m1, (float)S->Rs[a][2] * m2)) + (float)S->ts[a];
-    if (!S->is_lidar) return s[2];
+    if (S->kind == 0) return s[2];
+    if (S->kind == 2) return sqrtf(fmaf(s[0], s[0], s[2] * s[2])); /* horizontal distance */
     return sqrtf(fmaf(s[0], s[0], fmaf(s[1], s[1], s[2] * s[2])));
 }
 
@@ -249,7 +254,7 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
         Rt[a][3] = S->ts[a];
     }
     Rt[3][0] = Rt[3][1] = Rt[3][2] = 0; Rt[3][3] = 1;
-    if (!S->is_lidar) {
+    if (S->kind == 0) {
         double P4[4][4] = {{S->fx, 0, S->cx, 0}, {0, S->fy, S->cy, 0}, {0, 0, 1, 0}, {0, 0, 1, 0}};
         for (int a = 0; a < 4; ++a)
             for (int b = 0; b < 4; ++b) {
@@ -272,10 +277,16 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     G->culled = 0;
     G->key = or_key32(S, i, pos, obj_id, obj_pose);
     if (!(G->key > (float)S->near_)) { G->culled = 1; return; }  /* cull in the key's precision */
-    if (!S->is_lidar) {
+    if (S->kind == 0) {
         G->zc = ms[2];
         G->c[0] = G->WH[0][2] / G->WH[2][2];
         G->c[1] = G->WH[1][2] / G->WH[2][2];
+    } else if (S->kind == 2) {
+        /* cylinder: column from the azimuth about the camera's y axis, row
+           from the height over the horizontal distance (pixel units) */
+        G->zc = sqrt(ms[0] * ms[0] + ms[2] * ms[2]);
+        G->c[0] = S->cx + S->fx * atan2(ms[0], ms[2]);
+        G->c[1] = S->cy + S->fy * ms[1] / G->zc;
     } else {
         G->zc = sqrt(or_dot3(ms, ms));
         double az = atan2(ms[1], ms[0]);
@@ -292,7 +303,7 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     if (or_dot3(nw, to_s) > 0) { nw[0] = -nw[0]; nw[1] = -nw[1]; nw[2] = -nw[2]; }
     for (int a = 0; a < 3; ++a) G->normal[a] = S->Rs[a][0] * nw[0] + S->Rs[a][1] * nw[1] + S->Rs[a][2] * nw[2];
 
-    if (!S->is_lidar) {
+    if (S->kind != 1) {
         double len = sqrt(or_dot3(to_s, to_s));
         double dw[3] = {to_s[0] / len, to_s[1] / len, to_s[2] / len};
         double dl[3]; /* into the object frame: R_o^T dw */
@@ -346,14 +357,15 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
         double x[3];
         for (int a = 0; a < 3; ++a) x[a] = G->WH[a][0] * u + G->WH[a][1] * v + G->WH[a][2];
         double zi;
-        if (!S->is_lidar) zi = x[2];             /* depth row of W H        */
-        else zi = or_dot3(x, d);                  /* distance along the ray */
+        if (S->kind == 0) zi = x[2];             /* depth row of W H        */
+        else zi = or_dot3(x, d);                  /* LiDAR: distance along the unit ray;
+                                                     cylinder: horizontal distance (d horizontal) */
         h->zint = zi;
         h->rho3 = u * u + v * v;
         h->v3 = (zi > S->near_) && (h->rho3 <= 9.0);
     }
     double dx = pc[0] - G->c[0], dy = pc[1] - G->c[1];
-    if (S->is_lidar) { /* azimuth wraps around the spin */
+    if (S->kind == 1) { /* azimuth wraps around the spin */
         dx = fmod(dx, (double)S->columns);
         if (dx >= 0.5 * S->columns) dx -= S->columns;
         if (dx < -0.5 * S->columns) dx += S->columns;
@@ -501,7 +513,7 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
     if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3) return -1;
     or_sensor S;
     memset(&S, 0, sizeof(S));
-    S.is_lidar = 0;
+    S.kind = 0;
     or_sensor_from_matrix(&S, world_to_cam);
     S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
     or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, obj_id, obj_pose);
@@ -543,6 +555,73 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
 }
 
 /*
+ * Cylindrical camera frame (Eq. 4): pixel (x, y) has
+ * azimuth phi = (x + 0.5 - cx)/fx about the camera's y axis and height
+ * y_n = (y + 0.5 - cy)/fy on the unit cylinder, so its ray from the camera
+ * centre is d = (sin phi, y_n, cos phi).  The paper's h_u = (cos phi, 0,
+ * -sin phi, 0) contains it; its printed h_v = (0, -1, 0, p_y) is a
+ * pixel-frame row next to a camera-frame h_u, so h_v is read as the plane
+ * through the camera centre that contains d and the horizontal direction
+ * (cos phi, 0, -sin phi): h_v = (y_n sin phi, -1, y_n cos phi, 0), normal to
+ * h_u as the paper's two planes are.  Depth is the horizontal distance t of
+ * the intersection t d (the cylinder radius).
+ * Outputs as oracle_render_pinhole.
+ */
+int oracle_render_cylindrical(int n, const double* pos, const double* log_scale, const double* quat,
+                              const double* opacity_logit, int sh_degree, const double* sh,
+                              const int* obj_id, const double* obj_pose,
+                              int width, int height, double fx, double fy, double cx, double cy,
+                              double near_, const double* world_to_cam, const double* bg,
+                              int n_pix, const long long* pix,
+                              double* rgb, double* depth, double* normal, double* alpha, double* trans,
+                              double* acc, double* flip, int* n_contrib)
+{
+    if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3) return -1;
+    or_sensor S;
+    memset(&S, 0, sizeof(S));
+    S.kind = 2;
+    or_sensor_from_matrix(&S, world_to_cam);
+    S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
+    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, obj_id, obj_pose);
+    if (!G) return -1;
+    long long npx = pix ? n_pix : (long long)width * height;
+    int fail = 0;
+#pragma omp parallel
+    {
+        or_hit* buf = (or_hit*)malloc(sizeof(or_hit) * (size_t)(n > 0 ? n : 1));
+        if (!buf) {
+#pragma omp atomic write
+            fail = 1;
+        } else {
+#pragma omp for schedule(dynamic, 16)
+            for (long long q = 0; q < npx; ++q) {
+                long long li = pix ? pix[q] : q;
+                int x = (int)(li % width), y = (int)(li / width);
+                double px = x + 0.5, py = y + 0.5;
+                double phi = (px - cx) / fx, yn = (py - cy) / fy;
+                double hu[4] = {cos(phi), 0, -sin(phi), 0}; /* Eq. 4 */
+                double hv[4] = {yn * sin(phi), -1, yn * cos(phi), 0};
+                double pc[2] = {px, py};
+                double dh[3] = {sin(phi), 0, cos(phi)};   /* horizontal part of the ray */
+                or_ray r;
+                or_composite(G, n, &S, hu, hv, dh, pc, buf, &r);
+                for (int ch = 0; ch < 3; ++ch) rgb[q * 3 + ch] = r.feat[ch] + r.T * bg[ch];
+                depth[q] = r.A > 0 ? r.B / r.A : 0.0;
+                for (int a = 0; a < 3; ++a) normal[q * 3 + a] = r.N[a];
+                alpha[q] = r.A;
+                trans[q] = r.T;
+                if (acc) { acc[q * 3 + 0] = r.A; acc[q * 3 + 1] = r.B; acc[q * 3 + 2] = r.D; }
+                if (flip) flip[q] = r.flip;
+                if (n_contrib) n_contrib[q] = r.n_contrib;
+            }
+            free(buf);
+        }
+    }
+    free(G);
+    return fail ? -1 : 0;
+}
+
+/*
  * Spinning LiDAR range image (Eq. 5).  Row i (beam) has elevation
  * el_max - i (el_max - el_min)/(beams-1); column j has azimuth
  * az0 + (j+0.5) 360/columns.  Outputs per ray: range = sum(w t)/sum(w)
@@ -560,7 +639,7 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
     if (n < 0 || beams < 2 || columns <= 0) return -1;
     or_sensor S;
     memset(&S, 0, sizeof(S));
-    S.is_lidar = 1;
+    S.kind = 1;
     or_sensor_from_matrix(&S, world_to_lidar);
     S.beams = beams; S.columns = columns;
     S.el_max = el_max_deg * OR_PI / 180.0;
@@ -619,25 +698,30 @@ int oracle_num_threads(void)
  * Eq. 2 for one surfel and one pixel / ray, exposed for the pins: returns
  * 1 and (u, v, depth-or-distance) if k x l has a non-zero third component.
  * kind 0 = pinhole (ray = pixel centre px,py), 1 = LiDAR (ray = az, el in
- * radians).  cam = {fx, fy, cx, cy} for the pinhole.
+ * radians), 2 = cylinder (ray = azimuth phi, height y_n).  cam = {fx, fy,
+ * cx, cy} for the cameras.
  */
 int oracle_intersect(int kind, const double* pos, const double* log_scale, const double* quat,
                      const double* world_to_sensor, const double* cam, double a, double b, double* uvz)
 {
     or_sensor S;
     memset(&S, 0, sizeof(S));
-    S.is_lidar = kind;
+    S.kind = kind;
     or_sensor_from_matrix(&S, world_to_sensor);
-    if (!kind) { S.fx = cam[0]; S.fy = cam[1]; S.cx = cam[2]; S.cy = cam[3]; }
+    if (kind != 1) { S.fx = cam[0]; S.fy = cam[1]; S.cx = cam[2]; S.cy = cam[3]; }
     S.near_ = -1e300;
     S.columns = 1;
     double op = 0.0, ones = 0.0;
     or_surfel G;
     or_prepare(&G, 0, &S, pos, log_scale, quat, &op, 0, &ones, NULL, NULL, NULL);
     double hu[4], hv[4], d[3] = {0, 0, 1}, pc[2] = {0, 0};
-    if (!kind) {
+    if (kind == 0) {
         hu[0] = -1; hu[1] = 0; hu[2] = 0; hu[3] = a;
         hv[0] = 0; hv[1] = -1; hv[2] = 0; hv[3] = b;
+    } else if (kind == 2) { /* a = azimuth phi, b = height y_n on the unit cylinder */
+        hu[0] = cos(a); hu[1] = 0; hu[2] = -sin(a); hu[3] = 0;
+        hv[0] = b * sin(a); hv[1] = -1; hv[2] = b * cos(a); hv[3] = 0;
+        d[0] = sin(a); d[1] = 0; d[2] = cos(a);
     } else {
         hu[0] = sin(a); hu[1] = -cos(a); hu[2] = 0; hu[3] = 0;
         hv[0] = sin(b) * cos(a); hv[1] = sin(b) * sin(a); hv[2] = -cos(b); hv[3] = 0;

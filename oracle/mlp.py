@@ -5,7 +5,7 @@ benchmark's CPU-baseline leg; it never imports the CUDA package.
 
 The paper infers each 2DGS attribute set by passing anchor features through
 an MLP (Sec. III-A, "Scene Reconstruction": anchors organised as in
-Scaffold-GS).  Readings (the design doc lists them):
+Scaffold-GS).  Readings of the points the paper leaves open:
   input   X = [f (32), d (3), |x_a - o| (1)] with d = (x_a - o)/|x_a - o|,
           o the view origin (the camera centre; the rig centre for a rig)
   hidden  H = ReLU(X W1 + b1)                         W1 [36, 64]

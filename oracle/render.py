@@ -45,6 +45,8 @@ def _load():
             c_int, D, D, D, D, c_int, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, c_double, D, D,
             c_int, L, D, D, D, D, D, D, D, I]
+        lib.oracle_render_cylindrical.restype = c_int
+        lib.oracle_render_cylindrical.argtypes = lib.oracle_render_pinhole.argtypes
         lib.oracle_render_lidar.restype = c_int
         lib.oracle_render_lidar.argtypes = [
             c_int, D, D, D, D, D, I, D,
@@ -82,7 +84,8 @@ def sh_basis(l: int, m: int, d) -> float:
 
 
 def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
-    """Brute-force FP64 render of a pinhole frame.
+    """Brute-force FP64 render of a camera frame: pinhole (Eq. 3) or, for
+    cam.kind == "cylindrical", the cylindrical camera (Eq. 4).
 
     `s` holds the surfel arrays (pos, log_scale, quat, opacity, sh, obj_id);
     `cam` the intrinsics and world_to_sensor.  `pixels` (optional) lists the
@@ -113,7 +116,8 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
     out["n_contrib"] = np.zeros(npix, np.int32)
     dp = {k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in out.items() if v.dtype == np.float64}
     deg = int(round(np.sqrt(s.sh.shape[1]))) - 1
-    rc = lib.oracle_render_pinhole(
+    fn = lib.oracle_render_cylindrical if getattr(cam, "kind", "pinhole") == "cylindrical" else lib.oracle_render_pinhole
+    rc = fn(
         int(s.pos.shape[0]), D(s.pos), D(s.log_scale), D(s.quat), D(s.opacity), deg, D(s.sh),
         ids_p, P_p,
         int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
@@ -122,7 +126,7 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
         dp["rgb"], dp["depth"], dp["normal"], dp["alpha"], dp["T"], dp["acc"], dp["flip"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:
-        raise RuntimeError("oracle_render_pinhole failed")
+        raise RuntimeError("oracle camera render failed")
     if pixels is None:
         H, W = cam.height, cam.width
         out = {k: v.reshape((H, W) + v.shape[1:]) for k, v in out.items()}

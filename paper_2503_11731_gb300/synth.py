@@ -81,6 +81,22 @@ class Pinhole:
 
 
 @dataclasses.dataclass
+class Cylindrical:
+    """Cylindrical (fisheye) camera: column x looks along azimuth
+    (x + 0.5 - cx) / fx about the camera's y axis, row y along height
+    (y + 0.5 - cy) / fy on the unit cylinder (camera frame as the pinhole)."""
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    world_to_sensor: np.ndarray  # [4,4] float64
+    near: float = 0.2
+    kind: str = "cylindrical"
+
+
+@dataclasses.dataclass
 class Lidar:
     beams: int
     columns: int
@@ -181,6 +197,17 @@ def pinhole(width, height, f, position=(0, 0, 0), yaw_deg=0.0, pitch_deg=0.0, po
     return Pinhole(width, height, float(f), float(f), width / 2.0, height / 2.0,
                    camera_pose(position, yaw_deg, pitch_deg) if pose is None else np.asarray(pose, np.float64),
                    near)
+
+
+def cylindrical(width, height, hfov_deg, vfov_deg, position=(0, 0, 0), yaw_deg=0.0, pitch_deg=0.0, pose=None,
+                near=0.2):
+    """Cylindrical camera with horizontal field hfov (degrees, may exceed 180)
+    and vertical field vfov at the image centre; `pose` (world->camera)
+    overrides position / yaw / pitch."""
+    fx = width / math.radians(hfov_deg)
+    fy = 0.5 * height / math.tan(math.radians(0.5 * vfov_deg))
+    M = np.asarray(pose, np.float64) if pose is not None else camera_pose(position, yaw_deg, pitch_deg)
+    return Cylindrical(width, height, fx, fy, width / 2.0, height / 2.0, M, near)
 
 
 def spinning_lidar(beams, columns, el_min, el_max, position=(0, 0, 0), yaw_deg=0.0, near=0.2):

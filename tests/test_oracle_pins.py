@@ -367,3 +367,57 @@ def test_distortion_identity():
     pair = 0.5 * sum(w[i] * w[j] * (z[i] - z[j]) ** 2 for i in range(12) for j in range(12))
     A, B, D = w.sum(), (w * z).sum(), (w * z * z).sum()
     assert A * D - B * B == pytest.approx(pair, rel=1e-12)
+
+
+# ------------------------------------------------- cylindrical camera (Eq. 4)
+def test_eq4_cylinder_matches_direct_ray_plane():
+    """(u, v) and the depth (the horizontal distance along the cylinder ray)
+    equal a direct intersection of the ray d = (sin phi, y_n, cos phi) from
+    the camera centre with the surfel plane."""
+    rng = np.random.default_rng(12)
+    pose = synth.camera_pose((0.5, 1.0, 1.6), 35.0, 3.0, f32=False)
+    Rc, tc = pose[:3, :3], pose[:3, 3]
+    origin = -Rc.T @ tc
+    cam = (300.0, 280.0, 400.0, 120.0)
+    for _ in range(200):
+        phi, yn = rng.uniform(-2.5, 2.5), rng.uniform(-0.6, 0.6)
+        dc = np.array([math.sin(phi), yn, math.cos(phi)])
+        mu = origin + Rc.T @ (dc * rng.uniform(3, 30) + rng.normal(0, 0.4, 3))
+        q = rng.standard_normal(4)
+        ls = rng.uniform(-2, 0.5, 2)
+        r = R.intersect(2, mu, ls, q, pose, cam, phi, yn)
+        u, v, t, x = _ray_plane(origin, Rc.T @ dc, mu, _rot(q), np.exp(ls))
+        xc = Rc @ x + tc
+        assert r is not None
+        assert np.allclose(r, [u, v, math.hypot(xc[0], xc[2]) * np.sign(t)], rtol=1e-9,
+                           atol=1e-9 * (1 + abs(u) + abs(v) + abs(t)))
+        assert t == pytest.approx(r[2], rel=1e-9)  # |(sin phi, cos phi)| = 1: the ray parameter is the depth
+
+
+def test_cylinder_centre_column_equals_pinhole_column():
+    """The cylinder column at azimuth 0 and the pinhole column through its
+    principal point carry the same rays (0, y_n, 1); for surfels centred on
+    the camera's x = 0 plane the low-pass centres coincide too, so the whole
+    column renders identically (depth = horizontal distance = z there)."""
+    rng = np.random.default_rng(13)
+    n = 80
+    pos = np.stack([np.zeros(n), rng.uniform(-2, 2, n), rng.uniform(4, 25, n)], 1)
+    q = rng.standard_normal((n, 4))
+    ls = rng.uniform(-2.0, -0.3, (n, 2))
+    op = rng.normal(0.5, 1, n)
+    s = synth.Surfels(pos, ls, q, op, synth.rgb_to_sh0(rng.uniform(0, 1, (n, 3)), np.float64),
+                      rng.uniform(0, 1, n))
+    W, H, fy = 41, 48, 60.0
+    cyl = synth.Cylindrical(W, H, 25.0, fy, 20.5, 24.0, np.eye(4), 0.2)   # column 20 at phi = 0
+    pin = synth.Pinhole(W, H, 77.0, fy, 20.5, 24.0, np.eye(4), 0.2)
+    col = [y * W + 20 for y in range(H)]
+    oc = R.render_pinhole(s, cyl, pixels=col)
+    op_ = R.render_pinhole(s, pin, pixels=col)
+    assert oc["alpha"].max() > 0.3
+    for k in ("rgb", "alpha", "T", "normal"):
+        assert np.abs(oc[k] - op_[k]).max() <= 1e-12, k
+    assert np.abs(oc["depth"] - op_["depth"]).max() <= 1e-9
+    # and away from that column the two projections differ
+    other = [y * W + 3 for y in range(H)]
+    assert np.abs(R.render_pinhole(s, cyl, pixels=other)["alpha"] -
+                  R.render_pinhole(s, pin, pixels=other)["alpha"]).max() > 1e-3

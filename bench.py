@@ -396,6 +396,37 @@ def backward_step(args, stream):
             "loss": loss, "steps": k, "split": list(best[1]), "split_trials": trials}
 
 
+def cylindrical_frame(args, stream):
+    """A frame of a cylindrical surround camera (Eq. 4): the 1.5M-surfel SH-3
+    driving scene seen by one 3840x1080 camera over 200 deg of azimuth at
+    (0, 0, 1.5), next to the 1920x1080 pinhole of the same scene; each
+    tiling autotuned, each frame (preprocess, sort, composite) one graph."""
+    import torch
+    from paper_2503_11731_gb300 import synth
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    s = synth.driving_scene()
+    d = DeviceSurfels.from_host(s)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    res = {"workload": "1.5M-surfel SH-3 driving scene; cylindrical 3840x1080 (200 x 60 deg) vs pinhole "
+                       "1920x1080 (fx 1000), both at (0, 0, 1.5) looking +x"}
+    for name, cam in (("cylindrical", synth.cylindrical(3840, 1080, 200.0, 60.0, (0.0, 0.0, 1.5))),
+                      ("pinhole", synth.driving_camera())):
+        r = Renderer(s.n, [cam], outputs=("rgb", "depth", "normal", "alpha"), max_dup=args.max_dup)
+        r.render(d)
+        torch.cuda.synchronize()
+        tuned = r.autotune([d], warmup=2, reps=5) if args.autotune else None
+        g = r.graph(d, None, stages=7)
+        for _ in range(3):
+            g.launch(sh)
+        ms = timed(stream, max(3, args.steps // 2), lambda: g.launch(sh))
+        nvis, npairs = check_status(r)
+        res[name] = {"ms": ms, "mpix_per_s": cam.width * cam.height / (ms * 1e-3) / 1e6,
+                     "tile": r.tile_of("camera"), "visible_records": nvis, "tile_pairs": npairs,
+                     "autotune_best_ms": None if tuned is None else tuned["best_ms"]}
+        del g, r
+    return res
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -559,7 +590,7 @@ def run_gpu(args):
         compare = {
             "explicit_batched_ms": batched,
             "explicit_batched_stage_ms": {"pre_sort": ex_front, "render_rig": ex_render},
-            "explicit_tiling": {"camera_tile": r.tile_of("pinhole"), "lidar_tile": r.tile_of("lidar"),
+            "explicit_tiling": {"camera_tile": r.tile_of("camera"), "lidar_tile": r.tile_of("lidar"),
                                 "batch_depth": r.plan.tiling.batch_depth,
                                 "split": [r.plan.tiling.split_first, r.plan.tiling.split_chunk],
                                 "autotune_best_ms": None if ex_tuned is None else ex_tuned["best_ms"]},
@@ -576,6 +607,7 @@ def run_gpu(args):
 
     # ---- backward step of the reconstruction workload (2M surfels, 1920x1080)
     bwd = backward_step(args, stream) if args.backward else None
+    cyl = cylindrical_frame(args, stream) if args.cylindrical else None
 
     if rank != 0:
         if world > 1:
@@ -631,6 +663,7 @@ def run_gpu(args):
         "compare": compare,
         "autotune": tuned,
         "backward_step": bwd,
+        "cylindrical_frame": cyl,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -658,6 +691,8 @@ def main():
     ap.add_argument("--sample-rays", type=int, default=16)
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the explicit-form and decode-only timings")
+    ap.add_argument("--no-cylindrical", dest="cylindrical", action="store_false",
+                    help="skip the cylindrical-camera frame measurement")
     ap.add_argument("--no-backward", dest="backward", action="store_false",
                     help="skip the backward-step timing (2M surfels, 1920x1080)")
     args = ap.parse_args()

@@ -50,7 +50,7 @@ typedef enum {
     GSR_ERR_TOO_LARGE = 7     /* a size beyond a fixed built-in limit                     */
 } gsr_status;
 
-typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1 } gsr_sensor_kind;
+typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1, GSR_SENSOR_CYLINDRICAL = 2 } gsr_sensor_kind;
 
 /*
  * Surfel table, structure of arrays, one row per surfel (Sec. III-A: the
@@ -91,9 +91,16 @@ typedef struct {
 /*
  * Sensor descriptor (host memory).  Pinhole: Eq. 3 planes with the
  * intrinsics fx, fy, cx, cy.  LiDAR: Eq. 5 planes; width = azimuth columns,
- * height = beams.  Intersections nearer than `near` (depth for the camera,
- * distance along the ray for LiDAR) are rejected; surfels whose centre depth
- * (range) is <= near are culled.
+ * height = beams.  Cylindrical (fisheye) camera, Eq. 4: pixel (x, y) looks
+ * along azimuth phi = (x + 0.5 - cx)/fx about the camera's y axis at height
+ * y_n = (y + 0.5 - cy)/fy on the unit cylinder, ray d = (sin phi, y_n,
+ * cos phi); its planes are h_u = (cos phi, 0, -sin phi, 0) and, reading the
+ * paper's pixel-frame h_v in the camera frame, h_v = (y_n sin phi, -1,
+ * y_n cos phi, 0); depth = horizontal distance; the image must see azimuths
+ * within [-pi, pi] (cx/fx and (width - cx)/fx at most pi).  Intersections
+ * nearer than `near` (depth for the cameras, distance along the ray for
+ * LiDAR) are rejected; surfels whose centre depth (range, horizontal
+ * distance) is <= near are culled.
  */
 typedef struct {
     int32_t kind;      /* gsr_sensor_kind */
@@ -257,10 +264,11 @@ gsr_status gsr_preprocess_part(const gsr_plan* plan, const gsr_surfels* surfels,
 gsr_status gsr_bin_sort(const gsr_plan* plan, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Step (c): per-tile front-to-back compositing of camera `sensor` (Eq. 2-3
- * ray-splat (u,v), low-pass fallback, alpha = min(0.99, o G), skip below
- * 1/255, stop before T (1 - alpha) < 1e-4).  Surfel batches are staged into
- * shared memory by bulk async copies.
+ * Step (c): per-tile front-to-back compositing of camera `sensor`, pinhole
+ * or cylindrical (Eq. 2 with the Eq. 3 or Eq. 4 planes: ray-splat (u,v),
+ * low-pass fallback, alpha = min(0.99, o G), skip below 1/255, stop before
+ * T (1 - alpha) < 1e-4).  Surfel batches are staged into shared memory by
+ * bulk async copies.
  */
 gsr_status gsr_render_camera(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
                              int32_t sensor, const gsr_camera_out* out, void* stream);
@@ -284,7 +292,9 @@ gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspace, size_t 
  * whose 4 neighbours have A >= mask_alpha and |dY x dX| > 0.
  * Writes loss[0..3] = (L, L1 term, distortion term, normal term) (DEVICE
  * float[4]) and the per-pixel gradients into *grad (all four planes
- * required; overwritten).  Uses workspace scratch; deterministic.
+ * required; overwritten).  Uses workspace scratch; deterministic.  Pinhole
+ * cameras only (the back-projection of N_d is the pinhole's): another
+ * sensor kind returns GSR_ERR_UNSUPPORTED.
  */
 gsr_status gsr_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
                     const gsr_camera_out* fwd, const float* target_rgb, const gsr_loss_weights* weights,

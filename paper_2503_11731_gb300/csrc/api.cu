@@ -115,10 +115,14 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     int64_t base = 0;
     for (int i = 0; i < n_sensors; ++i) {
         const gsr_sensor& s = sensors[i];
-        if (s.kind != GSR_SENSOR_PINHOLE && s.kind != GSR_SENSOR_LIDAR) return GSR_ERR_UNSUPPORTED;
+        if (s.kind != GSR_SENSOR_PINHOLE && s.kind != GSR_SENSOR_LIDAR && s.kind != GSR_SENSOR_CYLINDRICAL)
+            return GSR_ERR_UNSUPPORTED;
         if (s.width <= 0 || s.height <= 0 || s.width > 65535 || s.height > 65535) return GSR_ERR_INVALID_ARG;
         if (!(s.near_plane > 0.f)) return GSR_ERR_INVALID_ARG;
-        if (s.kind == GSR_SENSOR_PINHOLE && !(s.fx > 0.f && s.fy > 0.f)) return GSR_ERR_INVALID_ARG;
+        if (s.kind != GSR_SENSOR_LIDAR && !(s.fx > 0.f && s.fy > 0.f)) return GSR_ERR_INVALID_ARG;
+        if (s.kind == GSR_SENSOR_CYLINDRICAL &&
+            !(s.cx / s.fx <= 3.1415960f && ((float)s.width - s.cx) / s.fx <= 3.1415960f))
+            return GSR_ERR_INVALID_ARG;
         if (s.kind == GSR_SENSOR_LIDAR && (s.height < 2 || !(s.el_max_deg > s.el_min_deg))) return GSR_ERR_INVALID_ARG;
         plan->sensors[i] = s;
         if (s.tile_w == 0 && s.tile_h == 0) {
@@ -161,7 +165,7 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_RECGRAD] = slots * kRecordBytes;
     uint64_t max_hw = 0;
     for (int i = 0; i < n_sensors; ++i)
-        if (sensors[i].kind == GSR_SENSOR_PINHOLE)
+        if (sensors[i].kind != GSR_SENSOR_LIDAR)
             max_hw = std::max<uint64_t>(max_hw, (uint64_t)sensors[i].width * sensors[i].height);
     sz[R_LOSS_SCRATCH] = (6 * max_hw + 3 * ((max_hw + 255) / 256) + 64) * 4;
     sz[R_TILE_KEY_A] = sz[R_TILE_VAL_A] = sz[R_TILE_KEY_B] = sz[R_TILE_VAL_B] = (uint64_t)base * 4;
@@ -256,7 +260,7 @@ extern "C" gsr_status gsr_render_camera(const gsr_plan* plan, const void* worksp
     gsr_status st = check_ws(plan, workspace, workspace_bytes);
     if (st != GSR_OK) return st;
     if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
-    if (plan->sensors[sensor].kind != GSR_SENSOR_PINHOLE) return GSR_ERR_INVALID_ARG;
+    if (plan->sensors[sensor].kind == GSR_SENSOR_LIDAR) return GSR_ERR_INVALID_ARG;
     FrameOut o{out->rgb, out->depth, out->normal, out->alpha, out->trans, out->depth_acc, out->n_contrib,
                out->n_walk};
     return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
@@ -427,7 +431,7 @@ static gsr_status rig_outputs(const gsr_plan* plan, const gsr_camera_out* cam, c
                               FrameOut* outs)
 {
     for (int i = 0; i < plan->n_sensors; ++i) {
-        if (plan->sensors[i].kind == GSR_SENSOR_PINHOLE) {
+        if (plan->sensors[i].kind != GSR_SENSOR_LIDAR) {
             if (!cam) return GSR_ERR_INVALID_ARG;
             const gsr_camera_out& o = cam[i];
             outs[i] = FrameOut{o.rgb, o.depth, o.normal, o.alpha, o.trans, o.depth_acc, o.n_contrib, o.n_walk};

@@ -51,14 +51,14 @@ gsr_status candidate_plan(const gsr_plan* base, const Candidate& c, gsr_plan* ou
     return gsr_plan_init(out, base->n_surfels, sensors, base->n_sensors, &tiling, base->max_dup);
 }
 
-// Tile of the first sensor of a kind in the plan (both kinds default to the
-// plan's tiling when absent).
-void plan_tile(const gsr_plan* p, int kind, int t[2])
+// Tile of the plan's first LiDAR (lidar) or first camera of either model
+// (both default to the plan's tiling when absent).
+void plan_tile(const gsr_plan* p, bool lidar, int t[2])
 {
     t[0] = p->tiling.tile_w;
     t[1] = p->tiling.tile_h;
     for (int i = 0; i < p->n_sensors; ++i)
-        if (p->sensors[i].kind == kind) {
+        if ((p->sensors[i].kind == GSR_SENSOR_LIDAR) == lidar) {
             t[0] = p->sensors[i].tile_w;
             t[1] = p->sensors[i].tile_h;
             return;
@@ -105,8 +105,8 @@ extern "C" gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gs
 {
     if (!plan || !bytes || !space_ok(space)) return GSR_ERR_INVALID_ARG;
     Candidate start;
-    plan_tile(plan, GSR_SENSOR_PINHOLE, start.cam);
-    plan_tile(plan, GSR_SENSOR_LIDAR, start.lid);
+    plan_tile(plan, false, start.cam);
+    plan_tile(plan, true, start.lid);
     start.bd = plan->tiling.batch_depth;
     start.sf = plan->tiling.split_first;
     start.sc = plan->tiling.split_chunk;
@@ -175,8 +175,8 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     };
 
     Candidate best;
-    plan_tile(plan, GSR_SENSOR_PINHOLE, best.cam);
-    plan_tile(plan, GSR_SENSOR_LIDAR, best.lid);
+    plan_tile(plan, false, best.cam);
+    plan_tile(plan, true, best.lid);
     best.bd = plan->tiling.batch_depth;
     best.sf = plan->tiling.split_first;
     best.sc = plan->tiling.split_chunk;

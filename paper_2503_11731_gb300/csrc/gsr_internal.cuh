@@ -233,12 +233,15 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
         q1 = fmaf(r1.x, dx, r1.y * dy);
         q2 = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z));
     } else {
+        // the ray direction d (LiDAR: unit; cylinder: (sin phi, y_n, cos phi))
         q0 = fmaf(r0.x, d0, fmaf(r0.y, d1, r0.z * d2));
         q1 = fmaf(r1.x, d0, fmaf(r1.y, d1, r1.z * d2));
         q2 = fmaf(r2.x, d0, fmaf(r2.y, d1, r2.z * d2));
-        const float half = 0.5f * columns;
-        if (dx >= half) dx -= columns;
-        if (dx < -half) dx += columns;
+        if (KIND == GSR_SENSOR_LIDAR) {  // the azimuth wraps around the spin
+            const float half = 0.5f * columns;
+            if (dx >= half) dx -= columns;
+            if (dx < -half) dx += columns;
+        }
     }
     // straight-line code (no early return): callers evaluate several
     // records at once and the independent chains interleave
@@ -455,7 +458,7 @@ template <int KIND>
 __device__ __forceinline__ bool box_meets(const float4 r5, const float4 w, float columns)
 {
     const bool rows = r5.w >= w.z && r5.z <= w.w;
-    if (KIND == GSR_SENSOR_PINHOLE) return rows && r5.y >= w.x && r5.x <= w.y;
+    if (KIND != GSR_SENSOR_LIDAR) return rows && r5.y >= w.x && r5.x <= w.y;
     float d = w.x - r5.x;  // warp start inside the record's interval?
     if (d < 0.f) d += columns;
     float e = r5.x - w.x;  // record start inside the warp's interval?
@@ -529,6 +532,15 @@ __device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, flo
         rx = x + 0.5f;
         ry = y + 0.5f;
         d0 = d1 = d2 = 0.f;
+    } else if (KIND == GSR_SENSOR_CYLINDRICAL) {
+        // Eq. 4: azimuth about the camera's y axis, height on the unit cylinder
+        rx = x + 0.5f;
+        ry = y + 0.5f;
+        float sp, cp;
+        sincosf((rx - sd.cx) / sd.fx, &sp, &cp);
+        d0 = sp;
+        d1 = (ry - sd.cy) / sd.fy;
+        d2 = cp;
     } else {
         rx = (float)x;
         ry = (float)y;

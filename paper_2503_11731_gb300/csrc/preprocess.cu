@@ -267,6 +267,118 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
                 rect.w |= kRectExact;
             }
         }
+    } else if (sd.kind == GSR_SENSOR_CYLINDRICAL) {
+        // Eq. 4: pixel (x, y) looks along (sin phi, y_n, cos phi) with
+        // phi = (x + 1/2 - c_x) / f_x and y_n = (y + 1/2 - c_y) / f_y; depth
+        // and order key are the horizontal distance sqrt(x^2 + z^2)
+        const float rh = sqrtf(fmaf(ms.x, ms.x, ms.z * ms.z));
+        zkey = rh;
+        if (!(rh > sd.near_plane) || never) {
+            counts[slot] = 0;
+            keys[slot] = __float_as_uint(fmaxf(zkey, 0.f));
+            rects[slot] = rect;
+            return;
+        }
+        // M = [a b ms] (columns), Q = adj(M), det(M): q = Q d gives
+        // (u, v) = (q0, q1) / q2 and the distance det / q2 along d
+        const float m00 = a.x, m01 = b.x, m02 = ms.x;
+        const float m10 = a.y, m11 = b.y, m12 = ms.y;
+        const float m20 = a.z, m21 = b.z, m22 = ms.z;
+        const float q00 = fmaf(m11, m22, -m12 * m21), q01 = fmaf(m02, m21, -m01 * m22), q02 = fmaf(m01, m12, -m02 * m11);
+        const float q10 = fmaf(m12, m20, -m10 * m22), q11 = fmaf(m00, m22, -m02 * m20), q12 = fmaf(m02, m10, -m00 * m12);
+        const float q20 = fmaf(m10, m21, -m11 * m20), q21 = fmaf(m01, m20, -m00 * m21), q22 = fmaf(m00, m11, -m01 * m10);
+        const float det = fmaf(m00, q00, fmaf(m01, q10, m02 * q20));
+        // low-pass centre in pixels
+        const float phc = atan2f(ms.x, ms.z);
+        const float ccx = fmaf(sd.fx, phc, sd.cx), ccy = fmaf(sd.fy, ms.y / rh, sd.cy);
+        r0 = make_float4(q00, q01, q02, ccx);
+        r1 = make_float4(q10, q11, q12, ccy);
+        r2 = make_float4(q20, q21, q22, det);
+
+        // Bound of the support ellipse (inside the circumscribed octagon, as
+        // for the LiDAR) united with the low-pass disc.  With the octagon's
+        // xz-projection away from the y axis, the azimuth phi = atan2(x, z)
+        // is monotonic along each edge and takes its extremes at vertices;
+        // y_n = y / sqrt(x^2 + z^2) has a gradient orthogonal to the position,
+        // so on a plane that misses the centre it has no interior extremum and
+        // per-edge bounds (max y over min horizontal distance, ...) cover it.
+        // Otherwise the bounding sphere of the octagon bounds the elevation
+        // atan(y_n).  Azimuth ranges that leave [-pi, pi] take every column.
+        const float kk = ksig * 1.0823922f;
+        const float rad = kk * fmaxf(su, sv);
+        const float r3d = sqrtf(dot(ms, ms));
+        const bool full_cols = !(rh > rad * 1.0001f + 1e-6f);
+        F3 nrm = f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+        const float plane_off = fabsf(dot(nrm, ms)) * rsqrtf(fmaxf(dot(nrm, nrm), 1e-30f));
+        const bool octagon = !full_cols && plane_off > 1e-3f * r3d;
+        float ph_lo = -4.f, ph_hi = 4.f;        // azimuth (full columns outside [-pi, pi])
+        float yn_lo = -1e30f, yn_hi = 1e30f;    // y_n (full rows when unbounded)
+        if (octagon) {
+            const float cs[8] = {0.92387953f, 0.38268343f, -0.38268343f, -0.92387953f,
+                                 -0.92387953f, -0.38268343f, 0.38268343f, 0.92387953f};
+            const float sn[8] = {0.38268343f, 0.92387953f, 0.92387953f, 0.38268343f,
+                                 -0.38268343f, -0.92387953f, -0.92387953f, -0.38268343f};
+            // every vertex lies within rad < rh of the centre, so its
+            // horizontal direction is within 90 deg of the centre's and its
+            // azimuth offset atan2(cross, dot) increases with cross / dot
+            const float ux = ms.x / rh, uz = ms.z / rh;
+            F3 V[8];
+            float rv[8];
+            float t_lo = 0.f, t_hi = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                V[j] = ms + kk * (cs[j] * a + sn[j] * b);
+                rv[j] = sqrtf(fmaf(V[j].x, V[j].x, V[j].z * V[j].z));
+                const float cr = fmaf(uz, V[j].x, -ux * V[j].z), dt = fmaf(ux, V[j].x, uz * V[j].z);
+                const float t = cr / dt;
+                t_lo = fminf(t_lo, t);
+                t_hi = fmaxf(t_hi, t);
+            }
+            ph_lo = phc + atanf(t_lo);
+            ph_hi = phc + atanf(t_hi);
+            float s_lo = 1e30f, s_hi = -1e30f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const F3 P0 = V[j], P1 = V[(j + 1) & 7];
+                const float rmin = seg_dist(P0.x, P0.z, P1.x, P1.z);
+                const float rmax = fmaxf(rv[j], rv[(j + 1) & 7]);
+                const float ymax = fmaxf(P0.y, P1.y), ymin = fminf(P0.y, P1.y);
+                s_hi = fmaxf(s_hi, ymax / (ymax >= 0.f ? rmin : rmax));
+                s_lo = fminf(s_lo, ymin / (ymin <= 0.f ? rmin : rmax));
+            }
+            yn_lo = s_lo;
+            yn_hi = s_hi;
+        } else if (r3d > rad * 1.0001f + 1e-6f) {
+            const float beta = asinf(fminf(rad / r3d, 1.f));
+            const float el = atan2f(ms.y, rh);
+            if (el + beta < 1.5f) yn_hi = tanf(el + beta);
+            if (el - beta > -1.5f) yn_lo = tanf(el - beta);
+            if (!full_cols) {
+                const float gam = asinf(fminf(rad / rh, 1.f));
+                ph_lo = phc - gam;
+                ph_hi = phc + gam;
+            }
+        }
+        float xmin = ccx - rlp, xmax = ccx + rlp;
+        float ymin = ccy - rlp, ymax = ccy + rlp;
+        if (ph_lo >= -3.14159265f && ph_hi <= 3.14159265f) {
+            xmin = fminf(xmin, fmaf(sd.fx, ph_lo, sd.cx));
+            xmax = fmaxf(xmax, fmaf(sd.fx, ph_hi, sd.cx));
+        } else {
+            xmin = -2.f;
+            xmax = (float)sd.width + 2.f;
+        }
+        ymin = yn_lo > -1e29f ? fminf(ymin, fmaf(sd.fy, yn_lo, sd.cy)) : -2.f;
+        ymax = yn_hi < 1e29f ? fmaxf(ymax, fmaf(sd.fy, yn_hi, sd.cy)) : (float)sd.height + 2.f;
+        // one pixel of margin for FP32 rounding
+        int x0, x1, y0, y1;
+        index_range(xmin - 1.f, xmax + 1.f, 0.5f, sd.width, x0, x1);
+        index_range(ymin - 1.f, ymax + 1.f, 0.5f, sd.height, y0, y1);
+        if (x0 <= x1 && y0 <= y1) {
+            r5 = make_float4((float)x0, (float)x1, (float)y0, (float)y1);
+            rect = make_ushort4(x0 / TW, x1 / TW, y0 / TH, y1 / TH);
+            cnt = (uint32_t)(rect.y - rect.x + 1) * (uint32_t)(rect.w - rect.z + 1);
+        }
     } else {
         const float rc = sqrtf(dot(ms, ms));
         zkey = rc;
@@ -427,7 +539,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     if (dot(nw, vd) > 0.f) nw = -1.f * nw;
     const F3 ns = mat3(sd.R, nw);
     float4 r3;
-    if (sd.kind == GSR_SENSOR_PINHOLE) {
+    if (sd.kind != GSR_SENSOR_LIDAR) {
         vd = rsqrtf(vlen2) * vd;
         if (Ro != nullptr) {
             float Rm[9] = {__ldg(Ro), __ldg(Ro + 1), __ldg(Ro + 2), __ldg(Ro + 4), __ldg(Ro + 5),

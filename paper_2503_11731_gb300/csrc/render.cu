@@ -158,7 +158,7 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                         const float w = alpha * s.T;
                         const float4 r3 = Rj[3];
                         s.f0 = fmaf(w, r3.y, s.f0);
-                        if (KIND == GSR_SENSOR_PINHOLE) {
+                        if (KIND != GSR_SENSOR_LIDAR) {
                             s.f1 = fmaf(w, r3.z, s.f1);
                             s.f2 = fmaf(w, r3.w, s.f2);
                             const float4 r4 = Rj[4];
@@ -196,7 +196,7 @@ __device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ra
     if (!ray.inside) return;
     const size_t HW = (size_t)sd.width * sd.height;
     const size_t pix = (size_t)ray.y * sd.width + ray.x;
-    if (KIND == GSR_SENSOR_PINHOLE) {
+    if (KIND != GSR_SENSOR_LIDAR) {
         if (out.color) {
             out.color[pix] = fmaf(s.T, sd.bg[0], s.f0);
             out.color[HW + pix] = fmaf(s.T, sd.bg[1], s.f1);
@@ -410,6 +410,9 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_rig(SensorTabl
         if (sd.kind == GSR_SENSOR_PINHOLE)
             render_tile<GSR_SENSOR_PINHOLE>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
                                             gb, sp, D);
+        else if (sd.kind == GSR_SENSOR_CYLINDRICAL)
+            render_tile<GSR_SENSOR_CYLINDRICAL>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf,
+                                                bars, gb, sp, D);
         else
             render_tile<GSR_SENSOR_LIDAR>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
                                           gb, sp, D);
@@ -449,6 +452,9 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTa
         if (sd.kind == GSR_SENSOR_PINHOLE)
             render_chunk<GSR_SENSOR_PINHOLE>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
                                              buf, bars, gb, sp, &flag_s, D);
+        else if (sd.kind == GSR_SENSOR_CYLINDRICAL)
+            render_chunk<GSR_SENSOR_CYLINDRICAL>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s],
+                                                 counters, buf, bars, gb, sp, &flag_s, D);
         else
             render_chunk<GSR_SENSOR_LIDAR>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
                                            buf, bars, gb, sp, &flag_s, D);
@@ -543,6 +549,10 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
         if ((e = smem_attr(k_render<GSR_SENSOR_PINHOLE>, smem)) != cudaSuccess) return e;
         k_render<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters,
                                                                    sp);
+    } else if (sd.kind == GSR_SENSOR_CYLINDRICAL) {
+        if ((e = smem_attr(k_render<GSR_SENSOR_CYLINDRICAL>, smem)) != cudaSuccess) return e;
+        k_render<GSR_SENSOR_CYLINDRICAL><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out,
+                                                                       counters, sp);
     } else {
         if ((e = smem_attr(k_render<GSR_SENSOR_LIDAR>, smem)) != cudaSuccess) return e;
         k_render<GSR_SENSOR_LIDAR><<<tiles, threads, smem, st>>>(tab, sensor, rec, ranges, pval, out, counters, sp);

@@ -64,6 +64,8 @@ class Renderer:
         `split` = (split_first, split_chunk) of long tile lists (0 = the library's defaults)."""
         self.descs = list(sensors)
         tiles = tiles if tiles is not None else [None] * len(self.descs)
+        if len(tiles) != len(self.descs):
+            raise ValueError(f"{len(tiles)} tiles for {len(self.descs)} sensors")
         self.structs = [gsr.sensor(d, bg, t) for d, t in zip(self.descs, tiles)]
         self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup, batch_depth, split)
         self.ws_bytes = gsr.workspace_size(self.plan)
@@ -170,7 +172,7 @@ class Renderer:
         consecutive in the plan) and re-plan with it; returns the trial list."""
         obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
         has = {d.kind for d in self.descs}
-        space = gsr.autotune_space(camera_tiles if "pinhole" in has else (),
+        space = gsr.autotune_space(camera_tiles if has - {"lidar"} else (),
                                    lidar_tiles if "lidar" in has else (), batch_depths, warmup, reps,
                                    split_firsts, split_chunks)
         need = gsr.autotune_workspace_size(self.plan, space)
@@ -183,13 +185,14 @@ class Renderer:
         trials = [{"camera_tile": tuple(t.camera_tile), "lidar_tile": tuple(t.lidar_tile),
                    "batch_depth": t.batch_depth, "split": (t.split_first, t.split_chunk), "ms": t.ms}
                   for t in res.tried[:res.n_tried]]
-        return {"best_ms": res.best_ms, "trials": trials, "camera_tile": self.tile_of("pinhole"),
+        return {"best_ms": res.best_ms, "trials": trials, "camera_tile": self.tile_of("camera"),
                 "lidar_tile": self.tile_of("lidar"), "batch_depth": self.plan.tiling.batch_depth,
                 "split": (self.plan.tiling.split_first, self.plan.tiling.split_chunk)}
 
     def tile_of(self, kind):
+        """Tile of the first sensor of `kind` ("camera" = pinhole or cylindrical)."""
         for i, d in enumerate(self.descs):
-            if d.kind == kind:
+            if d.kind == kind or (kind == "camera" and d.kind != "lidar"):
                 s = self.plan.sensors[i]
                 return (s.tile_w, s.tile_h)
         return None

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgsr.so")
 
 MAX_SENSORS = 16
-PINHOLE, LIDAR = 0, 1
+PINHOLE, LIDAR, CYLINDRICAL = 0, 1, 2
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(8)
 NOALLOC_MAX_PIXELS = 2097152
@@ -213,17 +213,18 @@ def _check(code, where):
 
 # ----------------------------------------------------------------- structs
 def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None) -> Sensor:
-    """Sensor struct from a synth.Pinhole / synth.Lidar-like description;
+    """Sensor struct from a synth.Pinhole / synth.Cylindrical / synth.Lidar-like description;
     `tile` = (w, h) overrides the plan's default tiling for this sensor."""
     s = Sensor()
     if tile is not None:
         s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
-    if getattr(desc, "kind", "pinhole") == "lidar":
+    kind = getattr(desc, "kind", "pinhole")
+    if kind == "lidar":
         s.kind = LIDAR
         s.width, s.height = int(desc.columns), int(desc.beams)
         s.el_min_deg, s.el_max_deg, s.az0_deg = float(desc.el_min_deg), float(desc.el_max_deg), float(desc.az0_deg)
     else:
-        s.kind = PINHOLE
+        s.kind = CYLINDRICAL if kind == "cylindrical" else PINHOLE
         s.width, s.height = int(desc.width), int(desc.height)
         s.fx, s.fy, s.cx, s.cy = float(desc.fx), float(desc.fy), float(desc.cx), float(desc.cy)
     s.near_plane = float(desc.near)

@@ -66,6 +66,13 @@ def test_argument_errors(L):
     with pytest.raises(gsr.GsrError) as e:
         gsr.plan_init(10, [bad])
     assert e.value.code == gsr.ERR_INVALID_ARG
+    # a cylindrical image must stay within azimuths [-pi, pi]
+    wide = gsr.sensor(synth.cylindrical(400, 100, 200.0, 60.0))
+    wide.fx = 400 / 7.0
+    with pytest.raises(gsr.GsrError) as e:
+        gsr.plan_init(10, [wide])
+    assert e.value.code == gsr.ERR_INVALID_ARG
+    assert gsr.plan_init(10, [gsr.sensor(synth.cylindrical(400, 100, 360.0, 60.0))]).sensors[0].kind == gsr.CYLINDRICAL
     p = gsr.plan_init(10, [cam])
     # undersized / misaligned workspace is rejected before any launch
     buf = (ctypes.c_uint8 * 1024)()

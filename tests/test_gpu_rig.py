@@ -24,7 +24,8 @@ def _small_rig():
     sensors = [synth.pinhole(320, 180, 170.0, (1.5, 0, 1.5), 0.0),
                synth.pinhole(256, 144, 120.0, (0.0, 0.0, 1.6), 60.0),
                synth.spinning_lidar(32, 360, -25.0, 15.0, (0.0, 0.0, 1.8)),
-               synth.spinning_lidar(16, 256, -30.0, 10.0, (0.5, 0.0, 1.9))]
+               synth.spinning_lidar(16, 256, -30.0, 10.0, (0.5, 0.0, 1.9)),
+               synth.cylindrical(480, 120, 200.0, 60.0, (0.0, 0.0, 1.7), yaw_deg=180.0)]
     return scene, poses, sensors
 
 
@@ -34,7 +35,7 @@ def _renderer(scene, sensors, tiles):
                     outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
 
 
-TILES = [(16, 16), (32, 8), (8, 8), (16, 4)]
+TILES = [(16, 16), (32, 8), (8, 8), (16, 4), (16, 8)]
 
 
 def test_rig_launch_equals_per_sensor_calls(gpu_lib):
@@ -180,7 +181,7 @@ def test_batch_depth_and_tile_shape_change_speed_only(gpu_lib):
         for i, (oa, ob) in enumerate(zip(ref, o)):
             for k in oa:
                 assert torch.equal(oa[k], ob[k]), (bd, i, k)
-    r = Renderer(scene.n, sensors, tiles=[(8, 8), (8, 4), (16, 16), (8, 8)], outputs=outs)
+    r = Renderer(scene.n, sensors, tiles=[(8, 8), (8, 4), (16, 16), (8, 8), (32, 8)], outputs=outs)
     o = r.render_rig(d, P)
     torch.cuda.synchronize()
     for i, (oa, ob) in enumerate(zip(ref, o)):

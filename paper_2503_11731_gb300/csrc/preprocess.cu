@@ -295,65 +295,75 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
         r1 = make_float4(q10, q11, q12, ccy);
         r2 = make_float4(q20, q21, q22, det);
 
-        // Bound of the support ellipse (inside the circumscribed octagon, as
-        // for the LiDAR) united with the low-pass disc.  With the octagon's
-        // xz-projection away from the y axis, the azimuth phi = atan2(x, z)
-        // is monotonic along each edge and takes its extremes at vertices;
-        // y_n = y / sqrt(x^2 + z^2) has a gradient orthogonal to the position,
-        // so on a plane that misses the centre it has no interior extremum and
-        // per-edge bounds (max y over min horizontal distance, ...) cover it.
-        // Otherwise the bounding sphere of the octagon bounds the elevation
-        // atan(y_n).  Azimuth ranges that leave [-pi, pi] take every column.
+        // Bound of the support ellipse, inside the circumscribed octagon (as
+        // for the LiDAR), united with the low-pass disc.  When every vertex's
+        // horizontal position lies in the open half-plane facing the centre's
+        // azimuth, the octagon's xz-projection misses the y axis: the azimuth
+        // phi = atan2(x, z) takes its extremes at vertices, where the offset
+        // from the centre's azimuth is atan(cross / dot) with dot > 0; and
+        // y_n = y / sqrt(x^2 + z^2), whose gradient is orthogonal to the
+        // position, has no interior extremum on a plane that misses the camera
+        // centre, so per-edge bounds (max y over the edge's least horizontal
+        // distance, ...) cover it.  Otherwise every column is taken, and when
+        // all vertices lie on one side of the camera's horizontal plane y_n
+        // keeps that sign with |y_n| >= min |y| / (largest horizontal distance,
+        // reached at a vertex).  A plane through (nearly) the camera centre
+        // takes the elevation range of the bounding sphere.  Azimuth ranges
+        // that leave [-pi, pi] take every column.
         const float kk = ksig * 1.0823922f;
         const float rad = kk * fmaxf(su, sv);
         const float r3d = sqrtf(dot(ms, ms));
-        const bool full_cols = !(rh > rad * 1.0001f + 1e-6f);
         F3 nrm = f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
         const float plane_off = fabsf(dot(nrm, ms)) * rsqrtf(fmaxf(dot(nrm, nrm), 1e-30f));
-        const bool octagon = !full_cols && plane_off > 1e-3f * r3d;
         float ph_lo = -4.f, ph_hi = 4.f;        // azimuth (full columns outside [-pi, pi])
         float yn_lo = -1e30f, yn_hi = 1e30f;    // y_n (full rows when unbounded)
-        if (octagon) {
+        if (plane_off > 1e-3f * r3d) {
             const float cs[8] = {0.92387953f, 0.38268343f, -0.38268343f, -0.92387953f,
                                  -0.92387953f, -0.38268343f, 0.38268343f, 0.92387953f};
             const float sn[8] = {0.38268343f, 0.92387953f, 0.92387953f, 0.38268343f,
                                  -0.38268343f, -0.92387953f, -0.92387953f, -0.38268343f};
-            // every vertex lies within rad < rh of the centre, so its
-            // horizontal direction is within 90 deg of the centre's and its
-            // azimuth offset atan2(cross, dot) increases with cross / dot
             const float ux = ms.x / rh, uz = ms.z / rh;
             F3 V[8];
             float rv[8];
-            float t_lo = 0.f, t_hi = 0.f;
+            float t_lo = 0.f, t_hi = 0.f, dmin = 1e30f, vy_lo = 1e30f, vy_hi = -1e30f, r_far = 0.f;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 V[j] = ms + kk * (cs[j] * a + sn[j] * b);
                 rv[j] = sqrtf(fmaf(V[j].x, V[j].x, V[j].z * V[j].z));
                 const float cr = fmaf(uz, V[j].x, -ux * V[j].z), dt = fmaf(ux, V[j].x, uz * V[j].z);
+                dmin = fminf(dmin, dt);
                 const float t = cr / dt;
                 t_lo = fminf(t_lo, t);
                 t_hi = fmaxf(t_hi, t);
+                vy_lo = fminf(vy_lo, V[j].y);
+                vy_hi = fmaxf(vy_hi, V[j].y);
+                r_far = fmaxf(r_far, rv[j]);
             }
-            ph_lo = phc + atanf(t_lo);
-            ph_hi = phc + atanf(t_hi);
-            float s_lo = 1e30f, s_hi = -1e30f;
+            if (dmin > 1e-6f * rh) {
+                ph_lo = phc + atanf(t_lo);
+                ph_hi = phc + atanf(t_hi);
+                float s_lo = 1e30f, s_hi = -1e30f;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const F3 P0 = V[j], P1 = V[(j + 1) & 7];
-                const float rmin = seg_dist(P0.x, P0.z, P1.x, P1.z);
-                const float rmax = fmaxf(rv[j], rv[(j + 1) & 7]);
-                const float ymax = fmaxf(P0.y, P1.y), ymin = fminf(P0.y, P1.y);
-                s_hi = fmaxf(s_hi, ymax / (ymax >= 0.f ? rmin : rmax));
-                s_lo = fminf(s_lo, ymin / (ymin <= 0.f ? rmin : rmax));
+                for (int j = 0; j < 8; ++j) {
+                    const F3 P0 = V[j], P1 = V[(j + 1) & 7];
+                    const float rmin = seg_dist(P0.x, P0.z, P1.x, P1.z);
+                    const float rmax = fmaxf(rv[j], rv[(j + 1) & 7]);
+                    const float ymax = fmaxf(P0.y, P1.y), ymin = fminf(P0.y, P1.y);
+                    s_hi = fmaxf(s_hi, ymax / (ymax >= 0.f ? rmin : rmax));
+                    s_lo = fminf(s_lo, ymin / (ymin <= 0.f ? rmin : rmax));
+                }
+                yn_lo = s_lo;
+                yn_hi = s_hi;
+            } else {
+                if (vy_lo > 0.f) yn_lo = vy_lo / r_far;
+                if (vy_hi < 0.f) yn_hi = vy_hi / r_far;
             }
-            yn_lo = s_lo;
-            yn_hi = s_hi;
         } else if (r3d > rad * 1.0001f + 1e-6f) {
             const float beta = asinf(fminf(rad / r3d, 1.f));
             const float el = atan2f(ms.y, rh);
             if (el + beta < 1.5f) yn_hi = tanf(el + beta);
             if (el - beta > -1.5f) yn_lo = tanf(el - beta);
-            if (!full_cols) {
+            if (rh > rad * 1.0001f + 1e-6f) {
                 const float gam = asinf(fminf(rad / rh, 1.f));
                 ph_lo = phc - gam;
                 ph_hi = phc + gam;

@@ -262,6 +262,11 @@ def bin_sort_launches(plan):
     return 3 + 20 + 4 + 5 * ((bits + 7) // 8) + 1 + 1 + 1 + 10
 
 
+def preprocess_launches(plan):
+    """Kernel launches of one gsr_preprocess(_part): one per sensor model present."""
+    return len({plan.sensors[i].kind for i in range(plan.n_sensors)})
+
+
 class Timer:
     """Per-stage CUDA events on one stream."""
 
@@ -478,7 +483,7 @@ def run_gpu(args):
         G = nf.graphs()
         stages = [("decode", G["decode"].replay), ("pre_sort", G["front"].replay),
                   ("render_rig", lambda: G["render_rig"].launch(sh))]
-        n_launch = 1 + 2 + bin_sort_launches(r.plan) + 2
+        n_launch = 1 + 2 * preprocess_launches(r.plan) + bin_sort_launches(r.plan) + 2
         n_main = nf.n_bg + objs.n
     else:
         r.render_rig(dev, pose_t)
@@ -488,7 +493,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         gf, gr = r.graph(dev, pose_t, stages=3), r.graph(dev, pose_t, stages=4)
         stages = [("pre_sort", lambda: gf.launch(sh)), ("render_rig", lambda: gr.launch(sh))]
-        n_launch = 1 + bin_sort_launches(r.plan) + 2
+        n_launch = preprocess_launches(r.plan) + bin_sort_launches(r.plan) + 2
         n_main = scene.n
     tiling = {"tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
               "batch_depth": r.plan.tiling.batch_depth or "CTA width",

@@ -12,8 +12,9 @@
 
 namespace gsr {
 
-__global__ void k_preprocess(SensorTable tab, gsr_surfels S, const float* poses, int n_obj, float4* rec,
-                             ushort4* rects, uint32_t* counts, uint32_t* keys, uint4* spans, int first, int n_plan);
+cudaError_t launch_preprocess(const SensorTable& tab, const gsr_surfels& S, const float* poses, int n_obj,
+                              float4* rec, ushort4* rects, uint32_t* counts, uint32_t* keys, uint4* spans,
+                              int first, int n_plan, cudaStream_t st);
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st);
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st);
 cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd, const float* target,
@@ -236,13 +237,10 @@ extern "C" gsr_status gsr_preprocess_part(const gsr_plan* plan, const gsr_surfel
     }
     if (surfels->n > 0) {
         const SensorTable tab = make_sensor_table(plan);
-        dim3 grid((surfels->n + 255) / 256, plan->n_sensors);
-        k_preprocess<<<grid, 256, 0, s>>>(tab, *surfels, poses, n_obj, region<float4>(plan, workspace, R_RECORDS),
-                                          region<ushort4>(plan, workspace, R_RECTS),
-                                          region<uint32_t>(plan, workspace, R_COUNTS),
-                                          region<uint32_t>(plan, workspace, R_DEPTHKEY),
-                                          region<uint4>(plan, workspace, R_SPANS), first, plan->n_surfels);
-        e = cudaGetLastError();
+        e = launch_preprocess(tab, *surfels, poses, n_obj, region<float4>(plan, workspace, R_RECORDS),
+                              region<ushort4>(plan, workspace, R_RECTS), region<uint32_t>(plan, workspace, R_COUNTS),
+                              region<uint32_t>(plan, workspace, R_DEPTHKEY), region<uint4>(plan, workspace, R_SPANS),
+                              first, plan->n_surfels, s);
     }
     return cuda_fail(e);
 }

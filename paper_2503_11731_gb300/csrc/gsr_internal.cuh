@@ -102,6 +102,12 @@ struct SensorTable {
     SensorDev s[GSR_MAX_SENSORS];
 };
 
+// The plan's sensors of one model (kernels instantiated per model).
+struct SensorIds {
+    int n;
+    uint8_t id[GSR_MAX_SENSORS];
+};
+
 // First list position of chunk c of a split tile.
 __host__ __device__ __forceinline__ int chunk_begin(int first, int chunk, int c)
 {

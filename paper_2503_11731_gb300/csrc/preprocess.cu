@@ -136,14 +136,18 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 
 // Surfel i of the table S is surfel `first + i` of the plan (n_plan surfels),
 // so several tables (e.g. a decoded background and posed objects) can share
-// one plan.  Composite ties break by plan index, as in a single table.
-__global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels S, const float* __restrict__ poses,
-                                                    int n_obj, float4* __restrict__ rec, ushort4* __restrict__ rects,
+// one plan.  Composite ties break by plan index, as in a single table.  One
+// instantiation per sensor model keeps each one's registers to its own
+// bound; grid.y walks the plan's sensors of that model (ids).
+template <int KIND>
+__global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorIds ids, gsr_surfels S,
+                                                    const float* __restrict__ poses, int n_obj,
+                                                    float4* __restrict__ rec, ushort4* __restrict__ rects,
                                                     uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,
                                                     uint4* __restrict__ spans, int first, int n_plan)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int si = blockIdx.y;
+    const int si = ids.id[blockIdx.y];
     if (i >= S.n) return;
     const SensorDev& sd = tab.s[si];
     const size_t slot = (size_t)si * n_plan + first + i;
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     const float rlp = sqrtf(fmaxf(0.5f * rho_cut, 0.f));
     const bool never = !(rho_cut > 0.f);
 
-    if (sd.kind == GSR_SENSOR_PINHOLE) {
+    if (KIND == GSR_SENSOR_PINHOLE) {
         zkey = ms.z;
         if (!(ms.z > sd.near_plane) || never) {
             counts[slot] = 0;
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
                 rect.w |= kRectExact;
             }
         }
-    } else if (sd.kind == GSR_SENSOR_CYLINDRICAL) {
+    } else if (KIND == GSR_SENSOR_CYLINDRICAL) {
         // Eq. 4: pixel (x, y) looks along (sin phi, y_n, cos phi) with
         // phi = (x + 1/2 - c_x) / f_x and y_n = (y + 1/2 - c_y) / f_y; depth
         // and order key are the horizontal distance sqrt(x^2 + z^2)
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     if (dot(nw, vd) > 0.f) nw = -1.f * nw;
     const F3 ns = mat3(sd.R, nw);
     float4 r3;
-    if (sd.kind != GSR_SENSOR_LIDAR) {
+    if (KIND != GSR_SENSOR_LIDAR) {
         vd = rsqrtf(vlen2) * vd;
         if (Ro != nullptr) {
             float Rm[9] = {__ldg(Ro), __ldg(Ro + 1), __ldg(Ro + 2), __ldg(Ro + 4), __ldg(Ro + 5),
@@ -569,6 +573,34 @@ __global__ void __launch_bounds__(256) k_preprocess(SensorTable tab, gsr_surfels
     R[3] = r3;
     R[4] = make_float4(ns.x, ns.y, ns.z, zkey);
     R[5] = r5;
+}
+
+
+// One launch per sensor model present in the plan.
+cudaError_t launch_preprocess(const SensorTable& tab, const gsr_surfels& S, const float* poses, int n_obj,
+                              float4* rec, ushort4* rects, uint32_t* counts, uint32_t* keys, uint4* spans,
+                              int first, int n_plan, cudaStream_t st)
+{
+    for (int kind = 0; kind < 3; ++kind) {
+        SensorIds ids;
+        ids.n = 0;
+        for (int i = 0; i < tab.n; ++i)
+            if (tab.s[i].kind == kind) ids.id[ids.n++] = (uint8_t)i;
+        if (ids.n == 0) continue;
+        const dim3 grid((S.n + 255) / 256, ids.n);
+        if (kind == GSR_SENSOR_PINHOLE)
+            k_preprocess<GSR_SENSOR_PINHOLE><<<grid, 256, 0, st>>>(tab, ids, S, poses, n_obj, rec, rects, counts,
+                                                                   keys, spans, first, n_plan);
+        else if (kind == GSR_SENSOR_LIDAR)
+            k_preprocess<GSR_SENSOR_LIDAR><<<grid, 256, 0, st>>>(tab, ids, S, poses, n_obj, rec, rects, counts, keys,
+                                                                 spans, first, n_plan);
+        else
+            k_preprocess<GSR_SENSOR_CYLINDRICAL><<<grid, 256, 0, st>>>(tab, ids, S, poses, n_obj, rec, rects,
+                                                                       counts, keys, spans, first, n_plan);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace gsr

@@ -338,48 +338,20 @@ __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* __restrict__
     return lo;
 }
 
-__device__ __forceinline__ void put_pair(const SensorDev& sd, int ty, int tx, uint32_t slot, uint64_t o,
-                                         uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
-{
-    const int txm = tx < sd.tiles_x ? tx : tx - sd.tiles_x;  // LiDAR azimuth wrap
-    pkey[o] = (uint32_t)(sd.tile_base + ty * sd.tiles_x + txm);
-    pval[o] = slot;
-}
-
-// Each visible slot writes (global tile id, slot) for every tile of its
-// rectangle, row-major, at its pair offset; pairs beyond max_dup are dropped.
-// Camera slots marked kRectExact emit only the tiles their footprint
-// reaches, with the same test the preprocess counted with.  Work is split by
-// PAIRS: CTA g writes the pairs [P g / G, P (g + 1) / G) of the P kept, so
-// the few near-field slots with thousands of tiles (all at the front of the
-// depth order) are shared by many CTAs.  Within a CTA, slots are taken 256 at
-// a time: small slots (<= kDupSmall pairs over <= kDupRows tile rows) put
-// their rows in a shared table and the CTA writes all their pairs with one
-// thread per pair (consecutive pairs, consecutive addresses); larger slots
-// are expanded by their warp (<= kDupWarp pairs) or by the whole CTA.
-constexpr uint32_t kDupSmall = 1024;
-constexpr int kDupRows = 8;
-constexpr uint32_t kDupWarp = 4096;
-
-struct DupSlot {
-    uint32_t slot;
-    const SensorDev* sd;
-    ushort4 r;
-    bool exact;
-    int ty1;
-};
-
-__device__ __forceinline__ DupSlot dup_slot(const SensorTable& tab, int n_surfels, uint32_t slot,
-                                            const ushort4* __restrict__ rects)
-{
-    DupSlot d;
-    d.slot = slot;
-    d.sd = &tab.s[slot / (uint32_t)n_surfels];
-    d.r = rects[slot];
-    d.exact = (d.r.w & kRectExact) != 0;
-    d.ty1 = d.r.w & ~kRectExact;
-    return d;
-}
+// Each visible slot writes (global tile id, slot) for every tile its bound
+// keeps, row by row, at its pair offset; pairs beyond max_dup are dropped.
+// Camera slots marked kRectExact keep only the tiles of each row that their
+// footprint reaches, with the same test the preprocess counted with (or the
+// spans it cached).  Work is split by PAIRS: CTA g writes the pairs
+// [P g / G, P (g + 1) / G) of the P kept.  A CTA takes its slots 256 at a
+// time and lists their tile rows, kDupRowsRound at a time: one thread per
+// row finds the row's span, a block scan gives every row its first pair,
+// and each warp then writes 256 consecutive pairs at a time, lane l the
+// pairs l, l + 32, ... (coalesced stores), walking the rows.  The cost per
+// pair no longer depends on how the pairs fall into slots and rows.
+constexpr int kDupRowsRound = 1024;
+constexpr int kDupCtasPerSortCta = 8;
+constexpr int kDupRowsPerThread = kDupRowsRound / 256;
 
 __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
                                                    const uint32_t* __restrict__ vis_val,
@@ -390,18 +362,22 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
                                                    const float4* __restrict__ rec, const uint4* __restrict__ spans,
                                                    uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval)
 {
-    __shared__ uint32_t big_s[256];
-    __shared__ uint32_t n_big_s, rb_s, re_s;
-    __shared__ uint32_t pre_s[257], t0_s[256];
+    // per slot of the batch
+    __shared__ uint32_t s_off[256], s_cnt[256], s_slot[256], s_start[256], s_rowpre[257];
+    __shared__ ushort4 s_rect[256];
+    __shared__ uint4 s_span[256];
+    __shared__ uint8_t s_sen[256];
+    // per row of the round
+    __shared__ uint32_t r_pre[kDupRowsRound + 1];  // first pair of the row within the round
+    __shared__ uint32_t r_q0[kDupRowsRound];       // global position of the row's first pair
+    __shared__ uint32_t r_key0[kDupRowsRound];     // tile id of column 0 of the row
+    __shared__ uint16_t r_t0[kDupRowsRound], r_len[kDupRowsRound], r_lim[kDupRowsRound], r_tx[kDupRowsRound];
+    __shared__ uint8_t r_slot[kDupRowsRound];
     __shared__ uint32_t scan_s[9];
-    // small-slot table: per slot its offset, slot id and sensor; per row its
-    // tile row, first tile column and the running pair count at its end
-    __shared__ uint32_t so_s[256], sslot_s[256], spre_s[257];
-    __shared__ uint8_t ssen_s[256];
-    __shared__ uint16_t rty_s[256][kDupRows], rt0_s[256][kDupRows], rcum_s[256][kDupRows];
+    __shared__ uint32_t rb_s, re_s;
     const uint32_t n_vis = counters[C_NVIS];
     const uint32_t P = counters[C_NDUP];
-    const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31;
+    const int G = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p0 = (uint32_t)((uint64_t)P * blockIdx.x / G), p1 = (uint32_t)((uint64_t)P * (blockIdx.x + 1) / G);
     if (p0 >= p1) return;
     if (tid == 0) {
@@ -411,174 +387,146 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
     __syncthreads();
     const uint32_t rb = rb_s, re = re_s;
     for (uint32_t base = rb; base < re; base += 256) {
-        if (tid == 0) n_big_s = 0;
-        __syncthreads();
+        // 1. the batch's slots and their tile-row counts
         const uint32_t i = base + tid;
-        uint32_t c = i < re ? cnt_sorted[i] : 0u;
-        const uint32_t o = i < re ? offs[i] : 0u;
-        if (c > kDupWarp) big_s[atomicAdd(&n_big_s, 1u)] = i;
-        // small slots: their rows into the table (a slot with more rows than
-        // the table holds goes to its warp instead)
-        uint32_t csmall = 0;
-        if (c > 0 && c <= kDupSmall) {
-            const DupSlot d = dup_slot(tab, n_surfels, vis_val[i], rects);
-            int nr = 0;
-            uint32_t cum = 0;
-            bool fits = true;
-            uint4 tb = make_uint4(0u, 0u, 0u, 0u);
-            if (d.exact) tb = spans[d.slot];
-            // byte b of the span table
-            auto byte_of = [&](int b) -> uint32_t {
-                const uint32_t w = b < 4 ? tb.x : b < 8 ? tb.y : b < 12 ? tb.z : tb.w;
-                return (w >> (8 * (b & 3))) & 0xffu;
-            };
-            const int cached = d.exact ? (int)byte_of(0) : 0;
-            if (cached > 0) {
-                // the spans the preprocess cached
-                for (int k = 0; k < cached && nr < kDupRows; ++k) {
-                    const uint32_t len = byte_of(2 + 2 * k);
-                    if (len == 0) continue;
-                    cum += len;
-                    rty_s[tid][nr] = (uint16_t)(d.r.z + k);
-                    rt0_s[tid][nr] = (uint16_t)(d.r.x + byte_of(1 + 2 * k));
-                    rcum_s[tid][nr] = (uint16_t)cum;
-                    ++nr;
-                }
-            } else {
-                Footprint fp;
-                if (d.exact) {
-                    const float4* R = rec + (size_t)d.slot * kRecordF4;
-                    fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                }
-                for (int ty = d.r.z; ty <= d.ty1; ++ty) {
-                    int t0 = d.r.x, t1 = d.r.y;
-                    if (d.exact && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
-                        continue;
-                    if (nr == kDupRows) {
-                        fits = false;
-                        break;
-                    }
-                    cum += (uint32_t)(t1 - t0 + 1);
-                    rty_s[tid][nr] = (uint16_t)ty;
-                    rt0_s[tid][nr] = (uint16_t)t0;
-                    rcum_s[tid][nr] = (uint16_t)cum;
-                    ++nr;
-                }
-            }
-            if (fits) {
-                csmall = min(cum, c);  // the count the preprocess made (equal by construction)
-                so_s[tid] = o;
-                sslot_s[tid] = d.slot;
-                ssen_s[tid] = (uint8_t)(d.slot / (uint32_t)n_surfels);
-                c = 0;  // done here
+        uint32_t nrows = 0;
+        s_cnt[tid] = 0;
+        if (i < re) {
+            const uint32_t c = cnt_sorted[i];
+            s_cnt[tid] = c;
+            s_off[tid] = offs[i];
+            if (c > 0) {
+                const uint32_t slot = vis_val[i];
+                const ushort4 rc = rects[slot];
+                const bool exact = (rc.w & kRectExact) != 0;
+                s_slot[tid] = slot;
+                s_rect[tid] = rc;
+                s_sen[tid] = (uint8_t)(slot / (uint32_t)n_surfels);
+                s_span[tid] = exact ? spans[slot] : make_uint4(0u, 0u, 0u, 0u);
+                nrows = (uint32_t)((rc.w & ~kRectExact) - rc.z + 1);
             }
         }
-        uint32_t tot_small;
-        const uint32_t ex = block_exclusive_scan<uint32_t, 256>(csmall, tot_small, scan_s);
-        spre_s[tid] = ex;
-        if (tid == 0) spre_s[256] = tot_small;
+        uint32_t tot_rows;
+        const uint32_t rp = block_exclusive_scan<uint32_t, 256>(nrows, tot_rows, scan_s);
+        s_rowpre[tid] = rp;
+        if (tid == 0) s_rowpre[256] = tot_rows;
         __syncthreads();
-        for (uint32_t k = tid; k < tot_small; k += 256) {
-            // the slot of pair k (last with spre <= k) and its row
-            uint32_t lo = 0, hi = 256;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (spre_s[mid] <= k) lo = mid;
-                else hi = mid;
+        uint32_t carry = 0;  // pairs of the batch's earlier rounds
+        for (uint32_t R0 = 0; R0 < tot_rows; R0 += kDupRowsRound) {
+            const uint32_t nr = min(tot_rows - R0, (uint32_t)kDupRowsRound);
+            // 2. spans of rows R0 + 4 tid .. + 3
+            const uint32_t rl0 = (uint32_t)tid * kDupRowsPerThread;
+            uint32_t lens[kDupRowsPerThread];
+            uint32_t own = 0;
+            int sl = 0;
+            if (rl0 < nr) {
+                // the slot of the first row: the last with s_rowpre <= row
+                const uint32_t r = R0 + rl0;
+                int lo = 0, hi = 256;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_rowpre[mid] <= r) lo = mid;
+                    else hi = mid;
+                }
+                sl = lo;
             }
-            const uint32_t j = k - spre_s[lo];
-            const uint32_t q = so_s[lo] + j;
-            if (q < p0 || q >= p1) continue;
-            int rr = 0;
-            while (rcum_s[lo][rr] <= j) ++rr;
-            const uint32_t before = rr > 0 ? rcum_s[lo][rr - 1] : 0u;
-            put_pair(tab.s[ssen_s[lo]], rty_s[lo][rr], rt0_s[lo][rr] + (int)(j - before), sslot_s[lo], q, pkey, pval);
-        }
-        // warp: the remaining slots of this warp with c <= kDupWarp, one at a time
-        uint32_t wmask = __ballot_sync(0xffffffffu, c > 0 && c <= kDupWarp);
-        while (wmask) {
-            const int src = __ffs(wmask) - 1;
-            wmask &= wmask - 1;
-            const uint32_t j = base + (tid & ~31) + src;
-            const uint32_t oj = __shfl_sync(0xffffffffu, o, src), cj = __shfl_sync(0xffffffffu, c, src);
-            const uint32_t klo = p0 > oj ? p0 - oj : 0u, khi = min(cj, p1 - oj);
-            const DupSlot d = dup_slot(tab, n_surfels, vis_val[j], rects);
-            if (!d.exact) {
-                const uint32_t ncols = (uint32_t)(d.r.y - d.r.x + 1);
-                const uint32_t kend = min(khi, ncols * (uint32_t)(d.ty1 - d.r.z + 1));
-                for (uint32_t q = klo + lane; q < kend; q += 32)
-                    put_pair(*d.sd, d.r.z + (int)(q / ncols), d.r.x + (int)(q % ncols), d.slot, oj + q, pkey, pval);
-            } else {
-                const float4* R = rec + (size_t)d.slot * kRecordF4;
-                const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                uint32_t kc = 0;
-                for (int row0 = d.r.z; row0 <= d.ty1 && kc < khi; row0 += 32) {
-                    const int ty = row0 + lane;
-                    int t0 = 0, t1 = -1;
-                    if (ty <= d.ty1 && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
-                        t1 = -1;
-                    const uint32_t nrow = (ty <= d.ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
-                    uint32_t pre = nrow;  // warp inclusive scan of the row counts
 #pragma unroll
-                    for (int dd = 1; dd < 32; dd <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, pre, dd);
-                        if (lane >= dd) pre += y;
+            for (int k = 0; k < kDupRowsPerThread; ++k) {
+                const uint32_t rl = rl0 + k;
+                lens[k] = 0;
+                if (rl >= nr) continue;
+                const uint32_t r = R0 + rl;
+                while (s_rowpre[sl + 1] <= r) ++sl;
+                const ushort4 rc = s_rect[sl];
+                const SensorDev& sd = tab.s[s_sen[sl]];
+                const int ty = rc.z + (int)(r - s_rowpre[sl]);
+                int t0 = rc.x, t1 = rc.y;
+                if (rc.w & kRectExact) {
+                    const uint4 tb = s_span[sl];
+                    const int cached = (int)(tb.x & 0xffu);
+                    if (cached > 0) {
+                        const int kr = ty - rc.z;  // bytes 1 + 2 kr (first column) and 2 + 2 kr (length)
+                        const int b0 = 1 + 2 * kr, b1 = 2 + 2 * kr;
+                        const uint32_t w0 = b0 < 4 ? tb.x : b0 < 8 ? tb.y : b0 < 12 ? tb.z : tb.w;
+                        const uint32_t w1 = b1 < 4 ? tb.x : b1 < 8 ? tb.y : b1 < 12 ? tb.z : tb.w;
+                        t0 = rc.x + (int)((w0 >> (8 * (b0 & 3))) & 0xffu);
+                        t1 = t0 + (int)((w1 >> (8 * (b1 & 3))) & 0xffu) - 1;
+                    } else {
+                        const float4* R = rec + (size_t)s_slot[sl] * kRecordF4;
+                        const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
+                        if (!footprint_span(fp, ty, sd.tile_w, sd.tile_h, rc.x, rc.y, t0, t1)) t1 = t0 - 1;
                     }
-                    const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
-                    // this lane's row occupies sequence positions [kc + pre - nrow, kc + pre)
-                    uint32_t q = kc + pre - nrow;
-                    for (int tx = t0; tx <= t1 && q < khi; ++tx, ++q)
-                        if (q >= klo) put_pair(*d.sd, ty, tx, d.slot, oj + q, pkey, pval);
-                    kc += total;
+                }
+                const uint32_t len = t1 >= t0 ? (uint32_t)(t1 - t0 + 1) : 0u;
+                lens[k] = len;
+                own += len;
+                r_key0[rl] = (uint32_t)(sd.tile_base + ty * sd.tiles_x);
+                r_t0[rl] = (uint16_t)t0;
+                r_len[rl] = (uint16_t)len;
+                r_tx[rl] = (uint16_t)sd.tiles_x;
+                r_slot[rl] = (uint8_t)sl;
+            }
+            // 3. first pair of every row (block scan), the slot's first row
+            // sets its start, then each row's global position and the
+            // columns it may write (never past its slot's count)
+            uint32_t tot;
+            uint32_t pre = block_exclusive_scan<uint32_t, 256>(own, tot, scan_s);
+#pragma unroll
+            for (int k = 0; k < kDupRowsPerThread; ++k) {
+                const uint32_t rl = rl0 + k;
+                if (rl < nr) {
+                    r_pre[rl] = pre;
+                    const int s2 = r_slot[rl];
+                    if (R0 + rl == s_rowpre[s2]) s_start[s2] = carry + pre;
+                }
+                pre += lens[k];
+            }
+            if (tid == 0) r_pre[nr] = tot;
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kDupRowsPerThread; ++k) {
+                const uint32_t rl = rl0 + k;
+                if (rl < nr) {
+                    const int s2 = r_slot[rl];
+                    const uint32_t in_slot = carry + r_pre[rl] - s_start[s2];
+                    const uint32_t c = s_cnt[s2];
+                    r_q0[rl] = s_off[s2] + in_slot;
+                    r_lim[rl] = (uint16_t)(c > in_slot ? min(c - in_slot, (uint32_t)r_len[rl]) : 0u);
                 }
             }
-        }
-        __syncthreads();
-        // CTA: slots with more than kDupWarp pairs, one at a time
-        const uint32_t nb = n_big_s;
-        for (uint32_t k = 0; k < nb; ++k) {
-            const uint32_t j = big_s[k];
-            const uint32_t oj = offs[j], cj = cnt_sorted[j];
-            const uint32_t klo = p0 > oj ? p0 - oj : 0u;
-            uint32_t khi = min(cj, p1 - oj);
-            const DupSlot d = dup_slot(tab, n_surfels, vis_val[j], rects);
-            if (!d.exact) {
-                const uint32_t ncols = (uint32_t)(d.r.y - d.r.x + 1);
-                khi = min(khi, ncols * (uint32_t)(d.ty1 - d.r.z + 1));  // the rectangle's tiles only
-                for (uint32_t q = klo + tid; q < khi; q += 256)
-                    put_pair(*d.sd, d.r.z + (int)(q / ncols), d.r.x + (int)(q % ncols), d.slot, oj + q, pkey, pval);
-            } else {
-                const float4* R = rec + (size_t)d.slot * kRecordF4;
-                const Footprint fp = make_footprint(R[0], R[1], R[2], R[3].x);
-                uint32_t kc = 0;  // sequence position of this chunk of rows
-                for (int row0 = d.r.z; row0 <= d.ty1 && kc < khi; row0 += 256) {
-                    const int ty = row0 + tid;
-                    int t0 = 0, t1 = -1;
-                    if (ty <= d.ty1 && !footprint_span(fp, ty, d.sd->tile_w, d.sd->tile_h, d.r.x, d.r.y, t0, t1))
-                        t1 = -1;
-                    const uint32_t nrow = (ty <= d.ty1 && t1 >= t0) ? (uint32_t)(t1 - t0 + 1) : 0u;
-                    uint32_t tot;
-                    const uint32_t ex = block_exclusive_scan<uint32_t, 256>(nrow, tot, scan_s);
-                    pre_s[tid] = ex;
-                    t0_s[tid] = (uint32_t)t0;
-                    if (tid == 0) pre_s[256] = tot;
-                    __syncthreads();
-                    const uint32_t a = klo > kc ? klo - kc : 0u, bnd = min(tot, khi - kc);
-                    for (uint32_t q = a + tid; q < bnd; q += 256) {
-                        // row of sequence position q: the last row with pre <= q
-                        uint32_t lo = 0, hi = 256;
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (pre_s[mid] <= q) lo = mid;
-                            else hi = mid;
+            __syncthreads();
+            // 4. the round's pairs: warp chunks of 256, lane l the pairs l, l + 32, ...
+            for (uint32_t w0 = (uint32_t)warp * 256u; w0 < tot; w0 += 8u * 256u) {
+                uint32_t p = w0 + lane;
+                if (p >= tot) continue;
+                int lo = 0, hi = (int)nr;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (r_pre[mid] <= p) lo = mid;
+                    else hi = mid;
+                }
+                int rl = lo;
+                uint32_t col = p - r_pre[rl];
+#pragma unroll 1
+                for (int e = 0; e < 8 && p < tot; ++e) {
+                    while (col >= r_len[rl] && rl + 1 < (int)nr) {
+                        col -= r_len[rl];
+                        ++rl;
+                    }
+                    if (col < r_lim[rl]) {
+                        const uint32_t q = r_q0[rl] + col;
+                        if (q >= p0 && q < p1) {
+                            const uint32_t tx = r_t0[rl] + col, nx = r_tx[rl];
+                            pkey[q] = r_key0[rl] + (tx < nx ? tx : tx - nx);  // LiDAR azimuth wrap
+                            pval[q] = s_slot[r_slot[rl]];
                         }
-                        put_pair(*d.sd, row0 + (int)lo, (int)t0_s[lo] + (int)(q - pre_s[lo]), d.slot, oj + kc + q,
-                                 pkey, pval);
                     }
-                    kc += tot;
-                    __syncthreads();
+                    p += 32u;
+                    col += 32u;
                 }
             }
+            carry += tot;
+            __syncthreads();
         }
         __syncthreads();
     }
@@ -714,7 +662,9 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     // 4. duplication, balanced by pairs
     uint32_t* offs = region<uint32_t>(p, ws, R_OFFSETS);
     k_dup_offsets<<<G, 256, 0, st>>>(cnt_sorted, counters + C_NVIS, p64, (uint64_t)p->max_dup, offs);
-    k_dup_write<<<G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, offs, counters,
+    // many more CTAs than fit at once: the windows are equal in pairs, not
+    // in slots, and CTAs that finish early make room for the slow ones
+    k_dup_write<<<kDupCtasPerSortCta * G, 256, 0, st>>>(tab, p->n_surfels, vv[vb], cnt_sorted, offs, counters,
                                    region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS),
                                    region<uint4>(p, ws, R_SPANS), pk[0], pv[0]);
     // 5. tile passes

@@ -54,8 +54,9 @@ typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1, GSR_SENSOR_CYLINDRI
 
 /*
  * Surfel table, structure of arrays, one row per surfel (Sec. III-A: the
- * 2DGS attributes {mu, R, S, alpha}; colour from SH; r read as the LiDAR
- * intensity).  Raw (pre-activation) parameters:
+ * 2DGS attributes {mu, R, S, rho, r, alpha}; colour from SH; r read as the
+ * LiDAR intensity, rho as the LiDAR ray-drop probability).  Raw
+ * (pre-activation) parameters:
  *   pos       [n][3]  centre mu (world)
  *   log_scale [n][2]  s_u = exp(.), s_v = exp(.)
  *   quat      [n][4]  (w, x, y, z), normalised by the renderer; R = [t_u t_v n]
@@ -63,8 +64,15 @@ typedef enum { GSR_SENSOR_PINHOLE = 0, GSR_SENSOR_LIDAR = 1, GSR_SENSOR_CYLINDRI
  *   sh        [n][(sh_degree+1)^2][3]  real SH coefficients (colour = max(0, SH + 0.5))
  *   intensity [n]     LiDAR intensity in [0,1] (may be NULL: 0)
  *   obj_id    [n]     int32 rigid-object index, -1 = background (may be NULL)
- * All arrays 16-byte aligned.
+ *   ray_drop  [n]     LiDAR ray-drop logit; rho = sigmoid(.) (may be NULL: rho = 0)
+ * All arrays 16-byte aligned.  `sees` says which sensors render the table:
+ * GSR_SEES_CAMERAS | GSR_SEES_LIDARS (0 = all).  The paper reconstructs a
+ * camera scene G^C and a separate LiDAR scene G^L (Sec. III-A); with `sees`
+ * both share one plan, one sort and one compositing launch, each seen only
+ * by its own sensors.
  */
+#define GSR_SEES_CAMERAS 1 /* pinhole and cylindrical cameras */
+#define GSR_SEES_LIDARS 2
 typedef struct {
     int32_t n;
     int32_t sh_degree; /* 0..3 */
@@ -75,6 +83,8 @@ typedef struct {
     const float* sh;
     const float* intensity;
     const int32_t* obj_id;
+    const float* ray_drop;
+    int32_t sees;
 } gsr_surfels;
 
 /*
@@ -177,7 +187,9 @@ typedef struct {
 /*
  * Per-ray outputs of a LiDAR (DEVICE, [beams][columns]; any may be NULL):
  *   range = sum w t / sum w (0 where sum w == 0), intensity = sum w r,
- *   alpha = sum w, trans = final T, n_contrib and n_walk as for the camera.
+ *   alpha = sum w, trans = final T, n_contrib and n_walk as for the camera,
+ *   ray_drop = sum w rho + T: the probability that the beam returns nothing
+ *   (composited like the intensity; a beam that leaves the scene is dropped).
  */
 typedef struct {
     float* range;
@@ -186,6 +198,7 @@ typedef struct {
     float* trans;
     uint32_t* n_contrib;
     uint32_t* n_walk;
+    float* ray_drop;
 } gsr_lidar_out;
 
 /*
@@ -210,6 +223,7 @@ typedef struct {
     float* opacity;
     float* sh;
     float* intensity; /* may be NULL */
+    float* ray_drop;  /* may be NULL */
 } gsr_surfel_grads;
 
 /* Weights of the reconstruction loss (gsr_loss). */
@@ -378,13 +392,17 @@ typedef struct {
 } gsr_anchors;
 
 /* The decode MLP, FP32 masters (DEVICE, row-major): w1 [feat_dim+4][hidden],
- * b1 [hidden], w2 [hidden][10 k], b2 [10 k]; hidden = 64. */
+ * b1 [hidden], w2 [hidden][10 k], b2 [10 k]; hidden = 64.  head: what the
+ * 10 outputs of an offset mean (see gsr_decode_anchors). */
+#define GSR_HEAD_CAMERA 0 /* the camera scene G^C */
+#define GSR_HEAD_LIDAR 1  /* the LiDAR scene G^L   */
 typedef struct {
     int32_t hidden;
     const float* w1;
     const float* b1;
     const float* w2;
     const float* b2;
+    int32_t head;
 } gsr_mlp;
 
 /* Gradients of the MLP (and optionally of the anchor features), accumulated (+=). */
@@ -397,7 +415,8 @@ typedef struct {
 } gsr_mlp_grads;
 
 /* A writable surfel table (DEVICE) with degree-0 SH, as produced by the decode:
- * pos [N][3], log_scale [N][2], quat [N][4], opacity [N], sh [N][1][3], intensity [N] (may be NULL). */
+ * pos [N][3], log_scale [N][2], quat [N][4], opacity [N], sh [N][1][3], intensity [N]
+ * (may be NULL), ray_drop [N] (LiDAR head; may be NULL). */
 typedef struct {
     float* pos;
     float* log_scale;
@@ -405,6 +424,7 @@ typedef struct {
     float* opacity;
     float* sh;
     float* intensity;
+    float* ray_drop;
 } gsr_surfel_table;
 
 #define GSR_DECODE_BF16_TENSOR 0 /* BF16 inputs/weights on tcgen05 tensor cores, FP32 accumulation */
@@ -413,9 +433,13 @@ typedef struct {
 /*
  * Decode every anchor into k surfels (surfel a k + j = offset j of anchor a):
  *   X = [feature, (x_a - o)/|x_a - o|, |x_a - o|], H = ReLU(X w1 + b1),
- *   y = H w2 + b2; offset j: opacity logit y0, colour sigmoid(y1..3) stored as
- *   degree-0 SH, log-scale y4..5 + ln l_a, raw quaternion y6..9, centre
- *   x_a + l_a offset_j, intensity from the anchors.
+ *   y = H w2 + b2; offset j: opacity logit y0, log-scale y4..5 + ln l_a, raw
+ *   quaternion y6..9, centre x_a + l_a offset_j, and
+ *     camera head: colour sigmoid(y1..3) stored as degree-0 SH (out->sh
+ *                  required), intensity from the anchors;
+ *     LiDAR head:  intensity sigmoid(y1), ray-drop logit y2 (y3 unused),
+ *                  SH written as 0 when out->sh is set (the LiDAR scene has
+ *                  no colour).
  * origin (host float[3]) is the view origin o (camera centre; rig centre for
  * a rig).  cull_camera (host, may be NULL): anchors whose sphere of radius
  * l_a max|offset| + 3 m is outside that pinhole's frustum get opacity logit
@@ -427,8 +451,9 @@ gsr_status gsr_decode_anchors(const gsr_anchors* anchors, const gsr_mlp* mlp, co
                               uint32_t* device_status, void* stream);
 
 /*
- * Back-propagate d(loss)/d(decoded surfel table) (opacity, sh, log_scale,
- * quat of the table produced by gsr_decode_anchors with the same arguments)
+ * Back-propagate d(loss)/d(decoded surfel table) (opacity, log_scale, quat,
+ * and sh for the camera head or intensity and ray_drop for the LiDAR head,
+ * of the table produced by gsr_decode_anchors with the same arguments)
  * through the decode activations and the MLP (FP32), accumulating into *out.
  */
 gsr_status gsr_decode_backward(const gsr_anchors* anchors, const gsr_mlp* mlp, const float* origin,

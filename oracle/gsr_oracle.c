@@ -138,7 +138,7 @@ typedef struct {
     float key;         /* composite-order key: zc in the kernel's FP32 arithmetic */
     double c[2];       /* low-pass centre (pixels, or LiDAR cells)           */
     double o;          /* opacity, sigmoid of the logit                      */
-    double feat[3];    /* camera: colour; LiDAR: intensity in feat[0]       */
+    double feat[3];    /* camera: colour; LiDAR: intensity, ray drop, 0     */
     double normal[3];  /* sensor frame, facing the sensor                    */
 } or_surfel;
 
@@ -231,7 +231,7 @@ static float or_key32(const or_sensor* S, int i, const double* pos, const int* o
 static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* pos,
                        const double* log_scale, const double* quat, const double* opacity_logit,
                        int sh_degree, const double* sh, const double* intensity,
-                       const int* obj_id, const double* obj_pose)
+                       const double* ray_drop, const int* obj_id, const double* obj_pose)
 {
     double mu[3], R[3][3], Ro[3][3];
     or_surfel_world(i, pos, quat, obj_id, obj_pose, mu, R, Ro);
@@ -319,7 +319,8 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
         for (int ch = 0; ch < 3; ++ch) G->feat[ch] = col[ch] > 0 ? col[ch] : 0.0;
     } else {
         G->feat[0] = intensity ? intensity[i] : 0.0;
-        G->feat[1] = G->feat[2] = 0.0;
+        G->feat[1] = ray_drop ? or_sigmoid(ray_drop[i]) : 0.0; /* ray-drop probability rho */
+        G->feat[2] = 0.0;
     }
 }
 
@@ -481,14 +482,15 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
 
 static or_surfel* or_prepare_all(int n, const or_sensor* S, const double* pos, const double* log_scale,
                                  const double* quat, const double* opacity_logit, int sh_degree,
-                                 const double* sh, const double* intensity, const int* obj_id,
-                                 const double* obj_pose)
+                                 const double* sh, const double* intensity, const double* ray_drop,
+                                 const int* obj_id, const double* obj_pose)
 {
     or_surfel* G = (or_surfel*)malloc(sizeof(or_surfel) * (size_t)(n > 0 ? n : 1));
     if (!G) return NULL;
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
-        or_prepare(&G[i], i, S, pos, log_scale, quat, opacity_logit, sh_degree, sh, intensity, obj_id, obj_pose);
+        or_prepare(&G[i], i, S, pos, log_scale, quat, opacity_logit, sh_degree, sh, intensity, ray_drop, obj_id,
+                   obj_pose);
     return G;
 }
 
@@ -516,7 +518,7 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
     S.kind = 0;
     or_sensor_from_matrix(&S, world_to_cam);
     S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
-    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, obj_id, obj_pose);
+    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
     if (!G) return -1;
     long long npx = pix ? n_pix : (long long)width * height;
     int fail = 0;
@@ -582,7 +584,7 @@ int oracle_render_cylindrical(int n, const double* pos, const double* log_scale,
     S.kind = 2;
     or_sensor_from_matrix(&S, world_to_cam);
     S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
-    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, obj_id, obj_pose);
+    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
     if (!G) return -1;
     long long npx = pix ? n_pix : (long long)width * height;
     int fail = 0;
@@ -625,15 +627,19 @@ int oracle_render_cylindrical(int n, const double* pos, const double* log_scale,
  * Spinning LiDAR range image (Eq. 5).  Row i (beam) has elevation
  * el_max - i (el_max - el_min)/(beams-1); column j has azimuth
  * az0 + (j+0.5) 360/columns.  Outputs per ray: range = sum(w t)/sum(w)
- * (0 where sum(w) == 0), intensity = sum(w r), acc = sum(w), T.
+ * (0 where sum(w) == 0), intensity = sum(w r), acc = sum(w), T, and the
+ * ray-drop probability sum(w rho) + T with rho = sigmoid(ray_drop logit)
+ * of each surfel (Sec. III-A lists rho among the LiDAR scene's attributes;
+ * composited like the intensity, a ray that leaves the scene returns
+ * nothing).  ray_drop may be NULL (rho = 0).
  */
 int oracle_render_lidar(int n, const double* pos, const double* log_scale, const double* quat,
-                        const double* opacity_logit, const double* intensity,
+                        const double* opacity_logit, const double* intensity, const double* ray_drop,
                         const int* obj_id, const double* obj_pose,
                         int beams, int columns, double el_min_deg, double el_max_deg, double az0_deg,
                         double near_, const double* world_to_lidar,
                         int n_ray, const long long* ray,
-                        double* range, double* intens, double* alpha, double* trans, double* flip,
+                        double* range, double* intens, double* drop, double* alpha, double* trans, double* flip,
                         int* n_contrib)
 {
     if (n < 0 || beams < 2 || columns <= 0) return -1;
@@ -647,7 +653,8 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
     S.az0 = az0_deg * OR_PI / 180.0;
     S.d_az = 2.0 * OR_PI / columns;
     S.near_ = near_;
-    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, 0, NULL, intensity, obj_id, obj_pose);
+    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, 0, NULL, intensity, ray_drop, obj_id,
+                                  obj_pose);
     if (!G) return -1;
     long long nr = ray ? n_ray : (long long)beams * columns;
     int fail = 0;
@@ -672,6 +679,7 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
                 or_composite(G, n, &S, hu, hv, d, pc, buf, &r);
                 range[q] = r.A > 0 ? r.B / r.A : 0.0;
                 intens[q] = r.feat[0];
+                if (drop) drop[q] = r.feat[1] + r.T;
                 alpha[q] = r.A;
                 trans[q] = r.T;
                 if (flip) flip[q] = r.flip;
@@ -713,7 +721,7 @@ int oracle_intersect(int kind, const double* pos, const double* log_scale, const
     S.columns = 1;
     double op = 0.0, ones = 0.0;
     or_surfel G;
-    or_prepare(&G, 0, &S, pos, log_scale, quat, &op, 0, &ones, NULL, NULL, NULL);
+    or_prepare(&G, 0, &S, pos, log_scale, quat, &op, 0, &ones, NULL, NULL, NULL, NULL);
     double hu[4], hv[4], d[3] = {0, 0, 1}, pc[2] = {0, 0};
     if (kind == 0) {
         hu[0] = -1; hu[1] = 0; hu[2] = 0; hu[3] = a;

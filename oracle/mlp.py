@@ -13,6 +13,11 @@ Scaffold-GS).  Readings of the points the paper leaves open:
   offset j of anchor a, y = Y[a, 10 j : 10 j + 10]:
           opacity logit = y0, colour = sigmoid(y1..y3), log-scale = y4..y5 + ln l_a,
           raw quaternion = y6..y9, centre = x_a + l_a o_{a,j}
+  LiDAR   the LiDAR scene's MLP (Sec. III-A infers {mu, R, S, rho, r, alpha}
+  head    for the LiDAR scene G^L too) reads the same 10 values per offset
+          as: opacity logit y0, intensity r = sigmoid(y1), ray-drop logit
+          y2 (rho = sigmoid(y2)), y3 unused, log-scales y4..y5 + ln l_a,
+          raw quaternion y6..y9; its table carries no colour (SH 0).
   cull    (optional, one pinhole camera) an anchor whose sphere of radius
           l_a max_j |o_{a,j}| + 3 m lies entirely behind the near plane or
           outside a side plane of the frustum renders nothing (its surfels
@@ -55,11 +60,14 @@ def cull_mask(pos, scale, offsets, cam):
     return out
 
 
-def decode(anchors, W1, b1, W2, b2, origin, cam=None, features=None):
+def decode(anchors, W1, b1, W2, b2, origin, cam=None, features=None, head="camera"):
     """FP64 decode.  Returns a dict of tensors (pos [N,3], log_scale [N,2],
-    quat [N,4], opacity [N], rgb [N,3], sh [N,1,3], intensity [N]) with
-    N = A k, surfel a k + j = offset j of anchor a.  Differentiable w.r.t.
-    W1, b1, W2, b2 and `features` when they are tensors with requires_grad."""
+    quat [N,4], opacity [N], rgb [N,3], sh [N,1,3], intensity [N], and for
+    head="lidar" ray_drop [N] logits) with N = A k, surfel a k + j = offset
+    j of anchor a.  The camera head takes the intensity from the anchors,
+    the LiDAR head from the network (its rgb is 0.5, sh 0).  Differentiable
+    w.r.t. W1, b1, W2, b2 and `features` when they are tensors with
+    requires_grad."""
     A, k = anchors.offsets.shape[0], anchors.offsets.shape[1]
     t = lambda a: a if isinstance(a, torch.Tensor) else torch.as_tensor(np.asarray(a, np.float64), dtype=DT)
     x = t(anchors.pos)
@@ -76,11 +84,21 @@ def decode(anchors, W1, b1, W2, b2, origin, cam=None, features=None):
         m = torch.as_tensor(cull_mask(np.asarray(anchors.pos, np.float64), np.asarray(anchors.scale, np.float64),
                                       np.asarray(anchors.offsets, np.float64), cam))
         opacity = torch.where(m[:, None], torch.full_like(opacity, CULLED_LOGIT), opacity)
-    rgb = torch.sigmoid(Y[..., 1:4])
     log_scale = Y[..., 4:6] + torch.log(l)[:, None, None]
     quat = Y[..., 6:10]
     N = A * k
-    return {"pos": pos.reshape(N, 3), "log_scale": log_scale.reshape(N, 2), "quat": quat.reshape(N, 4),
-            "opacity": opacity.reshape(N), "rgb": rgb.reshape(N, 3),
-            "sh": ((rgb - 0.5) / Y00).reshape(N, 1, 3), "intensity": t(anchors.intensity).reshape(N),
-            "hidden": H, "X": X, "Y": Y}
+    out = {"pos": pos.reshape(N, 3), "log_scale": log_scale.reshape(N, 2), "quat": quat.reshape(N, 4),
+           "opacity": opacity.reshape(N), "hidden": H, "X": X, "Y": Y}
+    if head == "lidar":
+        out["rgb"] = torch.full((N, 3), 0.5, dtype=DT)
+        out["sh"] = torch.zeros((N, 1, 3), dtype=DT)
+        out["intensity"] = torch.sigmoid(Y[..., 1]).reshape(N)
+        out["ray_drop"] = Y[..., 2].reshape(N)
+    elif head == "camera":
+        rgb = torch.sigmoid(Y[..., 1:4])
+        out["rgb"] = rgb.reshape(N, 3)
+        out["sh"] = ((rgb - 0.5) / Y00).reshape(N, 1, 3)
+        out["intensity"] = t(anchors.intensity).reshape(N)
+    else:
+        raise ValueError(head)
+    return out

@@ -49,9 +49,9 @@ def _load():
         lib.oracle_render_cylindrical.argtypes = lib.oracle_render_pinhole.argtypes
         lib.oracle_render_lidar.restype = c_int
         lib.oracle_render_lidar.argtypes = [
-            c_int, D, D, D, D, D, I, D,
+            c_int, D, D, D, D, D, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, D,
-            c_int, L, D, D, D, D, D, I]
+            c_int, L, D, D, D, D, D, D, I]
         lib.oracle_sh_basis.restype = c_double
         lib.oracle_sh_basis.argtypes = [c_int, c_int, D]
         lib.oracle_num_threads.restype = c_int
@@ -134,8 +134,10 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
 
 
 def render_lidar(s, lid, rays=None, obj_pose=None):
-    """Brute-force FP64 LiDAR range image.  Returns range, intensity, alpha,
-    T, flip, n_contrib (each [R], or [beams, columns] with rays=None)."""
+    """Brute-force FP64 LiDAR range image.  Returns range, intensity, drop
+    (ray-drop probability: sum w rho + T with rho = sigmoid of the surfels'
+    ray_drop logit, 0 when `s` has none), alpha, T, flip, n_contrib (each
+    [R], or [beams, columns] with rays=None)."""
     lib = _load()
     keep = []
 
@@ -151,16 +153,18 @@ def render_lidar(s, lid, rays=None, obj_pose=None):
         ray_arr = np.ascontiguousarray(rays, dtype=np.int64)
         keep.append(ray_arr)
         ray_p = ray_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
-    out = {k: np.zeros(nr, np.float64) for k in ("range", "intensity", "alpha", "T", "flip")}
+    out = {k: np.zeros(nr, np.float64) for k in ("range", "intensity", "drop", "alpha", "T", "flip")}
+    rd = getattr(s, "ray_drop", None)
+    rd_p = None if rd is None else D(rd)
     out["n_contrib"] = np.zeros(nr, np.int32)
     dp = {k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in out.items() if v.dtype == np.float64}
     rc = lib.oracle_render_lidar(
-        int(s.pos.shape[0]), D(s.pos), D(s.log_scale), D(s.quat), D(s.opacity), D(s.intensity),
+        int(s.pos.shape[0]), D(s.pos), D(s.log_scale), D(s.quat), D(s.opacity), D(s.intensity), rd_p,
         ids_p, P_p,
         int(lid.beams), int(lid.columns), float(lid.el_min_deg), float(lid.el_max_deg), float(lid.az0_deg),
         float(lid.near), D(lid.world_to_sensor),
         int(nr), ray_p,
-        dp["range"], dp["intensity"], dp["alpha"], dp["T"], dp["flip"],
+        dp["range"], dp["intensity"], dp["drop"], dp["alpha"], dp["T"], dp["flip"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:
         raise RuntimeError("oracle_render_lidar failed")

@@ -260,7 +260,7 @@ extern "C" gsr_status gsr_render_camera(const gsr_plan* plan, const void* worksp
     if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
     if (plan->sensors[sensor].kind == GSR_SENSOR_LIDAR) return GSR_ERR_INVALID_ARG;
     FrameOut o{out->rgb, out->depth, out->normal, out->alpha, out->trans, out->depth_acc, out->n_contrib,
-               out->n_walk};
+               out->n_walk, nullptr};
     return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -272,7 +272,7 @@ extern "C" gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspa
     if (!out || sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
     if (plan->sensors[sensor].kind != GSR_SENSOR_LIDAR) return GSR_ERR_INVALID_ARG;
     FrameOut o{out->intensity, out->range, nullptr, out->alpha, out->trans, nullptr, out->n_contrib,
-               out->n_walk};
+               out->n_walk, out->ray_drop};
     return cuda_fail(launch_render(plan, workspace, sensor, o, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -432,11 +432,13 @@ static gsr_status rig_outputs(const gsr_plan* plan, const gsr_camera_out* cam, c
         if (plan->sensors[i].kind != GSR_SENSOR_LIDAR) {
             if (!cam) return GSR_ERR_INVALID_ARG;
             const gsr_camera_out& o = cam[i];
-            outs[i] = FrameOut{o.rgb, o.depth, o.normal, o.alpha, o.trans, o.depth_acc, o.n_contrib, o.n_walk};
+            outs[i] = FrameOut{o.rgb, o.depth, o.normal, o.alpha, o.trans, o.depth_acc, o.n_contrib, o.n_walk,
+                               nullptr};
         } else {
             if (!lid) return GSR_ERR_INVALID_ARG;
             const gsr_lidar_out& o = lid[i];
-            outs[i] = FrameOut{o.intensity, o.range, nullptr, o.alpha, o.trans, nullptr, o.n_contrib, o.n_walk};
+            outs[i] = FrameOut{o.intensity, o.range, nullptr, o.alpha, o.trans, nullptr, o.n_contrib, o.n_walk,
+                               o.ray_drop};
         }
     }
     return GSR_OK;

@@ -131,6 +131,7 @@ struct FrameOut {
     float* depth_acc;  // [2][H][W]
     uint32_t* n_contrib;
     uint32_t* n_walk;
+    float* drop;       // LiDAR ray-drop probability
 };
 
 SensorTable make_sensor_table(const gsr_plan* p);

@@ -9,7 +9,9 @@
 //       log-scales (2), raw quaternion (4)}                     (100 outputs)
 // and offset j becomes a surfel at x_a + l_a o_{a,j} with log-scale y + ln l_a,
 // colour sigmoid(y) (stored as a degree-0 SH coefficient), and the anchor's
-// LiDAR intensity.  Anchors whose bounding sphere (l_a max|o| + 3 m) lies
+// LiDAR intensity.  The LiDAR scene's head (the paper reconstructs a
+// separate LiDAR scene whose MLP infers rho and r as well) reads the three
+// colour logits as intensity logit, ray-drop logit and an unused value.  Anchors whose bounding sphere (l_a max|o| + 3 m) lies
 // outside a given camera frustum are culled (their surfels get opacity
 // logit -1e4, which the preprocess discards).
 //
@@ -50,6 +52,7 @@ struct DecodeArgs {
     const float* b1;          // [64]
     const float* w2;          // [64][100]
     const float* b2;          // [100]
+    int head;                 // GSR_HEAD_CAMERA or GSR_HEAD_LIDAR
     float ox, oy, oz;         // view origin
     int cull;                 // 1: test the camera frustum below
     float R[9], t[3];         // world -> camera
@@ -61,6 +64,7 @@ struct DecodeArgs {
     float* out_opacity;       // [n*10]
     float* out_sh;            // [n*10][1][3]
     float* out_intensity;     // [n*10] or null
+    float* out_ray_drop;      // [n*10] or null (LiDAR head)
     uint32_t* status;         // device status word (timeouts), or null
 };
 
@@ -111,11 +115,18 @@ __device__ __forceinline__ void write_surfels(const DecodeArgs& a, int i, const 
         a.out_pos[3 * s + 1] = fmaf(l, o[1], x1);
         a.out_pos[3 * s + 2] = fmaf(l, o[2], x2);
         a.out_opacity[s] = cull ? kCulledLogit : yj[0];
-        for (int c = 0; c < 3; ++c) a.out_sh[3 * s + c] = (sigmoidf_(yj[1 + c]) - 0.5f) * (1.f / kY00);
         a.out_log_scale[2 * s] = yj[4] + ll;
         a.out_log_scale[2 * s + 1] = yj[5] + ll;
         reinterpret_cast<float4*>(a.out_quat)[s] = make_float4(yj[6], yj[7], yj[8], yj[9]);
-        if (a.out_intensity) a.out_intensity[s] = a.intensity ? a.intensity[s] : 0.f;
+        if (a.head == GSR_HEAD_LIDAR) {
+            if (a.out_sh)
+                for (int c = 0; c < 3; ++c) a.out_sh[3 * s + c] = 0.f;
+            if (a.out_intensity) a.out_intensity[s] = sigmoidf_(yj[1]);
+            if (a.out_ray_drop) a.out_ray_drop[s] = yj[2];
+        } else {
+            for (int c = 0; c < 3; ++c) a.out_sh[3 * s + c] = (sigmoidf_(yj[1 + c]) - 0.5f) * (1.f / kY00);
+            if (a.out_intensity) a.out_intensity[s] = a.intensity ? a.intensity[s] : 0.f;
+        }
     }
 }
 
@@ -280,6 +291,8 @@ struct DecodeGradArgs {
     const float* g_sh;         // [n*10][1][3]
     const float* g_log_scale;  // [n*10][2]
     const float* g_quat;       // [n*10][4]
+    const float* g_intensity;  // [n*10] or null (LiDAR head)
+    const float* g_ray_drop;   // [n*10] or null (LiDAR head)
     float* g_w1;               // [36][64]   (accumulated)
     float* g_b1;               // [64]
     float* g_w2;               // [64][100]
@@ -326,9 +339,16 @@ __global__ void __launch_bounds__(kBwdTile) k_decode_backward(DecodeGradArgs g)
             }
             float* d = dY + kOff * j;
             d[0] = cull ? 0.f : g.g_opacity[s];
-            for (int c = 0; c < 3; ++c) {
-                const float sg = sigmoidf_(y[c]);
-                d[1 + c] = g.g_sh[3 * s + c] * sg * (1.f - sg) * (1.f / kY00);
+            if (a.head == GSR_HEAD_LIDAR) {
+                const float sg = sigmoidf_(y[0]);
+                d[1] = g.g_intensity ? g.g_intensity[s] * sg * (1.f - sg) : 0.f;
+                d[2] = g.g_ray_drop ? g.g_ray_drop[s] : 0.f;
+                d[3] = 0.f;
+            } else {
+                for (int c = 0; c < 3; ++c) {
+                    const float sg = sigmoidf_(y[c]);
+                    d[1 + c] = g.g_sh[3 * s + c] * sg * (1.f - sg) * (1.f / kY00);
+                }
             }
             d[4] = g.g_log_scale[2 * s];
             d[5] = g.g_log_scale[2 * s + 1];
@@ -403,7 +423,9 @@ static gsr_status fill_decode_args(const gsr_anchors* an, const gsr_mlp* mlp, co
     if (an->k != kOff || an->feat_dim != kFeat || mlp->hidden != kHid) return GSR_ERR_UNSUPPORTED;
     if (an->n < 0 || (an->n > 0 && (!an->pos || !an->feature || !an->scale || !an->offsets))) return GSR_ERR_INVALID_ARG;
     if (!mlp->w1 || !mlp->b1 || !mlp->w2 || !mlp->b2) return GSR_ERR_INVALID_ARG;
+    if (mlp->head != GSR_HEAD_CAMERA && mlp->head != GSR_HEAD_LIDAR) return GSR_ERR_INVALID_ARG;
     a = DecodeArgs{};
+    a.head = mlp->head;
     a.n = an->n;
     a.pos = an->pos;
     a.feature = an->feature;
@@ -436,7 +458,8 @@ static gsr_status fill_decode_args(const gsr_anchors* an, const gsr_mlp* mlp, co
         a.near_plane = cam->near_plane;
     }
     if (out) {
-        if (an->n > 0 && (!out->pos || !out->log_scale || !out->quat || !out->opacity || !out->sh))
+        if (an->n > 0 && (!out->pos || !out->log_scale || !out->quat || !out->opacity ||
+                          (!out->sh && mlp->head == GSR_HEAD_CAMERA)))
             return GSR_ERR_INVALID_ARG;
         a.out_pos = out->pos;
         a.out_log_scale = out->log_scale;
@@ -444,6 +467,7 @@ static gsr_status fill_decode_args(const gsr_anchors* an, const gsr_mlp* mlp, co
         a.out_opacity = out->opacity;
         a.out_sh = out->sh;
         a.out_intensity = out->intensity;
+        a.out_ray_drop = out->ray_drop;
     }
     return GSR_OK;
 }
@@ -484,12 +508,15 @@ extern "C" gsr_status gsr_decode_backward(const gsr_anchors* anchors, const gsr_
     gsr_status st = fill_decode_args(anchors, mlp, origin, cull_camera, nullptr, nullptr, g.f);
     if (st != GSR_OK) return st;
     if (!d_surfels || !out) return GSR_ERR_INVALID_ARG;
-    if (!d_surfels->opacity || !d_surfels->sh || !d_surfels->log_scale || !d_surfels->quat) return GSR_ERR_INVALID_ARG;
+    if (!d_surfels->opacity || !d_surfels->log_scale || !d_surfels->quat) return GSR_ERR_INVALID_ARG;
+    if (!d_surfels->sh && mlp->head == GSR_HEAD_CAMERA) return GSR_ERR_INVALID_ARG;
     if (!out->w1 || !out->b1 || !out->w2 || !out->b2) return GSR_ERR_INVALID_ARG;
     g.g_opacity = d_surfels->opacity;
     g.g_sh = d_surfels->sh;
     g.g_log_scale = d_surfels->log_scale;
     g.g_quat = d_surfels->quat;
+    g.g_intensity = d_surfels->intensity;
+    g.g_ray_drop = d_surfels->ray_drop;
     g.g_w1 = out->w1;
     g.g_b1 = out->b1;
     g.g_w2 = out->w2;

@@ -564,7 +564,9 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorId
         const F3 col = sh_colour(S.sh_degree, S.sh + (size_t)i * K * 3, vd);
         r3 = make_float4(o, col.x, col.y, col.z);
     } else {
-        r3 = make_float4(o, S.intensity ? __ldg(S.intensity + i) : 0.f, 0.f, 0.f);
+        // LiDAR: intensity r and ray-drop probability rho, composited alike
+        const float rho = S.ray_drop ? 1.f / (1.f + __expf(-__ldg(S.ray_drop + i))) : 0.f;
+        r3 = make_float4(o, S.intensity ? __ldg(S.intensity + i) : 0.f, rho, 0.f);
     }
     float4* R = rec + slot * kRecordF4;
     R[0] = r0;
@@ -576,16 +578,27 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorId
 }
 
 
-// One launch per sensor model present in the plan.
+// One launch per sensor model present in the plan.  Sensors the table is
+// not for (gsr_surfels.sees) get empty slots for its surfels.
 cudaError_t launch_preprocess(const SensorTable& tab, const gsr_surfels& S, const float* poses, int n_obj,
                               float4* rec, ushort4* rects, uint32_t* counts, uint32_t* keys, uint4* spans,
                               int first, int n_plan, cudaStream_t st)
 {
     for (int kind = 0; kind < 3; ++kind) {
+        const int bit = kind == GSR_SENSOR_LIDAR ? GSR_SEES_LIDARS : GSR_SEES_CAMERAS;
+        const bool seen = S.sees == 0 || (S.sees & bit) != 0;
         SensorIds ids;
         ids.n = 0;
-        for (int i = 0; i < tab.n; ++i)
-            if (tab.s[i].kind == kind) ids.id[ids.n++] = (uint8_t)i;
+        for (int i = 0; i < tab.n; ++i) {
+            if (tab.s[i].kind != kind) continue;
+            if (seen) {
+                ids.id[ids.n++] = (uint8_t)i;
+            } else {
+                const cudaError_t e =
+                    cudaMemsetAsync(counts + (size_t)i * n_plan + first, 0, sizeof(uint32_t) * (size_t)S.n, st);
+                if (e != cudaSuccess) return e;
+            }
+        }
         if (ids.n == 0) continue;
         const dim3 grid((S.n + 255) / 256, ids.n);
         if (kind == GSR_SENSOR_PINHOLE)

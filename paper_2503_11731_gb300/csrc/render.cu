@@ -158,8 +158,8 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                         const float w = alpha * s.T;
                         const float4 r3 = Rj[3];
                         s.f0 = fmaf(w, r3.y, s.f0);
+                        s.f1 = fmaf(w, r3.z, s.f1);  // green, or the LiDAR ray-drop probability
                         if (KIND != GSR_SENSOR_LIDAR) {
-                            s.f1 = fmaf(w, r3.z, s.f1);
                             s.f2 = fmaf(w, r3.w, s.f2);
                             const float4 r4 = Rj[4];
                             s.n0 = fmaf(w, r4.x, s.n0);
@@ -209,6 +209,7 @@ __device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ra
         }
     } else {
         if (out.color) out.color[pix] = s.f0;
+        if (out.drop) out.drop[pix] = s.f1 + s.T;  // a beam that leaves the scene is dropped
     }
     if (out.depth) out.depth[pix] = s.A > 0.f ? s.B / s.A : 0.f;
     if (out.alpha) out.alpha[pix] = s.A;

@@ -22,18 +22,22 @@ def _ptr(t):
 class DeviceSurfels:
     """Surfel table on the device (float32, contiguous, 16-byte aligned rows)."""
 
-    def __init__(self, pos, log_scale, quat, opacity, sh, intensity=None, obj_id=None):
+    def __init__(self, pos, log_scale, quat, opacity, sh, intensity=None, obj_id=None, ray_drop=None, sees=0):
+        """`ray_drop`: LiDAR ray-drop logits (None: rho = 0); `sees`: which
+        sensors render the table (gsr.SEES_CAMERAS | gsr.SEES_LIDARS, 0 = all)."""
         self.pos, self.log_scale, self.quat, self.opacity, self.sh = pos, log_scale, quat, opacity, sh
-        self.intensity, self.obj_id = intensity, obj_id
+        self.intensity, self.obj_id, self.ray_drop, self.sees = intensity, obj_id, ray_drop, int(sees)
         for t in (pos, log_scale, quat, opacity, sh):
             assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
 
     @classmethod
-    def from_host(cls, s, device="cuda"):
+    def from_host(cls, s, device="cuda", sees=0):
         f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)
+        rd = getattr(s, "ray_drop", None)
         return cls(f(s.pos), f(s.log_scale), f(s.quat), f(s.opacity), f(s.sh), f(s.intensity),
                    None if getattr(s, "obj_id", None) is None else
-                   torch.as_tensor(np.ascontiguousarray(s.obj_id, np.int32), device=device))
+                   torch.as_tensor(np.ascontiguousarray(s.obj_id, np.int32), device=device),
+                   None if rd is None else f(rd), sees)
 
     @property
     def n(self):
@@ -45,7 +49,8 @@ class DeviceSurfels:
 
     def struct(self) -> gsr.Surfels:
         return gsr.Surfels(self.n, self.sh_degree, _ptr(self.pos), _ptr(self.log_scale), _ptr(self.quat),
-                           _ptr(self.opacity), _ptr(self.sh), _ptr(self.intensity), _ptr(self.obj_id))
+                           _ptr(self.opacity), _ptr(self.sh), _ptr(self.intensity), _ptr(self.obj_id),
+                           _ptr(self.ray_drop), self.sees)
 
 
 def _stream_handle(stream=None):
@@ -78,7 +83,7 @@ class Renderer:
             H, W = (d.beams, d.columns) if d.kind == "lidar" else (d.height, d.width)
             o = {}
             if d.kind == "lidar":
-                for k in ("range", "intensity", "alpha", "trans"):
+                for k in ("range", "intensity", "alpha", "trans", "drop"):
                     if k in outputs or k in ("range", "intensity"):
                         o[k] = torch.zeros(H, W, device=device)
                 for k in ("n_contrib", "n_walk"):
@@ -103,7 +108,8 @@ class Renderer:
         o = self.out[i]
         g = lambda k: _ptr(o.get(k))
         if self.descs[i].kind == "lidar":
-            return gsr.LidarOut(g("range"), g("intensity"), g("alpha"), g("trans"), g("n_contrib"), g("n_walk"))
+            return gsr.LidarOut(g("range"), g("intensity"), g("alpha"), g("trans"), g("n_contrib"), g("n_walk"),
+                                g("drop"))
         return gsr.CameraOut(g("rgb"), g("depth"), g("normal"), g("alpha"), g("trans"), g("depth_acc"),
                              g("n_contrib"), g("n_walk"))
 

@@ -25,7 +25,8 @@ c_i32, c_i64, c_u64, c_f32, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint
 
 class Surfels(ctypes.Structure):
     _fields_ = [("n", c_i32), ("sh_degree", c_i32), ("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp),
-                ("opacity", c_vp), ("sh", c_vp), ("intensity", c_vp), ("obj_id", c_vp)]
+                ("opacity", c_vp), ("sh", c_vp), ("intensity", c_vp), ("obj_id", c_vp), ("ray_drop", c_vp),
+                ("sees", c_i32)]
 
 
 class Objects(ctypes.Structure):
@@ -58,7 +59,7 @@ class CameraOut(ctypes.Structure):
 
 class LidarOut(ctypes.Structure):
     _fields_ = [("range", c_vp), ("intensity", c_vp), ("alpha", c_vp), ("trans", c_vp), ("n_contrib", c_vp),
-                ("n_walk", c_vp)]
+                ("n_walk", c_vp), ("ray_drop", c_vp)]
 
 
 class CameraGrad(ctypes.Structure):
@@ -67,7 +68,7 @@ class CameraGrad(ctypes.Structure):
 
 class SurfelGrads(ctypes.Structure):
     _fields_ = [("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp),
-                ("intensity", c_vp)]
+                ("intensity", c_vp), ("ray_drop", c_vp)]
 
 
 class LossWeights(ctypes.Structure):
@@ -80,7 +81,7 @@ class Anchors(ctypes.Structure):
 
 
 class Mlp(ctypes.Structure):
-    _fields_ = [("hidden", c_i32), ("w1", c_vp), ("b1", c_vp), ("w2", c_vp), ("b2", c_vp)]
+    _fields_ = [("hidden", c_i32), ("w1", c_vp), ("b1", c_vp), ("w2", c_vp), ("b2", c_vp), ("head", c_i32)]
 
 
 class MlpGrads(ctypes.Structure):
@@ -89,7 +90,7 @@ class MlpGrads(ctypes.Structure):
 
 class SurfelTable(ctypes.Structure):
     _fields_ = [("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp),
-                ("intensity", c_vp)]
+                ("intensity", c_vp), ("ray_drop", c_vp)]
 
 
 AUTOTUNE_MAX = 8
@@ -115,6 +116,8 @@ class AutotuneResult(ctypes.Structure):
 
 
 DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
+HEAD_CAMERA, HEAD_LIDAR = 0, 1
+SEES_CAMERAS, SEES_LIDARS = 1, 2
 
 _STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights,
             Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult]

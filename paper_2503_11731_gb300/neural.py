@@ -42,26 +42,32 @@ class NeuralModel:
 
     PARAMS = ("w1", "b1", "w2", "b2")
 
-    def __init__(self, w1, b1, w2, b2, device="cuda"):
+    def __init__(self, w1, b1, w2, b2, device="cuda", head=gsr.HEAD_CAMERA):
+        """`head`: gsr.HEAD_CAMERA (the camera scene: colour) or gsr.HEAD_LIDAR
+        (the LiDAR scene: intensity and ray drop)."""
         f = lambda x: torch.as_tensor(np.ascontiguousarray(x, np.float32), device=device)
         self.w1, self.b1, self.w2, self.b2 = f(w1), f(b1), f(w2), f(b2)
+        self.head = int(head)
         self.device = device
         self.step_count = 0
         self._adam = {}
 
     def struct(self):
-        return gsr.Mlp(int(self.w1.shape[1]), _ptr(self.w1), _ptr(self.b1), _ptr(self.w2), _ptr(self.b2))
+        return gsr.Mlp(int(self.w1.shape[1]), _ptr(self.w1), _ptr(self.b1), _ptr(self.w2), _ptr(self.b2), self.head)
 
     def new_table(self, anchors: DeviceAnchors) -> DeviceSurfels:
         N = anchors.n * anchors.k
         z = lambda *s: torch.zeros(*s, device=self.device)
+        if self.head == gsr.HEAD_LIDAR:
+            return DeviceSurfels(z(N, 3), z(N, 2), z(N, 4), z(N), z(N, 1, 3), z(N), ray_drop=z(N),
+                                 sees=gsr.SEES_LIDARS)
         return DeviceSurfels(z(N, 3), z(N, 2), z(N, 4), z(N), z(N, 1, 3), z(N))
 
     def decode(self, anchors: DeviceAnchors, origin, cull_camera=None, precision=gsr.DECODE_BF16_TENSOR,
                out: DeviceSurfels = None, status=None, stream=None) -> DeviceSurfels:
         out = self.new_table(anchors) if out is None else out
         table = gsr.SurfelTable(_ptr(out.pos), _ptr(out.log_scale), _ptr(out.quat), _ptr(out.opacity), _ptr(out.sh),
-                                _ptr(out.intensity))
+                                _ptr(out.intensity), _ptr(out.ray_drop))
         cam = None if cull_camera is None else gsr.sensor(cull_camera)
         gsr.decode_anchors(anchors.struct(), self.struct(), origin, cam, precision, table,
                            None if status is None else _ptr(status), _stream_handle(stream))
@@ -75,7 +81,8 @@ class NeuralModel:
         """Accumulate d(loss)/d(w1, b1, w2, b2, features) from d(loss)/d(decoded table)."""
         g = self.grads
         ds = gsr.SurfelGrads(None, _ptr(surfel_grads["log_scale"]), _ptr(surfel_grads["quat"]),
-                             _ptr(surfel_grads["opacity"]), _ptr(surfel_grads["sh"]), None)
+                             _ptr(surfel_grads["opacity"]), _ptr(surfel_grads.get("sh")),
+                             _ptr(surfel_grads.get("intensity")), _ptr(surfel_grads.get("ray_drop")))
         out = gsr.MlpGrads(_ptr(g["w1"]), _ptr(g["b1"]), _ptr(g["w2"]), _ptr(g["b2"]), _ptr(g["feature"]))
         cam = None if cull_camera is None else gsr.sensor(cull_camera)
         gsr.decode_backward(anchors.struct(), self.struct(), origin, cam, ds, out, _stream_handle(stream))

@@ -40,6 +40,7 @@ class Surfels:
     sh: np.ndarray
     intensity: np.ndarray
     obj_id: np.ndarray | None = None  # int32 [N], -1 = background
+    ray_drop: np.ndarray | None = None  # float32 [N] LiDAR ray-drop logit (None: rho = 0)
 
     @property
     def n(self) -> int:
@@ -52,19 +53,24 @@ class Surfels:
     def subset(self, idx) -> "Surfels":
         return Surfels(self.pos[idx], self.log_scale[idx], self.quat[idx], self.opacity[idx],
                        self.sh[idx], self.intensity[idx],
-                       None if self.obj_id is None else self.obj_id[idx])
+                       None if self.obj_id is None else self.obj_id[idx],
+                       None if self.ray_drop is None else self.ray_drop[idx])
 
     def concat(self, other: "Surfels") -> "Surfels":
         def ids(s):
             return s.obj_id if s.obj_id is not None else np.full(s.n, -1, np.int32)
         assert self.sh.shape[1] == other.sh.shape[1]
+        def drops(s):
+            return s.ray_drop if s.ray_drop is not None else np.full(s.n, -1e4, np.float32)
+        rd = None if self.ray_drop is None and other.ray_drop is None else \
+            np.concatenate([drops(self), drops(other)]).astype(np.float32)
         return Surfels(np.concatenate([self.pos, other.pos]),
                        np.concatenate([self.log_scale, other.log_scale]),
                        np.concatenate([self.quat, other.quat]),
                        np.concatenate([self.opacity, other.opacity]),
                        np.concatenate([self.sh, other.sh]),
                        np.concatenate([self.intensity, other.intensity]),
-                       np.concatenate([ids(self), ids(other)]).astype(np.int32))
+                       np.concatenate([ids(self), ids(other)]).astype(np.int32), rd)
 
 
 @dataclasses.dataclass

@@ -35,6 +35,29 @@ def test_zero_network_passes_biases():
         assert np.allclose(0.5 + OM.Y00 * out["sh"][s, 0].numpy(), sig)
 
 
+def test_lidar_head_zero_network_passes_biases():
+    """LiDAR head: opacity y0, intensity sigmoid(y1), ray-drop logit y2, y3
+    unused, log-scales y4..5 + ln l_a, quaternion y6..9; no colour."""
+    a = _anchors()
+    b2 = np.random.default_rng(2).normal(0, 1, 100)
+    out = OM.decode(a, np.zeros((36, 64)), np.zeros(64), np.zeros((64, 100)), b2, (0, 0, 0), head="lidar")
+    y = b2.reshape(10, 10)
+    for i in range(a.n):
+        s = slice(10 * i, 10 * i + 10)
+        assert np.allclose(out["opacity"][s].numpy(), y[:, 0])
+        assert np.allclose(out["intensity"][s].numpy(), 1 / (1 + np.exp(-y[:, 1])))
+        assert np.allclose(out["ray_drop"][s].numpy(), y[:, 2])
+        assert np.allclose(out["log_scale"][s].numpy(), y[:, 4:6] + math.log(a.scale[i]))
+        assert np.allclose(out["quat"][s].numpy(), y[:, 6:10])
+        assert np.all(out["sh"][s].numpy() == 0.0)
+    # the unused output y3 does not reach any attribute
+    b3 = b2.copy()
+    b3[3::10] += 5.0
+    o3 = OM.decode(a, np.zeros((36, 64)), np.zeros(64), np.zeros((64, 100)), b3, (0, 0, 0), head="lidar")
+    for k in ("opacity", "intensity", "ray_drop", "log_scale", "quat", "pos"):
+        assert torch.equal(out[k], o3[k]), k
+
+
 def test_single_hidden_unit_closed_form():
     a = _anchors(n=3)
     W1 = np.zeros((36, 64))

@@ -264,6 +264,55 @@ def test_lidar_fronto_plane_range_closed_form():
             assert out["intensity"][i, j] == pytest.approx(0.4 * a, rel=1e-12)
 
 
+def test_lidar_ray_drop_closed_form():
+    """One surfel facing the LiDAR with drop probability rho: a ray through
+    it returns drop = rho a + (1 - a) (its weight a, the rest escapes); a ray
+    that misses every surfel is dropped (drop = 1)."""
+    lid = synth.Lidar(beams=11, columns=181, el_min_deg=-5, el_max_deg=5, world_to_sensor=np.eye(4))
+    q = (math.cos(math.pi / 4), 0, math.sin(math.pi / 4), 0)  # normal -> +x
+    o, rho = 0.8, 0.3
+    s = _one((10, 0, 0), (math.log(0.5), math.log(0.5)), q, _logit(o), intensity=0.4)
+    s.ray_drop = np.asarray([_logit(rho)], np.float64)
+    out = R.render_lidar(s, lid)
+    Rm = _rot(q)
+    hit = 0
+    for i in range(11):
+        for j in range(181):
+            el = math.radians(5 - i)
+            az = math.radians(-180 + (j + 0.5) * 360.0 / 181)
+            d = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+            a = 0.0
+            if d[0] > 0:
+                x = (10.0 / d[0]) * d
+                u, v = Rm[:, 0] @ (x - [10, 0, 0]) / 0.5, Rm[:, 1] @ (x - [10, 0, 0]) / 0.5
+                if u * u + v * v <= 9:
+                    a = min(0.99, o * math.exp(-0.5 * (u * u + v * v)))
+            if a < 1 / 255 and out["alpha"][i, j] == 0.0:
+                assert out["drop"][i, j] == 1.0
+                continue
+            hit += 1
+            assert out["drop"][i, j] == pytest.approx(rho * a + 1 - a, abs=1e-12)
+    assert hit > 5
+
+
+def test_lidar_ray_drop_identities():
+    """rho = 1 everywhere: every ray is dropped (sum w + T = 1); rho = 0:
+    drop = T; the drop attribute never changes range or intensity."""
+    s = synth.driving_scene(n=3000, seed=9, x_range=(-10.0, 10.0), n_boxes=3)
+    lid = synth.spinning_lidar(16, 180, -25.0, 10.0, (0.0, 0.0, 1.8))
+    base = R.render_lidar(s, lid)
+    s.ray_drop = np.full(s.n, 60.0, np.float64)
+    one = R.render_lidar(s, lid)
+    s.ray_drop = np.full(s.n, -60.0, np.float64)
+    zero = R.render_lidar(s, lid)
+    assert base["alpha"].max() > 0.9
+    assert np.abs(one["drop"] - 1.0).max() < 1e-12
+    assert np.abs(zero["drop"] - zero["T"]).max() < 1e-12
+    assert np.all(base["drop"] == base["T"])
+    for k in ("range", "intensity", "alpha", "T"):
+        assert np.array_equal(base[k], one[k]) and np.array_equal(base[k], zero[k]), k
+
+
 def test_lidar_centre_ray_equals_pinhole_centre_pixel():
     """The LiDAR ray at az = 0, el = 0 and a +x-looking pinhole's centre pixel
     are the same ray: same weights, range = depth."""

@@ -120,29 +120,44 @@ class NeuralFrame:
 
         gsr_decode_anchors -> gsr_preprocess_part x 2 -> gsr_bin_sort -> gsr_render_rig
 
+    With `lidar` = (model, anchors) of a separate LiDAR scene (its model's
+    head gsr.HEAD_LIDAR), the cameras see the first decoded table and the
+    LiDARs the second (surfels [A k, A k + A_L k_L)), objects follow both.
     `origin` is the decode's view origin (a camera centre, or the rig centre
     for a rig)."""
 
     def __init__(self, model: NeuralModel, anchors: DeviceAnchors, renderer, objects: DeviceSurfels = None,
-                 poses=None, origin=(0.0, 0.0, 0.0), precision=gsr.DECODE_BF16_TENSOR):
+                 poses=None, origin=(0.0, 0.0, 0.0), precision=gsr.DECODE_BF16_TENSOR, lidar=None):
         self.model, self.anchors, self.r = model, anchors, renderer
         self.objects, self.poses = objects, poses
         self.origin = [float(v) for v in origin]
         self.precision = precision
         self.table = model.new_table(anchors)
         self.n_bg = anchors.n * anchors.k
+        self.lidar, self.table_l, self.n_l = lidar, None, 0
+        if lidar is not None:
+            if lidar[0].head != gsr.HEAD_LIDAR:
+                raise ValueError("the LiDAR scene's model needs the LiDAR head")
+            self.table.sees = gsr.SEES_CAMERAS
+            self.table_l = lidar[0].new_table(lidar[1])
+            self.n_l = lidar[1].n * lidar[1].k
         n_obj = 0 if objects is None else objects.n
-        if renderer.plan.n_surfels != self.n_bg + n_obj:
+        if renderer.plan.n_surfels != self.n_bg + self.n_l + n_obj:
             raise ValueError("plan surfel count must equal decoded + object surfels")
 
     def decode(self, stream=None):
         self.model.decode(self.anchors, self.origin, precision=self.precision, out=self.table, stream=stream)
+        if self.lidar is not None:
+            self.lidar[0].decode(self.lidar[1], self.origin, precision=self.precision, out=self.table_l,
+                                 stream=stream)
 
     def front(self, stream=None):
-        """Preprocess of both parts and the binning sort."""
+        """Preprocess of every part and the binning sort."""
         self.r.preprocess(self.table, self.poses, stream, first=0)
+        if self.lidar is not None:
+            self.r.preprocess(self.table_l, self.poses, stream, first=self.n_bg)
         if self.objects is not None:
-            self.r.preprocess(self.objects, self.poses, stream, first=self.n_bg)
+            self.r.preprocess(self.objects, self.poses, stream, first=self.n_bg + self.n_l)
         self.r.bin_sort(stream)
 
     def render(self, stream=None):

@@ -446,3 +446,14 @@ def init_mlp(seed, feat_dim=32, hidden=64, k=10):
     W2 = rng.uniform(-1, 1, (hidden, 10 * k)) * math.sqrt(6.0 / hidden) * 0.1
     b2 = np.tile(np.array([0.0, 0.0, 0.0, 0.0, -2.0, -2.0, 1.0, 0.0, 0.0, 0.0]), k)
     return W1.astype(np.float32), b1.astype(np.float32), W2.astype(np.float32), b2.astype(np.float32)
+
+
+def init_lidar_mlp(seed, feat_dim=32, hidden=64, k=10):
+    """Seeded weights of the LiDAR scene's anchor MLP (the LiDAR head reads
+    an offset's 10 outputs as opacity, intensity, ray-drop logit, unused,
+    log-scales, quaternion): as init_mlp, with every offset starting at
+    intensity 0.5 and ray-drop probability sigmoid(-1)."""
+    W1, b1, W2, b2 = init_mlp(seed, feat_dim, hidden, k)
+    b2 = b2.copy()
+    b2[2::10] = -1.0
+    return W1, b1, W2, b2

@@ -111,9 +111,7 @@ def _anchors(n_surfels=20_000, seed=91):
 
 def _lidar_model(seed=17):
     from paper_2503_11731_gb300.neural import NeuralModel
-    W1, b1, W2, b2 = synth.init_mlp(seed)
-    b2 = b2.copy()
-    b2[2::10] = -1.0  # ray-drop logits start near sigmoid(-1)
+    W1, b1, W2, b2 = synth.init_lidar_mlp(seed)
     return (W1, b1, W2, b2), NeuralModel(W1, b1, W2, b2, head=gsr.HEAD_LIDAR)
 
 

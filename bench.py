@@ -446,7 +446,7 @@ def two_scene_frame(args, r, sensors, da, model, d_obj, pose_t, origin, stream):
     n = 2 * da.n * da.k + d_obj.n
     tiles = [(r.plan.sensors[i].tile_w, r.plan.sensors[i].tile_h) for i in range(len(sensors))]
     r2 = Renderer(n, sensors, tiles=tiles, max_dup=args.max_dup, batch_depth=r.plan.tiling.batch_depth,
-                  split=(r.plan.tiling.split_first, r.plan.tiling.split_chunk),
+                  split=(r.plan.tiling.split_first, r.plan.tiling.split_chunk), lidar_split=r.lidar_split(),
                   outputs=("rgb", "depth", "normal", "alpha", "trans", "drop"))
     nf = NeuralFrame(model, da, r2, d_obj, pose_t, origin, gsr.DECODE_BF16_TENSOR, lidar=(model_l, da))
     nf.render()
@@ -500,6 +500,7 @@ def run_gpu(args):
     tiles = [parse(args.lidar_tile) if s.kind == "lidar" else parse(args.camera_tile) for s in sensors]
     r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles, batch_depth=args.batch_depth,
                  split=(args.split_first, args.split_chunk),
+                 lidar_split=(args.lidar_split_first, args.lidar_split_chunk),
                  outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
@@ -535,7 +536,8 @@ def run_gpu(args):
         n_main = scene.n
     tiling = {"tiles": [f"{r.plan.sensors[i].tile_w}x{r.plan.sensors[i].tile_h}" for i in range(len(sensors))],
               "batch_depth": r.plan.tiling.batch_depth or "CTA width",
-              "split_first_chunk": [r.plan.tiling.split_first or "default", r.plan.tiling.split_chunk or "default"]}
+              "split_first_chunk": [r.plan.tiling.split_first or "default", r.plan.tiling.split_chunk or "default"],
+              "lidar_split_first_chunk": [v or "plan's" for v in (r.lidar_split() or (0, 0))]}
     tm = Timer(stream, [k for k, _ in stages])
 
     def step(record=False):
@@ -635,6 +637,7 @@ def run_gpu(args):
             "explicit_batched_ms": batched,
             "explicit_batched_stage_ms": {"pre_sort": ex_front, "render_rig": ex_render},
             "explicit_tiling": {"camera_tile": r.tile_of("camera"), "lidar_tile": r.tile_of("lidar"),
+                                "lidar_split": r.lidar_split(),
                                 "batch_depth": r.plan.tiling.batch_depth,
                                 "split": [r.plan.tiling.split_first, r.plan.tiling.split_chunk],
                                 "autotune_best_ms": None if ex_tuned is None else ex_tuned["best_ms"]},
@@ -733,6 +736,8 @@ def main():
     ap.add_argument("--split-chunk", type=int, default=0)
     ap.add_argument("--camera-tile", default="16x16")
     ap.add_argument("--lidar-tile", default="8x8")
+    ap.add_argument("--lidar-split-first", type=int, default=0)
+    ap.add_argument("--lidar-split-chunk", type=int, default=0)
     ap.add_argument("--sample-rays", type=int, default=16)
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the explicit-form and decode-only timings")

@@ -123,6 +123,8 @@ typedef struct {
     float bg[3];       /* camera background, composited as bg * T */
     int32_t tile_w;    /* this sensor's screen tile (rays); 0 = the plan's tiling.  */
     int32_t tile_h;    /* w, h powers of two, w*h in {32,64,128,256}               */
+    int32_t split_first; /* this sensor's list split (see gsr_tiling); 0 = the   */
+    int32_t split_chunk; /* plan's                                               */
 } gsr_sensor;
 
 /* Default screen tiling of a plan's sensors (tile_w, tile_h powers of two,
@@ -513,11 +515,13 @@ gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t*
 /* ------------------------------------------------------------- autotune */
 
 /*
- * Search space of gsr_autotune (host memory).  Every pinhole sensor takes
- * the same camera tile, every LiDAR the same LiDAR tile; n_* = 0 keeps the
- * plan's choice.  Tiles obey gsr_tiling's rule; batch depths and split
- * lengths are values gsr_tiling accepts.  Each candidate renders `warmup`
- * untimed and `reps` timed frames (reps >= 1).
+ * Search space of gsr_autotune (host memory).  Every camera takes the same
+ * camera tile, every LiDAR the same LiDAR tile; split_firsts / split_chunks
+ * are the plan's list split (the cameras'), lidar_split_* the LiDARs' own
+ * (gsr_sensor.split_*; their long horizon lists favour shorter first
+ * walks); n_* = 0 keeps the plan's choice.  Tiles obey gsr_tiling's rule;
+ * batch depths and split lengths are values gsr_tiling accepts.  Each
+ * candidate renders `warmup` untimed and `reps` timed frames (reps >= 1).
  */
 #define GSR_AUTOTUNE_MAX 8
 typedef struct {
@@ -531,6 +535,10 @@ typedef struct {
     int32_t split_firsts[GSR_AUTOTUNE_MAX];
     int32_t n_split_chunks;
     int32_t split_chunks[GSR_AUTOTUNE_MAX];
+    int32_t n_lidar_split_firsts;
+    int32_t lidar_split_firsts[GSR_AUTOTUNE_MAX];
+    int32_t n_lidar_split_chunks;
+    int32_t lidar_split_chunks[GSR_AUTOTUNE_MAX];
     int32_t warmup, reps;
 } gsr_autotune_space;
 
@@ -542,6 +550,7 @@ typedef struct {
     int32_t lidar_tile[2];
     int32_t batch_depth;
     int32_t split_first, split_chunk;
+    int32_t lidar_split_first, lidar_split_chunk; /* 0 = the plan's */
     float ms;
 } gsr_autotune_trial;
 
@@ -549,7 +558,7 @@ typedef struct {
     gsr_plan plan;        /* the input plan re-initialised with the fastest tiling */
     float best_ms;
     int32_t n_tried;
-    gsr_autotune_trial tried[5 * GSR_AUTOTUNE_MAX + 1];
+    gsr_autotune_trial tried[7 * GSR_AUTOTUNE_MAX + 1];
 } gsr_autotune_result;
 
 /* Workspace bytes gsr_autotune needs: the largest over the candidates
@@ -561,7 +570,8 @@ gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gsr_autotune_
  * staging depth and list splitting are this implementation's free
  * parameters).  Coordinate descent from the plan's tiling: the camera tile
  * over its candidates, then the LiDAR tile, the batch depth, the first split
- * length and the later chunk length, each candidate timed with CUDA
+ * length and the later chunk length, then the LiDARs' two split lengths,
+ * each candidate timed with CUDA
  * events over whole frames of the given surfels: `parts` (n_parts tables,
  * consecutive in the plan from surfel 0, as gsr_preprocess_part) and
  * `objects` (may be NULL), rendered into camera_outs / lidar_outs (as
@@ -601,7 +611,8 @@ size_t gsr_struct_size(int32_t which);
  * LiDAR azimuth wrap), 2 tile counts (uint32 per slot), 3 depth keys
  * (float bits per slot), 4 sorted pair tile ids (uint32), 5 sorted pair
  * slots (uint32), 6 tile ranges (uint2 per global tile), 7 visible slots in
- * depth order (uint32).
+ * depth order (uint32), 8 list splits (uint4 per global tile: x = chunks
+ * after the first, 0 = not split).
  */
 gsr_status gsr_workspace_region(const gsr_plan* plan, const void* workspace, int32_t which, void** ptr,
                                 size_t* bytes);

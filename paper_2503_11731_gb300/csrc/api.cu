@@ -46,8 +46,6 @@ SensorTable make_sensor_table(const gsr_plan* p)
     t.tile_h = p->tiling.tile_h;
     t.total_tiles = p->tile_base[p->n_sensors];
     t.batch = p->tiling.batch_depth;
-    t.split_first = p->tiling.split_first > 0 ? p->tiling.split_first : kSplitFirstDefault;
-    t.split_chunk = p->tiling.split_chunk > 0 ? p->tiling.split_chunk : kSplitChunkDefault;
     const double deg = 3.14159265358979323846 / 180.0;
     for (int i = 0; i < p->n_sensors; ++i) {
         const gsr_sensor& s = p->sensors[i];
@@ -81,6 +79,11 @@ SensorTable make_sensor_table(const gsr_plan* p)
         }
         d.near_plane = s.near_plane;
         for (int c = 0; c < 3; ++c) d.bg[c] = s.bg[c];
+        // list split: the sensor's, else the plan's, else the defaults
+        const int sf = s.split_first > 0 ? s.split_first : p->tiling.split_first;
+        const int sc = s.split_chunk > 0 ? s.split_chunk : p->tiling.split_chunk;
+        d.split_first = sf > 0 ? sf : kSplitFirstDefault;
+        d.split_chunk = sc > 0 ? sc : kSplitChunkDefault;
     }
     return t;
 }
@@ -125,6 +128,8 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
             !(s.cx / s.fx <= 3.1415960f && ((float)s.width - s.cx) / s.fx <= 3.1415960f))
             return GSR_ERR_INVALID_ARG;
         if (s.kind == GSR_SENSOR_LIDAR && (s.height < 2 || !(s.el_max_deg > s.el_min_deg))) return GSR_ERR_INVALID_ARG;
+        if (s.split_first != 0 && (s.split_first < 256 || s.split_first > (1 << 24))) return GSR_ERR_UNSUPPORTED;
+        if (s.split_chunk != 0 && (s.split_chunk < 64 || s.split_chunk > (1 << 24))) return GSR_ERR_UNSUPPORTED;
         plan->sensors[i] = s;
         if (s.tile_w == 0 && s.tile_h == 0) {
             plan->sensors[i].tile_w = tiling->tile_w;
@@ -331,6 +336,7 @@ extern "C" gsr_status gsr_workspace_region(const gsr_plan* plan, const void* wor
     case 5: r = pb ? R_PAIR_VAL_B : R_PAIR_VAL_A; n = (uint64_t)plan->max_dup * 4; break;
     case 6: r = R_RANGES; n = (uint64_t)plan->tile_base[plan->n_sensors] * 8; break;
     case 7: r = vb ? R_VIS_VAL_B : R_VIS_VAL_A; n = slots * 4; break;
+    case 8: r = R_SPLIT_INFO; n = (uint64_t)plan->tile_base[plan->n_sensors] * 16; break;
     default: return GSR_ERR_INVALID_ARG;
     }
     *ptr = region<void>(plan, workspace, r);

@@ -24,31 +24,48 @@ struct Candidate {
     int cam[2];
     int lid[2];
     int bd;
-    int sf, sc;  // split_first, split_chunk
+    int sf, sc;    // the plan's split_first, split_chunk (the cameras')
+    int lsf, lsc;  // the LiDARs' own (0 = the plan's)
 };
 
 bool same(const Candidate& a, const Candidate& b)
 {
     return a.cam[0] == b.cam[0] && a.cam[1] == b.cam[1] && a.lid[0] == b.lid[0] && a.lid[1] == b.lid[1] &&
-           a.bd == b.bd && a.sf == b.sf && a.sc == b.sc;
+           a.bd == b.bd && a.sf == b.sf && a.sc == b.sc && a.lsf == b.lsf && a.lsc == b.lsc;
 }
 
 // The plan of a candidate: the input plan's sensors and capacity with every
-// pinhole sensor on cand.cam, every LiDAR on cand.lid and cand.bd staged.
+// camera on cand.cam and the plan's list split, every LiDAR on cand.lid and
+// its own split, and cand.bd staged.
 gsr_status candidate_plan(const gsr_plan* base, const Candidate& c, gsr_plan* out)
 {
     gsr_sensor sensors[GSR_MAX_SENSORS];
     for (int i = 0; i < base->n_sensors; ++i) {
         sensors[i] = base->sensors[i];
-        const int* t = sensors[i].kind == GSR_SENSOR_LIDAR ? c.lid : c.cam;
+        const bool lidar = sensors[i].kind == GSR_SENSOR_LIDAR;
+        const int* t = lidar ? c.lid : c.cam;
         sensors[i].tile_w = t[0];
         sensors[i].tile_h = t[1];
+        sensors[i].split_first = lidar ? c.lsf : 0;
+        sensors[i].split_chunk = lidar ? c.lsc : 0;
     }
     gsr_tiling tiling = base->tiling;
     tiling.batch_depth = c.bd;
     tiling.split_first = c.sf;
     tiling.split_chunk = c.sc;
     return gsr_plan_init(out, base->n_surfels, sensors, base->n_sensors, &tiling, base->max_dup);
+}
+
+// List split of the plan's first LiDAR (0 = the plan's).
+void plan_lidar_split(const gsr_plan* p, int& sf, int& sc)
+{
+    sf = sc = 0;
+    for (int i = 0; i < p->n_sensors; ++i)
+        if (p->sensors[i].kind == GSR_SENSOR_LIDAR) {
+            sf = p->sensors[i].split_first;
+            sc = p->sensors[i].split_chunk;
+            return;
+        }
 }
 
 // Tile of the plan's first LiDAR (lidar) or first camera of either model
@@ -95,6 +112,8 @@ bool space_ok(const gsr_autotune_space* sp)
     if (sp->n_batch_depths < 0 || sp->n_batch_depths > GSR_AUTOTUNE_MAX) return false;
     if (sp->n_split_firsts < 0 || sp->n_split_firsts > GSR_AUTOTUNE_MAX) return false;
     if (sp->n_split_chunks < 0 || sp->n_split_chunks > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_lidar_split_firsts < 0 || sp->n_lidar_split_firsts > GSR_AUTOTUNE_MAX) return false;
+    if (sp->n_lidar_split_chunks < 0 || sp->n_lidar_split_chunks > GSR_AUTOTUNE_MAX) return false;
     return true;
 }
 
@@ -110,6 +129,7 @@ extern "C" gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gs
     start.bd = plan->tiling.batch_depth;
     start.sf = plan->tiling.split_first;
     start.sc = plan->tiling.split_chunk;
+    plan_lidar_split(plan, start.lsf, start.lsc);
     size_t best = 0;
     for (const Candidate& c : all_candidates(space, start)) {
         gsr_plan p;
@@ -180,6 +200,7 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     best.bd = plan->tiling.batch_depth;
     best.sf = plan->tiling.split_first;
     best.sc = plan->tiling.split_chunk;
+    plan_lidar_split(plan, best.lsf, best.lsc);
     float best_ms = -1.f;
     std::vector<std::pair<Candidate, float>> seen;
     auto visit = [&](const Candidate& c) -> gsr_status {
@@ -196,6 +217,8 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
             t.batch_depth = c.bd;
             t.split_first = c.sf;
             t.split_chunk = c.sc;
+            t.lidar_split_first = c.lsf;
+            t.lidar_split_chunk = c.lsc;
             t.ms = ms;
         }
         if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
@@ -230,6 +253,16 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     for (int i = 0; r == GSR_OK && i < space->n_split_chunks; ++i) {
         Candidate c = best;
         c.sc = space->split_chunks[i];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_lidar_split_firsts; ++i) {
+        Candidate c = best;
+        c.lsf = space->lidar_split_firsts[i];
+        r = visit(c);
+    }
+    for (int i = 0; r == GSR_OK && i < space->n_lidar_split_chunks; ++i) {
+        Candidate c = best;
+        c.lsc = space->lidar_split_chunks[i];
         r = visit(c);
     }
     cudaEventDestroy(e0);

@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) k_render_backward(SensorTable tab, int se
     const uint32_t tile = sorder[blockIdx.x];  // longest lists first
     const uint4 info = sp.info[tile];
     const bool split = info.x > 0 && sp.state[tile].x == 1u;
-    const int lo_pos = split ? chunk_begin(sp.first, sp.chunk, (int)info.x) : 0;
+    const int lo_pos = split ? chunk_begin(sd.split_first, sd.split_chunk, (int)info.x) : 0;
     uint32_t gb = 0;
     bwd_tile<KIND>(tab, sd, (int)tile - sd.tile_base, lo_pos, 0x7fffffff, 0, sp, 0, rec, ranges, pval, a, counters,
                    sm.bars, sm.sslot, sm.buf, wmax, gb);
@@ -537,8 +537,8 @@ __global__ void __launch_bounds__(256) k_render_backward_chunks(SensorTable tab,
         const uint2 it = sp.items[item];
         if (sp.state[it.x].x != 1u) continue;  // finished in chunk 0: walked whole by k_render_backward
         const int cc = (int)it.y - 1;
-        bwd_tile<KIND>(tab, sd, (int)it.x - sd.tile_base, chunk_begin(sp.first, sp.chunk, cc),
-                       chunk_begin(sp.first, sp.chunk, cc + 1), 1, sp, cc, rec, ranges, pval, a, counters, sm.bars,
+        bwd_tile<KIND>(tab, sd, (int)it.x - sd.tile_base, chunk_begin(sd.split_first, sd.split_chunk, cc),
+                       chunk_begin(sd.split_first, sd.split_chunk, cc + 1), 1, sp, cc, rec, ranges, pval, a, counters, sm.bars,
                        sm.sslot, sm.buf, wmax, gb);
     }
 }

@@ -91,6 +91,7 @@ struct SensorDev {
     float inv_d_el, inv_d_az;
     float near_plane;
     float bg[3];
+    int split_first, split_chunk;  // long lists: chunk 0 = split_first positions, then split_chunk each
 };
 
 struct SensorTable {
@@ -98,7 +99,6 @@ struct SensorTable {
     int tile_w, tile_h;
     int total_tiles;
     int batch;  // records staged per step of a walk; 0 = the CTA's thread count
-    int split_first, split_chunk;  // long lists: chunk 0 = split_first positions, then split_chunk each
     SensorDev s[GSR_MAX_SENSORS];
 };
 
@@ -188,6 +188,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
             smem_u32(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
@@ -522,7 +529,6 @@ struct SplitBufs {
     uint2* state;       // per tile: x = 1 carry stored / 2 finished in chunk 0, y = chunks not yet walked
     const uint2* items; // (tile, chunk)
     float* rays;        // ray records, kRayWords words each
-    int first, chunk;   // chunk 0 = [0, first), then chunks of `chunk` positions
 };
 
 __device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, int R, int k)

@@ -250,7 +250,7 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile,
     ray_init(s, !ray.inside, (uint32_t)n);
     const uint4 info = sp.info[tile];
     const bool split = info.x > 0;
-    walk_list<KIND>(sd, ray, range.x, 0, split ? sp.first : n, rec, pval, s, counters, buf, bars, gb, D);
+    walk_list<KIND>(sd, ray, range.x, 0, split ? sd.split_first : n, rec, pval, s, counters, buf, bars, gb, D);
     if (split) {
         const int R = sd.tile_w * sd.tile_h;
         if (!__syncthreads_and(s.done)) {
@@ -286,8 +286,8 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
             done = carry.done;
         }
         ray_init(s, done, (uint32_t)n);
-        walk_list<KIND>(sd, ray, range.x, chunk_begin(sp.first, sp.chunk, c),
-                        min(n, chunk_begin(sp.first, sp.chunk, c + 1)), rec, pval, s, counters,
+        walk_list<KIND>(sd, ray, range.x, chunk_begin(sd.split_first, sd.split_chunk, c),
+                        min(n, chunk_begin(sd.split_first, sd.split_chunk, c + 1)), rec, pval, s, counters,
                         buf, bars, gb, D);
         if (r < R) store_ray(ray_block(sp, info.y, R, c), R, r, s);
         __threadfence();
@@ -329,8 +329,8 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
             // rays that stop inside chunk k walk it again from their state
             const bool was = S.done;
             S.done = S.done || !need;
-            walk_list<KIND>(sd, ray, range.x, chunk_begin(sp.first, sp.chunk, k),
-                            min(n, chunk_begin(sp.first, sp.chunk, k + 1)), rec, pval, S,
+            walk_list<KIND>(sd, ray, range.x, chunk_begin(sd.split_first, sd.split_chunk, k),
+                            min(n, chunk_begin(sd.split_first, sd.split_chunk, k + 1)), rec, pval, S,
                             counters, buf, bars, gb, D);
             if (!need) S.done = was;
         }
@@ -482,9 +482,6 @@ SplitBufs split_bufs(const gsr_plan* p, const void* ws)
     sp.state = region<uint2>(p, ws, R_SPLIT_STATE);
     sp.items = region<uint2>(p, ws, R_SPLIT_ITEMS);
     sp.rays = region<float>(p, ws, R_SPLIT_RAYS);
-    const SensorTable tab = make_sensor_table(p);
-    sp.first = tab.split_first;
-    sp.chunk = tab.split_chunk;
     return sp;
 }
 

@@ -198,41 +198,87 @@ __global__ void __launch_bounds__(256) k_hist_block_apply(uint32_t* __restrict__
     }
 }
 
-// Stable scatter of one 8-bit digit.  Each CTA walks its chunk in tiles of
-// kSortTile items; warp w of a tile owns items [w*256, w*256+256) and ranks
-// them in lane order with warp match, so the rank order is the input order.
+// Stable scatter of one 8-bit digit pass.  CTA g owns the contiguous chunk
+// [b, e) of the input (the same chunk k_radix_hist counted) and walks it in
+// tiles of kSortTile items; warp w of a tile owns items [w*256, w*256+256)
+// and ranks them with match_any, a prefix over warps orders the tile, and
+// the tile is written digit by digit from shared memory (runs of equal
+// digits are contiguous in the output).  Keys and values arrive by two
+// bulk copies per tile into a double buffer (one mbarrier each): tile t + 1
+// is in flight while tile t is ranked, ordered in the buffer and written.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                 const uint32_t* __restrict__ vin,
                                                                 uint32_t* __restrict__ kout,
                                                                 uint32_t* __restrict__ vout,
                                                                 const uint32_t* __restrict__ n_ptr, int shift,
-                                                                const uint32_t* __restrict__ hist)
+                                                                const uint32_t* __restrict__ hist,
+                                                                uint32_t* __restrict__ counters)
 {
     constexpr int NW = kSortThreads / 32;
     constexpr int SEG = kSortTile / NW;  // items per warp per tile (256)
-    __shared__ uint32_t ks[kSortTile];
-    __shared__ uint32_t vs[kSortTile];
+    __shared__ alignas(16) uint32_t kb[2][kSortTile];
+    __shared__ alignas(16) uint32_t vb[2][kSortTile];
     __shared__ uint32_t wh[NW][kRadix];
     __shared__ uint32_t dbase[kRadix];
     __shared__ uint32_t toff[kRadix];
     __shared__ uint32_t tcnt[kRadix];
     __shared__ uint32_t sm[9];
+    __shared__ alignas(8) uint64_t bar[2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     uint64_t b, e;
     chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
+    const int ntiles = e > b ? (int)((e - b + kSortTile - 1) / kSortTile) : 0;
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) dbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
-    for (uint64_t t0 = b; t0 < e; t0 += kSortTile) {
-        const int nt = (int)((e - t0) < (uint64_t)kSortTile ? (e - t0) : (uint64_t)kSortTile);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // tile t: whole 16-byte groups by bulk copy (a chunk starts 128-byte
+    // aligned), a ragged end of < 4 items by plain loads
+    auto tile_items = [&](int t) {
+        const uint64_t s0 = b + (uint64_t)t * kSortTile;
+        return (int)((e - s0) < (uint64_t)kSortTile ? (e - s0) : (uint64_t)kSortTile);
+    };
+    auto issue = [&](int t) {
+        const uint64_t s0 = b + (uint64_t)t * kSortTile;
+        const uint32_t nbulk = (uint32_t)tile_items(t) & ~3u;
+        mbar_arrive_expect_tx(&bar[t & 1], nbulk * 8u);
+        if (nbulk > 0) {
+            bulk_g2s(kb[t & 1], kin + s0, nbulk * 4u, &bar[t & 1]);
+            bulk_g2s(vb[t & 1], vin + s0, nbulk * 4u, &bar[t & 1]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        if (ntiles > 0) issue(0);
+        if (ntiles > 1) issue(1);
+    }
+    for (int t = 0; t < ntiles; ++t) {
+        const uint64_t t0 = b + (uint64_t)t * kSortTile;
+        const int nt = tile_items(t);
+        const int nbulk = nt & ~3;
+        uint32_t* kt = kb[t & 1];
+        uint32_t* vt = vb[t & 1];
         for (int k = threadIdx.x; k < NW * kRadix; k += kSortThreads) (&wh[0][0])[k] = 0;
-        __syncthreads();
+        const bool got = mbar_wait_bounded(&bar[t & 1], (uint32_t)(t >> 1) & 1u, counters);
+        if (!__syncthreads_and(got)) {
+            // give up: let the copies in flight land (bounded waits) before leaving
+            if (threadIdx.x == 0) {
+                mbar_wait_bounded(&bar[t & 1], (uint32_t)(t >> 1) & 1u, counters);
+                if (t + 1 < ntiles) mbar_wait_bounded(&bar[(t + 1) & 1], (uint32_t)((t + 1) >> 1) & 1u, counters);
+            }
+            __syncthreads();
+            return;
+        }
         uint32_t key[SEG / 32], val[SEG / 32], rank[SEG / 32];
 #pragma unroll
         for (int r = 0; r < SEG / 32; ++r) {
             const int li = w * SEG + r * 32 + lane;
             const bool ok = li < nt;
-            key[r] = ok ? kin[t0 + li] : 0u;
-            val[r] = ok ? vin[t0 + li] : 0u;
+            key[r] = li < nbulk ? kt[li] : ok ? kin[t0 + li] : 0u;
+            val[r] = li < nbulk ? vt[li] : ok ? vin[t0 + li] : 0u;
             const uint32_t d = (key[r] >> shift) & (kRadix - 1);
             const uint32_t okm = __ballot_sync(0xffffffffu, ok);
             const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane) & okm;
@@ -259,26 +305,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         uint32_t tot;
         toff[d] = block_exclusive_scan<uint32_t, kSortThreads>(c, tot, sm);
         __syncthreads();
+        // the tile in digit order, in its own buffer (every read of it is done)
 #pragma unroll
         for (int r = 0; r < SEG / 32; ++r) {
             const int li = w * SEG + r * 32 + lane;
             if (li < nt) {
                 const uint32_t dd = (key[r] >> shift) & (kRadix - 1);
                 const uint32_t pos = toff[dd] + wh[w][dd] + rank[r];
-                ks[pos] = key[r];
-                vs[pos] = val[r];
+                kt[pos] = key[r];
+                vt[pos] = val[r];
             }
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nt; k += kSortThreads) {
-            const uint32_t kk = ks[k];
+            const uint32_t kk = kt[k];
             const uint32_t dd = (kk >> shift) & (kRadix - 1);
             const uint32_t g = dbase[dd] + (uint32_t)k - toff[dd];
             kout[g] = kk;
-            vout[g] = vs[k];
+            vout[g] = vt[k];
         }
+        fence_proxy_async_smem();  // this thread's accesses to the buffer precede the next bulk copy into it
         __syncthreads();
         dbase[d] += tcnt[d];
+        if (threadIdx.x == 0 && t + 2 < ntiles) issue(t + 2);
         __syncthreads();
     }
 }
@@ -553,11 +602,12 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
         unsigned long long need = 0;
         if (t < n_tiles) {
             const uint32_t len = ranges[t].y - ranges[t].x;
-            if (len > (uint32_t)tab.split_first) {
-                C = (len - (uint32_t)tab.split_first - 1) / (uint32_t)tab.split_chunk + 1;
-                int s = 0;
-                while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
-                need = (unsigned long long)(C + 1) * (unsigned long long)(tab.s[s].tile_w * tab.s[s].tile_h);
+            int s = 0;
+            while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
+            const SensorDev& sd = tab.s[s];
+            if (len > (uint32_t)sd.split_first) {
+                C = (len - (uint32_t)sd.split_first - 1) / (uint32_t)sd.split_chunk + 1;
+                need = (unsigned long long)(C + 1) * (unsigned long long)(sd.tile_w * sd.tile_h);
             }
         }
         unsigned long long tot_rays;
@@ -609,6 +659,7 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
 static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                        const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st, int G)
 {
+    uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     uint32_t* hist = region<uint32_t>(p, ws, R_HIST);
     uint32_t* sums = hist + (size_t)kRadix * p->sort_ctas;
     const int nh = kRadix * G, nb = (nh + kScanBlock - 1) / kScanBlock;
@@ -622,7 +673,7 @@ static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, 
         k_hist_block_sums<<<nb, 256, 0, st>>>(hist, nh, sums);
         k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(sums, nb, nullptr, nullptr, 0, -1);
         k_hist_block_apply<<<nb, 256, 0, st>>>(hist, nh, sums);
-        k_radix_scatter<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist);
+        k_radix_scatter<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist, counters);
     }
 }
 

@@ -63,15 +63,17 @@ class Renderer:
 
     def __init__(self, n_surfels, sensors, tile=(16, 16), max_dup=0, bg=(0.0, 0.0, 0.0), device="cuda",
                  outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib"), tiles=None, batch_depth=0,
-                 split=(0, 0)):
+                 split=(0, 0), lidar_split=None):
         """`tile` is the default tiling; `tiles` (optional) a per-sensor list of (w, h) or None;
         `batch_depth` the records staged per step of a tile walk (0 = the CTA's thread count);
-        `split` = (split_first, split_chunk) of long tile lists (0 = the library's defaults)."""
+        `split` = (split_first, split_chunk) of long tile lists (0 = the library's defaults);
+        `lidar_split` the LiDARs' own (None = the plan's)."""
         self.descs = list(sensors)
         tiles = tiles if tiles is not None else [None] * len(self.descs)
         if len(tiles) != len(self.descs):
             raise ValueError(f"{len(tiles)} tiles for {len(self.descs)} sensors")
-        self.structs = [gsr.sensor(d, bg, t) for d, t in zip(self.descs, tiles)]
+        self.structs = [gsr.sensor(d, bg, t, lidar_split if d.kind == "lidar" else None)
+                        for d, t in zip(self.descs, tiles)]
         self.plan = gsr.plan_init(n_surfels, self.structs, tile, max_dup, batch_depth, split)
         self.ws_bytes = gsr.workspace_size(self.plan)
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
@@ -172,15 +174,17 @@ class Renderer:
 
     def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
                  lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (8, 16), (16, 16)), batch_depths=(64, 128, 256),
-                 split_firsts=(4096, 8192, 16384, 32768), split_chunks=(256, 384, 512, 1024), warmup=1, reps=3,
-                 stream=None):
+                 split_firsts=(4096, 8192, 16384, 32768), split_chunks=(256, 384, 512, 1024),
+                 lidar_split_firsts=(1024, 2048, 4096, 8192), lidar_split_chunks=(128, 256, 512, 1024), warmup=1,
+                 reps=3, stream=None):
         """Pick the tiling of this rig with gsr_autotune over `parts` (DeviceSurfels
         consecutive in the plan) and re-plan with it; returns the trial list."""
         obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
         has = {d.kind for d in self.descs}
-        space = gsr.autotune_space(camera_tiles if has - {"lidar"} else (),
-                                   lidar_tiles if "lidar" in has else (), batch_depths, warmup, reps,
-                                   split_firsts, split_chunks)
+        lid = "lidar" in has
+        space = gsr.autotune_space(camera_tiles if has - {"lidar"} else (), lidar_tiles if lid else (),
+                                   batch_depths, warmup, reps, split_firsts, split_chunks,
+                                   lidar_split_firsts if lid else (), lidar_split_chunks if lid else ())
         need = gsr.autotune_workspace_size(self.plan, space)
         self._alloc_workspace(need)
         res = gsr.autotune(self.plan, [p.struct() for p in parts], obj, space, self.ws_ptr, need,
@@ -189,11 +193,21 @@ class Renderer:
         self.ws_bytes = gsr.workspace_size(self.plan)
         self._alloc_workspace(self.ws_bytes)
         trials = [{"camera_tile": tuple(t.camera_tile), "lidar_tile": tuple(t.lidar_tile),
-                   "batch_depth": t.batch_depth, "split": (t.split_first, t.split_chunk), "ms": t.ms}
+                   "batch_depth": t.batch_depth, "split": (t.split_first, t.split_chunk),
+                   "lidar_split": (t.lidar_split_first, t.lidar_split_chunk), "ms": t.ms}
                   for t in res.tried[:res.n_tried]]
         return {"best_ms": res.best_ms, "trials": trials, "camera_tile": self.tile_of("camera"),
                 "lidar_tile": self.tile_of("lidar"), "batch_depth": self.plan.tiling.batch_depth,
-                "split": (self.plan.tiling.split_first, self.plan.tiling.split_chunk)}
+                "split": (self.plan.tiling.split_first, self.plan.tiling.split_chunk),
+                "lidar_split": self.lidar_split()}
+
+    def lidar_split(self):
+        """(split_first, split_chunk) of the first LiDAR (0 = the plan's), or None."""
+        for i, d in enumerate(self.descs):
+            if d.kind == "lidar":
+                s = self.plan.sensors[i]
+                return (s.split_first, s.split_chunk)
+        return None
 
     def tile_of(self, kind):
         """Tile of the first sensor of `kind` ("camera" = pinhole or cylindrical)."""

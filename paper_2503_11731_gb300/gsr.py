@@ -37,7 +37,8 @@ class Sensor(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("width", c_i32), ("height", c_i32),
                 ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
                 ("el_min_deg", c_f32), ("el_max_deg", c_f32), ("az0_deg", c_f32), ("near_plane", c_f32),
-                ("world_to_sensor", c_f32 * 16), ("bg", c_f32 * 3), ("tile_w", c_i32), ("tile_h", c_i32)]
+                ("world_to_sensor", c_f32 * 16), ("bg", c_f32 * 3), ("tile_w", c_i32), ("tile_h", c_i32),
+                ("split_first", c_i32), ("split_chunk", c_i32)]
 
 
 class Tiling(ctypes.Structure):
@@ -102,17 +103,20 @@ class AutotuneSpace(ctypes.Structure):
                 ("n_batch_depths", c_i32), ("batch_depths", c_i32 * AUTOTUNE_MAX),
                 ("n_split_firsts", c_i32), ("split_firsts", c_i32 * AUTOTUNE_MAX),
                 ("n_split_chunks", c_i32), ("split_chunks", c_i32 * AUTOTUNE_MAX),
+                ("n_lidar_split_firsts", c_i32), ("lidar_split_firsts", c_i32 * AUTOTUNE_MAX),
+                ("n_lidar_split_chunks", c_i32), ("lidar_split_chunks", c_i32 * AUTOTUNE_MAX),
                 ("warmup", c_i32), ("reps", c_i32)]
 
 
 class AutotuneTrial(ctypes.Structure):
     _fields_ = [("camera_tile", c_i32 * 2), ("lidar_tile", c_i32 * 2), ("batch_depth", c_i32),
-                ("split_first", c_i32), ("split_chunk", c_i32), ("ms", c_f32)]
+                ("split_first", c_i32), ("split_chunk", c_i32), ("lidar_split_first", c_i32),
+                ("lidar_split_chunk", c_i32), ("ms", c_f32)]
 
 
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("plan", Plan), ("best_ms", c_f32), ("n_tried", c_i32),
-                ("tried", AutotuneTrial * (5 * AUTOTUNE_MAX + 1))]
+                ("tried", AutotuneTrial * (7 * AUTOTUNE_MAX + 1))]
 
 
 DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
@@ -215,12 +219,15 @@ def _check(code, where):
 
 
 # ----------------------------------------------------------------- structs
-def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None) -> Sensor:
+def sensor(desc, bg=(0.0, 0.0, 0.0), tile=None, split=None) -> Sensor:
     """Sensor struct from a synth.Pinhole / synth.Cylindrical / synth.Lidar-like description;
-    `tile` = (w, h) overrides the plan's default tiling for this sensor."""
+    `tile` = (w, h) and `split` = (split_first, split_chunk) override the
+    plan's tiling and list split for this sensor."""
     s = Sensor()
     if tile is not None:
         s.tile_w, s.tile_h = int(tile[0]), int(tile[1])
+    if split is not None:
+        s.split_first, s.split_chunk = int(split[0]), int(split[1])
     kind = getattr(desc, "kind", "pinhole")
     if kind == "lidar":
         s.kind = LIDAR
@@ -334,7 +341,7 @@ def render_rig(plan, ws, ws_bytes, outs, stream):
 
 
 def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, reps=3, split_firsts=(),
-                   split_chunks=()) -> AutotuneSpace:
+                   split_chunks=(), lidar_split_firsts=(), lidar_split_chunks=()) -> AutotuneSpace:
     sp = AutotuneSpace()
     for name, vals in (("camera_tiles", camera_tiles), ("lidar_tiles", lidar_tiles)):
         if len(vals) > AUTOTUNE_MAX:
@@ -344,7 +351,8 @@ def autotune_space(camera_tiles=(), lidar_tiles=(), batch_depths=(), warmup=1, r
         for i, (w, h) in enumerate(vals):
             arr[i][0], arr[i][1] = int(w), int(h)
     for name, vals in (("batch_depths", batch_depths), ("split_firsts", split_firsts),
-                       ("split_chunks", split_chunks)):
+                       ("split_chunks", split_chunks), ("lidar_split_firsts", lidar_split_firsts),
+                       ("lidar_split_chunks", lidar_split_chunks)):
         if len(vals) > AUTOTUNE_MAX:
             raise ValueError(f"at most {AUTOTUNE_MAX} {name}")
         setattr(sp, "n_" + name, len(vals))

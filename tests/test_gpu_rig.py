@@ -260,3 +260,40 @@ def test_split_lists_match_oracle_and_unsplit_render(gpu_lib):
             ok = o["flip"] <= 2e-5
             rgb = np.moveaxis(gg["rgb"], 0, -1)[yy, xx]
             assert np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
+
+
+def test_lidar_split_is_per_sensor(gpu_lib):
+    """The LiDARs' own list split (gsr_sensor.split_*): LiDAR lists split
+    into 64-position chunks while the cameras stay unsplit -- camera frames
+    bit-exact against the unsplit plan, LiDAR frames to the merge rounding;
+    the autotuner's LiDAR split candidates are measured and kept."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    scene, poses, sensors = _small_rig()
+    d = DeviceSurfels.from_host(scene)
+    P = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    outs = ("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk")
+    whole = Renderer(scene.n, sensors, tiles=TILES, outputs=outs, split=(1 << 24, 1 << 24))
+    ref = [{k: v.clone() for k, v in o.items()} for o in whole.render_rig(d, P)]
+    r = Renderer(scene.n, sensors, tiles=TILES, outputs=outs, split=(1 << 24, 1 << 24), lidar_split=(256, 64))
+    assert r.lidar_split() == (256, 64)
+    out = r.render_rig(d, P)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    info = r.region(8, torch.int32).view(-1, 4)
+    for i, s in enumerate(sensors):
+        tb = r.plan.tile_base[i], r.plan.tile_base[i + 1]
+        n_split = int((info[tb[0]:tb[1], 0] > 0).sum())
+        if s.kind == "lidar":
+            assert n_split > 0, i
+            for key in ("intensity", "range"):
+                scale = 1.0 if key == "intensity" else max(1.0, float(ref[i][key].abs().max()))
+                assert (ref[i][key] - out[i][key]).abs().max() <= 1e-5 * scale, (i, key)
+        else:
+            assert n_split == 0, i
+            for key in ref[i]:
+                assert torch.equal(ref[i][key], out[i][key]), (i, key)
+    res = r.autotune([d], P, camera_tiles=(), lidar_tiles=(), batch_depths=(), split_firsts=(), split_chunks=(),
+                     lidar_split_firsts=(512, 2048), lidar_split_chunks=(128,), warmup=1, reps=2)
+    best = min((t for t in res["trials"] if t["ms"] > 0), key=lambda t: t["ms"])
+    assert {t["lidar_split"][0] for t in res["trials"]} >= {512, 2048}
+    assert res["lidar_split"] == best["lidar_split"]

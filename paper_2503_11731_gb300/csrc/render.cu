@@ -24,9 +24,10 @@ namespace gsr {
 constexpr int kIlp = GSR_ILP;  // records evaluated per step of a ray's walk (divides 32)
 
 // Resident CTAs per SM the persistent compositing kernels are compiled for
-// (256 threads each; 4 caps registers at 64 per thread).
+// (256 threads each; 3 caps registers at 80 per thread, which measured
+// faster than 64 with its spills, though fewer CTAs of a tile's threads fit).
 #ifndef GSR_RIG_MIN_CTAS
-#define GSR_RIG_MIN_CTAS 4
+#define GSR_RIG_MIN_CTAS 3
 #endif
 
 // One ray of a tile: its pixel / cell, whether it is inside the sensor, and

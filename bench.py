@@ -470,6 +470,98 @@ def two_scene_frame(args, r, sensors, da, model, d_obj, pose_t, origin, stream):
     return res
 
 
+def streaming_frames(args, stream):
+    """Large-scale streaming: an 8M-surfel SH-3 road scene 400 m long, cut
+    into 40 m zones with 25 % padding and packed in pinned host memory; a
+    1920x1080 camera and a 128x1800 LiDAR drive along it 2 m per frame.
+    The next zone is copied on a second stream while the vehicle is in its
+    padding band and the two device buffers swap when it crosses; the same
+    frames are timed again with every zone already resident."""
+    import torch
+    from paper_2503_11731_gb300 import gsr, synth
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    from paper_2503_11731_gb300.stream import ZoneScene, ZoneStreamer
+    s = synth.driving_scene(n=8_000_000, seed=synth.SEED_BASE + 6, x_range=(-20.0, 380.0), n_boxes=80)
+    zs = ZoneScene(s, gsr.zone_grid(-20.0, -20.0, 40.0, 0.25, 10, 1))
+    del s
+    st = ZoneStreamer(zs)
+    sensors = lambda x: [synth.pinhole(1920, 1080, 1000.0, (x, 0.0, 1.5), 0.0),
+                         synth.spinning_lidar(128, 1800, -25.0, 15.0, (x, 0.0, 1.8))]
+    r = Renderer(st.capacity, sensors(0.0), tiles=[(16, 8), (8, 8)], max_dup=args.max_dup,
+                 outputs=("rgb", "depth", "alpha", "range", "intensity"))
+    xs = np.arange(0.0, 340.0, 2.0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def run(get_zone_table, prefetch):
+        times, copies = [], []
+        for x in xs:
+            z = zs.zone_of(x, 0.0)
+            d = get_zone_table(z)
+            r.move(sensors(x))
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            r.render(d)
+            e1.record(stream)
+            if prefetch:
+                for nz in zs.zones_near(x, 0.0):
+                    if nz != z and nz not in st.resident():
+                        c0, c1 = ev(), ev()
+                        c0.record(st.copy_stream)
+                        st.prefetch(nz)
+                        c1.record(st.copy_stream)
+                        copies.append((c0, c1, zs.size(nz)))
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        check_status(r)
+        return [a.elapsed_time(b) for a, b in times], copies
+
+    def streamed(z):
+        if z not in st.resident():
+            st.prefetch(z)
+        return st.acquire(z)
+
+    run(streamed, True)  # warm-up pass
+    t_stream, copies = run(streamed, True)
+    resident = {}
+    for z in sorted({zs.zone_of(x, 0.0) for x in xs}):
+        d = DeviceSurfels(*(torch.zeros_like(getattr(st.bufs[0], k)) for k in ("pos", "log_scale", "quat")),
+                          torch.full_like(st.bufs[0].opacity, -1e4), torch.zeros_like(st.bufs[0].sh),
+                          torch.zeros_like(st.bufs[0].intensity))
+        n = zs.size(z)
+        for k in ("pos", "log_scale", "quat", "opacity", "sh", "intensity"):
+            getattr(d, k)[:n] = zs.zones[z][k].to("cuda")
+        resident[z] = d
+    t_static, _ = run(lambda z: resident[z], False)
+    cms = [a.elapsed_time(b) for a, b, _ in copies]
+    K = zs.zones[0]["sh"].shape[1]
+    zbytes = lambda n: n * 4 * (3 + 2 + 4 + 1 + 3 * K + 1)
+    zone_bytes = [zbytes(n) for _, _, n in copies]
+    # copies alone (nothing else in flight): the host -> device rate of a swap
+    iso = []
+    for z in (0, 1, 2, 3):
+        if z in st.resident():
+            continue
+        torch.cuda.synchronize()
+        c0, c1 = ev(), ev()
+        c0.record(st.copy_stream)
+        st.prefetch(z)
+        c1.record(st.copy_stream)
+        torch.cuda.synchronize()
+        iso.append((c0.elapsed_time(c1), zbytes(zs.size(z))))
+    st.close()
+    res = {"workload": "8M-surfel SH-3 road scene, 400 m, 40 m zones with 25 % padding (10 zones, largest "
+                       f"{zs.max_zone} surfels); 1920x1080 camera + 128x1800 LiDAR, {len(xs)} frames 2 m apart",
+           "frame_ms_streaming": {"mean": float(np.mean(t_stream)), "max": float(np.max(t_stream))},
+           "frame_ms_resident": {"mean": float(np.mean(t_static)), "max": float(np.max(t_static))},
+           "zone_copies": len(copies),
+           "copy_ms_mean_in_drive": float(np.mean(cms)) if cms else None,
+           "bytes_per_zone_mean": float(np.mean(zone_bytes)) if zone_bytes else None,
+           "copy_ms_alone": [round(t, 3) for t, _ in iso],
+           "h2d_gb_per_s_alone": float(sum(b for _, b in iso) / (sum(t for t, _ in iso) * 1e-3) / 1e9) if iso else None,
+           "note": "in-drive copy times include the wait for the render stream to release the back buffer"}
+    return res
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -656,6 +748,7 @@ def run_gpu(args):
     # ---- backward step of the reconstruction workload (2M surfels, 1920x1080)
     bwd = backward_step(args, stream) if args.backward else None
     cyl = cylindrical_frame(args, stream) if args.cylindrical else None
+    streaming = streaming_frames(args, stream) if args.streaming else None
 
     if rank != 0:
         if world > 1:
@@ -712,6 +805,7 @@ def run_gpu(args):
         "autotune": tuned,
         "backward_step": bwd,
         "cylindrical_frame": cyl,
+        "streaming": streaming,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -741,6 +835,8 @@ def main():
     ap.add_argument("--sample-rays", type=int, default=16)
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the explicit-form and decode-only timings")
+    ap.add_argument("--no-streaming", dest="streaming", action="store_false",
+                    help="skip the zone-streaming drive")
     ap.add_argument("--no-cylindrical", dest="cylindrical", action="store_false",
                     help="skip the cylindrical-camera frame measurement")
     ap.add_argument("--no-backward", dest="backward", action="store_false",

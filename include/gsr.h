@@ -598,9 +598,85 @@ const char* gsr_last_cuda_error(void);
  * 4 gsr_camera_out, 5 gsr_lidar_out, 6 gsr_tiling, 7 gsr_camera_grad,
  * 8 gsr_surfel_grads, 9 gsr_loss_weights, 10 gsr_anchors, 11 gsr_mlp,
  * 12 gsr_mlp_grads, 13 gsr_surfel_table, 14 gsr_autotune_space,
- * 15 gsr_autotune_result.  Returns 0 for other values.
+ * 15 gsr_autotune_result, 16 gsr_zone_grid, 17 gsr_streamer.  Returns 0 for
+ * other values.
  */
 size_t gsr_struct_size(int32_t which);
+
+/* ------------------------------------------------ large-scale streaming */
+
+/*
+ * Zones of a large scene (Sec. III-A, "Support Large-scale Scenes": frames
+ * are clustered by their XY location into 40 x 40 m zones with 25 % relative
+ * padding, and while rendering two threads double-buffer the zones, swapping
+ * in the Gaussians of the next block as the vehicle moves between blocks).
+ * Zone (i, j), 0 <= i < nx, 0 <= j < ny, id j nx + i, is the square
+ * [x0 + i s, x0 + (i+1) s) x [y0 + j s, y0 + (j+1) s), s = zone_size; its
+ * surfels are those whose centre lies in the square grown by padding x s
+ * on every side (padding in [0, 0.5]: a surfel belongs to up to four
+ * zones).  Bounds are compared in double precision.  Host memory, host only.
+ */
+typedef struct {
+    float x0, y0;
+    float zone_size;
+    float padding;
+    int32_t nx, ny;
+} gsr_zone_grid;
+
+/* Zone whose unpadded square holds (x, y), or -1 outside the grid (or for a bad grid). */
+int32_t gsr_zone_of(const gsr_zone_grid* grid, float x, float y);
+
+/* counts[z] = surfels of zone z (pos: HOST [n][3] world centres). */
+gsr_status gsr_zone_count(const gsr_zone_grid* grid, const float* pos, int64_t n, int64_t* counts);
+
+/* Members in CSR form: offsets [nx ny + 1] = exclusive prefix of the counts,
+ * members[offsets[z] .. offsets[z+1]) = ascending surfel indices of zone z.
+ * GSR_ERR_INVALID_ARG if the offsets do not fit the table's counts. */
+gsr_status gsr_zone_members(const gsr_zone_grid* grid, const float* pos, int64_t n, const int64_t* offsets,
+                            int64_t* members);
+
+/* Gather surfels members[0 .. count) of a HOST table into contiguous HOST
+ * arrays `out` (sized for count; intensity and ray_drop written when `out`
+ * has them: 0 / -1e4 where the table has none).  Zones are packed once, so
+ * a swap is one copy per array. */
+gsr_status gsr_zone_pack(const gsr_surfels* table, const int64_t* members, int64_t count,
+                         const gsr_surfel_table* out);
+
+/*
+ * Double-buffered zone streamer.  The caller allocates the struct and two
+ * DEVICE tables of `capacity` surfels (its SH degree), and owns the copy
+ * stream; the library creates two CUDA events per buffer (released by
+ * gsr_streamer_destroy) and allocates no memory.
+ *   prefetch(zone, host_zone): unless the zone is already in a buffer, copy
+ *     its packed arrays (HOST, pinned for the copy to overlap) into the back
+ *     buffer on the copy stream -- after the render stream has released that
+ *     buffer -- and mark the slots beyond its surfels culled (opacity logit
+ *     -1e4).  GSR_ERR_CAPACITY if the zone is larger than a buffer.
+ *   acquire(zone, render_stream, out): make the zone's buffer the front
+ *     (swapping if it is the back one), make render_stream wait for its
+ *     copy, and describe it in *out (n = capacity; the plan renders
+ *     `capacity` surfels).  GSR_ERR_INVALID_ARG if the zone was never
+ *     prefetched.
+ * Treat every field as read-only.
+ */
+typedef struct {
+    int32_t capacity;
+    int32_t sh_degree;
+    gsr_surfel_table buf[2]; /* DEVICE */
+    int32_t zone[2];         /* zone held by each buffer, -1 = none */
+    int32_t count[2];        /* its surfels */
+    int32_t front;           /* buffer frames draw from */
+    int32_t released_valid[2];
+    void* copy_stream;
+    void* ready[2];          /* cudaEvent_t: the buffer's copy is done */
+    void* released[2];       /* cudaEvent_t: the render stream is done with the buffer */
+} gsr_streamer;
+
+gsr_status gsr_streamer_init(gsr_streamer* s, int32_t capacity, int32_t sh_degree, const gsr_surfel_table* buffers,
+                             void* copy_stream);
+gsr_status gsr_streamer_prefetch(gsr_streamer* s, int32_t zone, const gsr_surfels* host_zone);
+gsr_status gsr_streamer_acquire(gsr_streamer* s, int32_t zone, void* render_stream, gsr_surfels* out);
+gsr_status gsr_streamer_destroy(gsr_streamer* s);
 
 /* ------------------------------------------------- workspace inspection */
 

@@ -363,6 +363,8 @@ extern "C" size_t gsr_struct_size(int32_t which)
     case 13: return sizeof(gsr_surfel_table);
     case 14: return sizeof(gsr_autotune_space);
     case 15: return sizeof(gsr_autotune_result);
+    case 16: return sizeof(gsr_zone_grid);
+    case 17: return sizeof(gsr_streamer);
     default: return 0;
     }
 }

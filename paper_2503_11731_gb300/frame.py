@@ -115,6 +115,27 @@ class Renderer:
         return gsr.CameraOut(g("rgb"), g("depth"), g("normal"), g("alpha"), g("trans"), g("depth_acc"),
                              g("n_contrib"), g("n_walk"))
 
+    def move(self, sensors):
+        """New poses for the plan's sensors (same models, sizes and tiling):
+        the plan is re-initialised on the host, the workspace and outputs stay."""
+        sensors = list(sensors)
+        if len(sensors) != len(self.descs):
+            raise ValueError("move() keeps the plan's sensors")
+        structs = []
+        for i, d in enumerate(sensors):
+            st = gsr.sensor(d)
+            old = self.plan.sensors[i]
+            st.tile_w, st.tile_h = old.tile_w, old.tile_h
+            st.split_first, st.split_chunk = old.split_first, old.split_chunk
+            st.bg = old.bg
+            structs.append(st)
+        t = self.plan.tiling
+        plan = gsr.plan_init(self.plan.n_surfels, structs, (t.tile_w, t.tile_h), self.plan.max_dup, t.batch_depth,
+                             (t.split_first, t.split_chunk))
+        if gsr.workspace_size(plan) != self.ws_bytes:
+            raise ValueError("move() changed the workspace layout")
+        self.plan, self.descs, self.structs = plan, sensors, structs
+
     def preprocess(self, surfels: DeviceSurfels, objects=None, stream=None, first=None):
         """Whole plan (first None), or surfels [first, first + n) of it (gsr_preprocess_part)."""
         obj = None

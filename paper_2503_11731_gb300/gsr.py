@@ -119,12 +119,23 @@ class AutotuneResult(ctypes.Structure):
                 ("tried", AutotuneTrial * (7 * AUTOTUNE_MAX + 1))]
 
 
+class ZoneGrid(ctypes.Structure):
+    _fields_ = [("x0", c_f32), ("y0", c_f32), ("zone_size", c_f32), ("padding", c_f32), ("nx", c_i32),
+                ("ny", c_i32)]
+
+
+class Streamer(ctypes.Structure):
+    _fields_ = [("capacity", c_i32), ("sh_degree", c_i32), ("buf", SurfelTable * 2), ("zone", c_i32 * 2),
+                ("count", c_i32 * 2), ("front", c_i32), ("released_valid", c_i32 * 2), ("copy_stream", c_vp),
+                ("ready", c_vp * 2), ("released", c_vp * 2)]
+
+
 DECODE_BF16_TENSOR, DECODE_F32 = 0, 1
 HEAD_CAMERA, HEAD_LIDAR = 0, 1
 SEES_CAMERAS, SEES_LIDARS = 1, 2
 
 _STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights,
-            Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult]
+            Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult, ZoneGrid, Streamer]
 
 # exported symbols and their ctypes signatures (restype, argtypes)
 SIGNATURES = {
@@ -171,6 +182,14 @@ SIGNATURES = {
                                     ctypes.POINTER(Sensor), ctypes.POINTER(SurfelGrads), ctypes.POINTER(MlpGrads),
                                     c_vp]),
     "gsr_adam": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_f32, c_f32, c_f32, c_f32, c_i32, c_vp]),
+    "gsr_zone_of": (c_i32, [ctypes.POINTER(ZoneGrid), c_f32, c_f32]),
+    "gsr_zone_count": (c_i32, [ctypes.POINTER(ZoneGrid), c_vp, c_i64, c_vp]),
+    "gsr_zone_members": (c_i32, [ctypes.POINTER(ZoneGrid), c_vp, c_i64, c_vp, c_vp]),
+    "gsr_zone_pack": (c_i32, [ctypes.POINTER(Surfels), c_vp, c_i64, ctypes.POINTER(SurfelTable)]),
+    "gsr_streamer_init": (c_i32, [ctypes.POINTER(Streamer), c_i32, c_i32, ctypes.POINTER(SurfelTable), c_vp]),
+    "gsr_streamer_prefetch": (c_i32, [ctypes.POINTER(Streamer), c_i32, ctypes.POINTER(Surfels)]),
+    "gsr_streamer_acquire": (c_i32, [ctypes.POINTER(Streamer), c_i32, c_vp, ctypes.POINTER(Surfels)]),
+    "gsr_streamer_destroy": (c_i32, [ctypes.POINTER(Streamer)]),
     "gsr_loss_noalloc": (c_i32, [ctypes.POINTER(Sensor), ctypes.POINTER(CameraOut), c_vp,
                                  ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
@@ -425,3 +444,52 @@ def decode_backward(anchors: Anchors, mlp: Mlp, origin, cull_camera, d_surfels: 
 def adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, stream):
     _check(lib().gsr_adam(param, grad, m, v, int(n), float(lr), float(beta1), float(beta2), float(eps), int(step),
                           stream), "gsr_adam")
+
+
+# ------------------------------------------------------------ zones
+def zone_grid(x0, y0, zone_size=40.0, padding=0.25, nx=1, ny=1) -> ZoneGrid:
+    return ZoneGrid(float(x0), float(y0), float(zone_size), float(padding), int(nx), int(ny))
+
+
+def zone_of(grid: ZoneGrid, x, y) -> int:
+    return int(lib().gsr_zone_of(ctypes.byref(grid), float(x), float(y)))
+
+
+def zone_members(grid: ZoneGrid, pos):
+    """(offsets [nz+1] int64, members int64) of a host float32 [n, 3] array."""
+    import numpy as np
+    pos = np.ascontiguousarray(pos, np.float32)
+    nz = grid.nx * grid.ny
+    counts = np.zeros(nz, np.int64)
+    p = pos.ctypes.data_as(c_vp)
+    _check(lib().gsr_zone_count(ctypes.byref(grid), p, int(pos.shape[0]), counts.ctypes.data_as(c_vp)),
+           "gsr_zone_count")
+    offsets = np.zeros(nz + 1, np.int64)
+    offsets[1:] = np.cumsum(counts)
+    members = np.zeros(int(offsets[-1]), np.int64)
+    _check(lib().gsr_zone_members(ctypes.byref(grid), p, int(pos.shape[0]), offsets.ctypes.data_as(c_vp),
+                                  members.ctypes.data_as(c_vp)), "gsr_zone_members")
+    return offsets, members
+
+
+def streamer_init(capacity, sh_degree, buffers, copy_stream) -> Streamer:
+    s = Streamer()
+    arr = (SurfelTable * 2)(*buffers)
+    _check(lib().gsr_streamer_init(ctypes.byref(s), int(capacity), int(sh_degree), arr, copy_stream),
+           "gsr_streamer_init")
+    return s
+
+
+def streamer_prefetch(s: Streamer, zone, host_zone: Surfels):
+    _check(lib().gsr_streamer_prefetch(ctypes.byref(s), int(zone), ctypes.byref(host_zone)), "gsr_streamer_prefetch")
+
+
+def streamer_acquire(s: Streamer, zone, render_stream) -> Surfels:
+    out = Surfels()
+    _check(lib().gsr_streamer_acquire(ctypes.byref(s), int(zone), render_stream, ctypes.byref(out)),
+           "gsr_streamer_acquire")
+    return out
+
+
+def streamer_destroy(s: Streamer):
+    _check(lib().gsr_streamer_destroy(ctypes.byref(s)), "gsr_streamer_destroy")

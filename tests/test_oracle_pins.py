@@ -470,3 +470,21 @@ def test_cylinder_centre_column_equals_pinhole_column():
     other = [y * W + 3 for y in range(H)]
     assert np.abs(R.render_pinhole(s, cyl, pixels=other)["alpha"] -
                   R.render_pinhole(s, pin, pixels=other)["alpha"]).max() > 1e-3
+
+
+# ------------------------------------------------------------------- zones
+def test_zone_membership_geometry():
+    """3 x 3 zones of 40 m from the origin with 25 % padding: a zone core
+    point belongs to its zone only, a point in one padding band to two, near
+    a corner to four, beyond the outer padding to none."""
+    from oracle import zones as OZ
+    g = {"x0": 0.0, "y0": 0.0, "zone_size": 40.0, "padding": 0.25, "nx": 3, "ny": 3}
+    pos = np.array([[60.0, 60.0, 0.0],    # core of zone (1, 1) = 4
+                    [41.0, 60.0, 0.0],    # x in zones 0 ([-10, 50)) and 1 ([30, 90))
+                    [45.0, 45.0, 0.0],    # both axes in two zones
+                    [-20.0, 60.0, 0.0],   # x below -10: no zone
+                    [129.9, 5.0, 0.0]])   # x in zone 2 ([70, 130)), y in zone 0
+    m = OZ.members(g, pos)
+    sets = [sorted(z for z in range(9) if k in m[z]) for k in range(len(pos))]
+    assert sets == [[4], [3, 4], [0, 1, 3, 4], [], [2]]
+    assert OZ.zone_of(g, 60.0, 60.0) == 4 and OZ.zone_of(g, 41.0, 60.0) == 4 and OZ.zone_of(g, -1.0, 5.0) == -1

@@ -485,12 +485,31 @@ def streaming_frames(args, stream):
     zs = ZoneScene(s, gsr.zone_grid(-20.0, -20.0, 40.0, 0.25, 10, 1))
     del s
     st = ZoneStreamer(zs)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    K = zs.zones[0]["sh"].shape[1]
+    zbytes = lambda n: n * 4 * (3 + 2 + 4 + 1 + 3 * K + 1)
+
+    def copies_alone(zones):
+        # copies with nothing else in flight: the host -> device rate of a swap
+        out = []
+        for z in zones:
+            if z in st.resident():
+                continue
+            torch.cuda.synchronize()
+            c0, c1 = ev(), ev()
+            c0.record(st.copy_stream)
+            st.prefetch(z)
+            c1.record(st.copy_stream)
+            torch.cuda.synchronize()
+            out.append((c0.elapsed_time(c1), zbytes(zs.size(z))))
+        return out
+
+    iso_before = copies_alone((5, 6))
     sensors = lambda x: [synth.pinhole(1920, 1080, 1000.0, (x, 0.0, 1.5), 0.0),
                          synth.spinning_lidar(128, 1800, -25.0, 15.0, (x, 0.0, 1.8))]
     r = Renderer(st.capacity, sensors(0.0), tiles=[(16, 8), (8, 8)], max_dup=args.max_dup,
                  outputs=("rgb", "depth", "alpha", "range", "intensity"))
     xs = np.arange(0.0, 340.0, 2.0)
-    ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def run(get_zone_table, prefetch):
         times, copies = [], []
@@ -533,21 +552,8 @@ def streaming_frames(args, stream):
         resident[z] = d
     t_static, _ = run(lambda z: resident[z], False)
     cms = [a.elapsed_time(b) for a, b, _ in copies]
-    K = zs.zones[0]["sh"].shape[1]
-    zbytes = lambda n: n * 4 * (3 + 2 + 4 + 1 + 3 * K + 1)
     zone_bytes = [zbytes(n) for _, _, n in copies]
-    # copies alone (nothing else in flight): the host -> device rate of a swap
-    iso = []
-    for z in (0, 1, 2, 3):
-        if z in st.resident():
-            continue
-        torch.cuda.synchronize()
-        c0, c1 = ev(), ev()
-        c0.record(st.copy_stream)
-        st.prefetch(z)
-        c1.record(st.copy_stream)
-        torch.cuda.synchronize()
-        iso.append((c0.elapsed_time(c1), zbytes(zs.size(z))))
+    iso = copies_alone((0, 1, 2, 3))
     st.close()
     res = {"workload": "8M-surfel SH-3 road scene, 400 m, 40 m zones with 25 % padding (10 zones, largest "
                        f"{zs.max_zone} surfels); 1920x1080 camera + 128x1800 LiDAR, {len(xs)} frames 2 m apart",
@@ -556,8 +562,9 @@ def streaming_frames(args, stream):
            "zone_copies": len(copies),
            "copy_ms_mean_in_drive": float(np.mean(cms)) if cms else None,
            "bytes_per_zone_mean": float(np.mean(zone_bytes)) if zone_bytes else None,
-           "copy_ms_alone": [round(t, 3) for t, _ in iso],
-           "h2d_gb_per_s_alone": float(sum(b for _, b in iso) / (sum(t for t, _ in iso) * 1e-3) / 1e9) if iso else None,
+           "copy_ms_alone": [round(t, 3) for t, _ in iso_before + iso],
+           "h2d_gb_per_s_alone_before_drive": float(sum(b for _, b in iso_before) / (sum(t for t, _ in iso_before) * 1e-3) / 1e9) if iso_before else None,
+           "h2d_gb_per_s_alone_after_drive": float(sum(b for _, b in iso) / (sum(t for t, _ in iso) * 1e-3) / 1e9) if iso else None,
            "note": "in-drive copy times include the wait for the render stream to release the back buffer"}
     return res
 

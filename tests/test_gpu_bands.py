@@ -1,6 +1,7 @@
 """GPU check of the pixel partition used for multi-GPU training: a camera
 cut into row bands (band cameras: same rays, cy shifted, height cut)
-renders every band row bit-exactly like the full image, and the gradients
+renders every band row like the full image (bit-exactly for the first
+band; to FP32 rounding of the shifted centre row for the others), and the gradients
 of the band losses (L1 + distortion, each band's share of the image mean)
 sum to the full image's gradient."""
 import numpy as np
@@ -46,7 +47,12 @@ def test_band_renders_and_gradients_sum_to_full_image(gpu_lib):
         y0, y1 = bounds[k], bounds[k + 1]
         bo, bl, bg = grads_of(D.band_camera(cam, y0, y1), y1 - y0)
         for key in ("rgb", "depth", "alpha", "trans", "normal", "depth_acc"):
-            assert torch.equal(bo[key], full_out[key][..., y0:y1, :]), (k, key)
+            a, b = bo[key], full_out[key][..., y0:y1, :]
+            if k == 0:  # same pixel frame: identical arithmetic
+                assert torch.equal(a, b), (k, key)
+            else:  # the centre's row moves by -y0 in FP32: rounding-level differences
+                scale = max(1.0, float(b.abs().max())) if key in ("depth", "depth_acc") else 1.0
+                assert (a - b).abs().max().item() <= 2e-5 * scale, (k, key)
         loss_sum += bl
         for key in g_sum:
             g_sum[key] += bg[key]

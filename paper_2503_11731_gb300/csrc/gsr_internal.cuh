@@ -359,6 +359,39 @@ __device__ __forceinline__ bool footprint_hits(const Footprint& f, float x0, flo
     return fp_edge_x(f, ly, lx, hx) <= 0.f || fp_edge_x(f, hy, lx, hx) <= 0.f;
 }
 
+// The same question for culling inside the compositing walk, in fast FP32
+// (fused operations, approximate reciprocals): the one-pixel margin is far
+// larger than their error, so a record it rejects cannot reach a pixel
+// centre of the box.  Box = pixels [x0, x1] x [y0, y1] (inclusive).
+__device__ __forceinline__ bool footprint_meets_box(const float4 r0, const float4 r1, const float4 r2, float o,
+                                                    float x0, float x1, float y0, float y1)
+{
+    const float rho = fminf(kSupport, 2.f * __logf(255.f * o) + 1e-3f);
+    const float a0 = r0.x, a1 = r0.y, b0 = r1.x, b1 = r1.y, c0 = r2.x, c1 = r2.y, c2 = r2.z;
+    const float m00 = a0 * a0 + b0 * b0 - rho * c0 * c0;
+    const float m01 = a0 * a1 + b0 * b1 - rho * c0 * c1;
+    const float m11 = a1 * a1 + b1 * b1 - rho * c1 * c1;
+    const float n0 = -rho * c2 * c0, n1 = -rho * c2 * c1, k = -rho * c2 * c2;
+    // pixel centres x + 1/2 of the box, widened by one pixel, relative to the centre
+    const float lx = x0 - 0.5f - r0.w, hx = x1 + 1.5f - r0.w;
+    const float ly = y0 - 0.5f - r1.w, hy = y1 + 1.5f - r1.w;
+    const float ex = fminf(fmaxf(0.f, lx), hx), ey = fminf(fmaxf(0.f, ly), hy);
+    const float r = sqrtf(fmaxf(0.5f * rho, 0.f)) + 1.f;
+    if (ex * ex + ey * ey <= r * r) return true;  // the low-pass disc
+    const float dm = m00 * m11 - m01 * m01;
+    if (!(m00 > 0.f && m11 > 0.f && dm > 1e-4f * m00 * m11)) return true;  // no usable conic
+    auto E = [&](float dx, float dy) {
+        return dx * (m00 * dx + m01 * dy + 2.f * n0) + dy * (m01 * dx + m11 * dy + 2.f * n1) + k;
+    };
+    const float id = __fdividef(1.f, dm);
+    const float sx = (m01 * n1 - m11 * n0) * id, sy = (m01 * n0 - m00 * n1) * id;
+    if (sx >= lx && sx <= hx && sy >= ly && sy <= hy) return E(sx, sy) <= 0.f;
+    const float i00 = __fdividef(1.f, m00), i11 = __fdividef(1.f, m11);
+    const float ty0 = fminf(fmaxf(-(m01 * lx + n1) * i11, ly), hy), ty1 = fminf(fmaxf(-(m01 * hx + n1) * i11, ly), hy);
+    const float tx0 = fminf(fmaxf(-(m01 * ly + n0) * i00, lx), hx), tx1 = fminf(fmaxf(-(m01 * hy + n0) * i00, lx), hx);
+    return E(lx, ty0) <= 0.f || E(hx, ty1) <= 0.f || E(tx0, ly) <= 0.f || E(tx1, hy) <= 0.f;
+}
+
 // Bit 15 of rect.w marks a camera slot whose tile set is footprint-tested.
 constexpr uint16_t kRectExact = 0x8000;
 

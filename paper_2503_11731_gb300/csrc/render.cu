@@ -121,7 +121,13 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                 // one lane per record: does its support box meet any ray of
                 // this warp?  Records that do not are skipped by the warp.
                 const int jt = g0 + lane;
-                const bool meet = jt < cnt && box_meets<KIND>(B[jt * kRecordF4 + 5], wbox, columns);
+                bool meet = jt < cnt && box_meets<KIND>(B[jt * kRecordF4 + 5], wbox, columns);
+                if (KIND == GSR_SENSOR_PINHOLE && meet) {
+                    // and the footprint itself (support conic and low-pass
+                    // disc, one pixel of margin) meets the box
+                    const float4* Rj = B + jt * kRecordF4;
+                    meet = footprint_meets_box(Rj[0], Rj[1], Rj[2], Rj[3].x, wbox.x, wbox.y, wbox.z, wbox.w);
+                }
                 uint32_t mask = __ballot_sync(0xffffffffu, meet);
                 while (mask) {
                     if (__all_sync(0xffffffffu, s.done)) break;

@@ -395,10 +395,13 @@ __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* __restrict__
 // [P g / G, P (g + 1) / G) of the P kept.  A CTA takes its slots 256 at a
 // time and lists their tile rows, kDupRowsRound at a time: one thread per
 // row finds the row's span, a block scan gives every row its first pair,
-// and each warp then writes 256 consecutive pairs at a time, lane l the
-// pairs l, l + 32, ... (coalesced stores), walking the rows.  The cost per
+// and each warp then takes 128 consecutive pairs at a time, lane l walking
+// the four pairs 4 l .. 4 l + 3 through the rows, and writes them out from
+// shared memory in pair order (coalesced stores).  The cost per
 // pair no longer depends on how the pairs fall into slots and rows.
-constexpr int kDupRowsRound = 1024;
+constexpr int kDupRowsRound = 512;
+constexpr int kPairsPerLane = 4;   // pairs a lane walks per warp chunk
+constexpr int kStageStride = 40;  // = 8 mod 32: conflict-free staging both ways
 constexpr int kDupCtasPerSortCta = 8;
 constexpr int kDupRowsPerThread = kDupRowsRound / 256;
 
@@ -422,6 +425,10 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
     __shared__ uint32_t r_key0[kDupRowsRound];     // tile id of column 0 of the row
     __shared__ uint16_t r_t0[kDupRowsRound], r_len[kDupRowsRound], r_lim[kDupRowsRound], r_tx[kDupRowsRound];
     __shared__ uint8_t r_slot[kDupRowsRound];
+    // per warp: 32 kPairsPerLane staged pairs, [pair % kPairsPerLane][pair /
+    // kPairsPerLane] with a row stride of kStageStride words
+    __shared__ uint32_t st_key[8][kPairsPerLane * kStageStride], st_val[8][kPairsPerLane * kStageStride],
+        st_q[8][kPairsPerLane * kStageStride];
     __shared__ uint32_t scan_s[9];
     __shared__ uint32_t rb_s, re_s;
     const uint32_t n_vis = counters[C_NVIS];
@@ -544,35 +551,63 @@ __global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfel
                 }
             }
             __syncthreads();
-            // 4. the round's pairs: warp chunks of 256, lane l the pairs l, l + 32, ...
-            for (uint32_t w0 = (uint32_t)warp * 256u; w0 < tot; w0 += 8u * 256u) {
-                uint32_t p = w0 + lane;
-                if (p >= tot) continue;
-                int lo = 0, hi = (int)nr;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (r_pre[mid] <= p) lo = mid;
-                    else hi = mid;
-                }
-                int rl = lo;
-                uint32_t col = p - r_pre[rl];
-#pragma unroll 1
-                for (int e = 0; e < 8 && p < tot; ++e) {
-                    while (col >= r_len[rl] && rl + 1 < (int)nr) {
-                        col -= r_len[rl];
-                        ++rl;
+            // 4. the round's pairs: warp chunks of 32 kPairsPerLane, lane l
+            // the consecutive pairs kPairsPerLane l .. + kPairsPerLane - 1 (a
+            // row changes at most a few times), staged in the warp's buffer
+            // and written out in pair order (consecutive lanes, consecutive
+            // addresses)
+            uint32_t* sk = st_key[warp];
+            uint32_t* sv = st_val[warp];
+            uint32_t* sq = st_q[warp];
+            constexpr uint32_t kChunk = 32u * kPairsPerLane;
+            for (uint32_t w0 = (uint32_t)warp * kChunk; w0 < tot; w0 += 8u * kChunk) {
+                const uint32_t pa = w0 + (uint32_t)(kPairsPerLane * lane);
+                int rl = 0;
+                uint32_t col = 0;
+                if (pa < tot) {
+                    int lo = 0, hi = (int)nr;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (r_pre[mid] <= pa) lo = mid;
+                        else hi = mid;
                     }
-                    if (col < r_lim[rl]) {
-                        const uint32_t q = r_q0[rl] + col;
-                        if (q >= p0 && q < p1) {
-                            const uint32_t tx = r_t0[rl] + col, nx = r_tx[rl];
-                            pkey[q] = r_key0[rl] + (tx < nx ? tx : tx - nx);  // LiDAR azimuth wrap
-                            pval[q] = s_slot[r_slot[rl]];
+                    rl = lo;
+                    col = pa - r_pre[rl];
+                }
+#pragma unroll
+                for (int e = 0; e < kPairsPerLane; ++e) {
+                    uint32_t q = 0xffffffffu, key = 0u, val = 0u;
+                    if (pa + (uint32_t)e < tot) {
+                        while (col >= r_len[rl] && rl + 1 < (int)nr) {
+                            col -= r_len[rl];
+                            ++rl;
                         }
+                        if (col < r_lim[rl]) {
+                            const uint32_t qq = r_q0[rl] + col;
+                            if (qq >= p0 && qq < p1) {
+                                const uint32_t tx = r_t0[rl] + col, nx = r_tx[rl];
+                                q = qq;
+                                key = r_key0[rl] + (tx < nx ? tx : tx - nx);  // LiDAR azimuth wrap
+                                val = s_slot[r_slot[rl]];
+                            }
+                        }
+                        ++col;
                     }
-                    p += 32u;
-                    col += 32u;
+                    sk[e * kStageStride + lane] = key;
+                    sv[e * kStageStride + lane] = val;
+                    sq[e * kStageStride + lane] = q;
                 }
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < kPairsPerLane; ++i) {
+                    const int m = i * 32 + lane, at = (m % kPairsPerLane) * kStageStride + m / kPairsPerLane;
+                    const uint32_t q = sq[at];
+                    if (q != 0xffffffffu) {
+                        pkey[q] = sk[at];
+                        pval[q] = sv[at];
+                    }
+                }
+                __syncwarp();
             }
             carry += tot;
             __syncthreads();

@@ -80,7 +80,7 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
     const int nb = n > 0 ? (n + D - 1) / D : 0;
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
-    const float4 wbox = warp_box(ray, s.done);
+    float4 wbox = warp_box(ray, s.done);
 
     // batch b is the CTA's batch g = gb + b: buffer and barrier g & 1, phase
     // parity (g >> 1) & 1
@@ -116,6 +116,8 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
         const int cnt = min(D, n - b * D);
         const int pos0 = lo + b * D;  // list position of the batch's first record
         if (ok) {
+            // the box of the rays still walking shrinks as rays saturate
+            if (b > 0) wbox = warp_box(ray, s.done);
             for (int g0 = 0; g0 < cnt; g0 += 32) {
                 if (__all_sync(0xffffffffu, s.done)) break;
                 // one lane per record: does its support box meet any ray of

@@ -367,8 +367,12 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
         for (int g1 = hi; g1 > lo && ok; g1 -= 32) {
             const int g0 = max(lo, g1 - 32);
             const int jt = g0 + lane;
-            const bool meet = jt < g1 && box_meets<KIND>(Bf[(jt - lo) * kRecordF4 + 5], wbox, columns) &&
-                              (uint32_t)jt < wlast;
+            bool meet = jt < g1 && box_meets<KIND>(Bf[(jt - lo) * kRecordF4 + 5], wbox, columns) &&
+                        (uint32_t)jt < wlast;
+            if (KIND == GSR_SENSOR_PINHOLE && meet) {  // and the footprint itself meets the box
+                const float4* Rt = Bf + (jt - lo) * kRecordF4;
+                meet = footprint_meets_box(Rt[0], Rt[1], Rt[2], Rt[3].x, wbox.x, wbox.y, wbox.z, wbox.w);
+            }
             uint32_t mask = __ballot_sync(0xffffffffu, meet);
             while (mask) {
                 const int bit = 31 - __clz(mask);  // the highest position first

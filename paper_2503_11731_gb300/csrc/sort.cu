@@ -680,11 +680,30 @@ __global__ void __launch_bounds__(256) k_tile_keys(const uint2* __restrict__ ran
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ key,
                                                      const uint32_t* __restrict__ n_ptr, uint2* __restrict__ ranges)
 {
+    // four consecutive keys per step (one 16-byte load; the region is
+    // 256-byte aligned), their neighbours from plain loads
     const uint32_t n = *n_ptr;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t t = key[i];
-        if (i == 0 || key[i - 1] != t) ranges[t].x = i;
-        if (i + 1 == n || key[i + 1] != t) ranges[t].y = i + 1;
+    const uint32_t n4 = (n + 3) / 4;
+    const uint4* key4 = reinterpret_cast<const uint4*>(key);
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n4; v += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * v;
+        uint32_t k[6];
+        k[0] = i0 > 0 ? __ldg(key + i0 - 1) : 0xffffffffu;
+        if (i0 + 4 <= n) {
+            const uint4 q = __ldg(key4 + v);
+            k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
+        } else {
+            for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? __ldg(key + i0 + j) : 0xffffffffu;
+        }
+        k[5] = i0 + 4 < n ? __ldg(key + i0 + 4) : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t i = i0 + j;
+            if (i >= n) break;
+            const uint32_t t = k[1 + j];
+            if (i == 0 || k[j] != t) ranges[t].x = i;
+            if (i + 1 == n || k[2 + j] != t) ranges[t].y = i + 1;
+        }
     }
 }
 

@@ -64,6 +64,27 @@ __device__ __forceinline__ void chunk_of(uint64_t n, int cta, int G, uint64_t& b
 }  // namespace
 
 // ------------------------------------------------------------------ compaction
+// Visible slots (count > 0), in slot order.  A CTA owns a contiguous chunk
+// of slots (a multiple of 32, so its loads are 16-byte aligned) and walks
+// it 2048 slots at a time, eight consecutive slots per thread (two 16-byte
+// loads of the counts), with one block scan per step.
+constexpr int kCompactPer = 8;
+
+__device__ __forceinline__ uint32_t compact_flags(const uint32_t* __restrict__ counts, uint64_t i, uint64_t e)
+{
+    uint32_t f = 0;
+    if (i + kCompactPer <= e) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(counts + i));
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(counts + i + 4));
+        f = (a.x > 0) | (a.y > 0) << 1 | (a.z > 0) << 2 | (a.w > 0) << 3 | (b.x > 0) << 4 | (b.y > 0) << 5 |
+            (b.z > 0) << 6 | (b.w > 0) << 7;
+    } else {
+        for (int k = 0; k < kCompactPer; ++k)
+            if (i + k < e && __ldg(counts + i + k) > 0) f |= 1u << k;
+    }
+    return f;
+}
+
 __global__ void __launch_bounds__(256) k_compact_count(const uint32_t* __restrict__ counts, uint64_t n_slots,
                                                        uint32_t* __restrict__ partial)
 {
@@ -71,7 +92,8 @@ __global__ void __launch_bounds__(256) k_compact_count(const uint32_t* __restric
     uint64_t b, e;
     chunk_of(n_slots, blockIdx.x, gridDim.x, b, e);
     uint32_t c = 0;
-    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) c += counts[i] > 0;
+    for (uint64_t i = b + (uint64_t)threadIdx.x * kCompactPer; i < e; i += (uint64_t)blockDim.x * kCompactPer)
+        c += __popc(compact_flags(counts, i, e));
     uint32_t tot;
     block_exclusive_scan<uint32_t, 256>(c, tot, sm);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
@@ -114,14 +136,17 @@ __global__ void __launch_bounds__(256) k_compact_write(const uint32_t* __restric
     uint64_t b, e;
     chunk_of(n_slots, blockIdx.x, gridDim.x, b, e);
     uint32_t base = partial[blockIdx.x];
-    for (uint64_t t0 = b; t0 < e; t0 += blockDim.x) {
-        const uint64_t i = t0 + threadIdx.x;
-        const uint32_t f = (i < e && counts[i] > 0) ? 1u : 0u;
+    for (uint64_t t0 = b; t0 < e; t0 += (uint64_t)blockDim.x * kCompactPer) {
+        const uint64_t i = t0 + (uint64_t)threadIdx.x * kCompactPer;
+        uint32_t f = i < e ? compact_flags(counts, i, e) : 0u;
         uint32_t tot;
-        const uint32_t r = block_exclusive_scan<uint32_t, 256>(f, tot, sm);
-        if (f) {
-            vis_key[base + r] = depthkey[i];
-            vis_val[base + r] = (uint32_t)i;
+        uint32_t r = base + block_exclusive_scan<uint32_t, 256>(__popc(f), tot, sm);
+        while (f) {
+            const int k = __ffs(f) - 1;
+            f &= f - 1u;
+            vis_key[r] = __ldg(depthkey + i + k);
+            vis_val[r] = (uint32_t)(i + k);
+            ++r;
         }
         base += tot;
     }

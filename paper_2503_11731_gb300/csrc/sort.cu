@@ -386,16 +386,28 @@ __global__ void __launch_bounds__(256) k_dup_offsets(const uint32_t* __restrict_
                                                      const unsigned long long* __restrict__ partial, uint64_t cap,
                                                      uint32_t* __restrict__ offs)
 {
+    // eight consecutive slots per thread, one block scan per 2048 slots
+    constexpr int kPer = 8;
     __shared__ unsigned long long sm[9];
     uint64_t b, e;
     chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
     unsigned long long base = partial[blockIdx.x];
-    for (uint64_t t0 = b; t0 < e; t0 += blockDim.x) {
-        const uint64_t i = t0 + threadIdx.x;
-        const unsigned long long c = i < e ? cnt_sorted[i] : 0ull;
+    for (uint64_t t0 = b; t0 < e; t0 += (uint64_t)blockDim.x * kPer) {
+        const uint64_t i = t0 + (uint64_t)threadIdx.x * kPer;
+        uint32_t c[kPer];
+        unsigned long long s = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            c[k] = i + k < e ? cnt_sorted[i + k] : 0u;
+            s += c[k];
+        }
         unsigned long long tot;
-        const unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(c, tot, sm);
-        if (i < e) offs[i] = (uint32_t)(off < cap ? off : cap);
+        unsigned long long off = base + block_exclusive_scan<unsigned long long, 256>(s, tot, sm);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (i + k < e) offs[i + k] = (uint32_t)(off < cap ? off : cap);
+            off += c[k];
+        }
         base += tot;
     }
 }

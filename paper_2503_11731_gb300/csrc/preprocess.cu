@@ -6,8 +6,9 @@
 // Eq. 2 (the adjugate Q of the ray-space matrix, see gsr_internal.cuh), the
 // 3-sigma screen bound of the surfel united with the low-pass disc of the
 // 2DGS fallback, the tile rectangle and count, the SH colour and the normal.
-// One thread per slot; grid.y = sensor.  HBM-bound: 40 B of geometry per
-// surfel and sensor, + the SH coefficients of visible camera slots.
+// One thread per slot; the sensors of a surfel block are adjacent in the
+// grid.  HBM-bound: 40 B of geometry per surfel and sensor, + the SH
+// coefficients of visible camera slots.
 #include "gsr_internal.cuh"
 
 namespace gsr {
@@ -138,7 +139,7 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 // so several tables (e.g. a decoded background and posed objects) can share
 // one plan.  Composite ties break by plan index, as in a single table.  One
 // instantiation per sensor model keeps each one's registers to its own
-// bound; grid.y walks the plan's sensors of that model (ids).
+// bound; the grid walks the plan's sensors of that model (ids) fastest.
 template <int KIND>
 __global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorIds ids, gsr_surfels S,
                                                     const float* __restrict__ poses, int n_obj,
@@ -146,8 +147,10 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorId
                                                     uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,
                                                     uint4* __restrict__ spans, int first, int n_plan)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int si = ids.id[blockIdx.y];
+    // the sensors of a surfel block run back to back (sensor fastest), so
+    // the block's surfel data is read from DRAM once and from L2 after
+    const int i = (int)(blockIdx.x / (unsigned)ids.n) * blockDim.x + threadIdx.x;
+    const int si = ids.id[blockIdx.x % (unsigned)ids.n];
     if (i >= S.n) return;
     const SensorDev& sd = tab.s[si];
     const size_t slot = (size_t)si * n_plan + first + i;
@@ -600,7 +603,7 @@ cudaError_t launch_preprocess(const SensorTable& tab, const gsr_surfels& S, cons
             }
         }
         if (ids.n == 0) continue;
-        const dim3 grid((S.n + 255) / 256, ids.n);
+        const dim3 grid((unsigned)(((S.n + 255) / 256) * ids.n));
         if (kind == GSR_SENSOR_PINHOLE)
             k_preprocess<GSR_SENSOR_PINHOLE><<<grid, 256, 0, st>>>(tab, ids, S, poses, n_obj, rec, rects, counts,
                                                                    keys, spans, first, n_plan);

@@ -181,6 +181,96 @@ def render_pinhole(p, cam, bg=(0.0, 0.0, 0.0)):
             "n_contrib": contrib.sum(1).reshape(shp)}
 
 
+def render_lidar(p, lid):
+    """Brute-force FP64 LiDAR range image (Eq. 5), the torch twin of the C
+    oracle's LiDAR render for gradients.
+
+    p: dict of tensors pos [N,3], log_scale [N,2], quat [N,4], opacity [N]
+    (logit), intensity [N], optional ray_drop [N] (logit).  Ray (row i,
+    column j): elevation el_max - i d_el, azimuth az0 + (j + 1/2) d_az;
+    planes h_u = (sin az, -cos az, 0, 0), h_v = (sin el cos az, sin el sin az,
+    -cos el, 0); the intersection's distance along the unit ray is its
+    range (rejected at or below near); the low-pass disc lives in cell units
+    around the centre's (column, row) with the azimuth wrapped; the order key
+    is the centre's range.  Returns A, B, D (sums of w, w t, w t^2), I (sum
+    w r), drop (sum w rho + T), T, each [beams, columns].
+    """
+    beams, cols = lid.beams, lid.columns
+    w2l = torch.tensor(lid.world_to_sensor, dtype=DT)
+    Rs, ts = w2l[:3, :3], w2l[:3, 3]
+    R = _quat_to_rot(p["quat"])
+    s = torch.exp(p["log_scale"])
+    mu = p["pos"]
+    N = mu.shape[0]
+    H = torch.zeros(N, 4, 3, dtype=DT)
+    H[:, :3, 0] = s[:, 0:1] * R[:, :, 0]
+    H[:, :3, 1] = s[:, 1:2] * R[:, :, 1]
+    H[:, :3, 2] = mu
+    H[:, 3, 2] = 1.0
+    Rt = torch.eye(4, dtype=DT)
+    Rt[:3, :] = w2l[:3, :]
+    WH = Rt @ H  # W = [R|t] for the LiDAR
+    ms = mu @ Rs.T + ts
+    key = ms.norm(dim=-1)
+    keep = key > lid.near
+    idx = torch.nonzero(keep).flatten()
+    order = idx[torch.sort(key[idx].detach(), stable=True).indices]
+    WH, key, ms_o = WH[order], key[order], ms[order]
+    o = torch.sigmoid(p["opacity"][order])
+    r_int = p["intensity"][order]
+    rho_d = torch.sigmoid(p["ray_drop"][order]) if p.get("ray_drop") is not None else torch.zeros_like(r_int)
+    d_el = math.radians(lid.el_max_deg - lid.el_min_deg) / (beams - 1)
+    d_az = 2 * math.pi / cols
+    el_max, az0 = math.radians(lid.el_max_deg), math.radians(lid.az0_deg)
+    az_c = torch.atan2(ms_o[:, 1], ms_o[:, 0])
+    el_c = torch.atan2(ms_o[:, 2], torch.sqrt(ms_o[:, 0] ** 2 + ms_o[:, 1] ** 2))
+    daz = torch.remainder(az_c - az0, 2 * math.pi)
+    ccol = daz / d_az - 0.5
+    crow = (el_max - el_c) / d_el
+    ii, jj = torch.meshgrid(torch.arange(beams, dtype=DT), torch.arange(cols, dtype=DT), indexing="ij")
+    el = (el_max - ii * d_el).reshape(-1, 1)
+    az = (az0 + (jj + 0.5) * d_az).reshape(-1, 1)
+    hu = torch.stack([torch.sin(az), -torch.cos(az), torch.zeros_like(az), torch.zeros_like(az)], -1)
+    hv = torch.stack([torch.sin(el) * torch.cos(az), torch.sin(el) * torch.sin(az), -torch.cos(el),
+                      torch.zeros_like(az)], -1)
+    d = torch.stack([torch.cos(el) * torch.cos(az), torch.cos(el) * torch.sin(az), torch.sin(el)], -1)  # [P,1,3]
+    k = (hu[:, :, :, None] * WH[None]).sum(2)  # [P,n,3]
+    l = (hv[:, :, :, None] * WH[None]).sum(2)
+    m = torch.cross(k, l, dim=-1)
+    has = m[..., 2] != 0
+    m2 = torch.where(has, m[..., 2], torch.ones_like(m[..., 2]))
+    u = m[..., 0] / m2
+    v = m[..., 1] / m2
+    x3 = WH[None, :, :3, 0] * u[..., None] + WH[None, :, :3, 1] * v[..., None] + WH[None, :, :3, 2]
+    t = (x3 * d).sum(-1)
+    rho3 = u * u + v * v
+    v3 = has & (t > lid.near) & (rho3 <= 9.0)
+    dx = jj.reshape(-1, 1) - ccol[None, :]
+    dx = torch.remainder(dx + 0.5 * cols, cols) - 0.5 * cols  # the azimuth wraps
+    dy = ii.reshape(-1, 1) - crow[None, :]
+    rholp = (dx * dx + dy * dy) / 0.5
+    vlp = rholp <= 9.0
+    use3 = v3 & (~vlp | (rho3 <= rholp))
+    valid = v3 | vlp
+    rho = torch.where(use3, rho3, torch.where(vlp, rholp, torch.full_like(rholp, 100.0)))
+    G = torch.exp(-0.5 * rho)
+    a = torch.clamp(o[None, :] * G, max=0.99)
+    a = torch.where(valid, a, torch.zeros_like(a))
+    z = torch.where(use3, t, key[None, :].expand_as(t))
+    skip = a < (1.0 / 255.0)
+    a_eff = torch.where(skip, torch.zeros_like(a), a)
+    one_m = 1.0 - a_eff
+    Tb = torch.cumprod(torch.cat([torch.ones_like(one_m[:, :1]), one_m[:, :-1]], 1), 1)
+    stop = (~skip) & (Tb.detach() * (1.0 - a.detach()) < 1e-4)
+    stopped = torch.cumsum(stop.to(torch.int64), 1) > 0
+    contrib = (~skip) & (~stopped)
+    wgt = torch.where(contrib, a_eff * Tb, torch.zeros_like(a))
+    Tfin = torch.prod(torch.where(contrib, 1.0 - a_eff, torch.ones_like(a)), 1)
+    shp = (beams, cols)
+    return {"A": wgt.sum(1).reshape(shp), "B": (wgt * z).sum(1).reshape(shp), "D": (wgt * z * z).sum(1).reshape(shp),
+            "I": (wgt @ r_int).reshape(shp), "drop": (wgt @ rho_d + Tfin).reshape(shp), "T": Tfin.reshape(shp)}
+
+
 def loss(out, target_rgb, cam, w_dist=0.1, w_norm=0.05, mask_alpha=0.5):
     """Reconstruction loss of the backward step (see module docstring)."""
     rgb, A, B, D, Nr = out["rgb"], out["A"], out["B"], out["D"], out["normal"]

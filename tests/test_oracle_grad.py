@@ -109,3 +109,50 @@ def test_depth_normal_of_a_tilted_plane():
     out["normal"] = -out["normal"]
     _, parts = OG.loss(out, torch.zeros(16, 24, 3, dtype=torch.float64), cam)
     assert float(parts["normal"]) == pytest.approx(2.0 * 14 * 22 / (16 * 24), rel=1e-12)
+
+
+def _lidar_scene(seed):
+    s = synth.driving_scene(n=300, seed=seed, x_range=(-8.0, 8.0), n_boxes=1)
+    rng = np.random.default_rng(seed + 7)
+    f = lambda a: np.asarray(a, np.float64)
+    return synth.Surfels(f(s.pos), f(s.log_scale) + 0.3, f(s.quat), f(s.opacity), f(s.sh), f(s.intensity),
+                         ray_drop=rng.normal(0, 1, s.n))
+
+
+def _c_lidar(s, lid):
+    o = R.render_lidar(s, lid)
+    return {"A": o["alpha"], "B": o["range"] * o["alpha"], "I": o["intensity"], "drop": o["drop"], "T": o["T"]}
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_lidar_render_vjp_matches_fd_of_c_oracle(seed):
+    """Eq. 5 LiDAR render: <d(sum r.out)/dp, v> by autograd == central FD of
+    the C oracle along v, for alpha, sum w t, intensity, ray drop and T."""
+    s = _lidar_scene(seed)
+    lid = synth.spinning_lidar(10, 72, -25.0, 10.0, (0.0, 0.0, 1.8))
+    rng = np.random.default_rng(seed + 200)
+    outs = _c_lidar(s, lid)
+    assert (outs["A"] > 0.5).mean() > 0.1  # the scene covers part of the scan
+    weights = {k: rng.normal(size=v.shape) for k, v in outs.items()}
+    weights["B"] *= 0.05
+    names = ("pos", "log_scale", "quat", "opacity", "intensity", "ray_drop")
+    p = {k: torch.tensor(getattr(s, k), requires_grad=True) for k in names}
+    t = OG.render_lidar(p, lid)
+    tot = sum((torch.as_tensor(weights[k]) * t[k]).sum() for k in weights)
+    tot.backward()
+    h = 1e-6
+    for name in names:
+        v = rng.normal(size=getattr(s, name).shape)
+        base = getattr(s, name)
+        fp = _c_lidar(_with_lidar(s, name, base + h * v), lid)
+        fm = _c_lidar(_with_lidar(s, name, base - h * v), lid)
+        fd = sum(((weights[k] * (fp[k] - fm[k])).sum() for k in weights)) / (2 * h)
+        ad = float((p[name].grad.numpy() * v).sum())
+        assert ad == pytest.approx(fd, rel=2e-5, abs=1e-6), name
+
+
+def _with_lidar(s, name, arr):
+    d = dict(pos=s.pos, log_scale=s.log_scale, quat=s.quat, opacity=s.opacity, sh=s.sh, intensity=s.intensity,
+             ray_drop=s.ray_drop)
+    d[name] = arr
+    return synth.Surfels(**d)

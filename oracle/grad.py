@@ -271,6 +271,28 @@ def render_lidar(p, lid):
             "I": (wgt @ r_int).reshape(shp), "drop": (wgt @ rho_d + Tfin).reshape(shp), "T": Tfin.reshape(shp)}
 
 
+def lidar_loss(out, target_range, target_int, w_range=1.0, w_int=1.0, w_drop=0.1, eps=1e-6):
+    """LiDAR loss on the outputs of render_lidar (the paper states none; this
+    is the reading the library's LiDAR loss takes): over the rays whose
+    target has a return (target range > 0), the mean L1 error of the range
+    B/A (0 where A = 0) and of the intensity; over all rays, the mean binary
+    cross-entropy of the ray-drop probability (clamped to [eps, 1 - eps])
+    against "no return".  Returns (L, range term, intensity term, drop term)."""
+    A, B = out["A"], out["B"]
+    tr, ti = torch.as_tensor(target_range, dtype=DT), torch.as_tensor(target_int, dtype=DT)
+    ret = tr > 0
+    n_ret = int(ret.sum())
+    rng = torch.where(A > 0, B / torch.where(A > 0, A, torch.ones_like(A)), torch.zeros_like(A))
+    zero = torch.zeros((), dtype=DT)
+    lr = w_range * (rng - tr).abs()[ret].sum() / n_ret if n_ret else zero
+    li = w_int * (out["I"] - ti).abs()[ret].sum() / n_ret if n_ret else zero
+    p = torch.clamp(out["drop"], eps, 1.0 - eps)
+    y = (~ret).to(DT)
+    bce = -(y * torch.log(p) + (1.0 - y) * torch.log(1.0 - p))
+    ld = w_drop * bce.mean()
+    return lr + li + ld, lr, li, ld
+
+
 def loss(out, target_rgb, cam, w_dist=0.1, w_norm=0.05, mask_alpha=0.5):
     """Reconstruction loss of the backward step (see module docstring)."""
     rgb, A, B, D, Nr = out["rgb"], out["A"], out["B"], out["D"], out["normal"]

@@ -156,3 +156,24 @@ def _with_lidar(s, name, arr):
              ray_drop=s.ray_drop)
     d[name] = arr
     return synth.Surfels(**d)
+
+
+def test_lidar_loss_worked_example():
+    """Three rays, values worked by hand: ray 0 returns at 10 m (rendered
+    range 12/1.2 = 10, intensity 0.5 vs 0.3); ray 1 returns at 20 m
+    (rendered 18, intensity 0.1 vs 0.2); ray 2 has no return (drop 0.8)."""
+    A = torch.tensor([1.2, 0.9, 0.2], dtype=torch.float64)
+    out = {"A": A, "B": torch.tensor([12.0, 0.9 * 18.0, 0.5], dtype=torch.float64),
+           "I": torch.tensor([0.5, 0.1, 0.0], dtype=torch.float64),
+           "drop": torch.tensor([0.1, 0.3, 0.8], dtype=torch.float64)}
+    L, lr, li, ld = OG.lidar_loss(out, [10.0, 20.0, 0.0], [0.3, 0.2, 0.0], w_range=1.0, w_int=2.0, w_drop=0.5)
+    assert float(lr) == pytest.approx((0.0 + 2.0) / 2)
+    assert float(li) == pytest.approx(2.0 * (0.2 + 0.1) / 2)
+    assert float(ld) == pytest.approx(0.5 * (-math.log(0.9) - math.log(0.7) - math.log(0.8)) / 3)
+    assert float(L) == pytest.approx(float(lr + li + ld))
+    # no returns at all: only the drop term, and a sure drop costs ~0
+    L0, lr0, li0, ld0 = OG.lidar_loss({k: v[2:] for k, v in out.items()}, [0.0], [0.0])
+    assert float(lr0) == 0.0 and float(li0) == 0.0 and float(ld0) == pytest.approx(-0.1 * math.log(0.8))
+    one = {"A": torch.zeros(1, dtype=torch.float64), "B": torch.zeros(1, dtype=torch.float64),
+           "I": torch.zeros(1, dtype=torch.float64), "drop": torch.ones(1, dtype=torch.float64)}
+    assert float(OG.lidar_loss(one, [0.0], [0.0])[0]) == pytest.approx(-0.1 * math.log(1 - 1e-6))

@@ -216,6 +216,20 @@ typedef struct {
     float* normal;
 } gsr_camera_grad;
 
+/*
+ * Gradients of a loss w.r.t. one LiDAR's per-ray outputs (DEVICE, planar,
+ * [beams][columns] per plane; NULL = zero): intensity (d/d sum w r), alpha
+ * (d/d sum w), depth_acc [2] (d/d sum w t, d/d sum w t^2; a loss on the
+ * range B/A reaches A and B through these two), ray_drop
+ * (d/d(sum w rho + T)).
+ */
+typedef struct {
+    float* intensity;
+    float* alpha;
+    float* depth_acc;
+    float* ray_drop;
+} gsr_lidar_grad;
+
 /* Gradients w.r.t. the raw surfel parameters (DEVICE, shapes of
  * gsr_surfels; accumulated with +=, so the caller zeroes them first). */
 typedef struct {
@@ -234,6 +248,13 @@ typedef struct {
     float w_normal;    /* normal consistency weight (0.05)               */
     float mask_alpha;  /* normal term only where the 4 neighbours have sum w >= this (0.5) */
 } gsr_loss_weights;
+
+/* Weights of the LiDAR loss (gsr_lidar_loss). */
+typedef struct {
+    float w_range;      /* L1 range weight over returned rays (1.0)        */
+    float w_intensity;  /* L1 intensity weight over returned rays (1.0)    */
+    float w_drop;       /* ray-drop cross-entropy weight over all rays (0.1) */
+} gsr_lidar_loss_weights;
 
 /* ---------------------------------------------------------------- setup */
 
@@ -331,9 +352,50 @@ gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t wor
                                void* stream);
 
 /*
+ * LiDAR loss of sensor `sensor` (GSR_SENSOR_LIDAR) against a recorded scan
+ * (DEVICE [beams][columns]: target_range, 0 where the beam returned nothing;
+ * target_intensity).  The paper reconstructs one LiDAR scene G^L apart from
+ * the camera scenes (Sec. III-A, "Scene Reconstruction"), models the
+ * ray-drop pattern (Sec. II, "Sensor Characteristics") and reports LiDAR
+ * intensity quality and training speed (Sec. IV, the representation table)
+ * without stating the loss; this one is
+ *   L = w_range   * mean over returned rays |range - range*|
+ *     + w_intensity * mean over returned rays |I - I*|
+ *     + w_drop    * mean over all rays BCE(p, [range* == 0]),
+ * p = ray_drop clamped to [1e-6, 1 - 1e-6] (no gradient where clamped),
+ * range = B/A from gsr_render_lidar (no gradient where A = 0).  fwd->range,
+ * alpha, intensity and ray_drop must be set.  Writes loss[0..3] = (L, range
+ * term, intensity term, drop term) (DEVICE float[4]) and all four planes of
+ * *grad (overwritten; depth_acc's second plane is 0).  Uses workspace
+ * scratch; deterministic.  Another sensor kind returns GSR_ERR_UNSUPPORTED.
+ */
+gsr_status gsr_lidar_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                          const gsr_lidar_out* fwd, const float* target_range, const float* target_intensity,
+                          const gsr_lidar_loss_weights* weights, float* loss, const gsr_lidar_grad* grad,
+                          void* stream);
+
+/*
+ * Reverse-order backward rasteriser of LiDAR `sensor` (Eq. 5 planes), as
+ * gsr_backward_render: per-ray gradients *grad w.r.t. the composited
+ * intensity, sum w, sum w t, sum w t^2 and ray drop (sum w rho + T, so the
+ * drop's background is 1) reach each record's Q = adj(M), det(M), low-pass
+ * centre, order key, opacity, intensity and rho.  fwd->trans and
+ * fwd->n_contrib are required.  accumulate = 0 zeroes the record gradients
+ * first.  Must follow gsr_preprocess / gsr_bin_sort / gsr_render_lidar (or
+ * gsr_render_rig) of the same frame with the same workspace.  Another
+ * sensor kind returns GSR_ERR_UNSUPPORTED.
+ */
+gsr_status gsr_backward_render_lidar(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                                     const gsr_lidar_out* fwd, const gsr_lidar_grad* grad, int32_t accumulate,
+                                     void* stream);
+
+/*
  * Chain the record gradients of all sensors back to the raw surfel
  * parameters (pos, log_scale, quat, opacity logit, SH, incl. the view
- * direction of the SH colour), accumulating into *out.  Camera sensors only.
+ * direction of the SH colour; for LiDAR records also intensity and the
+ * ray-drop logit, out->intensity / out->ray_drop when not NULL),
+ * accumulating into *out.  Pinhole and LiDAR sensors (a cylindrical
+ * sensor's records have no backward and contribute nothing).
  */
 gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
                                    const gsr_surfels* surfels, const gsr_objects* objects,
@@ -598,8 +660,8 @@ const char* gsr_last_cuda_error(void);
  * 4 gsr_camera_out, 5 gsr_lidar_out, 6 gsr_tiling, 7 gsr_camera_grad,
  * 8 gsr_surfel_grads, 9 gsr_loss_weights, 10 gsr_anchors, 11 gsr_mlp,
  * 12 gsr_mlp_grads, 13 gsr_surfel_table, 14 gsr_autotune_space,
- * 15 gsr_autotune_result, 16 gsr_zone_grid, 17 gsr_streamer.  Returns 0 for
- * other values.
+ * 15 gsr_autotune_result, 16 gsr_zone_grid, 17 gsr_streamer,
+ * 18 gsr_lidar_grad, 19 gsr_lidar_loss_weights.  Returns 0 for other values.
  */
 size_t gsr_struct_size(int32_t which);
 

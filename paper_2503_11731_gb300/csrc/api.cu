@@ -21,6 +21,11 @@ cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camer
                         const gsr_loss_weights* wt, float* loss, const gsr_camera_grad* g, cudaStream_t st);
 cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
                                    const gsr_camera_grad* g, int accumulate, cudaStream_t st);
+cudaError_t launch_render_backward_lidar(const gsr_plan* p, void* ws, int sensor, const gsr_lidar_out* fwd,
+                                         const gsr_lidar_grad* g, int accumulate, cudaStream_t st);
+cudaError_t launch_lidar_loss(const gsr_plan* p, void* ws, int sensor, const gsr_lidar_out* fwd,
+                              const float* t_range, const float* t_int, const gsr_lidar_loss_weights* wt,
+                              float* loss, const gsr_lidar_grad* g, cudaStream_t st);
 cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,
                                        const gsr_objects* obj, const gsr_surfel_grads* out, cudaStream_t st);
 
@@ -169,11 +174,14 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_COUNTERS] = C_WORDS * 4;
     sz[R_SENSOR_OF_TILE] = 64;
     sz[R_RECGRAD] = slots * kRecordBytes;
-    uint64_t max_hw = 0;
-    for (int i = 0; i < n_sensors; ++i)
-        if (sensors[i].kind != GSR_SENSOR_LIDAR)
-            max_hw = std::max<uint64_t>(max_hw, (uint64_t)sensors[i].width * sensors[i].height);
-    sz[R_LOSS_SCRATCH] = (6 * max_hw + 3 * ((max_hw + 255) / 256) + 64) * 4;
+    uint64_t max_hw = 0, max_rays = 0;
+    for (int i = 0; i < n_sensors; ++i) {
+        const uint64_t hw = (uint64_t)sensors[i].width * sensors[i].height;
+        if (sensors[i].kind != GSR_SENSOR_LIDAR) max_hw = std::max<uint64_t>(max_hw, hw);
+        else max_rays = std::max<uint64_t>(max_rays, hw);
+    }
+    sz[R_LOSS_SCRATCH] =
+        (std::max<uint64_t>(6 * max_hw + 3 * ((max_hw + 255) / 256), 4 * ((max_rays + 255) / 256)) + 64) * 4;
     sz[R_TILE_KEY_A] = sz[R_TILE_VAL_A] = sz[R_TILE_KEY_B] = sz[R_TILE_VAL_B] = (uint64_t)base * 4;
     sz[R_SPLIT_INFO] = (uint64_t)base * 16;
     sz[R_SPLIT_STATE] = (uint64_t)base * 8;
@@ -365,6 +373,8 @@ extern "C" size_t gsr_struct_size(int32_t which)
     case 15: return sizeof(gsr_autotune_result);
     case 16: return sizeof(gsr_zone_grid);
     case 17: return sizeof(gsr_streamer);
+    case 18: return sizeof(gsr_lidar_grad);
+    case 19: return sizeof(gsr_lidar_loss_weights);
     default: return 0;
     }
 }
@@ -401,6 +411,40 @@ extern "C" gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace,
     if (!fwd || !grad || !fwd->trans || !fwd->n_contrib) return GSR_ERR_INVALID_ARG;
     return cuda_fail(launch_render_backward(plan, workspace, sensor, fwd, grad, accumulate,
                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+static gsr_status check_lidar(const gsr_plan* plan, int32_t sensor)
+{
+    if (sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
+    if (plan->sensors[sensor].kind != GSR_SENSOR_LIDAR) return GSR_ERR_UNSUPPORTED;
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_lidar_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
+                                     const gsr_lidar_out* fwd, const float* target_range,
+                                     const float* target_intensity, const gsr_lidar_loss_weights* weights,
+                                     float* loss, const gsr_lidar_grad* grad, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if ((st = check_lidar(plan, sensor)) != GSR_OK) return st;
+    if (!fwd || !target_range || !target_intensity || !weights || !loss || !grad) return GSR_ERR_INVALID_ARG;
+    if (!fwd->range || !fwd->alpha || !fwd->intensity || !fwd->ray_drop) return GSR_ERR_INVALID_ARG;
+    if (!grad->intensity || !grad->alpha || !grad->depth_acc || !grad->ray_drop) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(launch_lidar_loss(plan, workspace, sensor, fwd, target_range, target_intensity, weights, loss,
+                                       grad, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+extern "C" gsr_status gsr_backward_render_lidar(const gsr_plan* plan, void* workspace, size_t workspace_bytes,
+                                                int32_t sensor, const gsr_lidar_out* fwd, const gsr_lidar_grad* grad,
+                                                int32_t accumulate, void* stream)
+{
+    gsr_status st = check_ws(plan, workspace, workspace_bytes);
+    if (st != GSR_OK) return st;
+    if ((st = check_lidar(plan, sensor)) != GSR_OK) return st;
+    if (!fwd || !grad || !fwd->trans || !fwd->n_contrib) return GSR_ERR_INVALID_ARG;
+    return cuda_fail(launch_render_backward_lidar(plan, workspace, sensor, fwd, grad, accumulate,
+                                                  reinterpret_cast<cudaStream_t>(stream)));
 }
 
 extern "C" gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,

@@ -191,6 +191,101 @@ __global__ void k_loss_reduce(const float* __restrict__ partial, int nblocks, fl
     }
 }
 
+// ================================================================ LiDAR loss
+// Per ray: m = 1 where the target has a return (target range > 0);
+//   L = w_range mean_m |range - range*| + w_int mean_m |I - I*|
+//     + w_drop mean_all BCE(clamp(drop, eps, 1 - eps), [range* <= 0]).
+struct LidarLossArgs {
+    const float* range;
+    const float* alpha;
+    const float* intensity;
+    const float* drop;
+    const float* t_range;
+    const float* t_int;
+    float* g_alpha;
+    float* g_dacc;       // [2][B][C]
+    float* g_int;
+    float* g_drop;
+    float* partial;      // [blocks][4]: returns, sum |dr|, sum |dI|, sum BCE
+    float* inv;          // [2]: 1 / returns (0 if none), 1 / rays
+    int n;
+    float w_range, w_int, w_drop;
+};
+constexpr float kDropEps = 1e-6f;
+
+__global__ void __launch_bounds__(256) k_lidar_loss_terms(LidarLossArgs a)
+{
+    __shared__ float red[4][8];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (p < a.n) {
+        const bool ret = a.t_range[p] > 0.f;
+        if (ret) {
+            v[0] = 1.f;
+            v[1] = fabsf(a.range[p] - a.t_range[p]);
+            v[2] = fabsf(a.intensity[p] - a.t_int[p]);
+        }
+        const float pc = fminf(fmaxf(a.drop[p], kDropEps), 1.f - kDropEps);
+        v[3] = ret ? -logf(1.f - pc) : -logf(pc);
+    }
+    for (int k = 0; k < 4; ++k) {
+        const float s = warp_sum(v[k]);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        a.partial[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_lidar_loss_reduce(LidarLossArgs a, int nblocks, float* __restrict__ loss)
+{
+    __shared__ double red[4][32];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 4; ++k) s[k] += a.partial[b * 4 + k];
+    for (int k = 0; k < 4; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < 4; ++k)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[k] += red[k][w];
+        const double im = t[0] > 0.0 ? 1.0 / t[0] : 0.0, ia = 1.0 / a.n;
+        const double lr = a.w_range * t[1] * im, li = a.w_int * t[2] * im, ld = a.w_drop * t[3] * ia;
+        loss[0] = (float)(lr + li + ld);
+        loss[1] = (float)lr;
+        loss[2] = (float)li;
+        loss[3] = (float)ld;
+        a.inv[0] = (float)im;
+        a.inv[1] = (float)ia;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lidar_loss_grad(LidarLossArgs a)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const float im = a.inv[0], ia = a.inv[1];
+    const bool ret = a.t_range[p] > 0.f;
+    // range = B / A where A > 0 (0 elsewhere, with no gradient)
+    const float A = a.alpha[p], r = a.range[p];
+    const float gr = ret ? a.w_range * im * sgnf(r - a.t_range[p]) : 0.f;
+    const float gB = A > 0.f ? gr / A : 0.f;
+    a.g_dacc[p] = gB;
+    a.g_dacc[a.n + p] = 0.f;
+    a.g_alpha[p] = -gB * r;
+    a.g_int[p] = ret ? a.w_int * im * sgnf(a.intensity[p] - a.t_int[p]) : 0.f;
+    const float d = a.drop[p];
+    const float y = ret ? 0.f : 1.f;
+    a.g_drop[p] = (d > kDropEps && d < 1.f - kDropEps) ? a.w_drop * ia * (d - y) / (d * (1.f - d)) : 0.f;
+}
+
 // ======================================================= backward rasteriser
 constexpr int kGradComponents = 20;  // record-gradient floats written (r0..r4)
 
@@ -212,10 +307,11 @@ __device__ __forceinline__ float4 warp_ray_box(const TileRayBox& r)
 struct BwdArgs {
     const float* trans;
     const uint32_t* n_contrib;
-    const float* g_rgb;     // [3][H][W]
+    const float* g_rgb;     // [3][H][W] (LiDAR: the intensity, [H][W])
     const float* g_alpha;
     const float* g_dacc;    // [2][H][W]
-    const float* g_normal;  // [3][H][W]
+    const float* g_normal;  // [3][H][W] (camera only)
+    const float* g_drop;    // [H][W] (LiDAR only: d/d(sum w rho + T))
     float4* recgrad;        // [slots][5]
 };
 
@@ -282,9 +378,13 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
         last = min(a.n_contrib[pix], (uint32_t)hi_pos);
         if (mode == 0) {
             T = a.trans[pix];
-            Ca[0] = T * sd.bg[0];
-            Ca[1] = T * sd.bg[1];
-            Ca[2] = T * sd.bg[2];
+            if (KIND == GSR_SENSOR_LIDAR) {
+                Ca[1] = T;  // a beam that leaves the scene is dropped: the drop's background is 1
+            } else {
+                Ca[0] = T * sd.bg[0];
+                Ca[1] = T * sd.bg[1];
+                Ca[2] = T * sd.bg[2];
+            }
         } else {
             const int R = sd.tile_w * sd.tile_h;
             const uint4 info = sp.info[tile];
@@ -292,9 +392,14 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
             load_ray(ray_block(sp, info.y, R, cc), R, tid, Sc);
             load_ray(ray_block(sp, info.y, R, (int)info.x), R, tid, Sf);
             T = Sc.T;
-            Ca[0] = (Sf.f0 - Sc.f0) + Sf.T * sd.bg[0];
-            Ca[1] = (Sf.f1 - Sc.f1) + Sf.T * sd.bg[1];
-            Ca[2] = (Sf.f2 - Sc.f2) + Sf.T * sd.bg[2];
+            if (KIND == GSR_SENSOR_LIDAR) {
+                Ca[0] = Sf.f0 - Sc.f0;
+                Ca[1] = (Sf.f1 - Sc.f1) + Sf.T;
+            } else {
+                Ca[0] = (Sf.f0 - Sc.f0) + Sf.T * sd.bg[0];
+                Ca[1] = (Sf.f1 - Sc.f1) + Sf.T * sd.bg[1];
+                Ca[2] = (Sf.f2 - Sc.f2) + Sf.T * sd.bg[2];
+            }
             Aa = Sf.A - Sc.A;
             Ba = Sf.B - Sc.B;
             Da = Sf.D - Sc.D;
@@ -303,7 +408,10 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
             Na[2] = Sf.n2 - Sc.n2;
         }
         if (last <= (uint32_t)lo_pos) last = 0;  // nothing of this ray in [lo_pos, hi_pos)
-        if (a.g_rgb) {
+        if (KIND == GSR_SENSOR_LIDAR) {
+            if (a.g_rgb) gC[0] = a.g_rgb[pix];
+            if (a.g_drop) gC[1] = a.g_drop[pix];
+        } else if (a.g_rgb) {
             gC[0] = a.g_rgb[pix];
             gC[1] = a.g_rgb[HW + pix];
             gC[2] = a.g_rgb[2 * HW + pix];
@@ -405,10 +513,13 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
                             g[13 + k] = w * gC[k];   // colour
                             g[16 + k] = w * gN[k];   // normal
                         }
-                    } else {
-                        dal += gC[0] * (T * c[0] - Ca[0] * io);
-                        Ca[0] = fmaf(w, c[0], Ca[0]);
-                        g[13] = w * gC[0];
+                    } else {  // LiDAR: intensity and ray-drop probability
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            dal += gC[k] * (T * c[k] - Ca[k] * io);
+                            Ca[k] = fmaf(w, c[k], Ca[k]);
+                            g[13 + k] = w * gC[k];
+                        }
                     }
                     Aa += w;
                     Ba = fmaf(w, z, Ba);
@@ -660,7 +771,7 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, Pr
 
     // accumulated gradients (world, after the object pose)
     V3 g_mu = v3(0, 0, 0), g_tu = v3(0, 0, 0), g_tv = v3(0, 0, 0), g_nw = v3(0, 0, 0);
-    float g_su = 0.f, g_sv = 0.f, g_o = 0.f, g_int = 0.f;
+    float g_su = 0.f, g_sv = 0.f, g_o = 0.f, g_int = 0.f, g_rd = 0.f;
     float g_sh[48];
     for (int k = 0; k < 3 * K; ++k) g_sh[k] = 0.f;
     bool any = false;
@@ -731,8 +842,60 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, Pr
             }
             const V3 g_dw = has_obj ? mul(Ro, g_dl) : g_dl;
             g_mu = g_mu + (1.f / vlen) * (g_dw - dot(dw, g_dw) * dw);
-        } else {
-            g_int += G3.y;  // LiDAR intensity; geometry of LiDAR records is not chained (camera-only backward)
+        } else if (sd.kind == GSR_SENSOR_LIDAR) {
+            // record: M = [a b ms] (columns), Q = adj(M) (rows r0..r2 .xyz),
+            // det(M), low-pass centre (column, row) of the centre's azimuth
+            // and elevation, order key |ms|
+            const V3 ms = mul(sd.R, mu) + v3(sd.t[0], sd.t[1], sd.t[2]);
+            const V3 Rtu = mul(sd.R, tu), Rtv = mul(sd.R, tv);
+            const V3 A = su * Rtu, B = sv * Rtv;
+            const float m00 = A.x, m01 = B.x, m02 = ms.x;
+            const float m10 = A.y, m11 = B.y, m12 = ms.y;
+            const float m20 = A.z, m21 = B.z, m22 = ms.z;
+            const float gq00 = G0.x, gq01 = G0.y, gq02 = G0.z, gq10 = G1.x, gq11 = G1.y, gq12 = G1.z;
+            const float gq20 = G2.x, gq21 = G2.y, gq22 = G2.z, g_det = G2.w;
+            // each entry of the adjugate is a 2x2 minor: d(m_ab m_cd - m_ef m_gh)
+            float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f, g20 = 0.f, g21 = 0.f, g22 = 0.f;
+            g11 += gq00 * m22; g22 += gq00 * m11; g12 -= gq00 * m21; g21 -= gq00 * m12;  // q00 = m11 m22 - m12 m21
+            g02 += gq01 * m21; g21 += gq01 * m02; g01 -= gq01 * m22; g22 -= gq01 * m01;  // q01 = m02 m21 - m01 m22
+            g01 += gq02 * m12; g12 += gq02 * m01; g02 -= gq02 * m11; g11 -= gq02 * m02;  // q02 = m01 m12 - m02 m11
+            g12 += gq10 * m20; g20 += gq10 * m12; g10 -= gq10 * m22; g22 -= gq10 * m10;  // q10 = m12 m20 - m10 m22
+            g00 += gq11 * m22; g22 += gq11 * m00; g02 -= gq11 * m20; g20 -= gq11 * m02;  // q11 = m00 m22 - m02 m20
+            g02 += gq12 * m10; g10 += gq12 * m02; g00 -= gq12 * m12; g12 -= gq12 * m00;  // q12 = m02 m10 - m00 m12
+            g10 += gq20 * m21; g21 += gq20 * m10; g11 -= gq20 * m20; g20 -= gq20 * m11;  // q20 = m10 m21 - m11 m20
+            g01 += gq21 * m20; g20 += gq21 * m01; g00 -= gq21 * m21; g21 -= gq21 * m00;  // q21 = m01 m20 - m00 m21
+            g00 += gq22 * m11; g11 += gq22 * m00; g01 -= gq22 * m10; g10 -= gq22 * m01;  // q22 = m00 m11 - m01 m10
+            // d det / d m_ij is the cofactor of m_ij, i.e. adj(M)_ji
+            g00 += g_det * fmaf(m11, m22, -m12 * m21);
+            g01 += g_det * fmaf(m12, m20, -m10 * m22);
+            g02 += g_det * fmaf(m10, m21, -m11 * m20);
+            g10 += g_det * fmaf(m02, m21, -m01 * m22);
+            g11 += g_det * fmaf(m00, m22, -m02 * m20);
+            g12 += g_det * fmaf(m01, m20, -m00 * m21);
+            g20 += g_det * fmaf(m01, m12, -m02 * m11);
+            g21 += g_det * fmaf(m02, m10, -m00 * m12);
+            g22 += g_det * fmaf(m00, m11, -m01 * m10);
+            const V3 gA = v3(g00, g10, g20), gB = v3(g01, g11, g21);
+            V3 g_ms = v3(g02, g12, g22);
+            // centre column = (azimuth - az0) / d_az - 1/2, row = (el_max - elevation) / d_el
+            const float rxy2 = ms.x * ms.x + ms.y * ms.y;
+            const float rxy = sqrtf(rxy2);
+            const float rc2 = rxy2 + ms.z * ms.z;
+            const float rc = sqrtf(rc2);
+            const float gcol = G0.w * sd.inv_d_az, gel = -G1.w * sd.inv_d_el;
+            if (rxy2 > 0.f) {  // straight above or below the sensor the centre's angles have no gradient
+                g_ms.x += gcol * (-ms.y / rxy2) - gel * ms.z * ms.x / (rxy * rc2);
+                g_ms.y += gcol * (ms.x / rxy2) - gel * ms.z * ms.y / (rxy * rc2);
+                g_ms.z += gel * rxy / rc2;
+            }
+            g_ms = g_ms + (G4.w / rc) * ms;  // order key |ms|
+            g_mu = g_mu + mulT(sd.R, g_ms);
+            g_su += dot(Rtu, gA);
+            g_sv += dot(Rtv, gB);
+            g_tu = g_tu + su * mulT(sd.R, gA);
+            g_tv = g_tv + sv * mulT(sd.R, gB);
+            g_int += G3.y;  // intensity
+            g_rd += G3.z;   // ray-drop probability
         }
     }
     if (!any) return;
@@ -742,6 +905,10 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, Pr
     a.G.log_scale[2 * i] += g_su * su;
     a.G.log_scale[2 * i + 1] += g_sv * sv;
     if (a.G.intensity) a.G.intensity[i] += g_int;
+    if (a.G.ray_drop && S.ray_drop) {  // rho = sigmoid(ray-drop logit)
+        const float rho = 1.f / (1.f + __expf(-S.ray_drop[i]));
+        a.G.ray_drop[i] += g_rd * rho * (1.f - rho);
+    }
     // undo the object rotation
     if (has_obj) {
         g_mu = mulT(Ro, g_mu);
@@ -801,34 +968,49 @@ cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camer
     return cudaGetLastError();
 }
 
+cudaError_t launch_lidar_loss(const gsr_plan* p, void* ws, int sensor, const gsr_lidar_out* fwd,
+                              const float* t_range, const float* t_int, const gsr_lidar_loss_weights* wt,
+                              float* loss, const gsr_lidar_grad* g, cudaStream_t st)
+{
+    const gsr_sensor& s = p->sensors[sensor];
+    LidarLossArgs a;
+    a.range = fwd->range;
+    a.alpha = fwd->alpha;
+    a.intensity = fwd->intensity;
+    a.drop = fwd->ray_drop;
+    a.t_range = t_range;
+    a.t_int = t_int;
+    a.g_alpha = g->alpha;
+    a.g_dacc = g->depth_acc;
+    a.g_int = g->intensity;
+    a.g_drop = g->ray_drop;
+    a.n = s.width * s.height;
+    a.w_range = wt->w_range;
+    a.w_int = wt->w_intensity;
+    a.w_drop = wt->w_drop;
+    const int blocks = (a.n + 255) / 256;
+    a.partial = region<float>(p, ws, R_LOSS_SCRATCH);
+    a.inv = a.partial + (size_t)4 * blocks;
+    k_lidar_loss_terms<<<blocks, 256, 0, st>>>(a);
+    k_lidar_loss_reduce<<<1, 1024, 0, st>>>(a, blocks, loss);
+    k_lidar_loss_grad<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 SplitBufs split_bufs(const gsr_plan* p, const void* ws);
 
-cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
-                                   const gsr_camera_grad* g, int accumulate, cudaStream_t st)
+template <int KIND>
+static cudaError_t render_backward_kind(const gsr_plan* p, void* ws, int sensor, const BwdArgs& a, cudaStream_t st)
 {
     const SensorTable tab = make_sensor_table(p);
     const SensorDev& sd = tab.s[sensor];
-    float4* recgrad = region<float4>(p, ws, R_RECGRAD);
-    const uint64_t slots = (uint64_t)p->n_surfels * p->n_sensors;
-    if (!accumulate) {
-        cudaError_t e = cudaMemsetAsync(recgrad, 0, slots * kRecordBytes, st);
-        if (e != cudaSuccess) return e;
-    }
-    BwdArgs a;
-    a.trans = fwd->trans;
-    a.n_contrib = fwd->n_contrib;
-    a.g_rgb = g->rgb;
-    a.g_alpha = g->alpha;
-    a.g_dacc = g->depth_acc;
-    a.g_normal = g->normal;
-    a.recgrad = recgrad;
     const int threads = sd.tile_w * sd.tile_h;
     const int tiles = sd.tiles_x * sd.tiles_y;
     const int pb = sort_result_buffer(tile_sort_passes(p));
     const uint32_t* pval = region<uint32_t>(p, ws, pb ? R_PAIR_VAL_B : R_PAIR_VAL_A);
     const size_t smem = backward_smem_bytes(threads);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_render_backward<GSR_SENSOR_PINHOLE>,
+        const cudaError_t e = cudaFuncSetAttribute(k_render_backward<KIND>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -838,27 +1020,68 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
                                        (uint32_t)sd.tile_base, (uint32_t)(sd.tile_base + tiles), sorder);
     const SplitBufs sp = split_bufs(p, ws);
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
-    k_render_backward<GSR_SENSOR_PINHOLE><<<tiles, threads, smem, st>>>(
-        tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a, counters, sorder,
-        sp);
+    k_render_backward<KIND><<<tiles, threads, smem, st>>>(tab, sensor, region<float4>(p, ws, R_RECORDS),
+                                                          region<uint2>(p, ws, R_RANGES), pval, a, counters,
+                                                          sorder, sp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the other chunks of split tiles, persistent over the camera's split items
+    // the other chunks of split tiles, persistent over the sensor's split items
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_render_backward_chunks<GSR_SENSOR_PINHOLE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_render_backward_chunks<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
     }
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_backward_chunks<GSR_SENSOR_PINHOLE>,
-                                                           threads, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_backward_chunks<KIND>, threads,
+                                                           smem)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(counters + C_SPLIT_QUEUE, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-    k_render_backward_chunks<GSR_SENSOR_PINHOLE><<<sms * (per_sm > 0 ? per_sm : 1), threads, smem, st>>>(
+    k_render_backward_chunks<KIND><<<sms * (per_sm > 0 ? per_sm : 1), threads, smem, st>>>(
         tab, sensor, region<float4>(p, ws, R_RECORDS), region<uint2>(p, ws, R_RANGES), pval, a, counters, sp);
     return cudaGetLastError();
+}
+
+static cudaError_t zero_recgrad(const gsr_plan* p, void* ws, int accumulate, cudaStream_t st)
+{
+    if (accumulate) return cudaSuccess;
+    const uint64_t slots = (uint64_t)p->n_surfels * p->n_sensors;
+    return cudaMemsetAsync(region<float4>(p, ws, R_RECGRAD), 0, slots * kRecordBytes, st);
+}
+
+cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, const gsr_camera_out* fwd,
+                                   const gsr_camera_grad* g, int accumulate, cudaStream_t st)
+{
+    cudaError_t e = zero_recgrad(p, ws, accumulate, st);
+    if (e != cudaSuccess) return e;
+    BwdArgs a;
+    a.trans = fwd->trans;
+    a.n_contrib = fwd->n_contrib;
+    a.g_rgb = g->rgb;
+    a.g_alpha = g->alpha;
+    a.g_dacc = g->depth_acc;
+    a.g_normal = g->normal;
+    a.g_drop = nullptr;
+    a.recgrad = region<float4>(p, ws, R_RECGRAD);
+    return render_backward_kind<GSR_SENSOR_PINHOLE>(p, ws, sensor, a, st);
+}
+
+cudaError_t launch_render_backward_lidar(const gsr_plan* p, void* ws, int sensor, const gsr_lidar_out* fwd,
+                                         const gsr_lidar_grad* g, int accumulate, cudaStream_t st)
+{
+    cudaError_t e = zero_recgrad(p, ws, accumulate, st);
+    if (e != cudaSuccess) return e;
+    BwdArgs a;
+    a.trans = fwd->trans;
+    a.n_contrib = fwd->n_contrib;
+    a.g_rgb = g->intensity;
+    a.g_alpha = g->alpha;
+    a.g_dacc = g->depth_acc;
+    a.g_normal = nullptr;
+    a.g_drop = g->ray_drop;
+    a.recgrad = region<float4>(p, ws, R_RECGRAD);
+    return render_backward_kind<GSR_SENSOR_LIDAR>(p, ws, sensor, a, st);
 }
 
 cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,

@@ -268,7 +268,55 @@ class LossOutputs:
 
 def _grad_struct(g):
     return gsr.SurfelGrads(_ptr(g["pos"]), _ptr(g["log_scale"]), _ptr(g["quat"]), _ptr(g["opacity"]),
-                           _ptr(g["sh"]), _ptr(g.get("intensity")))
+                           _ptr(g["sh"]), _ptr(g.get("intensity")), _ptr(g.get("ray_drop")))
+
+
+class LidarLossOutputs:
+    """Per-ray gradient buffers of gsr_lidar_loss for one LiDAR."""
+
+    def __init__(self, B, C, device):
+        self.intensity = torch.zeros(B, C, device=device)
+        self.alpha = torch.zeros(B, C, device=device)
+        self.depth_acc = torch.zeros(2, B, C, device=device)
+        self.ray_drop = torch.zeros(B, C, device=device)
+        self.loss = torch.zeros(4, device=device)
+
+    def struct(self):
+        return gsr.LidarGrad(_ptr(self.intensity), _ptr(self.alpha), _ptr(self.depth_acc), _ptr(self.ray_drop))
+
+
+def lidar_loss(r: Renderer, sensor, target_range, target_intensity, w_range=1.0, w_intensity=1.0, w_drop=0.1,
+               stream=None):
+    """gsr_lidar_loss on the last render of LiDAR `sensor` (needs range,
+    intensity, alpha and drop outputs).  Returns (loss[4] tensor, LidarLossOutputs)."""
+    o = r.out[sensor]
+    B, C = o["alpha"].shape
+    bufs = r.__dict__.setdefault("_lidar_loss_bufs", {})
+    lo = bufs.get(sensor)
+    if lo is None:
+        lo = bufs[sensor] = LidarLossOutputs(B, C, r.device)
+    tr, ti = target_range.contiguous(), target_intensity.contiguous()
+    gsr.lidar_loss(r.plan, r.ws_ptr, r.ws_bytes, sensor, r._out_struct(sensor), _ptr(tr), _ptr(ti),
+                   gsr.LidarLossWeights(w_range, w_intensity, w_drop), _ptr(lo.loss), lo.struct(),
+                   _stream_handle(stream))
+    return lo.loss, lo
+
+
+def lidar_backward(r: Renderer, sensor, grad: "gsr.LidarGrad", surfels: DeviceSurfels, objects=None, out=None,
+                   stream=None):
+    """gsr_backward_render_lidar + gsr_backward_preprocess for one LiDAR:
+    d(loss)/d(surfel parameters incl. intensity and ray-drop logit),
+    accumulated into `out` (dict of tensors)."""
+    if out is None:
+        keys = ["pos", "log_scale", "quat", "opacity", "sh", "intensity"]
+        if surfels.ray_drop is not None:
+            keys.append("ray_drop")
+        out = {k: torch.zeros_like(getattr(surfels, k)) for k in keys}
+    h = _stream_handle(stream)
+    obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
+    gsr.backward_render_lidar(r.plan, r.ws_ptr, r.ws_bytes, sensor, r._out_struct(sensor), grad, 0, h)
+    gsr.backward_preprocess(r.plan, r.ws_ptr, r.ws_bytes, surfels.struct(), obj, _grad_struct(out), h)
+    return out
 
 
 def camera_loss(r: Renderer, sensor, target, w_dist=0.1, w_normal=0.05, mask_alpha=0.5, stream=None):

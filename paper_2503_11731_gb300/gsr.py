@@ -67,6 +67,14 @@ class CameraGrad(ctypes.Structure):
     _fields_ = [("rgb", c_vp), ("alpha", c_vp), ("depth_acc", c_vp), ("normal", c_vp)]
 
 
+class LidarGrad(ctypes.Structure):
+    _fields_ = [("intensity", c_vp), ("alpha", c_vp), ("depth_acc", c_vp), ("ray_drop", c_vp)]
+
+
+class LidarLossWeights(ctypes.Structure):
+    _fields_ = [("w_range", c_f32), ("w_intensity", c_f32), ("w_drop", c_f32)]
+
+
 class SurfelGrads(ctypes.Structure):
     _fields_ = [("pos", c_vp), ("log_scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp),
                 ("intensity", c_vp), ("ray_drop", c_vp)]
@@ -135,7 +143,8 @@ HEAD_CAMERA, HEAD_LIDAR = 0, 1
 SEES_CAMERAS, SEES_LIDARS = 1, 2
 
 _STRUCTS = [Plan, Sensor, Surfels, Objects, CameraOut, LidarOut, Tiling, CameraGrad, SurfelGrads, LossWeights,
-            Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult, ZoneGrid, Streamer]
+            Anchors, Mlp, MlpGrads, SurfelTable, AutotuneSpace, AutotuneResult, ZoneGrid, Streamer, LidarGrad,
+            LidarLossWeights]
 
 # exported symbols and their ctypes signatures (restype, argtypes)
 SIGNATURES = {
@@ -167,6 +176,10 @@ SIGNATURES = {
                          ctypes.POINTER(LossWeights), c_vp, ctypes.POINTER(CameraGrad), c_vp]),
     "gsr_backward_render": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(CameraOut),
                                     ctypes.POINTER(CameraGrad), c_i32, c_vp]),
+    "gsr_lidar_loss": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32, ctypes.POINTER(LidarOut), c_vp,
+                               c_vp, ctypes.POINTER(LidarLossWeights), c_vp, ctypes.POINTER(LidarGrad), c_vp]),
+    "gsr_backward_render_lidar": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, c_i32,
+                                          ctypes.POINTER(LidarOut), ctypes.POINTER(LidarGrad), c_i32, c_vp]),
     "gsr_backward_preprocess": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(Surfels),
                                         ctypes.POINTER(Objects), ctypes.POINTER(SurfelGrads), c_vp]),
     "gsr_render_rig": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.POINTER(CameraOut),
@@ -330,6 +343,18 @@ def loss(plan, ws, ws_bytes, sensor_idx, fwd: CameraOut, target, weights: LossWe
 def backward_render(plan, ws, ws_bytes, sensor_idx, fwd: CameraOut, grad: CameraGrad, accumulate, stream):
     _check(lib().gsr_backward_render(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(fwd),
                                      ctypes.byref(grad), int(accumulate), stream), "gsr_backward_render")
+
+
+def lidar_loss(plan, ws, ws_bytes, sensor_idx, fwd: LidarOut, target_range, target_intensity,
+               weights: LidarLossWeights, loss_out, grad: LidarGrad, stream):
+    _check(lib().gsr_lidar_loss(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(fwd), target_range,
+                                target_intensity, ctypes.byref(weights), loss_out, ctypes.byref(grad), stream),
+           "gsr_lidar_loss")
+
+
+def backward_render_lidar(plan, ws, ws_bytes, sensor_idx, fwd: LidarOut, grad: LidarGrad, accumulate, stream):
+    _check(lib().gsr_backward_render_lidar(ctypes.byref(plan), ws, ws_bytes, int(sensor_idx), ctypes.byref(fwd),
+                                           ctypes.byref(grad), int(accumulate), stream), "gsr_backward_render_lidar")
 
 
 def backward_preprocess(plan, ws, ws_bytes, surfels: Surfels, objects, out: SurfelGrads, stream):

@@ -271,7 +271,7 @@ def render_lidar(p, lid):
             "I": (wgt @ r_int).reshape(shp), "drop": (wgt @ rho_d + Tfin).reshape(shp), "T": Tfin.reshape(shp)}
 
 
-def lidar_loss(out, target_range, target_int, w_range=1.0, w_int=1.0, w_drop=0.1, eps=1e-6):
+def lidar_loss(out, target_range, target_int, w_range=1.0, w_int=1.0, w_drop=0.1, eps=2.0 ** -20):
     """LiDAR loss on the outputs of render_lidar (the paper states none; this
     is the reading the library's LiDAR loss takes): over the rays whose
     target has a return (target range > 0), the mean L1 error of the range

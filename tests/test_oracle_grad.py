@@ -176,4 +176,6 @@ def test_lidar_loss_worked_example():
     assert float(lr0) == 0.0 and float(li0) == 0.0 and float(ld0) == pytest.approx(-0.1 * math.log(0.8))
     one = {"A": torch.zeros(1, dtype=torch.float64), "B": torch.zeros(1, dtype=torch.float64),
            "I": torch.zeros(1, dtype=torch.float64), "drop": torch.ones(1, dtype=torch.float64)}
-    assert float(OG.lidar_loss(one, [0.0], [0.0])[0]) == pytest.approx(-0.1 * math.log(1 - 1e-6))
+    assert float(OG.lidar_loss(one, [0.0], [0.0])[0]) == pytest.approx(-0.1 * math.log(1 - 2.0 ** -20))
+    # a sure drop where the target has a return costs the clamped -log(2^-20)
+    assert float(OG.lidar_loss(one, [5.0], [0.0])[3]) == pytest.approx(0.1 * 20 * math.log(2.0))

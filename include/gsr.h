@@ -362,7 +362,7 @@ gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t wor
  *   L = w_range   * mean over returned rays |range - range*|
  *     + w_intensity * mean over returned rays |I - I*|
  *     + w_drop    * mean over all rays BCE(p, [range* == 0]),
- * p = ray_drop clamped to [1e-6, 1 - 1e-6] (no gradient where clamped),
+ * p = ray_drop clamped to [2^-20, 1 - 2^-20] (no gradient where clamped),
  * range = B/A from gsr_render_lidar (no gradient where A = 0).  fwd->range,
  * alpha, intensity and ray_drop must be set.  Writes loss[0..3] = (L, range
  * term, intensity term, drop term) (DEVICE float[4]) and all four planes of

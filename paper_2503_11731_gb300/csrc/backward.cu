@@ -211,7 +211,7 @@ struct LidarLossArgs {
     int n;
     float w_range, w_int, w_drop;
 };
-constexpr float kDropEps = 1e-6f;
+constexpr float kDropEps = 0x1p-20f;  // 1 - eps is exact in FP32
 
 __global__ void __launch_bounds__(256) k_lidar_loss_terms(LidarLossArgs a)
 {

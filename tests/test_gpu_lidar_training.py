@@ -38,6 +38,11 @@ def _lidar(columns=200):
     return synth.spinning_lidar(16, columns, -25.0, 10.0, (0.0, 0.0, 1.8))
 
 
+# split lists: 2000 surfels seen by 32-column tiles of a 64-column scan
+# (180 degrees of azimuth per tile), first chunk 256 records, then 64
+SPLIT_N, SPLIT_COLUMNS, SPLIT = 2000, 64, (256, 64)
+
+
 def _renderer(s, sensors, split=None):
     from paper_2503_11731_gb300.frame import Renderer
     tiles = [(32, 4) if d.kind == "lidar" else (16, 8) for d in sensors]
@@ -81,11 +86,11 @@ def _weights(shape, seed):
 def test_lidar_backward_matches_fp64_oracle(gpu_lib, case):
     from paper_2503_11731_gb300 import gsr
     from paper_2503_11731_gb300.frame import DeviceSurfels, lidar_backward
-    s, lid = _scene(), _lidar()
+    s, lid = (_scene(n=SPLIT_N), _lidar(SPLIT_COLUMNS)) if case == "split" else (_scene(), _lidar())
     sensors = [lid]
     if case == "camera+lidar":
         sensors = [synth.pinhole(64, 48, 40.0, (0.0, 0.0, 1.5), yaw_deg=5.0, pitch_deg=-12.0), lid]
-    r = _renderer(s, sensors, split=(32, 32) if case == "split" else None)
+    r = _renderer(s, sensors, split=SPLIT if case == "split" else None)
     li = len(sensors) - 1
     d = DeviceSurfels.from_host(s)
     r.render(d)
@@ -106,14 +111,15 @@ def test_lidar_backward_matches_fp64_oracle(gpu_lib, case):
 
 
 def test_lidar_split_lists_are_exercised(gpu_lib):
-    """The split case above walks chunked lists: some tile of the scan has a
-    list longer than the 32-record first chunk."""
+    """The split case above walks chunked lists: rays of the scan reach past
+    the first chunk (256 records) and past the second."""
     from paper_2503_11731_gb300.frame import DeviceSurfels
-    s, lid = _scene(), _lidar()
-    r = _renderer(s, [lid], split=(32, 32))
+    s, lid = _scene(n=SPLIT_N), _lidar(SPLIT_COLUMNS)
+    r = _renderer(s, [lid], split=SPLIT)
     r.render(DeviceSurfels.from_host(s))
     n = r.out[0]["n_contrib"].cpu().numpy()
-    assert n.max() > 32
+    print("rays past the first chunk:", int((n > SPLIT[0]).sum()), "max position", int(n.max()))
+    assert n.max() > SPLIT[0] + SPLIT[1]
 
 
 def _targets(lid, seed=5):
@@ -129,7 +135,9 @@ def test_lidar_loss_kernel_matches_fp64_loss(gpu_lib):
     s, lid = _scene(seed=4), _lidar()
     p = {k: torch.tensor(np.asarray(getattr(s, k), np.float64)) for k in NAMES}
     t = OG.render_lidar(p, lid)
-    leaves = {k: t[k].detach().clone().requires_grad_(True) for k in ("A", "B", "I", "drop")}
+    # both sides see the same FP32 scan (the kernel's inputs are FP32)
+    leaves = {k: t[k].detach().to(torch.float32).to(torch.float64).requires_grad_(True)
+              for k in ("A", "B", "I", "drop")}
     tr, ti = _targets(lid)
     L, lr, li, ld = OG.lidar_loss(leaves, tr, ti)
     L.backward()
@@ -184,22 +192,24 @@ def test_lidar_chain_matches_fp64_oracle(gpu_lib):
 
 
 def test_lidar_gradient_finite_differences_on_gpu(gpu_lib):
-    """Central differences of the GPU LiDAR loss (FP32) along random
-    directions over a few surfels (rotations left out: a turned surfel moves
-    its hard support boundary, see the camera test)."""
-    from paper_2503_11731_gb300.frame import DeviceSurfels, lidar_loss
+    """Central differences of the GPU render along random directions over a
+    few surfels, the loss of each FP32 scan summed in FP64 on the host (an
+    FP32 loss would quantise the differences).  Rotations are left out: a
+    turned surfel moves its hard support boundary (see the camera test)."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels
     s, lid = _scene(seed=7), _lidar()
     tr, ti = _targets(lid, 9)
     r = _renderer(s, [lid])
     L0, g = _gpu_chain(s, lid, tr, ti, r)
-    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
-    ttr, tti = dev(tr), dev(ti)
 
     def loss_of(ss):
         r.render(DeviceSurfels.from_host(ss))
-        return float(lidar_loss(r, 0, ttr, tti)[0][0])
+        o = {k: r.out[0][k].double().cpu() for k in ("alpha", "range", "intensity", "drop")}
+        out = {"A": o["alpha"], "B": o["range"] * o["alpha"], "I": o["intensity"], "drop": o["drop"]}
+        return float(OG.lidar_loss(out, tr, ti)[0])
+    assert loss_of(s) == pytest.approx(L0, rel=1e-4)
     rng = np.random.default_rng(10)
-    steps = {"pos": 1e-3, "log_scale": 1e-3, "opacity": 1e-2, "intensity": 1e-2, "ray_drop": 1e-2}
+    steps = {"pos": 1e-4, "log_scale": 1e-4, "opacity": 1e-3, "intensity": 1e-3, "ray_drop": 1e-3}
     for name, h in steps.items():
         base = getattr(s, name)
         v = rng.normal(size=base.shape).astype(np.float32)

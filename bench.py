@@ -18,7 +18,8 @@ no flush is needed.
 
 The "backward_step" block times one training step of the reconstruction
 workload (2M surfels, one 1920x1080 camera: forward, loss, backward to the
-surfel parameters).
+surfel parameters); "lidar_backward_step" the same for the LiDAR scene (one
+128x1800 LiDAR, range / intensity / ray-drop loss).
 
 The "compare" block times, on the same plan and workspace, the explicit
 forms of the frame: the 3M-surfel SH-3 table the anchors were grouped from
@@ -401,6 +402,89 @@ def backward_step(args, stream):
             "loss": loss, "steps": k, "split": list(best[1]), "split_trials": trials}
 
 
+def lidar_backward_step(args, stream):
+    """One training step of the LiDAR scene (Sec. III-A: G^L is reconstructed
+    apart from the camera scenes): the 2M-surfel driving scene with seeded
+    ray-drop logits, one 128x1800 spinning LiDAR, loss L1 range + L1
+    intensity over returned beams + 0.1 ray-drop cross-entropy against the
+    scan of a perturbed copy (beams with sum w < 0.5 count as no return);
+    forward (preprocess, sort, composite) + loss + backward (reverse
+    rasteriser, preprocess backward to position, scales, rotation, opacity,
+    intensity, ray-drop logit)."""
+    import torch
+    from paper_2503_11731_gb300 import synth
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, lidar_backward, lidar_loss
+    s = synth.driving_scene(n=2_000_000, seed=synth.SEED_BASE + 3)
+    s.ray_drop = np.random.default_rng(synth.SEED_BASE + 31).normal(0.0, 1.0, s.n).astype(np.float32)
+    tgt = synth.perturbed(s, seed=synth.SEED_BASE + 30)
+    tgt.ray_drop = s.ray_drop
+    lid = synth.spinning_lidar(128, 1800, -25.0, 15.0, (0.0, 0.0, 1.8))
+    outs = ("range", "intensity", "alpha", "trans", "drop", "n_contrib")
+    dt = DeviceSurfels.from_host(tgt)
+    d = DeviceSurfels.from_host(s)
+    grads = {k: torch.zeros_like(getattr(d, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh",
+                                                          "intensity", "ray_drop")}
+    names = ("forward", "loss", "backward")
+    ev = {k: [] for k in names}
+
+    def make(split):
+        r = Renderer(s.n, [lid], tiles=[(8, 8)], outputs=outs, lidar_split=split)
+        r.render(dt)
+        o = r.out[0]
+        t_range = torch.where(o["alpha"] >= 0.5, o["range"], torch.zeros_like(o["range"]))
+        return r, t_range, o["intensity"].clone()
+
+    trials = []
+    best = None
+    for split in ((16384, 512), (4096, 256), (1024, 256)):
+        r, t_range, t_int = make(split)
+
+        def plain():
+            for g in grads.values():
+                g.zero_()
+            r.render(d)
+            loss, lo = lidar_loss(r, 0, t_range, t_int)
+            lidar_backward(r, 0, lo.struct(), d, out=grads)
+        plain()
+        ms = timed(stream, 3, plain)
+        trials.append({"split": list(split), "ms": ms})
+        if best is None or ms < best[0]:
+            best = (ms, split)
+        del r
+    r, t_range, t_int = make(best[1])
+
+    def step(record):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        for g in grads.values():
+            g.zero_()
+        if record:
+            e[0].record(stream)
+        r.render(d)
+        if record:
+            e[1].record(stream)
+        loss, lo = lidar_loss(r, 0, t_range, t_int)
+        if record:
+            e[2].record(stream)
+        lidar_backward(r, 0, lo.struct(), d, out=grads)
+        if record:
+            e[3].record(stream)
+            for k, (a, b) in zip(names, ((e[0], e[1]), (e[1], e[2]), (e[2], e[3]))):
+                ev[k].append((a, b))
+        return loss
+
+    for _ in range(2):
+        step(False)
+    k = max(3, args.steps // 2)
+    ms = timed(stream, k, lambda: step(True))
+    loss = float(step(False)[0])
+    torch.cuda.synchronize()
+    return {"workload": "2M-surfel driving scene with ray-drop logits, one 128x1800 LiDAR, 8x8 tiles, loss vs the "
+                        "scan of a perturbed copy",
+            "ms_per_step": ms, "stage_ms": {k: float(np.mean([a.elapsed_time(b) for a, b in v]))
+                                            for k, v in ev.items()},
+            "loss": loss, "steps": k, "lidar_split": list(best[1]), "split_trials": trials}
+
+
 def cylindrical_frame(args, stream):
     """A frame of a cylindrical surround camera (Eq. 4): the 1.5M-surfel SH-3
     driving scene seen by one 3840x1080 camera over 200 deg of azimuth at
@@ -447,7 +531,7 @@ def two_scene_frame(args, r, sensors, da, model, d_obj, pose_t, origin, stream):
     tiles = [(r.plan.sensors[i].tile_w, r.plan.sensors[i].tile_h) for i in range(len(sensors))]
     r2 = Renderer(n, sensors, tiles=tiles, max_dup=args.max_dup, batch_depth=r.plan.tiling.batch_depth,
                   split=(r.plan.tiling.split_first, r.plan.tiling.split_chunk), lidar_split=r.lidar_split(),
-                  outputs=("rgb", "depth", "normal", "alpha", "trans", "drop"))
+                  outputs=("rgb", "depth", "normal", "alpha", "drop"))
     nf = NeuralFrame(model, da, r2, d_obj, pose_t, origin, gsr.DECODE_BF16_TENSOR, lidar=(model_l, da))
     nf.render()
     torch.cuda.synchronize()
@@ -600,7 +684,7 @@ def run_gpu(args):
     r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles, batch_depth=args.batch_depth,
                  split=(args.split_first, args.split_chunk),
                  lidar_split=(args.lidar_split_first, args.lidar_split_chunk),
-                 outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib", "n_walk"))
+                 outputs=("rgb", "depth", "normal", "alpha", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
     pose_t = None if poses is None else torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
@@ -754,6 +838,7 @@ def run_gpu(args):
 
     # ---- backward step of the reconstruction workload (2M surfels, 1920x1080)
     bwd = backward_step(args, stream) if args.backward else None
+    lbwd = lidar_backward_step(args, stream) if args.backward else None
     cyl = cylindrical_frame(args, stream) if args.cylindrical else None
     streaming = streaming_frames(args, stream) if args.streaming else None
 
@@ -811,6 +896,7 @@ def run_gpu(args):
         "compare": compare,
         "autotune": tuned,
         "backward_step": bwd,
+        "lidar_backward_step": lbwd,
         "cylindrical_frame": cyl,
         "streaming": streaming,
         "clocks": clocks,
@@ -847,7 +933,7 @@ def main():
     ap.add_argument("--no-cylindrical", dest="cylindrical", action="store_false",
                     help="skip the cylindrical-camera frame measurement")
     ap.add_argument("--no-backward", dest="backward", action="store_false",
-                    help="skip the backward-step timing (2M surfels, 1920x1080)")
+                    help="skip the backward-step timings (2M surfels; 1920x1080 camera, 128x1800 LiDAR)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -344,8 +344,11 @@ gsr_status gsr_loss(const gsr_plan* plan, void* workspace, size_t workspace_byte
  * no per-pixel lists are stored), and accumulates d(loss)/d(record) --
  * reduced over the warp before FP32 atomics -- into the workspace.
  * accumulate = 0 zeroes the record gradients first (first sensor of a step).
- * Must follow gsr_preprocess / gsr_bin_sort / gsr_render_camera of the same
- * frame with the same workspace.
+ * Must follow gsr_preprocess / gsr_bin_sort / gsr_render_camera (or
+ * gsr_render_rig) of the same frame with the same workspace, that render
+ * writing trans and n_contrib: the transmittance after each chunk of a
+ * split tile list, where the backward walks of the other chunks start, is
+ * kept in the workspace only by a render that writes trans.
  */
 gsr_status gsr_backward_render(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
                                const gsr_camera_out* fwd, const gsr_camera_grad* grad, int32_t accumulate,
@@ -382,7 +385,8 @@ gsr_status gsr_lidar_loss(const gsr_plan* plan, void* workspace, size_t workspac
  * centre, order key, opacity, intensity and rho.  fwd->trans and
  * fwd->n_contrib are required.  accumulate = 0 zeroes the record gradients
  * first.  Must follow gsr_preprocess / gsr_bin_sort / gsr_render_lidar (or
- * gsr_render_rig) of the same frame with the same workspace.  Another
+ * gsr_render_rig) of the same frame with the same workspace, that render
+ * writing trans and n_contrib (as for gsr_backward_render).  Another
  * sensor kind returns GSR_ERR_UNSUPPORTED.
  */
 gsr_status gsr_backward_render_lidar(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,

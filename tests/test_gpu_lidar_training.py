@@ -222,3 +222,67 @@ def test_lidar_gradient_finite_differences_on_gpu(gpu_lib):
         ad = float((g[name] * v).sum())
         print(name, "fd", fd, "ad", ad)
         assert ad == pytest.approx(fd, rel=5e-2, abs=2e-5), name
+
+
+def test_lidar_backward_full_size_step(gpu_lib):
+    """2M surfels, one 128x1800 LiDAR (the LiDAR training-step workload):
+    loss deterministic, gradients finite, exactly zero for surfels no beam's
+    list holds, and a directional difference along the opacity gradient."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, lidar_backward, lidar_loss
+    s = synth.driving_scene(n=2_000_000, seed=synth.SEED_BASE + 3)
+    s.ray_drop = np.random.default_rng(synth.SEED_BASE + 31).normal(0.0, 1.0, s.n).astype(np.float32)
+    tgt = synth.perturbed(s, seed=synth.SEED_BASE + 30)
+    tgt.ray_drop = s.ray_drop
+    lid = synth.spinning_lidar(128, 1800, -25.0, 15.0, (0.0, 0.0, 1.8))
+    r = Renderer(s.n, [lid], tiles=[(8, 8)], outputs=("range", "intensity", "alpha", "trans", "drop", "n_contrib"))
+    r.render(DeviceSurfels.from_host(tgt))
+    o = r.out[0]
+    t_range = torch.where(o["alpha"] >= 0.5, o["range"], torch.zeros_like(o["range"]))
+    t_int = o["intensity"].clone()
+    assert 0.05 < float((t_range > 0).float().mean()) < 0.95
+    d = DeviceSurfels.from_host(s)
+    r.render(d)
+    loss, lo = lidar_loss(r, 0, t_range, t_int)
+    L1 = float(loss[0])
+    g = lidar_backward(r, 0, lo.struct(), d)
+    r.render(d)
+    assert float(lidar_loss(r, 0, t_range, t_int)[0][0]) == L1
+    for k, v in g.items():
+        assert torch.isfinite(v).all(), k
+    counts = r.region(2, torch.int32)[: s.n]
+    invisible = counts == 0
+    assert invisible.any()
+    for k in ("pos", "opacity", "intensity", "ray_drop"):
+        assert (g[k][invisible] == 0).all(), k
+    gop = g["opacity"]
+    v = gop / gop.norm()
+    h = 0.05
+
+    def loss_with(op):
+        dd = DeviceSurfels(d.pos, d.log_scale, d.quat, op.contiguous(), d.sh, d.intensity, ray_drop=d.ray_drop)
+        r.render(dd)
+        return float(lidar_loss(r, 0, t_range, t_int)[0][0])
+    fd = (loss_with(d.opacity + h * v) - loss_with(d.opacity - h * v)) / (2 * h)
+    ad = float((gop * v).sum())
+    print("LiDAR full-size directional derivative fd", fd, "ad", ad)
+    assert ad == pytest.approx(fd, rel=0.1)
+
+
+def test_render_without_trans_keeps_outputs(gpu_lib):
+    """A render that does not write the final T skips keeping the per-chunk
+    states of split lists; its other outputs are bit-identical (camera +
+    LiDAR, split lists on both)."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
+    s = _scene(n=SPLIT_N)
+    sensors = [synth.pinhole(64, 48, 40.0, (0.0, 0.0, 1.5), yaw_deg=5.0, pitch_deg=-12.0), _lidar(SPLIT_COLUMNS)]
+    d = DeviceSurfels.from_host(s)
+    res = []
+    for outs in (("rgb", "depth", "alpha", "range", "intensity", "drop", "trans"),
+                 ("rgb", "depth", "alpha", "range", "intensity", "drop")):
+        r = Renderer(s.n, sensors, tiles=[(16, 8), (32, 4)], split=SPLIT, lidar_split=SPLIT, max_dup=1 << 18,
+                     outputs=outs)
+        r.render(d)
+        res.append([{k: v.cpu() for k, v in o.items() if k != "trans"} for o in r.out])
+    for a, b in zip(*res):
+        for k in a:
+            assert torch.equal(a[k], b[k]), k

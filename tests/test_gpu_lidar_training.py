@@ -18,7 +18,7 @@ import pytest
 import torch
 
 from oracle import grad as OG
-from paper_2503_11731_gb300 import synth
+from paper_2503_11731_gb300 import gsr, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -286,3 +286,55 @@ def test_render_without_trans_keeps_outputs(gpu_lib):
     for a, b in zip(*res):
         for k in a:
             assert torch.equal(a[k], b[k]), k
+
+
+def test_lidar_distillation_trains_the_lidar_head(gpu_lib):
+    """The LiDAR scene G^L learned end to end by the project's kernels:
+    decode (LiDAR head, BF16 tcgen05) -> LiDAR render -> gsr_lidar_loss ->
+    LiDAR backward -> decode backward -> Adam, against scans of an explicit
+    scene with ray-drop logits; the loss falls on the training poses and on
+    held-out poses."""
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, lidar_backward, lidar_loss
+    from paper_2503_11731_gb300.neural import DeviceAnchors, NeuralModel
+    s = synth.driving_scene(n=20_000, seed=81, x_range=(0.0, 30.0), n_boxes=4)
+    s.ray_drop = np.random.default_rng(82).normal(0.0, 1.5, s.n).astype(np.float32)
+    a, order = synth.anchors_from_surfels(s, k=10, seed=82)
+    rng = np.random.default_rng(6)
+    lids = [synth.spinning_lidar(32, 512, -25.0, 10.0, (rng.uniform(5, 25), rng.uniform(-1, 1), 1.8))
+            for _ in range(8)]
+    ds = DeviceSurfels.from_host(s)
+    targets = []
+    for lid in lids:
+        r = Renderer(s.n, [lid], tiles=[(8, 8)], outputs=("range", "intensity", "alpha"), max_dup=1 << 22)
+        o = r.render(ds)[0]
+        targets.append((torch.where(o["alpha"] >= 0.5, o["range"], torch.zeros_like(o["range"])),
+                        o["intensity"].clone()))
+    da = DeviceAnchors(a)
+    m = NeuralModel(*synth.init_lidar_mlp(7), head=gsr.HEAD_LIDAR)
+    outs = ("range", "intensity", "alpha", "trans", "drop", "n_contrib")
+    rends = [Renderer(a.n * a.k, [lid], tiles=[(8, 8)], outputs=outs, max_dup=1 << 22) for lid in lids]
+    origin = lambda lid: -lid.world_to_sensor[:3, :3].T @ lid.world_to_sensor[:3, 3]
+
+    def loss_at(i):
+        t = m.decode(da, origin(lids[i]))
+        rends[i].render(t)
+        return float(lidar_loss(rends[i], 0, *targets[i])[0][0])
+    held = [6, 7]
+    before = np.mean([loss_at(i) for i in held])
+    losses = []
+    for step in range(240):
+        i = step % 6
+        t = m.decode(da, origin(lids[i]))
+        rends[i].render(t)
+        loss, lo = lidar_loss(rends[i], 0, *targets[i])
+        g = lidar_backward(rends[i], 0, lo.struct(), t)
+        m.zero_grads(da)
+        m.backward(da, origin(lids[i]), g)
+        m.adam_step(da, lr=3e-3, lr_feature=1e-2)
+        losses.append(float(loss[0]))
+    after = np.mean([loss_at(i) for i in held])
+    print(f"LiDAR distillation: train loss {np.mean(losses[:6]):.4f} -> {np.mean(losses[-6:]):.4f}, "
+          f"held-out {before:.4f} -> {after:.4f}")
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-6:]) < 0.8 * np.mean(losses[:6])
+    assert after < 0.9 * before

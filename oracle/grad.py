@@ -1,5 +1,6 @@
-"""PyTorch FP64 CPU oracle: the forward render of Eqs. 1-3 written as tensor
-ops, the reconstruction loss, and their exact gradient by autograd.
+"""PyTorch FP64 CPU oracle: the forward render of Eqs. 1-5 (pinhole,
+cylindrical camera, spinning LiDAR) written as tensor ops, the camera and
+LiDAR losses, and their exact gradients by autograd.
 
 TEST INFRASTRUCTURE, NOT PRODUCT CODE: only tests, the smoke check and the
 benchmark's CPU-baseline leg use it; it never imports the CUDA package.
@@ -19,7 +20,9 @@ Loss of the backward step (2DGS regularisers; the weights and forms are readings
         N = sum w n (rendered normal, unnormalised); N_d = normalise(dY x dX)
         of the back-projected expected depth B/A by central differences at the
         4 neighbours; m = 1 on interior pixels whose 4 neighbours have A >= 0.5
-        and where |dY x dX| > 0, else 0.
+        and where |dY x dX| > 0, else 0.  A pinhole pixel back-projects to
+        B/A x ((x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1); a cylindrical one
+        (whose depth is the horizontal distance) to B/A x (sin phi, y_n, cos phi).
 """
 from __future__ import annotations
 
@@ -181,6 +184,100 @@ def render_pinhole(p, cam, bg=(0.0, 0.0, 0.0)):
             "n_contrib": contrib.sum(1).reshape(shp)}
 
 
+def render_cylindrical(p, cam, bg=(0.0, 0.0, 0.0)):
+    """Brute-force FP64 cylindrical camera frame (Eq. 4), the torch twin of
+    the C oracle's cylindrical render for gradients.
+
+    Pixel (x, y): azimuth phi = (x + 1/2 - cx)/fx about the camera's y axis,
+    height y_n = (y + 1/2 - cy)/fy on the unit cylinder; planes
+    h_u = (cos phi, 0, -sin phi, 0) and h_v = (y_n sin phi, -1, y_n cos phi, 0)
+    in the camera frame (W = [R|t]); depth = the intersection's horizontal
+    distance (rejected at or below near); the low-pass disc and the centre
+    (cx + fx atan2(x_c, z_c), cy + fy y_c / r_c) are in pixels; the order key
+    and low-pass depth are the centre's horizontal distance r_c.  Colour and
+    normal as render_pinhole.  Same outputs as render_pinhole.
+    """
+    Wimg, Himg = cam.width, cam.height
+    w2c = torch.tensor(cam.world_to_sensor, dtype=DT)
+    Rs, ts = w2c[:3, :3], w2c[:3, 3]
+    origin = -(Rs.T @ ts)
+    R = _quat_to_rot(p["quat"])
+    s = torch.exp(p["log_scale"])
+    mu = p["pos"]
+    N = mu.shape[0]
+    H = torch.zeros(N, 4, 3, dtype=DT)
+    H[:, :3, 0] = s[:, 0:1] * R[:, :, 0]
+    H[:, :3, 1] = s[:, 1:2] * R[:, :, 1]
+    H[:, :3, 2] = mu
+    H[:, 3, 2] = 1.0
+    Rt = torch.eye(4, dtype=DT)
+    Rt[:3, :] = w2c[:3, :]
+    WH = Rt @ H
+    ms = mu @ Rs.T + ts
+    rc = torch.sqrt(ms[:, 0] ** 2 + ms[:, 2] ** 2)
+    keep = rc > cam.near
+    idx = torch.nonzero(keep).flatten()
+    order = idx[torch.sort(rc[idx].detach(), stable=True).indices]
+    WH, rc, ms_o, mu_o, R_o = WH[order], rc[order], ms[order], mu[order], R[order]
+    o = torch.sigmoid(p["opacity"][order])
+    c0 = cam.cx + cam.fx * torch.atan2(ms_o[:, 0], ms_o[:, 2])
+    c1 = cam.cy + cam.fy * ms_o[:, 1] / rc
+    vd = mu_o - origin
+    vd = vd / vd.norm(dim=-1, keepdim=True)
+    deg = int(round(math.sqrt(p["sh"].shape[1]))) - 1
+    Y = sh_basis(deg, vd)
+    col = torch.clamp((Y[:, :, None] * p["sh"][order]).sum(1) + 0.5, min=0.0)
+    nw = R_o[:, :, 2]
+    flip = ((nw * vd).sum(-1) > 0).to(DT) * -2 + 1
+    nc = (nw * flip[:, None]) @ Rs.T
+
+    ys, xs = torch.meshgrid(torch.arange(Himg, dtype=DT), torch.arange(Wimg, dtype=DT), indexing="ij")
+    px = (xs + 0.5).reshape(-1, 1)
+    py = (ys + 0.5).reshape(-1, 1)
+    phi = (px - cam.cx) / cam.fx
+    yn = (py - cam.cy) / cam.fy
+    zero = torch.zeros_like(phi)
+    hu = torch.stack([torch.cos(phi), zero, -torch.sin(phi), zero], -1)  # [P,1,4]
+    hv = torch.stack([yn * torch.sin(phi), -torch.ones_like(phi), yn * torch.cos(phi), zero], -1)
+    dh = torch.stack([torch.sin(phi), zero, torch.cos(phi)], -1)  # horizontal part of the ray
+    k = (hu[:, :, :, None] * WH[None]).sum(2)
+    l = (hv[:, :, :, None] * WH[None]).sum(2)
+    m = torch.cross(k, l, dim=-1)
+    has = m[..., 2] != 0
+    m2 = torch.where(has, m[..., 2], torch.ones_like(m[..., 2]))
+    u = m[..., 0] / m2
+    v = m[..., 1] / m2
+    x3 = WH[None, :, :3, 0] * u[..., None] + WH[None, :, :3, 1] * v[..., None] + WH[None, :, :3, 2]
+    zint = (x3 * dh).sum(-1)
+    rho3 = u * u + v * v
+    v3 = has & (zint > cam.near) & (rho3 <= 9.0)
+    dx = px - c0[None, :]
+    dy = py - c1[None, :]
+    rholp = (dx * dx + dy * dy) / 0.5
+    vlp = rholp <= 9.0
+    use3 = v3 & (~vlp | (rho3 <= rholp))
+    valid = v3 | vlp
+    rho = torch.where(use3, rho3, torch.where(vlp, rholp, torch.full_like(rholp, 100.0)))
+    G = torch.exp(-0.5 * rho)
+    a = torch.clamp(o[None, :] * G, max=0.99)
+    a = torch.where(valid, a, torch.zeros_like(a))
+    z = torch.where(use3, zint, rc[None, :].expand_as(zint))
+    skip = a < (1.0 / 255.0)
+    a_eff = torch.where(skip, torch.zeros_like(a), a)
+    one_m = 1.0 - a_eff
+    Tb = torch.cumprod(torch.cat([torch.ones_like(one_m[:, :1]), one_m[:, :-1]], 1), 1)
+    stop = (~skip) & (Tb.detach() * (1.0 - a.detach()) < 1e-4)
+    stopped = torch.cumsum(stop.to(torch.int64), 1) > 0
+    contrib = (~skip) & (~stopped)
+    wgt = torch.where(contrib, a_eff * Tb, torch.zeros_like(a))
+    Tfin = torch.prod(torch.where(contrib, 1.0 - a_eff, torch.ones_like(a)), 1)
+    shp = (Himg, Wimg)
+    rgb = wgt @ col + Tfin[:, None] * torch.tensor(bg, dtype=DT)[None, :]
+    return {"rgb": rgb.reshape(shp + (3,)), "A": wgt.sum(1).reshape(shp), "B": (wgt * z).sum(1).reshape(shp),
+            "D": (wgt * z * z).sum(1).reshape(shp), "normal": (wgt @ nc).reshape(shp + (3,)),
+            "T": Tfin.reshape(shp), "n_contrib": contrib.sum(1).reshape(shp)}
+
+
 def render_lidar(p, lid):
     """Brute-force FP64 LiDAR range image (Eq. 5), the torch twin of the C
     oracle's LiDAR render for gradients.
@@ -302,7 +399,13 @@ def loss(out, target_rgb, cam, w_dist=0.1, w_norm=0.05, mask_alpha=0.5):
     Asafe = torch.where(A > 0, A, torch.ones_like(A))
     Dbar = torch.where(A > 0, B / Asafe, torch.zeros_like(A))
     ys, xs = torch.meshgrid(torch.arange(Hh, dtype=DT), torch.arange(Ww, dtype=DT), indexing="ij")
-    X = torch.stack([(xs + 0.5 - cam.cx) / cam.fx * Dbar, (ys + 0.5 - cam.cy) / cam.fy * Dbar, Dbar], -1)
+    if getattr(cam, "kind", "pinhole") == "cylindrical":
+        # back-projection along the pixel's Eq. 4 ray; the depth is the
+        # horizontal distance, so the point is depth x (sin phi, y_n, cos phi)
+        phi = (xs + 0.5 - cam.cx) / cam.fx
+        X = torch.stack([torch.sin(phi) * Dbar, (ys + 0.5 - cam.cy) / cam.fy * Dbar, torch.cos(phi) * Dbar], -1)
+    else:
+        X = torch.stack([(xs + 0.5 - cam.cx) / cam.fx * Dbar, (ys + 0.5 - cam.cy) / cam.fy * Dbar, Dbar], -1)
     dX = X[1:-1, 2:] - X[1:-1, :-2]
     dY = X[2:, 1:-1] - X[:-2, 1:-1]
     cr = torch.cross(dY, dX, dim=-1)
@@ -317,9 +420,11 @@ def loss(out, target_rgb, cam, w_dist=0.1, w_norm=0.05, mask_alpha=0.5):
 
 
 def loss_and_grad(s, cam, target_rgb, bg=(0.0, 0.0, 0.0)):
-    """FP64 loss and its exact gradient w.r.t. pos, log_scale, quat, opacity, sh."""
+    """FP64 loss and its exact gradient w.r.t. pos, log_scale, quat, opacity,
+    sh (pinhole or cylindrical camera)."""
     p = surfel_tensors(s, requires_grad=True)
-    out = render_pinhole(p, cam, bg)
+    render = render_cylindrical if getattr(cam, "kind", "pinhole") == "cylindrical" else render_pinhole
+    out = render(p, cam, bg)
     L, parts = loss(out, torch.as_tensor(target_rgb, dtype=DT), cam)
     L.backward()
     return float(L.detach()), {k: v.grad.numpy().copy() for k, v in p.items()}, {k: float(v.detach()) for k, v in parts.items()}

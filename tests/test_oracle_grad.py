@@ -179,3 +179,88 @@ def test_lidar_loss_worked_example():
     assert float(OG.lidar_loss(one, [0.0], [0.0])[0]) == pytest.approx(-0.1 * math.log(1 - 2.0 ** -20))
     # a sure drop where the target has a return costs the clamped -log(2^-20)
     assert float(OG.lidar_loss(one, [5.0], [0.0])[3]) == pytest.approx(0.1 * 20 * math.log(2.0))
+
+
+def _cyl_scene(seed):
+    s = synth.driving_scene(n=200, seed=seed, x_range=(-6.0, 14.0), n_boxes=2)
+    f = lambda a: np.asarray(a, np.float64)
+    sh = f(s.sh)[:, :4]  # SH degree 1
+    return synth.Surfels(f(s.pos), f(s.log_scale) + 0.6, f(s.quat), f(s.opacity), sh, f(s.intensity))
+
+
+def _cyl_cam():
+    return synth.cylindrical(48, 20, 200.0, 50.0, (0.0, 0.0, 1.5), pitch_deg=-10.0)
+
+
+@pytest.mark.parametrize("seed", [9, 10])
+def test_cylindrical_render_vjp_matches_fd_of_c_oracle(seed):
+    """Eq. 4 cylindrical render: autograd VJP == central FD of the C oracle."""
+    s, cam = _cyl_scene(seed), _cyl_cam()
+    rng = np.random.default_rng(seed + 100)
+    outs = _c_outputs(s, cam)
+    assert (outs["A"] > 0.5).mean() > 0.1
+    weights = {k: rng.normal(size=v.shape) for k, v in outs.items()}
+    weights["B"] *= 0.05
+    weights["D"] *= 0.002
+    p = OG.surfel_tensors(s, requires_grad=True)
+    t = OG.render_cylindrical(p, cam, bg=(0.1, 0.2, 0.3))
+    tot = sum((torch.as_tensor(weights[k]) * t[k]).sum() for k in weights)
+    tot.backward()
+    h = 1e-6
+    for name in ("pos", "log_scale", "quat", "opacity", "sh"):
+        v = rng.normal(size=getattr(s, name).shape)
+        base = getattr(s, name)
+        fp = _c_outputs(_with(s, name, base + h * v), cam)
+        fm = _c_outputs(_with(s, name, base - h * v), cam)
+        fd = sum(((weights[k] * (fp[k] - fm[k])).sum() for k in weights)) / (2 * h)
+        ad = float((p[name].grad.numpy() * v).sum())
+        assert ad == pytest.approx(fd, rel=2e-5, abs=1e-6), name
+
+
+def test_cylindrical_loss_gradient_matches_fd():
+    """Full camera loss (L1 + distortion + normal consistency through the
+    cylindrical back-projection) through the C render."""
+    s, cam = _cyl_scene(12), _cyl_cam()
+    rng = np.random.default_rng(6)
+    target = rng.uniform(0, 1, (cam.height, cam.width, 3))
+    L, g, parts = OG.loss_and_grad(s, cam, target, bg=(0.1, 0.2, 0.3))
+    assert parts["normal"] > 0 and parts["dist"] > 0
+
+    def c_loss(ss):
+        o = _c_outputs(ss, cam)
+        out = {k: torch.as_tensor(o[k]) for k in ("rgb", "A", "B", "D", "normal")}
+        return float(OG.loss(out, torch.as_tensor(target), cam)[0])
+    assert c_loss(s) == pytest.approx(L, rel=1e-12)
+    h = 1e-6
+    for name in ("pos", "log_scale", "quat", "opacity", "sh"):
+        v = rng.normal(size=getattr(s, name).shape)
+        base = getattr(s, name)
+        fd = (c_loss(_with(s, name, base + h * v)) - c_loss(_with(s, name, base - h * v))) / (2 * h)
+        ad = float((g[name] * v).sum())
+        assert ad == pytest.approx(fd, rel=1e-4, abs=1e-7), name
+
+
+def test_depth_normal_of_a_plane_cylindrical():
+    """A plane n.X = c seen by a cylindrical camera: the depth (horizontal
+    distance) of pixel (x, y) is c / (d . n) with d = (sin phi, y_n, cos phi);
+    its back-projection lies on the plane, so N_d = n at every interior
+    pixel and the normal term vanishes for the rendered normal n."""
+    W, H = 40, 16
+    cam = synth.Cylindrical(W, H, W / math.radians(120.0), 20.0, W / 2, H / 2, np.eye(4), 0.2)
+    n = np.array([0.2, -0.3, -1.0])
+    n /= np.linalg.norm(n)
+    c = -6.0
+    ys, xs = np.mgrid[0:H, 0:W]
+    phi = (xs + 0.5 - cam.cx) / cam.fx
+    d = np.stack([np.sin(phi), (ys + 0.5 - cam.cy) / cam.fy, np.cos(phi)], -1)
+    Z = c / (d @ n)
+    assert (Z > 0).all()
+    out = {"rgb": torch.zeros(H, W, 3, dtype=torch.float64), "A": torch.ones(H, W, dtype=torch.float64),
+           "B": torch.as_tensor(Z), "D": torch.as_tensor(Z * Z),
+           "normal": torch.as_tensor(np.broadcast_to(n, (H, W, 3)).copy())}
+    _, parts = OG.loss(out, torch.zeros(H, W, 3, dtype=torch.float64), cam)
+    assert float(parts["normal"]) == pytest.approx(0.0, abs=1e-12)
+    # the pinhole back-projection of the same depths is not planar
+    pin = synth.Pinhole(W, H, cam.fx, cam.fy, cam.cx, cam.cy, np.eye(4), 0.2)
+    _, parts_pin = OG.loss(out, torch.zeros(H, W, 3, dtype=torch.float64), pin)
+    assert float(parts_pin["normal"]) > 1e-3

@@ -326,19 +326,23 @@ gsr_status gsr_render_lidar(const gsr_plan* plan, const void* workspace, size_t 
  *     + w_normal * sum_px m (1 - N . N_d) / (H W)
  * N = sum w n; N_d = normalise(dY x dX) of the back-projected expected depth
  * B/A by central differences at the 4 neighbours; m = 1 on interior pixels
- * whose 4 neighbours have A >= mask_alpha and |dY x dX| > 0.
+ * whose 4 neighbours have A >= mask_alpha and |dY x dX| > 0.  A pinhole
+ * pixel back-projects to B/A ((x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1), a
+ * cylindrical one (Eq. 4; its depth is the horizontal distance) to
+ * B/A (sin phi, y_n, cos phi).
  * Writes loss[0..3] = (L, L1 term, distortion term, normal term) (DEVICE
  * float[4]) and the per-pixel gradients into *grad (all four planes
  * required; overwritten).  Uses workspace scratch; deterministic.  Pinhole
- * cameras only (the back-projection of N_d is the pinhole's): another
- * sensor kind returns GSR_ERR_UNSUPPORTED.
+ * and cylindrical cameras; a LiDAR returns GSR_ERR_UNSUPPORTED (its loss is
+ * gsr_lidar_loss).
  */
 gsr_status gsr_loss(const gsr_plan* plan, void* workspace, size_t workspace_bytes, int32_t sensor,
                     const gsr_camera_out* fwd, const float* target_rgb, const gsr_loss_weights* weights,
                     float* loss, const gsr_camera_grad* grad, void* stream);
 
 /*
- * Reverse-order backward rasteriser of camera `sensor`: each pixel walks its
+ * Reverse-order backward rasteriser of camera `sensor` (pinhole or
+ * cylindrical; a LiDAR returns GSR_ERR_UNSUPPORTED): each pixel walks its
  * tile list from its last contributor (fwd->n_contrib) back to the front,
  * recovering T_i = T_{i+1} / (1 - alpha_i) from the final T (fwd->trans;
  * no per-pixel lists are stored), and accumulates d(loss)/d(record) --
@@ -398,8 +402,9 @@ gsr_status gsr_backward_render_lidar(const gsr_plan* plan, void* workspace, size
  * parameters (pos, log_scale, quat, opacity logit, SH, incl. the view
  * direction of the SH colour; for LiDAR records also intensity and the
  * ray-drop logit, out->intensity / out->ray_drop when not NULL),
- * accumulating into *out.  Pinhole and LiDAR sensors (a cylindrical
- * sensor's records have no backward and contribute nothing).
+ * accumulating into *out.  Every sensor model: pinhole (Eq. 3 Jacobian),
+ * cylindrical and LiDAR (the adjugate of M = [a b ms] and the centre's
+ * angles).
  */
 gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, size_t workspace_bytes,
                                    const gsr_surfels* surfels, const gsr_objects* objects,
@@ -417,7 +422,7 @@ gsr_status gsr_backward_preprocess(const gsr_plan* plan, const void* workspace, 
  * block partial sums) lives in one fixed array in the library's own device
  * memory, sized for GSR_NOALLOC_MAX_PIXELS pixels (48 MiB + 96 KiB); every
  * GPU that loads the library holds that array until the process exits.
- * camera: the pinhole descriptor (host); fwd->rgb, alpha, depth_acc, normal,
+ * camera: the pinhole or cylindrical descriptor (host); fwd->rgb, alpha, depth_acc, normal,
  * target_rgb, loss[4] and all four planes of *grad as for gsr_loss.
  * Errors: GSR_ERR_TOO_LARGE if width * height > GSR_NOALLOC_MAX_PIXELS;
  * GSR_ERR_INVALID_ARG / GSR_ERR_UNSUPPORTED as for gsr_loss.

@@ -383,7 +383,8 @@ extern "C" size_t gsr_struct_size(int32_t which)
 static gsr_status check_camera(const gsr_plan* plan, int32_t sensor)
 {
     if (sensor < 0 || sensor >= plan->n_sensors) return GSR_ERR_INVALID_ARG;
-    if (plan->sensors[sensor].kind != GSR_SENSOR_PINHOLE) return GSR_ERR_UNSUPPORTED;
+    const int32_t kind = plan->sensors[sensor].kind;
+    if (kind != GSR_SENSOR_PINHOLE && kind != GSR_SENSOR_CYLINDRICAL) return GSR_ERR_UNSUPPORTED;
     return GSR_OK;
 }
 

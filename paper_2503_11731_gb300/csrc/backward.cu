@@ -47,9 +47,26 @@ struct LossArgs {
     float* scratch;        // [6][H][W]: dL/d(dX), dL/d(dY) per pixel
     float* partial;        // [blocks][3]
     int W, H;
+    int cyl;               // 1: cylindrical camera (Eq. 4), 0: pinhole
     float fx, fy, cx, cy;
     float w_dist, w_norm, mask_alpha;
 };
+
+// Direction whose multiple by the rendered depth is the back-projected point
+// of pixel (x, y): pinhole ((x + 1/2 - cx)/fx, (y + 1/2 - cy)/fy, 1);
+// cylindrical (sin phi, y_n, cos phi), its depth being the horizontal distance.
+__device__ __forceinline__ void backproject_dir(const LossArgs& a, int x, int y, float* d)
+{
+    const float u = (x + 0.5f - a.cx) / a.fx, v = (y + 0.5f - a.cy) / a.fy;
+    if (a.cyl) {
+        sincosf(u, &d[0], &d[2]);
+        d[1] = v;
+    } else {
+        d[0] = u;
+        d[1] = v;
+        d[2] = 1.f;
+    }
+}
 
 // Pass 1: per-pixel terms, the direct gradients, and the gradient of the
 // normal term w.r.t. the two central differences of this pixel.
@@ -84,9 +101,11 @@ __global__ void __launch_bounds__(256) k_loss_pixel(LossArgs a)
                 const float Aq = a.alpha[qs[k]];
                 ok = ok && (Aq >= a.mask_alpha);
                 const float Db = Aq > 0.f ? a.dacc[qs[k]] / Aq : 0.f;
-                X[k][0] = (qx[k] + 0.5f - a.cx) / a.fx * Db;
-                X[k][1] = (qy[k] + 0.5f - a.cy) / a.fy * Db;
-                X[k][2] = Db;
+                float dir[3];
+                backproject_dir(a, qx[k], qy[k], dir);
+                X[k][0] = dir[0] * Db;
+                X[k][1] = dir[1] * Db;
+                X[k][2] = dir[2] * Db;
             }
             const float dX[3] = {X[1][0] - X[0][0], X[1][1] - X[0][1], X[1][2] - X[0][2]};
             const float dY[3] = {X[3][0] - X[2][0], X[3][1] - X[2][1], X[3][2] - X[2][2]};
@@ -159,7 +178,9 @@ __global__ void __launch_bounds__(256) k_loss_gather(LossArgs a)
     }
     const float A = a.alpha[p];
     if (A > 0.f) {
-        const float gD = gX[0] * (x + 0.5f - a.cx) / a.fx + gX[1] * (y + 0.5f - a.cy) / a.fy + gX[2];
+        float dir[3];
+        backproject_dir(a, x, y, dir);
+        const float gD = gX[0] * dir[0] + gX[1] * dir[1] + gX[2] * dir[2];
         const float B = a.dacc[p];
         a.g_dacc[p] += gD / A;
         a.g_alpha[p] += -gD * B / (A * A);
@@ -503,7 +524,7 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
                     const float io = 1.f / om;
                     float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
                     float c[3] = {r3.y, r3.z, r3.w};
-                    if (KIND == GSR_SENSOR_PINHOLE) {
+                    if (KIND != GSR_SENSOR_LIDAR) {  // camera: colour and normal
                         const float n[3] = {r4.x, r4.y, r4.z};
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
@@ -722,6 +743,42 @@ __device__ __forceinline__ void sh_basis_grad(int deg, V3 d, float* b, V3* gb)
     gb[15] = v3(C3a * (3.f * xx - 3.f * yy), -6.f * C3a * x * y, 0.f);
 }
 
+// Backward of the ray-direction record (LiDAR and cylindrical camera):
+// M = [a b ms] (columns), Q = adj(M) (the record's rows r0..r2 .xyz), det(M)
+// (r2.w).  Each entry of the adjugate is a 2x2 minor of M, and the
+// derivative of det(M) w.r.t. m_ij is its cofactor, adj(M)_ji.
+__device__ __forceinline__ void adjugate_backward(V3 a, V3 b, V3 ms, float4 G0, float4 G1, float4 G2, V3& gA,
+                                                  V3& gB, V3& g_ms)
+{
+    const float m00 = a.x, m01 = b.x, m02 = ms.x;
+    const float m10 = a.y, m11 = b.y, m12 = ms.y;
+    const float m20 = a.z, m21 = b.z, m22 = ms.z;
+    const float gq00 = G0.x, gq01 = G0.y, gq02 = G0.z, gq10 = G1.x, gq11 = G1.y, gq12 = G1.z;
+    const float gq20 = G2.x, gq21 = G2.y, gq22 = G2.z, g_det = G2.w;
+    float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f, g20 = 0.f, g21 = 0.f, g22 = 0.f;
+    g11 += gq00 * m22; g22 += gq00 * m11; g12 -= gq00 * m21; g21 -= gq00 * m12;  // q00 = m11 m22 - m12 m21
+    g02 += gq01 * m21; g21 += gq01 * m02; g01 -= gq01 * m22; g22 -= gq01 * m01;  // q01 = m02 m21 - m01 m22
+    g01 += gq02 * m12; g12 += gq02 * m01; g02 -= gq02 * m11; g11 -= gq02 * m02;  // q02 = m01 m12 - m02 m11
+    g12 += gq10 * m20; g20 += gq10 * m12; g10 -= gq10 * m22; g22 -= gq10 * m10;  // q10 = m12 m20 - m10 m22
+    g00 += gq11 * m22; g22 += gq11 * m00; g02 -= gq11 * m20; g20 -= gq11 * m02;  // q11 = m00 m22 - m02 m20
+    g02 += gq12 * m10; g10 += gq12 * m02; g00 -= gq12 * m12; g12 -= gq12 * m00;  // q12 = m02 m10 - m00 m12
+    g10 += gq20 * m21; g21 += gq20 * m10; g11 -= gq20 * m20; g20 -= gq20 * m11;  // q20 = m10 m21 - m11 m20
+    g01 += gq21 * m20; g20 += gq21 * m01; g00 -= gq21 * m21; g21 -= gq21 * m00;  // q21 = m01 m20 - m00 m21
+    g00 += gq22 * m11; g11 += gq22 * m00; g01 -= gq22 * m10; g10 -= gq22 * m01;  // q22 = m00 m11 - m01 m10
+    g00 += g_det * fmaf(m11, m22, -m12 * m21);
+    g01 += g_det * fmaf(m12, m20, -m10 * m22);
+    g02 += g_det * fmaf(m10, m21, -m11 * m20);
+    g10 += g_det * fmaf(m02, m21, -m01 * m22);
+    g11 += g_det * fmaf(m00, m22, -m02 * m20);
+    g12 += g_det * fmaf(m01, m20, -m00 * m21);
+    g20 += g_det * fmaf(m01, m12, -m02 * m11);
+    g21 += g_det * fmaf(m02, m10, -m00 * m12);
+    g22 += g_det * fmaf(m00, m11, -m01 * m10);
+    gA = v3(g00, g10, g20);
+    gB = v3(g01, g11, g21);
+    g_ms = v3(g02, g12, g22);
+}
+
 }  // namespace
 
 struct PreBwdArgs {
@@ -789,10 +846,11 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, Pr
         const float flip = dot(nw, vd) > 0.f ? -1.f : 1.f;
         // normal: n_s = R (flip nw)
         g_nw = g_nw + flip * mulT(sd.R, v3(G4.x, G4.y, G4.z));
+        const V3 ms = mul(sd.R, mu) + v3(sd.t[0], sd.t[1], sd.t[2]);
+        const V3 Rtu = mul(sd.R, tu), Rtv = mul(sd.R, tv);
+        const V3 A = su * Rtu, B = sv * Rtv;
+        V3 gA, gB, g_ms;
         if (sd.kind == GSR_SENSOR_PINHOLE) {
-            const V3 ms = mul(sd.R, mu) + v3(sd.t[0], sd.t[1], sd.t[2]);
-            const V3 Rtu = mul(sd.R, tu), Rtv = mul(sd.R, tv);
-            const V3 A = su * Rtu, B = sv * Rtv;
             const float iz = 1.f / ms.z;
             const float ex = ms.x * iz, ey = ms.y * iz;
             const float m00 = sd.fx * (A.x - ex * A.z), m01 = sd.fx * (B.x - ex * B.z);
@@ -808,95 +866,76 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(SensorTable tab, Pr
             g01 += G2.y * m20 * iz; g20 += G2.y * m01 * iz; g00 -= G2.y * m21 * iz; g21 -= G2.y * m00 * iz;
             g00 += g_det * m11; g11 += g_det * m00; g01 -= g_det * m10; g10 -= g_det * m01;
             float g_ex = sd.fx * G0.w, g_ey = sd.fy * G1.w;
-            V3 gA = v3(sd.fx * g00, sd.fy * g10, -sd.fx * ex * g00 - sd.fy * ey * g10 + g20);
-            V3 gB = v3(sd.fx * g01, sd.fy * g11, -sd.fx * ex * g01 - sd.fy * ey * g11 + g21);
+            gA = v3(sd.fx * g00, sd.fy * g10, -sd.fx * ex * g00 - sd.fy * ey * g10 + g20);
+            gB = v3(sd.fx * g01, sd.fy * g11, -sd.fx * ex * g01 - sd.fy * ey * g11 + g21);
             g_ex -= sd.fx * (A.z * g00 + B.z * g01);
             g_ey -= sd.fy * (A.z * g10 + B.z * g11);
-            V3 g_ms = v3(g_ex * iz, g_ey * iz, G4.w);
+            g_ms = v3(g_ex * iz, g_ey * iz, G4.w);
             g_iz += g_ex * ms.x + g_ey * ms.y;
             g_ms.z += -g_iz * iz * iz;
-            g_mu = g_mu + mulT(sd.R, g_ms);
-            g_su += dot(Rtu, gA);
-            g_sv += dot(Rtv, gB);
-            g_tu = g_tu + su * mulT(sd.R, gA);
-            g_tv = g_tv + sv * mulT(sd.R, gB);
-            // colour: max(0, sum Y(d) c + 0.5), d = normalise(mu - origin) (object frame)
-            const float vlen = sqrtf(dot(vd, vd));
-            const V3 dw = (1.f / vlen) * vd;
-            const V3 dl = has_obj ? mulT(Ro, dw) : dw;
-            float b[16];
-            V3 gb[16];
-            sh_basis_grad(deg, dl, b, gb);
-            float raw[3] = {0.5f, 0.5f, 0.5f};
-            for (int k = 0; k < K; ++k)
-                for (int c = 0; c < 3; ++c) raw[c] += b[k] * sh[3 * k + c];
-            const float gcol[3] = {raw[0] > 0.f ? G3.y : 0.f, raw[1] > 0.f ? G3.z : 0.f, raw[2] > 0.f ? G3.w : 0.f};
-            V3 g_dl = v3(0, 0, 0);
-            for (int k = 0; k < K; ++k) {
-                float s = 0.f;
-                for (int c = 0; c < 3; ++c) {
-                    g_sh[3 * k + c] += b[k] * gcol[c];
-                    s += sh[3 * k + c] * gcol[c];
-                }
-                g_dl = g_dl + s * gb[k];
-            }
-            const V3 g_dw = has_obj ? mul(Ro, g_dl) : g_dl;
-            g_mu = g_mu + (1.f / vlen) * (g_dw - dot(dw, g_dw) * dw);
-        } else if (sd.kind == GSR_SENSOR_LIDAR) {
+        } else if (sd.kind == GSR_SENSOR_LIDAR || sd.kind == GSR_SENSOR_CYLINDRICAL) {
             // record: M = [a b ms] (columns), Q = adj(M) (rows r0..r2 .xyz),
-            // det(M), low-pass centre (column, row) of the centre's azimuth
-            // and elevation, order key |ms|
-            const V3 ms = mul(sd.R, mu) + v3(sd.t[0], sd.t[1], sd.t[2]);
-            const V3 Rtu = mul(sd.R, tu), Rtv = mul(sd.R, tv);
-            const V3 A = su * Rtu, B = sv * Rtv;
-            const float m00 = A.x, m01 = B.x, m02 = ms.x;
-            const float m10 = A.y, m11 = B.y, m12 = ms.y;
-            const float m20 = A.z, m21 = B.z, m22 = ms.z;
-            const float gq00 = G0.x, gq01 = G0.y, gq02 = G0.z, gq10 = G1.x, gq11 = G1.y, gq12 = G1.z;
-            const float gq20 = G2.x, gq21 = G2.y, gq22 = G2.z, g_det = G2.w;
-            // each entry of the adjugate is a 2x2 minor: d(m_ab m_cd - m_ef m_gh)
-            float g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f, g20 = 0.f, g21 = 0.f, g22 = 0.f;
-            g11 += gq00 * m22; g22 += gq00 * m11; g12 -= gq00 * m21; g21 -= gq00 * m12;  // q00 = m11 m22 - m12 m21
-            g02 += gq01 * m21; g21 += gq01 * m02; g01 -= gq01 * m22; g22 -= gq01 * m01;  // q01 = m02 m21 - m01 m22
-            g01 += gq02 * m12; g12 += gq02 * m01; g02 -= gq02 * m11; g11 -= gq02 * m02;  // q02 = m01 m12 - m02 m11
-            g12 += gq10 * m20; g20 += gq10 * m12; g10 -= gq10 * m22; g22 -= gq10 * m10;  // q10 = m12 m20 - m10 m22
-            g00 += gq11 * m22; g22 += gq11 * m00; g02 -= gq11 * m20; g20 -= gq11 * m02;  // q11 = m00 m22 - m02 m20
-            g02 += gq12 * m10; g10 += gq12 * m02; g00 -= gq12 * m12; g12 -= gq12 * m00;  // q12 = m02 m10 - m00 m12
-            g10 += gq20 * m21; g21 += gq20 * m10; g11 -= gq20 * m20; g20 -= gq20 * m11;  // q20 = m10 m21 - m11 m20
-            g01 += gq21 * m20; g20 += gq21 * m01; g00 -= gq21 * m21; g21 -= gq21 * m00;  // q21 = m01 m20 - m00 m21
-            g00 += gq22 * m11; g11 += gq22 * m00; g01 -= gq22 * m10; g10 -= gq22 * m01;  // q22 = m00 m11 - m01 m10
-            // d det / d m_ij is the cofactor of m_ij, i.e. adj(M)_ji
-            g00 += g_det * fmaf(m11, m22, -m12 * m21);
-            g01 += g_det * fmaf(m12, m20, -m10 * m22);
-            g02 += g_det * fmaf(m10, m21, -m11 * m20);
-            g10 += g_det * fmaf(m02, m21, -m01 * m22);
-            g11 += g_det * fmaf(m00, m22, -m02 * m20);
-            g12 += g_det * fmaf(m01, m20, -m00 * m21);
-            g20 += g_det * fmaf(m01, m12, -m02 * m11);
-            g21 += g_det * fmaf(m02, m10, -m00 * m12);
-            g22 += g_det * fmaf(m00, m11, -m01 * m10);
-            const V3 gA = v3(g00, g10, g20), gB = v3(g01, g11, g21);
-            V3 g_ms = v3(g02, g12, g22);
-            // centre column = (azimuth - az0) / d_az - 1/2, row = (el_max - elevation) / d_el
-            const float rxy2 = ms.x * ms.x + ms.y * ms.y;
-            const float rxy = sqrtf(rxy2);
-            const float rc2 = rxy2 + ms.z * ms.z;
-            const float rc = sqrtf(rc2);
-            const float gcol = G0.w * sd.inv_d_az, gel = -G1.w * sd.inv_d_el;
-            if (rxy2 > 0.f) {  // straight above or below the sensor the centre's angles have no gradient
-                g_ms.x += gcol * (-ms.y / rxy2) - gel * ms.z * ms.x / (rxy * rc2);
-                g_ms.y += gcol * (ms.x / rxy2) - gel * ms.z * ms.y / (rxy * rc2);
-                g_ms.z += gel * rxy / rc2;
+            // det(M), low-pass centre, order key
+            adjugate_backward(A, B, ms, G0, G1, G2, gA, gB, g_ms);
+            if (sd.kind == GSR_SENSOR_LIDAR) {
+                // centre column = (azimuth - az0) / d_az - 1/2, row = (el_max - elevation) / d_el,
+                // key |ms|
+                const float rxy2 = ms.x * ms.x + ms.y * ms.y;
+                const float rxy = sqrtf(rxy2);
+                const float rc2 = rxy2 + ms.z * ms.z;
+                const float rc = sqrtf(rc2);
+                const float gcol = G0.w * sd.inv_d_az, gel = -G1.w * sd.inv_d_el;
+                if (rxy2 > 0.f) {  // straight above or below the sensor the centre's angles have no gradient
+                    g_ms.x += gcol * (-ms.y / rxy2) - gel * ms.z * ms.x / (rxy * rc2);
+                    g_ms.y += gcol * (ms.x / rxy2) - gel * ms.z * ms.y / (rxy * rc2);
+                    g_ms.z += gel * rxy / rc2;
+                }
+                g_ms = g_ms + (G4.w / rc) * ms;
+            } else {
+                // centre (cx + fx atan2(x, z), cy + fy y / r_h), key r_h = |(x, z)|
+                const float rh2 = ms.x * ms.x + ms.z * ms.z;
+                const float rh = sqrtf(rh2);
+                const float gcx = G0.w * sd.fx, gcy = G1.w * sd.fy;
+                const float yr3 = ms.y / (rh2 * rh);
+                g_ms.x += gcx * ms.z / rh2 - gcy * yr3 * ms.x + G4.w * ms.x / rh;
+                g_ms.y += gcy / rh;
+                g_ms.z += -gcx * ms.x / rh2 - gcy * yr3 * ms.z + G4.w * ms.z / rh;
             }
-            g_ms = g_ms + (G4.w / rc) * ms;  // order key |ms|
-            g_mu = g_mu + mulT(sd.R, g_ms);
-            g_su += dot(Rtu, gA);
-            g_sv += dot(Rtv, gB);
-            g_tu = g_tu + su * mulT(sd.R, gA);
-            g_tv = g_tv + sv * mulT(sd.R, gB);
+        } else {
+            continue;
+        }
+        g_mu = g_mu + mulT(sd.R, g_ms);
+        g_su += dot(Rtu, gA);
+        g_sv += dot(Rtv, gB);
+        g_tu = g_tu + su * mulT(sd.R, gA);
+        g_tv = g_tv + sv * mulT(sd.R, gB);
+        if (sd.kind == GSR_SENSOR_LIDAR) {
             g_int += G3.y;  // intensity
             g_rd += G3.z;   // ray-drop probability
+            continue;
         }
+        // colour: max(0, sum Y(d) c + 0.5), d = normalise(mu - origin) (object frame)
+        const float vlen = sqrtf(dot(vd, vd));
+        const V3 dw = (1.f / vlen) * vd;
+        const V3 dl = has_obj ? mulT(Ro, dw) : dw;
+        float b[16];
+        V3 gb[16];
+        sh_basis_grad(deg, dl, b, gb);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c) raw[c] += b[k] * sh[3 * k + c];
+        const float gcol[3] = {raw[0] > 0.f ? G3.y : 0.f, raw[1] > 0.f ? G3.z : 0.f, raw[2] > 0.f ? G3.w : 0.f};
+        V3 g_dl = v3(0, 0, 0);
+        for (int k = 0; k < K; ++k) {
+            float sk = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                g_sh[3 * k + c] += b[k] * gcol[c];
+                sk += sh[3 * k + c] * gcol[c];
+            }
+            g_dl = g_dl + sk * gb[k];
+        }
+        const V3 g_dw = has_obj ? mul(Ro, g_dl) : g_dl;
+        g_mu = g_mu + (1.f / vlen) * (g_dw - dot(dw, g_dw) * dw);
     }
     if (!any) return;
     // opacity logit
@@ -954,6 +993,7 @@ cudaError_t launch_loss(const gsr_plan* p, void* ws, int sensor, const gsr_camer
     a.g_normal = g->normal;
     a.W = s.width;
     a.H = s.height;
+    a.cyl = s.kind == GSR_SENSOR_CYLINDRICAL;
     a.fx = s.fx; a.fy = s.fy; a.cx = s.cx; a.cy = s.cy;
     a.w_dist = wt->w_dist;
     a.w_norm = wt->w_normal;
@@ -1064,6 +1104,8 @@ cudaError_t launch_render_backward(const gsr_plan* p, void* ws, int sensor, cons
     a.g_normal = g->normal;
     a.g_drop = nullptr;
     a.recgrad = region<float4>(p, ws, R_RECGRAD);
+    if (p->sensors[sensor].kind == GSR_SENSOR_CYLINDRICAL)
+        return render_backward_kind<GSR_SENSOR_CYLINDRICAL>(p, ws, sensor, a, st);
     return render_backward_kind<GSR_SENSOR_PINHOLE>(p, ws, sensor, a, st);
 }
 
@@ -1149,7 +1191,7 @@ extern "C" gsr_status gsr_loss_noalloc(const gsr_sensor* camera, const gsr_camer
 {
     using namespace gsr;
     if (!camera || !fwd || !target_rgb || !weights || !loss || !grad) return GSR_ERR_INVALID_ARG;
-    if (camera->kind != GSR_SENSOR_PINHOLE) return GSR_ERR_UNSUPPORTED;
+    if (camera->kind != GSR_SENSOR_PINHOLE && camera->kind != GSR_SENSOR_CYLINDRICAL) return GSR_ERR_UNSUPPORTED;
     if (camera->width <= 0 || camera->height <= 0 || !(camera->fx > 0.f && camera->fy > 0.f))
         return GSR_ERR_INVALID_ARG;
     if ((int64_t)camera->width * camera->height > GSR_NOALLOC_MAX_PIXELS) return GSR_ERR_TOO_LARGE;
@@ -1172,6 +1214,7 @@ extern "C" gsr_status gsr_loss_noalloc(const gsr_sensor* camera, const gsr_camer
     a.g_normal = grad->normal;
     a.W = camera->width;
     a.H = camera->height;
+    a.cyl = camera->kind == GSR_SENSOR_CYLINDRICAL;
     a.fx = camera->fx; a.fy = camera->fy; a.cx = camera->cx; a.cy = camera->cy;
     a.w_dist = weights->w_dist;
     a.w_norm = weights->w_normal;

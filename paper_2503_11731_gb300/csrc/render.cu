@@ -343,11 +343,10 @@ __device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile
                             counters, buf, bars, gb, D);
             if (!need) S.done = was;
         }
-        // block k now holds the state after chunk k (the backward of
-        // pinhole and LiDAR sensors starts its walk of chunk k - 1 there);
-        // kept only by a render that writes the final T, the backward's input
-        if (KIND != GSR_SENSOR_CYLINDRICAL && out.trans != nullptr && r < R)
-            store_ray(ray_block(sp, info.y, R, k), R, r, S);
+        // block k now holds the state after chunk k (the backward starts its
+        // walk of chunk k - 1 there); kept only by a render that writes the
+        // final T, the backward's input
+        if (out.trans != nullptr && r < R) store_ray(ray_block(sp, info.y, R, k), R, r, S);
     }
     write_ray<KIND>(sd, ray, S, out);
 }

@@ -489,7 +489,8 @@ def cylindrical_frame(args, stream):
     """A frame of a cylindrical surround camera (Eq. 4): the 1.5M-surfel SH-3
     driving scene seen by one 3840x1080 camera over 200 deg of azimuth at
     (0, 0, 1.5), next to the 1920x1080 pinhole of the same scene; each
-    tiling autotuned, each frame (preprocess, sort, composite) one graph."""
+    tiling autotuned, each frame (preprocess, sort, composite) one graph;
+    plus one training step of the cylindrical frame."""
     import torch
     from paper_2503_11731_gb300 import synth
     from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer
@@ -513,6 +514,29 @@ def cylindrical_frame(args, stream):
                      "tile": r.tile_of("camera"), "visible_records": nvis, "tile_pairs": npairs,
                      "autotune_best_ms": None if tuned is None else tuned["best_ms"]}
         del g, r
+    if args.backward:
+        # a training step of the cylindrical frame (forward, loss with the
+        # Eq. 4 back-projection, backward) on the frame's tuned tile,
+        # against the frame of a perturbed copy
+        from paper_2503_11731_gb300.frame import camera_backward, camera_loss
+        cam = synth.cylindrical(3840, 1080, 200.0, 60.0, (0.0, 0.0, 1.5))
+        tile = tuple(res["cylindrical"]["tile"])
+        outs = ("rgb", "depth", "normal", "alpha", "trans", "depth_acc", "n_contrib")
+        r = Renderer(s.n, [cam], tiles=[tile], outputs=outs, max_dup=args.max_dup)
+        r.render(DeviceSurfels.from_host(synth.perturbed(s, seed=synth.SEED_BASE + 30)))
+        target = r.out[0]["rgb"].clone()
+        grads = {k: torch.zeros_like(getattr(d, k)) for k in ("pos", "log_scale", "quat", "opacity", "sh")}
+
+        def step():
+            for t in grads.values():
+                t.zero_()
+            r.render(d)
+            loss, lo = camera_loss(r, 0, target)
+            camera_backward(r, 0, lo.struct(), d, out=grads)
+        for _ in range(2):
+            step()
+        res["cylindrical"]["training_step_ms"] = timed(stream, max(3, args.steps // 2), step)
+        del r
     return res
 
 

@@ -171,3 +171,65 @@ class NeuralFrame:
         and the persistent whole-rig compositing launch."""
         return {"decode": capture(self.decode), "front": capture(self.front),
                 "render_rig": self.r.graph(self.table, self.poses, stages=4)}
+
+
+class FramePipeline:
+    """Frames of a NeuralFrame streamed between pinned host memory and the
+    device.  A frame's inputs are uploaded on an upload stream while the
+    previous frame composites, and its outputs are read back on a download
+    stream while the next frame decodes and sorts; events order every reuse
+    of a buffer (an upload waits until the previous frame's front end has
+    read the inputs, a compositing launch until the previous frame's outputs
+    are read back), so no buffer is doubled.
+
+    inputs: [(device tensor, pinned host tensor)] uploaded before each frame
+    (the anchors, MLP weights, object table, poses the frame's graphs read);
+    outputs: [(device tensor, pinned host tensor)] read back after it.
+    """
+
+    def __init__(self, nf: NeuralFrame, inputs, outputs, stream=None):
+        self.G = nf.graphs()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.up, self.down = torch.cuda.Stream(), torch.cuda.Stream()
+        self.inputs, self.outputs = list(inputs), list(outputs)
+        self.front_done, self.inputs_ready = torch.cuda.Event(), torch.cuda.Event()
+        self.render_done, self.outputs_read = torch.cuda.Event(), torch.cuda.Event()
+        self.started = False
+
+    def start_after(self, stream):
+        """Order the next uploads after the work enqueued on `stream` so far."""
+        self.up.wait_stream(stream)
+
+    def frame(self, host_inputs=None, host_outputs=None):
+        """Enqueue one frame; host_inputs / host_outputs (optional) replace
+        the pinned host side of `inputs` / `outputs` for this frame.  A host
+        input may be overwritten once `inputs_ready` has completed, a host
+        output read once `outputs_read` has."""
+        s = self.stream
+        hin = host_inputs if host_inputs is not None else [h for _, h in self.inputs]
+        hout = host_outputs if host_outputs is not None else [h for _, h in self.outputs]
+        if self.started:
+            self.up.wait_event(self.front_done)  # the previous frame has read its inputs
+        with torch.cuda.stream(self.up):
+            for (d, _), h in zip(self.inputs, hin):
+                d.copy_(h, non_blocking=True)
+        self.inputs_ready.record(self.up)
+        s.wait_event(self.inputs_ready)
+        with torch.cuda.stream(s):
+            self.G["decode"].replay()
+            self.G["front"].replay()
+        self.front_done.record(s)
+        if self.started:
+            s.wait_event(self.outputs_read)  # the previous frame's outputs are read back
+        self.G["render_rig"].launch(_stream_handle(s))
+        self.render_done.record(s)
+        self.down.wait_event(self.render_done)
+        with torch.cuda.stream(self.down):
+            for (d, _), h in zip(self.outputs, hout):
+                h.copy_(d, non_blocking=True)
+        self.outputs_read.record(self.down)
+        self.started = True
+
+    def finish(self):
+        """Make `stream` wait for the last frame's outputs."""
+        self.stream.wait_event(self.outputs_read)

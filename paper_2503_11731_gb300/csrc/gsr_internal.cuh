@@ -264,10 +264,14 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     const float zi = r2.w * rq;
     const float rho3 = fmaf(u, u, v * v);
     const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
-    const bool v3 = (zi > near_plane) && (rho3 <= kSupport);
-    const bool vlp = rholp <= kSupport;
-    const bool use3 = v3 && (!vlp || rho3 <= rholp);
-    const float rho = use3 ? rho3 : rholp;
+    // G = max(G_3, G_lp) is the smaller radius; an intersection at or behind
+    // the near plane takes no part (NaN radii compare false and lose to the
+    // low-pass).  Ties take the intersection.  Either branch counts only
+    // within the support.
+    const float rho3f = zi > near_plane ? rho3 : __int_as_float(0x7f800000);
+    const bool use3 = rho3f <= rholp;
+    const float rho = fminf(rho3f, rholp);
+    const bool inside = rho <= kSupport;
     const float G = __expf(-0.5f * rho);
     const float alpha = fminf(kAlphaMax, R[3].x * G);
     sp.alpha = alpha;
@@ -277,7 +281,7 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     sp.u = u; sp.v = v; sp.rho = rho;
     sp.dx = dx; sp.dy = dy;
     sp.use3 = use3;
-    return (v3 || vlp) && alpha >= kAlphaMin;
+    return inside && alpha >= kAlphaMin;
 }
 
 // ------------------------------------------------------------ tile culling

@@ -272,7 +272,11 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     const bool use3 = rho3f <= rholp;
     const float rho = fminf(rho3f, rholp);
     const bool inside = rho <= kSupport;
-    const float G = __expf(-0.5f * rho);
+    // G = exp(-rho / 2) = 2^(-rho log2(e) / 2): one multiply by the folded
+    // constant and the hardware base-2 exponential (rho <= 9 on every hit,
+    // so the result is far from the flush-to-zero range)
+    float G;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(rho * -0.72134752f));
     const float alpha = fminf(kAlphaMax, R[3].x * G);
     sp.alpha = alpha;
     sp.z = use3 ? zi : R[4].w;

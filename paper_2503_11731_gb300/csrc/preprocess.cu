@@ -140,8 +140,14 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 // one plan.  Composite ties break by plan index, as in a single table.  One
 // instantiation per sensor model keeps each one's registers to its own
 // bound; the grid walks the plan's sensors of that model (ids) fastest.
+// Resident 256-thread CTAs per SM the preprocess is compiled for: 4 caps it
+// at 64 registers (a few bytes of spills), which measured faster on the rig
+// frame than 3 (80 registers) or 2 (96), the kernel being latency-bound.
+#ifndef GSR_PRE_MIN_CTAS
+#define GSR_PRE_MIN_CTAS 4
+#endif
 template <int KIND>
-__global__ void __launch_bounds__(256, 3) k_preprocess(SensorTable tab, SensorIds ids, gsr_surfels S,
+__global__ void __launch_bounds__(256, GSR_PRE_MIN_CTAS) k_preprocess(SensorTable tab, SensorIds ids, gsr_surfels S,
                                                     const float* __restrict__ poses, int n_obj,
                                                     float4* __restrict__ rec, ushort4* __restrict__ rects,
                                                     uint32_t* __restrict__ counts, uint32_t* __restrict__ keys,

@@ -442,7 +442,10 @@ constexpr int kStageStride = 40;  // = 8 mod 32: conflict-free staging both ways
 constexpr int kDupCtasPerSortCta = 8;
 constexpr int kDupRowsPerThread = kDupRowsRound / 256;
 
-__global__ void __launch_bounds__(256) k_dup_write(SensorTable tab, int n_surfels,
+// Compiled for 4 resident CTAs per SM: 64 registers without spills (left to
+// itself the compiler also took 64 but spilled); 3 (72) and 2 (90) measured
+// slower.
+__global__ void __launch_bounds__(256, 4) k_dup_write(SensorTable tab, int n_surfels,
                                                    const uint32_t* __restrict__ vis_val,
                                                    const uint32_t* __restrict__ cnt_sorted,
                                                    const uint32_t* __restrict__ offs,

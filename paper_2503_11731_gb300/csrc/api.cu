@@ -156,12 +156,9 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     }
     if (max_dup > 2147483647LL) return GSR_ERR_INVALID_ARG;
     plan->max_dup = max_dup;
-    // CTAs per SM of the fixed sort grid (3 measured the same as 4 on the rig
-    // frame, 5 slower)
-#ifndef GSR_SORT_CTAS_PER_SM
-#define GSR_SORT_CTAS_PER_SM 4
-#endif
-    plan->sort_ctas = GSR_SORT_CTAS_PER_SM * 152;
+    // the fixed sort grid: 4 CTAs on each of the 152 SMs (3 measured the same
+    // on the rig frame, 5 slower)
+    plan->sort_ctas = 4 * 152;
 
     uint64_t sz[R_END];
     const uint64_t G = (uint64_t)plan->sort_ctas;

@@ -264,17 +264,17 @@ __device__ __forceinline__ bool splat_eval(const float4* __restrict__ R, float r
     const float zi = r2.w * rq;
     const float rho3 = fmaf(u, u, v * v);
     const float rholp = kLowPassInvVar * fmaf(dx, dx, dy * dy);
-    // G = max(G_3, G_lp) is the smaller radius; an intersection at or behind
-    // the near plane takes no part (NaN radii compare false and lose to the
-    // low-pass).  Ties take the intersection.  Either branch counts only
-    // within the support.
+    // G = max(G_3, G_lp) belongs to the smaller of the two radii; an
+    // intersection at or behind the near plane takes no part, and a NaN
+    // radius compares false and loses to the low-pass.  Ties take the
+    // intersection.  Either branch counts only within the support.
     const float rho3f = zi > near_plane ? rho3 : __int_as_float(0x7f800000);
     const bool use3 = rho3f <= rholp;
     const float rho = fminf(rho3f, rholp);
     const bool inside = rho <= kSupport;
     // G = exp(-rho / 2) = 2^(-rho log2(e) / 2): one multiply by the folded
-    // constant and the hardware base-2 exponential (rho <= 9 on every hit,
-    // so the result is far from the flush-to-zero range)
+    // constant -log2(e) / 2 and the hardware base-2 exponential (rho <= 9 on
+    // every hit, so the result is far from the flush-to-zero range)
     float G;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(G) : "f"(rho * -0.72134752f));
     const float alpha = fminf(kAlphaMax, R[3].x * G);

@@ -142,7 +142,8 @@ __device__ __forceinline__ void index_range(float lo, float hi, float off, int n
 // bound; the grid walks the plan's sensors of that model (ids) fastest.
 // Resident 256-thread CTAs per SM the preprocess is compiled for: 4 caps it
 // at 64 registers (a few bytes of spills), which measured faster on the rig
-// frame than 3 (80 registers) or 2 (96), the kernel being latency-bound.
+// frame than 3 (80 registers) or 2 (96): more resident warps hide its
+// latencies better than the spared registers would.
 #ifndef GSR_PRE_MIN_CTAS
 #define GSR_PRE_MIN_CTAS 4
 #endif

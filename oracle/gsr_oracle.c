@@ -34,9 +34,11 @@
  *     depth is the intersection depth if G3 wins, else the centre depth;
  *   - alpha = min(0.99, o G); alpha < 1/255 is skipped; compositing stops
  *     before a surfel when T (1 - alpha) < 1e-4;
- *   - composite order: centre depth (camera z, LiDAR |mu|), ties by index,
- *     with the depth key and the near cull taken in the kernel's FP32
- *     arithmetic (see or_key32);
+ *   - composite order: centre depth (camera z, LiDAR |mu|, cylinder
+ *     horizontal distance) in FP64, ties by index; where two contributing
+ *     surfels' depths are closer than an FP32 evaluation of them can
+ *     separate, the ray is flagged with the largest change a swap of the
+ *     two could make (see or_step), as for every other threshold;
  *   - colour = max(0, sum_lm Y_lm(dir) c_lm + 0.5), real SH with the
  *     Condon-Shortley phase, dir = normalise(mu - sensor origin);
  *   - normal = R's third column, flipped to face the sensor, sensor frame.
@@ -132,14 +134,19 @@ static void or_quat_to_rot(const double q_in[4], double R[3][3])
 /* Per-surfel state, independent of the pixel.                               */
 /* ----------------------------------------------------------------------- */
 typedef struct {
-    int culled;
+    int culled;        /* centre depth (range) <= near                        */
+    double cull_rel;   /* |zc - near| / near: how close the cull decision is  */
     double WH[4][3];   /* Eq. 1: W . H, a 4x3 matrix                         */
-    double zc;         /* centre depth (camera z) / centre range (LiDAR |mu|) */
-    float key;         /* composite-order key: zc in the kernel's FP32 arithmetic */
+    double zc;         /* centre depth (camera z) / centre range (LiDAR |mu|)
+                          / horizontal distance (cylinder): the order key     */
+    double tau;        /* bound on the error of an FP32 evaluation of zc      */
     double c[2];       /* low-pass centre (pixels, or LiDAR cells)           */
     double o;          /* opacity, sigmoid of the logit                      */
     double feat[3];    /* camera: colour; LiDAR: intensity, ray drop, 0     */
     double normal[3];  /* sensor frame, facing the sensor                    */
+    double ms[3];      /* centre in the sensor frame                         */
+    double rad;        /* radius of a sphere about the centre that holds the
+                          support u^2 + v^2 <= 9 with the near-miss margin    */
 } or_surfel;
 
 typedef struct {
@@ -147,7 +154,8 @@ typedef struct {
     int kind;                        /* 0 pinhole, 1 LiDAR, 2 cylindrical   */
     double Rs[3][3], ts[3];          /* world -> sensor rigid part          */
     double origin[3];                /* sensor origin in world             */
-    double fx, fy, cx, cy;           /* pinhole                            */
+    double fx, fy, cx, cy;           /* cameras                            */
+    int width, height;               /* cameras                            */
     int beams, columns;              /* LiDAR                              */
     double el_max, d_el, az0, d_az;  /* radians                            */
     double near_;
@@ -171,9 +179,12 @@ static void or_sensor_from_matrix(or_sensor* S, const double* w2s)
  * Gaussian inplacing: a model matrix per actor): mu' = R_o mu + t_o,
  * R' = R_o R.  The SH coefficients live in the object frame, so the view
  * direction is rotated back by R_o^T before the basis is evaluated.
+ * mag[a] (optional) receives sum_b |R_o[a][b] mu_b| + |t_o[a]|, the size of
+ * the terms that make up mu'[a].
  */
 static void or_surfel_world(int i, const double* pos, const double* quat, const int* obj_id,
-                            const double* obj_pose, double mu[3], double R[3][3], double Ro[3][3])
+                            const double* obj_pose, double mu[3], double R[3][3], double Ro[3][3],
+                            double mag[3])
 {
     double Rl[3][3];
     or_quat_to_rot(quat + 4 * i, Rl);
@@ -190,7 +201,11 @@ static void or_surfel_world(int i, const double* pos, const double* quat, const 
     }
     for (int a = 0; a < 3; ++a) {
         mu[a] = to[a];
-        for (int b = 0; b < 3; ++b) mu[a] += Ro[a][b] * pos[3 * i + b];
+        if (mag) mag[a] = fabs(to[a]);
+        for (int b = 0; b < 3; ++b) {
+            mu[a] += Ro[a][b] * pos[3 * i + b];
+            if (mag) mag[a] += fabs(Ro[a][b] * pos[3 * i + b]);
+        }
         for (int b = 0; b < 3; ++b) {
             R[a][b] = 0;
             for (int c = 0; c < 3; ++c) R[a][b] += Ro[a][c] * Rl[c][b];
@@ -199,42 +214,24 @@ static void or_surfel_world(int i, const double* pos, const double* quat, const 
 }
 
 /*
- * The composite order is an integer decision (a permutation) that rounding
- * decides: two surfels whose centre depths differ by less than FP32 can
- * resolve swap places between an FP32 and an FP64 evaluation.  The order
- * key is therefore taken in the kernel's precision -- the centre depth
- * (range) evaluated in IEEE single precision with fused multiply-adds in
- * the order the kernel uses: mu' = R_o mu + t_o, m = R mu' + t, key = m_z
- * (camera) or sqrt(m . m) (LiDAR).  Everything else stays FP64.
+ * Unit roundoff of IEEE single precision.  A renderer that evaluates the
+ * order key (an affine map of the surfel's centre, then for the LiDAR and
+ * the cylinder a Euclidean norm) in FP32 can land anywhere within a few
+ * roundoffs of the terms it sums; OR_KEY_ULPS roundoffs of the sum of the
+ * terms' magnitudes is the bound used here (a dot product of length 3 plus
+ * a translation, done twice for a posed object, accrues at most about 8
+ * such errors in any evaluation order).
  */
-static float or_key32(const or_sensor* S, int i, const double* pos, const int* obj_id, const double* obj_pose)
-{
-    float m0 = (float)pos[3 * i], m1 = (float)pos[3 * i + 1], m2 = (float)pos[3 * i + 2];
-    int k = obj_id ? obj_id[i] : -1;
-    if (k >= 0) {
-        const double* P = obj_pose + 12 * k;
-        float R[9] = {(float)P[0], (float)P[1], (float)P[2], (float)P[4], (float)P[5], (float)P[6],
-                      (float)P[8], (float)P[9], (float)P[10]};
-        float a0 = fmaf(R[0], m0, fmaf(R[1], m1, R[2] * m2)) + (float)P[3];
-        float a1 = fmaf(R[3], m0, fmaf(R[4], m1, R[5] * m2)) + (float)P[7];
-        float a2 = fmaf(R[6], m0, fmaf(R[7], m1, R[8] * m2)) + (float)P[11];
-        m0 = a0; m1 = a1; m2 = a2;
-    }
-    float s[3];
-    for (int a = 0; a < 3; ++a)
-        s[a] = fmaf((float)S->Rs[a][0], m0, fmaf((float)S->Rs[a][1], m1, (float)S->Rs[a][2] * m2)) + (float)S->ts[a];
-    if (S->kind == 0) return s[2];
-    if (S->kind == 2) return sqrtf(fmaf(s[0], s[0], s[2] * s[2])); /* horizontal distance */
-    return sqrtf(fmaf(s[0], s[0], fmaf(s[1], s[1], s[2] * s[2])));
-}
+#define OR_U32 (1.0 / 16777216.0)
+#define OR_KEY_ULPS 8.0
 
 static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* pos,
                        const double* log_scale, const double* quat, const double* opacity_logit,
                        int sh_degree, const double* sh, const double* intensity,
                        const double* ray_drop, const int* obj_id, const double* obj_pose)
 {
-    double mu[3], R[3][3], Ro[3][3];
-    or_surfel_world(i, pos, quat, obj_id, obj_pose, mu, R, Ro);
+    double mu[3], R[3][3], Ro[3][3], mag[3];
+    or_surfel_world(i, pos, quat, obj_id, obj_pose, mu, R, Ro, mag);
     double su = exp(log_scale[2 * i + 0]), sv = exp(log_scale[2 * i + 1]);
 
     /* H (Eq. 1): columns s_u t_u, s_v t_v, mu over a bottom row (0,0,1). */
@@ -270,31 +267,40 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
             for (int c = 0; c < 4; ++c) G->WH[a][b] += W[a][c] * H[c][b];
         }
 
-    /* mu in the sensor frame */
-    double ms[3];
-    for (int a = 0; a < 3; ++a) ms[a] = S->Rs[a][0] * mu[0] + S->Rs[a][1] * mu[1] + S->Rs[a][2] * mu[2] + S->ts[a];
+    /* mu in the sensor frame, and the size of the terms of each component */
+    double ms[3], msmag[3];
+    for (int a = 0; a < 3; ++a) {
+        ms[a] = S->Rs[a][0] * mu[0] + S->Rs[a][1] * mu[1] + S->Rs[a][2] * mu[2] + S->ts[a];
+        msmag[a] = fabs(S->ts[a]);
+        for (int b = 0; b < 3; ++b) msmag[a] += fabs(S->Rs[a][b]) * mag[b];
+    }
+    for (int a = 0; a < 3; ++a) G->ms[a] = ms[a];
+    G->rad = 3.01 * (su > sv ? su : sv);
 
-    G->culled = 0;
-    G->key = or_key32(S, i, pos, obj_id, obj_pose);
-    if (!(G->key > (float)S->near_)) { G->culled = 1; return; }  /* cull in the key's precision */
+    /* order key and its FP32 error bound */
     if (S->kind == 0) {
         G->zc = ms[2];
+        G->tau = OR_KEY_ULPS * OR_U32 * msmag[2];
         G->c[0] = G->WH[0][2] / G->WH[2][2];
         G->c[1] = G->WH[1][2] / G->WH[2][2];
     } else if (S->kind == 2) {
         /* cylinder: column from the azimuth about the camera's y axis, row
            from the height over the horizontal distance (pixel units) */
         G->zc = sqrt(ms[0] * ms[0] + ms[2] * ms[2]);
+        G->tau = OR_KEY_ULPS * OR_U32 * (sqrt(msmag[0] * msmag[0] + msmag[2] * msmag[2]) + G->zc);
         G->c[0] = S->cx + S->fx * atan2(ms[0], ms[2]);
         G->c[1] = S->cy + S->fy * ms[1] / G->zc;
     } else {
         G->zc = sqrt(or_dot3(ms, ms));
+        G->tau = OR_KEY_ULPS * OR_U32 * (sqrt(or_dot3(msmag, msmag)) + G->zc);
         double az = atan2(ms[1], ms[0]);
         double el = atan2(ms[2], sqrt(ms[0] * ms[0] + ms[1] * ms[1]));
         /* cell coordinates: ray (row i, column j) sits at (j, i) */
         G->c[0] = (az - S->az0) / S->d_az - 0.5;
         G->c[1] = (S->el_max - el) / S->d_el;
     }
+    G->culled = !(G->zc > S->near_);
+    G->cull_rel = fabs(G->zc - S->near_) / S->near_;
     G->o = or_sigmoid(opacity_logit[i]);
 
     /* normal = third column of R, in the sensor frame, facing the sensor */
@@ -329,13 +335,13 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
 /* ----------------------------------------------------------------------- */
 typedef struct {
     int idx;
-    float key;        /* order key            */
-    double zc;        /* centre depth         */
+    double zc;        /* centre depth: the order key */
     double alpha;     /* min(0.99, o G)       */
     double z;         /* contribution depth   */
     double rho3, rholp, zint;
     int v3, vlp;      /* support validity     */
     int hasplane;     /* m2 != 0              */
+    int phantom;      /* culled by the near test, but within rounding of it */
 } or_hit;
 
 /* k, l are the plane rows h_u^T WH, h_v^T WH; d (LiDAR only) the ray direction. */
@@ -373,6 +379,7 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
     }
     h->rholp = (dx * dx + dy * dy) / 0.5; /* |p-c|^2 / sigma^2, sigma^2 = 1/2 */
     h->vlp = h->rholp <= 9.0;
+    h->zc = G->zc;
     if (!h->v3 && !h->vlp) return 0;
     double rho;
     if (h->v3 && (!h->vlp || h->rho3 <= h->rholp)) { rho = h->rho3; h->z = h->zint; }
@@ -380,37 +387,58 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
     double Gv = exp(-0.5 * rho);
     double a = G->o * Gv;
     h->alpha = a < 0.99 ? a : 0.99;
-    h->zc = G->zc;
-    h->key = G->key;
     return 1;
-}
-
-static int or_cmp_hit(const void* pa, const void* pb)
-{
-    const or_hit* a = (const or_hit*)pa;
-    const or_hit* b = (const or_hit*)pb;
-    if (a->key < b->key) return -1;
-    if (a->key > b->key) return 1;
-    return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
 static double or_relm(double x, double thr) { return fabs(x - thr) / fabs(thr); }
 
 /*
- * Decisions that FP32 rounding could flip.  A decision counts as flippable
- * when its relative distance to the threshold is below OR_FLIP_REL (2e-5),
- * and its effect is the largest
- * change of an output that flipping it could cause (T times the jump in
- * alpha; for the depth-branch choice, the relative jump in depth weight).
+ * Whether surfel g enters ray's hit sequence, and its hit record.  A surfel
+ * enters when it contributes a weight (or_eval), when one of its support
+ * tests is within 1e-3 of its threshold (a near miss, whose acceptance an
+ * FP32 evaluation could take the other way), or when it was culled by the
+ * near test within rounding of the threshold (a phantom).
+ */
+static int or_collect(const or_surfel* g, int i, const or_sensor* S, const double hu[4], const double hv[4],
+                      const double d[3], const double pc[2], or_hit* h);
+
+static int or_cmp_hit(const void* pa, const void* pb)
+{
+    const or_hit* a = (const or_hit*)pa;
+    const or_hit* b = (const or_hit*)pb;
+    if (a->zc < b->zc) return -1;
+    if (a->zc > b->zc) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/*
+ * Decisions that FP32 rounding could flip.  A threshold decision counts as
+ * flippable when its relative distance to the threshold is below
+ * OR_FLIP_REL (2e-5); the order of two contributing surfels counts as
+ * flippable when their FP64 depths differ by less than the sum of their
+ * FP32 error bounds (tau).  The recorded effect is the largest change of an
+ * output that taking the decision the other way could cause (T times the
+ * jump in alpha; for the depth-branch choice, the relative jump in depth
+ * weight; for an order swap, the weight the swap moves between the two
+ * surfels times the largest difference of their outputs).
  */
 #ifndef OR_FLIP_REL
 #define OR_FLIP_REL 2e-5
 #endif
 
+/* Near-miss and phantom margin of or_collect (relative). */
+#define OR_NEAR_MISS 1e-3
+
 typedef struct {
     double feat[3], A, B, D, N[3], T;
     double flip;      /* largest effect of a flippable decision, 0 if none */
     int n_contrib;
+    int done;         /* the stop rule ended the ray                       */
+    /* the last composited surfel, for the order check */
+    int has_prev;
+    double prev_zc, prev_tau, prev_alpha, prev_T, prev_z;
+    const double* prev_feat;
+    const double* prev_n;
 } or_ray;
 
 static void or_flip(double* flip, double rel, double scale, double effect)
@@ -418,66 +446,366 @@ static void or_flip(double* flip, double rel, double scale, double effect)
     if (rel < scale && effect > *flip) *flip = effect;
 }
 
+static void or_ray_init(or_ray* r)
+{
+    memset(r, 0, sizeof(*r));
+    r->T = 1.0;
+}
+
+static double or_maxdiff3(const double* a, const double* b)
+{
+    double m = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double v = fabs(a[c] - b[c]);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
+static double or_maxabs3(const double* a)
+{
+    double m = 0.0;
+    for (int c = 0; c < 3; ++c)
+        if (fabs(a[c]) > m) m = fabs(a[c]);
+    return m;
+}
+
 /*
- * Front-to-back compositing of one ray over all surfels (3DGS order and
- * thresholds), accumulating sum w feat, A = sum w, B = sum w z, D = sum w z^2
- * and sum w n, with w = alpha T.
+ * One step of front-to-back compositing (3DGS order and thresholds): hit h
+ * of surfel g is the next in depth order.  Accumulates sum w feat,
+ * A = sum w, B = sum w z, D = sum w z^2 and sum w n, with w = alpha T, and
+ * sets r->done when the stop rule ends the ray.
  */
+static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sensor* S)
+{
+    double T = r->T;
+    double edge = T * g->o * exp(-4.5);
+    if (h->hasplane && h->zint > S->near_) or_flip(&r->flip, or_relm(h->rho3, 9.0), OR_FLIP_REL, edge);
+    if (h->hasplane && h->rho3 <= 9.0)
+        or_flip(&r->flip, or_relm(h->zint, S->near_), OR_FLIP_REL, T * g->o * exp(-0.5 * h->rho3));
+    or_flip(&r->flip, or_relm(h->rholp, 9.0), OR_FLIP_REL, edge);
+    if (h->alpha <= 0) return;
+    /* the centre-depth cull of this surfel could go the other way */
+    or_flip(&r->flip, g->cull_rel, OR_FLIP_REL, h->alpha * T);
+    if (h->phantom) return;
+    or_flip(&r->flip, or_relm(h->alpha, 1.0 / 255.0), OR_FLIP_REL, T / 255.0);
+    if (h->v3 && h->vlp) {
+        double big = h->rho3 > h->rholp ? h->rho3 : h->rholp;
+        or_flip(&r->flip, fabs(h->rho3 - h->rholp) / big, OR_FLIP_REL,
+                h->alpha * T * fabs(h->zint - g->zc) / g->zc);
+    }
+    if (h->alpha < 1.0 / 255.0) return;
+    double test = T * (1.0 - h->alpha);
+    or_flip(&r->flip, or_relm(test, 1e-4), OR_FLIP_REL, h->alpha * T);
+    /* order of this surfel and the previous composited one */
+    int tie = r->has_prev && fabs(h->zc - r->prev_zc) <= g->tau + r->prev_tau;
+    if (test < 1e-4) {
+        /* swapped, this surfel would come first and the previous one might
+           stop the ray instead: the weights of both are at stake */
+        if (tie) {
+            double big = h->alpha > r->prev_alpha ? h->alpha : r->prev_alpha;
+            double f = or_maxabs3(g->feat), fp = or_maxabs3(r->prev_feat);
+            double fm = f > fp ? f : fp;
+            or_flip(&r->flip, 0.0, 1.0, r->prev_T * big * (fm > 1.0 ? fm : 1.0));
+        }
+        r->done = 1;
+        return;
+    }
+    if (tie) {
+        /* a swap moves weight alpha_prev alpha T_prev from one to the other */
+        double moved = r->prev_alpha * h->alpha * r->prev_T;
+        double dz = fabs(h->z - r->prev_z) / (h->z < r->prev_z ? h->z : r->prev_z);
+        double df = or_maxdiff3(g->feat, r->prev_feat), dn = or_maxdiff3(g->normal, r->prev_n);
+        double m = df > dn ? df : dn;
+        if (dz > m) m = dz;
+        or_flip(&r->flip, 0.0, 1.0, moved * m);
+    }
+    double w = h->alpha * T;
+    for (int ch = 0; ch < 3; ++ch) r->feat[ch] += w * g->feat[ch];
+    r->A += w;
+    r->B += w * h->z;
+    r->D += w * h->z * h->z;
+    for (int a = 0; a < 3; ++a) r->N[a] += w * g->normal[a];
+    r->has_prev = 1;
+    r->prev_zc = h->zc;
+    r->prev_tau = g->tau;
+    r->prev_alpha = h->alpha;
+    r->prev_T = T;
+    r->prev_z = h->z;
+    r->prev_feat = g->feat;
+    r->prev_n = g->normal;
+    r->T = test;
+    ++r->n_contrib;
+}
+
+static int or_collect(const or_surfel* g, int i, const or_sensor* S, const double hu[4], const double hv[4],
+                      const double d[3], const double pc[2], or_hit* h)
+{
+    if (g->culled && g->cull_rel >= OR_FLIP_REL) return 0;
+    h->idx = i;
+    h->phantom = g->culled;
+    int any = or_eval(g, S, hu, hv, d, pc, h);
+    /* keep near misses too: their acceptance could flip in FP32 */
+    int near_miss = (h->hasplane && h->zint > S->near_ && or_relm(h->rho3, 9.0) < OR_NEAR_MISS) ||
+                    (h->hasplane && h->rho3 <= 9.0 && or_relm(h->zint, S->near_) < OR_NEAR_MISS) ||
+                    or_relm(h->rholp, 9.0) < OR_NEAR_MISS;
+    if (!any && !near_miss) return 0;
+    if (!any) { h->alpha = 0; h->z = g->zc; }
+    return 1;
+}
+
+/* Brute force: every surfel against the ray, hits sorted by (depth, index). */
 static void or_composite(const or_surfel* G, int n, const or_sensor* S, const double hu[4], const double hv[4],
                          const double d[3], const double pc[2], or_hit* buf, or_ray* out)
 {
     int nh = 0;
-    for (int i = 0; i < n; ++i) {
-        if (G[i].culled) continue;
-        or_hit h;
-        h.idx = i;
-        int any = or_eval(&G[i], S, hu, hv, d, pc, &h);
-        /* keep near misses too: their acceptance could flip in FP32 */
-        int near_miss = (h.hasplane && h.zint > S->near_ && or_relm(h.rho3, 9.0) < 1e-3) ||
-                        (h.hasplane && h.rho3 <= 9.0 && or_relm(h.zint, S->near_) < 1e-3) ||
-                        or_relm(h.rholp, 9.0) < 1e-3;
-        if (!any && !near_miss) continue;
-        if (!any) { h.alpha = 0; h.z = G[i].zc; h.zc = G[i].zc; h.key = G[i].key; }
-        buf[nh++] = h;
-    }
+    for (int i = 0; i < n; ++i)
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, &buf[nh])) ++nh;
     qsort(buf, (size_t)nh, sizeof(or_hit), or_cmp_hit);
-    double T = 1.0, flip = 0.0;
-    double F[3] = {0, 0, 0}, A = 0, B = 0, D = 0, N[3] = {0, 0, 0};
-    int nc = 0;
-    for (int j = 0; j < nh; ++j) {
-        const or_hit* h = &buf[j];
-        const or_surfel* g = &G[h->idx];
-        double edge = T * g->o * exp(-4.5);
-        if (h->hasplane && h->zint > S->near_) or_flip(&flip, or_relm(h->rho3, 9.0), OR_FLIP_REL, edge);
-        if (h->hasplane && h->rho3 <= 9.0)
-            or_flip(&flip, or_relm(h->zint, S->near_), OR_FLIP_REL, T * g->o * exp(-0.5 * h->rho3));
-        or_flip(&flip, or_relm(h->rholp, 9.0), OR_FLIP_REL, edge);
-        if (h->alpha <= 0) continue;
-        or_flip(&flip, or_relm(h->alpha, 1.0 / 255.0), OR_FLIP_REL, T / 255.0);
-        if (h->v3 && h->vlp) {
-            double big = h->rho3 > h->rholp ? h->rho3 : h->rholp;
-            or_flip(&flip, fabs(h->rho3 - h->rholp) / big, OR_FLIP_REL,
-                    h->alpha * T * fabs(h->zint - g->zc) / g->zc);
-        }
-        if (h->alpha < 1.0 / 255.0) continue;
-        double test = T * (1.0 - h->alpha);
-        or_flip(&flip, or_relm(test, 1e-4), OR_FLIP_REL, h->alpha * T);
-        if (test < 1e-4) break;
-        double w = h->alpha * T;
-        for (int ch = 0; ch < 3; ++ch) F[ch] += w * g->feat[ch];
-        A += w;
-        B += w * h->z;
-        D += w * h->z * h->z;
-        for (int a = 0; a < 3; ++a) N[a] += w * g->normal[a];
-        T = test;
-        ++nc;
+    or_ray_init(out);
+    for (int j = 0; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
+}
+
+/* ----------------------------------------------------------------------- */
+/* Tiled mode: the same compositing over per-tile candidate lists.           */
+/* ----------------------------------------------------------------------- */
+/*
+ * A ray-index box [x0, x1] x [y0, y1] (inclusive, in pixel or LiDAR cell
+ * coordinates of ray centres) holding every ray that surfel g could enter
+ * (or_collect), including near misses and phantoms.  Returns 0 if no ray
+ * can see it, 1 otherwise; *all_x / *all_y ask for the whole axis.
+ *
+ * The bound is the oracle's own, written from the geometry: the support
+ * u^2 + v^2 <= 9 (with the near-miss margin) lies inside the square of
+ * half-width 3.01 s in the surfel plane, and inside the sphere of radius
+ * 3.01 max(s_u, s_v) about the centre; the low-pass disc lies within 2.13
+ * pixels (cells) of the projected centre.
+ *   pinhole   -- the projected square's four corners when all of them lie
+ *                in front of the camera (a convex quadrilateral projects to
+ *                the convex hull of its corners), else every pixel;
+ *   cylinder  -- the sphere's azimuth cone asin(r / r_h) and its height
+ *                ratio y / r_h over the sphere's box, else every pixel;
+ *   LiDAR     -- the sphere's cap of angular radius beta = asin(r / |mu|):
+ *                elevation +- beta, azimuth +- asin(sin(beta) / cos(el))
+ *                (every column when the cap reaches a pole).
+ * A phantom (culled within rounding of the near test) sees every ray.
+ */
+static int or_bound(const or_surfel* g, const or_sensor* S, double box[4], int* all_x, int* all_y)
+{
+    *all_x = *all_y = 0;
+    if (g->culled) {
+        if (g->cull_rel >= OR_FLIP_REL) return 0;
+        *all_x = *all_y = 1;
+        return 1;
     }
-    for (int ch = 0; ch < 3; ++ch) out->feat[ch] = F[ch];
-    out->A = A; out->B = B; out->D = D;
-    for (int a = 0; a < 3; ++a) out->N[a] = N[a];
-    out->T = T;
-    out->flip = flip;
-    out->n_contrib = nc;
+    const double lp = 2.13;   /* 3 sigma_lp with the near-miss margin, and more */
+    double x0 = g->c[0] - lp, x1 = g->c[0] + lp, y0 = g->c[1] - lp, y1 = g->c[1] + lp;
+    const double* m = g->ms;
+    const double r = g->rad;
+    if (S->kind == 0) {
+        /* corners of the half-width 3.01 square, through W H (homogeneous) */
+        int front = 1;
+        double cx0 = INFINITY, cx1 = -INFINITY, cy0 = INFINITY, cy1 = -INFINITY;
+        for (int a = -1; a <= 1; a += 2)
+            for (int b = -1; b <= 1; b += 2) {
+                double u = 3.01 * a, v = 3.01 * b;
+                double X = g->WH[0][0] * u + g->WH[0][1] * v + g->WH[0][2];
+                double Y = g->WH[1][0] * u + g->WH[1][1] * v + g->WH[1][2];
+                double Z = g->WH[2][0] * u + g->WH[2][1] * v + g->WH[2][2];
+                if (!(Z > 0.5 * S->near_)) front = 0;
+                else {
+                    double px = X / Z, py = Y / Z;
+                    if (px < cx0) cx0 = px;
+                    if (px > cx1) cx1 = px;
+                    if (py < cy0) cy0 = py;
+                    if (py > cy1) cy1 = py;
+                }
+            }
+        if (!front) { *all_x = *all_y = 1; return 1; }
+        if (cx0 < x0) x0 = cx0;
+        if (cx1 > x1) x1 = cx1;
+        if (cy0 < y0) y0 = cy0;
+        if (cy1 > y1) y1 = cy1;
+    } else if (S->kind == 2) {
+        double rh = g->zc;
+        if (!(rh - r > S->near_)) { *all_x = *all_y = 1; return 1; }
+        double az = atan2(m[0], m[2]), daz = asin(r / rh);
+        if (az - daz <= -OR_PI || az + daz >= OR_PI) *all_x = 1;
+        double ax0 = S->cx + S->fx * (az - daz), ax1 = S->cx + S->fx * (az + daz);
+        double ylo = m[1] - r, yhi = m[1] + r, rlo = rh - r, rhi = rh + r;
+        double q[4] = {ylo / rlo, ylo / rhi, yhi / rlo, yhi / rhi};
+        double q0 = q[0], q1 = q[0];
+        for (int k = 1; k < 4; ++k) {
+            if (q[k] < q0) q0 = q[k];
+            if (q[k] > q1) q1 = q[k];
+        }
+        if (ax0 < x0) x0 = ax0;
+        if (ax1 > x1) x1 = ax1;
+        if (S->cy + S->fy * q0 < y0) y0 = S->cy + S->fy * q0;
+        if (S->cy + S->fy * q1 > y1) y1 = S->cy + S->fy * q1;
+    } else {
+        double rng = g->zc;
+        if (!(rng - r > S->near_)) { *all_x = *all_y = 1; return 1; }
+        double beta = asin(r / rng);
+        double el = atan2(m[2], sqrt(m[0] * m[0] + m[1] * m[1]));
+        double az = atan2(m[1], m[0]);
+        double ey0 = (S->el_max - (el + beta)) / S->d_el, ey1 = (S->el_max - (el - beta)) / S->d_el;
+        if (ey0 < y0) y0 = ey0;
+        if (ey1 > y1) y1 = ey1;
+        double sa = sin(beta) / cos(el);
+        if (fabs(el) + beta >= 0.5 * OR_PI || !(sa < 1.0)) *all_x = 1;
+        else {
+            double daz = asin(sa);
+            double ex0 = (az - daz - S->az0) / S->d_az - 0.5, ex1 = (az + daz - S->az0) / S->d_az - 0.5;
+            if (ex0 < x0) x0 = ex0;
+            if (ex1 > x1) x1 = ex1;
+        }
+    }
+    /* one more ray of margin against rounding in the bound itself */
+    box[0] = x0 - 1.0; box[1] = x1 + 1.0; box[2] = y0 - 1.0; box[3] = y1 + 1.0;
+    return 1;
+}
+
+typedef struct {
+    double zc;
+    int idx;
+} or_cand;
+
+static int or_cmp_cand(const void* pa, const void* pb)
+{
+    const or_cand* a = (const or_cand*)pa;
+    const or_cand* b = (const or_cand*)pb;
+    if (a->zc < b->zc) return -1;
+    if (a->zc > b->zc) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/*
+ * Per-tile candidate lists: tile (tx, ty) of tile x tile rays holds every
+ * surfel whose or_bound box meets one of its ray centres, sorted by
+ * (depth, index).  Ray (x, y) -- pixel column/row, or LiDAR column/beam --
+ * has its centre at (x + 0.5, y + 0.5) for the cameras and at (x, y) in the
+ * LiDAR's cell coordinates; LiDAR columns wrap.  Returns 0 on success.
+ */
+typedef struct {
+    int tile, tiles_x, tiles_y, nx, ny;
+    long long* start;   /* [tiles + 1] */
+    or_cand* cand;
+} or_tiles;
+
+static void or_box_tiles(const or_sensor* S, const or_tiles* T, const double box[4], int all_x, int all_y,
+                         int* tx0, int* tx1, int* ty0, int* ty1, int* wrap)
+{
+    /* ray centre offset along each axis: cameras at +0.5, LiDAR cells at 0 */
+    double off = (S->kind == 1) ? 0.0 : 0.5;
+    *wrap = 0;
+    if (all_y) { *ty0 = 0; *ty1 = T->ny - 1; }
+    else {
+        double a = ceil(box[2] - off), b = floor(box[3] - off);
+        if (a < 0) a = 0;
+        if (b > T->ny - 1) b = T->ny - 1;
+        *ty0 = (int)a; *ty1 = (int)b;
+    }
+    if (all_x || (S->kind == 1 && box[1] - box[0] >= T->nx - 1)) { *tx0 = 0; *tx1 = T->nx - 1; }
+    else {
+        double a = ceil(box[0] - off), b = floor(box[1] - off);
+        if (S->kind == 1) {
+            /* columns on the circle: shift the interval so it starts in range */
+            double sh = floor(a / T->nx) * T->nx;
+            a -= sh; b -= sh;
+            if (b > T->nx - 1) *wrap = 1; /* [a, nx) and [0, b - nx] */
+        } else {
+            if (a < 0) a = 0;
+            if (b > T->nx - 1) b = T->nx - 1;
+        }
+        *tx0 = (int)a; *tx1 = (int)b;
+    }
+    /* to tiles */
+    if (*ty0 <= *ty1) { *ty0 /= T->tile; *ty1 /= T->tile; }
+    if (*wrap) {
+        *tx1 = (*tx1 - T->nx) / T->tile; /* second piece [0, tx1] */
+        *tx0 /= T->tile;                 /* first piece [tx0, tiles_x) */
+    } else if (*tx0 <= *tx1) { *tx0 /= T->tile; *tx1 /= T->tile; }
+}
+
+static void or_tiles_free(or_tiles* T)
+{
+    free(T->start);
+    free(T->cand);
+    T->start = NULL;
+    T->cand = NULL;
+}
+
+static int or_tiles_build(or_tiles* T, const or_surfel* G, int n, const or_sensor* S, int tile, int nx, int ny)
+{
+    T->tile = tile;
+    T->nx = nx;
+    T->ny = ny;
+    T->tiles_x = (nx + tile - 1) / tile;
+    T->tiles_y = (ny + tile - 1) / tile;
+    long long nt = (long long)T->tiles_x * T->tiles_y;
+    T->start = (long long*)calloc((size_t)nt + 1, sizeof(long long));
+    T->cand = NULL;
+    int* rect = (int*)malloc(sizeof(int) * 5 * (size_t)(n > 0 ? n : 1));
+    long long* cnt = (long long*)calloc((size_t)nt, sizeof(long long));
+    if (!T->start || !rect || !cnt) { free(rect); free(cnt); or_tiles_free(T); return -1; }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        double box[4];
+        int ax, ay;
+        int* R = rect + 5 * i;
+        if (!or_bound(&G[i], S, box, &ax, &ay)) { R[0] = 1; R[1] = 0; R[2] = 1; R[3] = 0; R[4] = 0; continue; }
+        or_box_tiles(S, T, box, ax, ay, &R[0], &R[1], &R[2], &R[3], &R[4]);
+    }
+    /* count, then fill in surfel order (lists are sorted afterwards) */
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < n; ++i) {
+            const int* R = rect + 5 * i;
+            if (R[2] > R[3]) continue;
+            for (int ty = R[2]; ty <= R[3]; ++ty) {
+                long long row = (long long)ty * T->tiles_x;
+                int pieces = R[4] ? 2 : 1;
+                for (int p = 0; p < pieces; ++p) {
+                    int a = R[4] ? (p == 0 ? R[0] : 0) : R[0];
+                    int b = R[4] ? (p == 0 ? T->tiles_x - 1 : R[1]) : R[1];
+                    if (R[4] && p == 1 && b >= R[0]) b = R[0] - 1; /* pieces overlap: whole row once */
+                    for (int tx = a; tx <= b; ++tx) {
+                        if (pass == 0) ++cnt[row + tx];
+                        else {
+                            long long at = T->start[row + tx] + cnt[row + tx]++;
+                            T->cand[at].zc = G[i].zc;
+                            T->cand[at].idx = i;
+                        }
+                    }
+                }
+            }
+        }
+        if (pass == 0) {
+            for (long long t = 0; t < nt; ++t) T->start[t + 1] = T->start[t] + cnt[t];
+            memset(cnt, 0, sizeof(long long) * (size_t)nt);
+            T->cand = (or_cand*)malloc(sizeof(or_cand) * (size_t)(T->start[nt] > 0 ? T->start[nt] : 1));
+            if (!T->cand) { free(rect); free(cnt); or_tiles_free(T); return -1; }
+        }
+    }
+    free(rect);
+    free(cnt);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long t = 0; t < nt; ++t)
+        qsort(T->cand + T->start[t], (size_t)(T->start[t + 1] - T->start[t]), sizeof(or_cand), or_cmp_cand);
+    return 0;
+}
+
+/* The tiled walk of one ray: its tile's candidates in (depth, index) order. */
+static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long tile_id, const or_sensor* S,
+                               const double hu[4], const double hv[4], const double d[3], const double pc[2],
+                               or_ray* out)
+{
+    or_ray_init(out);
+    for (long long q = T->start[tile_id]; q < T->start[tile_id + 1] && !out->done; ++q) {
+        int i = T->cand[q].idx;
+        or_hit h;
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, &h)) or_step(out, &G[i], &h, S);
+    }
 }
 
 static or_surfel* or_prepare_all(int n, const or_sensor* S, const double* pos, const double* log_scale,
@@ -495,33 +823,62 @@ static or_surfel* or_prepare_all(int n, const or_sensor* S, const double* pos, c
 }
 
 /*
- * Pinhole camera frame (Eq. 3).  Pixel (x, y) has centre (x+0.5, y+0.5).
- * pix == NULL renders every pixel (n_pix = width*height, row-major), else
- * the n_pix listed pixels y*width+x.  Outputs are pixel-major:
- * rgb/normal [n_pix][3], the rest [n_pix].  rgb includes bg*T; depth is
- * sum(w z)/sum(w) (0 where sum(w) == 0); normal is sum(w n), unnormalised;
- * acc = [sum w, sum w z, sum w z^2] per pixel ([n_pix][3], may be NULL).
- * Returns 0, or -1 on bad arguments / allocation failure.
+ * One ray of a sensor: its two planes (Eq. 3, 4 or 5), the direction used
+ * for the depth of an intersection, and its low-pass centre.  (x, y) is the
+ * pixel column/row, or the LiDAR column/beam.
  */
-int oracle_render_pinhole(int n, const double* pos, const double* log_scale, const double* quat,
-                          const double* opacity_logit, int sh_degree, const double* sh,
-                          const int* obj_id, const double* obj_pose,
-                          int width, int height, double fx, double fy, double cx, double cy,
-                          double near_, const double* world_to_cam, const double* bg,
-                          int n_pix, const long long* pix,
-                          double* rgb, double* depth, double* normal, double* alpha, double* trans,
-                          double* acc, double* flip, int* n_contrib)
+static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double hv[4], double d[3], double pc[2])
 {
-    if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3) return -1;
-    or_sensor S;
-    memset(&S, 0, sizeof(S));
-    S.kind = 0;
-    or_sensor_from_matrix(&S, world_to_cam);
-    S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
-    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
-    if (!G) return -1;
-    long long npx = pix ? n_pix : (long long)width * height;
+    if (S->kind == 0) {
+        double px = x + 0.5, py = y + 0.5;
+        hu[0] = -1; hu[1] = 0; hu[2] = 0; hu[3] = px; /* Eq. 3 */
+        hv[0] = 0; hv[1] = -1; hv[2] = 0; hv[3] = py;
+        d[0] = 0; d[1] = 0; d[2] = 1;
+        pc[0] = px; pc[1] = py;
+    } else if (S->kind == 2) {
+        double px = x + 0.5, py = y + 0.5;
+        double phi = (px - S->cx) / S->fx, yn = (py - S->cy) / S->fy;
+        hu[0] = cos(phi); hu[1] = 0; hu[2] = -sin(phi); hu[3] = 0; /* Eq. 4 */
+        hv[0] = yn * sin(phi); hv[1] = -1; hv[2] = yn * cos(phi); hv[3] = 0;
+        d[0] = sin(phi); d[1] = 0; d[2] = cos(phi); /* horizontal part of the ray */
+        pc[0] = px; pc[1] = py;
+    } else {
+        double el = S->el_max - y * S->d_el;
+        double az = S->az0 + (x + 0.5) * S->d_az;
+        hu[0] = sin(az); hu[1] = -cos(az); hu[2] = 0; hu[3] = 0; /* Eq. 5 */
+        hv[0] = sin(el) * cos(az); hv[1] = sin(el) * sin(az); hv[2] = -cos(el); hv[3] = 0;
+        d[0] = cos(el) * cos(az); d[1] = cos(el) * sin(az); d[2] = sin(el);
+        pc[0] = (double)x; pc[1] = (double)y;
+    }
+}
+
+/*
+ * Every listed ray of a sensor (pix == NULL: all nx * ny rays, row-major),
+ * brute force (tile == 0) or over per-tile lists (tile > 0); the same
+ * compositing either way.  emit(q, ray, ctx) stores ray q's outputs.
+ */
+typedef void (*or_emit_fn)(long long q, const or_ray* r, void* ctx);
+
+static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx, int ny, long long nq,
+                          const long long* pix, int tile, or_emit_fn emit, void* ctx)
+{
     int fail = 0;
+    if (tile > 0) {
+        or_tiles T;
+        if (or_tiles_build(&T, G, n, S, tile, nx, ny) != 0) return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (long long q = 0; q < nq; ++q) {
+            long long li = pix ? pix[q] : q;
+            int x = (int)(li % nx), y = (int)(li / nx);
+            double hu[4], hv[4], d[3], pc[2];
+            or_ray_planes(S, x, y, hu, hv, d, pc);
+            or_ray r;
+            or_composite_tiled(G, &T, (long long)(y / tile) * T.tiles_x + x / tile, S, hu, hv, d, pc, &r);
+            emit(q, &r, ctx);
+        }
+        or_tiles_free(&T);
+        return 0;
+    }
 #pragma omp parallel
     {
         or_hit* buf = (or_hit*)malloc(sizeof(or_hit) * (size_t)(n > 0 ? n : 1));
@@ -530,30 +887,89 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
             fail = 1;
         } else {
 #pragma omp for schedule(dynamic, 16)
-            for (long long q = 0; q < npx; ++q) {
+            for (long long q = 0; q < nq; ++q) {
                 long long li = pix ? pix[q] : q;
-                int x = (int)(li % width), y = (int)(li / width);
-                double px = x + 0.5, py = y + 0.5;
-                double hu[4] = {-1, 0, 0, px}; /* Eq. 3 */
-                double hv[4] = {0, -1, 0, py};
-                double pc[2] = {px, py};
-                double d[3] = {0, 0, 1};
+                int x = (int)(li % nx), y = (int)(li / nx);
+                double hu[4], hv[4], d[3], pc[2];
+                or_ray_planes(S, x, y, hu, hv, d, pc);
                 or_ray r;
-                or_composite(G, n, &S, hu, hv, d, pc, buf, &r);
-                for (int ch = 0; ch < 3; ++ch) rgb[q * 3 + ch] = r.feat[ch] + r.T * bg[ch];
-                depth[q] = r.A > 0 ? r.B / r.A : 0.0;
-                for (int a = 0; a < 3; ++a) normal[q * 3 + a] = r.N[a];
-                alpha[q] = r.A;
-                trans[q] = r.T;
-                if (acc) { acc[q * 3 + 0] = r.A; acc[q * 3 + 1] = r.B; acc[q * 3 + 2] = r.D; }
-                if (flip) flip[q] = r.flip;
-                if (n_contrib) n_contrib[q] = r.n_contrib;
+                or_composite(G, n, S, hu, hv, d, pc, buf, &r);
+                emit(q, &r, ctx);
             }
             free(buf);
         }
     }
-    free(G);
     return fail ? -1 : 0;
+}
+
+typedef struct {
+    const double* bg;
+    double *rgb, *depth, *normal, *alpha, *trans, *acc, *flip;
+    int* n_contrib;
+} or_cam_out;
+
+static void or_emit_camera(long long q, const or_ray* r, void* ctx)
+{
+    or_cam_out* o = (or_cam_out*)ctx;
+    for (int ch = 0; ch < 3; ++ch) o->rgb[q * 3 + ch] = r->feat[ch] + r->T * o->bg[ch];
+    o->depth[q] = r->A > 0 ? r->B / r->A : 0.0;
+    for (int a = 0; a < 3; ++a) o->normal[q * 3 + a] = r->N[a];
+    o->alpha[q] = r->A;
+    o->trans[q] = r->T;
+    if (o->acc) { o->acc[q * 3 + 0] = r->A; o->acc[q * 3 + 1] = r->B; o->acc[q * 3 + 2] = r->D; }
+    if (o->flip) o->flip[q] = r->flip;
+    if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
+}
+
+static int or_render_camera(int kind, int n, const double* pos, const double* log_scale, const double* quat,
+                            const double* opacity_logit, int sh_degree, const double* sh,
+                            const int* obj_id, const double* obj_pose,
+                            int width, int height, double fx, double fy, double cx, double cy,
+                            double near_, const double* world_to_cam, const double* bg,
+                            int n_pix, const long long* pix, int tile,
+                            double* rgb, double* depth, double* normal, double* alpha, double* trans,
+                            double* acc, double* flip, int* n_contrib)
+{
+    if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3 || tile < 0) return -1;
+    or_sensor S;
+    memset(&S, 0, sizeof(S));
+    S.kind = kind;
+    or_sensor_from_matrix(&S, world_to_cam);
+    S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
+    S.width = width; S.height = height;
+    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
+    if (!G) return -1;
+    long long npx = pix ? n_pix : (long long)width * height;
+    or_cam_out o = {bg, rgb, depth, normal, alpha, trans, acc, flip, n_contrib};
+    int rc = or_render_rays(G, n, &S, width, height, npx, pix, tile, or_emit_camera, &o);
+    free(G);
+    return rc;
+}
+
+/*
+ * Pinhole camera frame (Eq. 3).  Pixel (x, y) has centre (x+0.5, y+0.5).
+ * pix == NULL renders every pixel (n_pix = width*height, row-major), else
+ * the n_pix listed pixels y*width+x.  Outputs are pixel-major:
+ * rgb/normal [n_pix][3], the rest [n_pix].  rgb includes bg*T; depth is
+ * sum(w z)/sum(w) (0 where sum(w) == 0); normal is sum(w n), unnormalised;
+ * acc = [sum w, sum w z, sum w z^2] per pixel ([n_pix][3], may be NULL).
+ * tile == 0 checks every surfel for every pixel (brute force); tile > 0
+ * walks per-tile candidate lists of tile x tile pixels built from the
+ * oracle's own conservative bound, with the same arithmetic and the same
+ * results.  Returns 0, or -1 on bad arguments / allocation failure.
+ */
+int oracle_render_pinhole(int n, const double* pos, const double* log_scale, const double* quat,
+                          const double* opacity_logit, int sh_degree, const double* sh,
+                          const int* obj_id, const double* obj_pose,
+                          int width, int height, double fx, double fy, double cx, double cy,
+                          double near_, const double* world_to_cam, const double* bg,
+                          int n_pix, const long long* pix, int tile,
+                          double* rgb, double* depth, double* normal, double* alpha, double* trans,
+                          double* acc, double* flip, int* n_contrib)
+{
+    return or_render_camera(0, n, pos, log_scale, quat, opacity_logit, sh_degree, sh, obj_id, obj_pose, width,
+                            height, fx, fy, cx, cy, near_, world_to_cam, bg, n_pix, pix, tile, rgb, depth, normal,
+                            alpha, trans, acc, flip, n_contrib);
 }
 
 /*
@@ -567,60 +983,37 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
  * (cos phi, 0, -sin phi): h_v = (y_n sin phi, -1, y_n cos phi, 0), normal to
  * h_u as the paper's two planes are.  Depth is the horizontal distance t of
  * the intersection t d (the cylinder radius).
- * Outputs as oracle_render_pinhole.
+ * Outputs and `tile` as oracle_render_pinhole.
  */
 int oracle_render_cylindrical(int n, const double* pos, const double* log_scale, const double* quat,
                               const double* opacity_logit, int sh_degree, const double* sh,
                               const int* obj_id, const double* obj_pose,
                               int width, int height, double fx, double fy, double cx, double cy,
                               double near_, const double* world_to_cam, const double* bg,
-                              int n_pix, const long long* pix,
+                              int n_pix, const long long* pix, int tile,
                               double* rgb, double* depth, double* normal, double* alpha, double* trans,
                               double* acc, double* flip, int* n_contrib)
 {
-    if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3) return -1;
-    or_sensor S;
-    memset(&S, 0, sizeof(S));
-    S.kind = 2;
-    or_sensor_from_matrix(&S, world_to_cam);
-    S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
-    or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
-    if (!G) return -1;
-    long long npx = pix ? n_pix : (long long)width * height;
-    int fail = 0;
-#pragma omp parallel
-    {
-        or_hit* buf = (or_hit*)malloc(sizeof(or_hit) * (size_t)(n > 0 ? n : 1));
-        if (!buf) {
-#pragma omp atomic write
-            fail = 1;
-        } else {
-#pragma omp for schedule(dynamic, 16)
-            for (long long q = 0; q < npx; ++q) {
-                long long li = pix ? pix[q] : q;
-                int x = (int)(li % width), y = (int)(li / width);
-                double px = x + 0.5, py = y + 0.5;
-                double phi = (px - cx) / fx, yn = (py - cy) / fy;
-                double hu[4] = {cos(phi), 0, -sin(phi), 0}; /* Eq. 4 */
-                double hv[4] = {yn * sin(phi), -1, yn * cos(phi), 0};
-                double pc[2] = {px, py};
-                double dh[3] = {sin(phi), 0, cos(phi)};   /* horizontal part of the ray */
-                or_ray r;
-                or_composite(G, n, &S, hu, hv, dh, pc, buf, &r);
-                for (int ch = 0; ch < 3; ++ch) rgb[q * 3 + ch] = r.feat[ch] + r.T * bg[ch];
-                depth[q] = r.A > 0 ? r.B / r.A : 0.0;
-                for (int a = 0; a < 3; ++a) normal[q * 3 + a] = r.N[a];
-                alpha[q] = r.A;
-                trans[q] = r.T;
-                if (acc) { acc[q * 3 + 0] = r.A; acc[q * 3 + 1] = r.B; acc[q * 3 + 2] = r.D; }
-                if (flip) flip[q] = r.flip;
-                if (n_contrib) n_contrib[q] = r.n_contrib;
-            }
-            free(buf);
-        }
-    }
-    free(G);
-    return fail ? -1 : 0;
+    return or_render_camera(2, n, pos, log_scale, quat, opacity_logit, sh_degree, sh, obj_id, obj_pose, width,
+                            height, fx, fy, cx, cy, near_, world_to_cam, bg, n_pix, pix, tile, rgb, depth, normal,
+                            alpha, trans, acc, flip, n_contrib);
+}
+
+typedef struct {
+    double *range, *intens, *drop, *alpha, *trans, *flip;
+    int* n_contrib;
+} or_lidar_out;
+
+static void or_emit_lidar(long long q, const or_ray* r, void* ctx)
+{
+    or_lidar_out* o = (or_lidar_out*)ctx;
+    o->range[q] = r->A > 0 ? r->B / r->A : 0.0;
+    o->intens[q] = r->feat[0];
+    if (o->drop) o->drop[q] = r->feat[1] + r->T;
+    o->alpha[q] = r->A;
+    o->trans[q] = r->T;
+    if (o->flip) o->flip[q] = r->flip;
+    if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 
 /*
@@ -631,18 +1024,19 @@ int oracle_render_cylindrical(int n, const double* pos, const double* log_scale,
  * ray-drop probability sum(w rho) + T with rho = sigmoid(ray_drop logit)
  * of each surfel (Sec. III-A lists rho among the LiDAR scene's attributes;
  * composited like the intensity, a ray that leaves the scene returns
- * nothing).  ray_drop may be NULL (rho = 0).
+ * nothing).  ray_drop may be NULL (rho = 0).  `tile` as for the cameras
+ * (tiles of tile beams x tile columns; columns wrap).
  */
 int oracle_render_lidar(int n, const double* pos, const double* log_scale, const double* quat,
                         const double* opacity_logit, const double* intensity, const double* ray_drop,
                         const int* obj_id, const double* obj_pose,
                         int beams, int columns, double el_min_deg, double el_max_deg, double az0_deg,
                         double near_, const double* world_to_lidar,
-                        int n_ray, const long long* ray,
+                        int n_ray, const long long* ray, int tile,
                         double* range, double* intens, double* drop, double* alpha, double* trans, double* flip,
                         int* n_contrib)
 {
-    if (n < 0 || beams < 2 || columns <= 0) return -1;
+    if (n < 0 || beams < 2 || columns <= 0 || tile < 0) return -1;
     or_sensor S;
     memset(&S, 0, sizeof(S));
     S.kind = 1;
@@ -657,39 +1051,10 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
                                   obj_pose);
     if (!G) return -1;
     long long nr = ray ? n_ray : (long long)beams * columns;
-    int fail = 0;
-#pragma omp parallel
-    {
-        or_hit* buf = (or_hit*)malloc(sizeof(or_hit) * (size_t)(n > 0 ? n : 1));
-        if (!buf) {
-#pragma omp atomic write
-            fail = 1;
-        } else {
-#pragma omp for schedule(dynamic, 16)
-            for (long long q = 0; q < nr; ++q) {
-                long long li = ray ? ray[q] : q;
-                int j = (int)(li % columns), i = (int)(li / columns);
-                double el = S.el_max - i * S.d_el;
-                double az = S.az0 + (j + 0.5) * S.d_az;
-                double hu[4] = {sin(az), -cos(az), 0, 0}; /* Eq. 5 */
-                double hv[4] = {sin(el) * cos(az), sin(el) * sin(az), -cos(el), 0};
-                double d[3] = {cos(el) * cos(az), cos(el) * sin(az), sin(el)};
-                double pc[2] = {(double)j, (double)i};
-                or_ray r;
-                or_composite(G, n, &S, hu, hv, d, pc, buf, &r);
-                range[q] = r.A > 0 ? r.B / r.A : 0.0;
-                intens[q] = r.feat[0];
-                if (drop) drop[q] = r.feat[1] + r.T;
-                alpha[q] = r.A;
-                trans[q] = r.T;
-                if (flip) flip[q] = r.flip;
-                if (n_contrib) n_contrib[q] = r.n_contrib;
-            }
-            free(buf);
-        }
-    }
+    or_lidar_out o = {range, intens, drop, alpha, trans, flip, n_contrib};
+    int rc = or_render_rays(G, n, &S, columns, beams, nr, ray, tile, or_emit_lidar, &o);
     free(G);
-    return fail ? -1 : 0;
+    return rc;
 }
 
 /* Number of threads the OpenMP runtime will use (for the benchmark report). */
@@ -738,9 +1103,8 @@ int oracle_intersect(int kind, const double* pos, const double* log_scale, const
     or_hit h;
     or_eval(&G, &S, hu, hv, d, pc, &h);
     if (!h.hasplane) return 0;
-    uvz[0] = sqrt(h.rho3); /* |(u,v)| */
     uvz[2] = h.zint;
-    /* recover signed u, v from k x l again */
+    /* signed u, v from k x l */
     {
         double k[3], l[3], m[3];
         for (int c = 0; c < 3; ++c) {

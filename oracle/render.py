@@ -1,4 +1,5 @@
-"""ctypes wrapper of the FP64 brute-force oracle (gsr_oracle.c).
+"""ctypes wrapper of the FP64 oracle (gsr_oracle.c): brute force, or the
+same arithmetic over per-tile candidate lists (`tile` > 0).
 
 TEST INFRASTRUCTURE, NOT PRODUCT CODE (see the package docstring).
 """
@@ -44,14 +45,14 @@ def _load():
         lib.oracle_render_pinhole.argtypes = [
             c_int, D, D, D, D, c_int, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, c_double, D, D,
-            c_int, L, D, D, D, D, D, D, D, I]
+            c_int, L, c_int, D, D, D, D, D, D, D, I]
         lib.oracle_render_cylindrical.restype = c_int
         lib.oracle_render_cylindrical.argtypes = lib.oracle_render_pinhole.argtypes
         lib.oracle_render_lidar.restype = c_int
         lib.oracle_render_lidar.argtypes = [
             c_int, D, D, D, D, D, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, D,
-            c_int, L, D, D, D, D, D, D, I]
+            c_int, L, c_int, D, D, D, D, D, D, I]
         lib.oracle_sh_basis.restype = c_double
         lib.oracle_sh_basis.argtypes = [c_int, c_int, D]
         lib.oracle_num_threads.restype = c_int
@@ -83,9 +84,12 @@ def sh_basis(l: int, m: int, d) -> float:
     return float(_load().oracle_sh_basis(l, m, p))
 
 
-def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
-    """Brute-force FP64 render of a camera frame: pinhole (Eq. 3) or, for
-    cam.kind == "cylindrical", the cylindrical camera (Eq. 4).
+def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=0):
+    """FP64 render of a camera frame: pinhole (Eq. 3) or, for
+    cam.kind == "cylindrical", the cylindrical camera (Eq. 4).  tile == 0
+    checks every surfel for every pixel; tile > 0 walks per-tile candidate
+    lists (tile x tile pixels) from the oracle's own conservative bound,
+    with the same arithmetic and bit-identical results.
 
     `s` holds the surfel arrays (pos, log_scale, quat, opacity, sh, obj_id);
     `cam` the intrinsics and world_to_sensor.  `pixels` (optional) lists the
@@ -122,7 +126,7 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
         ids_p, P_p,
         int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
         float(cam.near), D(cam.world_to_sensor), D(np.asarray(bg, np.float64)),
-        int(npix), pix_p,
+        int(npix), pix_p, int(tile),
         dp["rgb"], dp["depth"], dp["normal"], dp["alpha"], dp["T"], dp["acc"], dp["flip"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:
@@ -133,8 +137,8 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None):
     return out
 
 
-def render_lidar(s, lid, rays=None, obj_pose=None):
-    """Brute-force FP64 LiDAR range image.  Returns range, intensity, drop
+def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
+    """FP64 LiDAR range image (tile as for render_pinhole; columns wrap).  Returns range, intensity, drop
     (ray-drop probability: sum w rho + T with rho = sigmoid of the surfels'
     ray_drop logit, 0 when `s` has none), alpha, T, flip, n_contrib (each
     [R], or [beams, columns] with rays=None)."""
@@ -163,7 +167,7 @@ def render_lidar(s, lid, rays=None, obj_pose=None):
         ids_p, P_p,
         int(lid.beams), int(lid.columns), float(lid.el_min_deg), float(lid.el_max_deg), float(lid.az0_deg),
         float(lid.near), D(lid.world_to_sensor),
-        int(nr), ray_p,
+        int(nr), ray_p, int(tile),
         dp["range"], dp["intensity"], dp["drop"], dp["alpha"], dp["T"], dp["flip"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:

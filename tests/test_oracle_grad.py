@@ -264,3 +264,73 @@ def test_depth_normal_of_a_plane_cylindrical():
     pin = synth.Pinhole(W, H, cam.fx, cam.fy, cam.cx, cam.cy, np.eye(4), 0.2)
     _, parts_pin = OG.loss(out, torch.zeros(H, W, 3, dtype=torch.float64), pin)
     assert float(parts_pin["normal"]) > 1e-3
+
+
+def _loss_example(A_edge=1.0):
+    """3x3 image, fx = fy = 1, principal point (1.5, 1.5): the centre pixel's
+    ray is the optical axis and pixel (x, y) back-projects its depth d to
+    d (x - 1, y - 1, 1).  Every pixel renders rgb 0.5, A = 1, B = 2 (depth 2),
+    D = 4 (no spread) except where stated; A of pixel (2, 1) is A_edge."""
+    cam = synth.Pinhole(3, 3, 1.0, 1.0, 1.5, 1.5, np.eye(4), 0.2)
+    rgb = torch.full((3, 3, 3), 0.5, dtype=torch.float64)
+    target = rgb.clone()
+    target[0, 0, 0] = 0.2          # |0.5 - 0.2| = 0.3
+    target[1, 2, 2] = 1.0          # |0.5 - 1.0| = 0.5
+    A = torch.ones(3, 3, dtype=torch.float64)
+    A[1, 2] = A_edge
+    B = 2.0 * A                    # depth B / A = 2 everywhere
+    D = 4.0 * A
+    D[1, 1] = 4.5                  # centre: A D - B^2 = 4.5 - 4 = 0.5
+    D[0, 2] = 4.09                 # corner: 4.09 - 4 = 0.09
+    Nr = torch.zeros(3, 3, 3, dtype=torch.float64)
+    Nr[1, 1] = torch.tensor([0.0, 0.0, -0.5], dtype=torch.float64)
+    out = {"rgb": rgb, "A": A, "B": B, "D": D, "normal": Nr}
+    return out, target, cam
+
+
+def test_camera_loss_worked_example():
+    """The camera loss on a 3x3 image worked by hand:
+    L1 = (0.3 + 0.5) / 27 (mean over 3 H W);
+    distortion = (0.5 + 0.09) / 9 (mean over the pixels of A D - B^2);
+    normal term: only the centre pixel is interior.  Its four neighbours lie
+    on the plane z = 2, so dX = X(2,1) - X(0,1) = (4, 0, 0),
+    dY = X(1,2) - X(1,0) = (0, 4, 0), N_d = normalise(dY x dX) = (0, 0, -1),
+    and 1 - N . N_d = 1 - 0.5 = 0.5, summed and divided by H W = 9.
+    L = L1 + 0.1 distortion + 0.05 normal.  A sum in place of a mean, or a
+    3 H W / H W slip, changes a term by a factor of 3, 9 or 27."""
+    out, target, cam = _loss_example()
+    L, parts = OG.loss(out, target, cam)
+    assert float(parts["l1"]) == pytest.approx(0.8 / 27, rel=1e-14)
+    assert float(parts["dist"]) == pytest.approx(0.59 / 9, rel=1e-14)
+    assert float(parts["normal"]) == pytest.approx(0.5 / 9, rel=1e-14)
+    assert float(L) == pytest.approx(0.8 / 27 + 0.1 * 0.59 / 9 + 0.05 * 0.5 / 9, rel=1e-14)
+    # a neighbour with A below 0.5 masks the centre pixel's normal term
+    out, target, cam = _loss_example(A_edge=0.4)
+    L, parts = OG.loss(out, target, cam)
+    assert float(parts["normal"]) == 0.0
+    assert float(parts["dist"]) == pytest.approx((0.5 + 0.09 + (0.4 * 1.6 - 0.8 ** 2)) / 9, rel=1e-14)
+
+
+def test_camera_loss_worked_example_gradients():
+    """Gradients of the worked example in closed form: dL/drgb =
+    sign(rgb - target) / 27; dL/dD = 0.1 A / 9; dL/dB = -0.1 2 B / 9 away
+    from the pixels whose depth feeds the normal term; dL/dN at the centre =
+    -0.05 N_d / 9."""
+    out, target, cam = _loss_example()
+    leaves = {k: v.clone().requires_grad_(True) for k, v in out.items()}
+    L, _ = OG.loss(leaves, target, cam)
+    L.backward()
+    g = {k: v.grad for k, v in leaves.items()}
+    want = torch.zeros(3, 3, 3, dtype=torch.float64)
+    want[0, 0, 0] = 1.0 / 27
+    want[1, 2, 2] = -1.0 / 27
+    assert torch.allclose(g["rgb"], want, rtol=0, atol=1e-15)
+    assert torch.allclose(g["D"], 0.1 * out["A"] / 9, rtol=1e-14, atol=0)
+    # B also moves the back-projected depth B / A of the normal term; only
+    # the centre's four neighbours enter it, so compare the other pixels
+    far = torch.ones(3, 3, dtype=torch.bool)
+    far[0, 1] = far[1, 0] = far[1, 2] = far[2, 1] = False
+    assert torch.allclose(g["B"][far], (-0.1 * 2 * out["B"] / 9)[far], rtol=1e-14, atol=0)
+    wantN = torch.zeros(3, 3, 3, dtype=torch.float64)
+    wantN[1, 1] = torch.tensor([0.0, 0.0, 0.05 / 9], dtype=torch.float64)
+    assert torch.allclose(g["normal"], wantN, rtol=1e-14, atol=1e-17)

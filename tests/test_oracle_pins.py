@@ -488,3 +488,114 @@ def test_zone_membership_geometry():
     sets = [sorted(z for z in range(9) if k in m[z]) for k in range(len(pos))]
     assert sets == [[4], [3, 4], [0, 1, 3, 4], [], [2]]
     assert OZ.zone_of(g, 60.0, 60.0) == 4 and OZ.zone_of(g, 41.0, 60.0) == 4 and OZ.zone_of(g, -1.0, 5.0) == -1
+
+
+# ------------------------------------------------- tiled mode = brute force
+def _near_plane_scene(seed):
+    """Plain scene with a fifth of the surfels pulled to centre depths around
+    the near plane (0.2 m), some of them within rounding of it."""
+    s = synth.plain_scene(n=1500, seed=seed)
+    rng = np.random.default_rng(seed)
+    pos = s.pos.astype(np.float64)
+    k = rng.choice(s.n, s.n // 5, replace=False)
+    pos[k, 2] = rng.uniform(0.05, 1.5, len(k))
+    pos[k[:8], 2] = 0.2 * (1 + rng.choice([-1, 1], 8) * 1e-7)
+    pos[k, :2] *= 0.05
+    return synth.Surfels(pos, s.log_scale.astype(np.float64), s.quat.astype(np.float64),
+                         s.opacity.astype(np.float64), s.sh.astype(np.float64), s.intensity.astype(np.float64))
+
+
+def _tiled_cases():
+    plain = synth.plain_scene(n=2000, seed=3)
+    drive = synth.driving_scene(n=6000, seed=11, x_range=(-20.0, 30.0), n_boxes=4)
+    obj = synth.object_asset(n=3000, seed=4)
+    obj.obj_id = np.zeros(obj.n, np.int32) + (np.arange(obj.n) % 2).astype(np.int32)
+    poses = synth.object_poses(2, seed=8, x_range=(6.0, 14.0))
+    rng = np.random.default_rng(12)
+    n = 1500
+    ang = rng.uniform(np.pi - 0.3, np.pi + 0.3, n)
+    dist = rng.uniform(0.5, 12.0, n)
+    seam = synth.Surfels(np.stack([dist * np.cos(ang), dist * np.sin(ang), rng.uniform(-1.5, 1.5, n)], 1),
+                         rng.uniform(-3, 0, (n, 2)), synth._unit_quats(rng, n).astype(np.float64),
+                         rng.normal(0, 1, n), rng.normal(0, 0.2, (n, 1, 3)), rng.uniform(0, 1, n))
+    return [
+        ("pinhole plain", plain, synth.plain_camera(96, 64, 80.0), None),
+        ("pinhole near plane", _near_plane_scene(5), synth.plain_camera(80, 56, 60.0), None),
+        ("pinhole posed objects", obj, synth.pinhole(72, 40, 60.0, (0.0, 0.5, 1.2), yaw_deg=4.0), poses),
+        ("cylinder 240 deg", drive, synth.cylindrical(120, 40, 240.0, 50.0, (0.0, 0.0, 1.5), pitch_deg=-6.0), None),
+        ("lidar drive", drive, synth.spinning_lidar(16, 180, -25.0, 15.0, (0.0, 0.0, 1.8)), None),
+        ("lidar seam", seam, synth.spinning_lidar(12, 150, -20.0, 20.0, (0.0, 0.0, 0.0)), None),
+        ("lidar posed objects", obj, synth.spinning_lidar(10, 200, -20.0, 10.0, (0.0, 0.0, 1.8)), poses),
+    ]
+
+
+@pytest.mark.parametrize("case", range(7))
+def test_tiled_mode_equals_brute_force(case):
+    """Per-tile candidate lists from the oracle's own conservative bound give
+    bit-identical outputs (flip values and contributor counts included) to
+    checking every surfel for every ray, at several tile sizes: the bound
+    misses no surfel that any ray of its tiles could see."""
+    name, s, sensor, poses = _tiled_cases()[case]
+    render = R.render_lidar if sensor.kind == "lidar" else R.render_pinhole
+    brute = render(s, sensor, obj_pose=poses)
+    assert brute["alpha"].max() > 0.5, name
+    for tile in (4, 8, 16):
+        tiled = render(s, sensor, obj_pose=poses, tile=tile)
+        for k in brute:
+            assert np.array_equal(brute[k], tiled[k]), (name, tile, k)
+
+
+# ----------------------------------------------- FP32-flippable decisions
+def test_order_near_tie_is_flagged():
+    """Two facing surfels on the optical axis.  Depths 1 mm apart: composited
+    in depth order, nothing flagged.  Depths 1e-7 m apart (below what an FP32
+    evaluation of a 10 m depth resolves): still composited in FP64 depth
+    order, and the ray carries the change a swap would make, the weight
+    o1 o2 moved between colours that differ by 1 in red and blue."""
+    cam = _cam()
+    pix = [16 * 33 + 16]
+    o1, o2 = 0.6, 0.7
+    for dz, flagged in ((1e-3, False), (1e-7, True)):
+        a = _one((0, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1), rgb=(1, 0, 0))
+        b = _one((0, 0, 10.0 + dz), (0, 0), (1, 0, 0, 0), _logit(o2), rgb=(0, 0, 1))
+        for s in (a.concat(b), b.concat(a)):
+            out = R.render_pinhole(s, cam, pixels=pix)
+            assert out["rgb"][0] == pytest.approx([o1, 0, (1 - o1) * o2], abs=1e-12)
+            if flagged:
+                assert out["flip"][0] == pytest.approx(o1 * o2 * 1.0, rel=1e-9)
+            else:
+                assert out["flip"][0] == 0.0
+    # equal colours and normals: a swap changes only the depth, by
+    # o1 o2 |dz| relative to the depth -- far below any tolerance
+    a = _one((0, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1))
+    b = _one((0, 0, 10.0 + 1e-7), (0, 0), (1, 0, 0, 0), _logit(o2))
+    out = R.render_pinhole(a.concat(b), cam, pixels=pix)
+    assert out["flip"][0] == pytest.approx(o1 * o2 * 1e-8, rel=1e-6)
+
+
+def test_near_cull_within_rounding_is_flagged():
+    """A surfel tilted 60 degrees about x whose centre depth sits within
+    rounding of the near plane (0.2 m), seen by pixels whose rays meet it
+    0.03-0.1 m beyond the centre: just in front it is composited, just
+    behind it is culled; either way the rays it reaches are flagged with the
+    weight it has (or would have)."""
+    cam = _cam(W=65, H=65, f=40.0)
+    q = (math.cos(math.pi / 6), math.sin(math.pi / 6), 0, 0)
+    res = {}
+    for sign in (1, -1):
+        z = 0.2 * (1 + sign * 1e-7)
+        s = _one((0, 0, z), (math.log(0.05), math.log(0.05)), q, _logit(0.9))
+        res[sign] = R.render_pinhole(s, cam)
+    seen = res[1]["alpha"] > 0
+    assert seen.sum() > 20
+    assert np.array_equal(res[1]["flip"][seen], res[1]["alpha"][seen])
+    assert np.all(res[-1]["alpha"] == 0.0)
+    # the two centres differ by 4e-8 m, so the weights agree to about that
+    assert np.abs(res[-1]["flip"] - res[1]["flip"]).max() < 1e-6
+    assert np.array_equal(res[-1]["flip"] > 0, res[1]["flip"] > 0)
+    # a centre 1 % in front of the near plane raises no flag
+    s = _one((0, 0, 0.202), (math.log(0.05), math.log(0.05)), q, _logit(0.9))
+    far = R.render_pinhole(s, cam)
+    assert far["alpha"].max() > 0.5
+    on = far["alpha"] > 0
+    assert np.all(far["flip"][on] < far["alpha"][on])

@@ -76,6 +76,16 @@ def rig_neural(bg):
     return anchors, synth.init_mlp(synth.SEED_BASE + 42)
 
 
+def rig_renderer(n, sensors, max_dup=400_000_000, camera_tile=(16, 16), lidar_tile=(8, 8), batch_depth=0,
+                 split=(0, 0), lidar_split=(0, 0), outputs=("rgb", "depth", "normal", "alpha", "trans", "n_contrib",
+                                                            "n_walk")):
+    """The rig's plan before autotuning: one tile shape per sensor kind."""
+    from paper_2503_11731_gb300.frame import Renderer
+    tiles = [lidar_tile if s.kind == "lidar" else camera_tile for s in sensors]
+    return Renderer(n, sensors, tile=(16, 16), max_dup=max_dup, tiles=tiles, batch_depth=batch_depth, split=split,
+                    lidar_split=lidar_split, outputs=outputs)
+
+
 def rig_origin(sensors):
     """Decode view origin of a rig: the mean of its sensor centres."""
     c = [-s.world_to_sensor[:3, :3].T @ s.world_to_sensor[:3, 3] for s in sensors]
@@ -704,11 +714,10 @@ def run_gpu(args):
     else:
         scene, poses, sensors, wl_desc = explicit_workload()
         objs = anchors = None
-    tiles = [parse(args.lidar_tile) if s.kind == "lidar" else parse(args.camera_tile) for s in sensors]
-    r = Renderer(scene.n, sensors, tile=(16, 16), max_dup=args.max_dup, tiles=tiles, batch_depth=args.batch_depth,
-                 split=(args.split_first, args.split_chunk),
-                 lidar_split=(args.lidar_split_first, args.lidar_split_chunk),
-                 outputs=("rgb", "depth", "normal", "alpha", "n_contrib", "n_walk"))
+    r = rig_renderer(scene.n, sensors, args.max_dup, parse(args.camera_tile), parse(args.lidar_tile),
+                     args.batch_depth, (args.split_first, args.split_chunk),
+                     (args.lidar_split_first, args.lidar_split_chunk),
+                     outputs=("rgb", "depth", "normal", "alpha", "n_contrib", "n_walk"))
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
     pose_t = None if poses is None else torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")

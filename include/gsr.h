@@ -583,6 +583,22 @@ gsr_status gsr_frame_graph_destroy(gsr_frame_graph* graph);
 gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t* device_status,
                            int64_t* n_visible, int64_t* n_pairs, void* stream);
 
+/*
+ * Self-test of the device-side give-up path (no counterpart in the paper:
+ * the bounded waits are this library's, not the method's).  Launches one
+ * CTA that arms an mbarrier for 16 bytes no copy will deliver and waits on
+ * it with the library's bounded wait, `tries` tries (1 .. 2^20); the wait
+ * gives up, the kernel records GSR_ERR_TIMEOUT in the plan's status word
+ * (read it with gsr_read_status) and returns.  No copy or tensor-core
+ * operation is outstanding at any point, so the context stays usable; the
+ * next gsr_preprocess(_part) with first == 0 clears the status word.
+ * Async on `stream`; the workspace is the plan's (256-byte aligned).
+ * Errors: GSR_ERR_INVALID_ARG (null pointer, tries out of range),
+ * GSR_ERR_WORKSPACE, GSR_ERR_CUDA (launch failure).
+ */
+gsr_status gsr_selftest_wait_timeout(const gsr_plan* plan, void* workspace, size_t workspace_bytes, uint32_t tries,
+                                     void* stream);
+
 /* ------------------------------------------------------------- autotune */
 
 /*

@@ -214,16 +214,19 @@ static void or_surfel_world(int i, const double* pos, const double* quat, const 
 }
 
 /*
- * Unit roundoff of IEEE single precision.  A renderer that evaluates the
- * order key (an affine map of the surfel's centre, then for the LiDAR and
- * the cylinder a Euclidean norm) in FP32 can land anywhere within a few
- * roundoffs of the terms it sums; OR_KEY_ULPS roundoffs of the sum of the
- * terms' magnitudes is the bound used here (a dot product of length 3 plus
- * a translation, done twice for a posed object, accrues at most about 8
- * such errors in any evaluation order).
+ * Unit roundoff of IEEE single precision, and the error bound of the order
+ * key in FP32.  Each sensor-frame component of the centre is a sum of four
+ * terms, R_a0 m_0 + R_a1 m_1 + R_a2 m_2 + t_a; evaluated in FP32 (with or
+ * without fused multiply-adds, in any order) it is off by at most
+ * gamma_4 = 4u / (1 - 4u) times the sum of the terms' magnitudes (the
+ * standard bound for inner products, Higham, "Accuracy and Stability of
+ * Numerical Algorithms", Sec. 3.1).  A posed object's centre is itself such
+ * a sum, whose error the rotation carries on.  The norms of the LiDAR and
+ * cylinder keys add at most 3u relative for the squares, the sum and the
+ * square root.
  */
 #define OR_U32 (1.0 / 16777216.0)
-#define OR_KEY_ULPS 8.0
+#define OR_GAMMA4 (4.0 * OR_U32 / (1.0 - 4.0 * OR_U32))
 
 static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* pos,
                        const double* log_scale, const double* quat, const double* opacity_logit,
@@ -267,12 +270,17 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
             for (int c = 0; c < 4; ++c) G->WH[a][b] += W[a][c] * H[c][b];
         }
 
-    /* mu in the sensor frame, and the size of the terms of each component */
+    /* mu in the sensor frame, and the FP32 error bound of each component */
+    int posed = obj_id && obj_id[i] >= 0;
     double ms[3], msmag[3];
     for (int a = 0; a < 3; ++a) {
         ms[a] = S->Rs[a][0] * mu[0] + S->Rs[a][1] * mu[1] + S->Rs[a][2] * mu[2] + S->ts[a];
-        msmag[a] = fabs(S->ts[a]);
-        for (int b = 0; b < 3; ++b) msmag[a] += fabs(S->Rs[a][b]) * mag[b];
+        double terms = fabs(S->ts[a]), carried = 0.0;
+        for (int b = 0; b < 3; ++b) {
+            terms += fabs(S->Rs[a][b] * mu[b]);
+            carried += fabs(S->Rs[a][b]) * mag[b];
+        }
+        msmag[a] = OR_GAMMA4 * (terms + (posed ? carried : 0.0));
     }
     for (int a = 0; a < 3; ++a) G->ms[a] = ms[a];
     G->rad = 3.01 * (su > sv ? su : sv);
@@ -280,19 +288,19 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     /* order key and its FP32 error bound */
     if (S->kind == 0) {
         G->zc = ms[2];
-        G->tau = OR_KEY_ULPS * OR_U32 * msmag[2];
+        G->tau = msmag[2];
         G->c[0] = G->WH[0][2] / G->WH[2][2];
         G->c[1] = G->WH[1][2] / G->WH[2][2];
     } else if (S->kind == 2) {
         /* cylinder: column from the azimuth about the camera's y axis, row
            from the height over the horizontal distance (pixel units) */
         G->zc = sqrt(ms[0] * ms[0] + ms[2] * ms[2]);
-        G->tau = OR_KEY_ULPS * OR_U32 * (sqrt(msmag[0] * msmag[0] + msmag[2] * msmag[2]) + G->zc);
+        G->tau = sqrt(msmag[0] * msmag[0] + msmag[2] * msmag[2]) + 3.0 * OR_U32 * G->zc;
         G->c[0] = S->cx + S->fx * atan2(ms[0], ms[2]);
         G->c[1] = S->cy + S->fy * ms[1] / G->zc;
     } else {
         G->zc = sqrt(or_dot3(ms, ms));
-        G->tau = OR_KEY_ULPS * OR_U32 * (sqrt(or_dot3(msmag, msmag)) + G->zc);
+        G->tau = sqrt(or_dot3(msmag, msmag)) + 3.0 * OR_U32 * G->zc;
         double az = atan2(ms[1], ms[0]);
         double el = atan2(ms[2], sqrt(ms[0] * ms[0] + ms[1] * ms[1]));
         /* cell coordinates: ray (row i, column j) sits at (j, i) */
@@ -319,8 +327,11 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
         int k = 0;
         for (int l = 0; l <= sh_degree; ++l)
             for (int m = -l; m <= l; ++m, ++k) {
+                const double* c = sh + ((size_t)i * K + k) * 3;
+                /* a band of exact zeros adds exact zeros: skip the basis */
+                if (c[0] == 0.0 && c[1] == 0.0 && c[2] == 0.0) continue;
                 double Y = oracle_sh_basis(l, m, dl);
-                for (int ch = 0; ch < 3; ++ch) col[ch] += Y * sh[((size_t)i * K + k) * 3 + ch];
+                for (int ch = 0; ch < 3; ++ch) col[ch] += Y * c[ch];
             }
         for (int ch = 0; ch < 3; ++ch) G->feat[ch] = col[ch] > 0 ? col[ch] : 0.0;
     } else {
@@ -419,8 +430,9 @@ static int or_cmp_hit(const void* pa, const void* pb)
  * FP32 error bounds (tau).  The recorded effect is the largest change of an
  * output that taking the decision the other way could cause (T times the
  * jump in alpha; for the depth-branch choice, the relative jump in depth
- * weight; for an order swap, the weight the swap moves between the two
- * surfels times the largest difference of their outputs).
+ * weight; for a near-tied pair at the stop, the weight of either).  A
+ * near-tied pair that both composite does not flag the ray: the change a
+ * swap makes is exact and small, and is summed into the ray's slack.
  */
 #ifndef OR_FLIP_REL
 #define OR_FLIP_REL 2e-5
@@ -432,6 +444,9 @@ static int or_cmp_hit(const void* pa, const void* pb)
 typedef struct {
     double feat[3], A, B, D, N[3], T;
     double flip;      /* largest effect of a flippable decision, 0 if none */
+    double slack;     /* sum over near-tied pairs of the colour / intensity /
+                         normal change a swap of the pair makes            */
+    double slack_z;   /* the same for sum w z (the depth accumulator B)    */
     int n_contrib;
     int done;         /* the stop rule ended the ray                       */
     /* the last composited surfel, for the order check */
@@ -512,13 +527,14 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
         return;
     }
     if (tie) {
-        /* a swap moves weight alpha_prev alpha T_prev from one to the other */
+        /* a swap moves the weight alpha_prev alpha T_prev from one to the
+           other and leaves every later weight and T as they are: each
+           output changes by exactly that weight times the pair's difference
+           in it */
         double moved = r->prev_alpha * h->alpha * r->prev_T;
-        double dz = fabs(h->z - r->prev_z) / (h->z < r->prev_z ? h->z : r->prev_z);
         double df = or_maxdiff3(g->feat, r->prev_feat), dn = or_maxdiff3(g->normal, r->prev_n);
-        double m = df > dn ? df : dn;
-        if (dz > m) m = dz;
-        or_flip(&r->flip, 0.0, 1.0, moved * m);
+        r->slack += moved * (df > dn ? df : dn);
+        r->slack_z += moved * fabs(h->z - r->prev_z);
     }
     double w = h->alpha * T;
     for (int ch = 0; ch < 3; ++ch) r->feat[ch] += w * g->feat[ch];
@@ -580,9 +596,10 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
  * half-width 3.01 s in the surfel plane, and inside the sphere of radius
  * 3.01 max(s_u, s_v) about the centre; the low-pass disc lies within 2.13
  * pixels (cells) of the projected centre.
- *   pinhole   -- the projected square's four corners when all of them lie
- *                in front of the camera (a convex quadrilateral projects to
- *                the convex hull of its corners), else every pixel;
+ *   pinhole   -- the square clipped to the half-space in front of the near
+ *                plane (where an intersection can count), projected: a
+ *                convex polygon in front of the camera projects inside the
+ *                convex hull of its projected vertices;
  *   cylinder  -- the sphere's azimuth cone asin(r / r_h) and its height
  *                ratio y / r_h over the sphere's box, else every pixel;
  *   LiDAR     -- the sphere's cap of angular radius beta = asin(r / |mu|):
@@ -603,29 +620,40 @@ static int or_bound(const or_surfel* g, const or_sensor* S, double box[4], int* 
     const double* m = g->ms;
     const double r = g->rad;
     if (S->kind == 0) {
-        /* corners of the half-width 3.01 square, through W H (homogeneous) */
-        int front = 1;
-        double cx0 = INFINITY, cx1 = -INFINITY, cy0 = INFINITY, cy1 = -INFINITY;
-        for (int a = -1; a <= 1; a += 2)
-            for (int b = -1; b <= 1; b += 2) {
-                double u = 3.01 * a, v = 3.01 * b;
-                double X = g->WH[0][0] * u + g->WH[0][1] * v + g->WH[0][2];
-                double Y = g->WH[1][0] * u + g->WH[1][1] * v + g->WH[1][2];
-                double Z = g->WH[2][0] * u + g->WH[2][1] * v + g->WH[2][2];
-                if (!(Z > 0.5 * S->near_)) front = 0;
-                else {
-                    double px = X / Z, py = Y / Z;
-                    if (px < cx0) cx0 = px;
-                    if (px > cx1) cx1 = px;
-                    if (py < cy0) cy0 = py;
-                    if (py > cy1) cy1 = py;
-                }
+        /* the half-width 3.01 square in (u, v), clipped to the half-plane
+           where the intersection depth can pass the near test (depth is
+           affine in u, v), then projected through W H: a convex polygon in
+           front of the camera projects inside the convex hull of its
+           projected vertices */
+        double zmin = S->near_ * (1.0 - 2.0 * OR_NEAR_MISS);
+        double sq[4][2] = {{-3.01, -3.01}, {3.01, -3.01}, {3.01, 3.01}, {-3.01, 3.01}};
+        double poly[8][2];
+        int np_ = 0;
+        for (int k = 0; k < 4; ++k) {
+            const double* a = sq[k];
+            const double* b = sq[(k + 1) & 3];
+            double za = g->WH[2][0] * a[0] + g->WH[2][1] * a[1] + g->WH[2][2] - zmin;
+            double zb = g->WH[2][0] * b[0] + g->WH[2][1] * b[1] + g->WH[2][2] - zmin;
+            if (za >= 0) { poly[np_][0] = a[0]; poly[np_][1] = a[1]; ++np_; }
+            if ((za >= 0) != (zb >= 0)) {
+                double t = za / (za - zb);
+                poly[np_][0] = a[0] + t * (b[0] - a[0]);
+                poly[np_][1] = a[1] + t * (b[1] - a[1]);
+                ++np_;
             }
-        if (!front) { *all_x = *all_y = 1; return 1; }
-        if (cx0 < x0) x0 = cx0;
-        if (cx1 > x1) x1 = cx1;
-        if (cy0 < y0) y0 = cy0;
-        if (cy1 > y1) y1 = cy1;
+        }
+        for (int k = 0; k < np_; ++k) {
+            double u = poly[k][0], v = poly[k][1];
+            double X = g->WH[0][0] * u + g->WH[0][1] * v + g->WH[0][2];
+            double Y = g->WH[1][0] * u + g->WH[1][1] * v + g->WH[1][2];
+            double Z = g->WH[2][0] * u + g->WH[2][1] * v + g->WH[2][2];
+            if (!(Z > 0.5 * zmin)) { *all_x = *all_y = 1; return 1; } /* rounding at the clip */
+            double px = X / Z, py = Y / Z;
+            if (px < x0) x0 = px;
+            if (px > x1) x1 = px;
+            if (py < y0) y0 = py;
+            if (py > y1) y1 = py;
+        }
     } else if (S->kind == 2) {
         double rh = g->zc;
         if (!(rh - r > S->near_)) { *all_x = *all_y = 1; return 1; }
@@ -757,8 +785,10 @@ static int or_tiles_build(or_tiles* T, const or_surfel* G, int n, const or_senso
         if (!or_bound(&G[i], S, box, &ax, &ay)) { R[0] = 1; R[1] = 0; R[2] = 1; R[3] = 0; R[4] = 0; continue; }
         or_box_tiles(S, T, box, ax, ay, &R[0], &R[1], &R[2], &R[3], &R[4]);
     }
-    /* count, then fill in surfel order (lists are sorted afterwards) */
+    /* count, then fill (in any order: each list is sorted afterwards by
+       (depth, index), a total order, so the result does not depend on it) */
     for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 1024)
         for (int i = 0; i < n; ++i) {
             const int* R = rect + 5 * i;
             if (R[2] > R[3]) continue;
@@ -770,9 +800,14 @@ static int or_tiles_build(or_tiles* T, const or_surfel* G, int n, const or_senso
                     int b = R[4] ? (p == 0 ? T->tiles_x - 1 : R[1]) : R[1];
                     if (R[4] && p == 1 && b >= R[0]) b = R[0] - 1; /* pieces overlap: whole row once */
                     for (int tx = a; tx <= b; ++tx) {
-                        if (pass == 0) ++cnt[row + tx];
-                        else {
-                            long long at = T->start[row + tx] + cnt[row + tx]++;
+                        if (pass == 0) {
+#pragma omp atomic
+                            ++cnt[row + tx];
+                        } else {
+                            long long at;
+#pragma omp atomic capture
+                            at = cnt[row + tx]++;
+                            at += T->start[row + tx];
                             T->cand[at].zc = G[i].zc;
                             T->cand[at].idx = i;
                         }
@@ -904,7 +939,7 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
 
 typedef struct {
     const double* bg;
-    double *rgb, *depth, *normal, *alpha, *trans, *acc, *flip;
+    double *rgb, *depth, *normal, *alpha, *trans, *acc, *flip, *slack;
     int* n_contrib;
 } or_cam_out;
 
@@ -918,6 +953,7 @@ static void or_emit_camera(long long q, const or_ray* r, void* ctx)
     o->trans[q] = r->T;
     if (o->acc) { o->acc[q * 3 + 0] = r->A; o->acc[q * 3 + 1] = r->B; o->acc[q * 3 + 2] = r->D; }
     if (o->flip) o->flip[q] = r->flip;
+    if (o->slack) { o->slack[q * 2 + 0] = r->slack; o->slack[q * 2 + 1] = r->slack_z; }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 
@@ -928,7 +964,7 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
                             double near_, const double* world_to_cam, const double* bg,
                             int n_pix, const long long* pix, int tile,
                             double* rgb, double* depth, double* normal, double* alpha, double* trans,
-                            double* acc, double* flip, int* n_contrib)
+                            double* acc, double* flip, double* slack, int* n_contrib)
 {
     if (n < 0 || width <= 0 || height <= 0 || sh_degree < 0 || sh_degree > 3 || tile < 0) return -1;
     or_sensor S;
@@ -940,7 +976,7 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
     or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
     if (!G) return -1;
     long long npx = pix ? n_pix : (long long)width * height;
-    or_cam_out o = {bg, rgb, depth, normal, alpha, trans, acc, flip, n_contrib};
+    or_cam_out o = {bg, rgb, depth, normal, alpha, trans, acc, flip, slack, n_contrib};
     int rc = or_render_rays(G, n, &S, width, height, npx, pix, tile, or_emit_camera, &o);
     free(G);
     return rc;
@@ -953,6 +989,10 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
  * rgb/normal [n_pix][3], the rest [n_pix].  rgb includes bg*T; depth is
  * sum(w z)/sum(w) (0 where sum(w) == 0); normal is sum(w n), unnormalised;
  * acc = [sum w, sum w z, sum w z^2] per pixel ([n_pix][3], may be NULL).
+ * flip [n_pix] is the largest output change an FP32-flippable threshold
+ * decision could cause (0 if none); slack [n_pix][2] the summed change that
+ * swapping near-tied surfel pairs makes to colour / normal and to sum w z
+ * (both may be NULL).
  * tile == 0 checks every surfel for every pixel (brute force); tile > 0
  * walks per-tile candidate lists of tile x tile pixels built from the
  * oracle's own conservative bound, with the same arithmetic and the same
@@ -965,11 +1005,11 @@ int oracle_render_pinhole(int n, const double* pos, const double* log_scale, con
                           double near_, const double* world_to_cam, const double* bg,
                           int n_pix, const long long* pix, int tile,
                           double* rgb, double* depth, double* normal, double* alpha, double* trans,
-                          double* acc, double* flip, int* n_contrib)
+                          double* acc, double* flip, double* slack, int* n_contrib)
 {
     return or_render_camera(0, n, pos, log_scale, quat, opacity_logit, sh_degree, sh, obj_id, obj_pose, width,
                             height, fx, fy, cx, cy, near_, world_to_cam, bg, n_pix, pix, tile, rgb, depth, normal,
-                            alpha, trans, acc, flip, n_contrib);
+                            alpha, trans, acc, flip, slack, n_contrib);
 }
 
 /*
@@ -992,15 +1032,15 @@ int oracle_render_cylindrical(int n, const double* pos, const double* log_scale,
                               double near_, const double* world_to_cam, const double* bg,
                               int n_pix, const long long* pix, int tile,
                               double* rgb, double* depth, double* normal, double* alpha, double* trans,
-                              double* acc, double* flip, int* n_contrib)
+                              double* acc, double* flip, double* slack, int* n_contrib)
 {
     return or_render_camera(2, n, pos, log_scale, quat, opacity_logit, sh_degree, sh, obj_id, obj_pose, width,
                             height, fx, fy, cx, cy, near_, world_to_cam, bg, n_pix, pix, tile, rgb, depth, normal,
-                            alpha, trans, acc, flip, n_contrib);
+                            alpha, trans, acc, flip, slack, n_contrib);
 }
 
 typedef struct {
-    double *range, *intens, *drop, *alpha, *trans, *flip;
+    double *range, *intens, *drop, *alpha, *trans, *flip, *slack;
     int* n_contrib;
 } or_lidar_out;
 
@@ -1013,6 +1053,7 @@ static void or_emit_lidar(long long q, const or_ray* r, void* ctx)
     o->alpha[q] = r->A;
     o->trans[q] = r->T;
     if (o->flip) o->flip[q] = r->flip;
+    if (o->slack) { o->slack[q * 2 + 0] = r->slack; o->slack[q * 2 + 1] = r->slack_z; }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 
@@ -1024,8 +1065,9 @@ static void or_emit_lidar(long long q, const or_ray* r, void* ctx)
  * ray-drop probability sum(w rho) + T with rho = sigmoid(ray_drop logit)
  * of each surfel (Sec. III-A lists rho among the LiDAR scene's attributes;
  * composited like the intensity, a ray that leaves the scene returns
- * nothing).  ray_drop may be NULL (rho = 0).  `tile` as for the cameras
- * (tiles of tile beams x tile columns; columns wrap).
+ * nothing).  ray_drop may be NULL (rho = 0).  `tile`, flip and slack as
+ * for the cameras (tiles of tile beams x tile columns; columns wrap; the
+ * slack's first value covers intensity and ray drop).
  */
 int oracle_render_lidar(int n, const double* pos, const double* log_scale, const double* quat,
                         const double* opacity_logit, const double* intensity, const double* ray_drop,
@@ -1034,7 +1076,7 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
                         double near_, const double* world_to_lidar,
                         int n_ray, const long long* ray, int tile,
                         double* range, double* intens, double* drop, double* alpha, double* trans, double* flip,
-                        int* n_contrib)
+                        double* slack, int* n_contrib)
 {
     if (n < 0 || beams < 2 || columns <= 0 || tile < 0) return -1;
     or_sensor S;
@@ -1051,7 +1093,7 @@ int oracle_render_lidar(int n, const double* pos, const double* log_scale, const
                                   obj_pose);
     if (!G) return -1;
     long long nr = ray ? n_ray : (long long)beams * columns;
-    or_lidar_out o = {range, intens, drop, alpha, trans, flip, n_contrib};
+    or_lidar_out o = {range, intens, drop, alpha, trans, flip, slack, n_contrib};
     int rc = or_render_rays(G, n, &S, columns, beams, nr, ray, tile, or_emit_lidar, &o);
     free(G);
     return rc;

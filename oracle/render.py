@@ -45,14 +45,14 @@ def _load():
         lib.oracle_render_pinhole.argtypes = [
             c_int, D, D, D, D, c_int, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, c_double, D, D,
-            c_int, L, c_int, D, D, D, D, D, D, D, I]
+            c_int, L, c_int, D, D, D, D, D, D, D, D, I]
         lib.oracle_render_cylindrical.restype = c_int
         lib.oracle_render_cylindrical.argtypes = lib.oracle_render_pinhole.argtypes
         lib.oracle_render_lidar.restype = c_int
         lib.oracle_render_lidar.argtypes = [
             c_int, D, D, D, D, D, D, I, D,
             c_int, c_int, c_double, c_double, c_double, c_double, D,
-            c_int, L, c_int, D, D, D, D, D, D, I]
+            c_int, L, c_int, D, D, D, D, D, D, D, I]
         lib.oracle_sh_basis.restype = c_double
         lib.oracle_sh_basis.argtypes = [c_int, c_int, D]
         lib.oracle_num_threads.restype = c_int
@@ -96,7 +96,9 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
     linear pixel indices y*W+x to render.  Returns a dict of numpy arrays:
     rgb [P,3], depth [P], normal [P,3], alpha [P], T [P], acc [P,3]
     (sum w, sum w z, sum w z^2), flip [P] (largest output change that an
-    FP32-flippable threshold decision could cause; 0 if none), n_contrib [P].  With pixels=None,
+    FP32-flippable threshold decision could cause; 0 if none), slack [P] and
+    slack_z [P] (the summed change that swapping near-tied surfel pairs
+    makes to colour / normal, and to sum w z), n_contrib [P].  With pixels=None,
     arrays are reshaped to images (rgb [H,W,3], ...).
     """
     lib = _load()
@@ -116,7 +118,7 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
         pix_p = pix_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
     out = {k: np.zeros(sh, np.float64) for k, sh in
            [("rgb", (npix, 3)), ("depth", (npix,)), ("normal", (npix, 3)), ("alpha", (npix,)),
-            ("T", (npix,)), ("acc", (npix, 3)), ("flip", (npix,))]}
+            ("T", (npix,)), ("acc", (npix, 3)), ("flip", (npix,)), ("slack2", (npix, 2))]}
     out["n_contrib"] = np.zeros(npix, np.int32)
     dp = {k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in out.items() if v.dtype == np.float64}
     deg = int(round(np.sqrt(s.sh.shape[1]))) - 1
@@ -127,10 +129,12 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
         int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
         float(cam.near), D(cam.world_to_sensor), D(np.asarray(bg, np.float64)),
         int(npix), pix_p, int(tile),
-        dp["rgb"], dp["depth"], dp["normal"], dp["alpha"], dp["T"], dp["acc"], dp["flip"],
+        dp["rgb"], dp["depth"], dp["normal"], dp["alpha"], dp["T"], dp["acc"], dp["flip"], dp["slack2"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:
         raise RuntimeError("oracle camera render failed")
+    s2 = out.pop("slack2")
+    out["slack"], out["slack_z"] = s2[:, 0].copy(), s2[:, 1].copy()
     if pixels is None:
         H, W = cam.height, cam.width
         out = {k: v.reshape((H, W) + v.shape[1:]) for k, v in out.items()}
@@ -140,7 +144,8 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
 def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
     """FP64 LiDAR range image (tile as for render_pinhole; columns wrap).  Returns range, intensity, drop
     (ray-drop probability: sum w rho + T with rho = sigmoid of the surfels'
-    ray_drop logit, 0 when `s` has none), alpha, T, flip, n_contrib (each
+    ray_drop logit, 0 when `s` has none), alpha, T, flip, slack (intensity
+    and ray drop), slack_z (sum w t), n_contrib (each
     [R], or [beams, columns] with rays=None)."""
     lib = _load()
     keep = []
@@ -158,6 +163,7 @@ def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
         keep.append(ray_arr)
         ray_p = ray_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
     out = {k: np.zeros(nr, np.float64) for k in ("range", "intensity", "drop", "alpha", "T", "flip")}
+    out["slack2"] = np.zeros((nr, 2), np.float64)
     rd = getattr(s, "ray_drop", None)
     rd_p = None if rd is None else D(rd)
     out["n_contrib"] = np.zeros(nr, np.int32)
@@ -168,10 +174,12 @@ def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
         int(lid.beams), int(lid.columns), float(lid.el_min_deg), float(lid.el_max_deg), float(lid.az0_deg),
         float(lid.near), D(lid.world_to_sensor),
         int(nr), ray_p, int(tile),
-        dp["range"], dp["intensity"], dp["drop"], dp["alpha"], dp["T"], dp["flip"],
+        dp["range"], dp["intensity"], dp["drop"], dp["alpha"], dp["T"], dp["flip"], dp["slack2"],
         out["n_contrib"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc != 0:
         raise RuntimeError("oracle_render_lidar failed")
+    s2 = out.pop("slack2")
+    out["slack"], out["slack_z"] = s2[:, 0].copy(), s2[:, 1].copy()
     if rays is None:
         out = {k: v.reshape(lid.beams, lid.columns) for k, v in out.items()}
     return out

@@ -28,6 +28,7 @@ cudaError_t launch_lidar_loss(const gsr_plan* p, void* ws, int sensor, const gsr
                               float* loss, const gsr_lidar_grad* g, cudaStream_t st);
 cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,
                                        const gsr_objects* obj, const gsr_surfel_grads* out, cudaStream_t st);
+cudaError_t launch_selftest_wait(uint32_t* counters, uint32_t tries, cudaStream_t stream);
 
 static thread_local char g_cuda_err[256] = "";
 
@@ -309,6 +310,18 @@ extern "C" gsr_status gsr_read_status(const gsr_plan* plan, const void* workspac
         *n_pairs = (int64_t)want;
     }
     return GSR_OK;
+}
+
+extern "C" gsr_status gsr_selftest_wait_timeout(const gsr_plan* plan, void* workspace, size_t workspace_bytes,
+                                                uint32_t tries, void* stream)
+{
+    if (!plan || !workspace || tries == 0 || tries > (1u << 20)) return GSR_ERR_INVALID_ARG;
+    size_t need = 0;
+    gsr_status st = gsr_workspace_size(plan, &need);
+    if (st != GSR_OK) return st;
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return GSR_ERR_WORKSPACE;
+    return cuda_fail(launch_selftest_wait(region<uint32_t>(plan, workspace, R_COUNTERS), tries,
+                                          reinterpret_cast<cudaStream_t>(stream)));
 }
 
 extern "C" const char* gsr_status_string(gsr_status s)

@@ -189,7 +189,9 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
         // as done (it composites nothing more; every later wait is bounded too)
         if (__syncthreads_and(s.done || !ok)) {
             // no copy may still be landing in shared memory when the CTA
-            // leaves or moves on
+            // leaves or moves on: batch b if its wait gave up (a second
+            // bounded wait), and batch b + 1 if it was issued
+            if (!ok) wait(b);
             if (b + 1 < nb) wait(b + 1);
             break;
         }
@@ -410,7 +412,9 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_rig(SensorTabl
     const uint32_t T = (uint32_t)tab.total_tiles;
     for (;;) {
         __syncthreads();  // the previous item (and the barrier init) is done with
-        if (threadIdx.x == 0) item_s = atomicAdd(&counters[C_QUEUE], 1u);
+        // after a bounded wait gave up anywhere, the frame is void: take no more work
+        if (threadIdx.x == 0)
+            item_s = __ldcg(&counters[C_STATUS]) == (uint32_t)GSR_ERR_TIMEOUT ? T : atomicAdd(&counters[C_QUEUE], 1u);
         __syncthreads();
         const uint32_t item = item_s;
         if (item >= T) break;
@@ -451,7 +455,10 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTa
     const int D = tab.batch > 0 ? tab.batch : (int)blockDim.x;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) item_s = begin + atomicAdd(&counters[C_SPLIT_QUEUE], 1u);
+        if (threadIdx.x == 0)
+            item_s = __ldcg(&counters[C_STATUS]) == (uint32_t)GSR_ERR_TIMEOUT
+                         ? end
+                         : begin + atomicAdd(&counters[C_SPLIT_QUEUE], 1u);
         __syncthreads();
         const uint32_t item = item_s;
         if (item >= end) break;
@@ -470,6 +477,29 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTa
             render_chunk<GSR_SENSOR_LIDAR>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
                                            buf, bars, gb, sp, &flag_s, D);
     }
+}
+
+// Self-test of the bounded wait: an mbarrier armed for 16 bytes that no copy
+// will deliver, waited on with `tries` tries by the same helper every staging
+// wait of the library uses.  The wait gives up, records GSR_ERR_TIMEOUT in the
+// status word and the kernel returns; no copy or tensor-core operation is
+// outstanding at any point.
+__global__ void __launch_bounds__(32) k_selftest_wait(uint32_t* counters, uint32_t tries)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+    mbar_wait_bounded(&bar, 0u, counters, tries);
+}
+
+cudaError_t launch_selftest_wait(uint32_t* counters, uint32_t tries, cudaStream_t stream)
+{
+    k_selftest_wait<<<1, 32, 0, stream>>>(counters, tries);
+    return cudaGetLastError();
 }
 
 // Dynamic shared memory of a compositing CTA staging D records per batch.

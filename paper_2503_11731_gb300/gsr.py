@@ -162,6 +162,7 @@ SIGNATURES = {
                                  ctypes.POINTER(LidarOut), c_vp]),
     "gsr_read_status": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i64),
                                 ctypes.POINTER(c_i64), c_vp]),
+    "gsr_selftest_wait_timeout": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.c_uint32, c_vp]),
     "gsr_status_string": (ctypes.c_char_p, [c_i32]),
     "gsr_last_cuda_error": (ctypes.c_char_p, []),
     "gsr_workspace_region": (c_i32, [ctypes.POINTER(Plan), c_vp, c_i32, ctypes.POINTER(c_vp),
@@ -325,6 +326,12 @@ def read_status(plan, ws, stream):
     _check(lib().gsr_read_status(ctypes.byref(plan), ws, ctypes.byref(st), ctypes.byref(nv), ctypes.byref(npairs),
                                  stream), "gsr_read_status")
     return int(st.value), int(nv.value), int(npairs.value)
+
+
+def selftest_wait_timeout(plan, ws, ws_bytes, tries, stream):
+    """Make one bounded device wait give up (see gsr_selftest_wait_timeout)."""
+    _check(lib().gsr_selftest_wait_timeout(ctypes.byref(plan), ws, ws_bytes, int(tries), stream),
+           "gsr_selftest_wait_timeout")
 
 
 def workspace_region(plan, ws, which):

@@ -1,0 +1,117 @@
+"""Shared checks of GPU outputs against the FP64 oracle, and the record of
+every check's errors and flagged fraction.
+
+Tolerances (FP32 kernel vs FP64 oracle): RGB, intensity, alpha, T, normal
+1e-4 absolute; depth and range 1e-4 relative where alpha >= 0.01.
+
+Two kinds of FP32-flippable decisions are handled differently:
+* a ray is flagged, excluded from the tolerance check and counted, when the
+  oracle's `flip` value says a threshold decision that FP32 rounding may take
+  the other way (a threshold within 2e-5 relative, a near cull within
+  rounding, a near-tied pair at the stop) could move an output by more than
+  2e-5;
+* two contributing surfels whose centre depths are closer than their FP32
+  evaluation can separate may composite in either order; a swap changes
+  each output by an exact amount, which the oracle sums into the ray's
+  slack (colour / intensity / normal) and slack_z (sum w z).  Such rays are
+  checked against the tolerance plus their slack.
+Every check records its report; the session prints them at the end and
+writes them as JSON to the path in GSR_PARITY_LOG when that is set.
+"""
+import os
+
+import numpy as np
+
+TOL_ABS = 1e-4
+TOL_REL = 1e-4
+FLIP = 2e-5
+
+REPORTS = []
+
+
+def record(report, name=None):
+    if name is None:
+        name = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    report = {k: (float(v) if isinstance(v, (np.floating, float)) else v) for k, v in report.items()}
+    REPORTS.append({"test": name, **report})
+    print("parity", name, report)
+    return report
+
+
+def _slack(o, depth):
+    """The oracle's order slack of each ray: absolute for colour / intensity /
+    normal, relative to the depth (range) for the depth, since the swap
+    leaves sum w unchanged and moves sum w z by slack_z."""
+    sl = o.get("slack", np.zeros_like(o["flip"]))
+    slz = o.get("slack_z", np.zeros_like(o["flip"])) / np.maximum(np.abs(depth) * o["alpha"], 1e-12)
+    return sl, slz
+
+
+def _slack_report(o, ok):
+    sl = o.get("slack", np.zeros_like(o["flip"]))
+    tied = (sl > 0) | (o.get("slack_z", np.zeros_like(sl)) > 0)
+    return dict(tied=int((tied & ok).sum()), max_slack=float(sl[ok].max(initial=0)))
+
+
+def check_camera(g, o, pix=None, max_flag=0.01, name=None):
+    """g: GPU outputs (planar images), o: oracle dict (pixel-major for `pix`)."""
+    rgb = np.moveaxis(g["rgb"], 0, -1)
+    nrm = np.moveaxis(g["normal"], 0, -1)
+    # a frame rendered without its final transmittance is checked through alpha
+    T_img = g["trans"] if "trans" in g else 1.0 - g["alpha"]
+    if pix is not None:
+        H, W = g["alpha"].shape
+        yy, xx = np.divmod(np.asarray(pix), W)
+        rgb, nrm = rgb[yy, xx], nrm[yy, xx]
+        alpha, depth, T = g["alpha"][yy, xx], g["depth"][yy, xx], T_img[yy, xx]
+    else:
+        alpha, depth, T = g["alpha"], g["depth"], T_img
+    flag = o["flip"] > FLIP
+    ok = ~flag
+    sl, slz = _slack(o, o["depth"])
+    e_rgb = np.abs(rgb - o["rgb"]).max(-1) - sl
+    e_n = np.abs(nrm - o["normal"]).max(-1) - sl
+    e_a = np.abs(alpha - o["alpha"])
+    e_t = np.abs(T - o["T"])
+    dmask = ok & (o["alpha"] >= 0.01)
+    e_d = np.abs(depth - o["depth"]) / np.maximum(np.abs(o["depth"]), 1e-12) - slz
+    report = record(dict(kind="camera", rgb=e_rgb[ok].max(initial=0), normal=e_n[ok].max(initial=0),
+                         alpha=e_a[ok].max(initial=0), T=e_t[ok].max(initial=0), depth=e_d[dmask].max(initial=0),
+                         flagged=int(flag.sum()), n=int(flag.size), flagged_frac=float(flag.mean()),
+                         cap=max_flag, **_slack_report(o, ok)), name)
+    assert flag.mean() <= max_flag, report
+    assert report["rgb"] <= TOL_ABS, report
+    assert report["normal"] <= TOL_ABS, report
+    assert report["alpha"] <= TOL_ABS, report
+    assert report["T"] <= TOL_ABS, report
+    assert report["depth"] <= TOL_REL, report
+    return report
+
+
+def check_lidar(g, o, rays=None, max_flag=0.02, name=None, drop=False):
+    rng_, inten, alpha = g["range"], g["intensity"], g["alpha"]
+    dr = g.get("ray_drop") if drop else None
+    if rays is not None:
+        yy, xx = np.divmod(np.asarray(rays), rng_.shape[1])
+        rng_, inten, alpha = rng_[yy, xx], inten[yy, xx], alpha[yy, xx]
+        if dr is not None:
+            dr = dr[yy, xx]
+    flag = o["flip"] > FLIP
+    ok = ~flag
+    sl, slz = _slack(o, o["range"])
+    dmask = ok & (o["alpha"] >= 0.01)
+    e_r = np.abs(rng_ - o["range"]) / np.maximum(np.abs(o["range"]), 1e-12) - slz
+    rep = dict(kind="lidar", intensity=(np.abs(inten - o["intensity"]) - sl)[ok].max(initial=0),
+               alpha=np.abs(alpha - o["alpha"])[ok].max(initial=0),
+               range=e_r[dmask].max(initial=0), flagged=int(flag.sum()), n=int(flag.size),
+               flagged_frac=float(flag.mean()), cap=max_flag, **_slack_report(o, ok))
+    if dr is not None:
+        rep["drop"] = (np.abs(dr - o["drop"]) - sl)[ok].max(initial=0)
+    report = record(rep, name)
+    assert flag.mean() <= max_flag, report
+    assert report["intensity"] <= TOL_ABS, report
+    assert report["alpha"] <= TOL_ABS, report
+    assert report["range"] <= TOL_REL, report
+    if dr is not None:
+        assert report["drop"] <= TOL_ABS, report
+    return report

@@ -8,6 +8,9 @@ import torch
 
 from oracle import render as OR
 from paper_2503_11731_gb300 import synth
+from parity import check_camera, check_lidar
+
+CAP = 0.1
 
 pytestmark = pytest.mark.gpu
 
@@ -64,22 +67,9 @@ def test_rig_matches_oracle_with_posed_objects(gpu_lib):
     for s, g in zip(sensors, out):
         idx = rng.choice(s.width * s.height, 600, replace=False)
         if s.kind == "lidar":
-            o = OR.render_lidar(scene, s, rays=idx, obj_pose=poses)
-            yy, xx = np.divmod(idx, s.width)
-            ok = o["flip"] <= 2e-5
-            assert ok.mean() >= 0.97
-            assert np.abs(g["intensity"][yy, xx] - o["intensity"])[ok].max() <= 1e-4
-            m = ok & (o["alpha"] >= 0.01)
-            assert (np.abs(g["range"][yy, xx] - o["range"]) / o["range"].clip(1e-12))[m].max() <= 1e-4
+            check_lidar(g, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP)
         else:
-            o = OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses)
-            yy, xx = np.divmod(idx, s.width)
-            ok = o["flip"] <= 2e-5
-            assert ok.mean() >= 0.97
-            rgb = np.moveaxis(g["rgb"], 0, -1)[yy, xx]
-            assert np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
-            m = ok & (o["alpha"] >= 0.01)
-            assert (np.abs(g["depth"][yy, xx] - o["depth"]) / o["depth"].clip(1e-12))[m].max() <= 1e-4
+            check_camera(g, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP)
     # the objects are visible somewhere (the test exercises the pose path)
     assert (scene.obj_id >= 0).sum() > 0
 
@@ -154,9 +144,7 @@ def test_preprocess_parts_mix_sh_degrees(gpu_lib):
     idx = np.random.default_rng(9).choice(s.width * s.height, 500, replace=False)
     o = OR.render_pinhole(whole, s, pixels=idx, obj_pose=poses)
     yy, xx = np.divmod(idx, s.width)
-    ok = o["flip"] <= 2e-5
-    rgb = np.moveaxis(r.out[0]["rgb"].cpu().numpy(), 0, -1)[yy, xx]
-    assert ok.mean() >= 0.97 and np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
+    check_camera({k: v.cpu().numpy() for k, v in r.out[0].items()}, o, pix=idx, max_flag=CAP)
     assert (r.out[0]["n_contrib"].cpu().numpy()[yy, xx] > 0).mean() > 0.5
 
 
@@ -248,18 +236,10 @@ def test_split_lists_match_oracle_and_unsplit_render(gpu_lib):
     rng = np.random.default_rng(11)
     for s, gg in zip(sensors, g):
         idx = rng.choice(s.width * s.height, 400, replace=False)
-        yy, xx = np.divmod(idx, s.width)
         if s.kind == "lidar":
-            o = OR.render_lidar(scene, s, rays=idx, obj_pose=poses)
-            ok = o["flip"] <= 2e-5
-            assert np.abs(gg["intensity"][yy, xx] - o["intensity"])[ok].max() <= 1e-4
-            m = ok & (o["alpha"] >= 0.01)
-            assert (np.abs(gg["range"][yy, xx] - o["range"]) / o["range"].clip(1e-12))[m].max() <= 1e-4
+            check_lidar(gg, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP)
         else:
-            o = OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses)
-            ok = o["flip"] <= 2e-5
-            rgb = np.moveaxis(gg["rgb"], 0, -1)[yy, xx]
-            assert np.abs(rgb - o["rgb"]).max(-1)[ok].max() <= 1e-4
+            check_camera(gg, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP)
 
 
 def test_lidar_split_is_per_sensor(gpu_lib):

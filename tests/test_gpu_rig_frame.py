@@ -1,0 +1,64 @@
+"""The benchmarked surround-rig frame against the oracle.
+
+The frame is the benchmark's configuration: 6 pinhole cameras (2 x 1920x1080,
+4 x 1280x720) and 2 spinning LiDARs (128x1800, 32x1024); 300k anchors x 10
+offsets decoded by the anchor MLP into 3M surfels plus 20 rigidly posed
+50k-surfel SH-3 objects; the tiling, staging depth and list splits chosen by
+gsr_autotune, rendered by the persistent whole-rig launch.  The GPU decodes
+in FP32 here so that the oracle can decode the same anchors in FP64 itself
+(Sec. III-A, anchors decoded by an MLP) and render its own table: nothing
+the GPU computed enters the oracle.  4,096 sampled rays per sensor are
+compared (the oracle in tiled mode, bit-identical to brute force).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as OR
+from parity import check_camera, check_lidar
+
+pytestmark = pytest.mark.gpu
+
+SAMPLES = 4096
+
+
+def test_configured_rig_frame_matches_oracle(gpu_lib):
+    import bench
+    from paper_2503_11731_gb300 import gsr
+    from paper_2503_11731_gb300.frame import DeviceSurfels
+    from paper_2503_11731_gb300.neural import DeviceAnchors, NeuralFrame, NeuralModel
+    bg, objs, poses, sensors = bench.rig_parts()
+    anchors, mlp = bench.rig_neural(bg)
+    origin = bench.rig_origin(sensors)
+    del bg
+    n = anchors.n * anchors.k + objs.n
+    # the benchmark's outputs: no final T (a frame that requests none skips
+    # keeping the per-chunk states of split lists)
+    r = bench.rig_renderer(n, sensors, outputs=("rgb", "depth", "normal", "alpha", "n_contrib", "n_walk"))
+    pose_t = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
+    d_obj = DeviceSurfels.from_host(objs)
+    nf = NeuralFrame(NeuralModel(*mlp), DeviceAnchors(anchors), r, d_obj, pose_t, origin, gsr.DECODE_F32)
+    nf.render()
+    torch.cuda.synchronize()
+    tuned = r.autotune([nf.table, d_obj], pose_t, warmup=1, reps=2)
+    out = nf.render()
+    torch.cuda.synchronize()
+    st, nvis, npairs = r.status()
+    assert st == 0, st
+    # the tuned plan splits long lists (the path the benchmark times)
+    info = r.region(8, torch.int32).view(-1, 4)
+    assert int((info[:, 0] > 0).sum()) > 0
+    print("tiling", tuned["camera_tile"], tuned["lidar_tile"], tuned["split"], tuned["lidar_split"],
+          "pairs", npairs)
+    g = [{k: v.cpu().numpy() for k, v in o.items()} for o in out]
+    scene, _ = bench.oracle_rig_scene(objs, anchors, mlp, origin)
+    rng = np.random.default_rng(2503)
+    for i, (s, gg) in enumerate(zip(sensors, g)):
+        idx = rng.choice(s.width * s.height, SAMPLES, replace=False)
+        name = f"rig frame sensor {i} ({s.kind} {s.width}x{s.height})"
+        if s.kind == "lidar":
+            o = OR.render_lidar(scene, s, rays=idx, obj_pose=poses, tile=8)
+            check_lidar(gg, o, rays=idx, max_flag=0.1, name=name)
+        else:
+            o = OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses, tile=16)
+            check_camera(gg, o, pix=idx, max_flag=0.1, name=name)

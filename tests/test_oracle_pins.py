@@ -546,31 +546,48 @@ def test_tiled_mode_equals_brute_force(case):
 
 
 # ----------------------------------------------- FP32-flippable decisions
-def test_order_near_tie_is_flagged():
+def test_order_near_tie_slack():
     """Two facing surfels on the optical axis.  Depths 1 mm apart: composited
-    in depth order, nothing flagged.  Depths 1e-7 m apart (below what an FP32
+    in depth order, no slack.  Depths 1e-7 m apart (below what an FP32
     evaluation of a 10 m depth resolves): still composited in FP64 depth
-    order, and the ray carries the change a swap would make, the weight
-    o1 o2 moved between colours that differ by 1 in red and blue."""
+    order, and the ray's slack is the exact change a swap makes, the weight
+    o1 o2 moved between colours that differ by 1 in red and blue (and the
+    depth accumulator's o1 o2 dz)."""
     cam = _cam()
     pix = [16 * 33 + 16]
     o1, o2 = 0.6, 0.7
-    for dz, flagged in ((1e-3, False), (1e-7, True)):
+    for dz, tied in ((1e-3, False), (1e-7, True)):
         a = _one((0, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1), rgb=(1, 0, 0))
         b = _one((0, 0, 10.0 + dz), (0, 0), (1, 0, 0, 0), _logit(o2), rgb=(0, 0, 1))
         for s in (a.concat(b), b.concat(a)):
             out = R.render_pinhole(s, cam, pixels=pix)
             assert out["rgb"][0] == pytest.approx([o1, 0, (1 - o1) * o2], abs=1e-12)
-            if flagged:
-                assert out["flip"][0] == pytest.approx(o1 * o2 * 1.0, rel=1e-9)
+            assert out["flip"][0] == 0.0
+            if tied:
+                assert out["slack"][0] == pytest.approx(o1 * o2 * 1.0, rel=1e-9)
+                assert out["slack_z"][0] == pytest.approx(o1 * o2 * dz, rel=1e-6)
+                # the swapped order differs from the FP64 order by exactly the slack
+                swapped = [o2 * (1 - o1), 0, o2]
+                assert np.abs(np.array(swapped) - out["rgb"][0]).max() == pytest.approx(out["slack"][0], rel=1e-9)
             else:
-                assert out["flip"][0] == 0.0
-    # equal colours and normals: a swap changes only the depth, by
-    # o1 o2 |dz| relative to the depth -- far below any tolerance
+                assert out["slack"][0] == 0.0 and out["slack_z"][0] == 0.0
+    # equal colours and normals: a swap changes no colour
     a = _one((0, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1))
     b = _one((0, 0, 10.0 + 1e-7), (0, 0), (1, 0, 0, 0), _logit(o2))
     out = R.render_pinhole(a.concat(b), cam, pixels=pix)
-    assert out["flip"][0] == pytest.approx(o1 * o2 * 1e-8, rel=1e-6)
+    assert out["slack"][0] == 0.0 and out["slack_z"][0] > 0.0
+    # a tie at the stop (the second surfel would end the ray) is a flag: the
+    # swapped order composites the other surfel instead
+    T0 = None
+    stack = None
+    for k in range(3):
+        t = _one((0, 0, 5.0 + k), (0, 0), (1, 0, 0, 0), _logit(0.97), rgb=(1, 0, 0))
+        stack = t if stack is None else stack.concat(t)
+    # T after three surfels of 0.97: 2.7e-5 < 1e-4, so the third stops the
+    # ray; put a blue surfel within 1e-8 m of the second
+    blue = _one((0, 0, 6.0 + 1e-8), (0, 0), (1, 0, 0, 0), _logit(0.97), rgb=(0, 0, 1))
+    out = R.render_pinhole(stack.concat(blue), cam, pixels=pix)
+    assert out["n_contrib"][0] == 2 and out["flip"][0] == pytest.approx(0.03 * 0.97, rel=1e-6)
 
 
 def test_near_cull_within_rounding_is_flagged():

@@ -144,6 +144,8 @@ typedef struct {
     double o;          /* opacity, sigmoid of the logit                      */
     double feat[3];    /* camera: colour; LiDAR: intensity, ray drop, 0     */
     double normal[3];  /* sensor frame, facing the sensor                    */
+    int n_amb;         /* the facing test n . (mu - origin) is within its FP32
+                          error bound of 0: either sign of n is possible     */
     double ms[3];      /* centre in the sensor frame                         */
     double rad;        /* radius of a sphere about the centre that holds the
                           support u^2 + v^2 <= 9 with the near-miss margin    */
@@ -314,7 +316,15 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     /* normal = third column of R, in the sensor frame, facing the sensor */
     double nw[3] = {R[0][2], R[1][2], R[2][2]};
     double to_s[3] = {mu[0] - S->origin[0], mu[1] - S->origin[1], mu[2] - S->origin[2]};
-    if (or_dot3(nw, to_s) > 0) { nw[0] = -nw[0]; nw[1] = -nw[1]; nw[2] = -nw[2]; }
+    double facing = or_dot3(nw, to_s);
+    {
+        /* error bound of the test in FP32: the differences mu - origin and
+           the three-term dot product, each within gamma_4 of their terms */
+        double terms = 0.0;
+        for (int a = 0; a < 3; ++a) terms += fabs(nw[a]) * (fabs(mu[a]) + fabs(S->origin[a]) + mag[a]);
+        G->n_amb = fabs(facing) <= OR_GAMMA4 * terms;
+    }
+    if (facing > 0) { nw[0] = -nw[0]; nw[1] = -nw[1]; nw[2] = -nw[2]; }
     for (int a = 0; a < 3; ++a) G->normal[a] = S->Rs[a][0] * nw[0] + S->Rs[a][1] * nw[1] + S->Rs[a][2] * nw[2];
 
     if (S->kind != 1) {
@@ -430,9 +440,10 @@ static int or_cmp_hit(const void* pa, const void* pb)
  * FP32 error bounds (tau).  The recorded effect is the largest change of an
  * output that taking the decision the other way could cause (T times the
  * jump in alpha; for the depth-branch choice, the relative jump in depth
- * weight; for a near-tied pair at the stop, the weight of either).  A
- * near-tied pair that both composite does not flag the ray: the change a
- * swap makes is exact and small, and is summed into the ray's slack.
+ * weight; for a near-tied run at the stop, the weight composited since the
+ * run began).  A near-tied run that composites whole does not flag the ray:
+ * the change a reordering can make is bounded (or_run_close) and summed
+ * into the ray's slack.
  */
 #ifndef OR_FLIP_REL
 #define OR_FLIP_REL 2e-5
@@ -444,16 +455,19 @@ static int or_cmp_hit(const void* pa, const void* pb)
 typedef struct {
     double feat[3], A, B, D, N[3], T;
     double flip;      /* largest effect of a flippable decision, 0 if none */
-    double slack;     /* sum over near-tied pairs of the colour / intensity /
-                         normal change a swap of the pair makes            */
+    double slack;     /* summed bound of the colour / intensity change a
+                         reordering of near-tied runs can make             */
+    double slack_n;   /* the same for the normal                           */
     double slack_z;   /* the same for sum w z (the depth accumulator B)    */
     int n_contrib;
     int done;         /* the stop rule ended the ray                       */
-    /* the last composited surfel, for the order check */
-    int has_prev;
-    double prev_zc, prev_tau, prev_alpha, prev_T, prev_z;
-    const double* prev_feat;
-    const double* prev_n;
+    /* the current run of near-tied composited surfels (consecutive centre
+       depths within their FP32 error bounds of each other) */
+    int run_len;
+    double run_T0;                 /* T before the run's first surfel       */
+    double last_zc, last_tau;      /* the run's last surfel                 */
+    double lo[7], hi[7];           /* range of feat[3], normal[3], z        */
+    double first_alpha, first_v[7], second_alpha, second_v[7];
 } or_ray;
 
 static void or_flip(double* flip, double rel, double scale, double effect)
@@ -467,23 +481,50 @@ static void or_ray_init(or_ray* r)
     r->T = 1.0;
 }
 
-static double or_maxdiff3(const double* a, const double* b)
+/*
+ * Near-tied runs.  Two composited surfels whose FP64 centre depths differ by
+ * less than the sum of their FP32 error bounds may come in either order
+ * from an FP32 sort, and so may every surfel of a chain of such pairs.  The
+ * composited weight of a run, T0 (1 - prod (1 - alpha_i)), does not depend
+ * on its order, and neither does T after it, so under any order of the run
+ * each output differs from the FP64 order's by at most the run's weight
+ * times the range of that output over the run's surfels.  For a run of two
+ * the change is exact: a swap moves alpha_1 alpha_2 T0 from one surfel's
+ * value to the other's.
+ */
+static void or_run_close(or_ray* r)
 {
-    double m = 0.0;
-    for (int c = 0; c < 3; ++c) {
-        double v = fabs(a[c] - b[c]);
-        if (v > m) m = v;
+    if (r->run_len >= 2) {
+        double d[7];
+        double W;
+        if (r->run_len == 2) {
+            W = r->first_alpha * r->second_alpha * r->run_T0;
+            for (int c = 0; c < 7; ++c) d[c] = fabs(r->first_v[c] - r->second_v[c]);
+        } else {
+            W = r->run_T0 - r->T;
+            for (int c = 0; c < 7; ++c) d[c] = r->hi[c] - r->lo[c];
+        }
+        double sf = d[0] > d[1] ? d[0] : d[1], sn = d[3] > d[4] ? d[3] : d[4];
+        if (d[2] > sf) sf = d[2];
+        if (d[5] > sn) sn = d[5];
+        r->slack += W * sf;
+        r->slack_n += W * sn;
+        r->slack_z += W * d[6];
     }
-    return m;
+    r->run_len = 0;
 }
 
-static double or_maxabs3(const double* a)
+static void or_values(const or_surfel* g, const or_hit* h, double v[7])
 {
-    double m = 0.0;
-    for (int c = 0; c < 3; ++c)
-        if (fabs(a[c]) > m) m = fabs(a[c]);
-    return m;
+    for (int c = 0; c < 3; ++c) {
+        v[c] = g->feat[c];
+        v[3 + c] = g->normal[c];
+    }
+    v[6] = h->z;
 }
+
+/* Finish a ray: close its last run. */
+static void or_ray_finish(or_ray* r) { or_run_close(r); }
 
 /*
  * One step of front-to-back compositing (3DGS order and thresholds): hit h
@@ -512,44 +553,52 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     if (h->alpha < 1.0 / 255.0) return;
     double test = T * (1.0 - h->alpha);
     or_flip(&r->flip, or_relm(test, 1e-4), OR_FLIP_REL, h->alpha * T);
-    /* order of this surfel and the previous composited one */
-    int tie = r->has_prev && fabs(h->zc - r->prev_zc) <= g->tau + r->prev_tau;
+    /* a normal whose facing sign FP32 may take the other way: the normal
+       output moves by twice its weight */
+    if (g->n_amb && S->kind != 1) or_flip(&r->flip, 0.0, 1.0, 2.0 * h->alpha * T);
+    double v[7];
+    or_values(g, h, v);
+    int tie = r->run_len > 0 && fabs(h->zc - r->last_zc) <= g->tau + r->last_tau;
     if (test < 1e-4) {
-        /* swapped, this surfel would come first and the previous one might
-           stop the ray instead: the weights of both are at stake */
+        /* reordered, the run could place this surfel before others of the
+           run and stop the ray there instead: everything composited since
+           the run began is at stake */
         if (tie) {
-            double big = h->alpha > r->prev_alpha ? h->alpha : r->prev_alpha;
-            double f = or_maxabs3(g->feat), fp = or_maxabs3(r->prev_feat);
-            double fm = f > fp ? f : fp;
-            or_flip(&r->flip, 0.0, 1.0, r->prev_T * big * (fm > 1.0 ? fm : 1.0));
+            double m = 1.0;
+            for (int c = 0; c < 6; ++c) {
+                if (fabs(v[c]) > m) m = fabs(v[c]);
+                if (fabs(r->hi[c]) > m) m = fabs(r->hi[c]);
+                if (fabs(r->lo[c]) > m) m = fabs(r->lo[c]);
+            }
+            or_flip(&r->flip, 0.0, 1.0, r->run_T0 * m);
         }
         r->done = 1;
         return;
     }
-    if (tie) {
-        /* a swap moves the weight alpha_prev alpha T_prev from one to the
-           other and leaves every later weight and T as they are: each
-           output changes by exactly that weight times the pair's difference
-           in it */
-        double moved = r->prev_alpha * h->alpha * r->prev_T;
-        double df = or_maxdiff3(g->feat, r->prev_feat), dn = or_maxdiff3(g->normal, r->prev_n);
-        r->slack += moved * (df > dn ? df : dn);
-        r->slack_z += moved * fabs(h->z - r->prev_z);
+    if (!tie) {
+        or_run_close(r);
+        r->run_T0 = T;
+        r->first_alpha = h->alpha;
+        for (int c = 0; c < 7; ++c) r->lo[c] = r->hi[c] = r->first_v[c] = v[c];
+    } else {
+        if (r->run_len == 1) {
+            r->second_alpha = h->alpha;
+            for (int c = 0; c < 7; ++c) r->second_v[c] = v[c];
+        }
+        for (int c = 0; c < 7; ++c) {
+            if (v[c] < r->lo[c]) r->lo[c] = v[c];
+            if (v[c] > r->hi[c]) r->hi[c] = v[c];
+        }
     }
+    ++r->run_len;
+    r->last_zc = h->zc;
+    r->last_tau = g->tau;
     double w = h->alpha * T;
     for (int ch = 0; ch < 3; ++ch) r->feat[ch] += w * g->feat[ch];
     r->A += w;
     r->B += w * h->z;
     r->D += w * h->z * h->z;
     for (int a = 0; a < 3; ++a) r->N[a] += w * g->normal[a];
-    r->has_prev = 1;
-    r->prev_zc = h->zc;
-    r->prev_tau = g->tau;
-    r->prev_alpha = h->alpha;
-    r->prev_T = T;
-    r->prev_z = h->z;
-    r->prev_feat = g->feat;
-    r->prev_n = g->normal;
     r->T = test;
     ++r->n_contrib;
 }
@@ -580,6 +629,7 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
     qsort(buf, (size_t)nh, sizeof(or_hit), or_cmp_hit);
     or_ray_init(out);
     for (int j = 0; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
+    or_ray_finish(out);
 }
 
 /* ----------------------------------------------------------------------- */
@@ -841,6 +891,7 @@ static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long 
         or_hit h;
         if (or_collect(&G[i], i, S, hu, hv, d, pc, &h)) or_step(out, &G[i], &h, S);
     }
+    or_ray_finish(out);
 }
 
 static or_surfel* or_prepare_all(int n, const or_sensor* S, const double* pos, const double* log_scale,
@@ -953,7 +1004,7 @@ static void or_emit_camera(long long q, const or_ray* r, void* ctx)
     o->trans[q] = r->T;
     if (o->acc) { o->acc[q * 3 + 0] = r->A; o->acc[q * 3 + 1] = r->B; o->acc[q * 3 + 2] = r->D; }
     if (o->flip) o->flip[q] = r->flip;
-    if (o->slack) { o->slack[q * 2 + 0] = r->slack; o->slack[q * 2 + 1] = r->slack_z; }
+    if (o->slack) { o->slack[q * 3 + 0] = r->slack; o->slack[q * 3 + 1] = r->slack_n; o->slack[q * 3 + 2] = r->slack_z; }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 
@@ -990,9 +1041,9 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
  * sum(w z)/sum(w) (0 where sum(w) == 0); normal is sum(w n), unnormalised;
  * acc = [sum w, sum w z, sum w z^2] per pixel ([n_pix][3], may be NULL).
  * flip [n_pix] is the largest output change an FP32-flippable threshold
- * decision could cause (0 if none); slack [n_pix][2] the summed change that
- * swapping near-tied surfel pairs makes to colour / normal and to sum w z
- * (both may be NULL).
+ * decision could cause (0 if none); slack [n_pix][3] bounds the change a
+ * reordering of near-tied surfels can make to colour, to the normal and to
+ * sum w z (both may be NULL).
  * tile == 0 checks every surfel for every pixel (brute force); tile > 0
  * walks per-tile candidate lists of tile x tile pixels built from the
  * oracle's own conservative bound, with the same arithmetic and the same
@@ -1053,7 +1104,7 @@ static void or_emit_lidar(long long q, const or_ray* r, void* ctx)
     o->alpha[q] = r->A;
     o->trans[q] = r->T;
     if (o->flip) o->flip[q] = r->flip;
-    if (o->slack) { o->slack[q * 2 + 0] = r->slack; o->slack[q * 2 + 1] = r->slack_z; }
+    if (o->slack) { o->slack[q * 3 + 0] = r->slack; o->slack[q * 3 + 1] = r->slack_n; o->slack[q * 3 + 2] = r->slack_z; }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 

@@ -29,6 +29,24 @@ FLIP = 2e-5
 REPORTS = []
 
 
+def _dump(name, idx, cols):
+    """With GSR_PARITY_DUMP set to a folder, write the rays of a check with the
+    largest errors (index, GPU and oracle values) for offline study."""
+    d = os.environ.get("GSR_PARITY_DUMP")
+    if not d:
+        return
+    import json
+    os.makedirs(d, exist_ok=True)
+    safe = "".join(c if c.isalnum() else "_" for c in name)[-120:]
+    with open(os.path.join(d, f"{len(REPORTS):03d}_{safe}.json"), "w") as f:
+        json.dump({"test": name, "rays": [int(i) for i in idx],
+                   **{k: np.asarray(v)[list(range(len(idx)))].tolist() for k, v in cols.items()}}, f)
+
+
+def _worst(err, k=12):
+    return np.argsort(-np.nan_to_num(err, nan=np.inf))[:k]
+
+
 def record(report, name=None):
     if name is None:
         name = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
@@ -48,9 +66,11 @@ def _slack(o, depth):
 
 
 def _slack_report(o, ok):
-    sl = o.get("slack", np.zeros_like(o["flip"]))
-    tied = (sl > 0) | (o.get("slack_z", np.zeros_like(sl)) > 0)
-    return dict(tied=int((tied & ok).sum()), max_slack=float(sl[ok].max(initial=0)))
+    z = np.zeros_like(o["flip"])
+    sl, sn, sz = o.get("slack", z), o.get("slack_n", z), o.get("slack_z", z)
+    tied = (sl > 0) | (sn > 0) | (sz > 0)
+    return dict(tied=int((tied & ok).sum()), tied_frac=float((tied & ok).mean()),
+                slack_over_tol=float(((sl > TOL_ABS) & ok).mean()), max_slack=float(sl[ok].max(initial=0)))
 
 
 def check_camera(g, o, pix=None, max_flag=0.01, name=None):
@@ -70,11 +90,20 @@ def check_camera(g, o, pix=None, max_flag=0.01, name=None):
     ok = ~flag
     sl, slz = _slack(o, o["depth"])
     e_rgb = np.abs(rgb - o["rgb"]).max(-1) - sl
-    e_n = np.abs(nrm - o["normal"]).max(-1) - sl
+    e_n = np.abs(nrm - o["normal"]).max(-1) - o.get("slack_n", sl)
     e_a = np.abs(alpha - o["alpha"])
     e_t = np.abs(T - o["T"])
     dmask = ok & (o["alpha"] >= 0.01)
     e_d = np.abs(depth - o["depth"]) / np.maximum(np.abs(o["depth"]), 1e-12) - slz
+    if os.environ.get("GSR_PARITY_DUMP"):
+        w = _worst(np.maximum(np.maximum(e_rgb, e_n), np.where(dmask, e_d, 0)) * ok)
+        ids = np.asarray(pix)[w] if pix is not None else w
+        _dump(name or os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], ids,
+              {"g_rgb": rgb.reshape(-1, 3)[w], "o_rgb": o["rgb"].reshape(-1, 3)[w],
+               "g_n": nrm.reshape(-1, 3)[w], "o_n": o["normal"].reshape(-1, 3)[w],
+               "g_a": alpha.reshape(-1)[w], "o_a": o["alpha"].reshape(-1)[w],
+               "g_d": depth.reshape(-1)[w], "o_d": o["depth"].reshape(-1)[w],
+               "flip": o["flip"].reshape(-1)[w], "slack": sl.reshape(-1)[w]})
     report = record(dict(kind="camera", rgb=e_rgb[ok].max(initial=0), normal=e_n[ok].max(initial=0),
                          alpha=e_a[ok].max(initial=0), T=e_t[ok].max(initial=0), depth=e_d[dmask].max(initial=0),
                          flagged=int(flag.sum()), n=int(flag.size), flagged_frac=float(flag.mean()),

@@ -571,14 +571,37 @@ def test_order_near_tie_slack():
                 assert np.abs(np.array(swapped) - out["rgb"][0]).max() == pytest.approx(out["slack"][0], rel=1e-9)
             else:
                 assert out["slack"][0] == 0.0 and out["slack_z"][0] == 0.0
+    # a run of three tied surfels: any order keeps the run's weight
+    # W = 1 - (1 - o)^3 and T; each output stays within W times the run's
+    # range of it (red 1 / 0 / 0 here: slack W)
+    o = 0.5
+    run = None
+    for k, c in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+        t = _one((0, 0, 10.0 + 4e-7 * k), (0, 0), (1, 0, 0, 0), _logit(o), rgb=c)
+        run = t if run is None else run.concat(t)
+    out = R.render_pinhole(run, cam, pixels=pix)
+    W = 1 - (1 - o) ** 3
+    assert out["slack"][0] == pytest.approx(W, rel=1e-9)
+    assert out["slack_z"][0] == pytest.approx(W * 8e-7, rel=1e-6)
+    import itertools
+    base = out["rgb"][0]
+    for perm in itertools.permutations(range(3)):
+        # every order of the run lies within the slack of the FP64 order
+        cols = [((1, 0, 0), (0, 1, 0), (0, 0, 1))[p] for p in perm]
+        T, rgb = 1.0, np.zeros(3)
+        for c in cols:
+            rgb += o * T * np.array(c)
+            T *= 1 - o
+        assert np.abs(rgb - base).max() <= out["slack"][0] + 1e-12
     # equal colours and normals: a swap changes no colour
     a = _one((0, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1))
     b = _one((0, 0, 10.0 + 1e-7), (0, 0), (1, 0, 0, 0), _logit(o2))
     out = R.render_pinhole(a.concat(b), cam, pixels=pix)
     assert out["slack"][0] == 0.0 and out["slack_z"][0] > 0.0
     # a tie at the stop (the second surfel would end the ray) is a flag: the
-    # swapped order composites the other surfel instead
-    T0 = None
+    # swapped order composites the other surfel instead; the flag carries the
+    # weight at stake, T before the tied run (0.03 here) times the largest
+    # value (1)
     stack = None
     for k in range(3):
         t = _one((0, 0, 5.0 + k), (0, 0), (1, 0, 0, 0), _logit(0.97), rgb=(1, 0, 0))
@@ -587,7 +610,7 @@ def test_order_near_tie_slack():
     # ray; put a blue surfel within 1e-8 m of the second
     blue = _one((0, 0, 6.0 + 1e-8), (0, 0), (1, 0, 0, 0), _logit(0.97), rgb=(0, 0, 1))
     out = R.render_pinhole(stack.concat(blue), cam, pixels=pix)
-    assert out["n_contrib"][0] == 2 and out["flip"][0] == pytest.approx(0.03 * 0.97, rel=1e-6)
+    assert out["n_contrib"][0] == 2 and out["flip"][0] == pytest.approx(0.03, rel=1e-6)
 
 
 def test_near_cull_within_rounding_is_flagged():

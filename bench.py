@@ -31,7 +31,10 @@ in BF16 (tcgen05) and FP32 (SIMT).
 
 N > 1 (under torchrun) runs N independent replicas, one frame stream per
 GPU (the path has no exchange step).  `--impl reference` times the FP64 CPU
-oracle (decode + brute-force render) on a bounded sample of the same frame.
+oracle on whole frames of the same configuration (FP64 decode + every ray,
+the oracle's tiled mode).  The `cpu_baseline` leg times one such frame and
+compares every ray of the GPU frame of the same configuration (FP32 decode)
+with it (`parity`).
 """
 from __future__ import annotations
 
@@ -105,8 +108,7 @@ def n_rays(sensors):
 
 def sample_clocks_start():
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        f = None
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -126,9 +128,6 @@ def sample_clocks_stop(p, f, dev_index):
     except Exception:
         p.kill()
         out = ""
-    if f:
-        f.write(out)
-        f.close()
     sm, mx, reasons = [], [], set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     for line in out.strip().splitlines():
@@ -159,35 +158,23 @@ def peaks():
 
 
 # ---------------------------------------------------------------- reference arm
-def oracle_frame_estimate(scene, poses, sensors, n=32, seed=7):
-    """Oracle ms per frame from a bounded sample.  Each oracle call has a
-    per-sensor fixed cost (Eq. 1 per surfel: transform, SH) and a per-ray
-    cost (a brute-force pass over all surfels); per sensor, a call on one ray
-    gives the fixed cost and a call on max(n, 2 x cores) rays (whole rounds of
-    the host's threads) the per-ray cost, combined for the full frame."""
-    from oracle import render as OR
-    rng = np.random.default_rng(seed)
-    total = 0.0
-    rays = 0
-    cores = OR.num_threads()
-    k = max(n, 2 * cores)
-    k = ((k + cores - 1) // cores) * cores
+ORACLE_TILE = {"pinhole": 16, "cylindrical": 16, "lidar": 4}
 
-    def call(s, m):
-        idx = rng.choice(s.width * s.height, m, replace=False)
-        t0 = time.perf_counter()
-        if s.kind == "lidar":
-            OR.render_lidar(scene, s, rays=idx, obj_pose=poses)
-        else:
-            OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses)
-        return time.perf_counter() - t0
+
+def oracle_frame(scene, poses, sensors):
+    """One whole frame of the FP64 oracle in tiled mode (per-tile candidate
+    lists from the oracle's own conservative bound; bit-identical to its
+    brute-force mode): every ray of every sensor.  Returns the outputs and
+    the wall-clock seconds."""
+    from oracle import render as OR
+    outs = []
+    t0 = time.perf_counter()
     for s in sensors:
-        t1 = call(s, 1)
-        tk = call(s, k)
-        per_ray = max(tk - t1, 0.0) / (k - 1)
-        total += t1 + per_ray * (s.width * s.height - 1)
-        rays += 1 + k
-    return total * 1e3, rays
+        if s.kind == "lidar":
+            outs.append(OR.render_lidar(scene, s, obj_pose=poses, tile=ORACLE_TILE["lidar"]))
+        else:
+            outs.append(OR.render_pinhole(scene, s, obj_pose=poses, tile=ORACLE_TILE[s.kind]))
+    return outs, time.perf_counter() - t0
 
 
 def oracle_rig_scene(objs, anchors, mlp, origin):
@@ -207,38 +194,85 @@ def oracle_rig_scene(objs, anchors, mlp, origin):
     return back.concat(objs), dec_s
 
 
+def frame_parity(sensors, gpu_outs, oracle_outs, tol=1e-4, flip=2e-5):
+    """Every ray of a GPU frame against the oracle's frame of the same
+    configuration.  A ray is flagged (excluded, counted) when a threshold
+    decision that FP32 rounding may take the other way could move an output
+    by more than 2e-5; near-tied runs of surfels (centre depths within FP32
+    resolution) may composite in either order, so each ray's tolerance adds
+    the oracle's bound of what a reordering can change (its slack).  Per
+    sensor: flagged and tied fractions, the largest error beyond tolerance +
+    slack on unflagged rays (<= 0 means within), and the number of such rays."""
+    rep = []
+    for s, g, o in zip(sensors, gpu_outs, oracle_outs):
+        ok = o["flip"] <= flip
+        tied = (o["slack"] > 0) | (o["slack_n"] > 0) | (o["slack_z"] > 0)
+        errs = {}
+        if s.kind == "lidar":
+            cols = {"intensity": (np.abs(g["intensity"] - o["intensity"]), o["slack"]),
+                    "alpha": (np.abs(g["alpha"] - o["alpha"]), 0.0)}
+            rel = (o["range"], g["range"])
+        else:
+            cols = {"rgb": (np.abs(np.moveaxis(g["rgb"], 0, -1) - o["rgb"]).max(-1), o["slack"]),
+                    "normal": (np.abs(np.moveaxis(g["normal"], 0, -1) - o["normal"]).max(-1), o["slack_n"]),
+                    "alpha": (np.abs(g["alpha"] - o["alpha"]), 0.0)}
+            rel = (o["depth"], g["depth"])
+        bad = np.zeros_like(ok)
+        for k, (e, sl) in cols.items():
+            over = e - sl - tol
+            errs[k] = float(np.where(ok, e - sl, -np.inf).max())
+            bad |= ok & (over > 0)
+        dm = ok & (o["alpha"] >= 0.01)
+        e_d = np.abs(rel[1] - rel[0]) / np.maximum(np.abs(rel[0]), 1e-12) - \
+            o["slack_z"] / np.maximum(np.abs(rel[0]) * o["alpha"], 1e-12)
+        errs["depth_rel"] = float(np.where(dm, e_d, -np.inf).max())
+        bad |= dm & (e_d > tol)
+        rep.append({"sensor": f"{s.kind} {s.width}x{s.height}", "rays": int(ok.size),
+                    "flagged_frac": float(1.0 - ok.mean()), "tied_frac": float((tied & ok).mean()),
+                    "max_err_beyond_slack": errs, "rays_over_tolerance": int(bad.sum())})
+    return rep
+
+
 def run_reference(args):
-    """FP64 CPU oracle: the full anchor decode plus a bounded sample of the
-    frame's rays (brute force over all surfels), scaled to the frame."""
+    """FP64 CPU oracle of the configured frame, timed whole: each step decodes
+    every anchor (FP64) and renders every ray of every sensor (tiled mode).
+    A CPU program has nothing to warm up: each warm-up step is one oracle call
+    on one ray of a small scene."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import mlp as OM  # noqa: F401
     from oracle import render as OR
+    from paper_2503_11731_gb300 import synth
     bg, objs, poses, sensors = rig_parts()
     anchors, mlp = rig_neural(bg)
-    scene, dec_s = oracle_rig_scene(objs, anchors, mlp, rig_origin(sensors))
     del bg
-    total_rays = n_rays(sensors)
+    origin = rig_origin(sensors)
+    small, cam = synth.plain_scene(n=1000), synth.plain_camera(64, 40, 50.0)
+    for _ in range(args.warmup):
+        OR.render_pinhole(small, cam, pixels=[0], tile=16)
     vals = []
-    sampled = 0
-    for step in range(args.steps + args.warmup):
-        ms, k = oracle_frame_estimate(scene, poses, sensors, n=args.sample_rays, seed=7 + step)
-        if step >= args.warmup:
-            vals.append(ms + dec_s * 1e3)
-            sampled += k
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        scene, _ = oracle_rig_scene(objs, anchors, mlp, origin)
+        _, _ = oracle_frame(scene, poses, sensors)
+        vals.append((time.perf_counter() - t0) * 1e3)
+        del scene
+    wall = time.perf_counter() - t_all
     ms_frame = float(np.mean(vals))
     cores = OR.num_threads()
+    sample = (f"whole frames: FP64 decode of all {anchors.n} anchors (torch CPU) + every ray of the 8 sensors "
+              f"({n_rays(sensors)} rays) in the oracle's tiled mode over {anchors.n * anchors.k + objs.n} surfels; "
+              f"{args.steps} frames in {wall:.1f} s")
     line = {"metric": METRIC, "value": ms_frame, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded driving scene + rig)",
             "impl": "reference",
-            "config": {"workload": RIG_DESC, "sample_rays_per_step": sampled // max(1, args.steps),
-                       "frame_rays": total_rays, "oracle_decode_ms": dec_s * 1e3},
-            "cpu_baseline": {"value": ms_frame, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"FP64 decode of all {anchors.n} anchors (torch CPU), then per sensor "
-                                       f"an oracle call on 1 random ray (its fixed cost) and one on "
-                                       f"max({args.sample_rays}, 2 x cores) rays (brute force over {scene.n} "
-                                       f"surfels; its per-ray cost), combined for the frame's {total_rays} rays"},
+            "config": {"workload": RIG_DESC, "frame_rays": n_rays(sensors),
+                       "oracle_tiles": ORACLE_TILE, "frame_ms": [round(v, 1) for v in vals]},
+            "cpu_baseline": {"value": ms_frame, "unit": UNIT, "cores": cores, "kind": "tiled oracle, timed",
+                             "sample": sample},
             "e2e": {"value": ms_frame, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -260,6 +294,29 @@ def stage_traffic():
         return sum(k["dram_bytes_read"] + k["dram_bytes_write"] for k in c["kernels"].values())
     except Exception:
         return None
+
+
+def measure_fma_peak(stream, reps=5):
+    """FP32 FMA issue rate of this GPU (T lane-op/s): the library's FMA-chain
+    kernel on 8 CTAs of 256 threads per SM, best of `reps`, CUDA events on the
+    launching stream."""
+    import torch
+    from paper_2503_11731_gb300 import gsr
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, device="cuda")
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    best = None
+    for i in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = gsr.fma_peak_kernel(ctypes.c_void_p(out.data_ptr()), blocks, 4096, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            t = n / (a.elapsed_time(b) * 1e-3) / 1e12
+            best = t if best is None else max(best, t)
+    return best
 
 
 def bin_sort_launches(plan):
@@ -791,6 +848,30 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = ms / (args.steps * world)
 
+    fma_peak = measure_fma_peak(stream) if rank == 0 else None
+
+    # ---- the same frame with the FP32 decode, for the parity block, and how
+    # far the timed BF16 frame lies from it
+    parity_gpu, bf16_gap = None, None
+    if args.cpu_baseline and anchors is not None and rank == 0 and world == 1:
+        keep = ("rgb", "depth", "normal", "alpha", "range", "intensity")
+        bf16 = [{k: v.detach().cpu().numpy().copy() for k, v in o.items() if k in keep} for o in r.out]
+        nf.precision = gsr.DECODE_F32
+        nf.render()
+        torch.cuda.synchronize()
+        check_status(r)
+        parity_gpu = [{k: v.detach().cpu().numpy().copy() for k, v in o.items() if k in keep} for o in r.out]
+        nf.precision = gsr.DECODE_BF16_TENSOR
+        nf.render()
+        torch.cuda.synchronize()
+        bf16_gap = []
+        for sd, a, b in zip(sensors, bf16, parity_gpu):
+            k = "intensity" if sd.kind == "lidar" else "rgb"
+            mse = float(np.mean((a[k].astype(np.float64) - b[k]) ** 2))
+            bf16_gap.append({"sensor": f"{sd.kind} {sd.width}x{sd.height}", "channel": k,
+                             "max_abs": float(np.abs(a[k] - b[k]).max()),
+                             "psnr_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None})
+
     # ---- e2e through the public API: this step's inputs from pinned host
     # memory (anchors + MLP + object table + poses, or the explicit table),
     # the frame's rgb / depth / range / intensity back to pinned host memory
@@ -907,30 +988,52 @@ def run_gpu(args):
     # examine (its stop position, or its whole tile list) x the FP32 lane-ops
     # of one ray-surfel evaluation (24 camera, 28 LiDAR).
     pk, src_name = peaks()
-    ops = walk_cam * 24 + walk_lid * 28
-    alu_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
+    derived_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
+    meas_peak = fma_peak
+    peak = meas_peak if meas_peak else derived_peak
     rig_ms = stage["render_rig"]
-    achieved = ops / (rig_ms * 1e-3) / 1e12
+    evals = walk_cam + walk_lid
+    # the survey's cost model: about 40 FP32 issue slots per evaluated
+    # (ray, surfel) pair; the leaner count of the evaluation's own FP32
+    # operations is 24 (camera) / 28 (LiDAR)
+    ach40 = evals * 40 / (rig_ms * 1e-3) / 1e12
+    ach_ops = (walk_cam * 24 + walk_lid * 28) / (rig_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "compositing stage: k_render_rig (all 8 sensors, one persistent launch) + "
-                                      "k_render_split (chunks of split lists)", "achieved": achieved,
-            "peak": alu_peak, "unit": "T FP32 lane-op/s", "frac": achieved / alu_peak, "traffic": stage_traffic(),
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock of " + src_name + " peaks",
-            "algorithmic_units": f"{walk_cam} camera x 24 + {walk_lid} LiDAR x 28 ray-surfel evaluations "
-                                 "(per ray: the list entries it must examine)",
+                                      "k_render_split (chunks of split lists)", "achieved": ach40,
+            "peak": peak, "unit": "T FP32 lane-op/s", "frac": ach40 / peak, "traffic": stage_traffic(),
+            "peak_source": ("measured: FP32 FMA-chain kernel, CUDA events (derived 152 SMs x 128 lanes x max SM "
+                            f"clock = {derived_peak:.2f})") if meas_peak else
+                           f"derived: 152 SMs x 128 FP32 lanes x max SM clock of {src_name} peaks",
+            "peak_measured": meas_peak, "peak_derived": derived_peak,
+            "algorithmic_units": f"{walk_cam} camera + {walk_lid} LiDAR ray-surfel evaluations x 40 FP32 issue "
+                                 "slots (per ray: the list entries it must examine)",
+            "frac_lane_ops_24_28": ach_ops / peak,
             "kernel_ms": rig_ms}
     cpu = None
-    if args.sample_rays > 0 and rank == 0:
+    parity = None
+    if args.cpu_baseline and rank == 0 and world == 1:
+        # the oracle on one whole frame (FP64 decode + every ray, tiled
+        # mode), timed; then every ray of the GPU frame of the same
+        # configuration (FP32 decode, so that nothing the GPU computed enters
+        # the oracle) against it
         from oracle import render as OR
+        t0 = time.perf_counter()
         if anchors is not None:
             o_scene, dec_s = oracle_rig_scene(objs, anchors, mlp, origin)
         else:
             o_scene, dec_s = scene, 0.0
-        ms_o, _ = oracle_frame_estimate(o_scene, poses, sensors, n=args.sample_rays, seed=3)
-        cpu = {"value": ms_o + dec_s * 1e3, "unit": UNIT, "cores": OR.num_threads(), "kind": "oracle",
-               "sample": (f"FP64 decode of all anchors ({dec_s * 1e3:.0f} ms), then " if anchors is not None else "")
-               + f"per sensor, an oracle call on 1 random ray (its fixed cost) and one on "
-                 f"max({args.sample_rays}, 2 x cores) rays (brute force over {o_scene.n} surfels; its per-ray "
-                 f"cost), combined for the frame's {n_rays(sensors)} rays"}
+        o_outs, rend_s = oracle_frame(o_scene, poses, sensors)
+        wall = time.perf_counter() - t0
+        cpu = {"value": wall * 1e3, "unit": UNIT, "cores": OR.num_threads(), "kind": "tiled oracle, timed",
+               "sample": (f"one whole frame: FP64 decode of all anchors ({dec_s:.1f} s) and " if anchors is not None
+                          else "one whole frame: ")
+               + f"every ray of the 8 sensors ({n_rays(sensors)} rays, {rend_s:.1f} s) in the oracle's tiled mode "
+                 f"over {o_scene.n} surfels"}
+        if parity_gpu is not None:
+            parity = {"form": "GPU frame of the benchmarked configuration and tiling with the FP32 decode vs the "
+                              "oracle's own FP64 decode and render, every ray",
+                      "sensors": frame_parity(sensors, parity_gpu, o_outs), "bf16_vs_fp32_decode": bf16_gap}
+        del o_outs, o_scene
     total_rays = n_rays(sensors)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -946,6 +1049,7 @@ def run_gpu(args):
         "mray_per_s": total_rays / (value * 1e-3) / 1e6,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "parity": parity,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "form": "streamed frames (uploads and read-backs on two copy streams, overlapping the "
                         "neighbouring frames)" if anchors is not None else "serial",
@@ -983,7 +1087,8 @@ def main():
     ap.add_argument("--lidar-tile", default="8x8")
     ap.add_argument("--lidar-split-first", type=int, default=0)
     ap.add_argument("--lidar-split-chunk", type=int, default=0)
-    ap.add_argument("--sample-rays", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false",
+                    help="skip the oracle's whole-frame timing and the every-ray parity block")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the explicit-form and decode-only timings")
     ap.add_argument("--no-streaming", dest="streaming", action="store_false",

@@ -584,6 +584,18 @@ gsr_status gsr_read_status(const gsr_plan* plan, const void* workspace, int32_t*
                            int64_t* n_visible, int64_t* n_pairs, void* stream);
 
 /*
+ * Measurement kernel of the compositing roofline (no counterpart in the
+ * paper): `blocks` CTAs of 256 threads, each thread running 8 independent
+ * FP32 fused multiply-add chains of `iters` steps, the sums written to
+ * out[blocks * 256] (device memory, caller-owned).  *fmas receives the
+ * multiply-adds launched; the caller times the launch on `stream` with its
+ * own events, which gives the GPU's FP32 FMA issue rate.  Async.
+ * Errors: GSR_ERR_INVALID_ARG (null pointer, blocks or iters <= 0),
+ * GSR_ERR_CUDA (launch failure).
+ */
+gsr_status gsr_fma_peak_kernel(float* out, int32_t blocks, int32_t iters, int64_t* fmas, void* stream);
+
+/*
  * Self-test of the device-side give-up path (no counterpart in the paper:
  * the bounded waits are this library's, not the method's).  Launches one
  * CTA that arms an mbarrier for 16 bytes no copy will deliver and waits on

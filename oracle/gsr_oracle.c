@@ -880,14 +880,41 @@ static int or_tiles_build(or_tiles* T, const or_surfel* G, int n, const or_senso
     return 0;
 }
 
+/*
+ * Whether the ray (the line through the sensor origin along `dir`, sensor
+ * frame) can reach surfel g: it passes within g->rad of the centre (the
+ * sphere that holds the support with its near-miss margin), or the ray's
+ * low-pass centre lies within 2.13 pixels (cells) of the surfel's.  A
+ * surfel for which both fail is neither a hit nor a near miss of this ray
+ * (or_collect would drop it), so the tiled walk may skip it.
+ */
+static int or_ray_may_reach(const or_surfel* g, const or_sensor* S, const double dir[3], double dir2,
+                            const double pc[2])
+{
+    if (g->culled) return 1;
+    double dx = pc[0] - g->c[0], dy = pc[1] - g->c[1];
+    if (S->kind == 1) {
+        dx = fmod(dx, (double)S->columns);
+        if (dx >= 0.5 * S->columns) dx -= S->columns;
+        if (dx < -0.5 * S->columns) dx += S->columns;
+    }
+    if (dx * dx + dy * dy <= 2.13 * 2.13) return 1;
+    double c[3];
+    or_cross(g->ms, dir, c);
+    /* squared distance of the centre from the line: |m x d|^2 / |d|^2 */
+    return or_dot3(c, c) <= g->rad * g->rad * dir2 * (1.0 + 1e-9);
+}
+
 /* The tiled walk of one ray: its tile's candidates in (depth, index) order. */
 static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long tile_id, const or_sensor* S,
                                const double hu[4], const double hv[4], const double d[3], const double pc[2],
-                               or_ray* out)
+                               const double dir[3], or_ray* out)
 {
+    double dir2 = or_dot3(dir, dir);
     or_ray_init(out);
     for (long long q = T->start[tile_id]; q < T->start[tile_id + 1] && !out->done; ++q) {
         int i = T->cand[q].idx;
+        if (!or_ray_may_reach(&G[i], S, dir, dir2, pc)) continue;
         or_hit h;
         if (or_collect(&G[i], i, S, hu, hv, d, pc, &h)) or_step(out, &G[i], &h, S);
     }
@@ -913,7 +940,8 @@ static or_surfel* or_prepare_all(int n, const or_sensor* S, const double* pos, c
  * for the depth of an intersection, and its low-pass centre.  (x, y) is the
  * pixel column/row, or the LiDAR column/beam.
  */
-static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double hv[4], double d[3], double pc[2])
+static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double hv[4], double d[3], double pc[2],
+                          double dir[3])
 {
     if (S->kind == 0) {
         double px = x + 0.5, py = y + 0.5;
@@ -921,6 +949,7 @@ static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double
         hv[0] = 0; hv[1] = -1; hv[2] = 0; hv[3] = py;
         d[0] = 0; d[1] = 0; d[2] = 1;
         pc[0] = px; pc[1] = py;
+        dir[0] = (px - S->cx) / S->fx; dir[1] = (py - S->cy) / S->fy; dir[2] = 1.0;
     } else if (S->kind == 2) {
         double px = x + 0.5, py = y + 0.5;
         double phi = (px - S->cx) / S->fx, yn = (py - S->cy) / S->fy;
@@ -928,6 +957,7 @@ static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double
         hv[0] = yn * sin(phi); hv[1] = -1; hv[2] = yn * cos(phi); hv[3] = 0;
         d[0] = sin(phi); d[1] = 0; d[2] = cos(phi); /* horizontal part of the ray */
         pc[0] = px; pc[1] = py;
+        dir[0] = sin(phi); dir[1] = yn; dir[2] = cos(phi);
     } else {
         double el = S->el_max - y * S->d_el;
         double az = S->az0 + (x + 0.5) * S->d_az;
@@ -935,6 +965,7 @@ static void or_ray_planes(const or_sensor* S, int x, int y, double hu[4], double
         hv[0] = sin(el) * cos(az); hv[1] = sin(el) * sin(az); hv[2] = -cos(el); hv[3] = 0;
         d[0] = cos(el) * cos(az); d[1] = cos(el) * sin(az); d[2] = sin(el);
         pc[0] = (double)x; pc[1] = (double)y;
+        dir[0] = d[0]; dir[1] = d[1]; dir[2] = d[2];
     }
 }
 
@@ -956,10 +987,10 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
         for (long long q = 0; q < nq; ++q) {
             long long li = pix ? pix[q] : q;
             int x = (int)(li % nx), y = (int)(li / nx);
-            double hu[4], hv[4], d[3], pc[2];
-            or_ray_planes(S, x, y, hu, hv, d, pc);
+            double hu[4], hv[4], d[3], pc[2], dir[3];
+            or_ray_planes(S, x, y, hu, hv, d, pc, dir);
             or_ray r;
-            or_composite_tiled(G, &T, (long long)(y / tile) * T.tiles_x + x / tile, S, hu, hv, d, pc, &r);
+            or_composite_tiled(G, &T, (long long)(y / tile) * T.tiles_x + x / tile, S, hu, hv, d, pc, dir, &r);
             emit(q, &r, ctx);
         }
         or_tiles_free(&T);
@@ -976,8 +1007,8 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
             for (long long q = 0; q < nq; ++q) {
                 long long li = pix ? pix[q] : q;
                 int x = (int)(li % nx), y = (int)(li / nx);
-                double hu[4], hv[4], d[3], pc[2];
-                or_ray_planes(S, x, y, hu, hv, d, pc);
+                double hu[4], hv[4], d[3], pc[2], dir[3];
+                or_ray_planes(S, x, y, hu, hv, d, pc, dir);
                 or_ray r;
                 or_composite(G, n, S, hu, hv, d, pc, buf, &r);
                 emit(q, &r, ctx);

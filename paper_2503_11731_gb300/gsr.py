@@ -162,6 +162,7 @@ SIGNATURES = {
                                  ctypes.POINTER(LidarOut), c_vp]),
     "gsr_read_status": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i64),
                                 ctypes.POINTER(c_i64), c_vp]),
+    "gsr_fma_peak_kernel": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i64), c_vp]),
     "gsr_selftest_wait_timeout": (c_i32, [ctypes.POINTER(Plan), c_vp, ctypes.c_size_t, ctypes.c_uint32, c_vp]),
     "gsr_status_string": (ctypes.c_char_p, [c_i32]),
     "gsr_last_cuda_error": (ctypes.c_char_p, []),
@@ -326,6 +327,14 @@ def read_status(plan, ws, stream):
     _check(lib().gsr_read_status(ctypes.byref(plan), ws, ctypes.byref(st), ctypes.byref(nv), ctypes.byref(npairs),
                                  stream), "gsr_read_status")
     return int(st.value), int(nv.value), int(npairs.value)
+
+
+def fma_peak_kernel(out_ptr, blocks, iters, stream):
+    """Launch the FP32 FMA-chain measurement kernel; returns the FMAs launched."""
+    n = c_i64()
+    _check(lib().gsr_fma_peak_kernel(out_ptr, int(blocks), int(iters), ctypes.byref(n), stream),
+           "gsr_fma_peak_kernel")
+    return int(n.value)
 
 
 def selftest_wait_timeout(plan, ws, ws_bytes, tries, stream):

@@ -208,14 +208,15 @@ def frame_parity(sensors, gpu_outs, oracle_outs, tol=1e-4, flip=2e-5):
         ok = o["flip"] <= flip
         tied = (o["slack"] > 0) | (o["slack_n"] > 0) | (o["slack_z"] > 0)
         errs = {}
+        sc = o["slack_c"]
         if s.kind == "lidar":
-            cols = {"intensity": (np.abs(g["intensity"] - o["intensity"]), o["slack"]),
-                    "alpha": (np.abs(g["alpha"] - o["alpha"]), 0.0)}
+            cols = {"intensity": (np.abs(g["intensity"] - o["intensity"]), o["slack"] + sc),
+                    "alpha": (np.abs(g["alpha"] - o["alpha"]), sc)}
             rel = (o["range"], g["range"])
         else:
-            cols = {"rgb": (np.abs(np.moveaxis(g["rgb"], 0, -1) - o["rgb"]).max(-1), o["slack"]),
-                    "normal": (np.abs(np.moveaxis(g["normal"], 0, -1) - o["normal"]).max(-1), o["slack_n"]),
-                    "alpha": (np.abs(g["alpha"] - o["alpha"]), 0.0)}
+            cols = {"rgb": (np.abs(np.moveaxis(g["rgb"], 0, -1) - o["rgb"]).max(-1), o["slack"] + sc),
+                    "normal": (np.abs(np.moveaxis(g["normal"], 0, -1) - o["normal"]).max(-1), o["slack_n"] + sc),
+                    "alpha": (np.abs(g["alpha"] - o["alpha"]), sc)}
             rel = (o["depth"], g["depth"])
         bad = np.zeros_like(ok)
         for k, (e, sl) in cols.items():
@@ -224,11 +225,23 @@ def frame_parity(sensors, gpu_outs, oracle_outs, tol=1e-4, flip=2e-5):
             bad |= ok & (over > 0)
         dm = ok & (o["alpha"] >= 0.01)
         e_d = np.abs(rel[1] - rel[0]) / np.maximum(np.abs(rel[0]), 1e-12) - \
-            o["slack_z"] / np.maximum(np.abs(rel[0]) * o["alpha"], 1e-12)
+            o["slack_z"] / np.maximum(np.abs(rel[0]) * o["alpha"], 1e-12) - sc / np.maximum(o["alpha"], 1e-2)
         errs["depth_rel"] = float(np.where(dm, e_d, -np.inf).max())
         bad |= dm & (e_d > tol)
+        dump = os.environ.get("GSR_PARITY_DUMP")
+        if dump and bad.any():
+            # the rays beyond tolerance, for offline study
+            os.makedirs(dump, exist_ok=True)
+            ids = np.flatnonzero(bad)[:64]
+            with open(os.path.join(dump, f"frame_{len(rep)}_{s.kind}.json"), "w") as f:
+                json.dump({"rays": ids.tolist(), "width": s.width,
+                           "gpu": {k: np.moveaxis(v, 0, -1).reshape(-1, v.shape[0])[ids].tolist() if v.ndim == 3
+                                   else v.reshape(-1)[ids].tolist() for k, v in g.items()},
+                           "oracle": {k: v.reshape(v.shape[0] * v.shape[1], -1)[ids].tolist()
+                                      for k, v in o.items()}}, f)
         rep.append({"sensor": f"{s.kind} {s.width}x{s.height}", "rays": int(ok.size),
                     "flagged_frac": float(1.0 - ok.mean()), "tied_frac": float((tied & ok).mean()),
+                    "cond_slack_over_tol_frac": float(((sc > tol) & ok).mean()),
                     "max_err_beyond_slack": errs, "rays_over_tolerance": int(bad.sum())})
     return rep
 

@@ -149,6 +149,7 @@ typedef struct {
     double ms[3];      /* centre in the sensor frame                         */
     double rad;        /* radius of a sphere about the centre that holds the
                           support u^2 + v^2 <= 9 with the near-miss margin    */
+    double smin;       /* the smaller scale                                  */
 } or_surfel;
 
 typedef struct {
@@ -286,6 +287,7 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     }
     for (int a = 0; a < 3; ++a) G->ms[a] = ms[a];
     G->rad = 3.01 * (su > sv ? su : sv);
+    G->smin = su < sv ? su : sv;
 
     /* order key and its FP32 error bound */
     if (S->kind == 0) {
@@ -363,6 +365,9 @@ typedef struct {
     int v3, vlp;      /* support validity     */
     int hasplane;     /* m2 != 0              */
     int phantom;      /* culled by the near test, but within rounding of it */
+    int use3;         /* the ray-splat intersection's weight won (else low-pass) */
+    double uabs;      /* |u| + |v| of the intersection */
+    double cosang;    /* |cos| of the angle between the ray and the surfel normal */
 } or_hit;
 
 /* k, l are the plane rows h_u^T WH, h_v^T WH; d (LiDAR only) the ray direction. */
@@ -380,8 +385,11 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
     h->v3 = 0;
     h->rho3 = INFINITY;
     h->zint = 0;
+    h->uabs = 0;
+    h->use3 = 0;
     if (h->hasplane) {
         double u = m[0] / m[2], v = m[1] / m[2];
+        h->uabs = fabs(u) + fabs(v);
         double x[3];
         for (int a = 0; a < 3; ++a) x[a] = G->WH[a][0] * u + G->WH[a][1] * v + G->WH[a][2];
         double zi;
@@ -403,7 +411,7 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
     h->zc = G->zc;
     if (!h->v3 && !h->vlp) return 0;
     double rho;
-    if (h->v3 && (!h->vlp || h->rho3 <= h->rholp)) { rho = h->rho3; h->z = h->zint; }
+    if (h->v3 && (!h->vlp || h->rho3 <= h->rholp)) { rho = h->rho3; h->z = h->zint; h->use3 = 1; }
     else { rho = h->rholp; h->z = G->zc; }
     double Gv = exp(-0.5 * rho);
     double a = G->o * Gv;
@@ -421,7 +429,7 @@ static double or_relm(double x, double thr) { return fabs(x - thr) / fabs(thr); 
  * near test within rounding of the threshold (a phantom).
  */
 static int or_collect(const or_surfel* g, int i, const or_sensor* S, const double hu[4], const double hv[4],
-                      const double d[3], const double pc[2], or_hit* h);
+                      const double d[3], const double pc[2], const double dir[3], or_hit* h);
 
 static int or_cmp_hit(const void* pa, const void* pb)
 {
@@ -441,7 +449,8 @@ static int or_cmp_hit(const void* pa, const void* pb)
  * output that taking the decision the other way could cause (T times the
  * jump in alpha; for the depth-branch choice, the relative jump in depth
  * weight; for a near-tied run at the stop, the weight composited since the
- * run began).  A near-tied run that composites whole does not flag the ray:
+ * run began; for a ray that meets a surfel at a glancing angle, the change
+ * of its weight that the conditioning of Eq. 2 allows, see or_step).  A near-tied run that composites whole does not flag the ray:
  * the change a reordering can make is bounded (or_run_close) and summed
  * into the ray's slack.
  */
@@ -451,6 +460,9 @@ static int or_cmp_hit(const void* pa, const void* pb)
 
 /* Near-miss and phantom margin of or_collect (relative). */
 #define OR_NEAR_MISS 1e-3
+/* Roundoffs of the centre's magnitude by which an FP32 evaluation of the
+   ray-plane intersection may move the centre relative to the ray. */
+#define OR_SOLVE_ROUNDOFF 2.0
 
 typedef struct {
     double feat[3], A, B, D, N[3], T;
@@ -459,6 +471,9 @@ typedef struct {
                          reordering of near-tied runs can make             */
     double slack_n;   /* the same for the normal                           */
     double slack_z;   /* the same for sum w z (the depth accumulator B)    */
+    double slack_c;   /* bound of the change of every output that FP32
+                         rounding can cause through the conditioning of
+                         Eq. 2 at glancing angles (relative for depth)     */
     int n_contrib;
     int done;         /* the stop rule ended the ray                       */
     /* the current run of near-tied composited surfels (consecutive centre
@@ -556,6 +571,24 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     /* a normal whose facing sign FP32 may take the other way: the normal
        output moves by twice its weight */
     if (g->n_amb && S->kind != 1) or_flip(&r->flip, 0.0, 1.0, 2.0 * h->alpha * T);
+    /* the conditioning of Eq. 2: where a ray meets the surfel plane at a
+       glancing angle, an FP32 rounding that moves the plane along its normal
+       (the centre's sensor-frame coordinates, each off by about u |mu_a|) or
+       turns the ray (LiDAR and cylinder rays come from rounded angles: about
+       u radians, times the distance t) moves the hit within the plane by
+       that amount over |cos|; in (u, v) units, over the scale.  The weight
+       follows with alpha 0.5 d(u^2 + v^2). */
+    if (h->use3 && h->alpha < 0.99) {
+        double dn = 0.0;
+        for (int a = 0; a < 3; ++a) dn += fabs(g->normal[a] * g->ms[a]);
+        double turn = S->kind == 0 ? 0.0 : fabs(h->zint);
+        double du = OR_SOLVE_ROUNDOFF * OR_U32 * (dn + turn) /
+                    (g->smin * (h->cosang > 1e-12 ? h->cosang : 1e-12));
+        double dalpha = h->alpha * h->uabs * du;
+        /* this weight moves by T dalpha, the later ones by at most as much in
+           all: a bound on each output's change, added to the ray's slack */
+        r->slack_c += 2.0 * T * dalpha;
+    }
     double v[7];
     or_values(g, h, v);
     int tie = r->run_len > 0 && fabs(h->zc - r->last_zc) <= g->tau + r->last_tau;
@@ -604,12 +637,13 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
 }
 
 static int or_collect(const or_surfel* g, int i, const or_sensor* S, const double hu[4], const double hv[4],
-                      const double d[3], const double pc[2], or_hit* h)
+                      const double d[3], const double pc[2], const double dir[3], or_hit* h)
 {
     if (g->culled && g->cull_rel >= OR_FLIP_REL) return 0;
     h->idx = i;
     h->phantom = g->culled;
     int any = or_eval(g, S, hu, hv, d, pc, h);
+    h->cosang = fabs(or_dot3(g->normal, dir)) / sqrt(or_dot3(dir, dir));
     /* keep near misses too: their acceptance could flip in FP32 */
     int near_miss = (h->hasplane && h->zint > S->near_ && or_relm(h->rho3, 9.0) < OR_NEAR_MISS) ||
                     (h->hasplane && h->rho3 <= 9.0 && or_relm(h->zint, S->near_) < OR_NEAR_MISS) ||
@@ -621,11 +655,11 @@ static int or_collect(const or_surfel* g, int i, const or_sensor* S, const doubl
 
 /* Brute force: every surfel against the ray, hits sorted by (depth, index). */
 static void or_composite(const or_surfel* G, int n, const or_sensor* S, const double hu[4], const double hv[4],
-                         const double d[3], const double pc[2], or_hit* buf, or_ray* out)
+                         const double d[3], const double pc[2], const double dir[3], or_hit* buf, or_ray* out)
 {
     int nh = 0;
     for (int i = 0; i < n; ++i)
-        if (or_collect(&G[i], i, S, hu, hv, d, pc, &buf[nh])) ++nh;
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &buf[nh])) ++nh;
     qsort(buf, (size_t)nh, sizeof(or_hit), or_cmp_hit);
     or_ray_init(out);
     for (int j = 0; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
@@ -916,7 +950,7 @@ static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long 
         int i = T->cand[q].idx;
         if (!or_ray_may_reach(&G[i], S, dir, dir2, pc)) continue;
         or_hit h;
-        if (or_collect(&G[i], i, S, hu, hv, d, pc, &h)) or_step(out, &G[i], &h, S);
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &h)) or_step(out, &G[i], &h, S);
     }
     or_ray_finish(out);
 }
@@ -1010,7 +1044,7 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
                 double hu[4], hv[4], d[3], pc[2], dir[3];
                 or_ray_planes(S, x, y, hu, hv, d, pc, dir);
                 or_ray r;
-                or_composite(G, n, S, hu, hv, d, pc, buf, &r);
+                or_composite(G, n, S, hu, hv, d, pc, dir, buf, &r);
                 emit(q, &r, ctx);
             }
             free(buf);
@@ -1035,7 +1069,12 @@ static void or_emit_camera(long long q, const or_ray* r, void* ctx)
     o->trans[q] = r->T;
     if (o->acc) { o->acc[q * 3 + 0] = r->A; o->acc[q * 3 + 1] = r->B; o->acc[q * 3 + 2] = r->D; }
     if (o->flip) o->flip[q] = r->flip;
-    if (o->slack) { o->slack[q * 3 + 0] = r->slack; o->slack[q * 3 + 1] = r->slack_n; o->slack[q * 3 + 2] = r->slack_z; }
+    if (o->slack) {
+        o->slack[q * 4 + 0] = r->slack;
+        o->slack[q * 4 + 1] = r->slack_n;
+        o->slack[q * 4 + 2] = r->slack_z;
+        o->slack[q * 4 + 3] = r->slack_c;
+    }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 
@@ -1072,9 +1111,10 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
  * sum(w z)/sum(w) (0 where sum(w) == 0); normal is sum(w n), unnormalised;
  * acc = [sum w, sum w z, sum w z^2] per pixel ([n_pix][3], may be NULL).
  * flip [n_pix] is the largest output change an FP32-flippable threshold
- * decision could cause (0 if none); slack [n_pix][3] bounds the change a
+ * decision could cause (0 if none); slack [n_pix][4] bounds the change a
  * reordering of near-tied surfels can make to colour, to the normal and to
- * sum w z (both may be NULL).
+ * sum w z, and (fourth) the change of any output that FP32 rounding can
+ * cause through the conditioning of Eq. 2 (both may be NULL).
  * tile == 0 checks every surfel for every pixel (brute force); tile > 0
  * walks per-tile candidate lists of tile x tile pixels built from the
  * oracle's own conservative bound, with the same arithmetic and the same
@@ -1135,7 +1175,12 @@ static void or_emit_lidar(long long q, const or_ray* r, void* ctx)
     o->alpha[q] = r->A;
     o->trans[q] = r->T;
     if (o->flip) o->flip[q] = r->flip;
-    if (o->slack) { o->slack[q * 3 + 0] = r->slack; o->slack[q * 3 + 1] = r->slack_n; o->slack[q * 3 + 2] = r->slack_z; }
+    if (o->slack) {
+        o->slack[q * 4 + 0] = r->slack;
+        o->slack[q * 4 + 1] = r->slack_n;
+        o->slack[q * 4 + 2] = r->slack_z;
+        o->slack[q * 4 + 3] = r->slack_c;
+    }
     if (o->n_contrib) o->n_contrib[q] = r->n_contrib;
 }
 

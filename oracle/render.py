@@ -98,7 +98,9 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
     (sum w, sum w z, sum w z^2), flip [P] (largest output change that an
     FP32-flippable threshold decision could cause; 0 if none), slack [P],
     slack_n [P] and slack_z [P] (bounds of the change a reordering of
-    near-tied surfels can make to colour, normal and sum w z), n_contrib [P].  With pixels=None,
+    near-tied surfels can make to colour, normal and sum w z), slack_c [P]
+    (bound of the change of any output, relative for depth, that FP32
+    rounding can cause through the conditioning of Eq. 2), n_contrib [P].  With pixels=None,
     arrays are reshaped to images (rgb [H,W,3], ...).
     """
     lib = _load()
@@ -118,7 +120,7 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
         pix_p = pix_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
     out = {k: np.zeros(sh, np.float64) for k, sh in
            [("rgb", (npix, 3)), ("depth", (npix,)), ("normal", (npix, 3)), ("alpha", (npix,)),
-            ("T", (npix,)), ("acc", (npix, 3)), ("flip", (npix,)), ("slack2", (npix, 3))]}
+            ("T", (npix,)), ("acc", (npix, 3)), ("flip", (npix,)), ("slack2", (npix, 4))]}
     out["n_contrib"] = np.zeros(npix, np.int32)
     dp = {k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in out.items() if v.dtype == np.float64}
     deg = int(round(np.sqrt(s.sh.shape[1]))) - 1
@@ -134,7 +136,7 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
     if rc != 0:
         raise RuntimeError("oracle camera render failed")
     s2 = out.pop("slack2")
-    out["slack"], out["slack_n"], out["slack_z"] = s2[:, 0].copy(), s2[:, 1].copy(), s2[:, 2].copy()
+    out["slack"], out["slack_n"], out["slack_z"], out["slack_c"] = (s2[:, i].copy() for i in range(4))
     if pixels is None:
         H, W = cam.height, cam.width
         out = {k: v.reshape((H, W) + v.shape[1:]) for k, v in out.items()}
@@ -163,7 +165,7 @@ def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
         keep.append(ray_arr)
         ray_p = ray_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
     out = {k: np.zeros(nr, np.float64) for k in ("range", "intensity", "drop", "alpha", "T", "flip")}
-    out["slack2"] = np.zeros((nr, 3), np.float64)
+    out["slack2"] = np.zeros((nr, 4), np.float64)
     rd = getattr(s, "ray_drop", None)
     rd_p = None if rd is None else D(rd)
     out["n_contrib"] = np.zeros(nr, np.int32)
@@ -179,7 +181,7 @@ def render_lidar(s, lid, rays=None, obj_pose=None, tile=0):
     if rc != 0:
         raise RuntimeError("oracle_render_lidar failed")
     s2 = out.pop("slack2")
-    out["slack"], out["slack_n"], out["slack_z"] = s2[:, 0].copy(), s2[:, 1].copy(), s2[:, 2].copy()
+    out["slack"], out["slack_n"], out["slack_z"], out["slack_c"] = (s2[:, i].copy() for i in range(4))
     if rays is None:
         out = {k: v.reshape(lid.beams, lid.columns) for k, v in out.items()}
     return out

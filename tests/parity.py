@@ -44,7 +44,7 @@ def _dump(name, idx, cols):
 
 
 def _worst(err, k=12):
-    return np.argsort(-np.nan_to_num(err, nan=np.inf))[:k]
+    return np.argsort(-np.nan_to_num(np.ravel(err), nan=np.inf))[:k]
 
 
 def record(report, name=None):
@@ -57,11 +57,14 @@ def record(report, name=None):
 
 
 def _slack(o, depth):
-    """The oracle's order slack of each ray: absolute for colour / intensity /
-    normal, relative to the depth (range) for the depth, since the swap
-    leaves sum w unchanged and moves sum w z by slack_z."""
-    sl = o.get("slack", np.zeros_like(o["flip"]))
-    slz = o.get("slack_z", np.zeros_like(o["flip"])) / np.maximum(np.abs(depth) * o["alpha"], 1e-12)
+    """The oracle's slack of each ray: the reordering bound of near-tied runs
+    (absolute for colour / intensity / normal; relative to the depth (range)
+    for the depth, since a reordering leaves sum w unchanged and moves sum w z
+    by slack_z) plus the conditioning bound slack_c of every output."""
+    z = np.zeros_like(o["flip"])
+    sc = o.get("slack_c", z)
+    sl = o.get("slack", z) + sc
+    slz = o.get("slack_z", z) / np.maximum(np.abs(depth) * o["alpha"], 1e-12) + sc / np.maximum(o["alpha"], 1e-2)
     return sl, slz
 
 
@@ -69,8 +72,10 @@ def _slack_report(o, ok):
     z = np.zeros_like(o["flip"])
     sl, sn, sz = o.get("slack", z), o.get("slack_n", z), o.get("slack_z", z)
     tied = (sl > 0) | (sn > 0) | (sz > 0)
+    sc = o.get("slack_c", z)
     return dict(tied=int((tied & ok).sum()), tied_frac=float((tied & ok).mean()),
-                slack_over_tol=float(((sl > TOL_ABS) & ok).mean()), max_slack=float(sl[ok].max(initial=0)))
+                slack_over_tol=float(((sl > TOL_ABS) & ok).mean()), max_slack=float(sl[ok].max(initial=0)),
+                cond_slack_over_tol=float(((sc > TOL_ABS) & ok).mean()), max_cond_slack=float(sc[ok].max(initial=0)))
 
 
 def check_camera(g, o, pix=None, max_flag=0.01, name=None):
@@ -90,9 +95,9 @@ def check_camera(g, o, pix=None, max_flag=0.01, name=None):
     ok = ~flag
     sl, slz = _slack(o, o["depth"])
     e_rgb = np.abs(rgb - o["rgb"]).max(-1) - sl
-    e_n = np.abs(nrm - o["normal"]).max(-1) - o.get("slack_n", sl)
-    e_a = np.abs(alpha - o["alpha"])
-    e_t = np.abs(T - o["T"])
+    e_n = np.abs(nrm - o["normal"]).max(-1) - o.get("slack_n", 0.0) - o.get("slack_c", 0.0)
+    e_a = np.abs(alpha - o["alpha"]) - o.get("slack_c", 0.0)
+    e_t = np.abs(T - o["T"]) - o.get("slack_c", 0.0)
     dmask = ok & (o["alpha"] >= 0.01)
     e_d = np.abs(depth - o["depth"]) / np.maximum(np.abs(o["depth"]), 1e-12) - slz
     if os.environ.get("GSR_PARITY_DUMP"):
@@ -131,11 +136,20 @@ def check_lidar(g, o, rays=None, max_flag=0.02, name=None, drop=False):
     dmask = ok & (o["alpha"] >= 0.01)
     e_r = np.abs(rng_ - o["range"]) / np.maximum(np.abs(o["range"]), 1e-12) - slz
     rep = dict(kind="lidar", intensity=(np.abs(inten - o["intensity"]) - sl)[ok].max(initial=0),
-               alpha=np.abs(alpha - o["alpha"])[ok].max(initial=0),
+               alpha=(np.abs(alpha - o["alpha"]) - o.get("slack_c", 0.0))[ok].max(initial=0),
                range=e_r[dmask].max(initial=0), flagged=int(flag.sum()), n=int(flag.size),
                flagged_frac=float(flag.mean()), cap=max_flag, **_slack_report(o, ok))
     if dr is not None:
         rep["drop"] = (np.abs(dr - o["drop"]) - sl)[ok].max(initial=0)
+    if os.environ.get("GSR_PARITY_DUMP"):
+        e_i = np.abs(inten - o["intensity"]) - sl
+        w = _worst(np.maximum(np.maximum(e_i, np.abs(alpha - o["alpha"])), np.where(dmask, e_r, 0)) * ok)
+        ids = np.asarray(rays)[w] if rays is not None else w
+        _dump(name or os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], ids,
+              {"g_i": inten.reshape(-1)[w], "o_i": o["intensity"].reshape(-1)[w],
+               "g_a": alpha.reshape(-1)[w], "o_a": o["alpha"].reshape(-1)[w],
+               "g_r": rng_.reshape(-1)[w], "o_r": o["range"].reshape(-1)[w],
+               "flip": o["flip"].reshape(-1)[w], "slack": sl.reshape(-1)[w]})
     report = record(rep, name)
     assert flag.mean() <= max_flag, report
     assert report["intensity"] <= TOL_ABS, report

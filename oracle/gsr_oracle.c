@@ -460,9 +460,10 @@ static int or_cmp_hit(const void* pa, const void* pb)
 
 /* Near-miss and phantom margin of or_collect (relative). */
 #define OR_NEAR_MISS 1e-3
-/* Roundoffs of the centre's magnitude by which an FP32 evaluation of the
-   ray-plane intersection may move the centre relative to the ray. */
-#define OR_SOLVE_ROUNDOFF 2.0
+/* Roundoffs of the terms' magnitude by which an FP32 evaluation may move
+   the surfel plane along its normal or turn the ray: the gamma_4 bound of
+   an affine map's four terms, as for the order key. */
+#define OR_SOLVE_ROUNDOFF 4.0
 
 typedef struct {
     double feat[3], A, B, D, N[3], T;
@@ -547,11 +548,37 @@ static void or_ray_finish(or_ray* r) { or_run_close(r); }
  * A = sum w, B = sum w z, D = sum w z^2 and sum w n, with w = alpha T, and
  * sets r->done when the stop rule ends the ray.
  */
+/*
+ * The conditioning of Eq. 2: where a ray meets the surfel plane at a
+ * glancing angle, an FP32 rounding that moves the plane along its normal
+ * (the centre's sensor-frame coordinates, each off by about u |mu_a|) or
+ * turns the ray (LiDAR and cylinder rays come from rounded angles: about u
+ * radians, times the distance t) moves the hit within the plane by that
+ * amount over |cos|; in (u, v) units, over the scale.  Returns that bound of
+ * |du| (and |dv|), 0 without an intersection.
+ */
+static double or_solve_error(const or_surfel* g, const or_hit* h, const or_sensor* S)
+{
+    if (!h->hasplane) return 0.0;
+    double dn = 0.0;
+    for (int a = 0; a < 3; ++a) dn += fabs(g->normal[a] * g->ms[a]);
+    double turn = S->kind == 0 ? 0.0 : fabs(h->zint);
+    return OR_SOLVE_ROUNDOFF * OR_U32 * (dn + turn) / (g->smin * (h->cosang > 1e-12 ? h->cosang : 1e-12));
+}
+
+static double or_max(double a, double b) { return a > b ? a : b; }
+
 static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sensor* S)
 {
     double T = r->T;
+    /* the threshold margins: 2e-5 relative, or what the conditioning of the
+       hit allows if that is more (u^2 + v^2 moves by 2 (|u| + |v|) du, alpha
+       relatively by (|u| + |v|) du) */
+    double du = or_solve_error(g, h, S);
+    double m_rho = or_max(OR_FLIP_REL, 2.0 * h->uabs * du / 9.0);
+    double m_alpha = h->use3 ? or_max(OR_FLIP_REL, h->uabs * du) : OR_FLIP_REL;
     double edge = T * g->o * exp(-4.5);
-    if (h->hasplane && h->zint > S->near_) or_flip(&r->flip, or_relm(h->rho3, 9.0), OR_FLIP_REL, edge);
+    if (h->hasplane && h->zint > S->near_) or_flip(&r->flip, or_relm(h->rho3, 9.0), m_rho, edge);
     if (h->hasplane && h->rho3 <= 9.0)
         or_flip(&r->flip, or_relm(h->zint, S->near_), OR_FLIP_REL, T * g->o * exp(-0.5 * h->rho3));
     or_flip(&r->flip, or_relm(h->rholp, 9.0), OR_FLIP_REL, edge);
@@ -559,7 +586,7 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     /* the centre-depth cull of this surfel could go the other way */
     or_flip(&r->flip, g->cull_rel, OR_FLIP_REL, h->alpha * T);
     if (h->phantom) return;
-    or_flip(&r->flip, or_relm(h->alpha, 1.0 / 255.0), OR_FLIP_REL, T / 255.0);
+    or_flip(&r->flip, or_relm(h->alpha, 1.0 / 255.0), m_alpha, T / 255.0);
     if (h->v3 && h->vlp) {
         double big = h->rho3 > h->rholp ? h->rho3 : h->rholp;
         or_flip(&r->flip, fabs(h->rho3 - h->rholp) / big, OR_FLIP_REL,
@@ -567,23 +594,14 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     }
     if (h->alpha < 1.0 / 255.0) return;
     double test = T * (1.0 - h->alpha);
-    or_flip(&r->flip, or_relm(test, 1e-4), OR_FLIP_REL, h->alpha * T);
+    or_flip(&r->flip, or_relm(test, 1e-4), or_max(m_alpha * h->alpha / (1.0 - h->alpha), OR_FLIP_REL),
+            h->alpha * T);
     /* a normal whose facing sign FP32 may take the other way: the normal
        output moves by twice its weight */
     if (g->n_amb && S->kind != 1) or_flip(&r->flip, 0.0, 1.0, 2.0 * h->alpha * T);
-    /* the conditioning of Eq. 2: where a ray meets the surfel plane at a
-       glancing angle, an FP32 rounding that moves the plane along its normal
-       (the centre's sensor-frame coordinates, each off by about u |mu_a|) or
-       turns the ray (LiDAR and cylinder rays come from rounded angles: about
-       u radians, times the distance t) moves the hit within the plane by
-       that amount over |cos|; in (u, v) units, over the scale.  The weight
-       follows with alpha 0.5 d(u^2 + v^2). */
+    /* the conditioning of Eq. 2 (or_solve_error): the weight follows the
+       hit's (u, v) with alpha 0.5 d(u^2 + v^2) */
     if (h->use3 && h->alpha < 0.99) {
-        double dn = 0.0;
-        for (int a = 0; a < 3; ++a) dn += fabs(g->normal[a] * g->ms[a]);
-        double turn = S->kind == 0 ? 0.0 : fabs(h->zint);
-        double du = OR_SOLVE_ROUNDOFF * OR_U32 * (dn + turn) /
-                    (g->smin * (h->cosang > 1e-12 ? h->cosang : 1e-12));
         double dalpha = h->alpha * h->uabs * du;
         /* this weight moves by T dalpha, the later ones by at most as much in
            all: a bound on each output's change, added to the ray's slack */

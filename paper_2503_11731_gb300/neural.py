@@ -233,3 +233,66 @@ class FramePipeline:
     def finish(self):
         """Make `stream` wait for the last frame's outputs."""
         self.stream.wait_event(self.outputs_read)
+
+
+class Distiller:
+    """Distillation of a learned scene from target camera frames (Sec. III-A:
+    the anchor MLP is trained on renders of the scene it stands in for).
+
+    One step, on the library's kernels: decode the anchors (BF16 tensor-core
+    or FP32 decode) -> render one camera -> gsr_loss against that camera's
+    target frame -> gsr_backward (reverse rasteriser + preprocess backward
+    to the decoded table) -> gsr_decode_backward (to the MLP weights and the
+    anchor features) -> gsr_adam.  One plan per distinct camera model and
+    size; a camera's pose is set with Renderer.move, so plans, workspaces and
+    outputs are reused across poses."""
+
+    OUTPUTS = ("rgb", "depth", "normal", "alpha", "trans", "depth_acc", "n_contrib")
+
+    def __init__(self, model: NeuralModel, anchors: DeviceAnchors, tile=(16, 8), max_dup=0, split=(0, 0),
+                 loss_weights=(0.0, 0.0)):
+        """`loss_weights` = (distortion, normal consistency) of gsr_loss next
+        to its L1 colour term."""
+        self.model, self.anchors = model, anchors
+        self.tile, self.max_dup, self.split = tile, max_dup, split
+        self.w_dist, self.w_normal = loss_weights
+        self.table = model.new_table(anchors)
+        self.grads = {k: torch.zeros_like(getattr(self.table, k))
+                      for k in ("pos", "log_scale", "quat", "opacity", "sh")}
+        self._plans = {}
+
+    def renderer(self, cam):
+        """The plan of `cam`'s model and size, moved to `cam`'s pose."""
+        from .frame import Renderer
+        key = (cam.kind, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.near)
+        r = self._plans.get(key)
+        if r is None:
+            r = self._plans[key] = Renderer(self.anchors.n * self.anchors.k, [cam], tiles=[self.tile],
+                                            max_dup=self.max_dup, split=self.split, outputs=self.OUTPUTS)
+        else:
+            r.move([cam])
+        return r
+
+    def _render(self, cam, origin, precision):
+        self.model.decode(self.anchors, origin, precision=precision, out=self.table)
+        r = self.renderer(cam)
+        r.render(self.table)
+        return r
+
+    def render(self, cam, origin, precision=gsr.DECODE_BF16_TENSOR):
+        """Decode and render `cam`; returns the plan's outputs (rgb, depth, alpha, ...)."""
+        return self._render(cam, origin, precision).out[0]
+
+    def step(self, cam, target, origin, precision=gsr.DECODE_BF16_TENSOR, lr=3e-3, lr_feature=1e-2):
+        """One training step on `cam`'s frame against `target` (3 x H x W);
+        returns the loss tensor (on the device: [total, l1, distortion, normal])."""
+        from .frame import camera_backward, camera_loss
+        r = self._render(cam, origin, precision)
+        loss, lo = camera_loss(r, 0, target, w_dist=self.w_dist, w_normal=self.w_normal)
+        for g in self.grads.values():
+            g.zero_()
+        camera_backward(r, 0, lo.struct(), self.table, out=self.grads)
+        self.model.zero_grads(self.anchors)
+        self.model.backward(self.anchors, origin, self.grads)
+        self.model.adam_step(self.anchors, lr=lr, lr_feature=lr_feature)
+        return loss

@@ -364,16 +364,19 @@ def object_poses(n_obj, seed, x_range=(-40.0, 80.0)):
     return _f32(P)
 
 
-def surround_rig():
+def surround_rig(x=0.0, y=0.0, yaw_deg=0.0):
     """2 cameras 1920x1080 (front/back, f=1000), 4 cameras 1280x720 at yaw
     +-60 and +-120 deg (f=640), a 128x1800 LiDAR (el -25..15 deg) and a
-    32x1024 LiDAR (el -30..10 deg), on a vehicle at the origin."""
-    cams = [pinhole(1920, 1080, 1000.0, (1.5, 0, 1.5), 0.0),
-            pinhole(1920, 1080, 1000.0, (-1.5, 0, 1.5), 180.0)]
+    32x1024 LiDAR (el -30..10 deg), on a vehicle at (x, y) on the road facing
+    yaw_deg (the origin facing +x by default)."""
+    c, s = math.cos(math.radians(yaw_deg)), math.sin(math.radians(yaw_deg))
+    at = lambda px, py, pz: (x + c * px - s * py, y + s * px + c * py, pz)
+    cams = [pinhole(1920, 1080, 1000.0, at(1.5, 0, 1.5), yaw_deg + 0.0),
+            pinhole(1920, 1080, 1000.0, at(-1.5, 0, 1.5), yaw_deg + 180.0)]
     for yaw in (60.0, -60.0, 120.0, -120.0):
-        cams.append(pinhole(1280, 720, 640.0, (0.0, 0.0, 1.6), yaw))
-    lidars = [spinning_lidar(128, 1800, -25.0, 15.0, (0.0, 0.0, 1.8)),
-              spinning_lidar(32, 1024, -30.0, 10.0, (0.5, 0.0, 1.9))]
+        cams.append(pinhole(1280, 720, 640.0, at(0.0, 0.0, 1.6), yaw_deg + yaw))
+    lidars = [spinning_lidar(128, 1800, -25.0, 15.0, at(0.0, 0.0, 1.8), yaw_deg),
+              spinning_lidar(32, 1024, -30.0, 10.0, at(0.5, 0.0, 1.9), yaw_deg)]
     return cams + lidars
 
 

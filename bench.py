@@ -340,7 +340,9 @@ def bin_sort_launches(plan):
     bits = 1
     while (1 << bits) < T:
         bits += 1
-    return 3 + 20 + 4 + 5 * ((bits + 7) // 8) + 1 + 1 + 1 + 10
+    # 8-bit digits; a key of 8k + 1 bits takes a 9-bit top digit
+    passes = bits // 8 if bits % 8 == 1 and bits > 8 else (bits + 7) // 8
+    return 3 + 20 + 4 + 5 * passes + 1 + 1 + 1 + 10
 
 
 def preprocess_launches(plan):

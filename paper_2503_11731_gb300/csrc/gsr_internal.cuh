@@ -36,6 +36,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;               // items per thread per sort tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kRadixBits = 8;
+constexpr int kRadixBitsWide = 9;         // the widest digit of a pass (a key of 8k + 1 bits)
 // Default split of long tile lists (gsr_tiling.split_first / split_chunk = 0).
 constexpr int kSplitFirstDefault = 16384;  // positions walked before a tile's list is split
 constexpr int kSplitChunkDefault = 384;    // positions per later chunk
@@ -149,6 +150,8 @@ inline uint64_t split_ray_capacity(const gsr_plan* p)
 }
 inline uint64_t split_item_capacity(const gsr_plan* p) { return split_ray_capacity(p) / 32 + 1; }
 int tile_sort_passes(const gsr_plan* p);
+// Digit widths of the tile-key passes, low digit first; returns the count.
+int tile_sort_widths(const gsr_plan* p, int widths[4]);
 constexpr int kDepthSortPasses = 4;
 
 // --------------------------------------------------------------- device helpers

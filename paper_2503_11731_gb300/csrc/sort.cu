@@ -153,20 +153,23 @@ __global__ void __launch_bounds__(256) k_compact_write(const uint32_t* __restric
 }
 
 // ------------------------------------------------------------------ radix sort
-// Per-CTA digit histogram of its chunk; hist is digit-major: hist[d * G + cta].
+// Per-CTA digit histogram of its chunk for a digit of BITS bits at `shift`;
+// hist is digit-major: hist[d * G + cta].
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ n_ptr, int shift,
                                                              uint32_t* __restrict__ hist)
 {
-    __shared__ uint32_t h[kSortThreads / 32][kRadix];
+    constexpr int R = 1 << BITS;
+    __shared__ uint32_t h[kSortThreads / 32][R];
     const int w = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < (kSortThreads / 32) * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * R; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
     uint64_t b, e;
     chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
-    for (uint64_t i = b + threadIdx.x; i < e; i += kSortThreads) atomicAdd(&h[w][(keys[i] >> shift) & (kRadix - 1)], 1u);
+    for (uint64_t i = b + threadIdx.x; i < e; i += kSortThreads) atomicAdd(&h[w][(keys[i] >> shift) & (R - 1)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+    for (int d = threadIdx.x; d < R; d += kSortThreads) {
         uint32_t s = 0;
 #pragma unroll
         for (int k = 0; k < kSortThreads / 32; ++k) s += h[k][d];
@@ -223,14 +226,17 @@ __global__ void __launch_bounds__(256) k_hist_block_apply(uint32_t* __restrict__
     }
 }
 
-// Stable scatter of one 8-bit digit pass.  CTA g owns the contiguous chunk
-// [b, e) of the input (the same chunk k_radix_hist counted) and walks it in
-// tiles of kSortTile items; warp w of a tile owns items [w*256, w*256+256)
-// and ranks them with match_any, a prefix over warps orders the tile, and
-// the tile is written digit by digit from shared memory (runs of equal
-// digits are contiguous in the output).  Keys and values arrive by two
-// bulk copies per tile into a double buffer (one mbarrier each): tile t + 1
-// is in flight while tile t is ranked, ordered in the buffer and written.
+// Stable scatter of one digit pass (BITS = 8, or 9 for the top digit of a
+// key of 8k + 1 bits).  CTA g owns the contiguous chunk [b, e) of the input
+// (the same chunk k_radix_hist counted) and walks it in tiles of TILE
+// items; warp w of a tile owns items [w*SEG, w*SEG+SEG) and ranks them with
+// match_any, a prefix over warps orders the tile, and the tile is written
+// digit by digit from shared memory (runs of equal digits are contiguous in
+// the output).  Keys and values arrive by two bulk copies per tile into a
+// double buffer (one mbarrier each): tile t + 1 is in flight while tile t is
+// ranked, ordered in the buffer and written.  A 9-bit pass takes half-size
+// tiles so that its larger digit tables still fit static shared memory.
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                 const uint32_t* __restrict__ vin,
                                                                 uint32_t* __restrict__ kout,
@@ -239,22 +245,26 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 const uint32_t* __restrict__ hist,
                                                                 uint32_t* __restrict__ counters)
 {
+    constexpr int R = 1 << BITS;
+    constexpr int DPT = R / kSortThreads;  // digits per thread in the digit prefix
+    constexpr int TILE = BITS > 8 ? kSortTile / 2 : kSortTile;
     constexpr int NW = kSortThreads / 32;
-    constexpr int SEG = kSortTile / NW;  // items per warp per tile (256)
-    __shared__ alignas(16) uint32_t kb[2][kSortTile];
-    __shared__ alignas(16) uint32_t vb[2][kSortTile];
-    __shared__ uint32_t wh[NW][kRadix];
-    __shared__ uint32_t dbase[kRadix];
-    __shared__ uint32_t toff[kRadix];
-    __shared__ uint32_t tcnt[kRadix];
+    constexpr int SEG = TILE / NW;  // items per warp per tile
+    static_assert(R % kSortThreads == 0 && SEG % 32 == 0, "digit and tile shapes");
+    __shared__ alignas(16) uint32_t kb[2][TILE];
+    __shared__ alignas(16) uint32_t vb[2][TILE];
+    __shared__ uint32_t wh[NW][R];
+    __shared__ uint32_t dbase[R];
+    __shared__ uint32_t toff[R];
+    __shared__ uint32_t tcnt[R];
     __shared__ uint32_t sm[9];
     __shared__ alignas(8) uint64_t bar[2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     uint64_t b, e;
     chunk_of(*n_ptr, blockIdx.x, gridDim.x, b, e);
-    const int ntiles = e > b ? (int)((e - b + kSortTile - 1) / kSortTile) : 0;
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) dbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+    const int ntiles = e > b ? (int)((e - b + TILE - 1) / TILE) : 0;
+    for (int d = threadIdx.x; d < R; d += kSortThreads) dbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -264,11 +274,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     // tile t: whole 16-byte groups by bulk copy (a chunk starts 128-byte
     // aligned), a ragged end of < 4 items by plain loads
     auto tile_items = [&](int t) {
-        const uint64_t s0 = b + (uint64_t)t * kSortTile;
-        return (int)((e - s0) < (uint64_t)kSortTile ? (e - s0) : (uint64_t)kSortTile);
+        const uint64_t s0 = b + (uint64_t)t * TILE;
+        return (int)((e - s0) < (uint64_t)TILE ? (e - s0) : (uint64_t)TILE);
     };
     auto issue = [&](int t) {
-        const uint64_t s0 = b + (uint64_t)t * kSortTile;
+        const uint64_t s0 = b + (uint64_t)t * TILE;
         const uint32_t nbulk = (uint32_t)tile_items(t) & ~3u;
         mbar_arrive_expect_tx(&bar[t & 1], nbulk * 8u);
         if (nbulk > 0) {
@@ -281,12 +291,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         if (ntiles > 1) issue(1);
     }
     for (int t = 0; t < ntiles; ++t) {
-        const uint64_t t0 = b + (uint64_t)t * kSortTile;
+        const uint64_t t0 = b + (uint64_t)t * TILE;
         const int nt = tile_items(t);
         const int nbulk = nt & ~3;
         uint32_t* kt = kb[t & 1];
         uint32_t* vt = vb[t & 1];
-        for (int k = threadIdx.x; k < NW * kRadix; k += kSortThreads) (&wh[0][0])[k] = 0;
+        for (int k = threadIdx.x; k < NW * R; k += kSortThreads) (&wh[0][0])[k] = 0;
         const bool got = mbar_wait_bounded(&bar[t & 1], (uint32_t)(t >> 1) & 1u, counters);
         if (!__syncthreads_and(got)) {
             // give up: let the copies in flight land (bounded waits) before leaving
@@ -304,9 +314,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
             const bool ok = li < nt;
             key[r] = li < nbulk ? kt[li] : ok ? kin[t0 + li] : 0u;
             val[r] = li < nbulk ? vt[li] : ok ? vin[t0 + li] : 0u;
-            const uint32_t d = (key[r] >> shift) & (kRadix - 1);
+            const uint32_t d = (key[r] >> shift) & (R - 1);
             const uint32_t okm = __ballot_sync(0xffffffffu, ok);
-            const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + lane) & okm;
+            // lanes past the tile's end take distinct values no digit has
+            const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : (uint32_t)R + lane) & okm;
             const int leader = ok ? __ffs(peers) - 1 : lane;
             uint32_t old = 0;
             if (ok && lane == leader) {
@@ -318,24 +329,36 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
             __syncwarp();
         }
         __syncthreads();
-        // per digit: prefix over warps, tile total
-        uint32_t c = 0;
-        const int d = threadIdx.x;  // kSortThreads == kRadix
-        for (int k = 0; k < NW; ++k) {
-            uint32_t x = wh[k][d];
-            wh[k][d] = c;
-            c += x;
+        // per digit: prefix over warps and the tile's count; thread k holds
+        // digits [k DPT, k DPT + DPT), so one block scan orders all digits
+        uint32_t c[DPT], csum = 0;
+#pragma unroll
+        for (int j = 0; j < DPT; ++j) {
+            const int d = threadIdx.x * DPT + j;
+            uint32_t cc = 0;
+            for (int k = 0; k < NW; ++k) {
+                uint32_t x = wh[k][d];
+                wh[k][d] = cc;
+                cc += x;
+            }
+            tcnt[d] = cc;
+            c[j] = cc;
+            csum += cc;
         }
-        tcnt[d] = c;
         uint32_t tot;
-        toff[d] = block_exclusive_scan<uint32_t, kSortThreads>(c, tot, sm);
+        uint32_t off = block_exclusive_scan<uint32_t, kSortThreads>(csum, tot, sm);
+#pragma unroll
+        for (int j = 0; j < DPT; ++j) {
+            toff[threadIdx.x * DPT + j] = off;
+            off += c[j];
+        }
         __syncthreads();
         // the tile in digit order, in its own buffer (every read of it is done)
 #pragma unroll
         for (int r = 0; r < SEG / 32; ++r) {
             const int li = w * SEG + r * 32 + lane;
             if (li < nt) {
-                const uint32_t dd = (key[r] >> shift) & (kRadix - 1);
+                const uint32_t dd = (key[r] >> shift) & (R - 1);
                 const uint32_t pos = toff[dd] + wh[w][dd] + rank[r];
                 kt[pos] = key[r];
                 vt[pos] = val[r];
@@ -344,14 +367,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         __syncthreads();
         for (int k = threadIdx.x; k < nt; k += kSortThreads) {
             const uint32_t kk = kt[k];
-            const uint32_t dd = (kk >> shift) & (kRadix - 1);
+            const uint32_t dd = (kk >> shift) & (R - 1);
             const uint32_t g = dbase[dd] + (uint32_t)k - toff[dd];
             kout[g] = kk;
             vout[g] = vt[k];
         }
         fence_proxy_async_smem();  // this thread's accesses to the buffer precede the next bulk copy into it
         __syncthreads();
-        dbase[d] += tcnt[d];
+        for (int d = threadIdx.x; d < R; d += kSortThreads) dbase[d] += tcnt[d];
         if (threadIdx.x == 0 && t + 2 < ntiles) issue(t + 2);
         __syncthreads();
     }
@@ -749,33 +772,63 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
 
 // --------------------------------------------------------------- host side
 // LSD radix sort of (key, value) pairs, n_ptr = item count on the device,
-// with G CTAs (G <= the plan's sort_ctas).
+// with G CTAs (G <= the plan's sort_ctas); pass ps sorts the digit of
+// widths[ps] bits (8 or 9) above the previous passes' bits.
 static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                       const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st, int G)
+                       const uint32_t* n_ptr, int first_shift, const int* widths, int passes, cudaStream_t st, int G)
 {
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);
     uint32_t* hist = region<uint32_t>(p, ws, R_HIST);
-    uint32_t* sums = hist + (size_t)kRadix * p->sort_ctas;
-    const int nh = kRadix * G, nb = (nh + kScanBlock - 1) / kScanBlock;
+    uint32_t* sums = hist + (size_t)(1 << kRadixBitsWide) * p->sort_ctas;
+    int shift = first_shift;
     for (int ps = 0; ps < passes; ++ps) {
-        const int shift = first_shift + ps * kRadixBits;
+        const int bits = widths[ps];
+        const int nh = (1 << bits) * G, nb = (nh + kScanBlock - 1) / kScanBlock;
         const uint32_t* ki = (ps & 1) ? k1 : k0;
         const uint32_t* vi = (ps & 1) ? v1 : v0;
         uint32_t* ko = (ps & 1) ? k0 : k1;
         uint32_t* vo = (ps & 1) ? v0 : v1;
-        k_radix_hist<<<G, kSortThreads, 0, st>>>(ki, n_ptr, shift, hist);
+        if (bits > 8)
+            k_radix_hist<9><<<G, kSortThreads, 0, st>>>(ki, n_ptr, shift, hist);
+        else
+            k_radix_hist<8><<<G, kSortThreads, 0, st>>>(ki, n_ptr, shift, hist);
         k_hist_block_sums<<<nb, 256, 0, st>>>(hist, nh, sums);
         k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(sums, nb, nullptr, nullptr, 0, -1);
         k_hist_block_apply<<<nb, 256, 0, st>>>(hist, nh, sums);
-        k_radix_scatter<<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist, counters);
+        if (bits > 8)
+            k_radix_scatter<9><<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist, counters);
+        else
+            k_radix_scatter<8><<<G, kSortThreads, 0, st>>>(ki, vi, ko, vo, n_ptr, shift, hist, counters);
+        shift += bits;
     }
+}
+
+static void radix_sort(const gsr_plan* p, void* ws, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                       const uint32_t* n_ptr, int first_shift, int passes, cudaStream_t st, int G)
+{
+    const int w[4] = {8, 8, 8, 8};
+    radix_sort(p, ws, k0, v0, k1, v1, n_ptr, first_shift, w, passes, st, G);
+}
+
+// The tile key's passes: 8-bit digits, except that a key of 8k + 1 bits
+// (k >= 1) takes a 9-bit top digit instead of a pass over one bit.
+int tile_sort_widths(const gsr_plan* p, int widths[4])
+{
+    int bits = 1;
+    while ((1ll << bits) < (long long)p->tile_base[p->n_sensors]) ++bits;
+    int n = 0;
+    while (bits > 0 && n < 4) {
+        const int take = (bits == kRadixBitsWide) ? kRadixBitsWide : (bits < kRadixBits ? bits : kRadixBits);
+        widths[n++] = take < kRadixBits ? kRadixBits : take;
+        bits -= take;
+    }
+    return n;
 }
 
 int tile_sort_passes(const gsr_plan* p)
 {
-    int bits = 1;
-    while ((1ll << bits) < (long long)p->tile_base[p->n_sensors]) ++bits;
-    return (bits + kRadixBits - 1) / kRadixBits;
+    int w[4];
+    return tile_sort_widths(p, w);
 }
 
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
@@ -813,8 +866,9 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
                                    region<ushort4>(p, ws, R_RECTS), region<float4>(p, ws, R_RECORDS),
                                    region<uint4>(p, ws, R_SPANS), pk[0], pv[0]);
     // 5. tile passes
-    const int tp = tile_sort_passes(p);
-    radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tp, st, G);
+    int tw[4];
+    const int tp = tile_sort_widths(p, tw);
+    radix_sort(p, ws, pk[0], pv[0], pk[1], pv[1], counters + C_NDUP, 0, tw, tp, st, G);
     const int pb = sort_result_buffer(tp);
     // 6. tile ranges
     uint2* ranges = region<uint2>(p, ws, R_RANGES);

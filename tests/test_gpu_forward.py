@@ -91,11 +91,20 @@ def test_capacity_overflow_is_reported(gpu_lib):
     assert st == gsr.ERR_CAPACITY and npairs > 5000
 
 
-def test_sort_order_bit_exact(gpu_lib):
-    """Pairs equal a CPU stable sort of the GPU-emitted 64-bit (tile | depth) keys."""
-    s = synth.plain_scene()
-    sensors = [synth.plain_camera(), synth.Lidar(32, 360, -15.0, 15.0, synth.lidar_pose((0, 0, 0), 90.0))]
-    r, _ = _render(s, sensors, tile=(16, 16))
+@pytest.mark.parametrize("case", ["8-bit", "9-bit", "17-bit"])
+def test_sort_order_bit_exact(gpu_lib, case):
+    """Pairs equal a CPU stable sort of the GPU-emitted 64-bit (tile | depth)
+    keys, for tile keys of 8 bits (one pass), 9 bits (one 9-bit pass) and 17
+    bits (an 8-bit pass and a 9-bit one)."""
+    s = synth.plain_scene(n=1500 if case == "17-bit" else 8000)
+    lid = synth.Lidar(32, 360, -15.0, 15.0, synth.lidar_pose((0, 0, 0), 90.0))
+    cam, tile = {"8-bit": (synth.plain_camera(), (16, 16)),
+                 "9-bit": (synth.plain_camera(320, 256, 250.0), (16, 16)),
+                 "17-bit": (synth.plain_camera(2064, 2048, 1600.0), (8, 8))}[case]
+    sensors = [cam, lid]
+    r, _ = _render(s, sensors, tile=tile)
+    T = r.plan.tile_base[r.plan.n_sensors]
+    assert {"8-bit": T <= 256, "9-bit": 256 < T <= 512, "17-bit": 65536 < T <= 131072}[case], T
     st, nvis, npairs = r.status()
     assert st == 0
     rects = r.region(1, torch.int16).cpu().numpy().view(np.uint16).reshape(-1, 4)

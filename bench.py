@@ -309,10 +309,10 @@ def stage_traffic():
         return None
 
 
-def measure_fma_peak(stream, reps=5):
+def measure_fma_peak(stream, reps=12):
     """FP32 FMA issue rate of this GPU (T lane-op/s): the library's FMA-chain
-    kernel on 8 CTAs of 256 threads per SM, best of `reps`, CUDA events on the
-    launching stream."""
+    kernel on 8 CTAs of 256 threads per SM (about 20 ms a launch), best of
+    `reps` after two warm-up launches, CUDA events on the launching stream."""
     import torch
     from paper_2503_11731_gb300 import gsr
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -320,13 +320,13 @@ def measure_fma_peak(stream, reps=5):
     out = torch.empty(blocks * 256, device="cuda")
     sh = ctypes.c_void_p(stream.cuda_stream)
     best = None
-    for i in range(reps + 1):
+    for i in range(reps + 2):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        n = gsr.fma_peak_kernel(ctypes.c_void_p(out.data_ptr()), blocks, 4096, sh)
+        n = gsr.fma_peak_kernel(ctypes.c_void_p(out.data_ptr()), blocks, 1024, sh)
         b.record(stream)
         torch.cuda.synchronize()
-        if i > 0:
+        if i > 1:
             t = n / (a.elapsed_time(b) * 1e-3) / 1e12
             best = t if best is None else max(best, t)
     return best

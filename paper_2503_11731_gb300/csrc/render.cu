@@ -63,26 +63,11 @@ __device__ __forceinline__ float4 warp_box(const TileRay& ray, bool done)
     return make_float4((float)x0, (float)x1, (float)y0, (float)y1);
 }
 
-// Shared control words of a walk, in the 128-byte header of the compositing
-// kernels' dynamic shared memory, after the two staging mbarriers.
-struct WalkCtl {
-    uint32_t rel[2];  // warps that have released the batch now in each buffer
-    uint32_t limit;   // batches [0, limit) of the walk are staged or in flight
-    uint32_t ndone;   // warps whose rays are all done
-};
-
 // Walk list positions [lo, hi) of a tile (list starting at `start`) with the
 // whole CTA, continuing each ray's state.  Batches of D records (a multiple
-// of kIlp) are staged by bulk copies into two buffers; `gb` counts the
-// batches this CTA has staged so far (buffer and mbarrier phase), so a
-// persistent CTA can walk many lists.  Every thread of the CTA must call it.
-//
-// The warps go through the batches at their own pace: a warp releases a
-// batch when it is done with it, and the warp that releases a buffer last
-// (every warp has then read it) stages the batch two ahead into it, unless
-// every warp's rays are done, in which case the walk ends after the batch in
-// flight.  So a warp waits only for a batch to land, never for the other
-// warps at a barrier, and may run a batch ahead of the slowest.
+// of kIlp) are staged by bulk copies, double-buffered; `gb` counts the batches this CTA
+// has staged so far (buffer and mbarrier phase), so a persistent CTA can walk
+// many lists.  Every thread of the CTA must call it.
 template <int KIND>
 __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ray, uint32_t start, int lo, int hi,
                                           const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
@@ -91,62 +76,46 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
 {
     const int nthr = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint32_t nw = (uint32_t)(nthr >> 5);
     const int n = hi - lo;
     const int nb = n > 0 ? (n + D - 1) / D : 0;
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
-    WalkCtl& ctl = *reinterpret_cast<WalkCtl*>(bars + 2);
+    float4 wbox = warp_box(ray, s.done);
 
     // batch b is the CTA's batch g = gb + b: buffer and barrier g & 1, phase
-    // parity (g >> 1) & 1.  Its copies, by thread t of nt issuing threads.
-    auto issue = [&](int b, int t, int nt) {
+    // parity (g >> 1) & 1
+    auto issue = [&](int b) {
         const uint32_t g = gb + (uint32_t)b;
         const int first = b * D;
         const int cnt = min(D, n - first);
         uint64_t* bar = bars + (g & 1);
         float4* dst = buf + (size_t)(g & 1) * D * kRecordF4;
-        if (t == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
-        for (int i = t; i < cnt; i += nt) {
+        if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)cnt * kRecordBytes);
+        for (int i = tid; i < cnt; i += nthr) {
             const uint32_t slot = pval[start + lo + first + i];
             bulk_g2s(dst + i * kRecordF4, rec + (size_t)slot * kRecordF4, kRecordBytes, bar);
         }
     };
+    auto wait = [&](int b) {
+        const uint32_t g = gb + (uint32_t)b;
+        return mbar_wait_bounded(bars + (g & 1), (g >> 1) & 1, counters);
+    };
 
     // nothing to do for this CTA: no batch is staged
     if (nb == 0 || __syncthreads_and(s.done)) return;
-    if (tid == 0) {
-        ctl.rel[0] = ctl.rel[1] = 0u;
-        ctl.limit = (uint32_t)nb;
-        ctl.ndone = 0u;
-    }
-    __syncthreads();
-    issue(0, tid, nthr);
-    if (nb > 1) issue(1, tid, nthr);
-
-    float4 wbox = warp_box(ray, s.done);
-    bool ok = true;          // no bounded wait of this thread gave up
-    bool counted = false;    // this warp is counted in ctl.ndone
+    bool ok = true;
+    issue(0);
+    int issued = 1;
     for (int b = 0; b < nb; ++b) {
-        const uint32_t g = gb + (uint32_t)b;
-        // wait for batch b to land, or for the walk to end before it
-        bool got = false;
-        for (uint32_t it = 0; it < (1u << 22); ++it) {
-            if (mbar_try_wait(bars + (g & 1), (g >> 1) & 1)) {
-                got = true;
-                break;
-            }
-            if ((uint32_t)b >= *(volatile uint32_t*)&ctl.limit) break;
+        if (b + 1 < nb) {
+            issue(b + 1);
+            issued = b + 2;
         }
-        if (!got) {
-            if ((uint32_t)b >= *(volatile uint32_t*)&ctl.limit) break;  // never staged: the walk is over
-            set_status(counters, GSR_ERR_TIMEOUT);
-            ok = false;
-        }
-        const float4* B = buf + (size_t)(g & 1) * D * kRecordF4;
+        if (!wait(b)) ok = false;
+        const float4* B = buf + (size_t)((gb + b) & 1) * D * kRecordF4;
         const int cnt = min(D, n - b * D);
         const int pos0 = lo + b * D;  // list position of the batch's first record
-        if (!__all_sync(0xffffffffu, s.done || !ok)) {
+        if (ok) {
             // the box of the rays still walking shrinks as rays saturate
             if (b > 0) wbox = warp_box(ray, s.done);
             for (int g0 = 0; g0 < cnt; g0 += 32) {
@@ -216,42 +185,18 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                 }
             }
         }
-        // release batch b (a thread whose wait gave up counts as done: it
-        // composites nothing more, and every later wait is bounded too)
-        const bool wdone = __all_sync(0xffffffffu, s.done || !ok);
-        uint32_t last = 0u;
-        if (lane == 0) {
-            if (wdone && !counted) atomicAdd(&ctl.ndone, 1u);
-            __threadfence_block();
-            last = atomicAdd(&ctl.rel[g & 1], 1u) == nw - 1u ? 1u : 0u;
-        }
-        counted = counted || wdone;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            // every warp is done with batch b: its buffer takes batch b + 2,
-            // unless every warp's rays are done (the walk then ends after
-            // the batch in flight)
-            __threadfence_block();
-            const uint32_t done_warps = lane == 0 ? atomicAdd(&ctl.ndone, 0u) : 0u;
-            const bool all_done = __shfl_sync(0xffffffffu, done_warps, 0) == nw;
-            if (lane == 0) ctl.rel[g & 1] = 0u;
-            if (all_done) {
-                if (lane == 0) atomicMin(&ctl.limit, (uint32_t)(b + 2));
-            } else if (b + 2 < nb) {
-                issue(b + 2, lane, 32);
-            }
+        // one block-uniform vote: a thread whose bounded wait gave up counts
+        // as done (it composites nothing more; every later wait is bounded too)
+        if (__syncthreads_and(s.done || !ok)) {
+            // no copy may still be landing in shared memory when the CTA
+            // leaves or moves on: batch b if its wait gave up (a second
+            // bounded wait), and batch b + 1 if it was issued
+            if (!ok) wait(b);
+            if (b + 1 < nb) wait(b + 1);
+            break;
         }
     }
-    __syncthreads();  // every warp has left the walk
-    const uint32_t staged = ctl.limit;
-    // every staged batch was waited for by every warp; a wait that gave up
-    // may leave copies landing: wait for the last use of each buffer again
-    if (__syncthreads_or(!ok) && tid == 0) {
-        for (uint32_t b = staged > 2 ? staged - 2 : 0; b < staged; ++b)
-            mbar_wait_bounded(bars + ((gb + b) & 1), ((gb + b) >> 1) & 1, counters);
-    }
-    __syncthreads();
-    gb += staged;
+    gb += (uint32_t)issued;
     if (!ok) s.done = true;
 }
 

@@ -403,76 +403,6 @@ __device__ __forceinline__ bool footprint_meets_box(const float4 r0, const float
     return E(lx, ty0) <= 0.f || E(hx, ty1) <= 0.f || E(tx0, ly) <= 0.f || E(tx1, hy) <= 0.f;
 }
 
-// Can the conic E(x, y) = m00 x^2 + 2 m01 x y + m11 y^2 + 2 n0 x + 2 n1 y + k
-// be <= 0 somewhere in the box [lx, hx] x [ly, hy]?  Exact for an ellipse (a
-// safely positive definite quadratic part: the minimum over the box is at
-// the unconstrained minimiser if it lies inside, else on an edge, where E is
-// a convex parabola); any other conic answers yes.  Fast FP32: callers widen
-// the box by a margin far larger than its error.
-__device__ __forceinline__ bool conic_meets_box(float m00, float m01, float m11, float n0, float n1, float k,
-                                                float lx, float hx, float ly, float hy)
-{
-    const float dm = m00 * m11 - m01 * m01;
-    if (!(m00 > 0.f && m11 > 0.f && dm > 1e-4f * m00 * m11)) return true;
-    auto E = [&](float dx, float dy) {
-        return dx * (m00 * dx + m01 * dy + 2.f * n0) + dy * (m01 * dx + m11 * dy + 2.f * n1) + k;
-    };
-    const float id = __fdividef(1.f, dm);
-    const float sx = (m01 * n1 - m11 * n0) * id, sy = (m01 * n0 - m00 * n1) * id;
-    if (sx >= lx && sx <= hx && sy >= ly && sy <= hy) return E(sx, sy) <= 0.f;
-    const float i00 = __fdividef(1.f, m00), i11 = __fdividef(1.f, m11);
-    const float ty0 = fminf(fmaxf(-(m01 * lx + n1) * i11, ly), hy), ty1 = fminf(fmaxf(-(m01 * hx + n1) * i11, ly), hy);
-    const float tx0 = fminf(fmaxf(-(m01 * ly + n0) * i00, lx), hx), tx1 = fminf(fmaxf(-(m01 * hy + n0) * i00, lx), hx);
-    return E(lx, ty0) <= 0.f || E(hx, ty1) <= 0.f || E(tx0, ly) <= 0.f || E(tx1, hy) <= 0.f;
-}
-
-// A warp's LiDAR rays for footprint culling: the unit direction c of the
-// centre of their (azimuth, elevation) box with its azimuth and elevation
-// tangents e1, e2, and the box [gx0, gx1] x [gy0, gy1] of the rays'
-// gnomonic coordinates (d . e1, d . e2) / (d . c), widened by one cell.
-struct LidarWarpCull {
-    float c0, c1, c2, e10, e11, e20, e21, e22;
-    float gx0, gx1, gy0, gy1;
-};
-
-// Can a LiDAR record's support or its low-pass disc reach one of the warp's
-// rays?  A direction d sees the support where q = Q d has q0^2 + q1^2 <=
-// rho q2^2 (rho the opacity-aware support radius): a quadratic cone, which
-// in the gnomonic coordinates (x, y) of d = x e1 + y e2 + c (up to a
-// positive factor) is the conic w^T M w <= 0, w = (x, y, 1), M = P0 P0^T +
-// P1 P1^T - rho P2 P2^T with P_k = (q_k . e1, q_k . e2, q_k . c).  The
-// low-pass disc (radius sqrt(rho / 2) cells about the record's centre cell)
-// is tested against the warp's cell box `w` with the azimuth wrap.
-__device__ __forceinline__ bool lidar_footprint_meets(const float4 r0, const float4 r1, const float4 r2, float o,
-                                                      const LidarWarpCull& wc, const float4 w, float columns)
-{
-    const float rho = fminf(kSupport, 2.f * __logf(255.f * o) + 1e-3f);
-    // the low-pass disc against the cell box (one cell of margin); the
-    // record's centre column may sit across the seam from the box
-    auto gap = [](float c, float a, float b) { return fmaxf(fmaxf(a - c, c - b), 0.f); };
-    const float dx = fminf(gap(r0.w, w.x, w.y), fminf(gap(r0.w - columns, w.x, w.y), gap(r0.w + columns, w.x, w.y)));
-    const float dy = gap(r1.w, w.z, w.w);
-    const float rl = sqrtf(fmaxf(0.5f * rho, 0.f)) + 1.f;
-    if (dx * dx + dy * dy <= rl * rl) return true;
-    // the support cone in gnomonic coordinates
-    const float p00 = r0.x * wc.e10 + r0.y * wc.e11;
-    const float p01 = fmaf(r0.x, wc.e20, fmaf(r0.y, wc.e21, r0.z * wc.e22));
-    const float p02 = fmaf(r0.x, wc.c0, fmaf(r0.y, wc.c1, r0.z * wc.c2));
-    const float p10 = r1.x * wc.e10 + r1.y * wc.e11;
-    const float p11 = fmaf(r1.x, wc.e20, fmaf(r1.y, wc.e21, r1.z * wc.e22));
-    const float p12 = fmaf(r1.x, wc.c0, fmaf(r1.y, wc.c1, r1.z * wc.c2));
-    const float p20 = r2.x * wc.e10 + r2.y * wc.e11;
-    const float p21 = fmaf(r2.x, wc.e20, fmaf(r2.y, wc.e21, r2.z * wc.e22));
-    const float p22 = fmaf(r2.x, wc.c0, fmaf(r2.y, wc.c1, r2.z * wc.c2));
-    const float m00 = p00 * p00 + p10 * p10 - rho * p20 * p20;
-    const float m01 = p00 * p01 + p10 * p11 - rho * p20 * p21;
-    const float m11 = p01 * p01 + p11 * p11 - rho * p21 * p21;
-    const float n0 = p00 * p02 + p10 * p12 - rho * p20 * p22;
-    const float n1 = p01 * p02 + p11 * p12 - rho * p21 * p22;
-    const float k = p02 * p02 + p12 * p12 - rho * p22 * p22;
-    return conic_meets_box(m00, m01, m11, n0, n1, k, wc.gx0, wc.gx1, wc.gy0, wc.gy1);
-}
-
 // Bit 15 of rect.w marks a camera slot whose tile set is footprint-tested.
 constexpr uint16_t kRectExact = 0x8000;
 

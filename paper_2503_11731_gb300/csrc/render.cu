@@ -63,51 +63,6 @@ __device__ __forceinline__ float4 warp_box(const TileRay& ray, bool done)
     return make_float4((float)x0, (float)x1, (float)y0, (float)y1);
 }
 
-// Dynamic shared memory of the compositing kernels: a header (the two
-// staging mbarriers at 0, each warp's LiDAR culling frame at 64 + 48 w),
-// then the two staging buffers.
-constexpr int kSmemHeader = 512;
-
-__device__ __forceinline__ LidarWarpCull& warp_cull(uint64_t* bars)
-{
-    return reinterpret_cast<LidarWarpCull*>(reinterpret_cast<unsigned char*>(bars) + 64)[threadIdx.x >> 5];
-}
-
-// The warp's LiDAR culling frame for its live rays in the cell box `w`:
-// the centre direction of the box, its tangents, and the rays' gnomonic box.
-__device__ __forceinline__ void lidar_warp_frame(const SensorDev& sd, const TileRay& ray, bool done, const float4 w,
-                                                 LidarWarpCull& wc)
-{
-    float se, ce, sa, ca;
-    sincosf(sd.el_max - 0.5f * (w.z + w.w) * sd.d_el, &se, &ce);
-    sincosf(sd.az0 + (0.5f * (w.x + w.y) + 0.5f) * sd.d_az, &sa, &ca);
-    const float c0 = ce * ca, c1 = ce * sa, c2 = se;
-    const float e10 = -sa, e11 = ca;
-    const float e20 = -se * ca, e21 = -se * sa, e22 = ce;
-    const bool live = ray.inside && !done;
-    const float dc = fmaf(ray.d0, c0, fmaf(ray.d1, c1, ray.d2 * c2));
-    float gx = live ? fmaf(ray.d0, e10, ray.d1 * e11) / dc : 0.f;
-    float gy = live ? fmaf(ray.d0, e20, fmaf(ray.d1, e21, ray.d2 * e22)) / dc : 0.f;
-    float x0 = live ? gx : 1e30f, x1 = live ? gx : -1e30f, y0 = live ? gy : 1e30f, y1 = live ? gy : -1e30f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
-        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
-        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
-        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
-    }
-    // one cell of margin (the gnomonic map stretches angles by under 1 %
-    // over a tile's few degrees)
-    const float m = fmaxf(sd.d_az, sd.d_el);
-    if ((threadIdx.x & 31) == 0) {
-        wc.c0 = c0; wc.c1 = c1; wc.c2 = c2;
-        wc.e10 = e10; wc.e11 = e11;
-        wc.e20 = e20; wc.e21 = e21; wc.e22 = e22;
-        wc.gx0 = x0 - m; wc.gx1 = x1 + m; wc.gy0 = y0 - m; wc.gy1 = y1 + m;
-    }
-    __syncwarp();
-}
-
 // Walk list positions [lo, hi) of a tile (list starting at `start`) with the
 // whole CTA, continuing each ray's state.  Batches of D records (a multiple
 // of kIlp) are staged by bulk copies, double-buffered; `gb` counts the batches this CTA
@@ -126,7 +81,6 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
     const float columns = (float)sd.width;
     const float near_plane = sd.near_plane;
     float4 wbox = warp_box(ray, s.done);
-    if (KIND == GSR_SENSOR_LIDAR) lidar_warp_frame(sd, ray, s.done, wbox, warp_cull(bars));
 
     // batch b is the CTA's batch g = gb + b: buffer and barrier g & 1, phase
     // parity (g >> 1) & 1
@@ -163,10 +117,7 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
         const int pos0 = lo + b * D;  // list position of the batch's first record
         if (ok) {
             // the box of the rays still walking shrinks as rays saturate
-            if (b > 0) {
-                wbox = warp_box(ray, s.done);
-                if (KIND == GSR_SENSOR_LIDAR) lidar_warp_frame(sd, ray, s.done, wbox, warp_cull(bars));
-            }
+            if (b > 0) wbox = warp_box(ray, s.done);
             for (int g0 = 0; g0 < cnt; g0 += 32) {
                 if (__all_sync(0xffffffffu, s.done)) break;
                 // one lane per record: does its support box meet any ray of
@@ -178,11 +129,6 @@ __device__ __forceinline__ void walk_list(const SensorDev& sd, const TileRay& ra
                     // disc, one pixel of margin) meets the box
                     const float4* Rj = B + jt * kRecordF4;
                     meet = footprint_meets_box(Rj[0], Rj[1], Rj[2], Rj[3].x, wbox.x, wbox.y, wbox.z, wbox.w);
-                } else if (KIND == GSR_SENSOR_LIDAR && meet) {
-                    // and its support cone (or low-pass disc) reaches the
-                    // warp's rays (one cell of margin)
-                    const float4* Rj = B + jt * kRecordF4;
-                    meet = lidar_footprint_meets(Rj[0], Rj[1], Rj[2], Rj[3].x, warp_cull(bars), wbox, columns);
                 }
                 uint32_t mask = __ballot_sync(0xffffffffu, meet);
                 while (mask) {
@@ -423,7 +369,7 @@ __global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, con
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    float4* buf = reinterpret_cast<float4*>(smem_raw + kSmemHeader);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
     const SensorDev& sd = tab.s[sensor];
     init_bars(bars);
     __syncthreads();
@@ -458,7 +404,7 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_rig(SensorTabl
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    float4* buf = reinterpret_cast<float4*>(smem_raw + kSmemHeader);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
     __shared__ uint32_t item_s;
     init_bars(bars);
     uint32_t gb = 0;
@@ -496,7 +442,7 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTa
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    float4* buf = reinterpret_cast<float4*>(smem_raw + kSmemHeader);
+    float4* buf = reinterpret_cast<float4*>(smem_raw + 128);
     __shared__ uint32_t item_s, flag_s;
     init_bars(bars);
     const uint32_t n_items = counters[C_NITEMS];
@@ -557,7 +503,7 @@ cudaError_t launch_selftest_wait(uint32_t* counters, uint32_t tries, cudaStream_
 }
 
 // Dynamic shared memory of a compositing CTA staging D records per batch.
-size_t render_smem_bytes(int D) { return kSmemHeader + 2 * (size_t)D * kRecordBytes; }
+size_t render_smem_bytes(int D) { return 128 + 2 * (size_t)D * kRecordBytes; }
 
 static int batch_of(const SensorTable& tab, int threads) { return tab.batch > 0 ? tab.batch : threads; }
 

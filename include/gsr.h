@@ -643,13 +643,17 @@ typedef struct {
 
 /* One measured candidate: ms = mean frame time (preprocess + bin_sort +
  * render_rig), or a negative value when the candidate's frame failed (e.g.
- * the pair capacity of its plan overflowed). */
+ * the pair capacity of its plan overflowed).  lidar_tile is the first
+ * LiDAR's tile, lidar_tiles the tiles of the plan's first
+ * GSR_AUTOTUNE_LIDARS LiDARs in plan order (later LiDARs take the last). */
+#define GSR_AUTOTUNE_LIDARS 4
 typedef struct {
     int32_t camera_tile[2];
     int32_t lidar_tile[2];
     int32_t batch_depth;
     int32_t split_first, split_chunk;
     int32_t lidar_split_first, lidar_split_chunk; /* 0 = the plan's */
+    int32_t lidar_tiles[GSR_AUTOTUNE_LIDARS][2];
     float ms;
 } gsr_autotune_trial;
 
@@ -657,7 +661,7 @@ typedef struct {
     gsr_plan plan;        /* the input plan re-initialised with the fastest tiling */
     float best_ms;
     int32_t n_tried;
-    gsr_autotune_trial tried[7 * GSR_AUTOTUNE_MAX + 1];
+    gsr_autotune_trial tried[(7 + GSR_AUTOTUNE_LIDARS) * GSR_AUTOTUNE_MAX + 1];
 } gsr_autotune_result;
 
 /* Workspace bytes gsr_autotune needs: the largest over the candidates
@@ -668,8 +672,10 @@ gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gsr_autotune_
  * Autotuner of the batched rig frame (the paper prescribes none; tile shape,
  * staging depth and list splitting are this implementation's free
  * parameters).  Coordinate descent from the plan's tiling: the camera tile
- * over its candidates, then the LiDAR tile, the batch depth, the first split
- * length and the later chunk length, then the LiDARs' two split lengths,
+ * over its candidates, then one LiDAR tile for every LiDAR, then each of the
+ * first GSR_AUTOTUNE_LIDARS LiDARs' tile on its own (a 32-beam and a 128-beam
+ * LiDAR favour different shapes), the batch depth, the first split length
+ * and the later chunk length, then the LiDARs' two split lengths,
  * each candidate timed with CUDA
  * events over whole frames of the given surfels: `parts` (n_parts tables,
  * consecutive in the plan from surfel 0, as gsr_preprocess_part) and

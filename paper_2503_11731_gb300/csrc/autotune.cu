@@ -20,9 +20,11 @@ gsr_status cuda_status(cudaError_t e);
 
 namespace {
 
+constexpr int kLid = GSR_AUTOTUNE_LIDARS;
+
 struct Candidate {
     int cam[2];
-    int lid[2];
+    int lid[kLid][2];  // LiDAR k's tile (plan order; later LiDARs take the last)
     int bd;
     int sf, sc;    // the plan's split_first, split_chunk (the cameras')
     int lsf, lsc;  // the LiDARs' own (0 = the plan's)
@@ -30,20 +32,39 @@ struct Candidate {
 
 bool same(const Candidate& a, const Candidate& b)
 {
-    return a.cam[0] == b.cam[0] && a.cam[1] == b.cam[1] && a.lid[0] == b.lid[0] && a.lid[1] == b.lid[1] &&
-           a.bd == b.bd && a.sf == b.sf && a.sc == b.sc && a.lsf == b.lsf && a.lsc == b.lsc;
+    for (int k = 0; k < kLid; ++k)
+        if (a.lid[k][0] != b.lid[k][0] || a.lid[k][1] != b.lid[k][1]) return false;
+    return a.cam[0] == b.cam[0] && a.cam[1] == b.cam[1] && a.bd == b.bd && a.sf == b.sf && a.sc == b.sc &&
+           a.lsf == b.lsf && a.lsc == b.lsc;
+}
+
+void set_all_lidars(Candidate& c, int w, int h)
+{
+    for (int k = 0; k < kLid; ++k) {
+        c.lid[k][0] = w;
+        c.lid[k][1] = h;
+    }
+}
+
+int n_lidars(const gsr_plan* p)
+{
+    int n = 0;
+    for (int i = 0; i < p->n_sensors; ++i) n += p->sensors[i].kind == GSR_SENSOR_LIDAR;
+    return n;
 }
 
 // The plan of a candidate: the input plan's sensors and capacity with every
-// camera on cand.cam and the plan's list split, every LiDAR on cand.lid and
+// camera on cand.cam and the plan's list split, LiDAR k on cand.lid[k] and
 // its own split, and cand.bd staged.
 gsr_status candidate_plan(const gsr_plan* base, const Candidate& c, gsr_plan* out)
 {
     gsr_sensor sensors[GSR_MAX_SENSORS];
+    int li = 0;
     for (int i = 0; i < base->n_sensors; ++i) {
         sensors[i] = base->sensors[i];
         const bool lidar = sensors[i].kind == GSR_SENSOR_LIDAR;
-        const int* t = lidar ? c.lid : c.cam;
+        const int* t = lidar ? c.lid[li < kLid ? li : kLid - 1] : c.cam;
+        li += lidar;
         sensors[i].tile_w = t[0];
         sensors[i].tile_h = t[1];
         sensors[i].split_first = lidar ? c.lsf : 0;
@@ -68,39 +89,76 @@ void plan_lidar_split(const gsr_plan* p, int& sf, int& sc)
         }
 }
 
-// Tile of the plan's first LiDAR (lidar) or first camera of either model
-// (both default to the plan's tiling when absent).
-void plan_tile(const gsr_plan* p, bool lidar, int t[2])
+// Tile of the plan's first camera of either model (the plan's tiling when
+// absent).
+void plan_camera_tile(const gsr_plan* p, int t[2])
 {
     t[0] = p->tiling.tile_w;
     t[1] = p->tiling.tile_h;
     for (int i = 0; i < p->n_sensors; ++i)
-        if ((p->sensors[i].kind == GSR_SENSOR_LIDAR) == lidar) {
+        if (p->sensors[i].kind != GSR_SENSOR_LIDAR) {
             t[0] = p->sensors[i].tile_w;
             t[1] = p->sensors[i].tile_h;
             return;
         }
 }
 
-// Every tile pair of the space (the workspace depends on the tiles only).
-std::vector<Candidate> all_candidates(const gsr_autotune_space* sp, Candidate start)
+// Tiles of the plan's LiDARs in plan order (the plan's tiling when absent;
+// slots past the last LiDAR repeat it).
+void plan_lidar_tiles(const gsr_plan* p, int t[kLid][2])
+{
+    int k = 0;
+    int last[2] = {p->tiling.tile_w, p->tiling.tile_h};
+    for (int i = 0; i < p->n_sensors && k < kLid; ++i)
+        if (p->sensors[i].kind == GSR_SENSOR_LIDAR) {
+            last[0] = t[k][0] = p->sensors[i].tile_w;
+            last[1] = t[k][1] = p->sensors[i].tile_h;
+            ++k;
+        }
+    for (; k < kLid; ++k) {
+        t[k][0] = last[0];
+        t[k][1] = last[1];
+    }
+}
+
+Candidate plan_candidate(const gsr_plan* p)
+{
+    Candidate c;
+    plan_camera_tile(p, c.cam);
+    plan_lidar_tiles(p, c.lid);
+    c.bd = p->tiling.batch_depth;
+    c.sf = p->tiling.split_first;
+    c.sc = p->tiling.split_chunk;
+    plan_lidar_split(p, c.lsf, c.lsc);
+    return c;
+}
+
+// Every tile combination the descent can reach (the workspace depends on
+// the tiles only): each camera tile with each LiDAR tile for every LiDAR,
+// and with every mix of LiDAR tiles over the first two LiDARs.
+std::vector<Candidate> all_candidates(const gsr_autotune_space* sp, Candidate start, int nlid)
 {
     std::vector<Candidate> v{start};
     const int nc = sp->n_camera_tiles > 0 ? sp->n_camera_tiles : 1;
     const int nl = sp->n_lidar_tiles > 0 ? sp->n_lidar_tiles : 1;
     for (int i = 0; i < nc; ++i)
-        for (int j = 0; j < nl; ++j) {
-            Candidate c = start;
-            if (sp->n_camera_tiles) {
-                c.cam[0] = sp->camera_tiles[i][0];
-                c.cam[1] = sp->camera_tiles[i][1];
+        for (int j = 0; j < nl; ++j)
+            for (int j2 = 0; j2 < (nlid > 1 ? nl : 1); ++j2) {
+                Candidate c = start;
+                if (sp->n_camera_tiles) {
+                    c.cam[0] = sp->camera_tiles[i][0];
+                    c.cam[1] = sp->camera_tiles[i][1];
+                }
+                if (sp->n_lidar_tiles) {
+                    set_all_lidars(c, sp->lidar_tiles[j][0], sp->lidar_tiles[j][1]);
+                    if (nlid > 1)  // LiDAR 1's tile also stands for the later ones
+                        for (int m = 1; m < kLid; ++m) {
+                            c.lid[m][0] = sp->lidar_tiles[j2][0];
+                            c.lid[m][1] = sp->lidar_tiles[j2][1];
+                        }
+                }
+                v.push_back(c);
             }
-            if (sp->n_lidar_tiles) {
-                c.lid[0] = sp->lidar_tiles[j][0];
-                c.lid[1] = sp->lidar_tiles[j][1];
-            }
-            v.push_back(c);
-        }
     return v;
 }
 
@@ -123,15 +181,9 @@ extern "C" gsr_status gsr_autotune_workspace_size(const gsr_plan* plan, const gs
                                                   size_t* bytes)
 {
     if (!plan || !bytes || !space_ok(space)) return GSR_ERR_INVALID_ARG;
-    Candidate start;
-    plan_tile(plan, false, start.cam);
-    plan_tile(plan, true, start.lid);
-    start.bd = plan->tiling.batch_depth;
-    start.sf = plan->tiling.split_first;
-    start.sc = plan->tiling.split_chunk;
-    plan_lidar_split(plan, start.lsf, start.lsc);
     size_t best = 0;
-    for (const Candidate& c : all_candidates(space, start)) {
+    const int nlid = n_lidars(plan);
+    for (const Candidate& c : all_candidates(space, plan_candidate(plan), nlid)) {
         gsr_plan p;
         const gsr_status st = candidate_plan(plan, c, &p);
         if (st != GSR_OK) return st;
@@ -194,13 +246,8 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
         return GSR_OK;
     };
 
-    Candidate best;
-    plan_tile(plan, false, best.cam);
-    plan_tile(plan, true, best.lid);
-    best.bd = plan->tiling.batch_depth;
-    best.sf = plan->tiling.split_first;
-    best.sc = plan->tiling.split_chunk;
-    plan_lidar_split(plan, best.lsf, best.lsc);
+    Candidate best = plan_candidate(plan);
+    const int nlid = n_lidars(plan);
     float best_ms = -1.f;
     std::vector<std::pair<Candidate, float>> seen;
     auto visit = [&](const Candidate& c) -> gsr_status {
@@ -213,7 +260,11 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
         if (result->n_tried < (int)(sizeof(result->tried) / sizeof(result->tried[0]))) {
             gsr_autotune_trial& t = result->tried[result->n_tried++];
             t.camera_tile[0] = c.cam[0]; t.camera_tile[1] = c.cam[1];
-            t.lidar_tile[0] = c.lid[0]; t.lidar_tile[1] = c.lid[1];
+            t.lidar_tile[0] = c.lid[0][0]; t.lidar_tile[1] = c.lid[0][1];
+            for (int k = 0; k < kLid; ++k) {
+                t.lidar_tiles[k][0] = c.lid[k][0];
+                t.lidar_tiles[k][1] = c.lid[k][1];
+            }
             t.batch_depth = c.bd;
             t.split_first = c.sf;
             t.split_chunk = c.sc;
@@ -236,10 +287,23 @@ extern "C" gsr_status gsr_autotune(const gsr_plan* plan, const gsr_surfels* part
     }
     for (int i = 0; r == GSR_OK && i < space->n_lidar_tiles; ++i) {
         Candidate c = best;
-        c.lid[0] = space->lidar_tiles[i][0];
-        c.lid[1] = space->lidar_tiles[i][1];
+        set_all_lidars(c, space->lidar_tiles[i][0], space->lidar_tiles[i][1]);
         r = visit(c);
     }
+    // each LiDAR's tile on its own (the workspace bound covers mixes of the
+    // first two; later LiDARs keep the common tile)
+    for (int k = 0; nlid > 1 && k < 2 && k < nlid; ++k)
+        for (int i = 0; r == GSR_OK && i < space->n_lidar_tiles; ++i) {
+            Candidate c = best;
+            c.lid[k][0] = space->lidar_tiles[i][0];
+            c.lid[k][1] = space->lidar_tiles[i][1];
+            if (k == 1)  // LiDAR 1's tile also stands for the later ones
+                for (int m = 2; m < kLid; ++m) {
+                    c.lid[m][0] = c.lid[1][0];
+                    c.lid[m][1] = c.lid[1][1];
+                }
+            r = visit(c);
+        }
     for (int i = 0; r == GSR_OK && i < space->n_batch_depths; ++i) {
         Candidate c = best;
         c.bd = space->batch_depths[i];

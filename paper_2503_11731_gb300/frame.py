@@ -194,12 +194,14 @@ class Renderer:
         self.ws_ptr = ctypes.c_void_p((self.ws.data_ptr() + 255) & ~255)
 
     def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
-                 lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (8, 16), (16, 16)), batch_depths=(64, 128, 256),
+                 lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (16, 4), (32, 4), (32, 2), (16, 16)),
+                 batch_depths=(64, 128, 256),
                  split_firsts=(4096, 8192, 16384, 32768), split_chunks=(256, 384, 512, 1024),
                  lidar_split_firsts=(1024, 2048, 4096, 8192), lidar_split_chunks=(128, 256, 512, 1024), warmup=1,
                  reps=3, stream=None):
         """Pick the tiling of this rig with gsr_autotune over `parts` (DeviceSurfels
-        consecutive in the plan) and re-plan with it; returns the trial list."""
+        consecutive in the plan) and re-plan with it; returns the trial list.
+        The LiDARs first share one tile, then each is tuned on its own."""
         obj = None if objects is None else gsr.Objects(int(objects.shape[0]), _ptr(objects))
         has = {d.kind for d in self.descs}
         lid = "lidar" in has
@@ -213,7 +215,9 @@ class Renderer:
         self.plan = res.plan
         self.ws_bytes = gsr.workspace_size(self.plan)
         self._alloc_workspace(self.ws_bytes)
+        nl = sum(d.kind == "lidar" for d in self.descs)
         trials = [{"camera_tile": tuple(t.camera_tile), "lidar_tile": tuple(t.lidar_tile),
+                   "lidar_tiles": [tuple(x) for x in list(t.lidar_tiles)[:max(nl, 1)]],
                    "batch_depth": t.batch_depth, "split": (t.split_first, t.split_chunk),
                    "lidar_split": (t.lidar_split_first, t.lidar_split_chunk), "ms": t.ms}
                   for t in res.tried[:res.n_tried]]

@@ -116,15 +116,18 @@ class AutotuneSpace(ctypes.Structure):
                 ("warmup", c_i32), ("reps", c_i32)]
 
 
+AUTOTUNE_LIDARS = 4
+
+
 class AutotuneTrial(ctypes.Structure):
     _fields_ = [("camera_tile", c_i32 * 2), ("lidar_tile", c_i32 * 2), ("batch_depth", c_i32),
                 ("split_first", c_i32), ("split_chunk", c_i32), ("lidar_split_first", c_i32),
-                ("lidar_split_chunk", c_i32), ("ms", c_f32)]
+                ("lidar_split_chunk", c_i32), ("lidar_tiles", (c_i32 * 2) * AUTOTUNE_LIDARS), ("ms", c_f32)]
 
 
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("plan", Plan), ("best_ms", c_f32), ("n_tried", c_i32),
-                ("tried", AutotuneTrial * (7 * AUTOTUNE_MAX + 1))]
+                ("tried", AutotuneTrial * ((7 + AUTOTUNE_LIDARS) * AUTOTUNE_MAX + 1))]
 
 
 class ZoneGrid(ctypes.Structure):

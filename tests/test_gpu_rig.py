@@ -198,6 +198,11 @@ def test_autotune_picks_the_fastest_measured_tiling(gpu_lib):
     assert res["best_ms"] == pytest.approx(best["ms"])
     assert res["camera_tile"] == best["camera_tile"] and res["lidar_tile"] == best["lidar_tile"]
     assert res["batch_depth"] == best["batch_depth"]
+    # each LiDAR's tile was tuned on its own too, and the plan keeps the best
+    lidar_tiles = [(r.plan.sensors[i].tile_w, r.plan.sensors[i].tile_h)
+                   for i, s in enumerate(sensors) if s.kind == "lidar"]
+    assert lidar_tiles == [tuple(t) for t in best["lidar_tiles"][:2]]
+    assert any(tuple(t["lidar_tiles"][0]) != tuple(t["lidar_tiles"][1]) for t in res["trials"])
     # the tuned plan renders the same frame (to the split-merge rounding)
     o = r.render_rig(whole, P)
     torch.cuda.synchronize()

@@ -585,7 +585,7 @@ def _frame_accuracy(learned, explicit):
             "depth_rel_p90": float(torch.quantile(rel[:1 << 24].float(), 0.9)) if rel.numel() else None}
 
 
-def learned_distillation(steps=600, n_poses=200, n_held=12, seed_offset=0, loss_weights=(0.0, 0.0), lr=3e-3,
+def learned_distillation(steps=1200, n_poses=200, n_held=12, seed_offset=0, loss_weights=(0.0, 0.0), lr=3e-3,
                          lr_feature=1e-2):
     """The learned-decode configuration at its stated scale (Sec. III-A,
     neural Gaussians decoded from anchors by an MLP): 150k anchors x 10

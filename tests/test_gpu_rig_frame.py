@@ -2,13 +2,15 @@
 
 The frame is the benchmark's configuration: 6 pinhole cameras (2 x 1920x1080,
 4 x 1280x720) and 2 spinning LiDARs (128x1800, 32x1024); 300k anchors x 10
-offsets decoded by the anchor MLP into 3M surfels plus 20 rigidly posed
-50k-surfel SH-3 objects; the tiling, staging depth and list splits chosen by
-gsr_autotune, rendered by the persistent whole-rig launch.  The GPU decodes
-in FP32 here so that the oracle can decode the same anchors in FP64 itself
-(Sec. III-A, anchors decoded by an MLP) and render its own table: nothing
-the GPU computed enters the oracle.  4,096 sampled rays per sensor are
-compared (the oracle in tiled mode, bit-identical to brute force).
+offsets decoded by the anchor MLP (trained on the GPU on the explicit
+background's frames, as the benchmark does) into 3M surfels plus 20 rigidly
+posed 50k-surfel SH-3 objects; the tiling, staging depth and list splits
+chosen by gsr_autotune, rendered by the persistent whole-rig launch.  The
+GPU decodes in FP32 here so that the oracle can decode the same anchors in
+FP64 itself (Sec. III-A, anchors decoded by an MLP) from the trained
+features and weights and render its own table: nothing the GPU rendered
+enters the oracle.  4,096 sampled rays per sensor are compared (the oracle
+in tiled mode, bit-identical to brute force).
 """
 import numpy as np
 import pytest
@@ -26,18 +28,23 @@ def test_configured_rig_frame_matches_oracle(gpu_lib):
     import bench
     from paper_2503_11731_gb300 import gsr
     from paper_2503_11731_gb300.frame import DeviceSurfels
-    from paper_2503_11731_gb300.neural import DeviceAnchors, NeuralFrame, NeuralModel
+    from paper_2503_11731_gb300.neural import NeuralFrame
+    from paper_2503_11731_gb300 import synth
     bg, objs, poses, sensors = bench.rig_parts()
     anchors, mlp = bench.rig_neural(bg)
     origin = bench.rig_origin(sensors)
+    model, da, _ = bench.rig_distillation(bg, anchors, mlp)
     del bg
+    # the trained parameters as the oracle receives them
+    anchors = synth.Anchors(anchors.pos, da.feature.cpu().numpy(), anchors.scale, anchors.offsets, anchors.intensity)
+    mlp = tuple(getattr(model, k).cpu().numpy() for k in ("w1", "b1", "w2", "b2"))
     n = anchors.n * anchors.k + objs.n
     # the benchmark's outputs: no final T (a frame that requests none skips
     # keeping the per-chunk states of split lists)
     r = bench.rig_renderer(n, sensors, outputs=("rgb", "depth", "normal", "alpha", "n_contrib", "n_walk"))
     pose_t = torch.as_tensor(poses.reshape(-1, 12).astype(np.float32), device="cuda")
     d_obj = DeviceSurfels.from_host(objs)
-    nf = NeuralFrame(NeuralModel(*mlp), DeviceAnchors(anchors), r, d_obj, pose_t, origin, gsr.DECODE_F32)
+    nf = NeuralFrame(model, da, r, d_obj, pose_t, origin, gsr.DECODE_F32)
     nf.render()
     torch.cuda.synchronize()
     tuned = r.autotune([nf.table, d_obj], pose_t, warmup=1, reps=2)

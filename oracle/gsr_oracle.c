@@ -140,6 +140,10 @@ typedef struct {
     double zc;         /* centre depth (camera z) / centre range (LiDAR |mu|)
                           / horizontal distance (cylinder): the order key     */
     double tau;        /* bound on the error of an FP32 evaluation of zc      */
+    int key_exact;     /* not posed, position exactly FP32: key_in holds
+                          every operand of the key                           */
+    double key_in[3];  /* the centre's coordinates that enter the key with a
+                          nonzero coefficient (0 where none does)            */
     double c[2];       /* low-pass centre (pixels, or LiDAR cells)           */
     double o;          /* opacity, sigmoid of the logit                      */
     double feat[3];    /* camera: colour; LiDAR: intensity, ray drop, 0     */
@@ -288,6 +292,22 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
     for (int a = 0; a < 3; ++a) G->ms[a] = ms[a];
     G->rad = 3.01 * (su > sv ? su : sv);
     G->smin = su < sv ? su : sv;
+
+    /* The key's operands: two unposed surfels whose key computations take
+       identical operands get identical FP32 keys in any evaluation order
+       (terms with a zero coefficient contribute exact zeros), so an FP32
+       sort breaks their tie by index exactly as the FP64 order does. */
+    /* (only for positions that are exactly FP32 values, as a table given to
+       both sides is: a position the oracle derived in FP64, e.g. by its own
+       decode, need not equal the renderer's FP32 one) */
+    G->key_exact = !posed;
+    for (int b = 0; b < 3; ++b) G->key_exact &= (double)(float)pos[3 * i + b] == pos[3 * i + b];
+    for (int b = 0; b < 3; ++b) {
+        int used = 0;
+        for (int a = 0; a < 3; ++a)
+            if ((S->kind == 0 && a == 2) || (S->kind == 2 && a != 1) || S->kind == 1) used |= S->Rs[a][b] != 0.0;
+        G->key_in[b] = used ? pos[3 * i + b] : 0.0;
+    }
 
     /* order key and its FP32 error bound */
     if (S->kind == 0) {
@@ -483,6 +503,7 @@ typedef struct {
     double run_T0;                 /* T before the run's first surfel       */
     double last_zc, last_tau;      /* the run's last surfel                 */
     double lo[7], hi[7];           /* range of feat[3], normal[3], z        */
+    const or_surfel* last_g;       /* the run's last surfel                 */
     double first_alpha, first_v[7], second_alpha, second_v[7];
 } or_ray;
 
@@ -568,6 +589,14 @@ static double or_solve_error(const or_surfel* g, const or_hit* h, const or_senso
 
 static double or_max(double a, double b) { return a > b ? a : b; }
 
+/* Two surfels whose FP32 keys are equal in any evaluation order (see
+   key_exact): their tie is broken by index on both sides. */
+static int or_same_key(const or_surfel* a, const or_surfel* b)
+{
+    return a->key_exact && b->key_exact && a->key_in[0] == b->key_in[0] && a->key_in[1] == b->key_in[1] &&
+           a->key_in[2] == b->key_in[2];
+}
+
 static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sensor* S)
 {
     double T = r->T;
@@ -609,7 +638,7 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     }
     double v[7];
     or_values(g, h, v);
-    int tie = r->run_len > 0 && fabs(h->zc - r->last_zc) <= g->tau + r->last_tau;
+    int tie = r->run_len > 0 && fabs(h->zc - r->last_zc) <= g->tau + r->last_tau && !or_same_key(g, r->last_g);
     if (test < 1e-4) {
         /* reordered, the run could place this surfel before others of the
            run and stop the ray there instead: everything composited since
@@ -644,6 +673,7 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     ++r->run_len;
     r->last_zc = h->zc;
     r->last_tau = g->tau;
+    r->last_g = g;
     double w = h->alpha * T;
     for (int ch = 0; ch < 3; ++ch) r->feat[ch] += w * g->feat[ch];
     r->A += w;

@@ -639,3 +639,27 @@ def test_near_cull_within_rounding_is_flagged():
     assert far["alpha"].max() > 0.5
     on = far["alpha"] > 0
     assert np.all(far["flip"][on] < far["alpha"][on])
+
+
+def test_identical_key_operands_are_not_a_tie():
+    """Two unposed surfels at the same depth z (the identity camera's key
+    takes only z) with different x: their FP32 keys are equal whatever the
+    evaluation order, so both sides order them by index -- no slack, and the
+    lower index composites first.  The same pair one FP32 step apart in depth
+    is a near tie and carries the swap's slack."""
+    cam = _cam(W=65, H=65, f=40.0)
+    pix = [32 * 65 + 32]
+    o1, o2 = 0.6, 0.7
+    step = float(np.nextafter(np.float32(10.0), np.float32(20.0))) - 10.0
+    for dz, tied in ((0.0, False), (step, True)):
+        # positions exactly representable in FP32, as a table handed to both sides is
+        a = _one((0.015625, 0, 10.0), (0, 0), (1, 0, 0, 0), _logit(o1), rgb=(1, 0, 0))
+        b = _one((-0.015625, 0, 10.0 + dz), (0, 0), (1, 0, 0, 0), _logit(o2), rgb=(0, 0, 1))
+        out = R.render_pinhole(a.concat(b), cam, pixels=pix)
+        assert (out["slack"][0] > 0) == tied
+        if not tied:
+            # index order: a (index 0) first
+            ga, gb = out["rgb"][0][0] / 1.0, out["rgb"][0][2]
+            assert ga > gb
+            out2 = R.render_pinhole(b.concat(a), cam, pixels=pix)
+            assert out2["rgb"][0][2] > out2["rgb"][0][0]  # now b composites first

@@ -10,7 +10,9 @@ from oracle import render as OR
 from paper_2503_11731_gb300 import synth
 from parity import check_camera, check_lidar
 
-CAP = 0.1
+# flagged-fraction caps: the measured fractions (of 400-600 sampled rays,
+# so one ray is 0.17-0.25 %) with a margin
+CAP = {"camera": 0.02, "lidar": 0.015}
 
 pytestmark = pytest.mark.gpu
 
@@ -67,9 +69,9 @@ def test_rig_matches_oracle_with_posed_objects(gpu_lib):
     for s, g in zip(sensors, out):
         idx = rng.choice(s.width * s.height, 600, replace=False)
         if s.kind == "lidar":
-            check_lidar(g, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP)
+            check_lidar(g, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP[s.kind if s.kind == "lidar" else "camera"])
         else:
-            check_camera(g, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP)
+            check_camera(g, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP[s.kind if s.kind == "lidar" else "camera"])
     # the objects are visible somewhere (the test exercises the pose path)
     assert (scene.obj_id >= 0).sum() > 0
 
@@ -144,7 +146,7 @@ def test_preprocess_parts_mix_sh_degrees(gpu_lib):
     idx = np.random.default_rng(9).choice(s.width * s.height, 500, replace=False)
     o = OR.render_pinhole(whole, s, pixels=idx, obj_pose=poses)
     yy, xx = np.divmod(idx, s.width)
-    check_camera({k: v.cpu().numpy() for k, v in r.out[0].items()}, o, pix=idx, max_flag=CAP)
+    check_camera({k: v.cpu().numpy() for k, v in r.out[0].items()}, o, pix=idx, max_flag=CAP[s.kind if s.kind == "lidar" else "camera"])
     assert (r.out[0]["n_contrib"].cpu().numpy()[yy, xx] > 0).mean() > 0.5
 
 
@@ -242,9 +244,9 @@ def test_split_lists_match_oracle_and_unsplit_render(gpu_lib):
     for s, gg in zip(sensors, g):
         idx = rng.choice(s.width * s.height, 400, replace=False)
         if s.kind == "lidar":
-            check_lidar(gg, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP)
+            check_lidar(gg, OR.render_lidar(scene, s, rays=idx, obj_pose=poses), rays=idx, max_flag=CAP[s.kind if s.kind == "lidar" else "camera"])
         else:
-            check_camera(gg, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP)
+            check_camera(gg, OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses), pix=idx, max_flag=CAP[s.kind if s.kind == "lidar" else "camera"])
 
 
 def test_lidar_split_is_per_sensor(gpu_lib):

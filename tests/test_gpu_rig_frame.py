@@ -22,6 +22,10 @@ from parity import check_camera, check_lidar
 pytestmark = pytest.mark.gpu
 
 SAMPLES = 4096
+# flagged-fraction caps per sensor: the measured fractions with a margin
+# (the front and back cameras see the decoded boxes' coplanar faces head on,
+# where runs of near-tied centre depths end rays: see the oracle's flags)
+CAPS = [0.07, 0.035, 0.012, 0.012, 0.012, 0.012, 0.02, 0.02]
 
 
 def test_configured_rig_frame_matches_oracle(gpu_lib):
@@ -65,7 +69,7 @@ def test_configured_rig_frame_matches_oracle(gpu_lib):
         name = f"rig frame sensor {i} ({s.kind} {s.width}x{s.height})"
         if s.kind == "lidar":
             o = OR.render_lidar(scene, s, rays=idx, obj_pose=poses, tile=8)
-            check_lidar(gg, o, rays=idx, max_flag=0.1, name=name)
+            check_lidar(gg, o, rays=idx, max_flag=CAPS[i], name=name)
         else:
             o = OR.render_pinhole(scene, s, pixels=idx, obj_pose=poses, tile=16)
-            check_camera(gg, o, pix=idx, max_flag=0.1, name=name)
+            check_camera(gg, o, pix=idx, max_flag=CAPS[i], name=name)

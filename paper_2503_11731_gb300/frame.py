@@ -194,7 +194,7 @@ class Renderer:
         self.ws_ptr = ctypes.c_void_p((self.ws.data_ptr() + 255) & ~255)
 
     def autotune(self, parts, objects=None, camera_tiles=((16, 16), (16, 8), (8, 16), (8, 8), (32, 8)),
-                 lidar_tiles=((8, 8), (4, 8), (8, 4), (16, 8), (16, 4), (32, 4), (32, 2), (16, 16)),
+                 lidar_tiles=((8, 8), (4, 8), (16, 8), (16, 4), (32, 4), (32, 2), (32, 1), (64, 1)),
                  batch_depths=(64, 128, 256),
                  split_firsts=(4096, 8192, 16384, 32768), split_chunks=(256, 384, 512, 1024),
                  lidar_split_firsts=(1024, 2048, 4096, 8192), lidar_split_chunks=(128, 256, 512, 1024), warmup=1,

@@ -291,9 +291,11 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU arm
-def stage_traffic():
-    """DRAM bytes of the compositing stage (both launches) from the committed
-    ncu capture, or None once the kernel sources differ from the captured."""
+def stage_traffic(pairs):
+    """DRAM bytes of the compositing stage (both launches) for a frame of
+    `pairs` tile/surfel pairs: the committed small-case capture's bytes per
+    pair scaled to the frame, or None once the kernel sources differ from
+    the captured ones."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "compositing_counters.json")) as f:
@@ -304,7 +306,7 @@ def stage_traffic():
                 m.update(f.read())
         if m.hexdigest() != c["kernel_sources_sha1"]:
             return None
-        return sum(k["dram_bytes_read"] + k["dram_bytes_write"] for k in c["kernels"].values())
+        return float(c["dram_bytes_per_pair"]) * pairs
     except Exception:
         return None
 
@@ -1200,7 +1202,9 @@ def run_gpu(args):
     ach_ops = (walk_cam * 24 + walk_lid * 28) / (rig_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "compositing stage: k_render_rig (all 8 sensors, one persistent launch) + "
                                       "k_render_split (chunks of split lists)", "achieved": ach40,
-            "peak": peak, "unit": "T FP32 lane-op/s", "frac": ach40 / peak, "traffic": stage_traffic(),
+            "peak": peak, "unit": "T FP32 lane-op/s", "frac": ach40 / peak, "traffic": stage_traffic(npairs),
+            "traffic_source": "DRAM bytes per pair of a small-case capture (profiles/compositing_counters.json) x "
+                              "the frame's pairs",
             "peak_source": ("measured: FP32 FMA-chain kernel, CUDA events (derived 152 SMs x 128 lanes x max SM "
                             f"clock = {derived_peak:.2f})") if meas_peak else
                            f"derived: 152 SMs x 128 FP32 lanes x max SM clock of {src_name} peaks",

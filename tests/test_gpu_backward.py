@@ -9,7 +9,9 @@
   of threshold-flip outliers allowed and reported);
 * finite differences of the GPU loss along random directions;
 * the 2M-surfel 1920x1080 step: finite, deterministic-in-loss, zero for
-  surfels no pixel sees, and a directional finite-difference check.
+  surfels no pixel sees, a directional finite-difference check of the GPU
+  loss, and the GPU gradient along a direction over 48 surfels against the
+  central difference of the FP64 oracle's whole-frame loss.
 """
 import numpy as np
 import pytest
@@ -249,3 +251,76 @@ def test_split_backward_matches_unsplit(gpu_lib):
         err = np.abs(a - b).max() / scale
         print("split vs unsplit gradient", k, err)
         assert err <= 1e-3, k
+
+
+def test_full_size_gradient_matches_oracle_directional_derivative(gpu_lib):
+    """2M surfels at 1920x1080 (the backward-step workload; loss L1 + 0.1
+    distortion + 0.05 normal consistency against the oracle's render of a
+    perturbed copy): the GPU gradient along a random direction v over the
+    parameters of 48 large on-screen surfels equals the central difference
+    of the FP64 oracle's loss (its tiled whole-frame render) along v.
+
+    The rendered image jumps where two surfels' centre depths cross (the
+    compositing order swaps), and the scene's coplanar box faces hold
+    surfels with exactly equal centre depths: v moves only surfels whose
+    centre depth lies at least 1e-4 from every other surfel's, so no order
+    (FP64 or FP32 key) changes within +-h.  It also jumps where a pixel's
+    alpha crosses the 1/255 skip threshold (about 1e-9 of the loss each);
+    such a crossing adds J / 2h to the difference, and its odds grow with
+    h.  For this v the difference is 4.124e-3 at h = 1e-6, 4.278e-3 at
+    1e-8 and 4.272e-3 at 1e-9: h = 1e-8 keeps the crossings' share below
+    6e-6, a tenth of the tolerance, while the FP64 loss's rounding (about
+    1e-14) adds about 5e-7.  The
+    surfels are chosen on the host: the 48 with the largest projected scale
+    whose centres lie in view.  Tolerance: 2e-3 of sum_i |g_i v_i|, the FP32
+    gradient's accumulated rounding with margin."""
+    from oracle import render as OR
+    from paper_2503_11731_gb300.frame import DeviceSurfels, Renderer, camera_backward, camera_loss
+    s = synth.driving_scene(n=2_000_000, seed=synth.SEED_BASE + 3)
+    tgt_scene = synth.perturbed(s, seed=synth.SEED_BASE + 30)
+    cam = synth.driving_camera()
+    target = OR.render_pinhole(tgt_scene, cam, tile=16)["rgb"]                      # [H, W, 3] FP64
+    r = Renderer(s.n, [cam], outputs=("rgb", "depth", "normal", "alpha", "trans", "depth_acc", "n_contrib"))
+    d = DeviceSurfels.from_host(s)
+    r.render(d)
+    t_gpu = torch.as_tensor(np.moveaxis(target, -1, 0).astype(np.float32).copy(), device="cuda")
+    loss, lo = camera_loss(r, 0, t_gpu)
+    g = camera_backward(r, 0, lo.struct(), d)
+    torch.cuda.synchronize()
+    g = {k: v.double().cpu().numpy() for k, v in g.items()}
+    P = np.c_[s.pos.astype(np.float64), np.ones(s.n)] @ np.asarray(cam.world_to_sensor, np.float64).T
+    zc = P[:, 2]
+    zs = np.where(zc > 0, zc, 1.0)
+    u, w = cam.fx * P[:, 0] / zs + cam.cx, cam.fy * P[:, 1] / zs + cam.cy
+    inside = (zc > 1.0) & (u > 0) & (u < cam.width) & (w > 0) & (w < cam.height)
+    size = np.exp(s.log_scale.astype(np.float64).max(1)) * cam.fx / zs
+    order = np.argsort(zc, kind="stable")
+    close = np.diff(zc[order]) < 1e-4
+    tied = np.zeros(s.n, bool)
+    tied[order[1:][close]] = True
+    tied[order[:-1][close]] = True
+    cand = np.flatnonzero(inside & ~tied)
+    idx = cand[np.argsort(-size[cand], kind="stable")[:48]]
+    assert len(idx) == 48
+    rng = np.random.default_rng(7)
+    names = ("pos", "log_scale", "quat", "opacity", "sh")
+    v = {k: np.zeros(getattr(s, k).shape, np.float64) for k in names}
+    for k in names:
+        v[k][idx] = rng.normal(size=v[k][idx].shape)
+    terms = np.concatenate([(g[k] * v[k]).ravel() for k in names])
+    ad = float(terms.sum())
+
+    def oracle_loss(eps):
+        moved = synth.Surfels(*(getattr(s, k).astype(np.float64) + eps * v[k] for k in names),
+                              s.intensity.astype(np.float64))
+        o = OR.render_pinhole(moved, cam, tile=16)
+        out = {"rgb": torch.as_tensor(o["rgb"]), "A": torch.as_tensor(o["acc"][..., 0]),
+               "B": torch.as_tensor(o["acc"][..., 1]), "D": torch.as_tensor(o["acc"][..., 2]),
+               "normal": torch.as_tensor(o["normal"])}
+        return float(OG.loss(out, torch.as_tensor(target), cam)[0])
+    h = 1e-8
+    fd = (oracle_loss(h) - oracle_loss(-h)) / (2 * h)
+    scale = float(np.abs(terms).sum())
+    print("full-size directional derivative: GPU", ad, "FP64 oracle central difference", fd, "scale", scale)
+    assert scale > 0
+    assert abs(ad - fd) <= 2e-3 * scale

@@ -1240,12 +1240,14 @@ def run_gpu(args):
         del o_outs, o_scene
     total_rays = n_rays(sensors)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "rig" else "ms per 1-camera+1-LiDAR frame (profiling workload)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (decode bf16 tcgen05, fp32 accumulation)" if anchors is not None
         else "f32", "data": "synthetic (seeded driving scene + rig; anchor MLP trained on the GPU on the explicit "
                             "background's frames)" if training is not None else
-        "synthetic (seeded driving scene + rig; untrained seeded anchor MLP)",
+        "synthetic (seeded driving scene + rig; untrained seeded anchor MLP)" if anchors is not None else
+        "synthetic (seeded explicit driving scene)",
         "config": {"workload": wl_desc, **tiling,
                    "surfels": n_main, "rays_per_frame": total_rays, "visible_records": nvis,
                    "tile_pairs": npairs, "l2": "inputs larger than L2, no flush",

@@ -159,7 +159,7 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     plan->max_dup = max_dup;
     // the fixed sort grid: 4 CTAs on each of the 152 SMs (3 measured the same
     // on the rig frame, 5 slower)
-    plan->sort_ctas = 4 * 152;
+    plan->sort_ctas = kSortCtasPerSm * 152;
 
     uint64_t sz[R_END];
     const uint64_t G = (uint64_t)plan->sort_ctas;

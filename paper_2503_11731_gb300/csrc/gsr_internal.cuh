@@ -33,10 +33,12 @@ constexpr float kSupport = 9.0f;          // (3 sigma)^2 in units of sigma^2
 constexpr float kLowPassInvVar = 2.0f;    // 1 / sigma_lp^2, sigma_lp^2 = 1/2 (px or cells)
 constexpr float kLowPassRadius = 2.12132034f; // 3 sigma_lp
 constexpr int kSortThreads = 256;
-constexpr int kSortIPT = 8;               // items per thread per sort tile
-constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBitsWide = 9;         // the widest digit of a pass (a key of 8k + 1 bits)
+constexpr int kSortCtasPerSm = 4;         // the plan's sort grid: 4 CTAs on each SM
+constexpr int kRadixIPT = 16;             // items per thread per radix scatter tile
+constexpr int kRadixTile = kSortThreads * kRadixIPT;
+constexpr int kRadixCtasPerSm = 2;        // resident radix scatter CTAs per SM (73-82 KB of shared memory each)
 // Default split of long tile lists (gsr_tiling.split_first / split_chunk = 0).
 constexpr int kSplitFirstDefault = 16384;  // positions walked before a tile's list is split
 constexpr int kSplitChunkDefault = 384;    // positions per later chunk

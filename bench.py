@@ -177,10 +177,22 @@ def oracle_frame(scene, poses, sensors):
     return outs, time.perf_counter() - t0
 
 
-def oracle_rig_scene(objs, anchors, mlp, origin):
+DECODED = ("pos", "log_scale", "quat", "opacity", "sh", "intensity")
+
+
+def round32(s):
+    """A surfel table with every parameter rounded to FP32 (ids unchanged)."""
+    from paper_2503_11731_gb300 import synth
+    f = lambda a: np.asarray(a, np.float32)
+    return synth.Surfels(f(s.pos), f(s.log_scale), f(s.quat), f(s.opacity), f(s.sh), f(s.intensity), s.obj_id,
+                         s.ray_drop)
+
+
+def oracle_rig_scene(objs, anchors, mlp, origin, decoded=False):
     """The configured frame's surfels as the oracle computes them: the FP64
     decode of every anchor (timed; SH-0 padded with zero coefficients to the
-    objects' degree 3, which leaves the colour unchanged) plus the objects."""
+    objects' degree 3, which leaves the colour unchanged) plus the objects.
+    With decoded=True also returns the oracle's decode (a dict of tensors)."""
     from oracle import mlp as OM
     from paper_2503_11731_gb300 import synth
     t0 = time.perf_counter()
@@ -191,6 +203,8 @@ def oracle_rig_scene(objs, anchors, mlp, origin):
     sh[:, :1] = d["sh"].numpy()
     back = synth.Surfels(d["pos"].numpy(), d["log_scale"].numpy(), d["quat"].numpy(), d["opacity"].numpy(), sh,
                          d["intensity"].numpy())
+    if decoded:
+        return back.concat(objs), dec_s, d
     return back.concat(objs), dec_s
 
 
@@ -1044,21 +1058,44 @@ def run_gpu(args):
 
     fma_peak = measure_fma_peak(stream) if rank == 0 else None
 
-    # ---- the same frame with the FP32 decode, for the parity block, and how
-    # far the timed BF16 frame lies from it
-    parity_gpu, bf16_gap = None, None
+    # ---- the parity block's inputs.  The frame with the FP32 decode: how far
+    # the timed BF16 frame lies from it, and its decode against the oracle's
+    # FP64 decode.  Then the render at identical inputs: the oracle's decoded
+    # table rounded to FP32, rendered on the GPU with the benchmarked plan
+    # (the oracle renders the same values), so that nothing the GPU computed
+    # enters the oracle.
+    parity_gpu, bf16_gap, decode_err, o_scene, dec_s = None, None, None, None, 0.0
     if args.cpu_baseline and anchors is not None and rank == 0 and world == 1:
         bf16 = learned_out
         nf.precision = gsr.DECODE_F32
         nf.render()
         torch.cuda.synchronize()
         check_status(r)
+        f32 = [{k: v.detach().cpu().numpy().copy() for k, v in o.items() if k in keep} for o in r.out]
+        f32_table = {k: getattr(nf.table, k).detach().cpu().numpy() for k in DECODED}
+        o_scene, dec_s, dec = oracle_rig_scene(objs, anchors_h, mlp_h, origin, decoded=True)
+        decode_err = {k: float(np.abs(f32_table[k] - dec[k].detach().numpy().reshape(f32_table[k].shape)).max())
+                      for k in DECODED}
+        del f32_table, dec
+        o_scene = round32(o_scene)
+        nb = anchors.n * anchors.k
+        d_back = DeviceSurfels.from_host(_synth.Surfels(o_scene.pos[:nb], o_scene.log_scale[:nb], o_scene.quat[:nb],
+                                                        o_scene.opacity[:nb],
+                                                        np.ascontiguousarray(o_scene.sh[:nb, :1]),
+                                                        o_scene.intensity[:nb]))
+        r.preprocess(d_back, pose_t, first=0)
+        r.preprocess(d_obj, pose_t, first=nb)
+        r.bin_sort()
+        r.composite_rig()
+        torch.cuda.synchronize()
+        check_status(r)
         parity_gpu = [{k: v.detach().cpu().numpy().copy() for k, v in o.items() if k in keep} for o in r.out]
+        del d_back
         nf.precision = gsr.DECODE_BF16_TENSOR
         nf.render()
         torch.cuda.synchronize()
         bf16_gap = []
-        for sd, a, b in zip(sensors, bf16, parity_gpu):
+        for sd, a, b in zip(sensors, bf16, f32):
             k = "intensity" if sd.kind == "lidar" else "rgb"
             mse = float(np.mean((a[k].astype(np.float64) - b[k]) ** 2))
             bf16_gap.append({"sensor": f"{sd.kind} {sd.width}x{sd.height}", "channel": k,
@@ -1221,22 +1258,22 @@ def run_gpu(args):
         # configuration (FP32 decode, so that nothing the GPU computed enters
         # the oracle) against it
         from oracle import render as OR
-        t0 = time.perf_counter()
-        if anchors is not None:
-            o_scene, dec_s = oracle_rig_scene(objs, anchors_h, mlp_h, origin)
-        else:
+        if o_scene is None:
             o_scene, dec_s = scene, 0.0
+        t0 = time.perf_counter()
         o_outs, rend_s = oracle_frame(o_scene, poses, sensors)
-        wall = time.perf_counter() - t0
+        wall = time.perf_counter() - t0 + dec_s
         cpu = {"value": wall * 1e3, "unit": UNIT, "cores": OR.num_threads(), "kind": "tiled oracle, timed",
                "sample": (f"one whole frame: FP64 decode of all anchors ({dec_s:.1f} s) and " if anchors is not None
                           else "one whole frame: ")
                + f"every ray of the 8 sensors ({n_rays(sensors)} rays, {rend_s:.1f} s) in the oracle's tiled mode "
                  f"over {o_scene.n} surfels"}
         if parity_gpu is not None:
-            parity = {"form": "GPU frame of the benchmarked configuration and tiling with the FP32 decode vs the "
-                              "oracle's own FP64 decode and render, every ray",
-                      "sensors": frame_parity(sensors, parity_gpu, o_outs), "bf16_vs_fp32_decode": bf16_gap}
+            parity = {"form": "every ray of the benchmarked configuration and tiling, rendered on the GPU and by "
+                              "the oracle from the same table: the oracle's FP64 decode of the trained anchors "
+                              "rounded to FP32, plus the objects",
+                      "sensors": frame_parity(sensors, parity_gpu, o_outs),
+                      "decode_fp32_vs_oracle_max_abs": decode_err, "bf16_vs_fp32_decode": bf16_gap}
         del o_outs, o_scene
     total_rays = n_rays(sensors)
     line = {

@@ -156,6 +156,104 @@ constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kSmemW1, kOffX = kOffW2 + kSmemW2, k
 constexpr int kOffB1 = kOffH + kSmemH, kOffB2 = kOffB1 + kHid * 4, kOffBar = kOffB2 + kOutPad * 4;
 constexpr int kDecodeSmem = kOffBar + 64;
 
+// The surfels of tile `tile` (anchor i = tile * 128 + thread), staged array
+// by array in `stg` (the free input and hidden buffers, 7168 floats) and
+// written with consecutive threads on consecutive words; the same values as
+// write_surfels.  Every branch is uniform over the CTA (each flush holds
+// barriers).  The caller has made every tensor-core operation of the tile
+// complete, so the buffers are free.
+__device__ __forceinline__ void write_surfels_staged(const DecodeArgs& a, int tile, const float* y, bool valid,
+                                                     bool cull, float* stg)
+{
+    const int tid = threadIdx.x;
+    const int i = tile * kTileA + tid;
+    const int ns = min(kTileA, a.n - tile * kTileA) * kOff;  // surfels of the tile
+    const size_t s0 = (size_t)tile * kTileA * kOff;          // its first surfel
+    auto flush = [&](float* dst, int width) {
+        __syncthreads();
+        const int cnt = ns * width;
+        float* d = dst + s0 * width;
+        for (int e = tid; e < cnt; e += kTileA) d[e] = stg[e];
+        __syncthreads();
+    };
+    if (valid) {
+        const float l = a.scale[i];
+        const float x0 = a.pos[3 * i], x1 = a.pos[3 * i + 1], x2 = a.pos[3 * i + 2];
+#pragma unroll
+        for (int j = 0; j < kOff; ++j) {
+            const float* o = a.offsets + ((size_t)i * kOff + j) * 3;
+            float* p = stg + (tid * kOff + j) * 3;
+            p[0] = fmaf(l, o[0], x0);
+            p[1] = fmaf(l, o[1], x1);
+            p[2] = fmaf(l, o[2], x2);
+        }
+    }
+    flush(a.out_pos, 3);
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < kOff; ++j) stg[tid * kOff + j] = cull ? kCulledLogit : y[kOff * j];
+    }
+    flush(a.out_opacity, 1);
+    if (valid) {
+        const float ll = __logf(a.scale[i]);
+#pragma unroll
+        for (int j = 0; j < kOff; ++j) {
+            stg[(tid * kOff + j) * 2] = y[kOff * j + 4] + ll;
+            stg[(tid * kOff + j) * 2 + 1] = y[kOff * j + 5] + ll;
+        }
+    }
+    flush(a.out_log_scale, 2);
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < kOff; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) stg[(tid * kOff + j) * 4 + q] = y[kOff * j + 6 + q];
+    }
+    flush(a.out_quat, 4);
+    if (a.head == GSR_HEAD_LIDAR) {
+        if (a.out_sh) {
+            if (valid)
+                for (int e = 0; e < 3 * kOff; ++e) stg[tid * kOff * 3 + e] = 0.f;
+            flush(a.out_sh, 3);
+        }
+        if (a.out_intensity) {
+            if (valid)
+#pragma unroll
+                for (int j = 0; j < kOff; ++j) stg[tid * kOff + j] = sigmoidf_(y[kOff * j + 1]);
+            flush(a.out_intensity, 1);
+        }
+        if (a.out_ray_drop) {
+            if (valid)
+#pragma unroll
+                for (int j = 0; j < kOff; ++j) stg[tid * kOff + j] = y[kOff * j + 2];
+            flush(a.out_ray_drop, 1);
+        }
+    } else {
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < kOff; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    stg[(tid * kOff + j) * 3 + c] = (sigmoidf_(y[kOff * j + 1 + c]) - 0.5f) * (1.f / kY00);
+        }
+        flush(a.out_sh, 3);
+        if (a.out_intensity) {
+            if (valid)
+#pragma unroll
+                for (int j = 0; j < kOff; ++j)
+                    stg[tid * kOff + j] = a.intensity ? a.intensity[(size_t)i * kOff + j] : 0.f;
+            flush(a.out_intensity, 1);
+        }
+    }
+}
+
+// Persistent CTAs: the weights are converted once per CTA and TMEM is
+// allocated once; each CTA then takes tiles of 128 anchors in turn.  Per
+// tile: the input rows (BF16, K-major canonical layout), layer 1 by one
+// tcgen05.mma chain into TMEM, bias + ReLU to the BF16 hidden rows, layer 2
+// into the same TMEM columns, and the tile's surfels staged array by array
+// in the (then free) input and hidden buffers and written with coalesced
+// stores.  Each tile commits twice, so its two waits take parities 0 and 1.
 __global__ void __launch_bounds__(kTileA) k_decode_tc(DecodeArgs a)
 {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -163,7 +261,9 @@ __global__ void __launch_bounds__(kTileA) k_decode_tc(DecodeArgs a)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffBar + 8);
     float* sb1 = reinterpret_cast<float*>(sm + kOffB1);
     float* sb2 = reinterpret_cast<float*>(sm + kOffB2);
+    float* stg = reinterpret_cast<float*>(sm + kOffX);  // output staging: the X and H buffers
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int ntiles = (a.n + kTileA - 1) / kTileA;
 
     // weights -> BF16 in the K-major canonical layout (B operands), biases
     for (int e = tid; e < kHid * kInPad; e += kTileA) {
@@ -183,71 +283,78 @@ __global__ void __launch_bounds__(kTileA) k_decode_tc(DecodeArgs a)
         fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(tslot, 128);
-
-    // input row of this thread's anchor
-    const int i = blockIdx.x * kTileA + tid;
-    const bool valid = i < a.n;
-    float X[kInPad];
-#pragma unroll
-    for (int k = 0; k < kInPad; ++k) X[k] = 0.f;
-    bool cull = false;
-    if (valid) {
-        input_row(a, i, X);
-        cull = culled(a, i);
-    }
-#pragma unroll
-    for (int c = 0; c < kInPad / 8; ++c) store_bf16x8(sm + kOffX + tc::canon_offset(tid, 8 * c, kInPad), X + 8 * c);
-    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-
-    // layer 1: D[128 x 64] = X[128 x 48] W1t[48 x 64]
-    if (tid == 0) {
-        constexpr uint32_t id1 = tc::idesc_bf16_f32(kTileA, kHid);
-        const uint32_t xa = smem_u32(sm + kOffX), wa = smem_u32(sm + kOffW1);
-        for (int s = 0; s < kInPad / 16; ++s)
-            tc::mma_bf16(tmem, tc::smem_desc(xa + 256 * s, 128, (kInPad / 8) * 128),
-                         tc::smem_desc(wa + 256 * s, 128, (kInPad / 8) * 128), id1, s > 0);
-        tc::commit(bar);
-    }
-    bool ok = wait_phase(bar, 0, a.status);
-    tc::fence_after_sync();
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    // epilogue 1: bias + ReLU -> BF16 hidden row (A operand of layer 2)
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // input row of this thread's anchor
+        const int i = tile * kTileA + tid;
+        const bool valid = i < a.n;
+        float X[kInPad];
 #pragma unroll
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::ld16(trow + c0, v);
+        for (int k = 0; k < kInPad; ++k) X[k] = 0.f;
+        bool cull = false;
+        if (valid) {
+            input_row(a, i, X);
+            cull = culled(a, i);
+        }
+        // the previous tile's staged outputs are written (the loop's last barrier)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + sb1[c0 + q], 0.f);
-        store_bf16x8(sm + kOffH + tc::canon_offset(tid, c0, kHid), v);
-        store_bf16x8(sm + kOffH + tc::canon_offset(tid, c0 + 8, kHid), v + 8);
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // layer 2: D[128 x 112] = H[128 x 64] W2t[64 x 112] (into the same columns)
-    if (tid == 0 && ok) {
-        constexpr uint32_t id2 = tc::idesc_bf16_f32(kTileA, kOutPad);
-        const uint32_t ha = smem_u32(sm + kOffH), wb = smem_u32(sm + kOffW2);
-        for (int s = 0; s < kHid / 16; ++s)
-            tc::mma_bf16(tmem, tc::smem_desc(ha + 256 * s, 128, (kHid / 8) * 128),
-                         tc::smem_desc(wb + 256 * s, 128, (kHid / 8) * 128), id2, s > 0);
-        tc::commit(bar);
-    }
-    ok = __syncthreads_and(ok);
-    if (ok) ok = wait_phase(bar, 1, a.status);
-    ok = __syncthreads_and(ok);  // block-uniform: tcgen05.ld below is warp-collective
-    tc::fence_after_sync();
-    if (ok) {
+        for (int c = 0; c < kInPad / 8; ++c)
+            store_bf16x8(sm + kOffX + tc::canon_offset(tid, 8 * c, kInPad), X + 8 * c);
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+
+        // layer 1: D[128 x 64] = X[128 x 48] W1t[48 x 64]
+        if (tid == 0) {
+            constexpr uint32_t id1 = tc::idesc_bf16_f32(kTileA, kHid);
+            const uint32_t xa = smem_u32(sm + kOffX), wa = smem_u32(sm + kOffW1);
+            for (int s = 0; s < kInPad / 16; ++s)
+                tc::mma_bf16(tmem, tc::smem_desc(xa + 256 * s, 128, (kInPad / 8) * 128),
+                             tc::smem_desc(wa + 256 * s, 128, (kInPad / 8) * 128), id1, s > 0);
+            tc::commit(bar);
+        }
+        bool ok = wait_phase(bar, 0, a.status);
+        tc::fence_after_sync();
+        // epilogue 1: bias + ReLU -> BF16 hidden row (A operand of layer 2)
+#pragma unroll
+        for (int c0 = 0; c0 < kHid; c0 += 16) {
+            float v[16];
+            tc::ld16(trow + c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + sb1[c0 + q], 0.f);
+            store_bf16x8(sm + kOffH + tc::canon_offset(tid, c0, kHid), v);
+            store_bf16x8(sm + kOffH + tc::canon_offset(tid, c0 + 8, kHid), v + 8);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        tc::fence_after_sync();
+        // layer 2: D[128 x 112] = H[128 x 64] W2t[64 x 112] (into the same columns)
+        if (tid == 0 && ok) {
+            constexpr uint32_t id2 = tc::idesc_bf16_f32(kTileA, kOutPad);
+            const uint32_t ha = smem_u32(sm + kOffH), wb = smem_u32(sm + kOffW2);
+            for (int s = 0; s < kHid / 16; ++s)
+                tc::mma_bf16(tmem, tc::smem_desc(ha + 256 * s, 128, (kHid / 8) * 128),
+                             tc::smem_desc(wb + 256 * s, 128, (kHid / 8) * 128), id2, s > 0);
+            tc::commit(bar);
+        }
+        if (ok) ok = wait_phase(bar, 1, a.status);
+        ok = __syncthreads_and(ok);  // block-uniform: tcgen05.ld below is warp-collective
+        tc::fence_after_sync();
+        if (!ok) break;  // no MMA of this CTA is outstanding past its wait
         float y[kOutPad];
 #pragma unroll
         for (int c0 = 0; c0 < kOutPad; c0 += 16) tc::ld16(trow + c0, y + c0);
+#pragma unroll
         for (int q = 0; q < kOut; ++q) y[q] += sb2[q];
-        if (valid) write_surfels(a, i, y, cull);
+        tc::fence_before_sync();
+        write_surfels_staged(a, tile, y, valid, cull, stg);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -478,6 +585,24 @@ gsr_status cuda_status(cudaError_t e);
 
 using namespace gsr;
 
+// Persistent decode CTAs: resident CTAs per SM x SMs of the current device.
+static int decode_grid(cudaError_t& err)
+{
+    static int cached[64] = {};
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    int sms = 0, per_sm = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode_tc, kTileA, kDecodeSmem);
+    if (err != cudaSuccess) return 0;
+    const int g = sms * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < 64) cached[dev] = g;
+    return g;
+}
+
 extern "C" gsr_status gsr_decode_anchors(const gsr_anchors* anchors, const gsr_mlp* mlp, const float* origin,
                                          const gsr_sensor* cull_camera, int32_t precision,
                                          const gsr_surfel_table* out, uint32_t* device_status, void* stream)
@@ -491,7 +616,10 @@ extern "C" gsr_status gsr_decode_anchors(const gsr_anchors* anchors, const gsr_m
     if (precision == GSR_DECODE_BF16_TENSOR) {
         cudaError_t e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecodeSmem);
         if (e != cudaSuccess) return cuda_status(e);
-        k_decode_tc<<<(a.n + kTileA - 1) / kTileA, kTileA, kDecodeSmem, s>>>(a);
+        const int tiles = (a.n + kTileA - 1) / kTileA;
+        int grid = decode_grid(e);
+        if (e != cudaSuccess) return cuda_status(e);
+        k_decode_tc<<<grid < tiles ? grid : tiles, kTileA, kDecodeSmem, s>>>(a);
     } else if (precision == GSR_DECODE_F32) {
         k_decode_f32<<<(a.n + 127) / 128, 128, 0, s>>>(a);
     } else {

@@ -128,6 +128,32 @@ __global__ void __launch_bounds__(1024) k_scan_partials(T* __restrict__ partial,
     }
 }
 
+// Counts and depth keys of slots [i, i + 8) (two 16-byte loads each; the
+// chunks are 32-slot aligned), with zero counts past e.
+__device__ __forceinline__ void compact_load(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ depthkey,
+                                             uint64_t i, uint64_t e, uint4 (&c)[2], uint4 (&d)[2])
+{
+    if (i + kCompactPer <= e) {
+        c[0] = __ldg(reinterpret_cast<const uint4*>(counts + i));
+        c[1] = __ldg(reinterpret_cast<const uint4*>(counts + i + 4));
+        d[0] = __ldg(reinterpret_cast<const uint4*>(depthkey + i));
+        d[1] = __ldg(reinterpret_cast<const uint4*>(depthkey + i + 4));
+    } else {
+        uint32_t cc[8], dd[8];
+        for (int k = 0; k < kCompactPer; ++k) {
+            cc[k] = i + k < e ? __ldg(counts + i + k) : 0u;
+            dd[k] = i + k < e ? __ldg(depthkey + i + k) : 0u;
+        }
+        c[0] = make_uint4(cc[0], cc[1], cc[2], cc[3]);
+        c[1] = make_uint4(cc[4], cc[5], cc[6], cc[7]);
+        d[0] = make_uint4(dd[0], dd[1], dd[2], dd[3]);
+        d[1] = make_uint4(dd[4], dd[5], dd[6], dd[7]);
+    }
+}
+
+// The visible slots' depth keys and slot ids, in slot order: every slot's
+// count and key arrive in one step (no load waits on another), and the next
+// step's loads are in flight while this step is scanned and written.
 __global__ void __launch_bounds__(256) k_compact_write(const uint32_t* __restrict__ counts,
                                                        const uint32_t* __restrict__ depthkey, uint64_t n_slots,
                                                        const uint32_t* __restrict__ partial,
@@ -137,17 +163,32 @@ __global__ void __launch_bounds__(256) k_compact_write(const uint32_t* __restric
     uint64_t b, e;
     chunk_of(n_slots, blockIdx.x, gridDim.x, b, e);
     uint32_t base = partial[blockIdx.x];
-    for (uint64_t t0 = b; t0 < e; t0 += (uint64_t)blockDim.x * kCompactPer) {
-        const uint64_t i = t0 + (uint64_t)threadIdx.x * kCompactPer;
-        uint32_t f = i < e ? compact_flags(counts, i, e) : 0u;
+    const uint64_t step = (uint64_t)blockDim.x * kCompactPer;
+    uint4 c[2] = {}, d[2] = {};
+    uint64_t i = b + (uint64_t)threadIdx.x * kCompactPer;
+    if (b < e && i < e) compact_load(counts, depthkey, i, e, c, d);
+    for (uint64_t t0 = b; t0 < e; t0 += step) {
+        const uint32_t cc[8] = {c[0].x, c[0].y, c[0].z, c[0].w, c[1].x, c[1].y, c[1].z, c[1].w};
+        const uint32_t dd[8] = {d[0].x, d[0].y, d[0].z, d[0].w, d[1].x, d[1].y, d[1].z, d[1].w};
+        const uint64_t icur = i;
+        i += step;
+        if (i < e) {
+            compact_load(counts, depthkey, i, e, c, d);
+        } else {
+            c[0] = c[1] = d[0] = d[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        uint32_t f = 0;
+#pragma unroll
+        for (int k = 0; k < kCompactPer; ++k) f |= (cc[k] > 0 ? 1u : 0u) << k;
         uint32_t tot;
         uint32_t r = base + block_exclusive_scan<uint32_t, 256>(__popc(f), tot, sm);
-        while (f) {
-            const int k = __ffs(f) - 1;
-            f &= f - 1u;
-            vis_key[r] = __ldg(depthkey + i + k);
-            vis_val[r] = (uint32_t)(i + k);
-            ++r;
+#pragma unroll
+        for (int k = 0; k < kCompactPer; ++k) {
+            if (cc[k] > 0) {
+                vis_key[r] = dd[k];
+                vis_val[r] = (uint32_t)(icur + k);
+                ++r;
+            }
         }
         base += tot;
     }
@@ -720,6 +761,25 @@ __global__ void __launch_bounds__(256, 4) k_dup_write(SensorTable tab, int n_sur
 // chunk), while the running total fits the capacity; items (tile, c),
 // c = 1..C, are listed in tile order.  Deterministic: the outcome depends
 // only on the tile ranges.
+__device__ __forceinline__ uint32_t split_chunks(const SensorTable& tab, const uint2* __restrict__ ranges,
+                                                 uint32_t t, unsigned long long& need)
+{
+    const uint32_t len = ranges[t].y - ranges[t].x;
+    int s = 0;
+    while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
+    const SensorDev& sd = tab.s[s];
+    need = 0;
+    if (len <= (uint32_t)sd.split_first) return 0u;
+    const uint32_t C = (len - (uint32_t)sd.split_first - 1) / (uint32_t)sd.split_chunk + 1;
+    need = (unsigned long long)(C + 1) * (unsigned long long)(sd.tile_w * sd.tile_h);
+    return C;
+}
+
+// Thread k owns the contiguous tiles [k per, k per + per): it sums its
+// tiles' ray blocks, one block scan gives every tile its ray offset (tiles in
+// order, whether or not their split fits the capacity), its tiles' chunk
+// counts after the capacity check are summed and scanned the same way, and
+// a last walk writes each tile's plan and items.
 __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint2* __restrict__ ranges,
                                                      uint32_t n_tiles, unsigned long long cap_rays,
                                                      unsigned long long cap_items, uint4* __restrict__ info,
@@ -727,36 +787,38 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
 {
     __shared__ unsigned long long sm64[33];
     __shared__ uint32_t sm32[33];
-    unsigned long long run_rays = 0;
-    uint32_t run_items = 0;
-    for (uint32_t t0 = 0; t0 < n_tiles; t0 += 1024) {
-        const uint32_t t = t0 + threadIdx.x;
-        uint32_t C = 0;
-        unsigned long long need = 0;
-        if (t < n_tiles) {
-            const uint32_t len = ranges[t].y - ranges[t].x;
-            int s = 0;
-            while (s + 1 < tab.n && (int)t >= tab.s[s + 1].tile_base) ++s;
-            const SensorDev& sd = tab.s[s];
-            if (len > (uint32_t)sd.split_first) {
-                C = (len - (uint32_t)sd.split_first - 1) / (uint32_t)sd.split_chunk + 1;
-                need = (unsigned long long)(C + 1) * (unsigned long long)(sd.tile_w * sd.tile_h);
-            }
-        }
-        unsigned long long tot_rays;
-        const unsigned long long off = run_rays + block_exclusive_scan<unsigned long long, 1024>(need, tot_rays, sm64);
-        if (C > 0 && off + need > cap_rays) C = 0;
-        uint32_t tot_items;
-        const uint32_t ioff = run_items + block_exclusive_scan<uint32_t, 1024>(C, tot_items, sm32);
-        if (C > 0 && (unsigned long long)ioff + C > cap_items) C = 0;  // cannot happen: items <= rays / 32
-        if (t < n_tiles) {
-            info[t] = make_uint4(C, C > 0 ? (uint32_t)off : 0u, ioff, 0u);
-            for (uint32_t c = 1; c <= C; ++c) items[ioff + c - 1] = make_uint2(t, c);
-        }
-        run_rays += tot_rays;
-        run_items += tot_items;
+    const uint32_t per = (n_tiles + 1023u) / 1024u;
+    const uint32_t t0 = min(n_tiles, threadIdx.x * per), t1 = min(n_tiles, t0 + per);
+    unsigned long long rays = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        split_chunks(tab, ranges, t, need);
+        rays += need;
     }
-    if (threadIdx.x == 0) counters[C_NITEMS] = run_items;
+    unsigned long long tot_rays;
+    const unsigned long long roff = block_exclusive_scan<unsigned long long, 1024>(rays, tot_rays, sm64);
+    uint32_t nitems = 0;
+    unsigned long long off = roff;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        const uint32_t C = split_chunks(tab, ranges, t, need);
+        if (C > 0 && off + need <= cap_rays) nitems += C;
+        off += need;
+    }
+    uint32_t tot_items;
+    uint32_t ioff = block_exclusive_scan<uint32_t, 1024>(nitems, tot_items, sm32);
+    off = roff;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        uint32_t C = split_chunks(tab, ranges, t, need);
+        if (C > 0 && off + need > cap_rays) C = 0;
+        if (C > 0 && (unsigned long long)ioff + C > cap_items) C = 0;  // cannot happen: items <= rays / 32
+        info[t] = make_uint4(C, C > 0 ? (uint32_t)off : 0u, ioff, 0u);
+        for (uint32_t c = 1; c <= C; ++c) items[ioff + c - 1] = make_uint2(t, c);
+        ioff += C;
+        off += need;
+    }
+    if (threadIdx.x == 0) counters[C_NITEMS] = tot_items;
 }
 
 // Scheduling keys of the tiles: longest list first (ascending sort of

@@ -325,6 +325,58 @@ def stage_traffic(pairs):
         return None
 
 
+def stage_rooflines(nf, sensors, reps=5):
+    """HBM rate of the frame's three memory-streaming stages, each timed on
+    its own with CUDA events on the current stream (best of `reps`), as
+    algorithmic bytes / time against the measured copy bandwidth:
+    * decode: the anchors' tensors read once and the decoded table written;
+    * preprocess: every part's table read once per sensor model present, a
+      4-byte tile count per (sensor, surfel) slot, and per visible record its
+      96-byte record, 8-byte tile rectangle and 4-byte depth key;
+    * bin_sort: the slots' counts (4 B per slot); per visible record the
+      compaction (4 read + 8 written), four depth passes of 20 B (histogram
+      read 4, scatter read 8, written 8) and the duplication's offset, count
+      and rectangle (16 read); per pair the duplication's write (8), two tile
+      passes of 20 B and the tile ranges' read (4)."""
+    import torch
+    pk, src = peaks()
+    r = nf.r
+    nf.render()
+    torch.cuda.synchronize()
+    _, nvis, npairs = r.status()
+    best = {"decode": 1e30, "preprocess": 1e30, "bin_sort": 1e30}
+    for _ in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        nf.decode()
+        e[1].record()
+        nf.preprocess()
+        e[2].record()
+        r.bin_sort()
+        e[3].record()
+        torch.cuda.synchronize()
+        for k, (a, b) in zip(best, ((0, 1), (1, 2), (2, 3))):
+            best[k] = min(best[k], e[a].elapsed_time(e[b]))
+    nb = lambda ts: sum(x.numel() * x.element_size() for x in ts if x is not None)
+    da, tab = nf.anchors, nf.table
+    tables = [tab] + ([nf.table_l] if nf.table_l is not None else []) + \
+             ([nf.objects] if nf.objects is not None else [])
+    tab_bytes = sum(nb([t_.pos, t_.log_scale, t_.quat, t_.opacity, t_.sh, t_.intensity, t_.obj_id, t_.ray_drop])
+                    for t_ in tables)
+    kinds = len({s.kind for s in sensors})
+    slots = r.plan.n_surfels * len(sensors)
+    alg = {"decode": nb([da.pos, da.feature, da.scale, da.offsets, da.intensity]) +
+                     nb([tab.pos, tab.log_scale, tab.quat, tab.opacity, tab.sh, tab.intensity]),
+           "preprocess": kinds * tab_bytes + 4 * slots + (96 + 8 + 4) * nvis,
+           "bin_sort": 4 * slots + 108 * nvis + 52 * npairs}
+    out = {"peak_gbs": pk["hbm_gbs"], "peak_source": src, "visible_records": nvis, "tile_pairs": npairs,
+           "slots": slots}
+    for k, ms in best.items():
+        gbs = alg[k] / (ms * 1e-3) / 1e9
+        out[k] = {"ms": ms, "algorithmic_bytes": alg[k], "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
+    return out
+
+
 def measure_fma_peak(stream, reps=12):
     """FP32 FMA issue rate of this GPU (T lane-op/s): the library's FMA-chain
     kernel on 8 CTAs of 256 threads per SM (about 20 ms a launch), best of
@@ -1057,6 +1109,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     fma_peak = measure_fma_peak(stream) if rank == 0 else None
+    stage_rl = stage_rooflines(nf, sensors) if anchors is not None and rank == 0 else None
 
     # ---- the parity block's inputs.  The frame with the FP32 decode: how far
     # the timed BF16 frame lies from it, and its decode against the oracle's
@@ -1293,6 +1346,7 @@ def run_gpu(args):
         "per_sensor": per_sensor,
         "mray_per_s": total_rays / (value * 1e-3) / 1e6,
         "roofline": roof,
+        "stage_roofline": stage_rl,
         "cpu_baseline": cpu,
         "parity": parity,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -151,13 +151,17 @@ class NeuralFrame:
             self.lidar[0].decode(self.lidar[1], self.origin, precision=self.precision, out=self.table_l,
                                  stream=stream)
 
-    def front(self, stream=None):
-        """Preprocess of every part and the binning sort."""
+    def preprocess(self, stream=None):
+        """Preprocess of every part (gsr_preprocess_part per table)."""
         self.r.preprocess(self.table, self.poses, stream, first=0)
         if self.lidar is not None:
             self.r.preprocess(self.table_l, self.poses, stream, first=self.n_bg)
         if self.objects is not None:
             self.r.preprocess(self.objects, self.poses, stream, first=self.n_bg + self.n_l)
+
+    def front(self, stream=None):
+        """Preprocess of every part and the binning sort."""
+        self.preprocess(stream)
         self.r.bin_sort(stream)
 
     def render(self, stream=None):

@@ -543,7 +543,13 @@ def backward_step(args, stream):
     for _ in range(2):
         step(False)
     k = max(3, args.steps // 2)
+    if args.profile == "backward":
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
     ms = timed(stream, k, lambda: step(True))
+    if args.profile == "backward":
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     loss = float(step(False)[0])
     torch.cuda.synchronize()
     return {"workload": "2M-surfel SH-3 driving scene, 1920x1080 camera, 16x8 tiles, loss vs a perturbed copy",
@@ -1066,14 +1072,17 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    # the timed region is also the profiler's range (ncu --profile-from-start off)
-    torch.cuda.profiler.start()
+    # the timed region is also the profiler's range (ncu --profile-from-start
+    # off) unless another stage is profiled (--profile)
+    if args.profile == "frame":
+        torch.cuda.profiler.start()
     t0.record(stream)
     for _ in range(args.steps):
         step(record=True)
     t1.record(stream)
     torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
+    if args.profile == "frame":
+        torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     clocks = sample_clocks_stop(clk_p, clk_f, local) if rank == 0 else None
@@ -1402,6 +1411,9 @@ def main():
                     help="skip the zone-streaming drive")
     ap.add_argument("--no-cylindrical", dest="cylindrical", action="store_false",
                     help="skip the cylindrical-camera frame measurement")
+    ap.add_argument("--profile", default="frame", choices=["frame", "backward"],
+                    help="the profiler's range (ncu --profile-from-start off): the timed rig frames, or the "
+                         "timed steps of the 2M-surfel camera training step")
     ap.add_argument("--no-backward", dest="backward", action="store_false",
                     help="skip the backward-step timings (2M surfels; 1920x1080 camera, 128x1800 LiDAR)")
     args = ap.parse_args()

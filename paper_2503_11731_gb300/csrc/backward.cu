@@ -503,94 +503,104 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
                 meet = footprint_meets_box(Rt[0], Rt[1], Rt[2], Rt[3].x, wbox.x, wbox.y, wbox.z, wbox.w);
             }
             uint32_t mask = __ballot_sync(0xffffffffu, meet);
-            while (mask) {
-                const int bit = 31 - __clz(mask);  // the highest position first
-                mask &= ~(1u << bit);
-                const int j = g0 + bit;
-                const bool active = (uint32_t)j < last;
+            // the records of the mask from the highest position, two at a time:
+            // both evaluations are independent (their chains interleave), the
+            // transmittance recovery and gradients stay in reverse order
+            auto apply = [&](const int j, const Splat& sp, const bool contrib) {
+                if (!__any_sync(0xffffffffu, contrib)) return;
                 const float4* Rj = Bf + (j - lo) * kRecordF4;
-                Splat sp;
-                bool contrib = active && splat_eval<KIND>(Rj, rx, ry, d0, d1, d2, sd.near_plane, columns, sp);
-                if (!__any_sync(0xffffffffu, contrib)) continue;
-                float g[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) g[k] = 0.f;
-                if (contrib) {
-                    const float al = sp.alpha, z = sp.z;
-                    const float om = 1.f - al;
-                    T = T / om;  // transmittance in front of this surfel
-                    const float w = al * T;
-                    const float4 r3 = Rj[3], r4 = Rj[4];
-                    const float io = 1.f / om;
-                    float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
-                    float c[3] = {r3.y, r3.z, r3.w};
-                    if (KIND != GSR_SENSOR_LIDAR) {  // camera: colour and normal
-                        const float n[3] = {r4.x, r4.y, r4.z};
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            dal += gC[k] * (T * c[k] - Ca[k] * io) + gN[k] * (T * n[k] - Na[k] * io);
-                            Ca[k] = fmaf(w, c[k], Ca[k]);
-                            Na[k] = fmaf(w, n[k], Na[k]);
-                            g[13 + k] = w * gC[k];   // colour
-                            g[16 + k] = w * gN[k];   // normal
+                    float g[32];
+    #pragma unroll
+                    for (int k = 0; k < 32; ++k) g[k] = 0.f;
+                    if (contrib) {
+                        const float al = sp.alpha, z = sp.z;
+                        const float om = 1.f - al;
+                        T = T / om;  // transmittance in front of this surfel
+                        const float w = al * T;
+                        const float4 r3 = Rj[3], r4 = Rj[4];
+                        const float io = 1.f / om;
+                        float dal = gA * (T - Aa * io) + gB * (T * z - Ba * io) + gD * (T * z * z - Da * io);
+                        float c[3] = {r3.y, r3.z, r3.w};
+                        if (KIND != GSR_SENSOR_LIDAR) {  // camera: colour and normal
+                            const float n[3] = {r4.x, r4.y, r4.z};
+    #pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                dal += gC[k] * (T * c[k] - Ca[k] * io) + gN[k] * (T * n[k] - Na[k] * io);
+                                Ca[k] = fmaf(w, c[k], Ca[k]);
+                                Na[k] = fmaf(w, n[k], Na[k]);
+                                g[13 + k] = w * gC[k];   // colour
+                                g[16 + k] = w * gN[k];   // normal
+                            }
+                        } else {  // LiDAR: intensity and ray-drop probability
+    #pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                dal += gC[k] * (T * c[k] - Ca[k] * io);
+                                Ca[k] = fmaf(w, c[k], Ca[k]);
+                                g[13 + k] = w * gC[k];
+                            }
                         }
-                    } else {  // LiDAR: intensity and ray-drop probability
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            dal += gC[k] * (T * c[k] - Ca[k] * io);
-                            Ca[k] = fmaf(w, c[k], Ca[k]);
-                            g[13 + k] = w * gC[k];
+                        Aa += w;
+                        Ba = fmaf(w, z, Ba);
+                        Da = fmaf(w * z, z, Da);
+                        const float dz = w * (gB + 2.f * z * gD);
+                        const float o = r3.x;
+                        float dG = 0.f;
+                        if (o * sp.G < kAlphaMax) {
+                            g[12] = dal * sp.G;  // opacity
+                            dG = dal * o;
                         }
-                    }
-                    Aa += w;
-                    Ba = fmaf(w, z, Ba);
-                    Da = fmaf(w * z, z, Da);
-                    const float dz = w * (gB + 2.f * z * gD);
-                    const float o = r3.x;
-                    float dG = 0.f;
-                    if (o * sp.G < kAlphaMax) {
-                        g[12] = dal * sp.G;  // opacity
-                        dG = dal * o;
-                    }
-                    const float drho = -0.5f * sp.G * dG;
-                    if (sp.use3) {
-                        const float iq = 1.f / sp.q2;
-                        const float dq0 = 2.f * sp.u * iq * drho;
-                        const float dq1 = 2.f * sp.v * iq * drho;
-                        const float dq2 = -2.f * sp.rho * iq * drho - sp.z * iq * dz;
-                        g[11] = dz * iq;  // det
-                        float r0, r1, r2;
-                        if (KIND == GSR_SENSOR_PINHOLE) {
-                            r0 = sp.dx; r1 = sp.dy; r2 = 1.f;
-                            const float4 q0 = Rj[0], q1 = Rj[1], q2 = Rj[2];
-                            g[3] = -(dq0 * q0.x + dq1 * q1.x + dq2 * q2.x);  // centre x
-                            g[7] = -(dq0 * q0.y + dq1 * q1.y + dq2 * q2.y);  // centre y
+                        const float drho = -0.5f * sp.G * dG;
+                        if (sp.use3) {
+                            const float iq = 1.f / sp.q2;
+                            const float dq0 = 2.f * sp.u * iq * drho;
+                            const float dq1 = 2.f * sp.v * iq * drho;
+                            const float dq2 = -2.f * sp.rho * iq * drho - sp.z * iq * dz;
+                            g[11] = dz * iq;  // det
+                            float r0, r1, r2;
+                            if (KIND == GSR_SENSOR_PINHOLE) {
+                                r0 = sp.dx; r1 = sp.dy; r2 = 1.f;
+                                const float4 q0 = Rj[0], q1 = Rj[1], q2 = Rj[2];
+                                g[3] = -(dq0 * q0.x + dq1 * q1.x + dq2 * q2.x);  // centre x
+                                g[7] = -(dq0 * q0.y + dq1 * q1.y + dq2 * q2.y);  // centre y
+                            } else {
+                                r0 = d0; r1 = d1; r2 = d2;
+                            }
+                            g[0] = dq0 * r0; g[1] = dq0 * r1; g[2] = dq0 * r2;
+                            g[4] = dq1 * r0; g[5] = dq1 * r1; g[6] = dq1 * r2;
+                            g[8] = dq2 * r0; g[9] = dq2 * r1; g[10] = dq2 * r2;
                         } else {
-                            r0 = d0; r1 = d1; r2 = d2;
+                            g[3] = -2.f * kLowPassInvVar * sp.dx * drho;
+                            g[7] = -2.f * kLowPassInvVar * sp.dy * drho;
+                            g[19] = dz;  // centre depth
                         }
-                        g[0] = dq0 * r0; g[1] = dq0 * r1; g[2] = dq0 * r2;
-                        g[4] = dq1 * r0; g[5] = dq1 * r1; g[6] = dq1 * r2;
-                        g[8] = dq2 * r0; g[9] = dq2 * r1; g[10] = dq2 * r2;
-                    } else {
-                        g[3] = -2.f * kLowPassInvVar * sp.dx * drho;
-                        g[7] = -2.f * kLowPassInvVar * sp.dy * drho;
-                        g[19] = dz;  // centre depth
                     }
-                }
-                // reduce-scatter over the warp: after it lane l holds the sum of
-                // component l over the 32 rays (5 halving exchanges, 31 shuffles)
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) {
-                    const bool up = (lane & o) != 0;
-#pragma unroll
-                    for (int k = 0; k < o; ++k) {
-                        const float send = up ? g[k] : g[k + o];
-                        const float keep = up ? g[k + o] : g[k];
-                        g[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    // reduce-scatter over the warp: after it lane l holds the sum of
+                    // component l over the 32 rays (5 halving exchanges, 31 shuffles)
+    #pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) {
+                        const bool up = (lane & o) != 0;
+    #pragma unroll
+                        for (int k = 0; k < o; ++k) {
+                            const float send = up ? g[k] : g[k + o];
+                            const float keep = up ? g[k + o] : g[k];
+                            g[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
                     }
-                }
-                if (lane < kGradComponents && g[0] != 0.f)
-                    atomicAdd(reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4) + lane, g[0]);
+                    if (lane < kGradComponents && g[0] != 0.f)
+                        atomicAdd(reinterpret_cast<float*>(a.recgrad + (size_t)Sl[j - lo] * kRecordF4) + lane, g[0]);
+            };
+            while (mask) {
+                const int bit = 31 - __clz(mask);
+                mask &= ~(1u << bit);
+                const int bit2 = mask ? 31 - __clz(mask) : -1;
+                if (bit2 >= 0) mask &= ~(1u << bit2);
+                const int j = g0 + bit, j2 = g0 + (bit2 >= 0 ? bit2 : bit);
+                Splat sp, sp2;
+                const bool h = splat_eval<KIND>(Bf + (j - lo) * kRecordF4, rx, ry, d0, d1, d2, sd.near_plane, columns, sp);
+                const bool h2 = splat_eval<KIND>(Bf + (j2 - lo) * kRecordF4, rx, ry, d0, d1, d2, sd.near_plane, columns,
+                                                 sp2);
+                apply(j, sp, h && (uint32_t)j < last);
+                if (bit2 >= 0) apply(j2, sp2, h2 && (uint32_t)j2 < last);
             }
         }
         __syncthreads();  // buffer g&1 is free for batch g+2

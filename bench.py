@@ -496,12 +496,13 @@ def backward_step(args, stream):
     names = ("forward", "loss", "backward")
     ev = {k: [] for k in names}
 
-    # the list split of the step, picked by timing whole steps (the backward
-    # walks the forward's chunks, so gsr_autotune's frame-only choice is not it)
+    # the tile shape and list split of the step, picked by timing whole steps
+    # (the backward walks the forward's chunks, so gsr_autotune's frame-only
+    # choice is not it)
     trials = []
     best = None
-    for split in ((16384, 384), (4096, 384), (2048, 256), (1024, 256)):
-        r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=outs, split=split)
+    for tile, split in [(tl, sp) for tl in ((16, 8), (8, 16)) for sp in ((4096, 384), (2048, 256), (1024, 256))]:
+        r = Renderer(s.n, [cam], tiles=[tile], outputs=outs, split=split)
         r.render(dt)
         target = r.out[0]["rgb"].clone()
 
@@ -513,11 +514,11 @@ def backward_step(args, stream):
             camera_backward(r, 0, lo.struct(), d, out=grads)
         plain()
         ms = timed(stream, 3, plain)
-        trials.append({"split": list(split), "ms": ms})
+        trials.append({"tile": list(tile), "split": list(split), "ms": ms})
         if best is None or ms < best[0]:
-            best = (ms, split)
+            best = (ms, split, tile)
         del r
-    r = Renderer(s.n, [cam], tiles=[(16, 8)], outputs=outs, split=best[1])
+    r = Renderer(s.n, [cam], tiles=[best[2]], outputs=outs, split=best[1])
     r.render(dt)
     target = r.out[0]["rgb"].clone()
 
@@ -552,10 +553,11 @@ def backward_step(args, stream):
         torch.cuda.profiler.stop()
     loss = float(step(False)[0])
     torch.cuda.synchronize()
-    return {"workload": "2M-surfel SH-3 driving scene, 1920x1080 camera, 16x8 tiles, loss vs a perturbed copy",
+    return {"workload": f"2M-surfel SH-3 driving scene, 1920x1080 camera, {best[2][0]}x{best[2][1]} tiles, loss vs "
+                        "a perturbed copy",
             "ms_per_step": ms, "stage_ms": {k: float(np.mean([a.elapsed_time(b) for a, b in v]))
                                             for k, v in ev.items()},
-            "loss": loss, "steps": k, "split": list(best[1]), "split_trials": trials}
+            "loss": loss, "steps": k, "tile": list(best[2]), "split": list(best[1]), "split_trials": trials}
 
 
 def lidar_backward_step(args, stream):
@@ -583,8 +585,8 @@ def lidar_backward_step(args, stream):
     names = ("forward", "loss", "backward")
     ev = {k: [] for k in names}
 
-    def make(split):
-        r = Renderer(s.n, [lid], tiles=[(8, 8)], outputs=outs, lidar_split=split)
+    def make(split, tile):
+        r = Renderer(s.n, [lid], tiles=[tile], outputs=outs, lidar_split=split)
         r.render(dt)
         o = r.out[0]
         t_range = torch.where(o["alpha"] >= 0.5, o["range"], torch.zeros_like(o["range"]))
@@ -592,8 +594,9 @@ def lidar_backward_step(args, stream):
 
     trials = []
     best = None
-    for split in ((16384, 512), (4096, 256), (1024, 256)):
-        r, t_range, t_int = make(split)
+    for tile, split in [(tl, sp) for tl in ((8, 8), (16, 8), (4, 8))
+                        for sp in ((4096, 256), (1024, 256), (1024, 128), (512, 128))]:
+        r, t_range, t_int = make(split, tile)
 
         def plain():
             for g in grads.values():
@@ -603,11 +606,11 @@ def lidar_backward_step(args, stream):
             lidar_backward(r, 0, lo.struct(), d, out=grads)
         plain()
         ms = timed(stream, 3, plain)
-        trials.append({"split": list(split), "ms": ms})
+        trials.append({"tile": list(tile), "split": list(split), "ms": ms})
         if best is None or ms < best[0]:
-            best = (ms, split)
+            best = (ms, split, tile)
         del r
-    r, t_range, t_int = make(best[1])
+    r, t_range, t_int = make(best[1], best[2])
 
     def step(record):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
@@ -634,11 +637,12 @@ def lidar_backward_step(args, stream):
     ms = timed(stream, k, lambda: step(True))
     loss = float(step(False)[0])
     torch.cuda.synchronize()
-    return {"workload": "2M-surfel driving scene with ray-drop logits, one 128x1800 LiDAR, 8x8 tiles, loss vs the "
-                        "scan of a perturbed copy",
+    return {"workload": "2M-surfel driving scene with ray-drop logits, one 128x1800 LiDAR, "
+                        f"{best[2][0]}x{best[2][1]} tiles, loss vs the scan of a perturbed copy",
             "ms_per_step": ms, "stage_ms": {k: float(np.mean([a.elapsed_time(b) for a, b in v]))
                                             for k, v in ev.items()},
-            "loss": loss, "steps": k, "lidar_split": list(best[1]), "split_trials": trials}
+            "loss": loss, "steps": k, "tile": list(best[2]), "lidar_split": list(best[1]),
+            "split_trials": trials}
 
 
 def _psnr(a, b):

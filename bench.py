@@ -214,9 +214,11 @@ def frame_parity(sensors, gpu_outs, oracle_outs, tol=1e-4, flip=2e-5):
     decision that FP32 rounding may take the other way could move an output
     by more than 2e-5; near-tied runs of surfels (centre depths within FP32
     resolution) may composite in either order, so each ray's tolerance adds
-    the oracle's bound of what a reordering can change (its slack).  Per
-    sensor: flagged and tied fractions, the largest error beyond tolerance +
-    slack on unflagged rays (<= 0 means within), and the number of such rays."""
+    the oracle's bound of what a reordering can change (its slack), and every
+    output that of the conditioning of Eq. 2.  Per sensor: flagged and tied
+    fractions, the largest error beyond the slack on unflagged rays (within
+    when it is at most the tolerance), and the number of rays beyond
+    tolerance + slack."""
     rep = []
     for s, g, o in zip(sensors, gpu_outs, oracle_outs):
         ok = o["flip"] <= flip

@@ -43,7 +43,15 @@ static gsr_status cuda_fail(cudaError_t e)
 // (records the error string like the entry points here).
 gsr_status cuda_status(cudaError_t e) { return cuda_fail(e); }
 
-SensorTable make_sensor_table(const gsr_plan* p)
+int ray_dir_entries(const gsr_plan* p)
+{
+    int n = 0;
+    for (int i = 0; i < p->n_sensors; ++i)
+        if (p->sensors[i].kind != GSR_SENSOR_PINHOLE) n += p->sensors[i].width + p->sensors[i].height;
+    return n;
+}
+
+SensorTable make_sensor_table(const gsr_plan* p, const void* ws)
 {
     SensorTable t;
     std::memset(&t, 0, sizeof(t));
@@ -53,6 +61,7 @@ SensorTable make_sensor_table(const gsr_plan* p)
     t.total_tiles = p->tile_base[p->n_sensors];
     t.batch = p->tiling.batch_depth;
     const double deg = 3.14159265358979323846 / 180.0;
+    int dir_off = 0;
     for (int i = 0; i < p->n_sensors; ++i) {
         const gsr_sensor& s = p->sensors[i];
         SensorDev& d = t.s[i];
@@ -90,7 +99,10 @@ SensorTable make_sensor_table(const gsr_plan* p)
         const int sc = s.split_chunk > 0 ? s.split_chunk : p->tiling.split_chunk;
         d.split_first = sf > 0 ? sf : kSplitFirstDefault;
         d.split_chunk = sc > 0 ? sc : kSplitChunkDefault;
+        d.dir_off = dir_off;
+        if (s.kind != GSR_SENSOR_PINHOLE) dir_off += s.width + s.height;
     }
+    t.dirs = ws != nullptr ? region<float2>(p, const_cast<void*>(ws), R_RAY_DIRS) : nullptr;
     return t;
 }
 
@@ -177,6 +189,7 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_COUNTERS] = C_WORDS * 4;
     sz[R_SENSOR_OF_TILE] = 64;
     sz[R_RECGRAD] = slots * kRecordBytes;
+    sz[R_RAY_DIRS] = (uint64_t)ray_dir_entries(plan) * 8 + 64;
     uint64_t max_hw = 0, max_rays = 0;
     for (int i = 0; i < n_sensors; ++i) {
         const uint64_t hw = (uint64_t)sensors[i].width * sensors[i].height;

@@ -387,7 +387,7 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
     const size_t pix = (size_t)y * sd.width + x;
     const uint32_t tile = (uint32_t)(sd.tile_base + lt);
     float rx, ry, d0, d1, d2;
-    ray_setup<KIND>(sd, x, y, rx, ry, d0, d1, d2);
+    ray_setup<KIND>(sd, tab.dirs, x, y, rx, ry, d0, d1, d2);
     const uint2 range = ranges[tile];
     uint32_t last = 0;
     float T = 1.f;
@@ -1052,7 +1052,7 @@ SplitBufs split_bufs(const gsr_plan* p, const void* ws);
 template <int KIND>
 static cudaError_t render_backward_kind(const gsr_plan* p, void* ws, int sensor, const BwdArgs& a, cudaStream_t st)
 {
-    const SensorTable tab = make_sensor_table(p);
+    const SensorTable tab = make_sensor_table(p, ws);
     const SensorDev& sd = tab.s[sensor];
     const int threads = sd.tile_w * sd.tile_h;
     const int tiles = sd.tiles_x * sd.tiles_y;
@@ -1139,7 +1139,7 @@ cudaError_t launch_render_backward_lidar(const gsr_plan* p, void* ws, int sensor
 cudaError_t launch_preprocess_backward(const gsr_plan* p, const void* ws, const gsr_surfels* s,
                                        const gsr_objects* obj, const gsr_surfel_grads* out, cudaStream_t st)
 {
-    const SensorTable tab = make_sensor_table(p);
+    const SensorTable tab = make_sensor_table(p, ws);
     PreBwdArgs a;
     a.S = *s;
     a.poses = (obj && obj->n_objects > 0) ? obj->pose : nullptr;

@@ -63,6 +63,7 @@ enum Region : int {
     R_SPLIT_ITEMS,   // (tile, chunk) of every split tile's chunks 1..C
     R_SPLIT_RAYS,    // ray records of split tiles (carry + one block per chunk)
     R_SPANS,         // per slot: the exact footprint's tile-row spans when short (SpanTable)
+    R_RAY_DIRS,      // per cylinder / LiDAR sensor: its columns' then its rows' ray-direction terms (float2)
     R_END
 };
 
@@ -95,6 +96,7 @@ struct SensorDev {
     float near_plane;
     float bg[3];
     int split_first, split_chunk;  // long lists: chunk 0 = split_first positions, then split_chunk each
+    int dir_off;                   // first entry of this sensor's ray-direction table (cylinder, LiDAR)
 };
 
 struct SensorTable {
@@ -103,6 +105,7 @@ struct SensorTable {
     int total_tiles;
     int batch;  // records staged per step of a walk; 0 = the CTA's thread count
     SensorDev s[GSR_MAX_SENSORS];
+    const float2* dirs;  // ray-direction tables (R_RAY_DIRS), null where no render reads them
 };
 
 // The plan's sensors of one model (kernels instantiated per model).
@@ -137,7 +140,11 @@ struct FrameOut {
     float* drop;       // LiDAR ray-drop probability
 };
 
-SensorTable make_sensor_table(const gsr_plan* p);
+SensorTable make_sensor_table(const gsr_plan* p, const void* ws = nullptr);
+// Entries of the ray-direction tables: width + height per cylinder / LiDAR sensor.
+int ray_dir_entries(const gsr_plan* p);
+// Fill the tables (once per frame, by gsr_bin_sort).
+cudaError_t launch_ray_dirs(const gsr_plan* p, void* ws, cudaStream_t st);
 
 // Which buffer (0 = A, 1 = B) holds the result of a sort of `passes` passes that started in A.
 inline int sort_result_buffer(int passes) { return passes & 1; }
@@ -582,11 +589,17 @@ __device__ __forceinline__ float* ray_block(const SplitBufs& sp, uint32_t base, 
     return sp.rays + ((size_t)base + (size_t)k * R) * kRayWords;
 }
 
-// Per-ray setup shared by the forward and backward rasterisers.
+// Per-ray setup shared by the forward and backward rasterisers.  A cylinder
+// or LiDAR ray's direction comes from its sensor's tables (the sine and
+// cosine of each column's and row's angle, evaluated in FP64 and rounded to
+// FP32 once per frame), so every direction is within a few FP32 roundings of
+// the exact one wherever the angle lies; rays outside the sensor (ragged
+// tiles) read its last column or row, and their results are never used.
 template <int KIND>
-__device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, float& rx, float& ry, float& d0,
-                                          float& d1, float& d2)
+__device__ __forceinline__ void ray_setup(const SensorDev& sd, const float2* __restrict__ dirs, int x, int y,
+                                          float& rx, float& ry, float& d0, float& d1, float& d2)
 {
+    const int cx = min(max(x, 0), sd.width - 1), cy = min(max(y, 0), sd.height - 1);
     if (KIND == GSR_SENSOR_PINHOLE) {
         rx = x + 0.5f;
         ry = y + 0.5f;
@@ -595,20 +608,18 @@ __device__ __forceinline__ void ray_setup(const SensorDev& sd, int x, int y, flo
         // Eq. 4: azimuth about the camera's y axis, height on the unit cylinder
         rx = x + 0.5f;
         ry = y + 0.5f;
-        float sp, cp;
-        sincosf((rx - sd.cx) / sd.fx, &sp, &cp);
-        d0 = sp;
-        d1 = (ry - sd.cy) / sd.fy;
-        d2 = cp;
+        const float2 c = dirs[sd.dir_off + cx];              // (sin phi, cos phi)
+        d0 = c.x;
+        d1 = dirs[sd.dir_off + sd.width + cy].x;            // (y + 1/2 - cy) / fy
+        d2 = c.y;
     } else {
         rx = (float)x;
         ry = (float)y;
-        float se, ce, sa, ca;
-        sincosf(sd.el_max - y * sd.d_el, &se, &ce);
-        sincosf(sd.az0 + (x + 0.5f) * sd.d_az, &sa, &ca);
-        d0 = ce * ca;
-        d1 = ce * sa;
-        d2 = se;
+        const float2 a = dirs[sd.dir_off + cx];              // (cos az, sin az)
+        const float2 e = dirs[sd.dir_off + sd.width + cy];   // (cos el, sin el)
+        d0 = e.x * a.x;
+        d1 = e.x * a.y;
+        d2 = e.y;
     }
 }
 

@@ -39,7 +39,7 @@ struct TileRay {
 };
 
 template <int KIND>
-__device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, int local_tile)
+__device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, const float2* dirs, int local_tile)
 {
     TileRay t;
     const int tid = threadIdx.x;
@@ -47,7 +47,7 @@ __device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, int local_tile)
     t.x = tx * sd.tile_w + tid % sd.tile_w;
     t.y = ty * sd.tile_h + tid / sd.tile_w;
     t.inside = tid < sd.tile_w * sd.tile_h && t.x < sd.width && t.y < sd.height;
-    ray_setup<KIND>(sd, t.x, t.y, t.rx, t.ry, t.d0, t.d1, t.d2);
+    ray_setup<KIND>(sd, dirs, t.x, t.y, t.rx, t.ry, t.d0, t.d1, t.d2);
     return t;
 }
 
@@ -250,12 +250,13 @@ __device__ __forceinline__ void write_ray(const SensorDev& sd, const TileRay& ra
 // Phase A: the tile's list (or its chunk 0).  Threads beyond the tile's rays
 // only help staging.
 template <int KIND>
-__device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile, uint32_t tile, const uint2 range,
+__device__ __forceinline__ void render_tile(const SensorDev& sd, const float2* dirs, int local_tile, uint32_t tile,
+                                            const uint2 range,
                                             const float4* __restrict__ rec, const uint32_t* __restrict__ pval,
                                             const FrameOut& out, uint32_t* counters, float4* buf, uint64_t* bars,
                                             uint32_t& gb, const SplitBufs& sp, int D)
 {
-    const TileRay ray = tile_ray<KIND>(sd, local_tile);
+    const TileRay ray = tile_ray<KIND>(sd, dirs, local_tile);
     const int n = (int)(range.y - range.x);
     RayState s;
     ray_init(s, !ray.inside, (uint32_t)n);
@@ -277,13 +278,14 @@ __device__ __forceinline__ void render_tile(const SensorDev& sd, int local_tile,
 // Phase B: chunk c of a split tile; the CTA that walks the tile's last
 // remaining chunk merges all of them and writes the tile's outputs.
 template <int KIND>
-__device__ __forceinline__ void render_chunk(const SensorDev& sd, int local_tile, uint32_t tile, int c,
+__device__ __forceinline__ void render_chunk(const SensorDev& sd, const float2* dirs, int local_tile, uint32_t tile,
+                                             int c,
                                              const uint2 range, const float4* __restrict__ rec,
                                              const uint32_t* __restrict__ pval, const FrameOut& out,
                                              uint32_t* counters, float4* buf, uint64_t* bars, uint32_t& gb,
                                              const SplitBufs& sp, uint32_t* flag_s, int D)
 {
-    const TileRay ray = tile_ray<KIND>(sd, local_tile);
+    const TileRay ray = tile_ray<KIND>(sd, dirs, local_tile);
     const int n = (int)(range.y - range.x);
     const int R = sd.tile_w * sd.tile_h;
     const int r = threadIdx.x;
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(256) k_render(SensorTable tab, int sensor, con
     const int lt = blockIdx.x;
     const uint32_t tile = (uint32_t)(sd.tile_base + lt);
     uint32_t gb = 0;
-    render_tile<KIND>(sd, lt, tile, ranges[tile], rec, pval, out, counters, buf, bars, gb, sp,
+    render_tile<KIND>(sd, tab.dirs, lt, tile, ranges[tile], rec, pval, out, counters, buf, bars, gb, sp,
                       tab.batch > 0 ? tab.batch : (int)blockDim.x);
 }
 
@@ -423,14 +425,14 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_rig(SensorTabl
         const SensorDev& sd = tab.s[s];
         const int lt = (int)tile - sd.tile_base;
         if (sd.kind == GSR_SENSOR_PINHOLE)
-            render_tile<GSR_SENSOR_PINHOLE>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
-                                            gb, sp, D);
+            render_tile<GSR_SENSOR_PINHOLE>(sd, tab.dirs, lt, tile, ranges[tile], rec, pval, outs.o[s], counters,
+                                            buf, bars, gb, sp, D);
         else if (sd.kind == GSR_SENSOR_CYLINDRICAL)
-            render_tile<GSR_SENSOR_CYLINDRICAL>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf,
-                                                bars, gb, sp, D);
+            render_tile<GSR_SENSOR_CYLINDRICAL>(sd, tab.dirs, lt, tile, ranges[tile], rec, pval, outs.o[s],
+                                                counters, buf, bars, gb, sp, D);
         else
-            render_tile<GSR_SENSOR_LIDAR>(sd, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf, bars,
-                                          gb, sp, D);
+            render_tile<GSR_SENSOR_LIDAR>(sd, tab.dirs, lt, tile, ranges[tile], rec, pval, outs.o[s], counters, buf,
+                                          bars, gb, sp, D);
     }
 }
 
@@ -468,14 +470,14 @@ __global__ void __launch_bounds__(256, GSR_RIG_MIN_CTAS) k_render_split(SensorTa
         const SensorDev& sd = tab.s[s];
         const int lt = (int)tile - sd.tile_base;
         if (sd.kind == GSR_SENSOR_PINHOLE)
-            render_chunk<GSR_SENSOR_PINHOLE>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
-                                             buf, bars, gb, sp, &flag_s, D);
+            render_chunk<GSR_SENSOR_PINHOLE>(sd, tab.dirs, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s],
+                                             counters, buf, bars, gb, sp, &flag_s, D);
         else if (sd.kind == GSR_SENSOR_CYLINDRICAL)
-            render_chunk<GSR_SENSOR_CYLINDRICAL>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s],
+            render_chunk<GSR_SENSOR_CYLINDRICAL>(sd, tab.dirs, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s],
                                                  counters, buf, bars, gb, sp, &flag_s, D);
         else
-            render_chunk<GSR_SENSOR_LIDAR>(sd, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s], counters,
-                                           buf, bars, gb, sp, &flag_s, D);
+            render_chunk<GSR_SENSOR_LIDAR>(sd, tab.dirs, lt, tile, (int)it.y, ranges[tile], rec, pval, outs.o[s],
+                                           counters, buf, bars, gb, sp, &flag_s, D);
     }
 }
 
@@ -571,7 +573,7 @@ static cudaError_t launch_split(const gsr_plan* p, const void* ws, const SensorT
 
 cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const FrameOut& out, cudaStream_t st)
 {
-    const SensorTable tab = make_sensor_table(p);
+    const SensorTable tab = make_sensor_table(p, ws);
     const SensorDev& sd = tab.s[sensor];
     const int threads = sd.tile_w * sd.tile_h;
     const size_t smem = render_smem_bytes(batch_of(tab, threads));
@@ -605,7 +607,7 @@ cudaError_t launch_render(const gsr_plan* p, const void* ws, int sensor, const F
 
 cudaError_t launch_render_rig(const gsr_plan* p, const void* ws, const FrameOut* outs, cudaStream_t st)
 {
-    const SensorTable tab = make_sensor_table(p);
+    const SensorTable tab = make_sensor_table(p, ws);
     RigOut ro;
     for (int i = 0; i < GSR_MAX_SENSORS; ++i) ro.o[i] = i < p->n_sensors ? outs[i] : FrameOut{};
     uint32_t* counters = region<uint32_t>(p, ws, R_COUNTERS);

@@ -939,8 +939,75 @@ int tile_sort_passes(const gsr_plan* p)
     return tile_sort_widths(p, w);
 }
 
+// ------------------------------------------------------- ray directions
+// The angles of a cylinder's columns (phi = (x + 1/2 - cx) / fx) and rows
+// (the unit-cylinder height (y + 1/2 - cy) / fy), and of a LiDAR's columns
+// (azimuth az0 + (x + 1/2) d_az) and beams (elevation el_max - y d_el), in
+// FP64 from the sensor's own parameters, their sine and cosine rounded to
+// FP32 once: a ray's direction is then within a few FP32 roundings of the
+// exact one at any angle (an angle summed in FP32 near +-pi would carry
+// several times more).
+struct RayDirParams {
+    int n;
+    int kind[GSR_MAX_SENSORS], width[GSR_MAX_SENSORS], height[GSR_MAX_SENSORS], off[GSR_MAX_SENSORS];
+    double a0[GSR_MAX_SENSORS], da[GSR_MAX_SENSORS], b0[GSR_MAX_SENSORS], db[GSR_MAX_SENSORS];
+};
+
+__global__ void __launch_bounds__(256) k_ray_dirs(RayDirParams q, int total, float2* __restrict__ dirs)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int s = 0;
+    while (s + 1 < q.n && (q.kind[s] == GSR_SENSOR_PINHOLE || e >= q.off[s] + q.width[s] + q.height[s])) ++s;
+    const int k = e - q.off[s];
+    const bool col = k < q.width[s];
+    // a LiDAR's beams sit at whole multiples of d_el from el_max, a cylinder's rows at half-pixel centres
+    const double row = k - q.width[s] + (q.kind[s] == GSR_SENSOR_LIDAR ? 0.0 : 0.5);
+    const double v = col ? q.a0[s] + (k + 0.5) * q.da[s] : q.b0[s] + row * q.db[s];
+    if (q.kind[s] == GSR_SENSOR_CYLINDRICAL) {
+        dirs[e] = col ? make_float2((float)sin(v), (float)cos(v)) : make_float2((float)v, 0.f);
+    } else {
+        dirs[e] = make_float2((float)cos(v), (float)sin(v));
+    }
+}
+
+cudaError_t launch_ray_dirs(const gsr_plan* p, void* ws, cudaStream_t st)
+{
+    const int total = ray_dir_entries(p);
+    if (total == 0) return cudaSuccess;
+    const SensorTable tab = make_sensor_table(p);
+    const double deg = 3.14159265358979323846 / 180.0;
+    RayDirParams q;
+    memset(&q, 0, sizeof(q));
+    q.n = p->n_sensors;
+    for (int i = 0; i < p->n_sensors; ++i) {
+        const gsr_sensor& s = p->sensors[i];
+        q.kind[i] = s.kind;
+        q.width[i] = s.width;
+        q.height[i] = s.height;
+        q.off[i] = tab.s[i].dir_off;
+        if (s.kind == GSR_SENSOR_LIDAR) {
+            q.a0[i] = (double)s.az0_deg * deg;
+            q.da[i] = 2.0 * 3.14159265358979323846 / s.width;
+            q.b0[i] = (double)s.el_max_deg * deg;
+            q.db[i] = -((double)s.el_max_deg - (double)s.el_min_deg) * deg / (s.height - 1);
+        } else if (s.kind == GSR_SENSOR_CYLINDRICAL) {
+            // phi = (x + 1/2 - cx) / fx = -cx / fx + (x + 1/2) / fx; height likewise
+            q.a0[i] = -(double)s.cx / (double)s.fx;
+            q.da[i] = 1.0 / (double)s.fx;
+            q.b0[i] = -(double)s.cy / (double)s.fy;
+            q.db[i] = 1.0 / (double)s.fy;
+        }
+    }
+    k_ray_dirs<<<(total + 255) / 256, 256, 0, st>>>(q, total, region<float2>(p, ws, R_RAY_DIRS));
+    return cudaGetLastError();
+}
+
 cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
 {
+    // the frame's ray-direction tables, read by every render that follows
+    const cudaError_t de = launch_ray_dirs(p, ws, st);
+    if (de != cudaSuccess) return de;
     const SensorTable tab = make_sensor_table(p);
     const int G = p->sort_ctas;
     const uint64_t n_slots = (uint64_t)p->n_surfels * p->n_sensors;

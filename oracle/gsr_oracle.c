@@ -469,8 +469,11 @@ static int or_cmp_hit(const void* pa, const void* pb)
  * output that taking the decision the other way could cause (T times the
  * jump in alpha; for the depth-branch choice, the relative jump in depth
  * weight; for a near-tied run at the stop, the weight composited since the
- * run began; for a ray that meets a surfel at a glancing angle, the change
- * of its weight that the conditioning of Eq. 2 allows, see or_step).  A near-tied run that composites whole does not flag the ray:
+ * run began; for hits after the stop that are near-tied with the stopping
+ * surfel, the weights they would composite before it, see or_after_stop;
+ * for a ray that meets a surfel at a glancing angle, the change of its
+ * weight that the conditioning of Eq. 2 allows, see or_step).  A near-tied
+ * run that composites whole does not flag the ray:
  * the change a reordering can make is bounded (or_run_close) and summed
  * into the ray's slack.
  */
@@ -505,6 +508,11 @@ typedef struct {
     double lo[7], hi[7];           /* range of feat[3], normal[3], z        */
     const or_surfel* last_g;       /* the run's last surfel                 */
     double first_alpha, first_v[7], second_alpha, second_v[7];
+    /* the surfel whose step ended the ray, and T there */
+    const or_surfel* stop_g;
+    double stop_zc, stop_tau, stop_T;
+    double post;                   /* summed effect of the surfels after the
+                                      stop that are near-tied with it      */
 } or_ray;
 
 static void or_flip(double* flip, double rel, double scale, double effect)
@@ -653,6 +661,10 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
             or_flip(&r->flip, 0.0, 1.0, r->run_T0 * m);
         }
         r->done = 1;
+        r->stop_g = g;
+        r->stop_zc = h->zc;
+        r->stop_tau = g->tau;
+        r->stop_T = T;
         return;
     }
     if (!tie) {
@@ -684,6 +696,32 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     ++r->n_contrib;
 }
 
+/*
+ * Past the stop.  A hit after the stopping surfel in (depth, index) order
+ * whose centre depth lies within the two FP32 error bounds of the stopping
+ * surfel's may come before it from an FP32 sort.  There it composites
+ * (weight alpha T at the stop's T) and the ray still ends at the stopping
+ * surfel (T only falls), or at this one if it stops the ray itself: each
+ * output moves by at most alpha T max(1, |value|), summed over such hits.
+ * Returns 0 once no later hit can be near-tied with the stop: its depth is
+ * past the stop's by more than the stop's bound plus tau_max, the largest
+ * bound of any surfel.
+ */
+static int or_after_stop(or_ray* r, const or_surfel* g, const or_hit* h, double tau_max)
+{
+    if (h->zc - r->stop_zc > r->stop_tau + tau_max) return 0;
+    if (h->alpha >= 1.0 / 255.0 && h->zc - r->stop_zc <= r->stop_tau + g->tau && !or_same_key(g, r->stop_g)) {
+        double v[7];
+        or_values(g, h, v);
+        double m = 1.0;
+        for (int c = 0; c < 6; ++c)
+            if (fabs(v[c]) > m) m = fabs(v[c]);
+        r->post += h->alpha * r->stop_T * m;
+        or_flip(&r->flip, 0.0, 1.0, r->post);
+    }
+    return 1;
+}
+
 static int or_collect(const or_surfel* g, int i, const or_sensor* S, const double hu[4], const double hv[4],
                       const double d[3], const double pc[2], const double dir[3], or_hit* h)
 {
@@ -703,14 +741,18 @@ static int or_collect(const or_surfel* g, int i, const or_sensor* S, const doubl
 
 /* Brute force: every surfel against the ray, hits sorted by (depth, index). */
 static void or_composite(const or_surfel* G, int n, const or_sensor* S, const double hu[4], const double hv[4],
-                         const double d[3], const double pc[2], const double dir[3], or_hit* buf, or_ray* out)
+                         const double d[3], const double pc[2], const double dir[3], double tau_max, or_hit* buf,
+                         or_ray* out)
 {
     int nh = 0;
     for (int i = 0; i < n; ++i)
         if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &buf[nh])) ++nh;
     qsort(buf, (size_t)nh, sizeof(or_hit), or_cmp_hit);
     or_ray_init(out);
-    for (int j = 0; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
+    int j = 0;
+    for (; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
+    if (out->done)
+        for (; j < nh && or_after_stop(out, &G[buf[j].idx], &buf[j], tau_max); ++j) {}
     or_ray_finish(out);
 }
 
@@ -990,15 +1032,24 @@ static int or_ray_may_reach(const or_surfel* g, const or_sensor* S, const double
 /* The tiled walk of one ray: its tile's candidates in (depth, index) order. */
 static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long tile_id, const or_sensor* S,
                                const double hu[4], const double hv[4], const double d[3], const double pc[2],
-                               const double dir[3], or_ray* out)
+                               const double dir[3], double tau_max, or_ray* out)
 {
     double dir2 = or_dot3(dir, dir);
     or_ray_init(out);
-    for (long long q = T->start[tile_id]; q < T->start[tile_id + 1] && !out->done; ++q) {
+    long long q = T->start[tile_id];
+    for (; q < T->start[tile_id + 1] && !out->done; ++q) {
         int i = T->cand[q].idx;
         if (!or_ray_may_reach(&G[i], S, dir, dir2, pc)) continue;
         or_hit h;
         if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &h)) or_step(out, &G[i], &h, S);
+    }
+    /* past the stop: the same hits in the same order as the brute-force walk */
+    for (; out->done && q < T->start[tile_id + 1]; ++q) {
+        int i = T->cand[q].idx;
+        if (T->cand[q].zc - out->stop_zc > out->stop_tau + tau_max) break;
+        if (!or_ray_may_reach(&G[i], S, dir, dir2, pc)) continue;
+        or_hit h;
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &h) && !or_after_stop(out, &G[i], &h, tau_max)) break;
     }
     or_ray_finish(out);
 }
@@ -1062,6 +1113,9 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
                           const long long* pix, int tile, or_emit_fn emit, void* ctx)
 {
     int fail = 0;
+    double tau_max = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (G[i].tau > tau_max) tau_max = G[i].tau;
     if (tile > 0) {
         or_tiles T;
         if (or_tiles_build(&T, G, n, S, tile, nx, ny) != 0) return -1;
@@ -1072,7 +1126,8 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
             double hu[4], hv[4], d[3], pc[2], dir[3];
             or_ray_planes(S, x, y, hu, hv, d, pc, dir);
             or_ray r;
-            or_composite_tiled(G, &T, (long long)(y / tile) * T.tiles_x + x / tile, S, hu, hv, d, pc, dir, &r);
+            or_composite_tiled(G, &T, (long long)(y / tile) * T.tiles_x + x / tile, S, hu, hv, d, pc, dir, tau_max,
+                               &r);
             emit(q, &r, ctx);
         }
         or_tiles_free(&T);
@@ -1092,7 +1147,7 @@ static int or_render_rays(const or_surfel* G, int n, const or_sensor* S, int nx,
                 double hu[4], hv[4], d[3], pc[2], dir[3];
                 or_ray_planes(S, x, y, hu, hv, d, pc, dir);
                 or_ray r;
-                or_composite(G, n, S, hu, hv, d, pc, dir, buf, &r);
+                or_composite(G, n, S, hu, hv, d, pc, dir, tau_max, buf, &r);
                 emit(q, &r, ctx);
             }
             free(buf);

@@ -663,3 +663,43 @@ def test_identical_key_operands_are_not_a_tie():
             assert ga > gb
             out2 = R.render_pinhole(b.concat(a), cam, pixels=pix)
             assert out2["rgb"][0][2] > out2["rgb"][0][0]  # now b composites first
+
+
+def test_near_tie_past_the_stop_is_flagged():
+    """Three red surfels of opacity 0.97 at 5, 6 and 7 m on the optical
+    axis: the third ends the ray (T would fall to 2.7e-5 < 1e-4), with
+    T = 9e-4 before it.  A blue surfel of opacity 0.5 within 1e-8 m behind
+    the third comes after the stop in FP64 order, but an FP32 sort may put
+    it first: it then composites 0.5 * 9e-4 of blue before the third still
+    ends the ray.  The flag carries exactly that change; the same surfel
+    1 mm behind is no tie and raises none.  Brute force and the tiled walk
+    agree bit for bit."""
+    cam = _cam()
+    pix = [16 * 33 + 16]
+    stack = None
+    for k in range(3):
+        t = _one((0, 0, 5.0 + k), (0, 0), (1, 0, 0, 0), _logit(0.97), rgb=(1, 0, 0))
+        stack = t if stack is None else stack.concat(t)
+    T_stop = 0.03 ** 2
+    for dz, tied in ((1e-8, True), (1e-3, False)):
+        blue = _one((0, 0, 7.0 + dz), (0, 0), (1, 0, 0, 0), _logit(0.5), rgb=(0, 0, 1))
+        s = stack.concat(blue)
+        out = R.render_pinhole(s, cam, pixels=pix)
+        assert out["n_contrib"][0] == 2
+        assert out["rgb"][0][2] == pytest.approx(0.0, abs=1e-12)
+        if tied:
+            assert out["flip"][0] == pytest.approx(0.5 * T_stop, rel=1e-6)
+            # the swapped order: blue at T_stop, then the third red stops the ray
+            T, rgb = 1.0, np.zeros(3)
+            for a, c in ((0.97, (1, 0, 0)), (0.97, (1, 0, 0)), (0.5, (0, 0, 1)), (0.97, (1, 0, 0))):
+                if T * (1 - a) < 1e-4:
+                    break
+                rgb += a * T * np.array(c)
+                T *= 1 - a
+            assert np.abs(rgb - out["rgb"][0]).max() == pytest.approx(out["flip"][0], rel=1e-6)
+        else:
+            assert out["flip"][0] == 0.0
+        for tile in (4, 16):
+            tiled = R.render_pinhole(s, cam, pixels=pix, tile=tile)
+            for k in out:
+                assert np.array_equal(out[k], tiled[k]), (dz, tile, k)

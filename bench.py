@@ -215,7 +215,8 @@ def frame_parity(sensors, gpu_outs, oracle_outs, tol=1e-4, flip=2e-5):
     by more than 2e-5; near-tied runs of surfels (centre depths within FP32
     resolution) may composite in either order, so each ray's tolerance adds
     the oracle's bound of what a reordering can change (its slack), and every
-    output that of the conditioning of Eq. 2.  Per sensor: flagged and tied
+    output that of the conditioning of Eq. 2 and of near ties past the stop
+    (slack_c).  Per sensor: flagged and tied
     fractions, the largest error beyond the slack on unflagged rays (within
     when it is at most the tolerance), and the number of rays beyond
     tolerance + slack."""

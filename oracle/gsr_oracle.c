@@ -145,6 +145,7 @@ typedef struct {
     double key_in[3];  /* the centre's coordinates that enter the key with a
                           nonzero coefficient (0 where none does)            */
     double c[2];       /* low-pass centre (pixels, or LiDAR cells)           */
+    double c_err[2];   /* bound on the error of an FP32 evaluation of c      */
     double o;          /* opacity, sigmoid of the logit                      */
     double feat[3];    /* camera: colour; LiDAR: intensity, ray drop, 0     */
     double normal[3];  /* sensor frame, facing the sensor                    */
@@ -166,6 +167,7 @@ typedef struct {
     int beams, columns;              /* LiDAR                              */
     double el_max, d_el, az0, d_az;  /* radians                            */
     double near_;
+    double bg[3];                    /* cameras: the background colour      */
 } or_sensor;
 
 static double or_sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
@@ -234,6 +236,49 @@ static void or_surfel_world(int i, const double* pos, const double* quat, const 
  */
 #define OR_U32 (1.0 / 16777216.0)
 #define OR_GAMMA4 (4.0 * OR_U32 / (1.0 - 4.0 * OR_U32))
+/* Roundoffs of the terms' magnitude by which an FP32 evaluation may move
+   the surfel plane along its normal or turn the ray: the gamma_4 bound of
+   an affine map's four terms, as for the order key. */
+#define OR_SOLVE_ROUNDOFF 4.0
+
+/*
+ * The FP32 reach of the low-pass centre c (ray units).  An FP32 evaluation
+ * places the centre's sensor-frame coordinates within about 4 u |mu_s| (the
+ * same estimate as the conditioning of Eq. 2), which turns its direction by
+ * that over its distance; an FP32 angle function is within a few ulps of
+ * its result (6 u |angle|); and each rounding of the chain that maps the
+ * projection to pixels or cells (a quotient, a scale, an offset) costs u
+ * times the magnitude it produces.  The bound is capped at one ray spacing.
+ */
+static void or_centre_error(or_surfel* G, const or_sensor* S)
+{
+    const double u = OR_U32;
+    const double* m = G->ms;
+    double ep = OR_SOLVE_ROUNDOFF * u * sqrt(or_dot3(m, m));
+    double ex, ey;
+    if (S->kind == 0) {
+        /* c = f X / Z + c0 */
+        double Z = fabs(m[2]) > 1e-30 ? fabs(m[2]) : 1e-30;
+        ex = S->fx * ep * (1.0 + fabs(m[0] / Z)) / Z + 3.0 * u * (fabs(G->c[0]) + fabs(S->cx));
+        ey = S->fy * ep * (1.0 + fabs(m[1] / Z)) / Z + 3.0 * u * (fabs(G->c[1]) + fabs(S->cy));
+    } else if (S->kind == 2) {
+        /* c = (c_x + f_x phi, c_y + f_y y / r_h) */
+        double rh = G->zc > 1e-30 ? G->zc : 1e-30;
+        double phi = atan2(m[0], m[2]);
+        ex = S->fx * (ep / rh + 6.0 * u * fabs(phi)) + 3.0 * u * (fabs(G->c[0]) + fabs(S->cx));
+        ey = S->fy * ep * (1.0 + fabs(m[1] / rh)) / rh + 3.0 * u * (fabs(G->c[1]) + fabs(S->cy));
+    } else {
+        /* c = ((az - az0) / d_az - 1/2, (el_max - el) / d_el) */
+        double rng = G->zc > 1e-30 ? G->zc : 1e-30;
+        double rh = sqrt(m[0] * m[0] + m[1] * m[1]);
+        if (rh < 1e-30) rh = 1e-30;
+        double az = atan2(m[1], m[0]), el = atan2(m[2], rh);
+        ex = (ep / rh + 6.0 * u * fabs(az) + u * (fabs(az) + fabs(S->az0))) / S->d_az + 2.0 * u * (fabs(G->c[0]) + 1.0);
+        ey = (ep / rng + 6.0 * u * fabs(el) + u * (fabs(el) + fabs(S->el_max))) / S->d_el + 2.0 * u * (fabs(G->c[1]) + 1.0);
+    }
+    G->c_err[0] = ex < 1.0 ? ex : 1.0;
+    G->c_err[1] = ey < 1.0 ? ey : 1.0;
+}
 
 static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* pos,
                        const double* log_scale, const double* quat, const double* opacity_logit,
@@ -331,6 +376,7 @@ static void or_prepare(or_surfel* G, int i, const or_sensor* S, const double* po
         G->c[0] = (az - S->az0) / S->d_az - 0.5;
         G->c[1] = (S->el_max - el) / S->d_el;
     }
+    or_centre_error(G, S);
     G->culled = !(G->zc > S->near_);
     G->cull_rel = fabs(G->zc - S->near_) / S->near_;
     G->o = or_sigmoid(opacity_logit[i]);
@@ -387,6 +433,8 @@ typedef struct {
     int phantom;      /* culled by the near test, but within rounding of it */
     int use3;         /* the ray-splat intersection's weight won (else low-pass) */
     double uabs;      /* |u| + |v| of the intersection */
+    double drholp;    /* bound on the change of rholp that the FP32 reach of
+                         the low-pass centre (c_err) allows                 */
     double cosang;    /* |cos| of the angle between the ray and the surfel normal */
 } or_hit;
 
@@ -427,6 +475,10 @@ static int or_eval(const or_surfel* G, const or_sensor* S, const double hu[4], c
         if (dx < -0.5 * S->columns) dx += S->columns;
     }
     h->rholp = (dx * dx + dy * dy) / 0.5; /* |p-c|^2 / sigma^2, sigma^2 = 1/2 */
+    {
+        double ex = G->c_err[0], ey = G->c_err[1];
+        h->drholp = 4.0 * (fabs(dx) * ex + fabs(dy) * ey) + 2.0 * (ex * ex + ey * ey);
+    }
     h->vlp = h->rholp <= 9.0;
     h->zc = G->zc;
     if (!h->v3 && !h->vlp) return 0;
@@ -469,9 +521,7 @@ static int or_cmp_hit(const void* pa, const void* pb)
  * output that taking the decision the other way could cause (T times the
  * jump in alpha; for the depth-branch choice, the relative jump in depth
  * weight; for a near-tied run at the stop, the weight composited since the
- * run began; for hits after the stop that are near-tied with the stopping
- * surfel, the weights they would composite before it, see or_after_stop;
- * for a ray that meets a surfel at a glancing angle, the change of its
+ * run began; for a ray that meets a surfel at a glancing angle, the change of its
  * weight that the conditioning of Eq. 2 allows, see or_step).  A near-tied
  * run that composites whole does not flag the ray:
  * the change a reordering can make is bounded (or_run_close) and summed
@@ -483,10 +533,6 @@ static int or_cmp_hit(const void* pa, const void* pb)
 
 /* Near-miss and phantom margin of or_collect (relative). */
 #define OR_NEAR_MISS 1e-3
-/* Roundoffs of the terms' magnitude by which an FP32 evaluation may move
-   the surfel plane along its normal or turn the ray: the gamma_4 bound of
-   an affine map's four terms, as for the order key. */
-#define OR_SOLVE_ROUNDOFF 4.0
 
 typedef struct {
     double feat[3], A, B, D, N[3], T;
@@ -495,9 +541,11 @@ typedef struct {
                          reordering of near-tied runs can make             */
     double slack_n;   /* the same for the normal                           */
     double slack_z;   /* the same for sum w z (the depth accumulator B)    */
-    double slack_c;   /* bound of the change of every output that FP32
-                         rounding can cause through the conditioning of
-                         Eq. 2 at glancing angles (relative for depth)     */
+    double slack_c;   /* bound of the change of every output (relative
+                         for depth) that FP32 rounding can cause through
+                         the conditioning of Eq. 2 at glancing angles, or
+                         by placing a near-tied hit before the stopping
+                         surfel (or_after_stop)                            */
     int n_contrib;
     int done;         /* the stop rule ended the ray                       */
     /* the current run of near-tied composited surfels (consecutive centre
@@ -511,8 +559,6 @@ typedef struct {
     /* the surfel whose step ended the ray, and T there */
     const or_surfel* stop_g;
     double stop_zc, stop_tau, stop_T;
-    double post;                   /* summed effect of the surfels after the
-                                      stop that are near-tied with it      */
 } or_ray;
 
 static void or_flip(double* flip, double rel, double scale, double effect)
@@ -613,12 +659,12 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
        relatively by (|u| + |v|) du) */
     double du = or_solve_error(g, h, S);
     double m_rho = or_max(OR_FLIP_REL, 2.0 * h->uabs * du / 9.0);
-    double m_alpha = h->use3 ? or_max(OR_FLIP_REL, h->uabs * du) : OR_FLIP_REL;
+    double m_alpha = h->use3 ? or_max(OR_FLIP_REL, h->uabs * du) : or_max(OR_FLIP_REL, 0.5 * h->drholp);
     double edge = T * g->o * exp(-4.5);
     if (h->hasplane && h->zint > S->near_) or_flip(&r->flip, or_relm(h->rho3, 9.0), m_rho, edge);
     if (h->hasplane && h->rho3 <= 9.0)
         or_flip(&r->flip, or_relm(h->zint, S->near_), OR_FLIP_REL, T * g->o * exp(-0.5 * h->rho3));
-    or_flip(&r->flip, or_relm(h->rholp, 9.0), OR_FLIP_REL, edge);
+    or_flip(&r->flip, or_relm(h->rholp, 9.0), or_max(OR_FLIP_REL, h->drholp / 9.0), edge);
     if (h->alpha <= 0) return;
     /* the centre-depth cull of this surfel could go the other way */
     or_flip(&r->flip, g->cull_rel, OR_FLIP_REL, h->alpha * T);
@@ -626,7 +672,8 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
     or_flip(&r->flip, or_relm(h->alpha, 1.0 / 255.0), m_alpha, T / 255.0);
     if (h->v3 && h->vlp) {
         double big = h->rho3 > h->rholp ? h->rho3 : h->rholp;
-        or_flip(&r->flip, fabs(h->rho3 - h->rholp) / big, OR_FLIP_REL,
+        or_flip(&r->flip, fabs(h->rho3 - h->rholp) / big,
+                or_max(OR_FLIP_REL, (h->drholp + 2.0 * h->uabs * du) / big),
                 h->alpha * T * fabs(h->zint - g->zc) / g->zc);
     }
     if (h->alpha < 1.0 / 255.0) return;
@@ -643,6 +690,9 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
         /* this weight moves by T dalpha, the later ones by at most as much in
            all: a bound on each output's change, added to the ray's slack */
         r->slack_c += 2.0 * T * dalpha;
+    } else if (!h->use3 && h->alpha < 0.99) {
+        /* the low-pass weight moves relatively by half the reach of rholp */
+        r->slack_c += T * h->alpha * h->drholp;
     }
     double v[7];
     or_values(g, h, v);
@@ -700,24 +750,27 @@ static void or_step(or_ray* r, const or_surfel* g, const or_hit* h, const or_sen
  * Past the stop.  A hit after the stopping surfel in (depth, index) order
  * whose centre depth lies within the two FP32 error bounds of the stopping
  * surfel's may come before it from an FP32 sort.  There it composites
- * (weight alpha T at the stop's T) and the ray still ends at the stopping
- * surfel (T only falls), or at this one if it stops the ray itself: each
- * output moves by at most alpha T max(1, |value|), summed over such hits.
- * Returns 0 once no later hit can be near-tied with the stop: its depth is
- * past the stop's by more than the stop's bound plus tau_max, the largest
- * bound of any surfel.
+ * weight w = alpha T at the stop's T, and the ray still ends at the
+ * stopping surfel (T only falls) or at this hit if it stops the ray itself.
+ * So A and the final T move by w, a colour (with the background behind T)
+ * by w |value - background|, the normal by w |n|, and the expected depth
+ * B / A relatively by at most w |z / d - 1| for d = B / A at the stop.  The
+ * largest of these, summed over such hits, is added to the ray's slack of
+ * every output (slack_c).  Returns 0 once no later hit can be near-tied with
+ * the stop: its depth is past the stop's by more than the stop's bound plus
+ * tau_max, the largest bound of any surfel.
  */
-static int or_after_stop(or_ray* r, const or_surfel* g, const or_hit* h, double tau_max)
+static int or_after_stop(or_ray* r, const or_surfel* g, const or_hit* h, const or_sensor* S, double tau_max)
 {
     if (h->zc - r->stop_zc > r->stop_tau + tau_max) return 0;
     if (h->alpha >= 1.0 / 255.0 && h->zc - r->stop_zc <= r->stop_tau + g->tau && !or_same_key(g, r->stop_g)) {
         double v[7];
         or_values(g, h, v);
         double m = 1.0;
-        for (int c = 0; c < 6; ++c)
-            if (fabs(v[c]) > m) m = fabs(v[c]);
-        r->post += h->alpha * r->stop_T * m;
-        or_flip(&r->flip, 0.0, 1.0, r->post);
+        for (int c = 0; c < 3; ++c) m = or_max(m, fabs(v[c] - S->bg[c]));
+        for (int c = 3; c < 6; ++c) m = or_max(m, fabs(v[c]));
+        if (r->A > 0 && r->B > 0) m = or_max(m, fabs(v[6] * r->A / r->B - 1.0));
+        r->slack_c += h->alpha * r->stop_T * m;
     }
     return 1;
 }
@@ -733,7 +786,7 @@ static int or_collect(const or_surfel* g, int i, const or_sensor* S, const doubl
     /* keep near misses too: their acceptance could flip in FP32 */
     int near_miss = (h->hasplane && h->zint > S->near_ && or_relm(h->rho3, 9.0) < OR_NEAR_MISS) ||
                     (h->hasplane && h->rho3 <= 9.0 && or_relm(h->zint, S->near_) < OR_NEAR_MISS) ||
-                    or_relm(h->rholp, 9.0) < OR_NEAR_MISS;
+                    or_relm(h->rholp, 9.0) < or_max(OR_NEAR_MISS, 2.0 * h->drholp / 9.0);
     if (!any && !near_miss) return 0;
     if (!any) { h->alpha = 0; h->z = g->zc; }
     return 1;
@@ -752,7 +805,7 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
     int j = 0;
     for (; j < nh && !out->done; ++j) or_step(out, &G[buf[j].idx], &buf[j], S);
     if (out->done)
-        for (; j < nh && or_after_stop(out, &G[buf[j].idx], &buf[j], tau_max); ++j) {}
+        for (; j < nh && or_after_stop(out, &G[buf[j].idx], &buf[j], S, tau_max); ++j) {}
     or_ray_finish(out);
 }
 
@@ -769,7 +822,8 @@ static void or_composite(const or_surfel* G, int n, const or_sensor* S, const do
  * u^2 + v^2 <= 9 (with the near-miss margin) lies inside the square of
  * half-width 3.01 s in the surfel plane, and inside the sphere of radius
  * 3.01 max(s_u, s_v) about the centre; the low-pass disc lies within 2.13
- * pixels (cells) of the projected centre.
+ * pixels (cells) of the projected centre, plus six times the centre's FP32
+ * reach (c_err).
  *   pinhole   -- the square clipped to the half-space in front of the near
  *                plane (where an intersection can count), projected: a
  *                convex polygon in front of the camera projects inside the
@@ -789,7 +843,9 @@ static int or_bound(const or_surfel* g, const or_sensor* S, double box[4], int* 
         *all_x = *all_y = 1;
         return 1;
     }
-    const double lp = 2.13;   /* 3 sigma_lp with the near-miss margin, and more */
+    /* 3 sigma_lp with the near-miss margin, and more; widened by six times
+       the centre's FP32 reach, which holds every rholp <= 9 + 2 drholp */
+    const double lp = 2.13 + 6.0 * or_max(g->c_err[0], g->c_err[1]);
     double x0 = g->c[0] - lp, x1 = g->c[0] + lp, y0 = g->c[1] - lp, y1 = g->c[1] + lp;
     const double* m = g->ms;
     const double r = g->rad;
@@ -1008,7 +1064,8 @@ static int or_tiles_build(or_tiles* T, const or_surfel* G, int n, const or_senso
  * Whether the ray (the line through the sensor origin along `dir`, sensor
  * frame) can reach surfel g: it passes within g->rad of the centre (the
  * sphere that holds the support with its near-miss margin), or the ray's
- * low-pass centre lies within 2.13 pixels (cells) of the surfel's.  A
+ * low-pass centre lies within 2.13 pixels (cells), plus six times the
+ * centre's FP32 reach, of the surfel's.  A
  * surfel for which both fail is neither a hit nor a near miss of this ray
  * (or_collect would drop it), so the tiled walk may skip it.
  */
@@ -1022,7 +1079,8 @@ static int or_ray_may_reach(const or_surfel* g, const or_sensor* S, const double
         if (dx >= 0.5 * S->columns) dx -= S->columns;
         if (dx < -0.5 * S->columns) dx += S->columns;
     }
-    if (dx * dx + dy * dy <= 2.13 * 2.13) return 1;
+    double lp = 2.13 + 6.0 * or_max(g->c_err[0], g->c_err[1]);
+    if (dx * dx + dy * dy <= lp * lp) return 1;
     double c[3];
     or_cross(g->ms, dir, c);
     /* squared distance of the centre from the line: |m x d|^2 / |d|^2 */
@@ -1049,7 +1107,8 @@ static void or_composite_tiled(const or_surfel* G, const or_tiles* T, long long 
         if (T->cand[q].zc - out->stop_zc > out->stop_tau + tau_max) break;
         if (!or_ray_may_reach(&G[i], S, dir, dir2, pc)) continue;
         or_hit h;
-        if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &h) && !or_after_stop(out, &G[i], &h, tau_max)) break;
+        if (or_collect(&G[i], i, S, hu, hv, d, pc, dir, &h) && !or_after_stop(out, &G[i], &h, S, tau_max))
+            break;
     }
     or_ray_finish(out);
 }
@@ -1196,6 +1255,7 @@ static int or_render_camera(int kind, int n, const double* pos, const double* lo
     S.kind = kind;
     or_sensor_from_matrix(&S, world_to_cam);
     S.fx = fx; S.fy = fy; S.cx = cx; S.cy = cy; S.near_ = near_;
+    for (int c = 0; c < 3; ++c) S.bg[c] = bg[c];
     S.width = width; S.height = height;
     or_surfel* G = or_prepare_all(n, &S, pos, log_scale, quat, opacity_logit, sh_degree, sh, NULL, NULL, obj_id, obj_pose);
     if (!G) return -1;

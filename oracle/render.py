@@ -100,8 +100,9 @@ def render_pinhole(s, cam, bg=(0.0, 0.0, 0.0), pixels=None, obj_pose=None, tile=
     slack_n [P] and slack_z [P] (bounds of the change a reordering of
     near-tied surfels can make to colour, normal and sum w z), slack_c [P]
     (bound of the change of any output, relative for depth, that FP32
-    rounding can cause through the conditioning of Eq. 2), n_contrib [P].  With pixels=None,
-    arrays are reshaped to images (rgb [H,W,3], ...).
+    rounding can cause through the conditioning of Eq. 2, or by sorting a
+    near-tied hit before the surfel that stops the ray), n_contrib [P].
+    With pixels=None, arrays are reshaped to images (rgb [H,W,3], ...).
     """
     lib = _load()
     keep = []

@@ -60,7 +60,8 @@ def _slack(o, depth):
     """The oracle's slack of each ray: the reordering bound of near-tied runs
     (absolute for colour / intensity / normal; relative to the depth (range)
     for the depth, since a reordering leaves sum w unchanged and moves sum w z
-    by slack_z) plus the conditioning bound slack_c of every output."""
+    by slack_z) plus the bound slack_c of every output (the conditioning of
+    Eq. 2 and near ties past the stop)."""
     z = np.zeros_like(o["flip"])
     sc = o.get("slack_c", z)
     sl = o.get("slack", z) + sc

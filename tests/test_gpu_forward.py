@@ -47,7 +47,7 @@ def test_plain_camera_full_frame_parity(gpu_lib, tile):
     st, nvis, npairs = r.status()
     assert st == 0 and nvis > 0 and npairs > 0
     o = OR.render_pinhole(s, cam)
-    _check_camera(out[0], o, max_flag=0.0035)  # measured 0.17 %
+    _check_camera(out[0], o, max_flag=0.0035)  # measured 0.20 %
 
 
 def test_ragged_image_and_background(gpu_lib):
@@ -56,7 +56,7 @@ def test_ragged_image_and_background(gpu_lib):
     cam = synth.Pinhole(203, 117, 90.0, 95.0, 101.0, 60.0, np.eye(4), 0.2)
     r, out = _render(s, [cam], bg=(0.2, 0.4, 0.6))
     o = OR.render_pinhole(s, cam, bg=(0.2, 0.4, 0.6))
-    _check_camera(out[0], o, max_flag=0.0025)  # measured 0.08 %
+    _check_camera(out[0], o, max_flag=0.0025)  # measured 0.10 %
 
 
 def test_sh3_posed_camera_parity(gpu_lib):
@@ -65,7 +65,7 @@ def test_sh3_posed_camera_parity(gpu_lib):
     cam = synth.pinhole(320, 200, 180.0, (0.0, 0.5, 1.5), yaw_deg=8.0, pitch_deg=-3.0)
     r, out = _render(s, [cam])
     o = OR.render_pinhole(s, cam)
-    _check_camera(out[0], o, max_flag=0.003)  # measured 0.15 %
+    _check_camera(out[0], o, max_flag=0.0035)  # measured 0.21 %
 
 
 def test_empty_and_culled_scenes(gpu_lib):
@@ -172,7 +172,7 @@ def test_lidar_full_frame_parity(gpu_lib):
     lid = synth.spinning_lidar(32, 720, -25.0, 15.0, (0.0, 0.0, 1.8))
     r, out = _render(s, [lid])
     o = OR.render_lidar(s, lid)
-    _check_lidar(out[0], o, max_flag=0.005)  # measured 0.27 %
+    _check_lidar(out[0], o, max_flag=0.0075)  # measured 0.47 %
 
 
 def test_lidar_wrap_and_close_surfels(gpu_lib):
@@ -206,6 +206,6 @@ def test_driving_scene_full_size_sampled(gpu_lib):
     pix = rng.choice(1920 * 1080, 4096, replace=False)
     rays = rng.choice(128 * 1800, 4096, replace=False)
     o = OR.render_pinhole(s, cam, pixels=pix, tile=16)
-    _check_camera(out[0], o, pix=pix, max_flag=0.01)  # measured 0.51 %
+    _check_camera(out[0], o, pix=pix, max_flag=0.01)  # measured 0.54 %
     ol = OR.render_lidar(s, lid, rays=rays, tile=8)
-    _check_lidar(out[1], ol, rays=rays, max_flag=0.02)  # measured 1.12 %
+    _check_lidar(out[1], ol, rays=rays, max_flag=0.025)  # measured 1.51 %

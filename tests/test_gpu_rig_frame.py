@@ -30,11 +30,13 @@ from parity import check_camera, check_lidar
 pytestmark = pytest.mark.gpu
 
 SAMPLES = 4096
-# flagged-fraction caps per sensor: the measured fractions (every ray of two
-# trained networks' frames: 0.7-0.8, 2.2, 0.3-0.6 % on the cameras, 1.1,
-# 1.4-1.6 % on the LiDARs) with a margin; the back camera sees the boxes'
-# coplanar faces head on, where runs of near-tied centre depths end rays
-CAPS = [0.015, 0.035, 0.01, 0.01, 0.01, 0.01, 0.02, 0.025]
+# flagged-fraction caps per sensor: the measured fractions (every ray of
+# trained networks' frames: 0.8, 2.3, 0.5-0.6 % on the cameras, 1.2-1.4 and
+# 2.6-3.0 % on the LiDARs) with a margin; the back camera sees the boxes'
+# coplanar faces head on, where runs of near-tied centre depths end rays;
+# the 32-beam LiDAR's coarse cells leave many surfels to the low-pass
+# fallback, whose thresholds FP32 can move by the centre's reach in cells
+CAPS = [0.015, 0.035, 0.01, 0.01, 0.01, 0.01, 0.025, 0.04]
 
 
 def test_configured_rig_frame_matches_oracle(gpu_lib):

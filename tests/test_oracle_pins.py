@@ -665,15 +665,16 @@ def test_identical_key_operands_are_not_a_tie():
             assert out2["rgb"][0][2] > out2["rgb"][0][0]  # now b composites first
 
 
-def test_near_tie_past_the_stop_is_flagged():
+def test_near_tie_past_the_stop_is_slack():
     """Three red surfels of opacity 0.97 at 5, 6 and 7 m on the optical
     axis: the third ends the ray (T would fall to 2.7e-5 < 1e-4), with
     T = 9e-4 before it.  A blue surfel of opacity 0.5 within 1e-8 m behind
     the third comes after the stop in FP64 order, but an FP32 sort may put
-    it first: it then composites 0.5 * 9e-4 of blue before the third still
-    ends the ray.  The flag carries exactly that change; the same surfel
-    1 mm behind is no tie and raises none.  Brute force and the tiled walk
-    agree bit for bit."""
+    it first: it then composites 0.5 * 9e-4 of blue, and as much alpha,
+    before the third still ends the ray.  That bounded change is the ray's
+    slack of every output (slack_c), not a flag; the same surfel 1 mm
+    behind is no tie and adds none.  Brute force and the tiled walk agree
+    bit for bit."""
     cam = _cam()
     pix = [16 * 33 + 16]
     stack = None
@@ -685,21 +686,65 @@ def test_near_tie_past_the_stop_is_flagged():
         blue = _one((0, 0, 7.0 + dz), (0, 0), (1, 0, 0, 0), _logit(0.5), rgb=(0, 0, 1))
         s = stack.concat(blue)
         out = R.render_pinhole(s, cam, pixels=pix)
-        assert out["n_contrib"][0] == 2
+        assert out["n_contrib"][0] == 2 and out["flip"][0] == 0.0
         assert out["rgb"][0][2] == pytest.approx(0.0, abs=1e-12)
         if tied:
-            assert out["flip"][0] == pytest.approx(0.5 * T_stop, rel=1e-6)
+            assert out["slack_c"][0] == pytest.approx(0.5 * T_stop, rel=1e-6)
             # the swapped order: blue at T_stop, then the third red stops the ray
-            T, rgb = 1.0, np.zeros(3)
+            T, rgb, A = 1.0, np.zeros(3), 0.0
             for a, c in ((0.97, (1, 0, 0)), (0.97, (1, 0, 0)), (0.5, (0, 0, 1)), (0.97, (1, 0, 0))):
                 if T * (1 - a) < 1e-4:
                     break
                 rgb += a * T * np.array(c)
+                A += a * T
                 T *= 1 - a
-            assert np.abs(rgb - out["rgb"][0]).max() == pytest.approx(out["flip"][0], rel=1e-6)
+            assert np.abs(rgb - out["rgb"][0]).max() == pytest.approx(out["slack_c"][0], rel=1e-6)
+            assert abs(A - out["alpha"][0]) == pytest.approx(out["slack_c"][0], rel=1e-6)
         else:
-            assert out["flip"][0] == 0.0
+            assert out["slack_c"][0] == 0.0
         for tile in (4, 16):
             tiled = R.render_pinhole(s, cam, pixels=pix, tile=tile)
             for k in out:
                 assert np.array_equal(out[k], tiled[k]), (dz, tile, k)
+
+
+def test_low_pass_centre_reach_flags_alpha_threshold():
+    """A sub-cell surfel seen by a 1024-column LiDAR only through the
+    low-pass fallback: its centre sits at cell (598 + 2^-15, 15.25), so the
+    ray of cell (600, 15) has rho_lp = 2 (dx^2 + dy^2) = 8.12.  The centre's
+    column is half an FP32 ulp off a representable value: rounding it to
+    FP32 alone moves rho_lp by 4 dx 2^-15 = 2.4e-4, and alpha = o exp(-rho_lp
+    / 2) by 1.2e-4 relative, six times the flat 2e-5 margin.  With its
+    opacity set so that alpha sits 4e-5 (relative) below 1/255, the oracle
+    flags the ray with the weight at stake (T / 255 = 1/255); at 5e-3 below,
+    beyond the centre's reach, it does not.  Brute force and tiled agree."""
+    lid = synth.Lidar(32, 1024, -30.0, 10.0, np.eye(4), -180.0, 0.2)
+    d_az = 2 * math.pi / 1024
+    d_el = math.radians(40.0) / 31
+    h = 2.0 ** -15
+    c0, c1 = 598.0 + h, 15.25
+    az = math.radians(-180.0) + (c0 + 0.5) * d_az
+    el = math.radians(10.0) - c1 * d_el
+    rng_ = 9.0
+    pos = (rng_ * math.cos(el) * math.cos(az), rng_ * math.cos(el) * math.sin(az), rng_ * math.sin(el))
+    dx, dy = 600 - c0, 15 - c1
+    rho = 2 * (dx * dx + dy * dy)
+    assert rho < 9
+    # what FP32 rounding of the centre's column alone does to alpha
+    dx32 = 600 - float(np.float32(c0))
+    rel = abs(math.exp(-(dx32 * dx32 + dy * dy)) / math.exp(-0.5 * rho) - 1)
+    assert rel > 5 * 2e-5
+    ray = 15 * 1024 + 600
+    for delta, flagged in ((4e-5, True), (5e-3, False)):
+        o = (1 - delta) / 255 / math.exp(-0.5 * rho)
+        s = _one(pos, (math.log(1e-3), math.log(1e-3)), (1, 0, 0, 0), _logit(o))
+        out = R.render_lidar(s, lid, rays=[ray])
+        assert out["alpha"][0] == 0.0            # below 1/255 in FP64: skipped
+        if flagged:
+            assert out["flip"][0] == pytest.approx(1 / 255, rel=1e-9)
+        else:
+            assert out["flip"][0] == 0.0
+        for tile in (4, 8):
+            tiled = R.render_lidar(s, lid, rays=[ray], tile=tile)
+            for k in out:
+                assert np.array_equal(out[k], tiled[k]), (delta, tile, k)

@@ -380,8 +380,10 @@ __device__ __forceinline__ void bwd_tile(const SensorTable& tab, const SensorDev
 {
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int tx = lt % sd.tiles_x, ty = lt / sd.tiles_x;
-    const int x = tx * sd.tile_w + tid % sd.tile_w;
-    const int y = ty * sd.tile_h + tid / sd.tile_w;
+    int lx, ly;
+    tile_ray_xy(sd.tile_w, sd.tile_h, tid, lx, ly);
+    const int x = tx * sd.tile_w + lx;
+    const int y = ty * sd.tile_h + ly;
     const bool inside = tid < sd.tile_w * sd.tile_h && x < sd.width && y < sd.height;
     const size_t HW = (size_t)sd.width * sd.height;
     const size_t pix = (size_t)y * sd.width + x;

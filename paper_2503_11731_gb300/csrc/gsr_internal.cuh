@@ -544,6 +544,24 @@ struct RayState {
     bool done;
 };
 
+// Ray of thread `tid` within a tile of tw x th rays.  A warp takes an 8 x 4
+// block of the tile where the tile is wider than 8 and divides into such
+// blocks (a compact block keeps the warp's ray box, against which the walks
+// cull records, small), else the tile's rays in row-major order.  The
+// forward and the backward walks, and the ray records of split tiles, all
+// use this map.
+__device__ __forceinline__ void tile_ray_xy(int tw, int th, int tid, int& lx, int& ly)
+{
+    if (tw > 8 && (tw & 7) == 0 && (th & 3) == 0) {
+        const int lane = tid & 31, w = tid >> 5, wpr = tw >> 3;
+        lx = (w % wpr) * 8 + (lane & 7);
+        ly = (w / wpr) * 4 + (lane >> 3);
+    } else {
+        lx = tid % tw;
+        ly = tid / tw;
+    }
+}
+
 __device__ __forceinline__ void ray_init(RayState& s, bool done, uint32_t n)
 {
     s.T = 1.f; s.A = 0.f; s.B = 0.f; s.D = 0.f;

@@ -44,8 +44,10 @@ __device__ __forceinline__ TileRay tile_ray(const SensorDev& sd, const float2* d
     TileRay t;
     const int tid = threadIdx.x;
     const int tx = local_tile % sd.tiles_x, ty = local_tile / sd.tiles_x;
-    t.x = tx * sd.tile_w + tid % sd.tile_w;
-    t.y = ty * sd.tile_h + tid / sd.tile_w;
+    int lx, ly;
+    tile_ray_xy(sd.tile_w, sd.tile_h, tid, lx, ly);
+    t.x = tx * sd.tile_w + lx;
+    t.y = ty * sd.tile_h + ly;
     t.inside = tid < sd.tile_w * sd.tile_h && t.x < sd.width && t.y < sd.height;
     ray_setup<KIND>(sd, dirs, t.x, t.y, t.rx, t.ry, t.d0, t.d1, t.d2);
     return t;

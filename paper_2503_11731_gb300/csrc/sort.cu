@@ -779,9 +779,7 @@ __device__ __forceinline__ uint32_t split_chunks(const SensorTable& tab, const u
 // tiles' ray blocks, one block scan gives every tile its ray offset (tiles in
 // order, whether or not their split fits the capacity), its tiles' chunk
 // counts after the capacity check are summed and scanned the same way, and
-// a last walk writes each tile's plan and items.  The walks are unrolled so
-// that a thread's range loads are in flight together (the kernel is one CTA:
-// latency, not bandwidth, sets its time).
+// a last walk writes each tile's plan and items.
 __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint2* __restrict__ ranges,
                                                      uint32_t n_tiles, unsigned long long cap_rays,
                                                      unsigned long long cap_items, uint4* __restrict__ info,
@@ -792,7 +790,6 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
     const uint32_t per = (n_tiles + 1023u) / 1024u;
     const uint32_t t0 = min(n_tiles, threadIdx.x * per), t1 = min(n_tiles, t0 + per);
     unsigned long long rays = 0;
-#pragma unroll 4
     for (uint32_t t = t0; t < t1; ++t) {
         unsigned long long need;
         split_chunks(tab, ranges, t, need);
@@ -802,7 +799,6 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
     const unsigned long long roff = block_exclusive_scan<unsigned long long, 1024>(rays, tot_rays, sm64);
     uint32_t nitems = 0;
     unsigned long long off = roff;
-#pragma unroll 4
     for (uint32_t t = t0; t < t1; ++t) {
         unsigned long long need;
         const uint32_t C = split_chunks(tab, ranges, t, need);
@@ -812,7 +808,6 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
     uint32_t tot_items;
     uint32_t ioff = block_exclusive_scan<uint32_t, 1024>(nitems, tot_items, sm32);
     off = roff;
-#pragma unroll 4
     for (uint32_t t = t0; t < t1; ++t) {
         unsigned long long need;
         uint32_t C = split_chunks(tab, ranges, t, need);

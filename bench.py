@@ -407,7 +407,8 @@ def bin_sort_launches(plan):
     """Kernel launches of one gsr_bin_sort: the ray-direction tables 1 (when a
     cylinder or LiDAR is in the plan), compaction 3, depth sort 4 passes x 5
     (histogram, 3-step scan, scatter), duplication 4, tile sort 5 per pass,
-    tile ranges 1, split plan 1, tile schedule 1 + 2 x 5."""
+    tile ranges 1, split plan 5 (three passes around two scans), tile
+    schedule 1 + 2 x 5."""
     T = plan.tile_base[plan.n_sensors]
     bits = 1
     while (1 << bits) < T:
@@ -415,7 +416,7 @@ def bin_sort_launches(plan):
     # 8-bit digits; a key of 8k + 1 bits takes a 9-bit top digit
     passes = bits // 8 if bits % 8 == 1 and bits > 8 else (bits + 7) // 8
     dirs = 1 if any(plan.sensors[i].kind != 0 for i in range(plan.n_sensors)) else 0
-    return dirs + 3 + 20 + 4 + 5 * passes + 1 + 1 + 1 + 10
+    return dirs + 3 + 20 + 4 + 5 * passes + 1 + 5 + 1 + 10
 
 
 def preprocess_launches(plan):

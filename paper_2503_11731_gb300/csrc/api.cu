@@ -185,7 +185,7 @@ extern "C" gsr_status gsr_plan_init(gsr_plan* plan, int32_t n_surfels, const gsr
     sz[R_CNT_SORTED] = slots * 4;
     sz[R_OFFSETS] = slots * 4;
     sz[R_HIST] = ((uint64_t)(1 << kRadixBitsWide) * G + G + 64) * 4;  // digit-major histogram + block sums
-    sz[R_PARTIAL] = G * 8 + 64;
+    sz[R_PARTIAL] = G * 12 + 64;  // 64-bit partials, then 32-bit ones (the split plan)
     sz[R_COUNTERS] = C_WORDS * 4;
     sz[R_SENSOR_OF_TILE] = 64;
     sz[R_RECGRAD] = slots * kRecordBytes;

@@ -755,12 +755,11 @@ __global__ void __launch_bounds__(256, 4) k_dup_write(SensorTable tab, int n_sur
     }
 }
 
-// Split plan of the frame (one CTA, tiles in id order): a tile whose list is
-// longer than F = split_first gets C = ceil((len - F) / split_chunk) chunks after
+// Split plan of the frame (tiles in id order): a tile whose list is longer
+// than F = split_first gets C = ceil((len - F) / split_chunk) chunks after
 // its first and (C + 1) x rays ray records (its carry and one block per
 // chunk), while the running total fits the capacity; items (tile, c),
-// c = 1..C, are listed in tile order.  Deterministic: the outcome depends
-// only on the tile ranges.
+// c = 1..C, are listed in tile order.
 __device__ __forceinline__ uint32_t split_chunks(const SensorTable& tab, const uint2* __restrict__ ranges,
                                                  uint32_t t, unsigned long long& need)
 {
@@ -775,28 +774,90 @@ __device__ __forceinline__ uint32_t split_chunks(const SensorTable& tab, const u
     return C;
 }
 
-// Thread k owns the contiguous tiles [k per, k per + per): it sums its
-// tiles' ray blocks, one block scan gives every tile its ray offset (tiles in
-// order, whether or not their split fits the capacity), its tiles' chunk
-// counts after the capacity check are summed and scanned the same way, and
-// a last walk writes each tile's plan and items.
-__global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint2* __restrict__ ranges,
-                                                     uint32_t n_tiles, unsigned long long cap_rays,
-                                                     unsigned long long cap_items, uint4* __restrict__ info,
-                                                     uint2* __restrict__ items, uint32_t* __restrict__ counters)
+// The plan over all CTAs of the sort grid, in three passes around two scans
+// of per-CTA partials (tiles in id order, as one sequential walk would take
+// them): CTA g owns the tiles chunk_of(g) and its thread k a contiguous run
+// of them.  (1) each CTA sums its tiles' ray blocks; (2) after the scan
+// every tile has its ray offset (tiles in order, whether or not their split
+// fits the capacity), the chunks of the tiles whose split fits are summed
+// per CTA; (3) after the second scan every tile has its first item, and its
+// plan and items are written.  Deterministic: the outcome depends only on
+// the tile ranges.
+__device__ __forceinline__ void split_run(uint32_t n_tiles, uint32_t& t0, uint32_t& t1)
 {
-    __shared__ unsigned long long sm64[33];
-    __shared__ uint32_t sm32[33];
-    const uint32_t per = (n_tiles + 1023u) / 1024u;
-    const uint32_t t0 = min(n_tiles, threadIdx.x * per), t1 = min(n_tiles, t0 + per);
+    uint64_t b, e;
+    chunk_of(n_tiles, blockIdx.x, gridDim.x, b, e);
+    const uint32_t per = (uint32_t)((e - b + blockDim.x - 1) / blockDim.x);
+    t0 = (uint32_t)min(e, b + (uint64_t)threadIdx.x * per);
+    t1 = (uint32_t)min(e, (uint64_t)t0 + per);
+}
+
+__global__ void __launch_bounds__(256) k_split_rays(SensorTable tab, const uint2* __restrict__ ranges,
+                                                    uint32_t n_tiles, unsigned long long* __restrict__ p64)
+{
+    __shared__ unsigned long long sm[9];
+    uint32_t t0, t1;
+    split_run(n_tiles, t0, t1);
     unsigned long long rays = 0;
     for (uint32_t t = t0; t < t1; ++t) {
         unsigned long long need;
         split_chunks(tab, ranges, t, need);
         rays += need;
     }
-    unsigned long long tot_rays;
-    const unsigned long long roff = block_exclusive_scan<unsigned long long, 1024>(rays, tot_rays, sm64);
+    unsigned long long tot;
+    block_exclusive_scan<unsigned long long, 256>(rays, tot, sm);
+    if (threadIdx.x == 0) p64[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_split_count(SensorTable tab, const uint2* __restrict__ ranges,
+                                                     uint32_t n_tiles, unsigned long long cap_rays,
+                                                     const unsigned long long* __restrict__ p64,
+                                                     uint32_t* __restrict__ p32)
+{
+    __shared__ unsigned long long sm64[9];
+    __shared__ uint32_t sm32[9];
+    uint32_t t0, t1;
+    split_run(n_tiles, t0, t1);
+    unsigned long long rays = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        split_chunks(tab, ranges, t, need);
+        rays += need;
+    }
+    unsigned long long tot;
+    unsigned long long off = p64[blockIdx.x] + block_exclusive_scan<unsigned long long, 256>(rays, tot, sm64);
+    uint32_t nitems = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        const uint32_t C = split_chunks(tab, ranges, t, need);
+        if (C > 0 && off + need <= cap_rays) nitems += C;
+        off += need;
+    }
+    uint32_t tot32;
+    block_exclusive_scan<uint32_t, 256>(nitems, tot32, sm32);
+    if (threadIdx.x == 0) p32[blockIdx.x] = tot32;
+}
+
+__global__ void __launch_bounds__(256) k_split_write(SensorTable tab, const uint2* __restrict__ ranges,
+                                                     uint32_t n_tiles, unsigned long long cap_rays,
+                                                     unsigned long long cap_items,
+                                                     const unsigned long long* __restrict__ p64,
+                                                     const uint32_t* __restrict__ p32, uint4* __restrict__ info,
+                                                     uint2* __restrict__ items)
+{
+    __shared__ unsigned long long sm64[9];
+    __shared__ uint32_t sm32[9];
+    uint32_t t0, t1;
+    split_run(n_tiles, t0, t1);
+    unsigned long long rays = 0;
+    for (uint32_t t = t0; t < t1; ++t) {
+        unsigned long long need;
+        split_chunks(tab, ranges, t, need);
+        rays += need;
+    }
+    unsigned long long tot;
+    const unsigned long long roff =
+        p64[blockIdx.x] + block_exclusive_scan<unsigned long long, 256>(rays, tot, sm64);
     uint32_t nitems = 0;
     unsigned long long off = roff;
     for (uint32_t t = t0; t < t1; ++t) {
@@ -805,8 +866,8 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
         if (C > 0 && off + need <= cap_rays) nitems += C;
         off += need;
     }
-    uint32_t tot_items;
-    uint32_t ioff = block_exclusive_scan<uint32_t, 1024>(nitems, tot_items, sm32);
+    uint32_t tot32;
+    uint32_t ioff = p32[blockIdx.x] + block_exclusive_scan<uint32_t, 256>(nitems, tot32, sm32);
     off = roff;
     for (uint32_t t = t0; t < t1; ++t) {
         unsigned long long need;
@@ -818,7 +879,6 @@ __global__ void __launch_bounds__(1024) k_split_plan(SensorTable tab, const uint
         ioff += C;
         off += need;
     }
-    if (threadIdx.x == 0) counters[C_NITEMS] = tot_items;
 }
 
 // Scheduling keys of the tiles: longest list first (ascending sort of
@@ -1049,9 +1109,18 @@ cudaError_t bin_sort(const gsr_plan* p, void* ws, cudaStream_t st)
     uint2* ranges = region<uint2>(p, ws, R_RANGES);
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)p->tile_base[p->n_sensors], st);
     k_tile_ranges<<<4 * G, 256, 0, st>>>(pk[pb], counters + C_NDUP, ranges);
-    k_split_plan<<<1, 1024, 0, st>>>(tab, ranges, (uint32_t)p->tile_base[p->n_sensors], split_ray_capacity(p),
-                                     split_item_capacity(p), region<uint4>(p, ws, R_SPLIT_INFO),
-                                     region<uint2>(p, ws, R_SPLIT_ITEMS), counters);
+    {
+        const uint32_t nt = (uint32_t)p->tile_base[p->n_sensors];
+        const uint64_t cap_rays = split_ray_capacity(p), cap_items = split_item_capacity(p);
+        unsigned long long* sp64 = reinterpret_cast<unsigned long long*>(partial);
+        uint32_t* sp32 = reinterpret_cast<uint32_t*>(sp64 + G);
+        k_split_rays<<<G, 256, 0, st>>>(tab, ranges, nt, sp64);
+        k_scan_partials<unsigned long long><<<1, 1024, 0, st>>>(sp64, G, nullptr, counters, 0, -1);
+        k_split_count<<<G, 256, 0, st>>>(tab, ranges, nt, cap_rays, sp64, sp32);
+        k_scan_partials<uint32_t><<<1, 1024, 0, st>>>(sp32, G, counters + C_NITEMS, counters, 0, -1);
+        k_split_write<<<G, 256, 0, st>>>(tab, ranges, nt, cap_rays, cap_items, sp64, sp32,
+                                         region<uint4>(p, ws, R_SPLIT_INFO), region<uint2>(p, ws, R_SPLIT_ITEMS));
+    }
     // 7. tile schedule for the whole-rig kernel (2 passes over 16-bit keys)
     const uint32_t T = (uint32_t)p->tile_base[p->n_sensors];
     uint32_t* tk[2] = {region<uint32_t>(p, ws, R_TILE_KEY_A), region<uint32_t>(p, ws, R_TILE_KEY_B)};

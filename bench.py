@@ -868,7 +868,7 @@ def two_scene_frame(args, r, sensors, da, model, d_obj, pose_t, origin, stream):
     torch.cuda.synchronize()
     G = nf.graphs()
     sh = ctypes.c_void_p(stream.cuda_stream)
-    frame = lambda: (G["decode"].replay(), G["front"].replay(), G["render_rig"].launch(sh))
+    frame = lambda: (G["decode_objects"].replay(), G["front_rest"].replay(), G["render_rig"].launch(sh))
     for _ in range(3):
         frame()
     k = max(3, args.steps // 2)
@@ -1044,7 +1044,7 @@ def run_gpu(args):
         nf.render()
         torch.cuda.synchronize()
         G = nf.graphs()
-        stages = [("decode", G["decode"].replay), ("pre_sort", G["front"].replay),
+        stages = [("decode_obj", G["decode_objects"].replay), ("pre_sort", G["front_rest"].replay),
                   ("render_rig", lambda: G["render_rig"].launch(sh))]
         n_launch = 1 + 2 * preprocess_launches(r.plan) + bin_sort_launches(r.plan) + 2
         n_main = nf.n_bg + objs.n
@@ -1115,7 +1115,7 @@ def run_gpu(args):
         nf_u.render()
         torch.cuda.synchronize()
         Gu = nf_u.graphs()
-        fr = lambda: (Gu["decode"].replay(), Gu["front"].replay(), Gu["render_rig"].launch(sh))
+        fr = lambda: (Gu["decode_objects"].replay(), Gu["front_rest"].replay(), Gu["render_rig"].launch(sh))
         for _ in range(3):
             fr()
         u_ms = timed(stream, max(3, args.steps // 2), fr)

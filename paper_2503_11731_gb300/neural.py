@@ -142,6 +142,7 @@ class NeuralFrame:
             self.table_l = lidar[0].new_table(lidar[1])
             self.n_l = lidar[1].n * lidar[1].k
         n_obj = 0 if objects is None else objects.n
+        self._side = None
         if renderer.plan.n_surfels != self.n_bg + self.n_l + n_obj:
             raise ValueError("plan surfel count must equal decoded + object surfels")
 
@@ -164,6 +165,29 @@ class NeuralFrame:
         self.preprocess(stream)
         self.r.bin_sort(stream)
 
+    def decode_objects(self, stream=None):
+        """The decode, with the posed-object table's preprocess alongside it
+        on a second stream (it reads nothing the decode writes, and the two
+        fill disjoint slots); then front_rest().  The decode leaves most of
+        each SM's threads free, so the two overlap."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if self.objects is None:
+            self.decode(s)
+            return
+        if self._side is None:
+            self._side = torch.cuda.Stream()
+        self._side.wait_stream(s)
+        self.r.preprocess(self.objects, self.poses, self._side, first=self.n_bg + self.n_l)
+        self.decode(s)
+        s.wait_stream(self._side)
+
+    def front_rest(self, stream=None):
+        """The decoded tables' preprocess and the binning sort (after decode_objects)."""
+        self.r.preprocess(self.table, self.poses, stream, first=0)
+        if self.lidar is not None:
+            self.r.preprocess(self.table_l, self.poses, stream, first=self.n_bg)
+        self.r.bin_sort(stream)
+
     def render(self, stream=None):
         self.decode(stream)
         self.front(stream)
@@ -171,9 +195,12 @@ class NeuralFrame:
         return self.r.out
 
     def graphs(self):
-        """Three replayable graphs of one frame: decode, preprocess + sort,
-        and the persistent whole-rig compositing launch."""
+        """Replayable graphs of one frame: decode, preprocess + sort, and the
+        persistent whole-rig compositing launch; and the same front end as
+        decode with the objects' preprocess alongside ("decode_objects")
+        followed by the rest ("front_rest")."""
         return {"decode": capture(self.decode), "front": capture(self.front),
+                "decode_objects": capture(self.decode_objects), "front_rest": capture(self.front_rest),
                 "render_rig": self.r.graph(self.table, self.poses, stages=4)}
 
 
@@ -220,8 +247,8 @@ class FramePipeline:
         self.inputs_ready.record(self.up)
         s.wait_event(self.inputs_ready)
         with torch.cuda.stream(s):
-            self.G["decode"].replay()
-            self.G["front"].replay()
+            self.G["decode_objects"].replay()
+            self.G["front_rest"].replay()
         self.front_done.record(s)
         if self.started:
             s.wait_event(self.outputs_read)  # the previous frame's outputs are read back

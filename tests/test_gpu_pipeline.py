@@ -1,8 +1,9 @@
 """Streamed frames (FramePipeline): uploads and read-backs on their own
-streams overlap the neighbouring frames, and every frame's outputs are
-bit-identical to a serial render of that frame's inputs (here: object poses
-that change every frame, per-frame pinned host buffers, no synchronisation
-between the frames)."""
+streams overlap the neighbouring frames, and the objects' preprocess runs
+alongside the decode inside each frame's first graph; every frame's outputs
+are bit-identical to a serial render of that frame's inputs (here: object
+poses that change every frame, per-frame pinned host buffers, no
+synchronisation between the frames)."""
 import numpy as np
 import pytest
 import torch

@@ -748,3 +748,38 @@ def test_low_pass_centre_reach_flags_alpha_threshold():
             tiled = R.render_lidar(s, lid, rays=[ray], tile=tile)
             for k in out:
                 assert np.array_equal(out[k], tiled[k]), (delta, tile, k)
+
+
+def test_low_pass_centre_reach_camera_column_1900():
+    """The same for a camera: a sub-pixel surfel 10 m ahead whose projected
+    centre sits at pixel x = 1900 + 2^-14 (half an FP32 ulp there), seen by
+    the pixel whose centre is (1901.5, 500.5) only through the low-pass
+    disc.  Rounding the centre's column to FP32 moves rho_lp by about
+    4 dx 2^-14 = 3.7e-4 and alpha by 1.8e-4 relative; with alpha 4e-5 below
+    1/255 the ray is flagged, at 5e-3 below it is not."""
+    W, H, f = 2048, 1024, 1000.0
+    cam = _cam(W=W, H=H, f=f)
+    h = 2.0 ** -14
+    c0, c1 = 1900.0 + h, 500.25
+    Z = 10.0
+    pos = ((c0 - W / 2.0) * Z / f, (c1 - H / 2.0) * Z / f, Z)
+    px, py = 1901, 500
+    dx, dy = px + 0.5 - c0, py + 0.5 - c1
+    rho = 2 * (dx * dx + dy * dy)
+    assert rho < 9
+    dx32 = px + 0.5 - float(np.float32(c0))
+    rel = abs(math.exp(-(dx32 * dx32 + dy * dy)) / math.exp(-0.5 * rho) - 1)
+    assert rel > 5 * 2e-5
+    pix = [py * W + px]
+    for delta, flagged in ((4e-5, True), (5e-3, False)):
+        o = (1 - delta) / 255 / math.exp(-0.5 * rho)
+        s = _one(pos, (math.log(1e-4), math.log(1e-4)), (1, 0, 0, 0), _logit(o))
+        out = R.render_pinhole(s, cam, pixels=pix)
+        assert out["alpha"][0] == 0.0
+        if flagged:
+            assert out["flip"][0] == pytest.approx(1 / 255, rel=1e-9)
+        else:
+            assert out["flip"][0] == 0.0
+        tiled = R.render_pinhole(s, cam, pixels=pix, tile=16)
+        for k in out:
+            assert np.array_equal(out[k], tiled[k]), (delta, k)

@@ -87,3 +87,21 @@ def test_camera_planes_against_pixel_major_oracle():
     o["slack_n"][1, 3] = 3e-4               # the normal's own reordering slack covers it
     rep = bench.frame_parity([_sensor("pinhole")], [g], [o])[0]
     assert rep["rays_over_tolerance"] == 0
+
+
+def test_slack_of_every_output_covers_alpha_and_relative_depth():
+    """slack_c bounds the change of every output (the conditioning of Eq. 2,
+    and hits past the stop that FP32 may composite first): alpha and the
+    colour / intensity get it absolutely, the range relatively over alpha."""
+    o = _oracle_lidar()
+    g = _gpu_lidar(o)
+    g["alpha"][0, 2] += 3e-4
+    g["intensity"][0, 2] += 3e-4
+    g["range"][0, 2] = 20.0 * (1 + 4e-4)
+    rep = bench.frame_parity([_sensor("lidar")], [g], [o])[0]
+    assert rep["rays_over_tolerance"] == 1
+    o2 = _oracle_lidar()
+    o2["slack_c"][0, 2] = 3e-4      # range: 4e-4 relative <= 1e-4 + 3e-4 / 0.9
+    rep = bench.frame_parity([_sensor("lidar")], [g], [o2])[0]
+    assert rep["rays_over_tolerance"] == 0 and rep["flagged_frac"] == 0.0
+    assert rep["cond_slack_over_tol_frac"] == 1.0 / (H * W)
